@@ -1,0 +1,218 @@
+"""FP64 CPU oracle of the multigrid curvature-energy sweep.
+
+TEST INFRASTRUCTURE ONLY: the plain restatement of the paper's method that
+the CUDA library is checked against.  Only ``tests/``, the package smoke check
+and the benchmark's CPU-baseline leg load it; the product path never does.
+It shares no code with the CUDA path.
+
+The numerics live in ``cm_oracle.c`` (plain C, IEEE double, optional OpenMP
+over the blocks of one colour, which the phase's snapshot semantics make
+order-independent).  This module compiles it with gcc and wraps it with
+ctypes and numpy.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "cm_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_SO = os.path.join(_BUILD, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+MEAN, GAUSS = 0, 1
+DEFAULT_G, DEFAULT_K = 9, 16
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle into oracle/_build/liboracle.so (gcc, -O2, OpenMP)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
+        tmp = _SO + f".{os.getpid()}.tmp"
+        cmd = ["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-fopenmp", "-fno-fast-math",
+               "-ffp-contract=off", _SRC, "-o", tmp, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _SO)
+    return _SO
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            L = ctypes.CDLL(_SO)
+            dp = ctypes.POINTER(ctypes.c_double)
+            ip = ctypes.POINTER(ctypes.c_int)
+            i, d = ctypes.c_int, ctypes.c_double
+            sig = {
+                "orc_plane_distance": (d, [dp, dp, dp, dp]),
+                "orc_direction_curvatures": (None, [dp, i, i, i, i, dp, dp]),
+                "orc_curvature": (d, [dp, i, i, i, i, i]),
+                "orc_curvature_map": (None, [dp, i, i, i, dp]),
+                "orc_energy": (d, [dp, dp, i, i, d, i]),
+                "orc_local_energy": (d, [dp, dp, i, i, i, i, i, i, d, d, i]),
+                "orc_ring_size": (i, [i, i, i, i, i, i]),
+                "orc_paper_candidate": (d, [dp, dp, i, i, i, i, d, i]),
+                "orc_block_min": (d, [dp, dp, i, i, i, i, i, i, d, i, i, i, i, dp]),
+                "orc_block_colour": (i, [i, i, i]),
+                "orc_auto_levels": (i, [i, i]),
+                "orc_phase": (i, [dp, dp, i, i, d, i, i, i, i, i, i, i, dp]),
+                "orc_level_sequential": (None, [dp, dp, i, i, d, i, i, i, i, i]),
+                "orc_cycle": (None, [dp, dp, i, i, d, i, i, i, i, i, i, i]),
+                "orc_solve": (i, [dp, i, i, d, i, i, i, d, dp, dp, i, i, i, i, i, dp, ip]),
+                "orc_num_threads": (i, []),
+                "orc_local_energy_batch": (None, [dp, dp, i, i, i, i, i, i, d, i, dp, i, dp]),
+            }
+            for name, (res, args) in sig.items():
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = L
+    return _lib
+
+
+def _dp(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+
+
+def plane_distance(X, Y, Z, O) -> float:
+    X, Y, Z, O = (_f64(v) for v in (X, Y, Z, O))
+    return lib().orc_plane_distance(_dp(X), _dp(Y), _dp(Z), _dp(O))
+
+
+def direction_curvatures(u, r: int, c: int):
+    u = _f64(u)
+    H, W = u.shape
+    kbar = np.zeros(4)
+    d = np.zeros(8)
+    lib().orc_direction_curvatures(_dp(u), H, W, r, c, _dp(kbar), _dp(d))
+    return kbar, d
+
+
+def curvature(u, r: int, c: int, kind: int) -> float:
+    u = _f64(u)
+    H, W = u.shape
+    return lib().orc_curvature(_dp(u), H, W, r, c, kind)
+
+
+def curvature_map(u, kind: int) -> np.ndarray:
+    u = _f64(u)
+    H, W = u.shape
+    out = np.zeros((H, W))
+    lib().orc_curvature_map(_dp(u), H, W, kind, _dp(out))
+    return out
+
+
+def energy(u, f, alpha: float, kind: int) -> float:
+    u, f = _f64(u), _f64(f)
+    H, W = u.shape
+    return lib().orc_energy(_dp(u), _dp(f), H, W, float(alpha), kind)
+
+
+def local_energy(u, f, r0, c0, bh, bw, c, alpha, kind) -> float:
+    u, f = _f64(u), _f64(f)
+    H, W = u.shape
+    return lib().orc_local_energy(_dp(u), _dp(f), H, W, r0, c0, bh, bw, float(c),
+                                  float(alpha), kind)
+
+
+def local_energy_batch(u, f, r0, c0, bh, bw, cs, alpha, kind) -> np.ndarray:
+    u, f, cs = _f64(u), _f64(f), _f64(cs)
+    H, W = u.shape
+    out = np.zeros(cs.size)
+    lib().orc_local_energy_batch(_dp(u), _dp(f), H, W, r0, c0, bh, bw, float(alpha), kind,
+                                 _dp(cs), cs.size, _dp(out))
+    return out
+
+
+def ring_size(H, W, r0, c0, bh, bw) -> int:
+    return lib().orc_ring_size(H, W, r0, c0, bh, bw)
+
+
+def paper_candidate(u, f, r, c, alpha, kind) -> float:
+    u, f = _f64(u), _f64(f)
+    H, W = u.shape
+    return lib().orc_paper_candidate(_dp(u), _dp(f), H, W, r, c, float(alpha), kind)
+
+
+def block_min(u, f, r0, c0, bh, bw, alpha, kind, G=DEFAULT_G, K=DEFAULT_K, use_paper=True):
+    """Returns (c, info) with info = dict(E_best, E_zero, c_fid, rho, S1, n_eval)."""
+    u, f = _f64(u), _f64(f)
+    H, W = u.shape
+    info = np.zeros(6)
+    c = lib().orc_block_min(_dp(u), _dp(f), H, W, r0, c0, bh, bw, float(alpha), kind, G, K,
+                            int(use_paper), _dp(info))
+    keys = ("E_best", "E_zero", "c_fid", "rho", "S1", "n_eval")
+    return c, dict(zip(keys, info.tolist()))
+
+
+def block_colour(bi, bj, ncolors) -> int:
+    return lib().orc_block_colour(bi, bj, ncolors)
+
+
+def auto_levels(H, W) -> int:
+    return lib().orc_auto_levels(H, W)
+
+
+def phase(u, f, alpha, kind, b, ncolors, k, G=DEFAULT_G, K=DEFAULT_K, use_paper=True):
+    """One (level, colour) phase from state u; returns (u_new, c_per_block)."""
+    u = _f64(u).copy()
+    f = _f64(f)
+    H, W = u.shape
+    nb = ((H + b - 1) // b) * ((W + b - 1) // b)
+    cs = np.zeros(nb)
+    lib().orc_phase(_dp(u), _dp(f), H, W, float(alpha), kind, b, ncolors, k, G, K,
+                    int(use_paper), _dp(cs))
+    return u, cs
+
+
+def level_sequential(u, f, alpha, kind, b, G=DEFAULT_G, K=DEFAULT_K, use_paper=True):
+    u = _f64(u).copy()
+    f = _f64(f)
+    H, W = u.shape
+    lib().orc_level_sequential(_dp(u), _dp(f), H, W, float(alpha), kind, b, G, K,
+                               int(use_paper))
+    return u
+
+
+def cycle(u, f, alpha, kind, levels=0, ncolors=2, G=DEFAULT_G, K=DEFAULT_K, use_paper=True,
+          sequential=False):
+    u = _f64(u).copy()
+    f = _f64(f)
+    H, W = u.shape
+    lib().orc_cycle(_dp(u), _dp(f), H, W, float(alpha), kind, levels, ncolors, G, K,
+                    int(use_paper), int(sequential))
+    return u
+
+
+def solve(f, alpha, kind, levels=0, cycles=20, tol=0.0, u0=None, ncolors=2, G=DEFAULT_G,
+          K=DEFAULT_K, use_paper=True, sequential=False):
+    """Alg. 3 outer loop.  Returns (u, trace, cycles_run, converged)."""
+    f = _f64(f)
+    H, W = f.shape
+    u = np.zeros_like(f)
+    trace = np.zeros(cycles + 1)
+    conv = ctypes.c_int(0)
+    u0p = None
+    if u0 is not None:
+        u0a = _f64(u0)
+        u0p = _dp(u0a)
+    n = lib().orc_solve(_dp(f), H, W, float(alpha), kind, levels, cycles, float(tol), u0p,
+                        _dp(u), ncolors, G, K, int(use_paper), int(sequential), _dp(trace),
+                        ctypes.byref(conv))
+    return u, trace[: n + 1], n, bool(conv.value)
+
+
+def num_threads() -> int:
+    return lib().orc_num_threads()

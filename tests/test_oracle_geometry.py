@@ -1,0 +1,198 @@
+"""Pins of the oracle's surface geometry (Sec. 2.1, Sec. 3, Table I).
+
+Each test checks the oracle against something other than itself: the
+paper's own closed form of one plane distance, hand-derived worked examples,
+analytic curvature of sphere caps and paraboloids, and exact invariances.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "worked_examples.json")
+
+
+def test_plane_distance_matches_eq_distance_to_tri():
+    """Eq. (distance to tri): for X = W, Y = E, Z = N the generic
+    d = XO . n/|n|, n = XZ x XY reduces to
+    (u_W + u_E - 2 u_O) / sqrt((u_W + u_E - 2 u_N)^2 + (u_E - u_W)^2 + 4)."""
+    rng = np.random.default_rng(1)
+    for _ in range(200):
+        uW, uE, uN, uO = rng.normal(size=4) * rng.choice([0.01, 1.0, 10.0])
+        X = [-1.0, 0.0, uW]
+        Y = [1.0, 0.0, uE]
+        Z = [0.0, -1.0, uN]
+        O = [0.0, 0.0, uO]
+        d = oracle.plane_distance(X, Y, Z, O)
+        ref = (uW + uE - 2 * uO) / math.sqrt((uW + uE - 2 * uN) ** 2 + (uE - uW) ** 2 + 4)
+        assert d == pytest.approx(ref, rel=1e-12, abs=1e-14)
+
+
+def test_plane_distance_is_euclidean_point_plane_distance():
+    """|d| equals the textbook point-to-plane distance of O to the plane
+    through X, Y, Z, for arbitrary points (not only grid neighbours)."""
+    rng = np.random.default_rng(2)
+    for _ in range(200):
+        X, Y, Z, O = rng.normal(size=(4, 3))
+        # plane a.x = b through X, Y, Z via least squares on homogeneous coords
+        M = np.array([np.append(P, 1.0) for P in (X, Y, Z)])
+        _, _, vt = np.linalg.svd(M)
+        p = vt[-1]
+        dist = abs(p[:3] @ O + p[3]) / np.linalg.norm(p[:3])
+        d = oracle.plane_distance(X, Y, Z, O)
+        assert abs(d) == pytest.approx(dist, rel=1e-9, abs=1e-12)
+
+
+@pytest.mark.parametrize("ex", json.load(open(GOLDEN))["examples"], ids=lambda e: e["name"])
+def test_worked_examples(ex):
+    u = np.array(ex["u"], dtype=np.float64)
+    kbar, d = oracle.direction_curvatures(u, 1, 1)
+    np.testing.assert_allclose(d, ex["d"], rtol=1e-12, atol=1e-14)
+    np.testing.assert_allclose(kbar, ex["kbar"], rtol=1e-12, atol=1e-14)
+    assert oracle.curvature(u, 1, 1, oracle.MEAN) == pytest.approx(ex["H"], rel=1e-12, abs=1e-14)
+    assert oracle.curvature(u, 1, 1, oracle.GAUSS) == pytest.approx(ex["K"], rel=1e-12, abs=1e-14)
+    f = u.copy()
+    f[1, 1] = ex["f_centre"]
+    cm = oracle.paper_candidate(u, f, 1, 1, ex["alpha"], oracle.MEAN)
+    cg = oracle.paper_candidate(u, f, 1, 1, ex["alpha"], oracle.GAUSS)
+    assert cm == pytest.approx(ex["c_paper_mean"], rel=1e-12, abs=1e-14)
+    assert cg == pytest.approx(ex["c_paper_gauss"], rel=1e-12, abs=1e-14)
+    assert np.mean(d) == pytest.approx(ex["c_half_mean"], rel=1e-12, abs=1e-14)
+
+
+def test_affine_images_have_zero_curvature():
+    """A plane is a minimal, developable surface: every tangent-plane distance
+    vanishes and H = K = 0 (Prop. 1 proof, Bernstein).  Dyadic slopes keep the
+    arithmetic exact.  With the clamp-to-edge boundary reading the replicated
+    border row/column is a kink, so this holds on interior pixels; a constant
+    image is flat everywhere and has zero curvature energy."""
+    y, x = np.mgrid[0:9, 0:11].astype(np.float64)
+    for a, b, c in [(0.25, -0.5, 0.125), (2.0, 0.0, -1.0), (0.0, 0.0, 0.75), (-3.5, 1.25, 8.0)]:
+        u = a * x + b * y + c
+        for kind in (oracle.MEAN, oracle.GAUSS):
+            cmap = oracle.curvature_map(u, kind)
+            assert np.all(cmap[1:-1, 1:-1] == 0.0)
+            for r in range(1, 8):
+                for cc in range(1, 10):
+                    kbar, d = oracle.direction_curvatures(u, r, cc)
+                    assert np.all(d == 0.0) and np.all(kbar == 0.0)
+    const = np.full((9, 11), 0.625)
+    for kind in (oracle.MEAN, oracle.GAUSS):
+        assert np.all(oracle.curvature_map(const, kind) == 0.0)
+        assert oracle.energy(const, const, 3.0, kind) == 0.0
+
+
+def sphere_cap(R, n):
+    y, x = np.mgrid[-n:n + 1, -n:n + 1].astype(np.float64)
+    return np.sqrt(R * R - x * x - y * y)
+
+
+@pytest.mark.parametrize("kind", [oracle.MEAN, oracle.GAUSS])
+def test_sphere_cap_closed_form_and_order(kind):
+    """Sphere of radius R (umbilic everywhere): |H| = 1/R, |K| = 1/R^2
+    (Table I definitions).  The relative error must fall as (h/R)^2."""
+    errs = []
+    Rs = [10.0, 20.0, 40.0, 80.0]
+    for R in Rs:
+        n = int(R / 2) + 2
+        u = sphere_cap(R, n)
+        cmap = oracle.curvature_map(u, kind)
+        yy, xx = np.mgrid[0:2 * n + 1, 0:2 * n + 1]
+        m = ((yy - n) ** 2 + (xx - n) ** 2 <= (R / 2) ** 2)
+        exact = 1.0 / R if kind == oracle.MEAN else 1.0 / (R * R)
+        # a cap bulging upward is concave: the sign convention gives H < 0, K > 0
+        if kind == oracle.MEAN:
+            assert np.all(cmap[m] < 0)
+        else:
+            assert np.all(cmap[m] > 0)
+        errs.append(np.max(np.abs(np.abs(cmap[m]) - exact)) / exact)
+    assert errs[-1] < 2e-4
+    orders = [math.log2(errs[i] / errs[i + 1]) for i in range(len(errs) - 1)]
+    for p in orders:
+        assert 1.8 < p < 2.2, orders
+
+
+def test_paraboloid_vertex():
+    """z = (a x^2 + b y^2)/2 at the vertex: principal curvatures a and b along
+    the axes.  For a = b (umbilic) the discrete values are exact; for a != b
+    the error is second order in the curvature scale."""
+    y, x = np.mgrid[-3:4, -3:4].astype(np.float64)
+    for a in (0.5, 0.25, -0.75):
+        u = 0.5 * a * (x * x + y * y)
+        kbar, _ = oracle.direction_curvatures(u, 3, 3)
+        np.testing.assert_allclose(kbar, [a] * 4, rtol=1e-13)
+        assert oracle.curvature(u, 3, 3, oracle.MEAN) == pytest.approx(a, rel=1e-13)
+        assert oracle.curvature(u, 3, 3, oracle.GAUSS) == pytest.approx(a * a, rel=1e-13)
+    errs = []
+    for s in (0.4, 0.2, 0.1, 0.05):
+        a, b = 1.5 * s, 0.5 * s
+        u = 0.5 * (a * x * x + b * y * y)
+        H = oracle.curvature(u, 3, 3, oracle.MEAN)
+        K = oracle.curvature(u, 3, 3, oracle.GAUSS)
+        errs.append((abs(H - (a + b) / 2) / ((a + b) / 2), abs(K - a * b) / (a * b)))
+    for i in range(len(errs) - 1):
+        for j in range(2):
+            p = math.log2(errs[i][j] / errs[i + 1][j])
+            assert 1.8 < p < 2.2
+
+
+def test_saddle_has_zero_mean_curvature_at_centre():
+    """z = a (x^2 - y^2)/2: opposite principal curvatures, H = 0 at the vertex
+    by symmetry; K < 0."""
+    y, x = np.mgrid[-3:4, -3:4].astype(np.float64)
+    u = 0.3 * (x * x - y * y)
+    assert abs(oracle.curvature(u, 3, 3, oracle.MEAN)) < 1e-15
+    assert oracle.curvature(u, 3, 3, oracle.GAUSS) < 0
+
+
+def test_translation_and_d4_invariance():
+    """F(u) is invariant under adding a constant to u and f (plane distances
+    depend on differences only) and under the eight symmetries of the square
+    (the plane set is closed under them)."""
+    rng = np.random.default_rng(3)
+    u = rng.random((13, 17))
+    f = rng.random((13, 17))
+    for kind in (oracle.MEAN, oracle.GAUSS):
+        E = oracle.energy(u, f, 7.0, kind)
+        assert oracle.energy(u + 0.37, f + 0.37, 7.0, kind) == pytest.approx(E, rel=1e-12)
+        for k in range(4):
+            for flip in (False, True):
+                v, g = np.rot90(u, k), np.rot90(f, k)
+                if flip:
+                    v, g = v[:, ::-1], g[:, ::-1]
+                assert oracle.energy(v, g, 7.0, kind) == pytest.approx(E, rel=1e-12)
+        # curvature map commutes with a transpose
+        np.testing.assert_allclose(oracle.curvature_map(u.T, kind),
+                                   oracle.curvature_map(u, kind).T, rtol=1e-12, atol=1e-14)
+
+
+def test_energy_is_sum_of_pixel_terms():
+    """Eq. (MCM)/(GCM): F is the plain sum of |kappa| + alpha/2 (u - f)^2;
+    a constant image has zero curvature energy and only the fidelity term."""
+    rng = np.random.default_rng(4)
+    u = rng.random((6, 7))
+    f = rng.random((6, 7))
+    for kind in (oracle.MEAN, oracle.GAUSS):
+        cmap = oracle.curvature_map(u, kind)
+        ref = np.sum(np.abs(cmap)) + 0.5 * 5.0 * np.sum((u - f) ** 2)
+        assert oracle.energy(u, f, 5.0, kind) == pytest.approx(ref, rel=1e-13)
+        c = np.full((6, 7), 0.3)
+        assert oracle.energy(c, f, 5.0, kind) == pytest.approx(2.5 * np.sum((0.3 - f) ** 2),
+                                                             rel=1e-13)
+
+
+def test_clamped_boundary_reading():
+    """Clamp-to-edge: a one-row image sees its N and S neighbours equal to
+    itself, so only the W-E line can bend; a 1x1 image is flat."""
+    u = np.array([[0.0, 1.0, 0.0, 2.0]])
+    kbar, d = oracle.direction_curvatures(u, 0, 1)
+    # N = S = O: the N-S line is flat
+    assert kbar[1] == 0.0
+    # W-E: delta = (0 + 0)/2 - 1 = -1 < 0 (a peak)
+    assert kbar[0] < 0
+    one = np.array([[0.4]])
+    assert oracle.curvature(one, 0, 0, oracle.MEAN) == 0.0
