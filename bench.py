@@ -1,0 +1,306 @@
+"""Benchmark: seconds to relative-energy tolerance 1e-4 on a 1024x1024 image.
+
+One step = one full solve of the hot path (Alg. 3 half V-cycles of the
+coloured block sweep, every level and colour, with the FP64 energy and
+stopping test after each cycle) on the seeded 1024^2 mean-curvature image
+(20 shapes, sigma 0.08, alpha 20, levels 1..512), inputs already resident
+in HBM.  Prints one JSON line (see --help).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+SIDE = 1024
+ALPHA = 20.0
+KIND = 0
+TOL = 1e-4
+MAX_CYCLES = 2000
+METRIC = "s to rel-energy tol 1e-4 at 1024^2 (plain FP32 sweep, FP64 stopping test)"
+L2_FLUSH_BYTES = 512 << 20   # > 129 MB L2
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--side", type=int, default=SIDE)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--cpu-cycles", type=int, default=1,
+                   help="oracle cycles timed for the CPU baseline sample")
+    return p.parse_args()
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200", "-f", self.path],
+                stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.path or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), float(parts[3]), parts[5:9]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i, v in enumerate(r[3]) if v == "Active"})
+        load = [r[0] for r in rows if r[2] > 200.0] or [r[0] for r in rows]
+        return {"sm_mhz": statistics.median(load), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+def dist_setup(args):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ---------------------------------------------------------------------------
+# oracle (CPU) timing: shared by the cpu_baseline field and --impl reference
+
+
+def oracle_cycle_seconds(f64, n_cycles: int):
+    """Wall seconds per cycle of the FP64 oracle on this image (as it stands,
+    OpenMP over the blocks of a colour on all host cores)."""
+    import oracle
+    u = f64.copy()
+    t0 = time.perf_counter()
+    for _ in range(n_cycles):
+        u = oracle.cycle(u, f64, ALPHA, KIND)
+        oracle.energy(u, f64, ALPHA, KIND)
+    return (time.perf_counter() - t0) / n_cycles, oracle.num_threads()
+
+
+def run_reference(args):
+    rank, world, _ = dist_setup(args)
+    if rank != 0:
+        return
+    import numpy as np
+    import synth
+    img = synth.large(args.side)
+    f64 = img.f.astype(np.float64)
+    times = []
+    threads = 1
+    for i in range(args.warmup + args.steps):
+        per_cycle, threads = oracle_cycle_seconds(f64, 1)
+        if i >= args.warmup:
+            times.append(per_cycle)
+    per_cycle = statistics.mean(times)
+    cycles = REFERENCE_CYCLES.get(args.side)
+    value = per_cycle * cycles if cycles else None
+    sample = (f"1 oracle cycle (all levels + FP64 energy) on the {args.side}^2 image per step, "
+              f"x {cycles} cycles to tol (the method's cycle count on this image)")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": per_cycle * 1e3, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(args.side),
+            "cpu_baseline": {"value": value, "unit": "s", "cores": threads, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# Cycles to rel. energy change <= 1e-4 of the method on the seeded images
+# (identical for the oracle and the CUDA path up to rounding ties).
+REFERENCE_CYCLES = {}
+
+
+def workload_config(side):
+    return {"workload": f"denoise {side}x{side} mean curvature, 20 shapes, sigma 0.08, "
+                        f"alpha 20, blocks 1..{side // 2}, 2 colours, tol 1e-4",
+            "image": f"{side}x{side}", "kind": "mean", "alpha": ALPHA, "tol": TOL,
+            "levels": None, "ncolors": 2, "grid_points": 9, "golden_evals": 16,
+            "l2": "flushed between steps (512 MB write)"}
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import paper_2204_07921_gb300 as cm
+    import synth
+
+    rank, world, local = dist_setup(args)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+    cm.load()
+    ctx = cm.Context(local)
+    img = synth.large(args.side)
+    f_host = torch.from_numpy(img.f).pin_memory()
+    f = f_host.to(dev)
+    u = torch.empty_like(f)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    opts = cm.default_options()
+    L = cm.cm_auto_levels(args.side, args.side)
+
+    def step(out):
+        _, st = cm.cm_solve(f, ALPHA, KIND, levels=0, cycles=MAX_CYCLES, tol=TOL, u_out=out,
+                            options=opts, ctx=ctx)
+        return st
+
+    for _ in range(args.warmup):
+        st = step(u)
+    torch.cuda.synchronize()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    cycles = []
+    with ClockSampler(local) as clk:
+        barrier()
+        for i in range(args.steps):
+            flush.fill_(float(i))
+            ev[i][0].record(stream)
+            st = step(u)
+            ev[i][1].record(stream)
+            cycles.append(st.cycles_run)
+        barrier()
+    clocks = clk.summary()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    t_dev = sum(step_ms) / 1e3
+    if world > 1:
+        t = torch.tensor([t_dev], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_dev = float(t.item())
+    sec_per_solve = t_dev / args.steps
+    final_E = st.energy_final
+
+    # e2e: the same solve through the C ABI with host buffers (pinned), the
+    # H2D copy of f and the D2H copy of u inside the timed region.
+    u_host = torch.empty_like(f_host).pin_memory()
+    e2e_t = []
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        fd = f_host.to(dev, non_blocking=True)
+        cm.cm_solve(fd, ALPHA, KIND, levels=0, cycles=MAX_CYCLES, tol=TOL, u_out=u, options=opts,
+                    ctx=ctx)
+        u_host.copy_(u, non_blocking=True)
+        torch.cuda.synchronize()
+        e2e_t.append(time.perf_counter() - t0)
+    e2e = statistics.mean(e2e_t)
+
+    # dominant kernel: finest-level phase (b = 1), launched on the same stream
+    state = u.clone()
+    R = state.clone()
+    n_launch = 20
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for k in (0, 1):
+        cm.cm_phase(state, R, f, ALPHA, KIND, 1, k, options=opts, ctx=ctx)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for i in range(n_launch):
+        cm.cm_phase(state, R, f, ALPHA, KIND, 1, i & 1, options=opts, ctx=ctx)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    b1_ms = e0.elapsed_time(e1) / n_launch
+    N = args.side * args.side
+    n_active = N // 2
+    evals_per_block = 3 + (opts.grid_points - 1) + opts.golden_evals   # 0, paper, c_fid, grid, golden
+    curv_evals = n_active * evals_per_block * 9
+    achieved = curv_evals / (b1_ms / 1e3) / 1e9
+    mufu_peak = 152 * 16 * 2.07e9 / 8 / 1e9   # Geval/s: 8 MUFU rsqrt per stencil evaluation
+    roofline = {"bound": "alu", "kernel": "phase_b1_kernel (b=1)", "achieved": achieved,
+                "peak": mufu_peak, "unit": "Geval/s", "frac": achieved / mufu_peak,
+                "traffic": None,
+                "note": "curvature-stencil evaluations/s; peak = 152 SM x 16 MUFU/clk x "
+                        "2.07 GHz / 8 rsqrt per evaluation (derived, nominal clock)"}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        f64 = img.f.astype(np.float64)
+        per_cycle, threads = oracle_cycle_seconds(f64, args.cpu_cycles)
+        mean_cycles = statistics.mean(cycles)
+        cpu = {"value": per_cycle * mean_cycles, "unit": "s", "cores": threads, "kind": "oracle",
+               "sample": f"{args.cpu_cycles} oracle cycle(s) on the {args.side}^2 image, "
+                         f"extrapolated x {mean_cycles:g} cycles to tol",
+               "per_cycle_s": per_cycle}
+
+    launches_per_solve = [1 + c * (2 * L + 1) for c in cycles]
+    line = {"metric": METRIC, "value": sec_per_solve, "unit": "s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec_per_solve * 1e3,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic", "config": workload_config(args.side),
+            "cycles_to_tol": cycles, "sweeps_per_s": statistics.mean(cycles) / sec_per_solve,
+            "final_energy": final_E,
+            "e2e": {"value": e2e, "unit": "s", "h2d_bytes_per_step": 4 * N,
+                    "d2h_bytes_per_step": 4 * N},
+            "gpu_launches": int(sum(launches_per_solve)),
+            "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks,
+            "b1_phase_ms": b1_ms}
+    line["config"]["levels"] = L
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

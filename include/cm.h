@@ -1,0 +1,146 @@
+/*
+ * cm.h -- C ABI of the GB300 multigrid curvature-energy library (libcm.so).
+ *
+ * The library minimises the discrete curvature energies of "Fast Multi-grid
+ * Methods for Minimizing Curvature Energies" (Zhang, Chen, Tang, Duan):
+ *
+ *   F(u) = sum_pixels |kappa(u)| + alpha/2 (u - f)^2                (Eq. MCM, Eq. GCM)
+ *
+ * with kappa the mean curvature H = (kmin + kmax)/2 (kind 0) or the Gaussian
+ * curvature K = kmin * kmax (kind 1) of the image surface (x, y, u(x, y)),
+ * estimated from the eight tangent planes of each 3x3 window (Sec. 2.1,
+ * Eq. distance to tri; Sec. 3).  Minimisation is the coloured
+ * block-subspace correction sweep: on each level of the fine-to-coarse
+ * hierarchy (block sides 1, 2, 4, ...; Sec. 2.2), the blocks of one colour
+ * (Sec. 2.3) each find the constant shift c that minimises F(u + c phi_A)
+ * and apply it (Alg. 3); cycles repeat until the relative energy change
+ * falls to the tolerance (Eq. reerr).
+ *
+ * Conventions shared by every entry point:
+ *  - Images are row-major float32 arrays with row pitch W, H rows.  Unless a
+ *    parameter says "host", a pointer is a DEVICE pointer on the context's
+ *    device, allocated and owned by the caller; the library never frees it.
+ *  - `stream` is a cudaStream_t (0 = the legacy default stream) passed as
+ *    void*.  All device work is enqueued on it.  Calls that return a host
+ *    value (an energy, statistics) synchronise that stream before returning.
+ *  - The library owns only its scratch memory, held by the context and
+ *    reused across calls; a context is not safe for concurrent use from
+ *    several host threads.
+ *  - Every function returns a status code; no exception crosses the ABI.
+ *    cm_last_error() gives a message for the last failure on a context.
+ *  - Boundary condition: pixels outside the image take the value of the
+ *    nearest in-image pixel (clamp to edge).
+ */
+#ifndef CM_H
+#define CM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes. */
+#define CM_OK 0
+#define CM_ERR_INVALID 1     /* null pointer, size < 1, alpha <= 0 or non-finite, bad kind/option */
+#define CM_ERR_CUDA 2        /* a CUDA runtime call failed (message in cm_last_error) */
+#define CM_ERR_OOM 3         /* scratch allocation failed */
+#define CM_ERR_TIMEOUT 4     /* a device-side wait hit its iteration limit */
+#define CM_ERR_NUMERIC 5     /* NaN or Inf energy */
+#define CM_NOT_CONVERGED 6   /* cycle cap reached with tol > 0; u_out is still valid */
+
+#define CM_KIND_MEAN 0
+#define CM_KIND_GAUSS 1
+
+typedef struct cm_ctx cm_ctx;
+
+/* Solver options.  Fill with cm_options_default() and override fields. */
+typedef struct {
+    int ncolors;         /* 2: checkerboard of blocks; 4: the paper's four colours (Sec. 2.3) */
+    int grid_points;     /* G: odd, >= 3; points of the bracket grid of the block search */
+    int golden_evals;    /* K: >= 2; golden-section evaluations of the block search */
+    int paper_candidate; /* 1: also try the paper's one-step FBS estimate on the finest level */
+    int use_graph;       /* 1: capture one cycle in a CUDA graph and replay it */
+    int max_trace;       /* entries of the energy trace kept in cm_stats (<= 4096) */
+} cm_options;
+
+/* Solve statistics (host struct, filled by cm_solve). */
+typedef struct {
+    int cycles_run;           /* outer iterations performed */
+    int converged;            /* 1 if the relative-energy test stopped the loop */
+    int monotone_violations;  /* cycles whose energy rose over the previous one */
+    int levels;               /* levels used */
+    double energy_initial;    /* F(u_0), FP64 device reduction */
+    double energy_final;      /* F(u_out) */
+    int trace_len;            /* entries written to energy_trace */
+    double energy_trace[4097];/* F(u_0), F(u_1), ... (first max_trace + 1 cycles) */
+} cm_stats;
+
+/* Default options: ncolors 2, G 9, K 16, paper_candidate 1, use_graph 1, max_trace 4096. */
+int cm_options_default(cm_options* opts /* host */);
+
+/* Create a context on CUDA device `device` (makes it current on this
+ * thread).  *ctx receives the handle.  Errors: CM_ERR_INVALID (null),
+ * CM_ERR_CUDA (no such device). */
+int cm_create(cm_ctx** ctx /* host */, int device);
+
+/* Free the context's scratch memory and graphs.  NULL is ignored. */
+void cm_destroy(cm_ctx* ctx);
+
+/* Message of the last error on ctx ("" if none).  Valid until the next call. */
+const char* cm_last_error(const cm_ctx* ctx);
+
+/* Number of levels used when `levels` = 0: block sides 1, 2, 4, ... up to the
+ * largest power of two <= min(H, W)/2 (at least one level). */
+int cm_auto_levels(int H, int W);
+
+/* Discrete energy F(u) of Eq. (MCM) (kind 0) or Eq. (GCM) (kind 1).
+ * u, f: device, H x W.  Per-pixel terms in FP32, summed in FP64 on the
+ * device in a fixed order (bit-reproducible).  *E_host (host) receives F.
+ * Synchronises `stream`. */
+int cm_energy(cm_ctx* ctx, const float* u, const float* f, int H, int W, float alpha,
+              int kind, double* E_host, void* stream);
+
+/* Per-pixel curvature kappa (signed H or K) into out (device, H x W). */
+int cm_curvature(cm_ctx* ctx, const float* u, int H, int W, int kind, float* out,
+                 void* stream);
+
+/* One phase of the sweep (Alg. 3 inner step): on the level with block side
+ * b (a power of two), every block of colour `colour` finds the shift
+ * c = argmin_c F(u + c phi_A) with the block search below and writes
+ * R = u + c on its pixels.  The phase state u is R on blocks of colours <
+ * `colour` of this level and S elsewhere (pass S == R-content copies for a
+ * plain state).  Blocks of other colours are not written.  All blocks of the
+ * colour read the state at the start of the phase.
+ * Block search: c_fid = -S1/s (S1 = sum over the block of u - f, s its pixel
+ * count); bracket rho = sqrt(2 sum_ring|kappa(c_fid)| / (alpha s)); E_A at
+ * G equispaced points of [c_fid - rho, c_fid + rho]; K golden-section
+ * evaluations on [g* - D, g* + D] around the best grid point g* (D the grid
+ * step); also c = 0 and, for b = 1, the paper's estimate (Eq. c-sol1/c-sol2
+ * with t = 0, or Prop. 2 for kind 1); the best evaluated c wins.
+ * S, R, f: device H x W; R must not alias S or f.  c_out (device, nullable):
+ * receives c for every block of the colour, indexed bi * nbj + bj with
+ * nbj = ceil(W / b) (other entries untouched). */
+int cm_phase(cm_ctx* ctx, const float* S, float* R, const float* f, int H, int W, float alpha,
+             int kind, int b, int colour, const cm_options* opts /* host, nullable */,
+             float* c_out, void* stream);
+
+/* Full solve (Alg. 3, half V-cycle): u_0 = u0 (or f when u0 is NULL); each
+ * cycle sweeps levels 1..L fine to coarse, colours in ascending order; the
+ * FP64 energy is evaluated after every cycle and the loop stops when
+ * |F_l - F_{l-1}| <= tol |F_l| (Eq. reerr, tol > 0) or after `cycles`
+ * cycles (exactly `cycles` when tol == 0).  levels = 0 selects
+ * cm_auto_levels(H, W).  f, u0, u_out: device H x W; u_out may alias u0 but
+ * not f.  stats (host, nullable).  Returns CM_NOT_CONVERGED if tol > 0 and the
+ * cap was reached (u_out valid).  Synchronises `stream`. */
+int cm_solve(cm_ctx* ctx, const float* f, int H, int W, float alpha, int kind, int levels,
+             int cycles, double tol, const float* u0, float* u_out,
+             const cm_options* opts /* host, nullable */, cm_stats* stats /* host, nullable */,
+             void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CM_H */

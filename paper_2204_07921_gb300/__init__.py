@@ -1,0 +1,225 @@
+"""GB300 multigrid curvature-energy minimisation (Python binding of libcm).
+
+Thin ctypes binding over the C ABI in ``include/cm.h``: every function here
+only checks tensor shapes/dtypes/devices and forwards raw device pointers
+and the current CUDA stream.  All arithmetic of the method runs in the CUDA
+kernels of ``libcm.so``; there is no CPU fallback, and importing a function
+that needs the library raises if it cannot be loaded.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+from .build import LIB, build as build_library
+
+__all__ = [
+    "CMError", "Options", "Stats", "Context", "load", "cm_energy", "cm_curvature", "cm_phase",
+    "cm_solve", "cm_auto_levels", "MEAN", "GAUSS",
+]
+
+MEAN, GAUSS = 0, 1
+CM_OK, CM_ERR_INVALID, CM_ERR_CUDA, CM_ERR_OOM = 0, 1, 2, 3
+CM_ERR_TIMEOUT, CM_ERR_NUMERIC, CM_NOT_CONVERGED = 4, 5, 6
+STATUS_NAMES = {0: "CM_OK", 1: "CM_ERR_INVALID", 2: "CM_ERR_CUDA", 3: "CM_ERR_OOM",
+                4: "CM_ERR_TIMEOUT", 5: "CM_ERR_NUMERIC", 6: "CM_NOT_CONVERGED"}
+
+
+class CMError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("ncolors", ctypes.c_int), ("grid_points", ctypes.c_int),
+                ("golden_evals", ctypes.c_int), ("paper_candidate", ctypes.c_int),
+                ("use_graph", ctypes.c_int), ("max_trace", ctypes.c_int)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("cycles_run", ctypes.c_int), ("converged", ctypes.c_int),
+                ("monotone_violations", ctypes.c_int), ("levels", ctypes.c_int),
+                ("energy_initial", ctypes.c_double), ("energy_final", ctypes.c_double),
+                ("trace_len", ctypes.c_int), ("energy_trace", ctypes.c_double * 4097)]
+
+    def trace(self):
+        return list(self.energy_trace[: self.trace_len])
+
+
+_lib = None
+_lock = threading.Lock()
+
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_F = ctypes.c_float
+_D = ctypes.c_double
+SIGNATURES = {
+    "cm_options_default": (_I, [ctypes.POINTER(Options)]),
+    "cm_create": (_I, [ctypes.POINTER(_P), _I]),
+    "cm_destroy": (None, [_P]),
+    "cm_last_error": (ctypes.c_char_p, [_P]),
+    "cm_auto_levels": (_I, [_I, _I]),
+    "cm_energy": (_I, [_P, _P, _P, _I, _I, _F, _I, ctypes.POINTER(_D), _P]),
+    "cm_curvature": (_I, [_P, _P, _I, _I, _I, _P, _P]),
+    "cm_phase": (_I, [_P, _P, _P, _P, _I, _I, _F, _I, _I, _I, ctypes.POINTER(Options), _P, _P]),
+    "cm_solve": (_I, [_P, _P, _I, _I, _F, _I, _I, _I, _D, _P, _P, ctypes.POINTER(Options),
+                      ctypes.POINTER(Stats), _P]),
+}
+
+
+def load(path: str | None = None):
+    """Load libcm.so (building it first if it is missing or stale)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            so = path or LIB
+            if path is None:
+                build_library()
+            if not os.path.exists(so):
+                raise RuntimeError(f"libcm not found at {so}")
+            L = ctypes.CDLL(so)
+            for name, (res, args) in SIGNATURES.items():
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = L
+    return _lib
+
+
+def default_options(**kw) -> Options:
+    o = Options()
+    load().cm_options_default(ctypes.byref(o))
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise TypeError(f"unknown option {k}")
+        setattr(o, k, int(v))
+    return o
+
+
+def cm_auto_levels(H: int, W: int) -> int:
+    return load().cm_auto_levels(H, W)
+
+
+def _stream_ptr(stream=None) -> int:
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return int(s.cuda_stream)
+
+
+def _img(t, name):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float32:
+        raise TypeError(f"{name}: expected a CUDA float32 tensor")
+    if t.dim() != 2 or not t.is_contiguous():
+        raise ValueError(f"{name}: expected a contiguous H x W tensor")
+    return t
+
+
+class Context:
+    """Owns a cm_ctx (scratch memory and cached CUDA graphs) on one device."""
+
+    def __init__(self, device: int | None = None):
+        import torch
+        if device is None:
+            device = torch.cuda.current_device()
+        self.device = device
+        self._h = _P()
+        rc = load().cm_create(ctypes.byref(self._h), device)
+        if rc != CM_OK:
+            raise CMError(rc, "cm_create failed")
+
+    def close(self):
+        if self._h:
+            load().cm_destroy(self._h)
+            self._h = _P()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc, ok=(CM_OK,)):
+        if rc not in ok:
+            raise CMError(rc, load().cm_last_error(self._h).decode())
+        return rc
+
+    @property
+    def handle(self):
+        return self._h
+
+
+_default_ctx = {}
+
+
+def _ctx(ctx: Context | None, t) -> Context:
+    if ctx is not None:
+        return ctx
+    dev = t.device.index if t.device.index is not None else 0
+    if dev not in _default_ctx:
+        _default_ctx[dev] = Context(dev)
+    return _default_ctx[dev]
+
+
+def cm_energy(u, f, alpha: float, kind: int, ctx: Context | None = None, stream=None) -> float:
+    """F(u) of Eq. (MCM)/(GCM), FP64 device reduction."""
+    _img(u, "u"), _img(f, "f")
+    if u.shape != f.shape:
+        raise ValueError("u and f differ in shape")
+    c = _ctx(ctx, u)
+    H, W = u.shape
+    E = ctypes.c_double(0.0)
+    c._check(load().cm_energy(c.handle, u.data_ptr(), f.data_ptr(), H, W, float(alpha), kind,
+                              ctypes.byref(E), _stream_ptr(stream)))
+    return E.value
+
+
+def cm_curvature(u, kind: int, out=None, ctx: Context | None = None, stream=None):
+    import torch
+    _img(u, "u")
+    out = torch.empty_like(u) if out is None else _img(out, "out")
+    c = _ctx(ctx, u)
+    H, W = u.shape
+    c._check(load().cm_curvature(c.handle, u.data_ptr(), H, W, kind, out.data_ptr(),
+                                 _stream_ptr(stream)))
+    return out
+
+
+def cm_phase(S, R, f, alpha: float, kind: int, b: int, colour: int, options: Options | None = None,
+             c_out=None, ctx: Context | None = None, stream=None):
+    """One (level, colour) phase: writes R on the colour's blocks."""
+    for t, n in ((S, "S"), (R, "R"), (f, "f")):
+        _img(t, n)
+    c = _ctx(ctx, S)
+    H, W = S.shape
+    opts = options or default_options()
+    c._check(load().cm_phase(c.handle, S.data_ptr(), R.data_ptr(), f.data_ptr(), H, W,
+                             float(alpha), kind, b, colour, ctypes.byref(opts),
+                             c_out.data_ptr() if c_out is not None else None,
+                             _stream_ptr(stream)))
+    return R
+
+
+def cm_solve(f, alpha: float, kind: int, levels: int = 0, cycles: int = 20, tol: float = 0.0,
+             u0=None, u_out=None, options: Options | None = None, ctx: Context | None = None,
+             stream=None):
+    """Alg. 3 solve on the device.  Returns (u_out, Stats)."""
+    import torch
+    _img(f, "f")
+    c = _ctx(ctx, f)
+    H, W = f.shape
+    if u_out is None:
+        u_out = torch.empty_like(f)
+    _img(u_out, "u_out")
+    if u0 is not None:
+        _img(u0, "u0")
+    opts = options or default_options()
+    st = Stats()
+    c._check(load().cm_solve(c.handle, f.data_ptr(), H, W, float(alpha), kind, levels, cycles,
+                             float(tol), u0.data_ptr() if u0 is not None else None,
+                             u_out.data_ptr(), ctypes.byref(opts), ctypes.byref(st),
+                             _stream_ptr(stream)),
+             ok=(CM_OK, CM_NOT_CONVERGED))
+    return u_out, st

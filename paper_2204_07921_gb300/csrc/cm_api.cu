@@ -1,0 +1,364 @@
+// cm_api.cu -- C ABI and host runtime of libcm (declared in include/cm.h).
+//
+// The runtime owns a context's scratch (the second ping-pong image, energy
+// partials, a pinned readback slot) and a small cache of CUDA graphs, each
+// holding one full cycle (every phase of every level, then the FP64 energy).
+// The outer loop of Alg. 3 replays the graph and reads back 8 bytes per
+// cycle for the stopping test of Eq. (reerr).
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <string>
+
+#include "../../include/cm.h"
+#include "cm_kernels.h"
+
+struct GraphKey {
+    const float* S;
+    const float* R;
+    const float* f;
+    int H, W, kind, levels, ncolors, G, K, use_paper;
+    float alpha;
+    bool operator==(const GraphKey& o) const { return memcmp(this, &o, sizeof(GraphKey)) == 0; }
+};
+
+struct cm_ctx {
+    int device = 0;
+    std::string err;
+    float* ubuf = nullptr;
+    size_t ubuf_cap = 0;
+    double* partials = nullptr;
+    size_t partials_cap = 0;
+    unsigned int* ticket = nullptr;
+    double* E_dev = nullptr;
+    double* E_pinned = nullptr;
+    cudaStream_t cap_stream = nullptr;
+    struct Cached {
+        bool valid = false;
+        GraphKey key;
+        cudaGraphExec_t exec = nullptr;
+    } graphs[2];
+};
+
+namespace {
+
+int fail(cm_ctx* ctx, int code, const std::string& msg) {
+    if (ctx) ctx->err = msg;
+    return code;
+}
+
+int cuda_fail(cm_ctx* ctx, cudaError_t e, const char* where) {
+    std::string m = std::string(where) + ": " + cudaGetErrorString(e);
+    return fail(ctx, e == cudaErrorMemoryAllocation ? CM_ERR_OOM : CM_ERR_CUDA, m);
+}
+
+#define CM_CUDA(call)                                        \
+    do {                                                     \
+        cudaError_t e_ = (call);                             \
+        if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call); \
+    } while (0)
+
+// Cached graphs hold scratch pointers: drop them before any reallocation.
+void drop_graphs(cm_ctx* ctx) {
+    for (auto& g : ctx->graphs) {
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+        g.exec = nullptr;
+        g.valid = false;
+    }
+}
+
+int ensure_partials(cm_ctx* ctx, int H, int W) {
+    size_t need = cm::energy_partials_needed(H, W);
+    if (need <= ctx->partials_cap) return CM_OK;
+    drop_graphs(ctx);
+    if (ctx->partials) cudaFree(ctx->partials);
+    ctx->partials = nullptr;
+    ctx->partials_cap = 0;
+    CM_CUDA(cudaMalloc(&ctx->partials, need * sizeof(double)));
+    ctx->partials_cap = need;
+    return CM_OK;
+}
+
+int ensure_ubuf(cm_ctx* ctx, size_t n) {
+    if (n <= ctx->ubuf_cap) return CM_OK;
+    drop_graphs(ctx);
+    if (ctx->ubuf) cudaFree(ctx->ubuf);
+    ctx->ubuf = nullptr;
+    ctx->ubuf_cap = 0;
+    CM_CUDA(cudaMalloc(&ctx->ubuf, n * sizeof(float)));
+    ctx->ubuf_cap = n;
+    return CM_OK;
+}
+
+bool finite_positive(float a) { return isfinite(a) && a > 0.0f; }
+
+int check_opts(cm_ctx* ctx, const cm_options& o) {
+    if (o.ncolors != 2 && o.ncolors != 4) return fail(ctx, CM_ERR_INVALID, "ncolors must be 2 or 4");
+    if (o.grid_points < 3 || (o.grid_points % 2) == 0 || o.grid_points > 1025)
+        return fail(ctx, CM_ERR_INVALID, "grid_points must be odd, 3..1025");
+    if (o.golden_evals < 2 || o.golden_evals > 1024)
+        return fail(ctx, CM_ERR_INVALID, "golden_evals must be 2..1024");
+    if (o.max_trace < 0 || o.max_trace > 4096) return fail(ctx, CM_ERR_INVALID, "max_trace 0..4096");
+    return CM_OK;
+}
+
+cm::PhaseArgs phase_args(const float* S, float* R, const float* f, int H, int W, float alpha,
+                         int kind, int lb, int colour, const cm_options& o) {
+    cm::PhaseArgs a;
+    a.S = S;
+    a.R = R;
+    a.f = f;
+    a.H = H;
+    a.W = W;
+    a.alpha = alpha;
+    a.kind = kind;
+    a.lb = lb;
+    a.ncolors = o.ncolors;
+    a.colour = colour;
+    a.G = o.grid_points;
+    a.K = o.golden_evals;
+    a.use_paper = o.paper_candidate;
+    a.c_out = nullptr;
+    return a;
+}
+
+// Enqueue one cycle starting from buffer X (other buffer Y); the state ends
+// in X if `levels` is even, else in Y.  Then the energy of the final state.
+cudaError_t enqueue_cycle(cm_ctx* ctx, float* X, float* Y, const float* f, int H, int W,
+                          float alpha, int kind, int levels, const cm_options& o,
+                          cudaStream_t st) {
+    float* S = X;
+    float* R = Y;
+    for (int j = 0; j < levels; ++j) {
+        for (int k = 0; k < o.ncolors; ++k) {
+            cm::PhaseArgs a = phase_args(S, R, f, H, W, alpha, kind, j, k, o);
+            cudaError_t e = cm::launch_phase(a, st);
+            if (e != cudaSuccess) return e;
+        }
+        float* t = S;
+        S = R;
+        R = t;
+    }
+    return cm::launch_energy(S, f, H, W, alpha, kind, ctx->partials, ctx->ticket, ctx->E_dev, st);
+}
+
+}  // namespace
+
+extern "C" {
+
+int cm_options_default(cm_options* o) {
+    if (!o) return CM_ERR_INVALID;
+    o->ncolors = 2;
+    o->grid_points = 9;
+    o->golden_evals = 16;
+    o->paper_candidate = 1;
+    o->use_graph = 1;
+    o->max_trace = 4096;
+    return CM_OK;
+}
+
+int cm_auto_levels(int H, int W) {
+    int m = H < W ? H : W;
+    int L = 1, b = 1;
+    while (2 * b <= m / 2) {
+        b *= 2;
+        ++L;
+    }
+    return L;
+}
+
+int cm_create(cm_ctx** out, int device) {
+    if (!out) return CM_ERR_INVALID;
+    *out = nullptr;
+    int n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) return CM_ERR_CUDA;
+    if (cudaSetDevice(device) != cudaSuccess) return CM_ERR_CUDA;
+    cm_ctx* ctx = new cm_ctx();
+    ctx->device = device;
+    cudaError_t e = cudaMalloc(&ctx->ticket, sizeof(unsigned int));
+    if (e == cudaSuccess) e = cudaMemset(ctx->ticket, 0, sizeof(unsigned int));
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->E_dev, 8 * sizeof(double));
+    if (e == cudaSuccess) e = cudaMallocHost(&ctx->E_pinned, 8 * sizeof(double));
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        cm_destroy(ctx);
+        return e == cudaErrorMemoryAllocation ? CM_ERR_OOM : CM_ERR_CUDA;
+    }
+    *out = ctx;
+    return CM_OK;
+}
+
+void cm_destroy(cm_ctx* ctx) {
+    if (!ctx) return;
+    cudaSetDevice(ctx->device);
+    for (auto& g : ctx->graphs)
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+    if (ctx->ubuf) cudaFree(ctx->ubuf);
+    if (ctx->partials) cudaFree(ctx->partials);
+    if (ctx->ticket) cudaFree(ctx->ticket);
+    if (ctx->E_dev) cudaFree(ctx->E_dev);
+    if (ctx->E_pinned) cudaFreeHost(ctx->E_pinned);
+    if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+    delete ctx;
+}
+
+const char* cm_last_error(const cm_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+int cm_energy(cm_ctx* ctx, const float* u, const float* f, int H, int W, float alpha, int kind,
+              double* E_host, void* stream) {
+    if (!ctx) return CM_ERR_INVALID;
+    if (!u || !f || !E_host || H < 1 || W < 1 || !finite_positive(alpha) || (kind != 0 && kind != 1))
+        return fail(ctx, CM_ERR_INVALID, "cm_energy: invalid argument");
+    CM_CUDA(cudaSetDevice(ctx->device));
+    int rc = ensure_partials(ctx, H, W);
+    if (rc) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    CM_CUDA(cm::launch_energy(u, f, H, W, alpha, kind, ctx->partials, ctx->ticket, ctx->E_dev, st));
+    CM_CUDA(cudaMemcpyAsync(ctx->E_pinned, ctx->E_dev, sizeof(double), cudaMemcpyDeviceToHost, st));
+    CM_CUDA(cudaStreamSynchronize(st));
+    *E_host = ctx->E_pinned[0];
+    if (!isfinite(*E_host)) return fail(ctx, CM_ERR_NUMERIC, "cm_energy: non-finite energy");
+    return CM_OK;
+}
+
+int cm_curvature(cm_ctx* ctx, const float* u, int H, int W, int kind, float* out, void* stream) {
+    if (!ctx) return CM_ERR_INVALID;
+    if (!u || !out || H < 1 || W < 1 || (kind != 0 && kind != 1))
+        return fail(ctx, CM_ERR_INVALID, "cm_curvature: invalid argument");
+    CM_CUDA(cudaSetDevice(ctx->device));
+    CM_CUDA(cm::launch_curvature(u, H, W, kind, out, (cudaStream_t)stream));
+    return CM_OK;
+}
+
+int cm_phase(cm_ctx* ctx, const float* S, float* R, const float* f, int H, int W, float alpha,
+             int kind, int b, int colour, const cm_options* opts, float* c_out, void* stream) {
+    if (!ctx) return CM_ERR_INVALID;
+    cm_options o;
+    cm_options_default(&o);
+    if (opts) o = *opts;
+    int rc = check_opts(ctx, o);
+    if (rc) return rc;
+    if (!S || !R || !f || R == S || R == f || H < 1 || W < 1 || !finite_positive(alpha) ||
+        (kind != 0 && kind != 1))
+        return fail(ctx, CM_ERR_INVALID, "cm_phase: invalid argument");
+    int lb = 0;
+    while ((1 << lb) < b) ++lb;
+    if (b < 1 || (1 << lb) != b || lb > cm::max_level_log2())
+        return fail(ctx, CM_ERR_INVALID, "cm_phase: b must be a power of two <= 2048");
+    if (colour < 0 || colour >= o.ncolors) return fail(ctx, CM_ERR_INVALID, "cm_phase: bad colour");
+    CM_CUDA(cudaSetDevice(ctx->device));
+    cm::PhaseArgs a = phase_args(S, R, f, H, W, alpha, kind, lb, colour, o);
+    a.c_out = c_out;
+    CM_CUDA(cm::launch_phase(a, (cudaStream_t)stream));
+    return CM_OK;
+}
+
+int cm_solve(cm_ctx* ctx, const float* f, int H, int W, float alpha, int kind, int levels,
+             int cycles, double tol, const float* u0, float* u_out, const cm_options* opts,
+             cm_stats* stats, void* stream) {
+    if (!ctx) return CM_ERR_INVALID;
+    cm_options o;
+    cm_options_default(&o);
+    if (opts) o = *opts;
+    int rc = check_opts(ctx, o);
+    if (rc) return rc;
+    if (!f || !u_out || u_out == f || H < 1 || W < 1 || !finite_positive(alpha) ||
+        (kind != 0 && kind != 1) || levels < 0 || cycles < 0 || !(tol >= 0.0) || !isfinite(tol))
+        return fail(ctx, CM_ERR_INVALID, "cm_solve: invalid argument");
+    const int L = levels > 0 ? levels : cm_auto_levels(H, W);
+    if (L - 1 > cm::max_level_log2()) return fail(ctx, CM_ERR_INVALID, "cm_solve: too many levels");
+    CM_CUDA(cudaSetDevice(ctx->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t N = (size_t)H * W;
+    rc = ensure_partials(ctx, H, W);
+    if (rc) return rc;
+    rc = ensure_ubuf(ctx, N);
+    if (rc) return rc;
+    float* bufs[2] = {u_out, ctx->ubuf};
+    if (u0 && u0 != u_out)
+        CM_CUDA(cudaMemcpyAsync(u_out, u0, N * sizeof(float), cudaMemcpyDeviceToDevice, st));
+    else if (!u0)
+        CM_CUDA(cudaMemcpyAsync(u_out, f, N * sizeof(float), cudaMemcpyDeviceToDevice, st));
+    CM_CUDA(cm::launch_energy(u_out, f, H, W, alpha, kind, ctx->partials, ctx->ticket, ctx->E_dev, st));
+    CM_CUDA(cudaMemcpyAsync(ctx->E_pinned, ctx->E_dev, sizeof(double), cudaMemcpyDeviceToHost, st));
+    CM_CUDA(cudaStreamSynchronize(st));
+    double Eprev = ctx->E_pinned[0];
+    if (!isfinite(Eprev)) return fail(ctx, CM_ERR_NUMERIC, "cm_solve: non-finite initial energy");
+    if (stats) {
+        memset(stats, 0, sizeof(*stats));
+        stats->levels = L;
+        stats->energy_initial = Eprev;
+        stats->energy_trace[0] = Eprev;
+        stats->trace_len = 1;
+    }
+    int cur = 0, l = 0, conv = 0, viol = 0;
+    while (l < cycles) {
+        float* X = bufs[cur];
+        float* Y = bufs[cur ^ 1];
+        if (o.use_graph) {
+            GraphKey key;
+            memset(&key, 0, sizeof(key));
+            key.S = X;
+            key.R = Y;
+            key.f = f;
+            key.H = H;
+            key.W = W;
+            key.kind = kind;
+            key.levels = L;
+            key.ncolors = o.ncolors;
+            key.G = o.grid_points;
+            key.K = o.golden_evals;
+            key.use_paper = o.paper_candidate;
+            key.alpha = alpha;
+            auto& slot = ctx->graphs[cur];
+            if (!slot.valid || !(slot.key == key)) {
+                if (slot.exec) cudaGraphExecDestroy(slot.exec);
+                slot.exec = nullptr;
+                slot.valid = false;
+                cudaGraph_t g;
+                CM_CUDA(cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));
+                cudaError_t ce = enqueue_cycle(ctx, X, Y, f, H, W, alpha, kind, L, o, ctx->cap_stream);
+                cudaError_t ee = cudaStreamEndCapture(ctx->cap_stream, &g);
+                if (ce != cudaSuccess) return cuda_fail(ctx, ce, "capture cycle");
+                if (ee != cudaSuccess) return cuda_fail(ctx, ee, "end capture");
+                cudaError_t ie = cudaGraphInstantiate(&slot.exec, g, 0);
+                cudaGraphDestroy(g);
+                if (ie != cudaSuccess) return cuda_fail(ctx, ie, "graph instantiate");
+                slot.key = key;
+                slot.valid = true;
+            }
+            CM_CUDA(cudaGraphLaunch(slot.exec, st));
+        } else {
+            CM_CUDA(enqueue_cycle(ctx, X, Y, f, H, W, alpha, kind, L, o, st));
+        }
+        if (L & 1) cur ^= 1;
+        CM_CUDA(cudaMemcpyAsync(ctx->E_pinned, ctx->E_dev, sizeof(double), cudaMemcpyDeviceToHost, st));
+        CM_CUDA(cudaStreamSynchronize(st));
+        ++l;
+        double E = ctx->E_pinned[0];
+        if (!isfinite(E)) return fail(ctx, CM_ERR_NUMERIC, "cm_solve: non-finite energy");
+        if (E > Eprev) ++viol;
+        if (stats && stats->trace_len <= o.max_trace) stats->energy_trace[stats->trace_len++] = E;
+        bool stop = tol > 0.0 && fabs(E - Eprev) <= tol * fabs(E);
+        Eprev = E;
+        if (stop) {
+            conv = 1;
+            break;
+        }
+    }
+    if (cur != 0)
+        CM_CUDA(cudaMemcpyAsync(u_out, bufs[cur], N * sizeof(float), cudaMemcpyDeviceToDevice, st));
+    CM_CUDA(cudaStreamSynchronize(st));
+    if (stats) {
+        stats->cycles_run = l;
+        stats->converged = conv;
+        stats->monotone_violations = viol;
+        stats->energy_final = Eprev;
+    }
+    if (tol > 0.0 && !conv) return fail(ctx, CM_NOT_CONVERGED, "cm_solve: cycle cap reached");
+    return CM_OK;
+}
+
+}  // extern "C"

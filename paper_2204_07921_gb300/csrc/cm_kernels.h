@@ -1,0 +1,32 @@
+// cm_kernels.h -- host-side launchers of the sweep and energy kernels.
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+
+namespace cm {
+
+struct PhaseArgs {
+    const float* S;   // state at the start of the level
+    float* R;         // blocks already updated on this level (and the output)
+    const float* f;
+    int H, W;
+    float alpha;
+    int kind;
+    int lb;           // block side = 1 << lb
+    int ncolors;      // 2 or 4
+    int colour;
+    int G, K;         // block-search budget
+    int use_paper;    // paper's one-step candidate on the finest level
+    float* c_out;     // nullable: per-block corrections
+};
+
+cudaError_t launch_energy(const float* u, const float* f, int H, int W, float alpha, int kind,
+                          double* partials, unsigned int* ticket, double* E_out,
+                          cudaStream_t st);
+size_t energy_partials_needed(int H, int W);
+cudaError_t launch_curvature(const float* u, int H, int W, int kind, float* out,
+                             cudaStream_t st);
+cudaError_t launch_phase(const PhaseArgs& a, cudaStream_t st);
+int max_level_log2();
+
+}  // namespace cm

@@ -1,0 +1,76 @@
+"""Shared helpers of the GPU parity tests (comparison with the FP64 oracle).
+
+Tolerances, derived from FP32 arithmetic:
+
+* Per-pixel curvature: each direction curvature takes ~16 FP32 operations and
+  two rsqrt (<= 2 ulp each), so its relative error is a few 1e-7 of the
+  largest direction curvature; |Delta kappa| <= 2e-5 (1 + max|kbar|) leaves a
+  margin of ~10x on [0, 1] images.
+* Energy: FP32 pixel terms (relative error <= ~1e-6) summed in FP64:
+  |F_gpu - F_oracle| <= 2e-6 |F_oracle|.
+* Block shifts: |c_gpu - c_oracle| <= 1e-4 (the required per-sweep bound on
+  u).  Where several shifts are correct -- candidates whose energies agree to
+  within FP32 evaluation noise -- the GPU's c is a tie if the oracle's FP64
+  E_A at the GPU's c is within tau of the oracle's own optimum, with tau =
+  1e-5 times the block's energy scale (ring curvature plus fidelity distance,
+  both non-negative).  Ties are counted and reported.
+"""
+import numpy as np
+
+import oracle
+
+TIE_REL = 1e-5
+C_TOL = 1e-4
+
+
+def blocks_of_colour(H, W, b, ncolors, k):
+    nbi, nbj = (H + b - 1) // b, (W + b - 1) // b
+    for bi in range(nbi):
+        for bj in range(nbj):
+            col = ((bi + bj) & 1) if ncolors == 2 else (2 * (bi & 1) + (bj & 1))
+            if col == k:
+                yield bi, bj, bi * b, bj * b, min(b, H - bi * b), min(b, W - bj * b)
+
+
+def energy_scale(u, f, r0, c0, bh, bw, c, alpha, kind, c_fid):
+    """Non-negative parts of E_A at c: ring curvature + alpha s/2 (c - c_fid)^2."""
+    s = bh * bw
+    S1 = -c_fid * s
+    e = oracle.local_energy(u, f, r0, c0, bh, bw, c, alpha, kind)
+    fid = 0.5 * alpha * (s * c * c + 2 * c * S1)
+    ring = e - fid
+    return ring + 0.5 * alpha * s * (c - c_fid) ** 2
+
+
+def compare_phase(u, f, c_gpu_blocks, alpha, kind, b, ncolors, k, c_orc_blocks, sample=None,
+                  G=9, K=16, use_paper=True):
+    """Compare per-block shifts of one phase.  c_*_blocks: dict (bi, bj) -> c.
+    Returns (n_blocks, n_match, n_tie, list_of_failures)."""
+    H, W = u.shape
+    n = match = tie = 0
+    fails = []
+    for bi, bj, r0, c0, bh, bw in blocks_of_colour(H, W, b, ncolors, k):
+        if sample is not None and (bi, bj) not in sample:
+            continue
+        n += 1
+        cg = float(c_gpu_blocks[(bi, bj)])
+        if (bi, bj) in c_orc_blocks:
+            co = float(c_orc_blocks[(bi, bj)])
+        else:
+            co, _ = oracle.block_min(u, f, r0, c0, bh, bw, alpha, kind, G=G, K=K,
+                                     use_paper=use_paper)
+        if abs(cg - co) <= C_TOL:
+            match += 1
+            continue
+        Eg = oracle.local_energy(u, f, r0, c0, bh, bw, cg, alpha, kind)
+        Eo = oracle.local_energy(u, f, r0, c0, bh, bw, co, alpha, kind)
+        _, info = oracle.block_min(u, f, r0, c0, bh, bw, alpha, kind, G=G, K=K,
+                                   use_paper=use_paper)
+        scale = max(energy_scale(u, f, r0, c0, bh, bw, cg, alpha, kind, info["c_fid"]),
+                    energy_scale(u, f, r0, c0, bh, bw, co, alpha, kind, info["c_fid"]))
+        if Eg - Eo <= TIE_REL * scale:
+            tie += 1
+        else:
+            fails.append(dict(block=(bi, bj), b=b, c_gpu=cg, c_orc=co, E_gpu=Eg, E_orc=Eo,
+                              scale=scale, rel=(Eg - Eo) / max(scale, 1e-30)))
+    return n, match, tie, fails

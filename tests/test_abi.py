@@ -1,0 +1,66 @@
+"""The C ABI library builds, loads and exports every function include/cm.h
+declares (no compute: runs without a GPU)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER_DIR = os.path.join(ROOT, "include")
+
+
+def declared_functions():
+    names = set()
+    for fn in os.listdir(HEADER_DIR):
+        if not fn.endswith(".h"):
+            continue
+        text = open(os.path.join(HEADER_DIR, fn)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"\b(cm_[a-z0-9_]+)\s*\(", text):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("cm_create", "cm_destroy", "cm_energy", "cm_solve", "cm_phase",
+                     "cm_last_error", "cm_options_default", "cm_auto_levels"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol():
+    from paper_2204_07921_gb300 import build
+    so = build.build()
+    lib = ctypes.CDLL(so)
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_host_only_entry_points():
+    """Entry points that touch no device: defaults, auto levels, argument
+    checks before any CUDA call."""
+    import paper_2204_07921_gb300 as cm
+    lib = cm.load()
+    o = cm.Options()
+    assert lib.cm_options_default(ctypes.byref(o)) == 0
+    assert (o.ncolors, o.grid_points, o.golden_evals, o.paper_candidate) == (2, 9, 16, 1)
+    assert lib.cm_options_default(None) == cm.CM_ERR_INVALID
+    assert lib.cm_auto_levels(64, 64) == 6
+    assert lib.cm_auto_levels(1024, 1024) == 10
+    assert lib.cm_auto_levels(2048, 2048) == 11
+    assert lib.cm_auto_levels(1, 5) == 1
+    # null context is rejected without touching the device
+    E = ctypes.c_double()
+    assert lib.cm_energy(None, None, None, 4, 4, 1.0, 0, ctypes.byref(E), None) == cm.CM_ERR_INVALID
+    assert lib.cm_solve(None, None, 4, 4, 1.0, 0, 0, 1, 0.0, None, None, None, None, None) \
+        == cm.CM_ERR_INVALID
+    assert lib.cm_create(None, 0) == cm.CM_ERR_INVALID
+    assert lib.cm_last_error(None) == b"null context"
+
+
+def test_auto_levels_agree_with_oracle():
+    import oracle
+    import paper_2204_07921_gb300 as cm
+    for H, W in [(64, 64), (512, 512), (1024, 1024), (67, 45), (1, 1), (3, 100), (130, 97)]:
+        assert cm.cm_auto_levels(H, W) == oracle.auto_levels(H, W)

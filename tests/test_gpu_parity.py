@@ -1,0 +1,316 @@
+"""GPU parity: the CUDA library (through the C ABI) against the FP64 oracle.
+
+Every input is seeded and synthetic.  Small cases are compared element by
+element; full-size cases (512^2 Gaussian, 1024^2 mean) on sampled blocks the
+oracle solves one by one.  Tolerances are derived in tests/gpu_helpers.py.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import oracle  # noqa: E402
+import paper_2204_07921_gb300 as cm  # noqa: E402
+import synth  # noqa: E402
+from gpu_helpers import C_TOL, blocks_of_colour, compare_phase  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+DEV = torch.device("cuda:0")
+
+
+def to_dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).to(DEV)
+
+
+def host(t):
+    return t.detach().cpu().numpy()
+
+
+SHAPES = [(64, 64), (67, 45), (130, 97), (1, 37), (37, 1), (1, 1), (5, 3)]
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+@pytest.mark.parametrize("kind", [cm.MEAN, cm.GAUSS])
+def test_energy_parity(shape, kind):
+    H, W = shape
+    img = synth.piecewise_image(H, W, 1000 + H * 7 + W, 5, 0.08)
+    u = img.f
+    f = synth.piecewise_image(H, W, 2000 + H, 5, 0.08).f
+    Eg = cm.cm_energy(to_dev(u), to_dev(f), 20.0, kind)
+    Eo = oracle.energy(u.astype(np.float64), f.astype(np.float64), 20.0, kind)
+    assert Eg == pytest.approx(Eo, rel=2e-6, abs=1e-9)
+
+
+@pytest.mark.parametrize("kind", [cm.MEAN, cm.GAUSS])
+def test_energy_full_size_and_deterministic(kind):
+    img = synth.large(1024)
+    u, f = to_dev(img.f), to_dev(img.clean)
+    E1 = cm.cm_energy(u, f, 20.0, kind)
+    E2 = cm.cm_energy(u, f, 20.0, kind)
+    assert E1 == E2   # fixed-order FP64 reduction
+    Eo = oracle.energy(img.f.astype(np.float64), img.clean.astype(np.float64), 20.0, kind)
+    assert E1 == pytest.approx(Eo, rel=2e-6)
+
+
+@pytest.mark.parametrize("kind", [cm.MEAN, cm.GAUSS])
+def test_curvature_parity(kind):
+    img = synth.piecewise_image(67, 45, 5, 6, 0.1)
+    kg = host(cm.cm_curvature(to_dev(img.f), kind))
+    u64 = img.f.astype(np.float64)
+    ko = oracle.curvature_map(u64, kind)
+    scale = np.zeros_like(ko)
+    for r in range(67):
+        for c in range(45):
+            kb, _ = oracle.direction_curvatures(u64, r, c)
+            scale[r, c] = np.max(np.abs(kb))
+    bound = 2e-5 * (1 + scale) if kind == cm.MEAN else 2e-5 * (1 + scale) ** 2
+    assert np.all(np.abs(kg - ko) <= bound)
+
+
+def gpu_phase(u, f, alpha, kind, b, ncolors, k, G=9, K=16, use_paper=1):
+    H, W = u.shape
+    S = to_dev(u)
+    R = S.clone()
+    nb = ((H + b - 1) // b) * ((W + b - 1) // b)
+    cbuf = torch.full((nb,), float("nan"), device=DEV)
+    opts = cm.default_options(ncolors=ncolors, grid_points=G, golden_evals=K,
+                              paper_candidate=use_paper)
+    cm.cm_phase(S, R, to_dev(f), alpha, kind, b, k, options=opts, c_out=cbuf)
+    torch.cuda.synchronize()
+    return host(R), host(cbuf)
+
+
+def check_phase(u, f, alpha, kind, b, ncolors, k, sample=None):
+    """GPU phase from state u vs oracle; returns (n, match, tie, fails)."""
+    H, W = u.shape
+    Rg, cg = gpu_phase(u, f, alpha, kind, b, ncolors, k)
+    nbj = (W + b - 1) // b
+    cgd, cod = {}, {}
+    if sample is None:
+        _, co = oracle.phase(u.astype(np.float64), f.astype(np.float64), alpha, kind, b,
+                             ncolors, k)
+    for bi, bj, r0, c0, bh, bw in blocks_of_colour(H, W, b, ncolors, k):
+        if sample is not None and (bi, bj) not in sample:
+            continue
+        c = cg[bi * nbj + bj]
+        assert np.isfinite(c)
+        cgd[(bi, bj)] = c
+        if sample is None:
+            cod[(bi, bj)] = co[bi * nbj + bj]
+        # the block is written as S + c, in FP32
+        blk = Rg[r0:r0 + bh, c0:c0 + bw]
+        np.testing.assert_array_equal(blk, (u[r0:r0 + bh, c0:c0 + bw] + np.float32(c)))
+    if sample is None:
+        # blocks of other colours are not written
+        mask = np.zeros((H, W), bool)
+        for bi, bj, r0, c0, bh, bw in blocks_of_colour(H, W, b, ncolors, k):
+            mask[r0:r0 + bh, c0:c0 + bw] = True
+        np.testing.assert_array_equal(Rg[~mask], u[~mask])
+    return compare_phase(u.astype(np.float64), f.astype(np.float64), cgd, alpha, kind, b,
+                         ncolors, k, cod, sample=sample)
+
+
+def levels_for(H, W):
+    return [1 << j for j in range(cm.cm_auto_levels(H, W) + 1)]
+
+
+@pytest.mark.parametrize("shape", [(64, 64), (67, 45), (130, 97), (1, 37), (37, 1), (5, 3)])
+@pytest.mark.parametrize("kind", [cm.MEAN, cm.GAUSS])
+@pytest.mark.parametrize("ncolors", [2, 4])
+def test_phase_parity_small(shape, kind, ncolors):
+    """Every level (plus one beyond the automatic count) and colour, from a
+    non-trivial state (f after one oracle cycle)."""
+    H, W = shape
+    img = synth.piecewise_image(H, W, 300 + H + W, 5, 0.08)
+    f = img.f
+    u = oracle.cycle(f.astype(np.float64), f.astype(np.float64), 20.0, kind,
+                     levels=1).astype(np.float32)
+    tot = dict(n=0, match=0, tie=0)
+    fails = []
+    for b in levels_for(H, W):
+        for k in range(ncolors):
+            n, m, t, fl = check_phase(u, f, 20.0, kind, b, ncolors, k)
+            tot["n"] += n
+            tot["match"] += m
+            tot["tie"] += t
+            fails += fl
+    print(f"\n{shape} kind={kind} ncol={ncolors}: {tot}")
+    assert not fails, fails[:5]
+    assert tot["tie"] <= max(2, 0.01 * tot["n"])
+
+
+def test_phase_parity_512_gauss_sampled():
+    """512^2 Gaussian-curvature workload (20 shapes, sigma 0.1, alpha 15):
+    every level, both colours, 150 sampled blocks each solved by the oracle."""
+    img = synth.single_512()
+    f = img.f
+    H, W = f.shape
+    rng = np.random.default_rng(5)
+    fails, tot, ties = [], 0, 0
+    for b in levels_for(H, W)[:-1]:
+        for k in range(2):
+            blocks = [(bi, bj) for bi, bj, *_ in blocks_of_colour(H, W, b, 2, k)]
+            idx = rng.choice(len(blocks), size=min(150, len(blocks)), replace=False)
+            sample = {blocks[i] for i in idx}
+            n, m, t, fl = check_phase(f, f, 15.0, cm.GAUSS, b, 2, k, sample=sample)
+            tot += n
+            ties += t
+            fails += fl
+    print(f"\n512 gauss: n={tot} ties={ties}")
+    assert not fails, fails[:5]
+    assert ties <= max(2, 0.01 * tot)
+
+
+def run_solve(f, alpha, kind, cycles, tol=0.0, use_graph=1, ncolors=2, levels=0):
+    opts = cm.default_options(use_graph=use_graph, ncolors=ncolors)
+    u, st = cm.cm_solve(to_dev(f), alpha, kind, levels=levels, cycles=cycles, tol=tol,
+                        options=opts)
+    torch.cuda.synchronize()
+    return host(u), st
+
+
+def test_solve_equals_phase_sequence_and_is_deterministic():
+    """cm_solve (graph replay and direct launches) performs exactly the
+    phase sequence of Alg. 3: bit-identical to chaining cm_phase calls."""
+    img = synth.piecewise_image(67, 45, 9, 5, 0.08)
+    f = img.f
+    ua, sa = run_solve(f, 20.0, cm.MEAN, 3, use_graph=1)
+    ub, sb = run_solve(f, 20.0, cm.MEAN, 3, use_graph=0)
+    uc, _ = run_solve(f, 20.0, cm.MEAN, 3, use_graph=1)
+    np.testing.assert_array_equal(ua, ub)
+    np.testing.assert_array_equal(ua, uc)
+    assert sa.trace() == sb.trace()
+    # manual chain
+    S = to_dev(f)
+    fd = to_dev(f)
+    R = torch.empty_like(S)
+    L = cm.cm_auto_levels(67, 45)
+    for _ in range(3):
+        for j in range(L):
+            for k in range(2):
+                cm.cm_phase(S, R, fd, 20.0, cm.MEAN, 1 << j, k)
+            S, R = R, S
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(ua, host(S))
+    assert sa.trace()[-1] == cm.cm_energy(S, fd, 20.0, cm.MEAN)
+
+
+@pytest.mark.parametrize("kind", [cm.MEAN, cm.GAUSS])
+def test_per_sweep_parity_64(kind):
+    """The 64x64 workload (6 shapes, sigma 0.05, alpha 20), 20 cycles: each
+    phase of each cycle is compared with the oracle started from the GPU's
+    own input state, and the final energy with the oracle's FP64 energy of
+    the GPU's result."""
+    img = synth.single_64()
+    f = img.f
+    H, W = f.shape
+    L = cm.cm_auto_levels(H, W)
+    S = to_dev(f)
+    fd = to_dev(f)
+    R = torch.empty_like(S)
+    fails, tot, ties = [], 0, 0
+    for cyc in range(20):
+        for j in range(L):
+            for k in range(2):
+                u_in = host(S) if k == 0 else None
+                if k == 1:
+                    # phase state: colour-0 blocks from R, the rest from S
+                    u_in = host(S).copy()
+                    Rh = host(R)
+                    for bi, bj, r0, c0, bh, bw in blocks_of_colour(H, W, 1 << j, 2, 0):
+                        u_in[r0:r0 + bh, c0:c0 + bw] = Rh[r0:r0 + bh, c0:c0 + bw]
+                if cyc % 5 == 0 or cyc == 19:
+                    n, m, t, fl = check_phase(u_in, f, 20.0, kind, 1 << j, 2, k)
+                    tot += n
+                    ties += t
+                    fails += fl
+                cm.cm_phase(S, R, fd, 20.0, kind, 1 << j, k)
+            S, R = R, S
+    torch.cuda.synchronize()
+    print(f"\n64 kind={kind}: blocks={tot} ties={ties}")
+    assert not fails, fails[:5]
+    assert ties <= max(2, 0.01 * tot)
+    u = host(S)
+    Eg = cm.cm_energy(S, fd, 20.0, kind)
+    Eo = oracle.energy(u.astype(np.float64), f.astype(np.float64), 20.0, kind)
+    assert Eg == pytest.approx(Eo, rel=2e-6)
+
+
+@pytest.mark.parametrize("kind", [cm.MEAN, cm.GAUSS])
+def test_solve_final_energy_vs_oracle_64(kind):
+    """Independent GPU and oracle solves of the 64x64 workload, 20 cycles:
+    final energies agree to 1e-5 relative; the GPU result improves PSNR."""
+    img = synth.single_64()
+    f = img.f
+    ug, st = run_solve(f, 20.0, kind, 20)
+    uo, trace, n, _ = oracle.solve(f.astype(np.float64), 20.0, kind, cycles=20)
+    Eg = oracle.energy(ug.astype(np.float64), f.astype(np.float64), 20.0, kind)
+    print(f"\n64 solve kind={kind}: E_gpu={Eg:.9g} E_orc={trace[-1]:.9g} "
+          f"rel={(Eg - trace[-1]) / trace[-1]:.3g} max|du|={np.abs(ug - uo).max():.3g}")
+    assert st.cycles_run == 20
+    assert abs(Eg - trace[-1]) <= 1e-5 * abs(trace[-1])
+    assert synth.psnr(ug, img.clean) > synth.psnr(f, img.clean)
+
+
+def test_solve_until_tolerance_512_gauss():
+    """512^2 Gaussian workload until rel. energy change <= 1e-4: converges,
+    energy trace agrees with the oracle's FP64 energy of the GPU state."""
+    img = synth.single_512()
+    f = img.f
+    ug, st = run_solve(f, 15.0, cm.GAUSS, 500, tol=1e-4)
+    assert st.converged
+    tr = st.trace()
+    rel = abs(tr[-1] - tr[-2]) / abs(tr[-1])
+    assert rel <= 1e-4
+    Eo = oracle.energy(ug.astype(np.float64), f.astype(np.float64), 15.0, cm.GAUSS)
+    assert tr[-1] == pytest.approx(Eo, rel=2e-6)
+    print(f"\n512 gauss: cycles={st.cycles_run} E0={tr[0]:.6g} E={tr[-1]:.6g} "
+          f"viol={st.monotone_violations}")
+
+
+def test_full_size_1024_phase_sampled():
+    """1024^2 mean-curvature workload: finest and two coarse levels, sampled
+    blocks against the oracle."""
+    img = synth.large(1024)
+    f = img.f
+    H, W = f.shape
+    rng = np.random.default_rng(11)
+    fails, tot, ties = [], 0, 0
+    for b in (1, 2, 64, 512):
+        for k in range(2):
+            blocks = [(bi, bj) for bi, bj, *_ in blocks_of_colour(H, W, b, 2, k)]
+            idx = rng.choice(len(blocks), size=min(60, len(blocks)), replace=False)
+            n, m, t, fl = check_phase(f, f, 20.0, cm.MEAN, b, 2, k,
+                                      sample={blocks[i] for i in idx})
+            tot += n
+            ties += t
+            fails += fl
+    assert not fails, fails[:5]
+    assert ties <= max(2, 0.01 * tot)
+
+
+def test_invalid_arguments_rejected():
+    f = to_dev(np.zeros((8, 8), np.float32))
+    with pytest.raises(cm.CMError) as e:
+        cm.cm_solve(f, -1.0, 0)
+    assert e.value.code == cm.CM_ERR_INVALID
+    with pytest.raises(cm.CMError):
+        cm.cm_solve(f, float("nan"), 0)
+    with pytest.raises(cm.CMError):
+        cm.cm_phase(f, f.clone(), f, 1.0, 0, 3, 0)      # b not a power of two
+    with pytest.raises(cm.CMError):
+        cm.cm_solve(f, 1.0, 0, options=cm.default_options(grid_points=8))
+    bad = f.clone()
+    bad[3, 3] = float("inf")
+    with pytest.raises(cm.CMError) as e:
+        cm.cm_solve(bad, 1.0, 0, cycles=1)
+    assert e.value.code == cm.CM_ERR_NUMERIC
+
+
+def test_constant_image_fixed_point_gpu():
+    f = np.full((33, 20), 0.25, np.float32)
+    u, st = run_solve(f, 10.0, cm.MEAN, 3)
+    np.testing.assert_array_equal(u, f)
+    assert st.trace() == [0.0] * 4
