@@ -150,7 +150,7 @@ extern "C" {
 
 int cm_options_default(cm_options* o) {
     if (!o) return CM_ERR_INVALID;
-    o->ncolors = 2;
+    o->ncolors = 4;
     o->grid_points = 9;
     o->golden_evals = 16;
     o->paper_candidate = 1;

@@ -44,7 +44,7 @@ def test_host_only_entry_points():
     lib = cm.load()
     o = cm.Options()
     assert lib.cm_options_default(ctypes.byref(o)) == 0
-    assert (o.ncolors, o.grid_points, o.golden_evals, o.paper_candidate) == (2, 9, 16, 1)
+    assert (o.ncolors, o.grid_points, o.golden_evals, o.paper_candidate) == (4, 9, 16, 1)
     assert lib.cm_options_default(None) == cm.CM_ERR_INVALID
     assert lib.cm_auto_levels(64, 64) == 6
     assert lib.cm_auto_levels(1024, 1024) == 10

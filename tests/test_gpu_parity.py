@@ -163,7 +163,7 @@ def test_phase_parity_512_gauss_sampled():
     assert ties <= max(2, 0.01 * tot)
 
 
-def run_solve(f, alpha, kind, cycles, tol=0.0, use_graph=1, ncolors=2, levels=0):
+def run_solve(f, alpha, kind, cycles, tol=0.0, use_graph=1, ncolors=4, levels=0):
     opts = cm.default_options(use_graph=use_graph, ncolors=ncolors)
     u, st = cm.cm_solve(to_dev(f), alpha, kind, levels=levels, cycles=cycles, tol=tol,
                         options=opts)
@@ -189,7 +189,7 @@ def test_solve_equals_phase_sequence_and_is_deterministic():
     L = cm.cm_auto_levels(67, 45)
     for _ in range(3):
         for j in range(L):
-            for k in range(2):
+            for k in range(4):
                 cm.cm_phase(S, R, fd, 20.0, cm.MEAN, 1 << j, k)
             S, R = R, S
     torch.cuda.synchronize()
@@ -210,6 +210,7 @@ def test_per_sweep_parity_64(kind):
     S = to_dev(f)
     fd = to_dev(f)
     R = torch.empty_like(S)
+    opts2 = cm.default_options(ncolors=2)
     fails, tot, ties = [], 0, 0
     for cyc in range(20):
         for j in range(L):
@@ -226,7 +227,7 @@ def test_per_sweep_parity_64(kind):
                     tot += n
                     ties += t
                     fails += fl
-                cm.cm_phase(S, R, fd, 20.0, kind, 1 << j, k)
+                cm.cm_phase(S, R, fd, 20.0, kind, 1 << j, k, options=opts2)
             S, R = R, S
     torch.cuda.synchronize()
     print(f"\n64 kind={kind}: blocks={tot} ties={ties}")
@@ -240,34 +241,54 @@ def test_per_sweep_parity_64(kind):
 
 @pytest.mark.parametrize("kind", [cm.MEAN, cm.GAUSS])
 def test_solve_final_energy_vs_oracle_64(kind):
-    """Independent GPU and oracle solves of the 64x64 workload, 20 cycles:
-    final energies agree to 1e-5 relative; the GPU result improves PSNR."""
+    """The 64x64 workload (2 colours, 20 cycles).  The GPU's FP64-reduced
+    final energy equals the oracle's FP64 energy of the GPU's result to 1e-5
+    relative (measured ~1e-7).  An independent oracle solve follows the same
+    phase sequence, but each energy tie (accepted per phase above) sends the
+    two trajectories apart, so their final energies are compared loosely
+    (1e-3) and both must have descended from F(f) by the same margin."""
     img = synth.single_64()
     f = img.f
-    ug, st = run_solve(f, 20.0, kind, 20)
-    uo, trace, n, _ = oracle.solve(f.astype(np.float64), 20.0, kind, cycles=20)
+    ug, st = run_solve(f, 20.0, kind, 20, ncolors=2)
+    uo, trace, n, _ = oracle.solve(f.astype(np.float64), 20.0, kind, cycles=20, ncolors=2)
     Eg = oracle.energy(ug.astype(np.float64), f.astype(np.float64), 20.0, kind)
-    print(f"\n64 solve kind={kind}: E_gpu={Eg:.9g} E_orc={trace[-1]:.9g} "
-          f"rel={(Eg - trace[-1]) / trace[-1]:.3g} max|du|={np.abs(ug - uo).max():.3g}")
+    print(f"\n64 solve kind={kind}: E_gpu={Eg:.9g} (reported {st.energy_final:.9g}) "
+          f"E_orc={trace[-1]:.9g} rel={(Eg - trace[-1]) / trace[-1]:.3g} "
+          f"max|du|={np.abs(ug - uo).max():.3g}")
     assert st.cycles_run == 20
-    assert abs(Eg - trace[-1]) <= 1e-5 * abs(trace[-1])
+    assert abs(st.energy_final - Eg) <= 1e-5 * abs(Eg)
+    assert abs(Eg - trace[-1]) <= 1e-3 * abs(trace[-1])
+    assert (trace[0] - Eg) == pytest.approx(trace[0] - trace[-1], rel=1e-3)
     assert synth.psnr(ug, img.clean) > synth.psnr(f, img.clean)
 
 
 def test_solve_until_tolerance_512_gauss():
-    """512^2 Gaussian workload until rel. energy change <= 1e-4: converges,
-    energy trace agrees with the oracle's FP64 energy of the GPU state."""
+    """512^2 Gaussian workload (four colours) until rel. energy change <= 1e-4:
+    converges, the energy never rises, and the final reported energy agrees
+    with the oracle's FP64 energy of the GPU state."""
     img = synth.single_512()
     f = img.f
-    ug, st = run_solve(f, 15.0, cm.GAUSS, 500, tol=1e-4)
+    ug, st = run_solve(f, 15.0, cm.GAUSS, 500, tol=1e-4, ncolors=4)
+    print(f"\n512 gauss: cycles={st.cycles_run} E={st.trace()} viol={st.monotone_violations}")
     assert st.converged
     tr = st.trace()
-    rel = abs(tr[-1] - tr[-2]) / abs(tr[-1])
-    assert rel <= 1e-4
+    assert abs(tr[-1] - tr[-2]) / abs(tr[-1]) <= 1e-4
+    assert st.monotone_violations == 0
     Eo = oracle.energy(ug.astype(np.float64), f.astype(np.float64), 15.0, cm.GAUSS)
     assert tr[-1] == pytest.approx(Eo, rel=2e-6)
-    print(f"\n512 gauss: cycles={st.cycles_run} E0={tr[0]:.6g} E={tr[-1]:.6g} "
-          f"viol={st.monotone_violations}")
+    assert synth.psnr(ug, img.clean) > synth.psnr(f, img.clean)
+
+
+def test_two_colour_gaussian_oscillation_is_reported():
+    """Two colours at the finest level update diagonal neighbours at once
+    (snapshot semantics); for Gaussian curvature on the 512^2 workload this
+    oscillates: the solve reports energy rises and, with a cap, returns
+    CM_NOT_CONVERGED with a valid u_out."""
+    img = synth.single_512()
+    ug, st = run_solve(img.f, 15.0, cm.GAUSS, 60, tol=1e-6, ncolors=2)
+    assert not st.converged and st.cycles_run == 60
+    assert st.monotone_violations > 0
+    assert np.all(np.isfinite(ug))
 
 
 def test_full_size_1024_phase_sampled():
