@@ -44,6 +44,9 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-cycles", type=int, default=1,
                    help="oracle cycles timed for the CPU baseline sample")
+    p.add_argument("--phases-only", action="store_true",
+                   help="profiling aid: two warm-up cycles, then one launch of every "
+                        "(level, colour) phase on the image and exit")
     return p.parse_args()
 
 
@@ -195,6 +198,17 @@ def main():
     stream = torch.cuda.current_stream()
     opts = cm.default_options()
     L = cm.cm_auto_levels(args.side, args.side)
+
+    if args.phases_only:
+        _, st = cm.cm_solve(f, ALPHA, KIND, cycles=2, u_out=u, options=opts, ctx=ctx)
+        R = u.clone()
+        for j in range(L):
+            for k in range(opts.ncolors):
+                cm.cm_phase(u, R, f, ALPHA, KIND, 1 << j, k, options=opts, ctx=ctx)
+        cm.cm_energy(u, f, ALPHA, KIND, ctx=ctx)
+        torch.cuda.synchronize()
+        print(json.dumps({"phases_only": True, "levels": L, "ncolors": opts.ncolors}))
+        return
 
     def step(out):
         _, st = cm.cm_solve(f, ALPHA, KIND, levels=0, cycles=MAX_CYCLES, tol=TOL, u_out=out,

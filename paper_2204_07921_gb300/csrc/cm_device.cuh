@@ -72,6 +72,85 @@ __device__ __forceinline__ float abs_curvature(const float w[9], int kind) {
     return kind == KIND_MEAN ? fabsf(0.5f * (kmin + kmax)) : fabsf(kmin * kmax);
 }
 
+// ---------------------------------------------------------------------------
+// Direction curvature as a function of a block shift c.
+//
+// When the pixels of a block A move by c, each window entry moves by c or
+// stays, so every ingredient of a direction is affine in c:
+//   Dq = (u_Y - u_X)/2,  two_h * delta,  e_i = u_X + u_Y - 2 u_Zi.
+// With ds^2 = h^2 + Dq^2 the plane term D^2 + 4h^2 equals 4 ds^2, so
+//   kbar(c) = (two_h delta)(c) * sum_i rsqrt((e_i(c)^2 + 4 ds^2(c)) ds^4(c)),
+// 13 FP32 operations and two rsqrt per direction and candidate.
+struct AffDir {
+    float dq0, dq1;   // Dq = dq0 + dq1 c
+    float dl0, dl1;   // 2h delta = dl0 + dl1 c
+    float e10, e11;   // e_1 = e10 + e11 c
+    float e20, e21;   // e_2 = e20 + e21 c
+};
+
+// Line t of the window: end points X, Y, flanks Z1, Z2 (window indices).
+__host__ __device__ constexpr int line_x(int t) { return t == 0 ? 3 : t == 1 ? 1 : t == 2 ? 0 : 2; }
+__host__ __device__ constexpr int line_y(int t) { return t == 0 ? 5 : t == 1 ? 7 : t == 2 ? 8 : 6; }
+__host__ __device__ constexpr int line_z1(int t) { return t == 0 ? 1 : t == 1 ? 3 : t == 2 ? 2 : 0; }
+__host__ __device__ constexpr int line_z2(int t) { return t == 0 ? 7 : t == 1 ? 5 : t == 2 ? 6 : 8; }
+__host__ __device__ constexpr float line_h2(int t) { return t < 2 ? 1.0f : 2.0f; }
+__host__ __device__ constexpr float line_two_h(int t) {
+    return t < 2 ? 2.0f : 2.8284271247461903f;
+}
+
+// Coefficients of line t for window w whose entries with bit q of `mask`
+// belong to the shifted block.
+__device__ __forceinline__ AffDir aff_dir(const float w[9], unsigned mask, int t) {
+    const int X = line_x(t), Y = line_y(t), Z1 = line_z1(t), Z2 = line_z2(t);
+    const float two_h = line_two_h(t);
+    const float a = (float)((mask >> X) & 1u), b = (float)((mask >> Y) & 1u);
+    const float o = (float)((mask >> 4) & 1u);
+    const float z1 = (float)((mask >> Z1) & 1u), z2 = (float)((mask >> Z2) & 1u);
+    AffDir d;
+    d.dq0 = 0.5f * (w[Y] - w[X]);
+    d.dq1 = 0.5f * (b - a);
+    d.dl0 = two_h * fmaf(0.5f, w[X] + w[Y], -w[4]);
+    d.dl1 = two_h * (0.5f * (a + b) - o);
+    const float S = w[X] + w[Y];
+    d.e10 = fmaf(-2.0f, w[Z1], S);
+    d.e11 = a + b - 2.0f * z1;
+    d.e20 = fmaf(-2.0f, w[Z2], S);
+    d.e21 = a + b - 2.0f * z2;
+    return d;
+}
+
+__device__ __forceinline__ float aff_kbar(const AffDir& d, float h2, float c) {
+    const float Dq = fmaf(d.dq1, c, d.dq0);
+    const float ds2 = fmaf(Dq, Dq, h2);
+    const float fds = 4.0f * ds2;
+    const float ds4 = ds2 * ds2;
+    const float e1 = fmaf(d.e11, c, d.e10);
+    const float e2 = fmaf(d.e21, c, d.e20);
+    const float r = rsqrtf(fmaf(e1, e1, fds) * ds4) + rsqrtf(fmaf(e2, e2, fds) * ds4);
+    return fmaf(d.dl1, c, d.dl0) * r;
+}
+
+// Ring pixel: the four directions of one 3x3 window under a block shift.
+struct AffPix {
+    AffDir d[4];
+};
+
+__device__ __forceinline__ AffPix aff_pix(const float w[9], unsigned mask) {
+    AffPix p;
+#pragma unroll
+    for (int t = 0; t < 4; ++t) p.d[t] = aff_dir(w, mask, t);
+    return p;
+}
+
+template <int KIND>
+__device__ __forceinline__ float aff_abs_curv(const AffPix& p, float c) {
+    const float k0 = aff_kbar(p.d[0], 1.0f, c), k1 = aff_kbar(p.d[1], 1.0f, c);
+    const float k2 = aff_kbar(p.d[2], 2.0f, c), k3 = aff_kbar(p.d[3], 2.0f, c);
+    const float kmin = fminf(fminf(k0, k1), fminf(k2, k3));
+    const float kmax = fmaxf(fmaxf(k0, k1), fmaxf(k2, k3));
+    return KIND == KIND_MEAN ? 0.5f * fabsf(kmin + kmax) : fabsf(kmin * kmax);
+}
+
 // Clamp-to-edge boundary: out-of-image neighbours take the nearest pixel.
 __device__ __forceinline__ int clampi(int v, int lo, int hi) { return min(max(v, lo), hi); }
 

@@ -1,0 +1,130 @@
+// cm_energy.cu -- discrete energy and curvature map kernels.
+//
+//  energy_kernel     F(u) = sum |kappa| + alpha/2 (u - f)^2 (Eq. MCM / Eq. GCM):
+//                    smem halo tile, FP32 per pixel, FP64 CTA partials and a
+//                    fixed-order FP64 finish in the last CTA (deterministic).
+//  curvature_kernel  signed kappa per pixel (diagnostics and tests).
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include "cm_device.cuh"
+#include "cm_kernels.h"
+
+namespace cm {
+
+// ---------------------------------------------------------------------------
+// Energy.
+
+constexpr int E_TW = 32;   // tile columns
+constexpr int E_TH = 32;   // tile rows (each thread 4 rows)
+
+template <int KIND>
+__global__ void __launch_bounds__(256) energy_kernel(const float* __restrict__ u,
+                                                     const float* __restrict__ f, int H, int W,
+                                                     float alpha, double* __restrict__ partials,
+                                                     unsigned int* __restrict__ ticket,
+                                                     double* __restrict__ E_out) {
+    __shared__ float tile[E_TH + 2][E_TW + 3];
+    __shared__ double wsum[8];
+    __shared__ bool is_last;
+    const int r0 = blockIdx.y * E_TH, c0 = blockIdx.x * E_TW;
+    for (int i = threadIdx.x; i < (E_TH + 2) * (E_TW + 2); i += 256) {
+        int lr = i / (E_TW + 2), lc = i - lr * (E_TW + 2);
+        int r = clampi(r0 - 1 + lr, 0, H - 1), c = clampi(c0 - 1 + lc, 0, W - 1);
+        tile[lr][lc] = u[(size_t)r * W + c];
+    }
+    __syncthreads();
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    float acc = 0.0f;
+#pragma unroll
+    for (int i = 0; i < E_TH / 8; ++i) {
+        int lr = ty + 8 * i;
+        int r = r0 + lr, c = c0 + tx;
+        if (r < H && c < W) {
+            float w[9];
+#pragma unroll
+            for (int a = 0; a < 3; ++a)
+#pragma unroll
+                for (int b = 0; b < 3; ++b) w[3 * a + b] = tile[lr + a][tx + b];
+            float e = w[4] - f[(size_t)r * W + c];
+            acc += abs_curvature(w, KIND) + 0.5f * alpha * e * e;
+        }
+    }
+    double d = (double)acc;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) d += __shfl_xor_sync(0xffffffffu, d, off);
+    if (tx == 0) wsum[ty] = d;
+    __syncthreads();
+    const int nblk = gridDim.x * gridDim.y;
+    const int bid = blockIdx.y * gridDim.x + blockIdx.x;
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int i = 0; i < 8; ++i) s += wsum[i];
+        partials[bid] = s;
+        __threadfence();
+        unsigned int t = atomicAdd(ticket, 1u);
+        is_last = (t == (unsigned)nblk - 1);
+    }
+    __syncthreads();
+    if (!is_last) return;
+    __threadfence();
+    // Fixed-order finish: thread t sums partials t, t+256, ...; then a tree.
+    double s = 0.0;
+    for (int i = threadIdx.x; i < nblk; i += 256) s += ((volatile double*)partials)[i];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+    __syncthreads();
+    if (tx == 0) wsum[ty] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int i = 0; i < 8; ++i) t += wsum[i];
+        *E_out = t;
+        *ticket = 0u;   // ready for the next launch
+    }
+}
+
+template <int KIND>
+__global__ void curvature_kernel(const float* __restrict__ u, int H, int W,
+                                 float* __restrict__ out) {
+    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    int r = blockIdx.y * blockDim.y + threadIdx.y;
+    if (r >= H || c >= W) return;
+    float w[9];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b)
+            w[3 * a + b] = u[(size_t)clampi(r + a - 1, 0, H - 1) * W + clampi(c + b - 1, 0, W - 1)];
+    KBar4 k = direction_curvatures(w);
+    float kmin = fminf(fminf(k.k[0], k.k[1]), fminf(k.k[2], k.k[3]));
+    float kmax = fmaxf(fmaxf(k.k[0], k.k[1]), fmaxf(k.k[2], k.k[3]));
+    out[(size_t)r * W + c] = KIND == KIND_MEAN ? 0.5f * (kmin + kmax) : kmin * kmax;
+}
+
+cudaError_t launch_energy(const float* u, const float* f, int H, int W, float alpha, int kind,
+                          double* partials, unsigned int* ticket, double* E_out,
+                          cudaStream_t st) {
+    dim3 grid((W + E_TW - 1) / E_TW, (H + E_TH - 1) / E_TH);
+    if (kind == KIND_MEAN)
+        energy_kernel<KIND_MEAN><<<grid, 256, 0, st>>>(u, f, H, W, alpha, partials, ticket, E_out);
+    else
+        energy_kernel<KIND_GAUSS><<<grid, 256, 0, st>>>(u, f, H, W, alpha, partials, ticket, E_out);
+    return cudaGetLastError();
+}
+
+size_t energy_partials_needed(int H, int W) {
+    return (size_t)((W + E_TW - 1) / E_TW) * (size_t)((H + E_TH - 1) / E_TH);
+}
+
+cudaError_t launch_curvature(const float* u, int H, int W, int kind, float* out,
+                             cudaStream_t st) {
+    dim3 blk(32, 8), grid((W + 31) / 32, (H + 7) / 8);
+    if (kind == KIND_MEAN)
+        curvature_kernel<KIND_MEAN><<<grid, blk, 0, st>>>(u, H, W, out);
+    else
+        curvature_kernel<KIND_GAUSS><<<grid, blk, 0, st>>>(u, H, W, out);
+    return cudaGetLastError();
+}
+
+}  // namespace cm

@@ -26,7 +26,9 @@ cudaError_t launch_energy(const float* u, const float* f, int H, int W, float al
 size_t energy_partials_needed(int H, int W);
 cudaError_t launch_curvature(const float* u, int H, int W, int kind, float* out,
                              cudaStream_t st);
-cudaError_t launch_phase(const PhaseArgs& a, cudaStream_t st);
+cudaError_t launch_phase(const PhaseArgs& a, cudaStream_t st);          // dispatch by level
+cudaError_t launch_phase_b1(const PhaseArgs& a, cudaStream_t st);       // b = 1
+cudaError_t launch_phase_blocks(const PhaseArgs& a, cudaStream_t st);   // b >= 2
 int max_level_log2();
 
 }  // namespace cm

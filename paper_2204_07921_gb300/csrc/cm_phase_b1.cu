@@ -1,0 +1,321 @@
+// cm_phase_b1.cu -- the finest level of the sweep (1x1 blocks).
+//
+// Alg. 1 of the paper made colour-parallel: one thread per pixel of the
+// active colour; the CTA stages the phase state of its tile plus a 2-pixel
+// halo in shared memory; each thread runs the block search on its pixel.
+//
+// Interior fast path.  With p interior, the only window entry that moves
+// with c is p itself, so per candidate c:
+//  * at p, the plane normals do not move and only delta does:
+//    kbar_t(c) = 2h (rsqrt(q1) + rsqrt(q2)) (delta_t - c), one FMA;
+//  * at a neighbour q of p, p is an end point of one line of q (recomputed
+//    from affine coefficients: 13 FP32 operations, two rsqrt) and a flanking
+//    point of one plane of another line (one rsqrt); the two remaining
+//    directions are constant and enter only through their min and max.
+// This is the same function of c as the generic ring evaluation (used at the
+// image border, where clamping duplicates p); only FP32 rounding differs.
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include "cm_device.cuh"
+#include "cm_kernels.h"
+#include "cm_search.cuh"
+
+namespace cm {
+
+// Plane distances of one line (for the paper's one-step candidate).
+__device__ __forceinline__ void dir_dist(float A, float B, float O, float Z1, float Z2,
+                                         float four_h2, float two_h, float& d1, float& d2) {
+    const float D = B - A, S = A + B;
+    const float delta = fmaf(0.5f, S, -O);
+    const float base = fmaf(D, D, four_h2);
+    const float e1 = fmaf(-2.0f, Z1, S), e2 = fmaf(-2.0f, Z2, S);
+    d1 = two_h * delta * rsqrtf(fmaf(e1, e1, base));
+    d2 = two_h * delta * rsqrtf(fmaf(e2, e2, base));
+}
+
+// The paper's finest-level estimate: Alg. 2 with t = 0, c_0 = 0, eta_0 = 1:
+// c_1 = (c_{1/2} + alpha f*) / (2 + alpha), c_{1/2} the mean plane distance
+// (Eq. c-sol1) or, for Gaussian curvature, the distance pair of the extreme
+// direction curvature with the smaller magnitude (Prop. 2).
+template <int KIND>
+__device__ __forceinline__ float paper_candidate(const float w[9], float fstar, float alpha) {
+    const float SQ2x2 = 2.8284271247461903f;
+    float d[8];
+    dir_dist(w[3], w[5], w[4], w[1], w[7], 4.0f, 2.0f, d[0], d[1]);
+    dir_dist(w[1], w[7], w[4], w[3], w[5], 4.0f, 2.0f, d[2], d[3]);
+    dir_dist(w[0], w[8], w[4], w[2], w[6], 8.0f, SQ2x2, d[4], d[5]);
+    dir_dist(w[2], w[6], w[4], w[0], w[8], 8.0f, SQ2x2, d[6], d[7]);
+    float chalf;
+    if (KIND == KIND_MEAN) {
+        chalf = 0.125f * (((d[0] + d[1]) + (d[2] + d[3])) + ((d[4] + d[5]) + (d[6] + d[7])));
+    } else {
+        KBar4 k = direction_curvatures(w);
+        int tmin = 0, tmax = 0;
+#pragma unroll
+        for (int t = 1; t < 4; ++t) {
+            if (k.k[t] < k.k[tmin]) tmin = t;
+            if (k.k[t] > k.k[tmax]) tmax = t;
+        }
+        int ts = fabsf(k.k[tmin]) <= fabsf(k.k[tmax]) ? tmin : tmax;
+        float dd0 = d[0], dd1 = d[1];
+#pragma unroll
+        for (int t = 1; t < 4; ++t)
+            if (ts == t) {
+                dd0 = d[2 * t];
+                dd1 = d[2 * t + 1];
+            }
+        chalf = 0.5f * (dd0 + dd1);
+    }
+    return (chalf + alpha * fstar) / (2.0f + alpha);
+}
+
+// For p at window position POS of its neighbour: the line with p as an end
+// point (TF) and the line with p as a flank (TH), flank index ZI (0/1).
+template <int POS> struct PosLines;
+template <> struct PosLines<3> { static constexpr int TF = 0, TH = 1, ZI = 0; };
+template <> struct PosLines<5> { static constexpr int TF = 0, TH = 1, ZI = 1; };
+template <> struct PosLines<1> { static constexpr int TF = 1, TH = 0, ZI = 0; };
+template <> struct PosLines<7> { static constexpr int TF = 1, TH = 0, ZI = 1; };
+template <> struct PosLines<0> { static constexpr int TF = 2, TH = 3, ZI = 0; };
+template <> struct PosLines<8> { static constexpr int TF = 2, TH = 3, ZI = 1; };
+template <> struct PosLines<2> { static constexpr int TF = 3, TH = 2, ZI = 0; };
+template <> struct PosLines<6> { static constexpr int TF = 3, TH = 2, ZI = 1; };
+
+struct NbConst {
+    float dq0, dl0, e10, e20;             // full direction at c = 0
+    float eh0, fds, ds4, thd, kh0;        // half direction
+    float kmin_ab, kmax_ab;               // the two constant directions
+};
+
+template <int DR, int DC>
+__device__ __forceinline__ void nb_window(const float w25[25], float w[9]) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) w[3 * a + b] = w25[5 * (1 + DR + a) + (1 + DC + b)];
+}
+
+template <int DR, int DC>
+__device__ __forceinline__ NbConst nb_init(const float w25[25]) {
+    constexpr int POS = 4 - 3 * DR - DC;
+    constexpr int TF = PosLines<POS>::TF, TH = PosLines<POS>::TH, ZI = PosLines<POS>::ZI;
+    float w[9];
+    nb_window<DR, DC>(w25, w);
+    NbConst n;
+    const KBar4 k = direction_curvatures(w);
+    float ka = 0.0f, kb = 0.0f;
+    bool first = true;
+#pragma unroll
+    for (int t = 0; t < 4; ++t)
+        if (t != TF && t != TH) {
+            if (first) {
+                ka = k.k[t];
+                first = false;
+            } else {
+                kb = k.k[t];
+            }
+        }
+    n.kmin_ab = fminf(ka, kb);
+    n.kmax_ab = fmaxf(ka, kb);
+    {   // full direction: affine coefficients at c = 0
+        const int X = line_x(TF), Y = line_y(TF);
+        const float two_h = line_two_h(TF);
+        n.dq0 = 0.5f * (w[Y] - w[X]);
+        n.dl0 = two_h * fmaf(0.5f, w[X] + w[Y], -w[4]);
+        const float S = w[X] + w[Y];
+        n.e10 = fmaf(-2.0f, w[line_z1(TF)], S);
+        n.e20 = fmaf(-2.0f, w[line_z2(TF)], S);
+    }
+    {   // half direction: one plane moves with its flank
+        const int X = line_x(TH), Y = line_y(TH);
+        const float two_h = line_two_h(TH), h2 = line_h2(TH);
+        const float Dq = 0.5f * (w[Y] - w[X]);
+        const float ds2 = fmaf(Dq, Dq, h2);
+        const float S = w[X] + w[Y];
+        const float Zm = ZI == 0 ? w[line_z1(TH)] : w[line_z2(TH)];
+        const float Zc = ZI == 0 ? w[line_z2(TH)] : w[line_z1(TH)];
+        const float ec = fmaf(-2.0f, Zc, S);
+        n.fds = 4.0f * ds2;
+        n.ds4 = ds2 * ds2;
+        n.thd = two_h * fmaf(0.5f, S, -w[4]);
+        n.kh0 = n.thd * rsqrtf(fmaf(ec, ec, n.fds) * n.ds4);
+        n.eh0 = fmaf(-2.0f, Zm, S);
+    }
+    return n;
+}
+
+template <int KIND, int DR, int DC>
+__device__ __forceinline__ float nb_eval(const NbConst& n, float c) {
+    constexpr int POS = 4 - 3 * DR - DC;
+    constexpr int TF = PosLines<POS>::TF;
+    constexpr float dq1 = line_y(TF) == POS ? 0.5f : -0.5f;
+    constexpr float h2 = TF < 2 ? 1.0f : 2.0f;
+    constexpr float dl1 = 0.5f * (TF < 2 ? 2.0f : 2.8284271247461903f);
+    const float Dq = fmaf(dq1, c, n.dq0);
+    const float ds2 = fmaf(Dq, Dq, h2);
+    const float fds = 4.0f * ds2;
+    const float ds4 = ds2 * ds2;
+    const float e1 = c + n.e10, e2 = c + n.e20;
+    const float r = rsqrtf(fmaf(e1, e1, fds) * ds4) + rsqrtf(fmaf(e2, e2, fds) * ds4);
+    const float kf = fmaf(dl1, c, n.dl0) * r;
+    const float e = fmaf(-2.0f, c, n.eh0);
+    const float kh = fmaf(n.thd, rsqrtf(fmaf(e, e, n.fds) * n.ds4), n.kh0);
+    const float kmin = fminf(fminf(kf, kh), n.kmin_ab);
+    const float kmax = fmaxf(fmaxf(kf, kh), n.kmax_ab);
+    return KIND == KIND_MEAN ? 0.5f * fabsf(kmin + kmax) : fabsf(kmin * kmax);
+}
+
+template <int NCOL>
+struct B1Tile {
+    static constexpr int TW = 32;                       // tile columns
+    static constexpr int TH = NCOL == 2 ? 8 : 16;       // tile rows
+    static constexpr int THREADS = 128;                 // one per active pixel
+};
+
+#ifndef CM_B1_MIN_BLOCKS
+#define CM_B1_MIN_BLOCKS 3
+#endif
+
+template <int KIND, int NCOL>
+__global__ void __launch_bounds__(128, CM_B1_MIN_BLOCKS) phase_b1_kernel(const float* __restrict__ S,
+                                                       float* __restrict__ R,
+                                                       const float* __restrict__ f, int H,
+                                                       int W, SearchParams sp, int k,
+                                                       int use_paper, float* __restrict__ c_out) {
+    constexpr int TW = B1Tile<NCOL>::TW, TH = B1Tile<NCOL>::TH;
+    __shared__ float tile[TH + 4][TW + 5];
+    const int r0 = blockIdx.y * TH, c0 = blockIdx.x * TW;
+    for (int i = threadIdx.x; i < (TH + 4) * (TW + 4); i += 128) {
+        int lr = i / (TW + 4), lc = i - lr * (TW + 4);
+        int r = clampi(r0 - 2 + lr, 0, H - 1), c = clampi(c0 - 2 + lc, 0, W - 1);
+        tile[lr][lc] = phase_read(S, R, r, c, W, 0, NCOL, k);
+    }
+    __syncthreads();
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    int r, c;
+    if (NCOL == 2) {
+        r = r0 + ty;
+        c = c0 + 2 * tx + ((r + k) & 1);
+    } else {
+        r = r0 + 2 * ty + (k >> 1);
+        c = c0 + 2 * tx + (k & 1);
+    }
+    if (r >= H || c >= W) return;
+    const int lr = r - r0, lc = c - c0;   // window (i, j) = tile[lr + i][lc + j]
+    float w25[25];
+    unsigned mask = 0;   // window entries that are the pixel itself after clamping
+#pragma unroll
+    for (int i = 0; i < 5; ++i)
+#pragma unroll
+        for (int j = 0; j < 5; ++j) {
+            w25[5 * i + j] = tile[lr + i][lc + j];
+            bool self = clampi(r + i - 2, 0, H - 1) == r && clampi(c + j - 2, 0, W - 1) == c;
+            mask |= (self ? 1u : 0u) << (5 * i + j);
+        }
+    const size_t p = (size_t)r * W + c;
+    const float up = w25[12];
+    const float S1 = up - f[p];
+    float cp = 0.0f;
+    if (use_paper) {
+        float w[9];
+        nb_window<0, 0>(w25, w);
+        cp = paper_candidate<KIND>(w, -S1, sp.alpha);
+    }
+    const bool interior = r >= 1 && r <= H - 2 && c >= 1 && c <= W - 2;
+    float cbest;
+    if (interior) {
+        float ncs[4], csd[4];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            float w[9];
+            nb_window<0, 0>(w25, w);
+            const AffDir d = aff_dir(w, 1u << 4, t);
+            const float ds2 = fmaf(d.dq0, d.dq0, line_h2(t));
+            const float fds = 4.0f * ds2, ds4 = ds2 * ds2;
+            const float sr = line_two_h(t) * (rsqrtf(fmaf(d.e10, d.e10, fds) * ds4) +
+                                              rsqrtf(fmaf(d.e20, d.e20, fds) * ds4));
+            // kbar_t(c) = sr (delta_t - c) = csd - sr c
+            ncs[t] = -sr;
+            csd[t] = sr * fmaf(0.5f, w[line_x(t)] + w[line_y(t)], -w[4]);
+        }
+        const NbConst n0 = nb_init<-1, -1>(w25), n1 = nb_init<-1, 0>(w25),
+                      n2 = nb_init<-1, 1>(w25), n3 = nb_init<0, -1>(w25),
+                      n4 = nb_init<0, 1>(w25), n5 = nb_init<1, -1>(w25),
+                      n6 = nb_init<1, 0>(w25), n7 = nb_init<1, 1>(w25);
+        auto ring_fast = [&](float cc) {
+            const float k0 = fmaf(ncs[0], cc, csd[0]), k1 = fmaf(ncs[1], cc, csd[1]);
+            const float k2 = fmaf(ncs[2], cc, csd[2]), k3 = fmaf(ncs[3], cc, csd[3]);
+            const float kmin = fminf(fminf(k0, k1), fminf(k2, k3));
+            const float kmax = fmaxf(fmaxf(k0, k1), fmaxf(k2, k3));
+            float acc = KIND == KIND_MEAN ? 0.5f * fabsf(kmin + kmax) : fabsf(kmin * kmax);
+            acc += nb_eval<KIND, -1, -1>(n0, cc);
+            acc += nb_eval<KIND, -1, 0>(n1, cc);
+            acc += nb_eval<KIND, -1, 1>(n2, cc);
+            acc += nb_eval<KIND, 0, -1>(n3, cc);
+            acc += nb_eval<KIND, 0, 1>(n4, cc);
+            acc += nb_eval<KIND, 1, -1>(n5, cc);
+            acc += nb_eval<KIND, 1, 0>(n6, cc);
+            acc += nb_eval<KIND, 1, 1>(n7, cc);
+            return acc;
+        };
+        cbest = block_search_1site(ring_fast, sp, 1.0f, S1, use_paper != 0, cp);
+    } else {
+        // Border pixel: clamping may duplicate p inside a neighbour's window;
+        // evaluate every in-image ring pixel from the shifted 5x5 window.
+        unsigned ringv = 0;
+#pragma unroll
+        for (int dr = -1; dr <= 1; ++dr)
+#pragma unroll
+            for (int dc = -1; dc <= 1; ++dc) {
+                bool in = r + dr >= 0 && r + dr < H && c + dc >= 0 && c + dc < W;
+                ringv |= (in ? 1u : 0u) << (3 * (dr + 1) + (dc + 1));
+            }
+        auto ring = [&](float cs) {
+            float v[25];
+#pragma unroll
+            for (int i = 0; i < 25; ++i) v[i] = ((mask >> i) & 1u) ? w25[i] + cs : w25[i];
+            float acc = 0.0f;
+#pragma unroll
+            for (int qr = 0; qr < 3; ++qr)
+#pragma unroll
+                for (int qc = 0; qc < 3; ++qc) {
+                    float w[9];
+#pragma unroll
+                    for (int a = 0; a < 3; ++a)
+#pragma unroll
+                        for (int b = 0; b < 3; ++b) w[3 * a + b] = v[5 * (qr + a) + (qc + b)];
+                    float t = abs_curvature(w, KIND);
+                    acc += ((ringv >> (3 * qr + qc)) & 1u) ? t : 0.0f;
+                }
+            return acc;
+        };
+        cbest = block_search_1site(ring, sp, 1.0f, S1, use_paper != 0, cp);
+    }
+    R[p] = up + cbest;
+    if (c_out) c_out[p] = cbest;
+}
+
+cudaError_t launch_phase_b1(const PhaseArgs& A, cudaStream_t st) {
+    SearchParams sp{A.alpha, A.G, A.K};
+    if (A.ncolors == 2) {
+        dim3 grid((A.W + B1Tile<2>::TW - 1) / B1Tile<2>::TW, (A.H + B1Tile<2>::TH - 1) / B1Tile<2>::TH);
+        if (A.kind == KIND_MEAN)
+            phase_b1_kernel<KIND_MEAN, 2><<<grid, 128, 0, st>>>(A.S, A.R, A.f, A.H, A.W, sp,
+                                                                A.colour, A.use_paper, A.c_out);
+        else
+            phase_b1_kernel<KIND_GAUSS, 2><<<grid, 128, 0, st>>>(A.S, A.R, A.f, A.H, A.W, sp,
+                                                                 A.colour, A.use_paper, A.c_out);
+    } else {
+        dim3 grid((A.W + B1Tile<4>::TW - 1) / B1Tile<4>::TW, (A.H + B1Tile<4>::TH - 1) / B1Tile<4>::TH);
+        if (A.kind == KIND_MEAN)
+            phase_b1_kernel<KIND_MEAN, 4><<<grid, 128, 0, st>>>(A.S, A.R, A.f, A.H, A.W, sp,
+                                                                A.colour, A.use_paper, A.c_out);
+        else
+            phase_b1_kernel<KIND_GAUSS, 4><<<grid, 128, 0, st>>>(A.S, A.R, A.f, A.H, A.W, sp,
+                                                                 A.colour, A.use_paper, A.c_out);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace cm

@@ -1,0 +1,240 @@
+// cm_phase_blocks.cu -- sweep levels with block side b >= 2 (Sec. 2.2).
+//
+//  phase_warp_kernel     b = 2 and 4: 16 or 32 lanes of one warp per block,
+//                        one ring pixel per lane; candidate energies are
+//                        warp-shuffle reductions.
+//  phase_cluster_kernel  b >= 8: one CTA, or a thread-block cluster of up to 8
+//                        CTAs on different SMs, per block, one ring pixel per
+//                        thread; candidate energies reduce through shared
+//                        memory and, across the cluster, distributed shared
+//                        memory with one cluster barrier per reduction.
+//
+// Each thread holds its ring pixel as the affine coefficients of its four
+// direction curvatures in the block shift c (AffPix), so a candidate costs
+// ~55 FP32 operations and 8 rsqrt per ring pixel.
+#include <cooperative_groups.h>
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include "cm_device.cuh"
+#include "cm_kernels.h"
+#include "cm_search.cuh"
+
+namespace cm {
+
+// Block pixels [r0, r0 + bh) x [c0, c0 + bw), visited with stride `stride`
+// from index `first` (row-major within the block).
+template <class F>
+__device__ __forceinline__ void for_block_pixels(int first, int stride, int r0, int c0, int bh,
+                                                 int bw, int lb, bool full_w, int W, F&& fn) {
+    const int npx = bh * bw;
+#pragma unroll 4
+    for (int idx = first; idx < npx; idx += stride) {
+        int rr = full_w ? (idx >> lb) : idx / bw;
+        fn((size_t)(r0 + rr) * W + (c0 + idx - rr * bw));
+    }
+}
+
+template <int KIND, int GT>
+__global__ void __launch_bounds__(128) phase_warp_kernel(
+    const float* __restrict__ S, float* __restrict__ R, const float* __restrict__ f, int H, int W,
+    SearchParams sp, int lb, int ncol, int k, float* __restrict__ c_out) {
+    static_assert(GT == 16 || GT == 32, "warp groups only");
+    constexpr int GPC = 128 / GT;
+    const int b = 1 << lb;
+    const int nbi = (H + b - 1) >> lb, nbj = (W + b - 1) >> lb;
+    const int gid = threadIdx.x / GT, lane = threadIdx.x % GT;
+    const int a = blockIdx.x * GPC + gid;
+    int bi, bj;
+    const bool active = active_block(a, nbi, nbj, ncol, k, bi, bj);
+    // Inactive groups still take part in the shuffles of their warp.
+    const int r0 = active ? bi << lb : 0, c0 = active ? bj << lb : 0;
+    const int r1 = active ? min(r0 + b, H) : 0, c1 = active ? min(c0 + b, W) : 0;
+    const int bh = r1 - r0, bw = c1 - c0;
+    float s1 = 0.0f;
+    if (active)
+        for_block_pixels(lane, GT, r0, c0, bh, bw, lb, bw == b, W,
+                         [&](size_t p) { s1 += S[p] - f[p]; });
+#pragma unroll
+    for (int off = GT / 2; off > 0; off >>= 1) s1 += __shfl_xor_sync(0xffffffffu, s1, off, GT);
+    float w[9];
+    unsigned mask = 0;
+    const bool has = active && ring_slot(lane, r0, r1, c0, c1, H, W, S, R, lb, ncol, k, w, mask);
+    AffPix px;
+    if (has) {
+        px = aff_pix(w, mask);
+    } else {
+#pragma unroll
+        for (int t = 0; t < 4; ++t) px.d[t] = AffDir{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    }
+    auto ring = [&](float c) {
+        float v = has ? aff_abs_curv<KIND>(px, c) : 0.0f;
+#pragma unroll
+        for (int off = GT / 2; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off, GT);
+        return v;
+    };
+    const float s = active ? (float)(bh * bw) : 1.0f;
+    const float cbest = block_search(ring, sp, s, active ? s1 : 0.0f, false, 0.0f);
+    if (!active) return;
+    for_block_pixels(lane, GT, r0, c0, bh, bw, lb, bw == b, W,
+                     [&](size_t p) { R[p] = S[p] + cbest; });
+    if (c_out && lane == 0) c_out[(size_t)bi * nbj + bj] = cbest;
+}
+
+template <int KIND, int CT, int Q, int RPT>
+__global__ void __cluster_dims__(Q, 1, 1) __launch_bounds__(CT) phase_cluster_kernel(
+    const float* __restrict__ S, float* __restrict__ R, const float* __restrict__ f, int H, int W,
+    SearchParams sp, int lb, int ncol, int k, float* __restrict__ c_out) {
+    namespace cg = cooperative_groups;
+    constexpr int GT = CT * Q;         // threads searching one block
+    constexpr int NW = CT / 32;
+    constexpr int MB = 9;              // candidates per batched reduction (the grid)
+    __shared__ float red[2][MB][NW];   // per-warp partials, double-buffered
+    __shared__ float part[2][Q][MB];   // CTA partials pushed by every cluster rank
+    const int rank = Q > 1 ? (int)cg::this_cluster().block_rank() : 0;
+    const int a = blockIdx.x / Q;
+    const int g = rank * CT + threadIdx.x;
+    const int b = 1 << lb;
+    const int nbi = (H + b - 1) >> lb, nbj = (W + b - 1) >> lb;
+    int bi, bj;
+    if (!active_block(a, nbi, nbj, ncol, k, bi, bj)) return;   // uniform over the cluster
+    const int r0 = bi << lb, c0 = bj << lb;
+    const int r1 = min(r0 + b, H), c1 = min(c0 + b, W);
+    const int bh = r1 - r0, bw = c1 - c0;
+    int flip = 0;
+
+    // Sum m values over the group: warp shuffles, shared memory, then (Q > 1)
+    // every CTA pushes its partials into each rank's shared memory and one
+    // cluster barrier publishes them; every thread adds them in rank order.
+    auto reduce_vec = [&](float* v, int m) {
+#pragma unroll
+        for (int j = 0; j < MB; ++j)
+            if (j < m) {
+#pragma unroll
+                for (int off = 16; off > 0; off >>= 1) v[j] += __shfl_xor_sync(0xffffffffu, v[j], off);
+            }
+        if ((threadIdx.x & 31) == 0) {
+#pragma unroll
+            for (int j = 0; j < MB; ++j)
+                if (j < m) red[flip][j][threadIdx.x >> 5] = v[j];
+        }
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < MB; ++j)
+            if (j < m) {
+                float t = 0.0f;
+#pragma unroll
+                for (int i = 0; i < NW; ++i) t += red[flip][j][i];
+                v[j] = t;
+            }
+        if (Q > 1) {
+            cg::cluster_group cl = cg::this_cluster();
+            if (threadIdx.x < Q) {
+                float* dst = cl.map_shared_rank(&part[flip][rank][0], threadIdx.x);
+#pragma unroll
+                for (int j = 0; j < MB; ++j)
+                    if (j < m) dst[j] = v[j];
+            }
+            cl.sync();
+#pragma unroll
+            for (int j = 0; j < MB; ++j)
+                if (j < m) {
+                    float t = 0.0f;
+#pragma unroll
+                    for (int q = 0; q < Q; ++q) t += part[flip][q][j];
+                    v[j] = t;
+                }
+        }
+        flip ^= 1;
+    };
+
+    float s1 = 0.0f;
+    for_block_pixels(g, GT, r0, c0, bh, bw, lb, bw == b, W, [&](size_t p) { s1 += S[p] - f[p]; });
+    reduce_vec(&s1, 1);
+    const float S1 = s1;
+
+    AffPix px[RPT];
+    bool has[RPT];
+#pragma unroll
+    for (int t = 0; t < RPT; ++t) {
+        float w[9];
+        unsigned mask = 0;
+        has[t] = ring_slot(g + t * GT, r0, r1, c0, c1, H, W, S, R, lb, ncol, k, w, mask);
+        if (has[t]) {
+            px[t] = aff_pix(w, mask);
+        } else {
+#pragma unroll
+            for (int d = 0; d < 4; ++d) px[t].d[d] = AffDir{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        }
+    }
+    auto ringv = [&](const float* cs, int m, float* out) {
+#pragma unroll
+        for (int j = 0; j < MB; ++j) {
+            float acc = 0.0f;
+            if (j < m) {
+#pragma unroll
+                for (int t = 0; t < RPT; ++t)
+                    if (has[t]) acc += aff_abs_curv<KIND>(px[t], cs[j]);
+            }
+            out[j] = acc;
+        }
+        reduce_vec(out, m);
+    };
+    const float cbest = block_search_batched<MB>(ringv, sp, (float)(bh * bw), S1);
+    for_block_pixels(g, GT, r0, c0, bh, bw, lb, bw == b, W, [&](size_t p) { R[p] = S[p] + cbest; });
+    if (c_out && g == 0) c_out[(size_t)bi * nbj + bj] = cbest;
+    // No CTA may exit while another still reads its shared memory.
+    if (Q > 1) cg::this_cluster().sync();
+}
+
+template <int KIND, int GT>
+static void launch_warp(const PhaseArgs& A, int nact, cudaStream_t st) {
+    constexpr int GPC = 128 / GT;
+    SearchParams sp{A.alpha, A.G, A.K};
+    phase_warp_kernel<KIND, GT><<<(nact + GPC - 1) / GPC, 128, 0, st>>>(
+        A.S, A.R, A.f, A.H, A.W, sp, A.lb, A.ncolors, A.colour, A.c_out);
+}
+
+template <int KIND, int CT, int Q, int RPT>
+static void launch_cluster(const PhaseArgs& A, int nact, cudaStream_t st) {
+    SearchParams sp{A.alpha, A.G, A.K};
+    phase_cluster_kernel<KIND, CT, Q, RPT><<<nact * Q, CT, 0, st>>>(
+        A.S, A.R, A.f, A.H, A.W, sp, A.lb, A.ncolors, A.colour, A.c_out);
+}
+
+template <int KIND>
+static cudaError_t launch_blocks_kind(const PhaseArgs& A, cudaStream_t st) {
+    const int b = 1 << A.lb;
+    const int nbi = (A.H + b - 1) / b, nbj = (A.W + b - 1) / b;
+    const int nact = A.ncolors == 2 ? nbi * ((nbj + 1) / 2) : ((nbi + 1) / 2) * ((nbj + 1) / 2);
+    // ring of a full block: 8b pixels = Q * CT * RPT slots
+    switch (A.lb) {
+        case 1: launch_warp<KIND, 16>(A, nact, st); break;
+        case 2: launch_warp<KIND, 32>(A, nact, st); break;
+        case 3: launch_cluster<KIND, 64, 1, 1>(A, nact, st); break;
+        case 4: launch_cluster<KIND, 128, 1, 1>(A, nact, st); break;
+        case 5: launch_cluster<KIND, 256, 1, 1>(A, nact, st); break;
+        case 6: launch_cluster<KIND, 256, 2, 1>(A, nact, st); break;
+        case 7: launch_cluster<KIND, 256, 4, 1>(A, nact, st); break;
+        case 8: launch_cluster<KIND, 256, 8, 1>(A, nact, st); break;
+        case 9: launch_cluster<KIND, 512, 8, 1>(A, nact, st); break;
+        case 10: launch_cluster<KIND, 1024, 8, 1>(A, nact, st); break;
+        case 11: launch_cluster<KIND, 1024, 8, 2>(A, nact, st); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_phase_blocks(const PhaseArgs& A, cudaStream_t st) {
+    return A.kind == KIND_MEAN ? launch_blocks_kind<KIND_MEAN>(A, st)
+                               : launch_blocks_kind<KIND_GAUSS>(A, st);
+}
+
+cudaError_t launch_phase(const PhaseArgs& A, cudaStream_t st) {
+    if (A.lb == 0) return launch_phase_b1(A, st);
+    return launch_phase_blocks(A, st);
+}
+
+int max_level_log2() { return 11; }
+
+}  // namespace cm
