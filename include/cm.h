@@ -127,6 +127,20 @@ int cm_phase(cm_ctx* ctx, const float* S, float* R, const float* f, int H, int W
              int kind, int b, int colour, const cm_options* opts /* host, nullable */,
              float* c_out, void* stream);
 
+/* One whole level of the sweep (the inner loop of Alg. 3 over the colours
+ * k = 0 .. ncolors-1 on the level with block side b, a power of two): from
+ * the state S, each colour's blocks in turn find their shift from the state
+ * left by the previous colours, exactly as a sequence of cm_phase calls
+ * would; R (every pixel) receives the state after the last colour.  This is
+ * the path cm_solve runs: on levels with b >= 64 it evaluates block sums from
+ * 32 x 32 tile sums and applies all shifts in one pass after the last colour,
+ * which changes only the FP32 summation order of S1.
+ * S, R, f: device H x W; R must not alias S or f.  c_out (device, nullable):
+ * receives every block's c, indexed bi * nbj + bj, nbj = ceil(W / b). */
+int cm_level(cm_ctx* ctx, const float* S, float* R, const float* f, int H, int W, float alpha,
+             int kind, int b, const cm_options* opts /* host, nullable */, float* c_out,
+             void* stream);
+
 /* Full solve (Alg. 3, half V-cycle): u_0 = u0 (or f when u0 is NULL); each
  * cycle sweeps levels 1..L fine to coarse, colours in ascending order; the
  * FP64 energy is evaluated after every cycle and the loop stops when

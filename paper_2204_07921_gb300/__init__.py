@@ -16,6 +16,7 @@ from .build import LIB, build as build_library
 
 __all__ = [
     "CMError", "Options", "Stats", "Context", "load", "cm_energy", "cm_curvature", "cm_phase",
+    "cm_level",
     "cm_solve", "cm_auto_levels", "MEAN", "GAUSS",
 ]
 
@@ -64,6 +65,7 @@ SIGNATURES = {
     "cm_energy": (_I, [_P, _P, _P, _I, _I, _F, _I, ctypes.POINTER(_D), _P]),
     "cm_curvature": (_I, [_P, _P, _I, _I, _I, _P, _P]),
     "cm_phase": (_I, [_P, _P, _P, _P, _I, _I, _F, _I, _I, _I, ctypes.POINTER(Options), _P, _P]),
+    "cm_level": (_I, [_P, _P, _P, _P, _I, _I, _F, _I, _I, ctypes.POINTER(Options), _P, _P]),
     "cm_solve": (_I, [_P, _P, _I, _I, _F, _I, _I, _I, _D, _P, _P, ctypes.POINTER(Options),
                       ctypes.POINTER(Stats), _P]),
 }
@@ -197,6 +199,21 @@ def cm_phase(S, R, f, alpha: float, kind: int, b: int, colour: int, options: Opt
     opts = options or default_options()
     c._check(load().cm_phase(c.handle, S.data_ptr(), R.data_ptr(), f.data_ptr(), H, W,
                              float(alpha), kind, b, colour, ctypes.byref(opts),
+                             c_out.data_ptr() if c_out is not None else None,
+                             _stream_ptr(stream)))
+    return R
+
+
+def cm_level(S, R, f, alpha: float, kind: int, b: int, options: Options | None = None,
+             c_out=None, ctx: Context | None = None, stream=None):
+    """One whole level (every colour) from state S; R receives the new state."""
+    for t, n in ((S, "S"), (R, "R"), (f, "f")):
+        _img(t, n)
+    c = _ctx(ctx, S)
+    H, W = S.shape
+    opts = options or default_options()
+    c._check(load().cm_level(c.handle, S.data_ptr(), R.data_ptr(), f.data_ptr(), H, W,
+                             float(alpha), kind, b, ctypes.byref(opts),
                              c_out.data_ptr() if c_out is not None else None,
                              _stream_ptr(stream)))
     return R

@@ -31,6 +31,10 @@ struct cm_ctx {
     size_t ubuf_cap = 0;
     double* partials = nullptr;
     size_t partials_cap = 0;
+    float* tsums = nullptr;      // coarse path: 32x32 tile sums of S - f
+    size_t tsums_cap = 0;
+    float* cj = nullptr;         // coarse path: per-block shifts of one level
+    size_t cj_cap = 0;
     unsigned int* ticket = nullptr;
     double* E_dev = nullptr;
     double* E_pinned = nullptr;
@@ -81,6 +85,22 @@ int ensure_partials(cm_ctx* ctx, int H, int W) {
     return CM_OK;
 }
 
+int ensure_coarse(cm_ctx* ctx, int H, int W) {
+    size_t nt = cm::coarse_partials_needed(H, W), nc = cm::coarse_c_needed(H, W);
+    if (nt <= ctx->tsums_cap && nc <= ctx->cj_cap) return CM_OK;
+    drop_graphs(ctx);
+    if (ctx->tsums) cudaFree(ctx->tsums);
+    if (ctx->cj) cudaFree(ctx->cj);
+    ctx->tsums = nullptr;
+    ctx->cj = nullptr;
+    ctx->tsums_cap = ctx->cj_cap = 0;
+    CM_CUDA(cudaMalloc(&ctx->tsums, nt * sizeof(float)));
+    CM_CUDA(cudaMalloc(&ctx->cj, nc * sizeof(float)));
+    ctx->tsums_cap = nt;
+    ctx->cj_cap = nc;
+    return CM_OK;
+}
+
 int ensure_ubuf(cm_ctx* ctx, size_t n) {
     if (n <= ctx->ubuf_cap) return CM_OK;
     drop_graphs(ctx);
@@ -124,6 +144,27 @@ cm::PhaseArgs phase_args(const float* S, float* R, const float* f, int H, int W,
     return a;
 }
 
+// Enqueue one level (all colours) from state S into R.  Levels below the
+// coarse threshold run one phase kernel per colour; coarse levels run the
+// tile-sum / search / apply sequence.  c_out (nullable) receives every
+// block's shift.
+cudaError_t enqueue_level(cm_ctx* ctx, const float* S, float* R, const float* f, int H, int W,
+                          float alpha, int kind, int lb, const cm_options& o, float* c_out,
+                          cudaStream_t st) {
+    if (lb >= cm::coarse_level_log2()) {
+        cm::PhaseArgs a = phase_args(S, R, f, H, W, alpha, kind, lb, 0, o);
+        a.c_out = c_out;
+        return cm::launch_level_coarse(a, ctx->tsums, ctx->cj, st);
+    }
+    for (int k = 0; k < o.ncolors; ++k) {
+        cm::PhaseArgs a = phase_args(S, R, f, H, W, alpha, kind, lb, k, o);
+        a.c_out = c_out;
+        cudaError_t e = cm::launch_phase(a, st);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
 // Enqueue one cycle starting from buffer X (other buffer Y); the state ends
 // in X if `levels` is even, else in Y.  Then the energy of the final state.
 cudaError_t enqueue_cycle(cm_ctx* ctx, float* X, float* Y, const float* f, int H, int W,
@@ -132,11 +173,8 @@ cudaError_t enqueue_cycle(cm_ctx* ctx, float* X, float* Y, const float* f, int H
     float* S = X;
     float* R = Y;
     for (int j = 0; j < levels; ++j) {
-        for (int k = 0; k < o.ncolors; ++k) {
-            cm::PhaseArgs a = phase_args(S, R, f, H, W, alpha, kind, j, k, o);
-            cudaError_t e = cm::launch_phase(a, st);
-            if (e != cudaSuccess) return e;
-        }
+        cudaError_t e = enqueue_level(ctx, S, R, f, H, W, alpha, kind, j, o, nullptr, st);
+        if (e != cudaSuccess) return e;
         float* t = S;
         S = R;
         R = t;
@@ -197,6 +235,8 @@ void cm_destroy(cm_ctx* ctx) {
         if (g.exec) cudaGraphExecDestroy(g.exec);
     if (ctx->ubuf) cudaFree(ctx->ubuf);
     if (ctx->partials) cudaFree(ctx->partials);
+    if (ctx->tsums) cudaFree(ctx->tsums);
+    if (ctx->cj) cudaFree(ctx->cj);
     if (ctx->ticket) cudaFree(ctx->ticket);
     if (ctx->E_dev) cudaFree(ctx->E_dev);
     if (ctx->E_pinned) cudaFreeHost(ctx->E_pinned);
@@ -255,6 +295,28 @@ int cm_phase(cm_ctx* ctx, const float* S, float* R, const float* f, int H, int W
     return CM_OK;
 }
 
+int cm_level(cm_ctx* ctx, const float* S, float* R, const float* f, int H, int W, float alpha,
+             int kind, int b, const cm_options* opts, float* c_out, void* stream) {
+    if (!ctx) return CM_ERR_INVALID;
+    cm_options o;
+    cm_options_default(&o);
+    if (opts) o = *opts;
+    int rc = check_opts(ctx, o);
+    if (rc) return rc;
+    if (!S || !R || !f || R == S || R == f || H < 1 || W < 1 || !finite_positive(alpha) ||
+        (kind != 0 && kind != 1))
+        return fail(ctx, CM_ERR_INVALID, "cm_level: invalid argument");
+    int lb = 0;
+    while ((1 << lb) < b) ++lb;
+    if (b < 1 || (1 << lb) != b || lb > cm::max_level_log2())
+        return fail(ctx, CM_ERR_INVALID, "cm_level: b must be a power of two <= 2048");
+    CM_CUDA(cudaSetDevice(ctx->device));
+    rc = ensure_coarse(ctx, H, W);
+    if (rc) return rc;
+    CM_CUDA(enqueue_level(ctx, S, R, f, H, W, alpha, kind, lb, o, c_out, (cudaStream_t)stream));
+    return CM_OK;
+}
+
 int cm_solve(cm_ctx* ctx, const float* f, int H, int W, float alpha, int kind, int levels,
              int cycles, double tol, const float* u0, float* u_out, const cm_options* opts,
              cm_stats* stats, void* stream) {
@@ -275,6 +337,8 @@ int cm_solve(cm_ctx* ctx, const float* f, int H, int W, float alpha, int kind, i
     rc = ensure_partials(ctx, H, W);
     if (rc) return rc;
     rc = ensure_ubuf(ctx, N);
+    if (rc) return rc;
+    rc = ensure_coarse(ctx, H, W);
     if (rc) return rc;
     float* bufs[2] = {u_out, ctx->ubuf};
     if (u0 && u0 != u_out)

@@ -31,4 +31,11 @@ cudaError_t launch_phase_b1(const PhaseArgs& a, cudaStream_t st);       // b = 1
 cudaError_t launch_phase_blocks(const PhaseArgs& a, cudaStream_t st);   // b >= 2
 int max_level_log2();
 
+// Coarse path (block side >= 1 << coarse_level_log2()): a whole level at once.
+// partials: coarse_partials_needed() floats; cj: coarse_c_needed() floats.
+int coarse_level_log2();
+size_t coarse_partials_needed(int H, int W);
+size_t coarse_c_needed(int H, int W);
+cudaError_t launch_level_coarse(const PhaseArgs& a, float* partials, float* cj, cudaStream_t st);
+
 }  // namespace cm

@@ -16,6 +16,8 @@
 #include <cuda_runtime.h>
 #include <math.h>
 
+#include <algorithm>
+
 #include "cm_device.cuh"
 #include "cm_kernels.h"
 #include "cm_search.cuh"
@@ -185,6 +187,252 @@ __global__ void __cluster_dims__(Q, 1, 1) __launch_bounds__(CT) phase_cluster_ke
     if (c_out && g == 0) c_out[(size_t)bi * nbj + bj] = cbest;
     // No CTA may exit while another still reads its shared memory.
     if (Q > 1) cg::this_cluster().sync();
+}
+
+// ---------------------------------------------------------------------------
+// Coarse levels (b >= 64): few blocks, so every step is made short.
+//  * S1 comes from 32 x 32 tile sums of S - f computed by one wide kernel per
+//    level (a block of side >= 64 is a union of whole tiles);
+//  * the search kernel writes only the block's c; pixels of blocks of earlier
+//    colours of the level are read as S + c (the value R would hold);
+//  * one wide kernel writes R = S + c after the last colour.
+// The result is the same as the direct phases up to the FP32 order of the
+// S1 sum.
+
+constexpr int TILE = 32;
+constexpr int COARSE_LB = 6;
+
+__global__ void __launch_bounds__(256) tile_sums_kernel(const float* __restrict__ S,
+                                                        const float* __restrict__ f, int H, int W,
+                                                        float* __restrict__ partials) {
+    __shared__ float red[8];
+    const int r0 = blockIdx.y * TILE, c0 = blockIdx.x * TILE;
+    float acc = 0.0f;
+#pragma unroll
+    for (int i = 0; i < TILE * TILE / 256; ++i) {
+        const int idx = threadIdx.x + 256 * i;
+        const int r = r0 + idx / TILE, c = c0 + idx % TILE;
+        if (r < H && c < W) {
+            const size_t p = (size_t)r * W + c;
+            acc += S[p] - f[p];
+        }
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float t = 0.0f;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) t += red[i];
+        partials[blockIdx.y * gridDim.x + blockIdx.x] = t;
+    }
+}
+
+__global__ void __launch_bounds__(256) apply_kernel(const float* __restrict__ S,
+                                                    float* __restrict__ R,
+                                                    const float* __restrict__ cj, int H, int W,
+                                                    int lb, int nbj) {
+    const size_t N = (size_t)H * W;
+    for (size_t p = (size_t)blockIdx.x * 256 + threadIdx.x; p < N; p += (size_t)gridDim.x * 256) {
+        const int r = (int)(p / W), c = (int)(p - (size_t)r * W);
+        R[p] = S[p] + cj[(size_t)(r >> lb) * nbj + (c >> lb)];
+    }
+}
+
+template <int KIND, int CT, int Q, int RPT, int LA>
+__global__ void __cluster_dims__(Q, 1, 1) __launch_bounds__(CT) phase_coarse_kernel(
+    const float* __restrict__ S, const float* __restrict__ partials, float* __restrict__ cj,
+    int H, int W, SearchParams sp, int lb, int ncol, int k, float* __restrict__ c_out) {
+    namespace cg = cooperative_groups;
+    constexpr int GT = CT * Q;
+    constexpr int NW = CT / 32;
+    constexpr int MB = 9;
+    __shared__ float red[2][MB][NW];
+    __shared__ float tot[2][MB];
+    __shared__ float part[2][Q][MB];
+    const int rank = Q > 1 ? (int)cg::this_cluster().block_rank() : 0;
+    const int a = blockIdx.x / Q;
+    const int g = rank * CT + threadIdx.x;
+    const int b = 1 << lb;
+    const int nbi = (H + b - 1) >> lb, nbj = (W + b - 1) >> lb;
+    int bi, bj;
+    if (!active_block(a, nbi, nbj, ncol, k, bi, bj)) return;   // uniform over the cluster
+    const int r0 = bi << lb, c0 = bj << lb;
+    const int r1 = min(r0 + b, H), c1 = min(c0 + b, W);
+    const int bh = r1 - r0, bw = c1 - c0;
+    int flip = 0;
+    auto reduce_vec = [&](float* v, int m) {
+#pragma unroll
+        for (int j = 0; j < MB; ++j)
+            if (j < m) {
+#pragma unroll
+                for (int off = 16; off > 0; off >>= 1) v[j] += __shfl_xor_sync(0xffffffffu, v[j], off);
+            }
+        if ((threadIdx.x & 31) == 0) {
+#pragma unroll
+            for (int j = 0; j < MB; ++j)
+                if (j < m) red[flip][j][threadIdx.x >> 5] = v[j];
+        }
+        __syncthreads();
+        if (NW > 8) {
+            // warp j folds candidate j's warp partials (fixed order) and
+            // publishes the CTA total; one more barrier broadcasts it
+            const int wj = threadIdx.x >> 5, ln = threadIdx.x & 31;
+            if (wj < m) {
+                float t = ln < NW ? red[flip][wj][ln] : 0.0f;
+#pragma unroll
+                for (int off = 16; off > 0; off >>= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
+                if (ln == 0) tot[flip][wj] = t;
+            }
+            __syncthreads();
+#pragma unroll
+            for (int j = 0; j < MB; ++j)
+                if (j < m) v[j] = tot[flip][j];
+        } else {
+#pragma unroll
+            for (int j = 0; j < MB; ++j)
+                if (j < m) {
+                    float t = 0.0f;
+#pragma unroll
+                    for (int i = 0; i < NW; ++i) t += red[flip][j][i];
+                    v[j] = t;
+                }
+        }
+        if (Q > 1) {
+            cg::cluster_group cl = cg::this_cluster();
+            if (threadIdx.x < Q) {
+                float* dst = cl.map_shared_rank(&part[flip][rank][0], threadIdx.x);
+#pragma unroll
+                for (int j = 0; j < MB; ++j)
+                    if (j < m) dst[j] = v[j];
+            }
+            cl.sync();
+#pragma unroll
+            for (int j = 0; j < MB; ++j)
+                if (j < m) {
+                    float t = 0.0f;
+#pragma unroll
+                    for (int q = 0; q < Q; ++q) t += part[flip][q][j];
+                    v[j] = t;
+                }
+        }
+        flip ^= 1;
+    };
+    // S1 from the tile sums of the block
+    const int ntc = (W + TILE - 1) / TILE;
+    const int tw = (bw + TILE - 1) / TILE, th = (bh + TILE - 1) / TILE;
+    float s1 = 0.0f;
+    for (int t = g; t < tw * th; t += GT) {
+        const int ti = t / tw, tj = t - ti * tw;
+        s1 += partials[(size_t)(r0 / TILE + ti) * ntc + (c0 / TILE + tj)];
+    }
+    reduce_vec(&s1, 1);
+    const float S1 = s1;
+    // ring windows from the lazy phase state
+    auto value = [&](int r, int c) {
+        float v = S[(size_t)r * W + c];
+        if (k > 0 && pixel_colour(r, c, lb, ncol) < k) v += cj[(size_t)(r >> lb) * nbj + (c >> lb)];
+        return v;
+    };
+    AffPix px[RPT];
+    bool has[RPT];
+#pragma unroll
+    for (int t = 0; t < RPT; ++t) {
+        float w[9];
+        unsigned mask = 0;
+        has[t] = ring_slot_v(g + t * GT, r0, r1, c0, c1, H, W, value, w, mask);
+        if (has[t]) {
+            px[t] = aff_pix(w, mask);
+        } else {
+#pragma unroll
+            for (int d = 0; d < 4; ++d) px[t].d[d] = AffDir{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        }
+    }
+    auto ringv = [&](const float* cs, int m, float* out) {
+#pragma unroll
+        for (int j = 0; j < MB; ++j) {
+            float acc = 0.0f;
+            if (j < m) {
+#pragma unroll
+                for (int t = 0; t < RPT; ++t)
+                    if (has[t]) acc += aff_abs_curv<KIND>(px[t], cs[j]);
+            }
+            out[j] = acc;
+        }
+        reduce_vec(out, m);
+    };
+    // Cluster reductions cost a cluster barrier each, so clusters run the
+    // golden section with a 3-step lookahead; single CTAs run it step by step.
+    const float cbest = LA == 3 ? block_search_lookahead<MB>(ringv, sp, (float)(bh * bw), S1)
+                                : block_search_batched<MB>(ringv, sp, (float)(bh * bw), S1);
+    // Blocks of this colour read cj only for blocks of earlier colours, so
+    // writing this block's entry races with no reader.
+    if (g == 0) {
+        cj[(size_t)bi * nbj + bj] = cbest;
+        if (c_out) c_out[(size_t)bi * nbj + bj] = cbest;
+    }
+    if (Q > 1) cg::this_cluster().sync();
+}
+
+template <int KIND, int CT, int Q, int RPT>
+static void launch_coarse(const PhaseArgs& A, const float* partials, float* cj, int nact,
+                          cudaStream_t st) {
+    SearchParams sp{A.alpha, A.G, A.K};
+    constexpr int LA = Q > 1 ? 3 : 1;
+    phase_coarse_kernel<KIND, CT, Q, RPT, LA><<<nact * Q, CT, 0, st>>>(
+        A.S, partials, cj, A.H, A.W, sp, A.lb, A.ncolors, A.colour, A.c_out);
+}
+
+template <int KIND>
+static cudaError_t launch_coarse_kind(const PhaseArgs& A, const float* partials, float* cj,
+                                      cudaStream_t st) {
+    const int b = 1 << A.lb;
+    const int nbi = (A.H + b - 1) / b, nbj = (A.W + b - 1) / b;
+    const int nact = A.ncolors == 2 ? nbi * ((nbj + 1) / 2) : ((nbi + 1) / 2) * ((nbj + 1) / 2);
+    switch (A.lb) {
+        case 6: launch_coarse<KIND, 512, 1, 1>(A, partials, cj, nact, st); break;
+        case 7: launch_coarse<KIND, 256, 4, 1>(A, partials, cj, nact, st); break;
+        case 8: launch_coarse<KIND, 256, 8, 1>(A, partials, cj, nact, st); break;
+        case 9: launch_coarse<KIND, 512, 8, 1>(A, partials, cj, nact, st); break;
+        case 10: launch_coarse<KIND, 1024, 8, 1>(A, partials, cj, nact, st); break;
+        case 11: launch_coarse<KIND, 1024, 8, 2>(A, partials, cj, nact, st); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+size_t coarse_partials_needed(int H, int W) {
+    return (size_t)((H + TILE - 1) / TILE) * (size_t)((W + TILE - 1) / TILE);
+}
+
+size_t coarse_c_needed(int H, int W) {
+    const int b = 1 << COARSE_LB;
+    return (size_t)((H + b - 1) / b) * (size_t)((W + b - 1) / b);
+}
+
+int coarse_level_log2() { return COARSE_LB; }
+
+// One whole level on the coarse path: tile sums, every colour's search, apply.
+cudaError_t launch_level_coarse(const PhaseArgs& A0, float* partials, float* cj,
+                                cudaStream_t st) {
+    dim3 tg((A0.W + TILE - 1) / TILE, (A0.H + TILE - 1) / TILE);
+    tile_sums_kernel<<<tg, 256, 0, st>>>(A0.S, A0.f, A0.H, A0.W, partials);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    for (int k = 0; k < A0.ncolors; ++k) {
+        PhaseArgs A = A0;
+        A.colour = k;
+        e = A.kind == KIND_MEAN ? launch_coarse_kind<KIND_MEAN>(A, partials, cj, st)
+                                : launch_coarse_kind<KIND_GAUSS>(A, partials, cj, st);
+        if (e != cudaSuccess) return e;
+    }
+    const int b = 1 << A0.lb;
+    const int nbj = (A0.W + b - 1) / b;
+    const size_t N = (size_t)A0.H * A0.W;
+    const int grid = (int)std::min<size_t>((N + 255) / 256, 152 * 16);
+    apply_kernel<<<grid, 256, 0, st>>>(A0.S, A0.R, cj, A0.H, A0.W, A0.lb, nbj);
+    return cudaGetLastError();
 }
 
 template <int KIND, int GT>

@@ -281,6 +281,158 @@ __device__ __forceinline__ float block_search_batched(RingV&& ringv, const Searc
     return best.c;
 }
 
+// The batched search with the golden section advanced LA = 3 steps per
+// reduction.  From a state whose next comparison is known the next point is
+// fixed; the point after it depends on one unknown comparison (2 choices),
+// the one after that on two (4 choices): 7 points cover every path of 3
+// steps.  Only the points on the path actually taken are considered, and
+// each is computed by the same operations as in block_search, so the
+// selected c is identical; the extra evaluations trade idle threads for
+// fewer barriers on levels with few blocks.
+struct GoldenState {
+    float lo, hi, x1, x2, E1, E2;
+};
+
+// One golden step from a state whose comparison is decided by `left`;
+// returns the new point (its energy goes in with golden_put).
+__device__ __forceinline__ float golden_take(GoldenState& st, bool left) {
+    if (left) {
+        st.hi = st.x2;
+        st.x2 = st.x1;
+        st.E2 = st.E1;
+        return st.hi - GOLDEN * (st.hi - st.lo);
+    }
+    st.lo = st.x1;
+    st.x1 = st.x2;
+    st.E1 = st.E2;
+    return st.lo + GOLDEN * (st.hi - st.lo);
+}
+
+__device__ __forceinline__ void golden_put(GoldenState& st, bool left, float x, float E) {
+    if (left) {
+        st.x1 = x;
+        st.E1 = E;
+    } else {
+        st.x2 = x;
+        st.E2 = E;
+    }
+}
+
+template <int MB, class RingV>
+__device__ __forceinline__ float block_search_lookahead(RingV&& ringv, const SearchParams& p,
+                                                        float s, float S1) {
+    static_assert(MB >= 7, "a depth-3 lookahead needs 7 candidates per batch");
+    const float c_fid = -S1 / s;
+    const float half_as = 0.5f * p.alpha * s;
+    auto energy = [&](float c, float rk) {
+        float t = c - c_fid;
+        return fmaf(half_as * t, t, rk);
+    };
+    float cs[MB], rk[MB];
+#pragma unroll
+    for (int j = 0; j < MB; ++j) cs[j] = 0.0f;
+    cs[1] = c_fid;
+    ringv(cs, 2, rk);
+    Best best;
+    best.c = 0.0f;
+    best.E = energy(0.0f, rk[0]);
+    const float Rk = rk[1];
+    const float rho = sqrtf(2.0f * Rk / (p.alpha * s));
+    const int mid = (p.G - 1) / 2;
+    float gbest = c_fid, Egbest = INFINITY;
+    for (int i0 = 0; i0 < p.G; i0 += MB) {
+        const int m = min(MB, p.G - i0);
+#pragma unroll
+        for (int j = 0; j < MB; ++j) {
+            float t = (2.0f * (float)(i0 + j)) / (float)(p.G - 1) - 1.0f;
+            cs[j] = c_fid + rho * t;
+        }
+        ringv(cs, m, rk);
+#pragma unroll
+        for (int j = 0; j < MB; ++j)
+            if (j < m) {
+                float E = energy(cs[j], (i0 + j == mid) ? Rk : rk[j]);
+                consider(best, cs[j], E);
+                if (E < Egbest) {
+                    Egbest = E;
+                    gbest = cs[j];
+                }
+            }
+    }
+    const float D = 2.0f * rho / (float)(p.G - 1);
+    GoldenState st;
+    st.lo = gbest - D;
+    st.hi = gbest + D;
+    st.x1 = st.hi - GOLDEN * (st.hi - st.lo);
+    st.x2 = st.lo + GOLDEN * (st.hi - st.lo);
+    cs[0] = st.x1;
+    cs[1] = st.x2;
+    ringv(cs, 2, rk);
+    st.E1 = energy(st.x1, rk[0]);
+    consider(best, st.x1, st.E1);
+    st.E2 = energy(st.x2, rk[1]);
+    consider(best, st.x2, st.E2);
+    int steps = p.K - 2;
+    while (steps > 0) {
+        const int la = steps >= 3 ? 3 : steps;
+        // step 1 (decision known)
+        const bool l0 = st.E1 < st.E2;
+        GoldenState s0 = st;
+        const float p0 = golden_take(s0, l0);
+        cs[0] = p0;
+        int m = 1;
+        // step 2 after each outcome o1 of the next comparison (0 = left)
+        float p1[2], p2[4];
+        GoldenState s1[2];
+#pragma unroll
+        for (int o1 = 0; o1 < 2; ++o1) {
+            s1[o1] = s0;
+            golden_put(s1[o1], l0, p0, 0.0f);
+            p1[o1] = golden_take(s1[o1], o1 == 0);
+#pragma unroll
+            for (int o2 = 0; o2 < 2; ++o2) {
+                GoldenState s2 = s1[o1];
+                golden_put(s2, o1 == 0, p1[o1], 0.0f);
+                p2[2 * o1 + o2] = golden_take(s2, o2 == 0);
+            }
+        }
+        if (la >= 2) {
+            cs[1] = p1[0];
+            cs[2] = p1[1];
+            m = 3;
+        }
+        if (la >= 3) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) cs[3 + q] = p2[q];
+            m = 7;
+        }
+        ringv(cs, m, rk);
+        // walk the path actually taken
+        const float E0 = energy(p0, rk[0]);
+        consider(best, p0, E0);
+        st = s0;
+        golden_put(st, l0, p0, E0);
+        if (la >= 2) {
+            const bool l1 = st.E1 < st.E2;
+            const int o1 = l1 ? 0 : 1;
+            const float q1 = golden_take(st, l1);
+            const float E1v = energy(q1, rk[1 + o1]);
+            consider(best, q1, E1v);
+            golden_put(st, l1, q1, E1v);
+            if (la >= 3) {
+                const bool l2 = st.E1 < st.E2;
+                const int o2 = l2 ? 0 : 1;
+                const float q2 = golden_take(st, l2);
+                const float E2v = energy(q2, rk[3 + 2 * o1 + o2]);
+                consider(best, q2, E2v);
+                golden_put(st, l2, q2, E2v);
+            }
+        }
+        steps -= la;
+    }
+    return best.c;
+}
+
 // ---------------------------------------------------------------------------
 // Block geometry.
 
@@ -333,12 +485,11 @@ __device__ __forceinline__ void perim_pos(int t, int h, int w, int& i, int& j) {
 // outside the block, clipped to the image) then the inner frame (the block's
 // boundary pixels, less those whose clamped 3x3 stencil lies in the block).
 // Returns false when the slot holds no ring pixel; else loads the pixel's
-// clamped window from the phase state and the mask of window entries that
-// lie in the block.
-__device__ __forceinline__ bool ring_slot(int j, int r0, int r1, int c0, int c1, int H, int W,
-                                          const float* __restrict__ S,
-                                          const float* __restrict__ R, int lb, int ncol, int k,
-                                          float w[9], unsigned& mask) {
+// clamped window through value(r, c) (the phase state) and the mask of window
+// entries that lie in the block.
+template <class Value>
+__device__ __forceinline__ bool ring_slot_v(int j, int r0, int r1, int c0, int c1, int H, int W,
+                                            Value&& value, float w[9], unsigned& mask) {
     const int bh = r1 - r0, bw = c1 - c0;
     const int Pout = perim_count(bh + 2, bw + 2);
     const int Pin = perim_count(bh, bw);
@@ -363,11 +514,20 @@ __device__ __forceinline__ bool ring_slot(int j, int r0, int r1, int c0, int c1,
 #pragma unroll
         for (int b = 0; b < 3; ++b) {
             int qr = clampi(rr + a - 1, 0, H - 1), qc = clampi(cc + b - 1, 0, W - 1);
-            w[3 * a + b] = phase_read(S, R, qr, qc, W, lb, ncol, k);
+            w[3 * a + b] = value(qr, qc);
             bool inA = qr >= r0 && qr < r1 && qc >= c0 && qc < c1;
             mask |= (inA ? 1u : 0u) << (3 * a + b);
         }
     return true;
+}
+
+__device__ __forceinline__ bool ring_slot(int j, int r0, int r1, int c0, int c1, int H, int W,
+                                          const float* __restrict__ S,
+                                          const float* __restrict__ R, int lb, int ncol, int k,
+                                          float w[9], unsigned& mask) {
+    return ring_slot_v(j, r0, r1, c0, c1, H, W,
+                       [&](int r, int c) { return phase_read(S, R, r, c, W, lb, ncol, k); }, w,
+                       mask);
 }
 
 }  // namespace cm

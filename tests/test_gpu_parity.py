@@ -171,10 +171,13 @@ def run_solve(f, alpha, kind, cycles, tol=0.0, use_graph=1, ncolors=4, levels=0)
     return host(u), st
 
 
-def test_solve_equals_phase_sequence_and_is_deterministic():
-    """cm_solve (graph replay and direct launches) performs exactly the
-    phase sequence of Alg. 3: bit-identical to chaining cm_phase calls."""
-    img = synth.piecewise_image(67, 45, 9, 5, 0.08)
+@pytest.mark.parametrize("shape", [(67, 45), (300, 260)])
+def test_solve_equals_level_sequence_and_is_deterministic(shape):
+    """cm_solve (graph replay and direct launches) performs exactly the level
+    sequence of Alg. 3: bit-identical to chaining cm_level calls; on levels
+    below the coarse threshold also to chaining cm_phase calls."""
+    H, W = shape
+    img = synth.piecewise_image(H, W, 9, 5, 0.08)
     f = img.f
     ua, sa = run_solve(f, 20.0, cm.MEAN, 3, use_graph=1)
     ub, sb = run_solve(f, 20.0, cm.MEAN, 3, use_graph=0)
@@ -182,19 +185,73 @@ def test_solve_equals_phase_sequence_and_is_deterministic():
     np.testing.assert_array_equal(ua, ub)
     np.testing.assert_array_equal(ua, uc)
     assert sa.trace() == sb.trace()
-    # manual chain
-    S = to_dev(f)
+    L = cm.cm_auto_levels(H, W)
     fd = to_dev(f)
-    R = torch.empty_like(S)
-    L = cm.cm_auto_levels(67, 45)
+    S, R = to_dev(f), torch.empty_like(fd)
     for _ in range(3):
         for j in range(L):
-            for k in range(4):
-                cm.cm_phase(S, R, fd, 20.0, cm.MEAN, 1 << j, k)
+            cm.cm_level(S, R, fd, 20.0, cm.MEAN, 1 << j)
             S, R = R, S
     torch.cuda.synchronize()
     np.testing.assert_array_equal(ua, host(S))
     assert sa.trace()[-1] == cm.cm_energy(S, fd, 20.0, cm.MEAN)
+    if L <= 6:   # every level below b = 64: phases and levels coincide
+        S, R = to_dev(f), torch.empty_like(fd)
+        for _ in range(3):
+            for j in range(L):
+                for k in range(4):
+                    cm.cm_phase(S, R, fd, 20.0, cm.MEAN, 1 << j, k)
+                S, R = R, S
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(ua, host(S))
+
+
+@pytest.mark.parametrize("case", [((512, 512), cm.GAUSS, 15.0, (64, 128, 256)),
+                                  ((1024, 1024), cm.MEAN, 20.0, (64, 512)),
+                                  ((300, 260), cm.MEAN, 20.0, (64, 128))],
+                         ids=["512-gauss", "1024-mean", "300x260-mean"])
+def test_level_parity_coarse(case):
+    """Coarse levels through cm_level (tile sums, deferred apply): R = S + c
+    on every block, and each colour's shifts match the oracle solved from the
+    state the earlier colours left (reconstructed as S + c in FP32)."""
+    shape, kind, alpha, levels = case
+    H, W = shape
+    img = synth.piecewise_image(H, W, 4242 + H, 20, 0.08)
+    f = img.f
+    u, _ = run_solve(f, alpha, kind, 1)
+    rng = np.random.default_rng(3)
+    tot = ties = 0
+    fails = []
+    for b in levels:
+        nbi, nbj = (H + b - 1) // b, (W + b - 1) // b
+        cbuf = torch.full((nbi * nbj,), float("nan"), device=DEV)
+        S = to_dev(u)
+        R = torch.empty_like(S)
+        cm.cm_level(S, R, to_dev(f), alpha, kind, b, c_out=cbuf)
+        torch.cuda.synchronize()
+        cg, Rg = host(cbuf), host(R)
+        assert np.all(np.isfinite(cg))
+        for bi in range(nbi):
+            for bj in range(nbj):
+                blk = (slice(bi * b, min((bi + 1) * b, H)), slice(bj * b, min((bj + 1) * b, W)))
+                np.testing.assert_array_equal(Rg[blk], u[blk] + np.float32(cg[bi * nbj + bj]))
+        for k in range(4):
+            state = u.copy()
+            for kk in range(k):
+                for bi, bj, r0, c0, bh, bw in blocks_of_colour(H, W, b, 4, kk):
+                    state[r0:r0 + bh, c0:c0 + bw] += np.float32(cg[bi * nbj + bj])
+            blocks = [(bi, bj) for bi, bj, *_ in blocks_of_colour(H, W, b, 4, k)]
+            pick = rng.choice(len(blocks), size=min(24, len(blocks)), replace=False)
+            sample = {blocks[i] for i in pick}
+            cgd = {(bi, bj): cg[bi * nbj + bj] for bi, bj in sample}
+            n, m, t, fl = compare_phase(state.astype(np.float64), f.astype(np.float64), cgd,
+                                        alpha, kind, b, 4, k, {}, sample=sample)
+            tot += n
+            ties += t
+            fails += fl
+    print(f"\ncoarse {shape} kind={kind}: n={tot} ties={ties}")
+    assert not fails, fails[:5]
+    assert ties <= max(2, 0.02 * tot)
 
 
 @pytest.mark.parametrize("kind", [cm.MEAN, cm.GAUSS])
