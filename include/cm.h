@@ -154,6 +154,32 @@ int cm_solve(cm_ctx* ctx, const float* f, int H, int W, float alpha, int kind, i
              const cm_options* opts /* host, nullable */, cm_stats* stats /* host, nullable */,
              void* stream);
 
+/* Energy without allocation.  The paper has no counterpart: this is a
+ * service for callers that cannot let a library allocate device memory -- a
+ * host whose caching allocator already holds (nearly) all of it, code that
+ * must not take the implicit device-wide synchronisation of cudaMalloc and
+ * cudaFree, or a pipeline that forbids allocation after start-up.  It
+ * computes the same F(u) as cm_energy with the same kernel, but takes no
+ * context and allocates nothing: its scratch (one FP64 partial per 32 x 32
+ * tile and an arrival counter) is a fixed array inside the library, about
+ * 128 KiB, which every GPU that loads the library holds until the process
+ * exits.
+ * u, f: device, H x W, row-major float32 on the current device.  E_dev:
+ * device pointer to one double that receives F(u) when the work on `stream`
+ * completes (the call does not synchronise).
+ * Returns CM_ERR_INVALID for null pointers, sizes < 1, a bad alpha or kind,
+ * and for images with more than CM_NOALLOC_MAX_TILES tiles of 32 x 32 pixels
+ * (ceil(H/32) * ceil(W/32) > 16384, e.g. larger than 4096 x 4096);
+ * CM_ERR_CUDA if a CUDA call fails.
+ * The first call on a device looks up the array's device address (with that
+ * device current); make that first call before any stream capture.  Every
+ * call shares the one array and clears its counter before use, so calls whose
+ * work overlaps on the GPU (on different streams, or from several host
+ * threads without ordering) race and must be serialised by the caller. */
+#define CM_NOALLOC_MAX_TILES 16384
+int cm_energy_noalloc(const float* u, const float* f, int H, int W, float alpha, int kind,
+                      double* E_dev, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

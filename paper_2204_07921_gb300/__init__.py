@@ -16,7 +16,7 @@ from .build import LIB, build as build_library
 
 __all__ = [
     "CMError", "Options", "Stats", "Context", "load", "cm_energy", "cm_curvature", "cm_phase",
-    "cm_level",
+    "cm_level", "cm_energy_noalloc",
     "cm_solve", "cm_auto_levels", "MEAN", "GAUSS",
 ]
 
@@ -65,6 +65,7 @@ SIGNATURES = {
     "cm_energy": (_I, [_P, _P, _P, _I, _I, _F, _I, ctypes.POINTER(_D), _P]),
     "cm_curvature": (_I, [_P, _P, _I, _I, _I, _P, _P]),
     "cm_phase": (_I, [_P, _P, _P, _P, _I, _I, _F, _I, _I, _I, ctypes.POINTER(Options), _P, _P]),
+    "cm_energy_noalloc": (_I, [_P, _P, _I, _I, _F, _I, _P, _P]),
     "cm_level": (_I, [_P, _P, _P, _P, _I, _I, _F, _I, _I, ctypes.POINTER(Options), _P, _P]),
     "cm_solve": (_I, [_P, _P, _I, _I, _F, _I, _I, _I, _D, _P, _P, ctypes.POINTER(Options),
                       ctypes.POINTER(Stats), _P]),
@@ -176,6 +177,24 @@ def cm_energy(u, f, alpha: float, kind: int, ctx: Context | None = None, stream=
     c._check(load().cm_energy(c.handle, u.data_ptr(), f.data_ptr(), H, W, float(alpha), kind,
                               ctypes.byref(E), _stream_ptr(stream)))
     return E.value
+
+
+def cm_energy_noalloc(u, f, alpha: float, kind: int, E_out, stream=None):
+    """F(u) into the one-element float64 CUDA tensor E_out, without any
+    device allocation (the library's fixed scratch array; see include/cm.h)."""
+    import torch
+    _img(u, "u"), _img(f, "f")
+    if u.shape != f.shape:
+        raise ValueError("u and f differ in shape")
+    if not (isinstance(E_out, torch.Tensor) and E_out.is_cuda and E_out.dtype == torch.float64
+            and E_out.numel() >= 1):
+        raise TypeError("E_out: expected a CUDA float64 tensor")
+    H, W = u.shape
+    rc = load().cm_energy_noalloc(u.data_ptr(), f.data_ptr(), H, W, float(alpha), kind,
+                                  E_out.data_ptr(), _stream_ptr(stream))
+    if rc != CM_OK:
+        raise CMError(rc, "cm_energy_noalloc failed")
+    return E_out
 
 
 def cm_curvature(u, kind: int, out=None, ctx: Context | None = None, stream=None):
