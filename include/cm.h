@@ -154,6 +154,26 @@ int cm_solve(cm_ctx* ctx, const float* f, int H, int W, float alpha, int kind, i
              const cm_options* opts /* host, nullable */, cm_stats* stats /* host, nullable */,
              void* stream);
 
+/* Batched solve: n independent images of uneven sizes (Alg. 3 on each).
+ * Arrays f, H, W, alpha, kind, u0 (nullable; entries may be NULL) and u_out
+ * are HOST arrays of length n; the image pointers they hold are device
+ * pointers.  levels, cycles, tol and opts apply to every image (levels = 0:
+ * cm_auto_levels per image).  One CUDA graph holds one cycle of every image
+ * (an independent chain per image, so images run concurrently); each image
+ * stops on its own relative-energy test (Eq. reerr), evaluated on the device,
+ * after which its kernels return at entry; the host replays the graph until no
+ * image is active, reading back one small state array per cycle.  Every
+ * image's result and statistics equal those of cm_solve on that image alone
+ * (same kernels, same order).  stats: host array of n (nullable).  Returns
+ * CM_NOT_CONVERGED if tol > 0 and an image hit the cap, CM_ERR_NUMERIC on a
+ * non-finite energy.  Scratch: one context arena (an image-sized buffer and
+ * small sums per image).  Synchronises `stream`. */
+int cm_solve_batched(cm_ctx* ctx, int n, const float* const* f, const int* H, const int* W,
+                     const float* alpha, const int* kind, int levels, int cycles, double tol,
+                     const float* const* u0, float* const* u_out,
+                     const cm_options* opts /* host, nullable */,
+                     cm_stats* stats /* host, n entries, nullable */, void* stream);
+
 /* Energy without allocation.  The paper has no counterpart: this is a
  * service for callers that cannot let a library allocate device memory -- a
  * host whose caching allocator already holds (nearly) all of it, code that

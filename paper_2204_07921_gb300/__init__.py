@@ -16,7 +16,7 @@ from .build import LIB, build as build_library
 
 __all__ = [
     "CMError", "Options", "Stats", "Context", "load", "cm_energy", "cm_curvature", "cm_phase",
-    "cm_level", "cm_energy_noalloc",
+    "cm_level", "cm_energy_noalloc", "cm_solve_batched",
     "cm_solve", "cm_auto_levels", "MEAN", "GAUSS",
 ]
 
@@ -67,6 +67,10 @@ SIGNATURES = {
     "cm_phase": (_I, [_P, _P, _P, _P, _I, _I, _F, _I, _I, _I, ctypes.POINTER(Options), _P, _P]),
     "cm_energy_noalloc": (_I, [_P, _P, _I, _I, _F, _I, _P, _P]),
     "cm_level": (_I, [_P, _P, _P, _P, _I, _I, _F, _I, _I, ctypes.POINTER(Options), _P, _P]),
+    "cm_solve_batched": (_I, [_P, _I, ctypes.POINTER(_P), ctypes.POINTER(_I), ctypes.POINTER(_I),
+                              ctypes.POINTER(_F), ctypes.POINTER(_I), _I, _I, _D,
+                              ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(Options),
+                              ctypes.POINTER(Stats), _P]),
     "cm_solve": (_I, [_P, _P, _I, _I, _F, _I, _I, _I, _D, _P, _P, ctypes.POINTER(Options),
                       ctypes.POINTER(Stats), _P]),
 }
@@ -259,3 +263,34 @@ def cm_solve(f, alpha: float, kind: int, levels: int = 0, cycles: int = 20, tol:
                              _stream_ptr(stream)),
              ok=(CM_OK, CM_NOT_CONVERGED))
     return u_out, st
+
+
+def cm_solve_batched(fs, alphas, kinds, levels: int = 0, cycles: int = 2000, tol: float = 1e-4,
+                     u0s=None, u_outs=None, options: Options | None = None,
+                     ctx: Context | None = None, stream=None):
+    """Solve many images (lists of CUDA float32 H x W tensors) together.
+    Returns (u_outs, [Stats])."""
+    import torch
+    n = len(fs)
+    if n == 0:
+        return [], []
+    for i, t in enumerate(fs):
+        _img(t, f"f[{i}]")
+    if u_outs is None:
+        u_outs = [torch.empty_like(t) for t in fs]
+    c = _ctx(ctx, fs[0])
+    PA = _P * n
+    f_arr = PA(*[t.data_ptr() for t in fs])
+    u_arr = PA(*[t.data_ptr() for t in u_outs])
+    u0_arr = PA(*[(t.data_ptr() if t is not None else None) for t in u0s]) if u0s else None
+    H = (_I * n)(*[t.shape[0] for t in fs])
+    W = (_I * n)(*[t.shape[1] for t in fs])
+    al = (_F * n)(*[float(a) for a in alphas])
+    kd = (_I * n)(*[int(k) for k in kinds])
+    opts = options or default_options()
+    stats = (Stats * n)()
+    c._check(load().cm_solve_batched(c.handle, n, f_arr, H, W, al, kd, levels, cycles, float(tol),
+                                     u0_arr, u_arr, ctypes.byref(opts), stats,
+                                     _stream_ptr(stream)),
+             ok=(CM_OK, CM_NOT_CONVERGED))
+    return u_outs, list(stats)

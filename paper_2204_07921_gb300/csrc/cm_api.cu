@@ -12,7 +12,10 @@
 
 #include <string>
 
+#include <vector>
+
 #include "../../include/cm.h"
+#include "cm_batched.h"
 #include "cm_kernels.h"
 
 struct GraphKey {
@@ -39,6 +42,13 @@ struct cm_ctx {
     double* E_dev = nullptr;
     double* E_pinned = nullptr;
     cudaStream_t cap_stream = nullptr;
+    // batched solve: arena, capture streams/events and the cached batch graph
+    unsigned char* arena = nullptr;
+    size_t arena_cap = 0;
+    std::vector<cudaStream_t> bstreams;
+    std::vector<cudaEvent_t> bevents;
+    cudaGraphExec_t bgraph = nullptr;
+    std::vector<unsigned char> bgraph_key;
     struct Cached {
         bool valid = false;
         GraphKey key;
@@ -148,17 +158,19 @@ cm::PhaseArgs phase_args(const float* S, float* R, const float* f, int H, int W,
 // coarse threshold run one phase kernel per colour; coarse levels run the
 // tile-sum / search / apply sequence.  c_out (nullable) receives every
 // block's shift.
-cudaError_t enqueue_level(cm_ctx* ctx, const float* S, float* R, const float* f, int H, int W,
-                          float alpha, int kind, int lb, const cm_options& o, float* c_out,
-                          cudaStream_t st) {
+cudaError_t enqueue_level(float* tsums, float* cj, const float* S, float* R, const float* f,
+                          int H, int W, float alpha, int kind, int lb, const cm_options& o,
+                          float* c_out, const int* active, cudaStream_t st) {
     if (lb >= cm::coarse_level_log2()) {
         cm::PhaseArgs a = phase_args(S, R, f, H, W, alpha, kind, lb, 0, o);
         a.c_out = c_out;
-        return cm::launch_level_coarse(a, ctx->tsums, ctx->cj, st);
+        a.active = active;
+        return cm::launch_level_coarse(a, tsums, cj, st);
     }
     for (int k = 0; k < o.ncolors; ++k) {
         cm::PhaseArgs a = phase_args(S, R, f, H, W, alpha, kind, lb, k, o);
         a.c_out = c_out;
+        a.active = active;
         cudaError_t e = cm::launch_phase(a, st);
         if (e != cudaSuccess) return e;
     }
@@ -173,7 +185,8 @@ cudaError_t enqueue_cycle(cm_ctx* ctx, float* X, float* Y, const float* f, int H
     float* S = X;
     float* R = Y;
     for (int j = 0; j < levels; ++j) {
-        cudaError_t e = enqueue_level(ctx, S, R, f, H, W, alpha, kind, j, o, nullptr, st);
+        cudaError_t e = enqueue_level(ctx->tsums, ctx->cj, S, R, f, H, W, alpha, kind, j, o,
+                                      nullptr, nullptr, st);
         if (e != cudaSuccess) return e;
         float* t = S;
         S = R;
@@ -241,6 +254,10 @@ void cm_destroy(cm_ctx* ctx) {
     if (ctx->E_dev) cudaFree(ctx->E_dev);
     if (ctx->E_pinned) cudaFreeHost(ctx->E_pinned);
     if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+    if (ctx->bgraph) cudaGraphExecDestroy(ctx->bgraph);
+    for (auto s : ctx->bstreams) cudaStreamDestroy(s);
+    for (auto e : ctx->bevents) cudaEventDestroy(e);
+    if (ctx->arena) cudaFree(ctx->arena);
     delete ctx;
 }
 
@@ -313,7 +330,8 @@ int cm_level(cm_ctx* ctx, const float* S, float* R, const float* f, int H, int W
     CM_CUDA(cudaSetDevice(ctx->device));
     rc = ensure_coarse(ctx, H, W);
     if (rc) return rc;
-    CM_CUDA(enqueue_level(ctx, S, R, f, H, W, alpha, kind, lb, o, c_out, (cudaStream_t)stream));
+    CM_CUDA(enqueue_level(ctx->tsums, ctx->cj, S, R, f, H, W, alpha, kind, lb, o, c_out, nullptr,
+                          (cudaStream_t)stream));
     return CM_OK;
 }
 
@@ -422,6 +440,220 @@ int cm_solve(cm_ctx* ctx, const float* f, int H, int W, float alpha, int kind, i
         stats->energy_final = Eprev;
     }
     if (tol > 0.0 && !conv) return fail(ctx, CM_NOT_CONVERGED, "cm_solve: cycle cap reached");
+    return CM_OK;
+}
+
+
+// ---------------------------------------------------------------------------
+// Batched solve.
+
+namespace {
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+struct ImgLayout {
+    size_t ubuf, partials, ticket, tsums, cj, trace;
+    int L;
+};
+
+}  // namespace
+
+int cm_solve_batched(cm_ctx* ctx, int n, const float* const* f, const int* H, const int* W,
+                     const float* alpha, const int* kind, int levels, int cycles, double tol,
+                     const float* const* u0, float* const* u_out, const cm_options* opts,
+                     cm_stats* stats, void* stream) {
+    if (!ctx) return CM_ERR_INVALID;
+    cm_options o;
+    cm_options_default(&o);
+    if (opts) o = *opts;
+    int rc = check_opts(ctx, o);
+    if (rc) return rc;
+    if (n < 1 || !f || !H || !W || !alpha || !kind || !u_out || levels < 0 || cycles < 0 ||
+        !(tol >= 0.0) || !isfinite(tol))
+        return fail(ctx, CM_ERR_INVALID, "cm_solve_batched: invalid argument");
+    for (int i = 0; i < n; ++i) {
+        if (!f[i] || !u_out[i] || u_out[i] == f[i] || H[i] < 1 || W[i] < 1 ||
+            !finite_positive(alpha[i]) || (kind[i] != 0 && kind[i] != 1))
+            return fail(ctx, CM_ERR_INVALID, "cm_solve_batched: invalid image " + std::to_string(i));
+        const int L = levels > 0 ? levels : cm_auto_levels(H[i], W[i]);
+        if (L - 1 > cm::max_level_log2())
+            return fail(ctx, CM_ERR_INVALID, "cm_solve_batched: too many levels");
+    }
+    CM_CUDA(cudaSetDevice(ctx->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    const int trace_cap = std::min(cycles, o.max_trace);
+    // arena: per-image scratch, then the state array and initial energies
+    std::vector<ImgLayout> lay(n);
+    size_t off = 0;
+    for (int i = 0; i < n; ++i) {
+        const size_t N = (size_t)H[i] * W[i];
+        ImgLayout& L = lay[i];
+        L.L = levels > 0 ? levels : cm_auto_levels(H[i], W[i]);
+        L.ubuf = off; off = align256(off + N * sizeof(float));
+        L.partials = off; off = align256(off + cm::energy_partials_needed(H[i], W[i]) * sizeof(double));
+        L.ticket = off; off = align256(off + sizeof(unsigned int));
+        L.tsums = off; off = align256(off + cm::coarse_partials_needed(H[i], W[i]) * sizeof(float));
+        L.cj = off; off = align256(off + cm::coarse_c_needed(H[i], W[i]) * sizeof(float));
+        L.trace = off; off = align256(off + (size_t)(trace_cap + 1) * sizeof(double));
+    }
+    const size_t state_off = off;
+    const size_t sb = cm::batch_state_bytes();
+    off = align256(off + (size_t)n * sb);
+    const size_t e0_off = off;
+    off = align256(off + (size_t)n * sizeof(double));
+    const size_t enow_off = off;
+    off = align256(off + (size_t)n * sizeof(double));
+    if (off > ctx->arena_cap) {
+        if (ctx->bgraph) cudaGraphExecDestroy(ctx->bgraph);
+        ctx->bgraph = nullptr;
+        ctx->bgraph_key.clear();
+        if (ctx->arena) cudaFree(ctx->arena);
+        ctx->arena = nullptr;
+        ctx->arena_cap = 0;
+        CM_CUDA(cudaMalloc(&ctx->arena, off));
+        ctx->arena_cap = off;
+    }
+    unsigned char* A = ctx->arena;
+    auto state_ptr = [&](int i) { return (cm::ImgDev*)(A + state_off + (size_t)i * sb); };
+    auto active_ptr = [&](int i) { return (const int*)(A + state_off + (size_t)i * sb + cm::batch_active_offset()); };
+    double* E0 = (double*)(A + e0_off);
+    double* Enow = (double*)(A + enow_off);
+    // initial state u_0 and energies
+    for (int i = 0; i < n; ++i) {
+        const size_t N = (size_t)H[i] * W[i];
+        const float* src = (u0 && u0[i]) ? u0[i] : f[i];
+        if (src != u_out[i])
+            CM_CUDA(cudaMemcpyAsync(u_out[i], src, N * sizeof(float), cudaMemcpyDeviceToDevice, st));
+        CM_CUDA(cudaMemsetAsync(A + lay[i].ticket, 0, sizeof(unsigned int), st));
+        CM_CUDA(cm::launch_energy(u_out[i], f[i], H[i], W[i], alpha[i], kind[i],
+                                  (double*)(A + lay[i].partials), (unsigned int*)(A + lay[i].ticket),
+                                  &E0[i], st));
+    }
+    CM_CUDA(cm::launch_batch_init(state_ptr(0), E0, n, cycles, st));
+    // the batch-cycle graph (cached for identical batches)
+    std::vector<unsigned char> key;
+    auto put = [&](const void* p, size_t b) {
+        const unsigned char* c = (const unsigned char*)p;
+        key.insert(key.end(), c, c + b);
+    };
+    put(&n, sizeof(n));
+    put(&o, sizeof(o));
+    put(&levels, sizeof(levels));
+    put(&cycles, sizeof(cycles));
+    put(&tol, sizeof(tol));
+    put(&ctx->arena, sizeof(ctx->arena));
+    for (int i = 0; i < n; ++i) {
+        put(&f[i], sizeof(f[i]));
+        put(&u_out[i], sizeof(u_out[i]));
+        put(&H[i], sizeof(int));
+        put(&W[i], sizeof(int));
+        put(&alpha[i], sizeof(float));
+        put(&kind[i], sizeof(int));
+    }
+    if (!ctx->bgraph || ctx->bgraph_key != key) {
+        if (ctx->bgraph) cudaGraphExecDestroy(ctx->bgraph);
+        ctx->bgraph = nullptr;
+        ctx->bgraph_key.clear();
+        while ((int)ctx->bstreams.size() < n) {
+            cudaStream_t s2;
+            CM_CUDA(cudaStreamCreateWithFlags(&s2, cudaStreamNonBlocking));
+            ctx->bstreams.push_back(s2);
+        }
+        while ((int)ctx->bevents.size() < n + 1) {
+            cudaEvent_t e2;
+            CM_CUDA(cudaEventCreateWithFlags(&e2, cudaEventDisableTiming));
+            ctx->bevents.push_back(e2);
+        }
+        cudaStream_t cs = ctx->cap_stream;
+        CM_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+        cudaError_t ce = cudaEventRecord(ctx->bevents[n], cs);
+        for (int i = 0; i < n && ce == cudaSuccess; ++i) {
+            cudaStream_t si = ctx->bstreams[i];
+            ce = cudaStreamWaitEvent(si, ctx->bevents[n], 0);
+            const ImgLayout& L = lay[i];
+            float* X = u_out[i];
+            float* Y = (float*)(A + L.ubuf);
+            float* Sb = X;
+            float* Rb = Y;
+            for (int j = 0; j < L.L && ce == cudaSuccess; ++j) {
+                ce = enqueue_level((float*)(A + L.tsums), (float*)(A + L.cj), Sb, Rb, f[i], H[i],
+                                   W[i], alpha[i], kind[i], j, o, nullptr, active_ptr(i), si);
+                float* t = Sb;
+                Sb = Rb;
+                Rb = t;
+            }
+            const size_t N = (size_t)H[i] * W[i];
+            if (ce == cudaSuccess && (L.L & 1)) ce = cm::launch_batch_copy(Sb, X, N, active_ptr(i), si);
+            if (ce == cudaSuccess)
+                ce = cm::launch_energy(X, f[i], H[i], W[i], alpha[i], kind[i],
+                                       (double*)(A + L.partials), (unsigned int*)(A + L.ticket),
+                                       &Enow[i], si, active_ptr(i));
+            if (ce == cudaSuccess)
+                ce = cm::launch_batch_stop(state_ptr(i), &Enow[i], tol, cycles,
+                                           (double*)(A + L.trace), trace_cap, si);
+            if (ce == cudaSuccess) ce = cudaEventRecord(ctx->bevents[i], si);
+            if (ce == cudaSuccess) ce = cudaStreamWaitEvent(cs, ctx->bevents[i], 0);
+        }
+        cudaGraph_t g;
+        cudaError_t ee = cudaStreamEndCapture(cs, &g);
+        if (ce != cudaSuccess) return cuda_fail(ctx, ce, "capture batch cycle");
+        if (ee != cudaSuccess) return cuda_fail(ctx, ee, "end batch capture");
+        cudaError_t ie = cudaGraphInstantiate(&ctx->bgraph, g, 0);
+        cudaGraphDestroy(g);
+        if (ie != cudaSuccess) return cuda_fail(ctx, ie, "batch graph instantiate");
+        ctx->bgraph_key = key;
+    }
+    // replay until every image has stopped (each replay is one cycle of
+    // every still-active image)
+    std::vector<unsigned char> host_state((size_t)n * sb);
+    int replays = 0;
+    for (; replays < cycles; ++replays) {
+        CM_CUDA(cudaGraphLaunch(ctx->bgraph, st));
+        CM_CUDA(cudaMemcpyAsync(host_state.data(), state_ptr(0), (size_t)n * sb,
+                                cudaMemcpyDeviceToHost, st));
+        CM_CUDA(cudaStreamSynchronize(st));
+        int any = 0;
+        for (int i = 0; i < n; ++i) {
+            int c, cv, v, ne, act;
+            double E;
+            cm::batch_read_state(host_state.data() + (size_t)i * sb, &c, &cv, &v, &E, &ne, &act);
+            any |= act;
+        }
+        if (!any) break;
+    }
+    if (cycles == 0) {
+        CM_CUDA(cudaMemcpyAsync(host_state.data(), state_ptr(0), (size_t)n * sb,
+                                cudaMemcpyDeviceToHost, st));
+    }
+    std::vector<double> e0h(n);
+    CM_CUDA(cudaMemcpyAsync(e0h.data(), E0, n * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CM_CUDA(cudaStreamSynchronize(st));
+    int status = CM_OK;
+    for (int i = 0; i < n; ++i) {
+        int c, cv, v, ne, act;
+        double E;
+        cm::batch_read_state(host_state.data() + (size_t)i * sb, &c, &cv, &v, &E, &ne, &act);
+        if (ne) status = CM_ERR_NUMERIC;
+        else if (tol > 0.0 && !cv && status == CM_OK) status = CM_NOT_CONVERGED;
+        if (stats) {
+            cm_stats& s2 = stats[i];
+            memset(&s2, 0, sizeof(s2));
+            s2.cycles_run = c;
+            s2.converged = cv;
+            s2.monotone_violations = v;
+            s2.levels = lay[i].L;
+            s2.energy_initial = e0h[i];
+            s2.energy_final = c > 0 ? E : e0h[i];
+            const int tl = std::min(c, trace_cap);
+            s2.energy_trace[0] = e0h[i];
+            if (tl > 0)
+                CM_CUDA(cudaMemcpy(&s2.energy_trace[1], (double*)(A + lay[i].trace) + 1,
+                                   (size_t)tl * sizeof(double), cudaMemcpyDeviceToHost));
+            s2.trace_len = tl + 1;
+        }
+    }
+    if (status == CM_ERR_NUMERIC) return fail(ctx, status, "cm_solve_batched: non-finite energy");
+    if (status == CM_NOT_CONVERGED) return fail(ctx, status, "cm_solve_batched: cycle cap reached");
     return CM_OK;
 }
 

@@ -23,7 +23,9 @@ __global__ void __launch_bounds__(256) energy_kernel(const float* __restrict__ u
                                                      const float* __restrict__ f, int H, int W,
                                                      float alpha, double* __restrict__ partials,
                                                      unsigned int* __restrict__ ticket,
-                                                     double* __restrict__ E_out) {
+                                                     double* __restrict__ E_out,
+                                                     const int* __restrict__ active) {
+    if (active && *active == 0) return;
     __shared__ float tile[E_TH + 2][E_TW + 3];
     __shared__ double wsum[8];
     __shared__ bool is_last;
@@ -104,12 +106,12 @@ __global__ void curvature_kernel(const float* __restrict__ u, int H, int W,
 
 cudaError_t launch_energy(const float* u, const float* f, int H, int W, float alpha, int kind,
                           double* partials, unsigned int* ticket, double* E_out,
-                          cudaStream_t st) {
+                          cudaStream_t st, const int* active) {
     dim3 grid((W + E_TW - 1) / E_TW, (H + E_TH - 1) / E_TH);
     if (kind == KIND_MEAN)
-        energy_kernel<KIND_MEAN><<<grid, 256, 0, st>>>(u, f, H, W, alpha, partials, ticket, E_out);
+        energy_kernel<KIND_MEAN><<<grid, 256, 0, st>>>(u, f, H, W, alpha, partials, ticket, E_out, active);
     else
-        energy_kernel<KIND_GAUSS><<<grid, 256, 0, st>>>(u, f, H, W, alpha, partials, ticket, E_out);
+        energy_kernel<KIND_GAUSS><<<grid, 256, 0, st>>>(u, f, H, W, alpha, partials, ticket, E_out, active);
     return cudaGetLastError();
 }
 

@@ -18,11 +18,12 @@ struct PhaseArgs {
     int G, K;         // block-search budget
     int use_paper;    // paper's one-step candidate on the finest level
     float* c_out;     // nullable: per-block corrections
+    const int* active = nullptr;   // nullable: kernels return at once when *active == 0
 };
 
 cudaError_t launch_energy(const float* u, const float* f, int H, int W, float alpha, int kind,
                           double* partials, unsigned int* ticket, double* E_out,
-                          cudaStream_t st);
+                          cudaStream_t st, const int* active = nullptr);
 size_t energy_partials_needed(int H, int W);
 cudaError_t launch_curvature(const float* u, int H, int W, int kind, float* out,
                              cudaStream_t st);

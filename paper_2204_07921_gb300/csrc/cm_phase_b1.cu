@@ -182,7 +182,9 @@ __global__ void __launch_bounds__(128, CM_B1_MIN_BLOCKS) phase_b1_kernel(const f
                                                        float* __restrict__ R,
                                                        const float* __restrict__ f, int H,
                                                        int W, SearchParams sp, int k,
-                                                       int use_paper, float* __restrict__ c_out) {
+                                                       int use_paper, float* __restrict__ c_out,
+                                                       const int* __restrict__ active) {
+    if (active && *active == 0) return;
     constexpr int TW = B1Tile<NCOL>::TW, TH = B1Tile<NCOL>::TH;
     __shared__ float tile[TH + 4][TW + 5];
     const int r0 = blockIdx.y * TH, c0 = blockIdx.x * TW;
@@ -302,18 +304,18 @@ cudaError_t launch_phase_b1(const PhaseArgs& A, cudaStream_t st) {
         dim3 grid((A.W + B1Tile<2>::TW - 1) / B1Tile<2>::TW, (A.H + B1Tile<2>::TH - 1) / B1Tile<2>::TH);
         if (A.kind == KIND_MEAN)
             phase_b1_kernel<KIND_MEAN, 2><<<grid, 128, 0, st>>>(A.S, A.R, A.f, A.H, A.W, sp,
-                                                                A.colour, A.use_paper, A.c_out);
+                                                                A.colour, A.use_paper, A.c_out, A.active);
         else
             phase_b1_kernel<KIND_GAUSS, 2><<<grid, 128, 0, st>>>(A.S, A.R, A.f, A.H, A.W, sp,
-                                                                 A.colour, A.use_paper, A.c_out);
+                                                                 A.colour, A.use_paper, A.c_out, A.active);
     } else {
         dim3 grid((A.W + B1Tile<4>::TW - 1) / B1Tile<4>::TW, (A.H + B1Tile<4>::TH - 1) / B1Tile<4>::TH);
         if (A.kind == KIND_MEAN)
             phase_b1_kernel<KIND_MEAN, 4><<<grid, 128, 0, st>>>(A.S, A.R, A.f, A.H, A.W, sp,
-                                                                A.colour, A.use_paper, A.c_out);
+                                                                A.colour, A.use_paper, A.c_out, A.active);
         else
             phase_b1_kernel<KIND_GAUSS, 4><<<grid, 128, 0, st>>>(A.S, A.R, A.f, A.H, A.W, sp,
-                                                                 A.colour, A.use_paper, A.c_out);
+                                                                 A.colour, A.use_paper, A.c_out, A.active);
     }
     return cudaGetLastError();
 }

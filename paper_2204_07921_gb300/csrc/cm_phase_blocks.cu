@@ -40,28 +40,30 @@ __device__ __forceinline__ void for_block_pixels(int first, int stride, int r0, 
 template <int KIND, int GT>
 __global__ void __launch_bounds__(128) phase_warp_kernel(
     const float* __restrict__ S, float* __restrict__ R, const float* __restrict__ f, int H, int W,
-    SearchParams sp, int lb, int ncol, int k, float* __restrict__ c_out) {
+    SearchParams sp, int lb, int ncol, int k, float* __restrict__ c_out,
+    const int* __restrict__ active) {
     static_assert(GT == 16 || GT == 32, "warp groups only");
+    if (active && *active == 0) return;
     constexpr int GPC = 128 / GT;
     const int b = 1 << lb;
     const int nbi = (H + b - 1) >> lb, nbj = (W + b - 1) >> lb;
     const int gid = threadIdx.x / GT, lane = threadIdx.x % GT;
     const int a = blockIdx.x * GPC + gid;
     int bi, bj;
-    const bool active = active_block(a, nbi, nbj, ncol, k, bi, bj);
-    // Inactive groups still take part in the shuffles of their warp.
-    const int r0 = active ? bi << lb : 0, c0 = active ? bj << lb : 0;
-    const int r1 = active ? min(r0 + b, H) : 0, c1 = active ? min(c0 + b, W) : 0;
+    const bool blk_on = active_block(a, nbi, nbj, ncol, k, bi, bj);
+    // Groups without a block still take part in the shuffles of their warp.
+    const int r0 = blk_on ? bi << lb : 0, c0 = blk_on ? bj << lb : 0;
+    const int r1 = blk_on ? min(r0 + b, H) : 0, c1 = blk_on ? min(c0 + b, W) : 0;
     const int bh = r1 - r0, bw = c1 - c0;
     float s1 = 0.0f;
-    if (active)
+    if (blk_on)
         for_block_pixels(lane, GT, r0, c0, bh, bw, lb, bw == b, W,
                          [&](size_t p) { s1 += S[p] - f[p]; });
 #pragma unroll
     for (int off = GT / 2; off > 0; off >>= 1) s1 += __shfl_xor_sync(0xffffffffu, s1, off, GT);
     float w[9];
     unsigned mask = 0;
-    const bool has = active && ring_slot(lane, r0, r1, c0, c1, H, W, S, R, lb, ncol, k, w, mask);
+    const bool has = blk_on && ring_slot(lane, r0, r1, c0, c1, H, W, S, R, lb, ncol, k, w, mask);
     AffPix px;
     if (has) {
         px = aff_pix(w, mask);
@@ -75,9 +77,9 @@ __global__ void __launch_bounds__(128) phase_warp_kernel(
         for (int off = GT / 2; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off, GT);
         return v;
     };
-    const float s = active ? (float)(bh * bw) : 1.0f;
-    const float cbest = block_search(ring, sp, s, active ? s1 : 0.0f, false, 0.0f);
-    if (!active) return;
+    const float s = blk_on ? (float)(bh * bw) : 1.0f;
+    const float cbest = block_search(ring, sp, s, blk_on ? s1 : 0.0f, false, 0.0f);
+    if (!blk_on) return;
     for_block_pixels(lane, GT, r0, c0, bh, bw, lb, bw == b, W,
                      [&](size_t p) { R[p] = S[p] + cbest; });
     if (c_out && lane == 0) c_out[(size_t)bi * nbj + bj] = cbest;
@@ -86,8 +88,10 @@ __global__ void __launch_bounds__(128) phase_warp_kernel(
 template <int KIND, int CT, int Q, int RPT>
 __global__ void __cluster_dims__(Q, 1, 1) __launch_bounds__(CT) phase_cluster_kernel(
     const float* __restrict__ S, float* __restrict__ R, const float* __restrict__ f, int H, int W,
-    SearchParams sp, int lb, int ncol, int k, float* __restrict__ c_out) {
+    SearchParams sp, int lb, int ncol, int k, float* __restrict__ c_out,
+    const int* __restrict__ active) {
     namespace cg = cooperative_groups;
+    if (active && *active == 0) return;   // uniform over the grid
     constexpr int GT = CT * Q;         // threads searching one block
     constexpr int NW = CT / 32;
     constexpr int MB = 9;              // candidates per batched reduction (the grid)
@@ -204,7 +208,9 @@ constexpr int COARSE_LB = 6;
 
 __global__ void __launch_bounds__(256) tile_sums_kernel(const float* __restrict__ S,
                                                         const float* __restrict__ f, int H, int W,
-                                                        float* __restrict__ partials) {
+                                                        float* __restrict__ partials,
+                                                        const int* __restrict__ active) {
+    if (active && *active == 0) return;
     __shared__ float red[8];
     const int r0 = blockIdx.y * TILE, c0 = blockIdx.x * TILE;
     float acc = 0.0f;
@@ -232,7 +238,8 @@ __global__ void __launch_bounds__(256) tile_sums_kernel(const float* __restrict_
 __global__ void __launch_bounds__(256) apply_kernel(const float* __restrict__ S,
                                                     float* __restrict__ R,
                                                     const float* __restrict__ cj, int H, int W,
-                                                    int lb, int nbj) {
+                                                    int lb, int nbj, const int* __restrict__ active) {
+    if (active && *active == 0) return;
     const size_t N = (size_t)H * W;
     for (size_t p = (size_t)blockIdx.x * 256 + threadIdx.x; p < N; p += (size_t)gridDim.x * 256) {
         const int r = (int)(p / W), c = (int)(p - (size_t)r * W);
@@ -243,8 +250,10 @@ __global__ void __launch_bounds__(256) apply_kernel(const float* __restrict__ S,
 template <int KIND, int CT, int Q, int RPT, int LA>
 __global__ void __cluster_dims__(Q, 1, 1) __launch_bounds__(CT) phase_coarse_kernel(
     const float* __restrict__ S, const float* __restrict__ partials, float* __restrict__ cj,
-    int H, int W, SearchParams sp, int lb, int ncol, int k, float* __restrict__ c_out) {
+    int H, int W, SearchParams sp, int lb, int ncol, int k, float* __restrict__ c_out,
+    const int* __restrict__ active) {
     namespace cg = cooperative_groups;
+    if (active && *active == 0) return;   // uniform over the grid
     constexpr int GT = CT * Q;
     constexpr int NW = CT / 32;
     constexpr int MB = 9;
@@ -381,7 +390,7 @@ static void launch_coarse(const PhaseArgs& A, const float* partials, float* cj, 
     SearchParams sp{A.alpha, A.G, A.K};
     constexpr int LA = Q > 1 ? 3 : 1;
     phase_coarse_kernel<KIND, CT, Q, RPT, LA><<<nact * Q, CT, 0, st>>>(
-        A.S, partials, cj, A.H, A.W, sp, A.lb, A.ncolors, A.colour, A.c_out);
+        A.S, partials, cj, A.H, A.W, sp, A.lb, A.ncolors, A.colour, A.c_out, A.active);
 }
 
 template <int KIND>
@@ -417,7 +426,7 @@ int coarse_level_log2() { return COARSE_LB; }
 cudaError_t launch_level_coarse(const PhaseArgs& A0, float* partials, float* cj,
                                 cudaStream_t st) {
     dim3 tg((A0.W + TILE - 1) / TILE, (A0.H + TILE - 1) / TILE);
-    tile_sums_kernel<<<tg, 256, 0, st>>>(A0.S, A0.f, A0.H, A0.W, partials);
+    tile_sums_kernel<<<tg, 256, 0, st>>>(A0.S, A0.f, A0.H, A0.W, partials, A0.active);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     for (int k = 0; k < A0.ncolors; ++k) {
@@ -431,7 +440,7 @@ cudaError_t launch_level_coarse(const PhaseArgs& A0, float* partials, float* cj,
     const int nbj = (A0.W + b - 1) / b;
     const size_t N = (size_t)A0.H * A0.W;
     const int grid = (int)std::min<size_t>((N + 255) / 256, 152 * 16);
-    apply_kernel<<<grid, 256, 0, st>>>(A0.S, A0.R, cj, A0.H, A0.W, A0.lb, nbj);
+    apply_kernel<<<grid, 256, 0, st>>>(A0.S, A0.R, cj, A0.H, A0.W, A0.lb, nbj, A0.active);
     return cudaGetLastError();
 }
 
@@ -440,14 +449,14 @@ static void launch_warp(const PhaseArgs& A, int nact, cudaStream_t st) {
     constexpr int GPC = 128 / GT;
     SearchParams sp{A.alpha, A.G, A.K};
     phase_warp_kernel<KIND, GT><<<(nact + GPC - 1) / GPC, 128, 0, st>>>(
-        A.S, A.R, A.f, A.H, A.W, sp, A.lb, A.ncolors, A.colour, A.c_out);
+        A.S, A.R, A.f, A.H, A.W, sp, A.lb, A.ncolors, A.colour, A.c_out, A.active);
 }
 
 template <int KIND, int CT, int Q, int RPT>
 static void launch_cluster(const PhaseArgs& A, int nact, cudaStream_t st) {
     SearchParams sp{A.alpha, A.G, A.K};
     phase_cluster_kernel<KIND, CT, Q, RPT><<<nact * Q, CT, 0, st>>>(
-        A.S, A.R, A.f, A.H, A.W, sp, A.lb, A.ncolors, A.colour, A.c_out);
+        A.S, A.R, A.f, A.H, A.W, sp, A.lb, A.ncolors, A.colour, A.c_out, A.active);
 }
 
 template <int KIND>
