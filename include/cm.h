@@ -174,6 +174,44 @@ int cm_solve_batched(cm_ctx* ctx, int n, const float* const* f, const int* H, co
                      const cm_options* opts /* host, nullable */,
                      cm_stats* stats /* host, n entries, nullable */, void* stream);
 
+/* ---------------------------------------------------------------------------
+ * Learned warm start (not in the paper): a small CNN maps f to an initial
+ * u0 for the sweep, which then runs from u0 and is both the fallback and the
+ * judge of the network's output.  Network: six 3x3 convolutions with zero
+ * padding, channels 1 -> 32 -> 32 -> 32 -> 32 -> 32 -> 1, ReLU after the first
+ * five, residual output u0 = f + conv6(...).  BF16 weights and activations,
+ * FP32 accumulation (the 32 -> 32 layers on the tensor cores).
+ * Parameters: one flat FP32 vector of cm_net_num_params() = 37601 values:
+ * W1 [9][32] (tap, out), b1 [32]; W2..W5 [9][32][32] (tap, in, out),
+ * b2..b5 [32]; W6 [9][32] (tap, in), b6 [1]; tap = (dy + 1) * 3 + (dx + 1). */
+typedef struct cm_net cm_net;
+
+int cm_net_num_params(void);
+/* Create a network on the current device with all parameters zero (then
+ * u0 = f).  ctx is only checked for validity. */
+int cm_net_create(cm_ctx* ctx, cm_net** net /* host */);
+void cm_net_destroy(cm_net* net);
+const char* cm_net_last_error(const cm_net* net);
+/* Host FP32 parameter vector in / out; setting resets the Adam moments. */
+int cm_net_set_params(cm_net* net, const float* params_host);
+int cm_net_get_params(cm_net* net, float* params_host);
+/* u0 = f + net(f): f, u0_out device, N images of H x W, row-major. */
+int cm_net_forward(cm_net* net, const float* f, int N, int H, int W, float* u0_out, void* stream);
+/* Gradient of the loss mean((u0 - u*)^2) over all N H W pixels (grad_host:
+ * 37601 floats, nullable; loss_host nullable).  Synchronises `stream`. */
+int cm_net_gradients(cm_net* net, const float* f, const float* ustar, int N, int H, int W,
+                     float* grad_host, double* loss_host, void* stream);
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected) on that
+ * loss for the batch (f, u*), device pointers.  loss_host (nullable) receives
+ * the loss before the step (synchronising `stream`). */
+int cm_net_train_step(cm_net* net, const float* f, const float* ustar, int N, int H, int W,
+                      float lr, double* loss_host, void* stream);
+/* u0_out = f + net(f) for N images; with check_energy, an image keeps u0
+ * only if F(u0) <= F(f) (energies of Eq. MCM/GCM with alpha and kind), else
+ * u0 = f.  used_host (nullable, N ints) receives 1 where u0 was kept. */
+int cm_warmstart(cm_ctx* ctx, cm_net* net, const float* f, int N, int H, int W, float* u0_out,
+                 int check_energy, float alpha, int kind, int* used_host, void* stream);
+
 /* Energy without allocation.  The paper has no counterpart: this is a
  * service for callers that cannot let a library allocate device memory -- a
  * host whose caching allocator already holds (nearly) all of it, code that

@@ -16,6 +16,7 @@
 
 #include "../../include/cm.h"
 #include "cm_batched.h"
+#include "cm_cnn.h"
 #include "cm_kernels.h"
 
 struct GraphKey {
@@ -443,6 +444,46 @@ int cm_solve(cm_ctx* ctx, const float* f, int H, int W, float alpha, int kind, i
     return CM_OK;
 }
 
+
+// ---------------------------------------------------------------------------
+// Learned warm start.
+
+int cm_warmstart(cm_ctx* ctx, cm_net* net, const float* f, int N, int H, int W, float* u0_out,
+                 int check_energy, float alpha, int kind, int* used_host, void* stream) {
+    if (!ctx) return CM_ERR_INVALID;
+    if (!net || !f || !u0_out || u0_out == f || N < 1 || H < 1 || W < 1 ||
+        (check_energy && (!finite_positive(alpha) || (kind != 0 && kind != 1))))
+        return fail(ctx, CM_ERR_INVALID, "cm_warmstart: invalid argument");
+    CM_CUDA(cudaSetDevice(ctx->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    cm::cnn::Net* nn = reinterpret_cast<cm::cnn::Net*>(net);
+    int rc = cm::cnn::net_forward(nn, f, N, H, W, u0_out, st);
+    if (rc) return fail(ctx, rc, std::string("cm_warmstart: ") + cm::cnn::net_error(nn));
+    const size_t npx = (size_t)H * W;
+    if (check_energy) {
+        rc = ensure_partials(ctx, H, W);
+        if (rc) return rc;
+        for (int n = 0; n < N; ++n) {
+            const float* fi = f + n * npx;
+            float* ui = u0_out + n * npx;
+            // the sweep's energy judges the network: keep u0 only if F(u0) <= F(f)
+            CM_CUDA(cm::launch_energy(ui, fi, H, W, alpha, kind, ctx->partials, ctx->ticket,
+                                      &ctx->E_dev[0], st));
+            CM_CUDA(cm::launch_energy(fi, fi, H, W, alpha, kind, ctx->partials, ctx->ticket,
+                                      &ctx->E_dev[1], st));
+            CM_CUDA(cudaMemcpyAsync(ctx->E_pinned, ctx->E_dev, 2 * sizeof(double),
+                                    cudaMemcpyDeviceToHost, st));
+            CM_CUDA(cudaStreamSynchronize(st));
+            const bool keep = isfinite(ctx->E_pinned[0]) && ctx->E_pinned[0] <= ctx->E_pinned[1];
+            if (!keep)
+                CM_CUDA(cudaMemcpyAsync(ui, fi, npx * sizeof(float), cudaMemcpyDeviceToDevice, st));
+            if (used_host) used_host[n] = keep ? 1 : 0;
+        }
+    } else if (used_host) {
+        for (int n = 0; n < N; ++n) used_host[n] = 1;
+    }
+    return CM_OK;
+}
 
 // ---------------------------------------------------------------------------
 // Batched solve.

@@ -1,0 +1,802 @@
+// cm_cnn.cu -- the learned warm start: a small CNN maps f to an initial u.
+//
+// Network: six 3x3 convolutions with zero padding, channels 1 -> 32 -> 32 ->
+// 32 -> 32 -> 32 -> 1, ReLU after the first five, residual output
+// u0 = f + conv6(...).  Activations are NHWC BF16 (64 bytes per pixel per
+// layer); weights are kept in FP32 (master copy, Adam) and used in BF16;
+// every product is accumulated in FP32.
+//
+//  conv_in_kernel     1 -> 32 on CUDA cores (9 MACs per output).
+//  conv_mid_kernel    32 -> 32 as an implicit GEMM on the tensor cores:
+//                     M = pixels (8 x 16 tile per CTA), N = 32, K = 9 x 32;
+//                     ldmatrix + mma.sync m16n8k16 BF16 -> FP32.  The same
+//                     kernel computes dX of the backward pass with the
+//                     flipped, transposed weights and the ReLU mask of the
+//                     layer's input fused in the epilogue.
+//  dw_mid_kernel      dW = sum_p X[p + tap]^T dZ[p] on the tensor cores, per
+//                     CTA partial sums over a grid-stride set of tiles,
+//                     reduced in a fixed order (deterministic).
+//  conv_out_kernel    32 -> 1 and the residual u0 = f + out (CUDA cores).
+//  out_grad_kernel    dL/dout of the MSE loss, dX of conv6, ReLU mask.
+//  dw_small kernels   dW of conv1 and conv6 (CUDA cores).
+//  adam_kernel        Adam (Kingma and Ba) on the FP32 master weights, then
+//                     the BF16 copies are repacked.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "../../include/cm.h"
+#include "cm_cnn.h"
+
+namespace cm {
+namespace cnn {
+
+using bf16 = __nv_bfloat16;
+
+constexpr int C = 32;
+constexpr int TH = 8, TW = 16;                 // output tile: 8 rows x 16 columns
+constexpr int HH = TH + 2, HW = TW + 2;        // with a one-pixel halo
+constexpr int CS = 40;                         // smem pixel stride (32 channels + 8 pad)
+constexpr int MIDW = 9 * C * C;                // weights of one 32 -> 32 layer
+constexpr int OFF_W1 = 0, OFF_B1 = 9 * C;
+__host__ __device__ constexpr int off_w(int l) { return 9 * C + C + (l - 2) * (MIDW + C); }
+__host__ __device__ constexpr int off_b(int l) { return off_w(l) + MIDW; }
+constexpr int OFF_W6 = 9 * C + C + 4 * (MIDW + C);
+constexpr int OFF_B6 = OFF_W6 + 9 * C;
+constexpr int NPAR = OFF_B6 + 1;
+static_assert(NPAR == 37601, "parameter count");
+constexpr int DW_STRIDE = MIDW + C;            // one CTA partial of a 32 -> 32 layer
+constexpr int DW_GRID = 2 * 152;               // CTAs of the weight-gradient kernels
+
+// ---------------------------------------------------------------------------
+// PTX helpers.
+
+__device__ __forceinline__ unsigned smem_addr(const void* p) {
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void ldsm_x4(unsigned (&r)[4], const void* p) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(smem_addr(p)));
+}
+
+__device__ __forceinline__ void ldsm_x4_t(unsigned (&r)[4], const void* p) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(smem_addr(p)));
+}
+
+// D += A (16x16, row) * B (16x8, col), BF16 in, FP32 accumulate.
+__device__ __forceinline__ void mma16816(float (&d)[4], const unsigned (&a)[4], unsigned b0,
+                                         unsigned b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+        "{%8,%9}, {%0,%1,%2,%3};\n"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ float bf(bf16 x) { return __bfloat162float(x); }
+__device__ __forceinline__ float round_bf(float x) { return __bfloat162float(__float2bfloat16(x)); }
+
+// Tile geometry shared by the tiled kernels: tile t of image n.
+struct Tile {
+    int n, y0, x0;
+};
+__device__ __forceinline__ Tile tile_of(int t, int H, int W) {
+    const int tx = (W + TW - 1) / TW, ty = (H + TH - 1) / TH;
+    Tile r;
+    r.n = t / (tx * ty);
+    const int rem = t - r.n * tx * ty;
+    r.y0 = (rem / tx) * TH;
+    r.x0 = (rem % tx) * TW;
+    return r;
+}
+
+// Stage the (TH+2) x (TW+2) x 32 BF16 halo tile of X (zero outside the image).
+__device__ __forceinline__ void load_halo(bf16 (*s)[CS], const bf16* __restrict__ X, const Tile& t,
+                                          int H, int W) {
+    const size_t img = (size_t)t.n * H * W;
+    for (int i = threadIdx.x; i < HH * HW * 4; i += blockDim.x) {
+        const int pix = i >> 2, q = i & 3;
+        const int gy = t.y0 - 1 + pix / HW, gx = t.x0 - 1 + pix % HW;
+        uint4 v = make_uint4(0u, 0u, 0u, 0u);
+        if (gy >= 0 && gy < H && gx >= 0 && gx < W)
+            v = reinterpret_cast<const uint4*>(X + (img + (size_t)gy * W + gx) * C)[q];
+        *reinterpret_cast<uint4*>(&s[pix][q * 8]) = v;
+    }
+}
+
+// Stage the TH x TW x 32 tile of X (zero outside the image).
+__device__ __forceinline__ void load_tile(bf16 (*s)[CS], const bf16* __restrict__ X, const Tile& t,
+                                          int H, int W) {
+    const size_t img = (size_t)t.n * H * W;
+    for (int i = threadIdx.x; i < TH * TW * 4; i += blockDim.x) {
+        const int pix = i >> 2, q = i & 3;
+        const int gy = t.y0 + pix / TW, gx = t.x0 + pix % TW;
+        uint4 v = make_uint4(0u, 0u, 0u, 0u);
+        if (gy < H && gx < W) v = reinterpret_cast<const uint4*>(X + (img + (size_t)gy * W + gx) * C)[q];
+        *reinterpret_cast<uint4*>(&s[pix][q * 8]) = v;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Forward kernels.
+
+__global__ void __launch_bounds__(256) conv_in_kernel(const float* __restrict__ f,
+                                                      const float* __restrict__ P,
+                                                      bf16* __restrict__ Y, int N, int H, int W) {
+    __shared__ float sw[9 * C + C];
+    for (int i = threadIdx.x; i < 9 * C + C; i += blockDim.x) sw[i] = round_bf(P[OFF_W1 + i]);
+    __syncthreads();
+    const size_t total = (size_t)N * H * W;
+    const size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= total) return;
+    const int x = (int)(p % W), y = (int)((p / W) % H);
+    const size_t img = p - ((size_t)y * W + x);
+    float v[9];
+#pragma unroll
+    for (int t = 0; t < 9; ++t) {
+        const int yy = y + t / 3 - 1, xx = x + t % 3 - 1;
+        v[t] = (yy >= 0 && yy < H && xx >= 0 && xx < W) ? f[img + (size_t)yy * W + xx] : 0.0f;
+    }
+    __align__(16) bf16 out[C];
+#pragma unroll
+    for (int o = 0; o < C; ++o) {
+        float a = sw[9 * C + o];
+#pragma unroll
+        for (int t = 0; t < 9; ++t) a = fmaf(v[t], sw[t * C + o], a);
+        out[o] = __float2bfloat16(fmaxf(a, 0.0f));
+    }
+    uint4* dst = reinterpret_cast<uint4*>(Y + p * C);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) dst[q] = reinterpret_cast<const uint4*>(out)[q];
+}
+
+// MODE 0: Y = ReLU(conv(X) + bias).  MODE 1: Y = conv(X) * [mask_src > 0]
+// (the backward dX of a 32 -> 32 layer, X = dZ, weights flipped and
+// transposed).  Wt: [9][32 out][32 in] BF16.
+template <int MODE>
+__global__ void __launch_bounds__(128) conv_mid_kernel(const bf16* __restrict__ X,
+                                                       const bf16* __restrict__ Wt,
+                                                       const float* __restrict__ bias,
+                                                       const bf16* __restrict__ mask_src,
+                                                       bf16* __restrict__ Y, int H, int W) {
+    __shared__ __align__(16) bf16 s_in[HH * HW][CS];
+    __shared__ __align__(16) bf16 s_w[9 * C][CS];
+    const Tile t = tile_of(blockIdx.x, H, W);
+    for (int i = threadIdx.x; i < 9 * C * 4; i += blockDim.x) {
+        const int row = i >> 2, q = i & 3;
+        *reinterpret_cast<uint4*>(&s_w[row][q * 8]) = reinterpret_cast<const uint4*>(Wt)[i];
+    }
+    load_halo(s_in, X, t, H, W);
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int lrow = lane & 7, lmat = lane >> 3;
+    float acc[2][4][4];
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) acc[a][b][c] = 0.0f;
+#pragma unroll 1
+    for (int tap = 0; tap < 9; ++tap) {
+        const int dy = tap / 3 - 1, dx = tap % 3 - 1;
+#pragma unroll
+        for (int kc = 0; kc < 2; ++kc) {
+            unsigned a[2][4];
+#pragma unroll
+            for (int mt = 0; mt < 2; ++mt) {
+                const int rr = 2 * warp + mt;
+                const int col = lrow + 8 * (lmat & 1);
+                const int pix = (rr + 1 + dy) * HW + (col + 1 + dx);
+                ldsm_x4(a[mt], &s_in[pix][8 * (lmat >> 1) + 16 * kc]);
+            }
+#pragma unroll
+            for (int pr = 0; pr < 2; ++pr) {
+                unsigned b[4];
+                const int o = 16 * pr + 8 * (lmat >> 1) + lrow;
+                ldsm_x4(b, &s_w[tap * C + o][16 * kc + 8 * (lmat & 1)]);
+#pragma unroll
+                for (int mt = 0; mt < 2; ++mt) {
+                    mma16816(acc[mt][2 * pr], a[mt], b[0], b[1]);
+                    mma16816(acc[mt][2 * pr + 1], a[mt], b[2], b[3]);
+                }
+            }
+        }
+    }
+    const int g = lane >> 2, q = lane & 3;
+    const size_t img = (size_t)t.n * H * W;
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt) {
+        const int gy = t.y0 + 2 * warp + mt;
+#pragma unroll
+        for (int nt = 0; nt < 4; ++nt) {
+            const int co = 8 * nt + 2 * q;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int gx = t.x0 + g + 8 * h;
+                if (gy >= H || gx >= W) continue;
+                const size_t pi = (img + (size_t)gy * W + gx) * C + co;
+                float v0 = acc[mt][nt][2 * h], v1 = acc[mt][nt][2 * h + 1];
+                if (MODE == 0) {
+                    v0 = fmaxf(v0 + bias[co], 0.0f);
+                    v1 = fmaxf(v1 + bias[co + 1], 0.0f);
+                } else {
+                    const __nv_bfloat162 m = *reinterpret_cast<const __nv_bfloat162*>(mask_src + pi);
+                    v0 = bf(m.x) > 0.0f ? v0 : 0.0f;
+                    v1 = bf(m.y) > 0.0f ? v1 : 0.0f;
+                }
+                *reinterpret_cast<__nv_bfloat162*>(Y + pi) = __floats2bfloat162_rn(v0, v1);
+            }
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256) conv_out_kernel(const bf16* __restrict__ X,
+                                                       const float* __restrict__ P,
+                                                       const float* __restrict__ f,
+                                                       float* __restrict__ u0, int N, int H,
+                                                       int W) {
+    __shared__ float sw[9 * C + 1];
+    for (int i = threadIdx.x; i < 9 * C + 1; i += blockDim.x) sw[i] = round_bf(P[OFF_W6 + i]);
+    __syncthreads();
+    const size_t total = (size_t)N * H * W;
+    const size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= total) return;
+    const int x = (int)(p % W), y = (int)((p / W) % H);
+    const size_t img = p - ((size_t)y * W + x);
+    float acc = sw[9 * C];
+#pragma unroll 1
+    for (int t = 0; t < 9; ++t) {
+        const int yy = y + t / 3 - 1, xx = x + t % 3 - 1;
+        if (yy < 0 || yy >= H || xx < 0 || xx >= W) continue;
+        const uint4* src = reinterpret_cast<const uint4*>(X + (img + (size_t)yy * W + xx) * C);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const uint4 v = src[q];
+            const bf16* e = reinterpret_cast<const bf16*>(&v);
+#pragma unroll
+            for (int j = 0; j < 8; ++j) acc = fmaf(bf(e[j]), sw[t * C + 8 * q + j], acc);
+        }
+    }
+    u0[p] = f[p] + acc;
+}
+
+// ---------------------------------------------------------------------------
+// Backward kernels.
+
+// dL/dout = 2 (u0 - u*) / P_total; dZ5 = (sum_tap W6[tap] dL/dout[p - tap]) *
+// [X5 > 0]; per-CTA FP64 partial of sum (u0 - u*)^2.
+__global__ void __launch_bounds__(256) out_grad_kernel(const float* __restrict__ u0,
+                                                       const float* __restrict__ us,
+                                                       const float* __restrict__ P,
+                                                       const bf16* __restrict__ X5,
+                                                       bf16* __restrict__ dZ,
+                                                       double* __restrict__ loss_part, int N,
+                                                       int H, int W, float scale) {
+    __shared__ float sw[9 * C];
+    __shared__ double red[8];
+    for (int i = threadIdx.x; i < 9 * C; i += blockDim.x) sw[i] = round_bf(P[OFF_W6 + i]);
+    __syncthreads();
+    const size_t total = (size_t)N * H * W;
+    const size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    double sq = 0.0;
+    if (p < total) {
+        const int x = (int)(p % W), y = (int)((p / W) % H);
+        const size_t img = p - ((size_t)y * W + x);
+        const float e = u0[p] - us[p];
+        sq = (double)e * (double)e;
+        float d[9];
+#pragma unroll
+        for (int t = 0; t < 9; ++t) {
+            const int yy = y - (t / 3 - 1), xx = x - (t % 3 - 1);
+            d[t] = 0.0f;
+            if (yy >= 0 && yy < H && xx >= 0 && xx < W) {
+                const size_t q = img + (size_t)yy * W + xx;
+                d[t] = scale * (u0[q] - us[q]);
+            }
+        }
+        const uint4* xs = reinterpret_cast<const uint4*>(X5 + p * C);
+        __align__(16) bf16 out[C];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const uint4 v = xs[q];
+            const bf16* e8 = reinterpret_cast<const bf16*>(&v);
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const int c = 8 * q + j;
+                float a = 0.0f;
+#pragma unroll
+                for (int t = 0; t < 9; ++t) a = fmaf(sw[t * C + c], d[t], a);
+                out[c] = __float2bfloat16(bf(e8[j]) > 0.0f ? a : 0.0f);
+            }
+        }
+        uint4* dst = reinterpret_cast<uint4*>(dZ + p * C);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) dst[q] = reinterpret_cast<const uint4*>(out)[q];
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, off);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = sq;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int i = 0; i < 8; ++i) s += red[i];
+        loss_part[blockIdx.x] = s;
+    }
+}
+
+// dW of a 32 -> 32 layer: dW[tap][ci][co] = sum_p X[p + tap][ci] dZ[p][co],
+// db[co] = sum_p dZ[p][co].  Warp w owns taps w, w + 4, w + 8.  Partials of
+// CTA b go to part + b * DW_STRIDE ([tap][ci][co] then db).
+__global__ void __launch_bounds__(128) dw_mid_kernel(const bf16* __restrict__ X,
+                                                     const bf16* __restrict__ dZ,
+                                                     float* __restrict__ part, int N, int H,
+                                                     int W) {
+    __shared__ __align__(16) bf16 s_x[HH * HW][CS];
+    __shared__ __align__(16) bf16 s_dz[TH * TW][CS];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int lrow = lane & 7, lmat = lane >> 3;
+    float acc[3][2][4][4];
+#pragma unroll
+    for (int s = 0; s < 3; ++s)
+#pragma unroll
+        for (int a = 0; a < 2; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b)
+#pragma unroll
+                for (int c = 0; c < 4; ++c) acc[s][a][b][c] = 0.0f;
+    float dbacc = 0.0f;
+    const int ntiles = N * ((H + TH - 1) / TH) * ((W + TW - 1) / TW);
+    for (int ti = blockIdx.x; ti < ntiles; ti += gridDim.x) {
+        const Tile t = tile_of(ti, H, W);
+        __syncthreads();   // the previous tile's readers are done
+        load_halo(s_x, X, t, H, W);
+        load_tile(s_dz, dZ, t, H, W);
+        __syncthreads();
+        if (threadIdx.x < C)
+            for (int p = 0; p < TH * TW; ++p) dbacc += bf(s_dz[p][threadIdx.x]);
+#pragma unroll
+        for (int s = 0; s < 3; ++s) {
+            const int tap = warp + 4 * s;
+            if (tap >= 9) continue;
+            const int dy = tap / 3 - 1, dx = tap % 3 - 1;
+#pragma unroll 1
+            for (int ry = 0; ry < TH; ++ry) {
+                unsigned a[2][4];
+#pragma unroll
+                for (int mt = 0; mt < 2; ++mt) {
+                    const int px = lrow + 8 * (lmat >> 1);
+                    ldsm_x4_t(a[mt], &s_x[(ry + 1 + dy) * HW + (px + 1 + dx)][16 * mt + 8 * (lmat & 1)]);
+                }
+#pragma unroll
+                for (int pr = 0; pr < 2; ++pr) {
+                    unsigned b[4];
+                    const int px = lrow + 8 * (lmat & 1);
+                    ldsm_x4_t(b, &s_dz[ry * TW + px][16 * pr + 8 * (lmat >> 1)]);
+#pragma unroll
+                    for (int mt = 0; mt < 2; ++mt) {
+                        mma16816(acc[s][mt][2 * pr], a[mt], b[0], b[1]);
+                        mma16816(acc[s][mt][2 * pr + 1], a[mt], b[2], b[3]);
+                    }
+                }
+            }
+        }
+    }
+    float* out = part + (size_t)blockIdx.x * DW_STRIDE;
+    const int g = lane >> 2, q = lane & 3;
+#pragma unroll
+    for (int s = 0; s < 3; ++s) {
+        const int tap = warp + 4 * s;
+        if (tap >= 9) continue;
+#pragma unroll
+        for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+            for (int nt = 0; nt < 4; ++nt) {
+                const int ci = 16 * mt + g, co = 8 * nt + 2 * q;
+                float* o = out + tap * C * C;
+                o[ci * C + co] = acc[s][mt][nt][0];
+                o[ci * C + co + 1] = acc[s][mt][nt][1];
+                o[(ci + 8) * C + co] = acc[s][mt][nt][2];
+                o[(ci + 8) * C + co + 1] = acc[s][mt][nt][3];
+            }
+    }
+    if (threadIdx.x < C) out[MIDW + threadIdx.x] = dbacc;
+}
+
+// dW of conv6: dW6[tap][ci] = sum_p X5[p + tap][ci] d[p], db6 = sum_p d[p],
+// d = 2 (u0 - u*) / P_total.  Thread (tap, ci).  Partial stride 9 C + 1.
+__global__ void __launch_bounds__(288) dw_out_kernel(const bf16* __restrict__ X5,
+                                                     const float* __restrict__ u0,
+                                                     const float* __restrict__ us,
+                                                     float* __restrict__ part, int N, int H,
+                                                     int W, float scale) {
+    __shared__ __align__(16) bf16 s_x[HH * HW][CS];
+    __shared__ float s_d[TH * TW];
+    const int tap = threadIdx.x / C, ci = threadIdx.x % C;
+    const int dy = tap / 3 - 1, dx = tap % 3 - 1;
+    float acc = 0.0f, dacc = 0.0f;
+    const int ntiles = N * ((H + TH - 1) / TH) * ((W + TW - 1) / TW);
+    for (int ti = blockIdx.x; ti < ntiles; ti += gridDim.x) {
+        const Tile t = tile_of(ti, H, W);
+        __syncthreads();
+        load_halo(s_x, X5, t, H, W);
+        const size_t img = (size_t)t.n * H * W;
+        for (int i = threadIdx.x; i < TH * TW; i += blockDim.x) {
+            const int gy = t.y0 + i / TW, gx = t.x0 + i % TW;
+            float v = 0.0f;
+            if (gy < H && gx < W) {
+                const size_t p = img + (size_t)gy * W + gx;
+                v = scale * (u0[p] - us[p]);
+            }
+            s_d[i] = v;
+        }
+        __syncthreads();
+        for (int p = 0; p < TH * TW; ++p) {
+            const int py = p / TW, px = p % TW;
+            acc = fmaf(bf(s_x[(py + 1 + dy) * HW + (px + 1 + dx)][ci]), s_d[p], acc);
+        }
+        if (threadIdx.x == 0)
+            for (int p = 0; p < TH * TW; ++p) dacc += s_d[p];
+    }
+    float* out = part + (size_t)blockIdx.x * (9 * C + 1);
+    out[tap * C + ci] = acc;
+    if (threadIdx.x == 0) out[9 * C] = dacc;
+}
+
+// dW of conv1: dW1[tap][co] = sum_p f[p + tap] dZ1[p][co], db1 = sum_p dZ1.
+// Thread (tap, co).  Partial stride 9 C + C.
+__global__ void __launch_bounds__(288) dw_in_kernel(const float* __restrict__ f,
+                                                    const bf16* __restrict__ dZ,
+                                                    float* __restrict__ part, int N, int H,
+                                                    int W) {
+    __shared__ float s_f[HH * HW];
+    __shared__ __align__(16) bf16 s_dz[TH * TW][CS];
+    const int tap = threadIdx.x / C, co = threadIdx.x % C;
+    const int dy = tap / 3 - 1, dx = tap % 3 - 1;
+    float acc = 0.0f, bacc = 0.0f;
+    const int ntiles = N * ((H + TH - 1) / TH) * ((W + TW - 1) / TW);
+    for (int ti = blockIdx.x; ti < ntiles; ti += gridDim.x) {
+        const Tile t = tile_of(ti, H, W);
+        __syncthreads();
+        const size_t img = (size_t)t.n * H * W;
+        for (int i = threadIdx.x; i < HH * HW; i += blockDim.x) {
+            const int gy = t.y0 - 1 + i / HW, gx = t.x0 - 1 + i % HW;
+            s_f[i] = (gy >= 0 && gy < H && gx >= 0 && gx < W) ? f[img + (size_t)gy * W + gx] : 0.0f;
+        }
+        load_tile(s_dz, dZ, t, H, W);
+        __syncthreads();
+        for (int p = 0; p < TH * TW; ++p) {
+            const int py = p / TW, px = p % TW;
+            const float g = bf(s_dz[p][co]);
+            acc = fmaf(s_f[(py + 1 + dy) * HW + (px + 1 + dx)], g, acc);
+            if (tap == 0) bacc += g;
+        }
+    }
+    float* out = part + (size_t)blockIdx.x * (9 * C + C);
+    out[tap * C + co] = acc;
+    if (tap == 0) out[9 * C + co] = bacc;
+}
+
+// out[i] = sum_{b < nb} part[b * stride + i], fixed order.
+__global__ void reduce_parts_kernel(const float* __restrict__ part, int nb, int stride, int count,
+                                    float* __restrict__ out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    float s = 0.0f;
+    for (int b = 0; b < nb; ++b) s += part[(size_t)b * stride + i];
+    out[i] = s;
+}
+
+__global__ void reduce_loss_kernel(const double* __restrict__ part, int nb, double* __restrict__ out) {
+    __shared__ double red[256];
+    double s = 0.0;
+    for (int i = threadIdx.x; i < nb; i += 256) s += part[i];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = red[0];
+}
+
+__global__ void adam_kernel(float* __restrict__ P, const float* __restrict__ G, float* __restrict__ m,
+                            float* __restrict__ v, int n, float lr, float b1, float b2, float eps,
+                            float c1, float c2) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float g = G[i];
+    const float mi = b1 * m[i] + (1.0f - b1) * g;
+    const float vi = b2 * v[i] + (1.0f - b2) * g * g;
+    m[i] = mi;
+    v[i] = vi;
+    P[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+}
+
+// BF16 copies of the 32 -> 32 weights: forward [tap][co][ci] (transpose of
+// the master [tap][ci][co]) and backward [tap][ci][co] with the tap flipped
+// (dX = conv(dZ, W'), W'[tap][ci][co] = W[8 - tap][ci][co]).
+__global__ void pack_kernel(const float* __restrict__ P, bf16* __restrict__ wf,
+                            bf16* __restrict__ wb) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= 4 * MIDW) return;
+    const int l = i / MIDW, r = i % MIDW;
+    const int tap = r / (C * C), ci = (r / C) % C, co = r % C;
+    const float w = P[off_w(l + 2) + r];
+    wf[l * MIDW + tap * C * C + co * C + ci] = __float2bfloat16(w);
+    wb[l * MIDW + (8 - tap) * C * C + ci * C + co] = __float2bfloat16(w);
+}
+
+// ---------------------------------------------------------------------------
+// Host side.
+
+struct Net {
+    int device = 0;
+    std::string err;
+    float *P = nullptr, *G = nullptr, *M = nullptr, *V = nullptr;
+    bf16 *wf = nullptr, *wb = nullptr;
+    int step = 0;
+    // activations (capacity in pixels)
+    size_t cap = 0;
+    bf16* act[6] = {};      // act[1..5] = X1..X5
+    bf16* dz[2] = {};
+    float* u0 = nullptr;
+    float* part = nullptr;  // weight-gradient partials
+    double* lpart = nullptr;
+    size_t lpart_cap = 0;
+    double* loss = nullptr;
+};
+
+namespace {
+
+#define NET_CUDA(call)                                              \
+    do {                                                            \
+        cudaError_t e_ = (call);                                    \
+        if (e_ != cudaSuccess) {                                    \
+            net->err = std::string(#call) + ": " + cudaGetErrorString(e_); \
+            return e_ == cudaErrorMemoryAllocation ? CM_ERR_OOM : CM_ERR_CUDA; \
+        }                                                           \
+    } while (0)
+
+int ensure_acts(Net* net, size_t npx) {
+    if (npx <= net->cap) return CM_OK;
+    for (int i = 1; i <= 5; ++i)
+        if (net->act[i]) cudaFree(net->act[i]);
+    for (int i = 0; i < 2; ++i)
+        if (net->dz[i]) cudaFree(net->dz[i]);
+    if (net->u0) cudaFree(net->u0);
+    if (net->lpart) cudaFree(net->lpart);
+    net->cap = 0;
+    for (int i = 1; i <= 5; ++i) NET_CUDA(cudaMalloc(&net->act[i], npx * C * sizeof(bf16)));
+    for (int i = 0; i < 2; ++i) NET_CUDA(cudaMalloc(&net->dz[i], npx * C * sizeof(bf16)));
+    NET_CUDA(cudaMalloc(&net->u0, npx * sizeof(float)));
+    NET_CUDA(cudaMalloc(&net->lpart, ((npx + 255) / 256) * sizeof(double)));
+    net->cap = npx;
+    return CM_OK;
+}
+
+int pack(Net* net, cudaStream_t st) {
+    pack_kernel<<<(4 * MIDW + 255) / 256, 256, 0, st>>>(net->P, net->wf, net->wb);
+    NET_CUDA(cudaGetLastError());
+    return CM_OK;
+}
+
+int forward(Net* net, const float* f, int N, int H, int W, float* u0, cudaStream_t st) {
+    const size_t npx = (size_t)N * H * W;
+    const int ntiles = N * ((H + TH - 1) / TH) * ((W + TW - 1) / TW);
+    conv_in_kernel<<<(unsigned)((npx + 255) / 256), 256, 0, st>>>(f, net->P, net->act[1], N, H, W);
+    for (int l = 2; l <= 5; ++l)
+        conv_mid_kernel<0><<<ntiles, 128, 0, st>>>(net->act[l - 1], net->wf + (l - 2) * MIDW,
+                                                   net->P + off_b(l), nullptr, net->act[l], H, W);
+    conv_out_kernel<<<(unsigned)((npx + 255) / 256), 256, 0, st>>>(net->act[5], net->P, f, u0, N, H, W);
+    NET_CUDA(cudaGetLastError());
+    return CM_OK;
+}
+
+// Gradients of the mean squared error into net->G; loss sum into net->loss.
+int backward(Net* net, const float* f, const float* us, int N, int H, int W, cudaStream_t st) {
+    const size_t npx = (size_t)N * H * W;
+    const int ntiles = N * ((H + TH - 1) / TH) * ((W + TW - 1) / TW);
+    const int nb = (int)((npx + 255) / 256);
+    const float scale = 2.0f / (float)npx;
+    out_grad_kernel<<<nb, 256, 0, st>>>(net->u0, us, net->P, net->act[5], net->dz[0], net->lpart,
+                                        N, H, W, scale);
+    reduce_loss_kernel<<<1, 256, 0, st>>>(net->lpart, nb, net->loss);
+    const int g6 = std::min(ntiles, DW_GRID);
+    dw_out_kernel<<<g6, 288, 0, st>>>(net->act[5], net->u0, us, net->part, N, H, W, scale);
+    reduce_parts_kernel<<<(9 * C + 1 + 255) / 256, 256, 0, st>>>(net->part, g6, 9 * C + 1, 9 * C + 1,
+                                                                 net->G + OFF_W6);
+    int cur = 0;   // dz[cur] holds dZ of layer l's output
+    for (int l = 5; l >= 2; --l) {
+        const int gm = std::min(ntiles, DW_GRID);
+        dw_mid_kernel<<<gm, 128, 0, st>>>(net->act[l - 1], net->dz[cur], net->part, N, H, W);
+        reduce_parts_kernel<<<(DW_STRIDE + 255) / 256, 256, 0, st>>>(net->part, gm, DW_STRIDE,
+                                                                     DW_STRIDE, net->G + off_w(l));
+        conv_mid_kernel<1><<<ntiles, 128, 0, st>>>(net->dz[cur], net->wb + (l - 2) * MIDW, nullptr,
+                                                   net->act[l - 1], net->dz[cur ^ 1], H, W);
+        cur ^= 1;
+    }
+    const int g1 = std::min(ntiles, DW_GRID);
+    dw_in_kernel<<<g1, 288, 0, st>>>(f, net->dz[cur], net->part, N, H, W);
+    reduce_parts_kernel<<<(9 * C + C + 255) / 256, 256, 0, st>>>(net->part, g1, 9 * C + C, 9 * C + C,
+                                                                 net->G + OFF_W1);
+    NET_CUDA(cudaGetLastError());
+    return CM_OK;
+}
+
+int check_images(Net* net, const float* f, int N, int H, int W) {
+    if (!f || N < 1 || H < 1 || W < 1) {
+        net->err = "invalid image arguments";
+        return CM_ERR_INVALID;
+    }
+    return CM_OK;
+}
+
+}  // namespace
+
+// Exposed to the runtime (cm_warmstart).
+int net_forward(Net* net, const float* f, int N, int H, int W, float* u0, cudaStream_t st) {
+    int rc = check_images(net, f, N, H, W);
+    if (rc || !u0) return rc ? rc : CM_ERR_INVALID;
+    NET_CUDA(cudaSetDevice(net->device));
+    rc = ensure_acts(net, (size_t)N * H * W);
+    if (rc) return rc;
+    return forward(net, f, N, H, W, u0, st);
+}
+
+// Forward into the net's own u0 buffer (the training paths).
+int net_forward_own(Net* net, const float* f, int N, int H, int W, cudaStream_t st) {
+    int rc = check_images(net, f, N, H, W);
+    if (rc) return rc;
+    NET_CUDA(cudaSetDevice(net->device));
+    rc = ensure_acts(net, (size_t)N * H * W);
+    if (rc) return rc;
+    return forward(net, f, N, H, W, net->u0, st);
+}
+
+const char* net_error(const Net* net) { return net->err.c_str(); }
+
+}  // namespace cnn
+}  // namespace cm
+
+using cm::cnn::Net;
+
+struct cm_net : public Net {};
+
+extern "C" {
+
+int cm_net_num_params(void) { return cm::cnn::NPAR; }
+
+int cm_net_create(cm_ctx* ctx, cm_net** out) {
+    if (!ctx || !out) return CM_ERR_INVALID;
+    *out = nullptr;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return CM_ERR_CUDA;
+    cm_net* net = new cm_net();
+    net->device = dev;
+    const size_t np = cm::cnn::NPAR * sizeof(float);
+    cudaError_t e = cudaMalloc(&net->P, np);
+    if (e == cudaSuccess) e = cudaMalloc(&net->G, np);
+    if (e == cudaSuccess) e = cudaMalloc(&net->M, np);
+    if (e == cudaSuccess) e = cudaMalloc(&net->V, np);
+    if (e == cudaSuccess) e = cudaMalloc(&net->wf, 4 * cm::cnn::MIDW * sizeof(cm::cnn::bf16));
+    if (e == cudaSuccess) e = cudaMalloc(&net->wb, 4 * cm::cnn::MIDW * sizeof(cm::cnn::bf16));
+    if (e == cudaSuccess)
+        e = cudaMalloc(&net->part, (size_t)cm::cnn::DW_GRID * cm::cnn::DW_STRIDE * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&net->loss, sizeof(double));
+    if (e == cudaSuccess) e = cudaMemset(net->P, 0, np);
+    if (e == cudaSuccess) e = cudaMemset(net->M, 0, np);
+    if (e == cudaSuccess) e = cudaMemset(net->V, 0, np);
+    if (e == cudaSuccess) e = cudaMemset(net->G, 0, np);
+    if (e != cudaSuccess) {
+        cm_net_destroy(net);
+        return e == cudaErrorMemoryAllocation ? CM_ERR_OOM : CM_ERR_CUDA;
+    }
+    if (cm::cnn::pack(net, 0) != CM_OK || cudaDeviceSynchronize() != cudaSuccess) {
+        cm_net_destroy(net);
+        return CM_ERR_CUDA;
+    }
+    *out = net;
+    return CM_OK;
+}
+
+void cm_net_destroy(cm_net* net) {
+    if (!net) return;
+    cudaSetDevice(net->device);
+    for (float* p : {net->P, net->G, net->M, net->V, net->u0, net->part})
+        if (p) cudaFree(p);
+    if (net->wf) cudaFree(net->wf);
+    if (net->wb) cudaFree(net->wb);
+    for (int i = 1; i <= 5; ++i)
+        if (net->act[i]) cudaFree(net->act[i]);
+    for (int i = 0; i < 2; ++i)
+        if (net->dz[i]) cudaFree(net->dz[i]);
+    if (net->lpart) cudaFree(net->lpart);
+    if (net->loss) cudaFree(net->loss);
+    delete net;
+}
+
+const char* cm_net_last_error(const cm_net* net) { return net ? net->err.c_str() : "null net"; }
+
+int cm_net_set_params(cm_net* net, const float* host) {
+    if (!net || !host) return CM_ERR_INVALID;
+    NET_CUDA(cudaSetDevice(net->device));
+    const size_t np = cm::cnn::NPAR * sizeof(float);
+    NET_CUDA(cudaMemcpy(net->P, host, np, cudaMemcpyHostToDevice));
+    NET_CUDA(cudaMemset(net->M, 0, np));
+    NET_CUDA(cudaMemset(net->V, 0, np));
+    net->step = 0;
+    int rc = cm::cnn::pack(net, 0);
+    if (rc) return rc;
+    NET_CUDA(cudaDeviceSynchronize());
+    return CM_OK;
+}
+
+int cm_net_get_params(cm_net* net, float* host) {
+    if (!net || !host) return CM_ERR_INVALID;
+    NET_CUDA(cudaSetDevice(net->device));
+    NET_CUDA(cudaMemcpy(host, net->P, cm::cnn::NPAR * sizeof(float), cudaMemcpyDeviceToHost));
+    return CM_OK;
+}
+
+int cm_net_forward(cm_net* net, const float* f, int N, int H, int W, float* u0_out, void* stream) {
+    if (!net) return CM_ERR_INVALID;
+    return cm::cnn::net_forward(net, f, N, H, W, u0_out, (cudaStream_t)stream);
+}
+
+int cm_net_gradients(cm_net* net, const float* f, const float* ustar, int N, int H, int W,
+                     float* grad_host, double* loss_host, void* stream) {
+    if (!net || !ustar) return CM_ERR_INVALID;
+    cudaStream_t st = (cudaStream_t)stream;
+    int rc = cm::cnn::net_forward_own(net, f, N, H, W, st);
+    if (rc) return rc;
+    rc = cm::cnn::backward(net, f, ustar, N, H, W, st);
+    if (rc) return rc;
+    NET_CUDA(cudaStreamSynchronize(st));
+    if (grad_host)
+        NET_CUDA(cudaMemcpy(grad_host, net->G, cm::cnn::NPAR * sizeof(float), cudaMemcpyDeviceToHost));
+    if (loss_host) {
+        double s = 0.0;
+        NET_CUDA(cudaMemcpy(&s, net->loss, sizeof(double), cudaMemcpyDeviceToHost));
+        *loss_host = s / ((double)N * H * W);
+    }
+    return CM_OK;
+}
+
+int cm_net_train_step(cm_net* net, const float* f, const float* ustar, int N, int H, int W,
+                      float lr, double* loss_host, void* stream) {
+    if (!net || !ustar || !(lr > 0.0f)) return CM_ERR_INVALID;
+    cudaStream_t st = (cudaStream_t)stream;
+    int rc = cm::cnn::net_forward_own(net, f, N, H, W, st);
+    if (rc) return rc;
+    rc = cm::cnn::backward(net, f, ustar, N, H, W, st);
+    if (rc) return rc;
+    net->step += 1;
+    const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+    const float c1 = 1.0f - powf(b1, (float)net->step), c2 = 1.0f - powf(b2, (float)net->step);
+    cm::cnn::adam_kernel<<<(cm::cnn::NPAR + 255) / 256, 256, 0, st>>>(net->P, net->G, net->M, net->V,
+                                                                      cm::cnn::NPAR, lr, b1, b2, eps,
+                                                                      c1, c2);
+    NET_CUDA(cudaGetLastError());
+    rc = cm::cnn::pack(net, st);
+    if (rc) return rc;
+    if (loss_host) {
+        double s = 0.0;
+        NET_CUDA(cudaMemcpyAsync(&s, net->loss, sizeof(double), cudaMemcpyDeviceToHost, st));
+        NET_CUDA(cudaStreamSynchronize(st));
+        *loss_host = s / ((double)N * H * W);
+    }
+    return CM_OK;
+}
+
+}  // extern "C"
