@@ -1,10 +1,13 @@
 """Benchmark: seconds to relative-energy tolerance 1e-4 on a 1024x1024 image.
 
-One step = one full solve of the hot path (Alg. 3 half V-cycles of the
+One step = the learned warm start (CNN inference and its energy check) and
+one full solve of the hot path from its output (Alg. 3 half V-cycles of the
 coloured block sweep, every level and colour, with the FP64 energy and
 stopping test after each cycle) on the seeded 1024^2 mean-curvature image
 (20 shapes, sigma 0.08, alpha 20, levels 1..512), inputs already resident
-in HBM.  Prints one JSON line (see --help).
+in HBM.  The plain sweep from f is timed the same way and reported next to
+it, with the 16-image warm-start evaluation and the 64-image batched solve.
+Prints one JSON line (see --help).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 """
@@ -31,7 +34,9 @@ TOL = 1e-4
 NCOLORS = 4
 COARSE_LB = 6          # levels with block side >= 64 run the coarse path
 MAX_CYCLES = 2000
-METRIC = "s to rel-energy tol 1e-4 at 1024^2 (plain FP32 sweep, FP64 stopping test)"
+METRIC = ("s to rel-energy tol 1e-4 at 1024^2 (learned warm start + FP32 sweep with FP64 "
+          "stopping test; plain sweep reported alongside)")
+WARMSTART_PARAMS = os.path.join(ROOT, "paper_2204_07921_gb300", "data", "warmstart_mean_a20.npz")
 L2_FLUSH_BYTES = 512 << 20   # > 129 MB L2
 
 
@@ -45,6 +50,8 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-cycles", type=int, default=1,
                    help="oracle cycles timed for the CPU baseline sample")
+    p.add_argument("--no-warmstart-eval", action="store_true",
+                   help="skip the 16-image warm-start evaluation")
     p.add_argument("--no-batched", action="store_true",
                    help="skip the 64-image batched measurement")
     p.add_argument("--phases-only", action="store_true",
@@ -131,13 +138,22 @@ def oracle_cycle_seconds(f64, n_cycles: int):
 
 
 def run_reference(args):
+    """The reference arm of this build is the FP64 oracle, run as it stands
+    on the host cores: one full solve to tol 1e-4 (its own cycle count and
+    time), then warm-up and timed single-cycle samples; value = mean cycle
+    time x the oracle's cycle count."""
     rank, world, _ = dist_setup(args)
     if rank != 0:
         return
     import numpy as np
+    import oracle
     import synth
     img = synth.large(args.side)
     f64 = img.f.astype(np.float64)
+    t0 = time.perf_counter()
+    _, trace, cycles, conv = oracle.solve(f64, ALPHA, KIND, cycles=MAX_CYCLES, tol=TOL,
+                                          ncolors=NCOLORS)
+    full_s = time.perf_counter() - t0
     times = []
     threads = 1
     for i in range(args.warmup + args.steps):
@@ -145,15 +161,16 @@ def run_reference(args):
         if i >= args.warmup:
             times.append(per_cycle)
     per_cycle = statistics.mean(times)
-    cycles = REFERENCE_CYCLES.get(args.side)
-    value = per_cycle * cycles if cycles else None
-    sample = (f"1 oracle cycle (all levels + FP64 energy) on the {args.side}^2 image per step, "
-              f"x {cycles} cycles to tol (the method's cycle count on this image)")
+    value = per_cycle * cycles
+    sample = (f"oracle: one full solve to tol ({cycles} cycles, {full_s:.1f} s), then "
+              f"{args.steps} timed single-cycle samples of the {args.side}^2 image x {cycles}")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": per_cycle * 1e3, "higher_is_better": False, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": workload_config(args.side),
+            "config": workload_config(args.side), "oracle_cycles": cycles,
+            "oracle_converged": bool(conv), "oracle_full_solve_s": full_s,
+            "oracle_final_energy": float(trace[-1]),
             "cpu_baseline": {"value": value, "unit": "s", "cores": threads, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": "s", "h2d_bytes_per_step": 0,
@@ -161,14 +178,10 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-# Cycles to rel. energy change <= 1e-4 of the method on the seeded images
-# (identical for the oracle and the CUDA path up to rounding ties).
-REFERENCE_CYCLES = {}
-
-
 def workload_config(side):
     return {"workload": f"denoise {side}x{side} mean curvature, 20 shapes, sigma 0.08, "
-                        f"alpha 20, blocks 1..{side // 2}, 4 colours, tol 1e-4",
+                        f"alpha 20, blocks 1..{side // 2}, 4 colours, tol 1e-4; learned warm "
+                        f"start (6 conv3x3, 32 ch, BF16) then the sweep",
             "image": f"{side}x{side}", "kind": "mean", "alpha": ALPHA, "tol": TOL,
             "levels": None, "ncolors": 4, "grid_points": 9, "golden_evals": 16,
             "l2": "flushed between steps (512 MB write)"}
@@ -257,13 +270,25 @@ def main():
         print(json.dumps({"phases_only": True, "levels": L, "ncolors": opts.ncolors}))
         return
 
-    def step(out):
-        _, st = cm.cm_solve(f, ALPHA, KIND, levels=0, cycles=MAX_CYCLES, tol=TOL, u_out=out,
+    from paper_2204_07921_gb300 import warmstart as ws
+    net = ws.Net.load(WARMSTART_PARAMS, ctx=ctx)
+    U0 = torch.empty_like(f)
+
+    def plain_step(fin, out):
+        _, st = cm.cm_solve(fin, ALPHA, KIND, levels=0, cycles=MAX_CYCLES, tol=TOL, u_out=out,
                             options=opts, ctx=ctx)
         return st
 
+    def warm_step(fin, out):
+        # learned warm start (inference + the energy check) then the sweep from u0
+        ws.warmstart(net, fin, ALPHA, KIND, check_energy=True, out=U0)
+        _, st = cm.cm_solve(fin, ALPHA, KIND, levels=0, cycles=MAX_CYCLES, tol=TOL, u0=U0,
+                            u_out=out, options=opts, ctx=ctx)
+        return st
+
     for _ in range(args.warmup):
-        st = step(u)
+        warm_step(f, u)
+        plain_step(f, u)
     torch.cuda.synchronize()
 
     def barrier():
@@ -271,30 +296,37 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
 
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-          for _ in range(args.steps)]
-    cycles = []
-    with ClockSampler(local) as clk:
+    def timed_steps(fn):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)]
+        sts = []
         barrier()
         for i in range(args.steps):
-            flush.fill_(float(i))
+            flush.fill_(float(i))       # L2 flush outside the timed events
             ev[i][0].record(stream)
-            st = step(u)
+            sts.append(fn(f, u))
             ev[i][1].record(stream)
-            cycles.append(st.cycles_run)
         barrier()
-    clocks = clk.summary()
-    step_ms = [a.elapsed_time(b) for a, b in ev]
-    t_dev = sum(step_ms) / 1e3
-    if world > 1:
-        t = torch.tensor([t_dev], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_dev = float(t.item())
-    sec_per_solve = t_dev / args.steps
-    final_E = st.energy_final
+        t = sum(a.elapsed_time(b) for a, b in ev) / 1e3
+        if world > 1:
+            tt = torch.tensor([t], device=dev, dtype=torch.float64)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            t = float(tt.item())
+        return t / args.steps, sts
 
-    # e2e: the same solve through the C ABI with host buffers (pinned), the
-    # H2D copy of f and the D2H copy of u inside the timed region.
+    with ClockSampler(local) as clk:
+        sec_warm, st_warm = timed_steps(warm_step)
+        psnr_warm = synth.psnr(u.cpu().numpy(), img.clean)
+        sec_plain, st_plain = timed_steps(plain_step)
+        psnr_plain = synth.psnr(u.cpu().numpy(), img.clean)
+    clocks = clk.summary()
+    cycles = [s.cycles_run for s in st_warm]
+    cycles_plain = [s.cycles_run for s in st_plain]
+    sec_per_solve = sec_warm
+    final_E = st_warm[-1].energy_final
+
+    # e2e: the warm-start solve through the C ABI with host buffers (pinned):
+    # the H2D copy of f and the D2H copy of u inside the timed region.
     u_host = torch.empty_like(f_host).pin_memory()
     fd = torch.empty_like(f)     # persistent device input buffer of the e2e leg
     e2e_t = []
@@ -303,8 +335,7 @@ def main():
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         fd.copy_(f_host, non_blocking=True)
-        cm.cm_solve(fd, ALPHA, KIND, levels=0, cycles=MAX_CYCLES, tol=TOL, u_out=u, options=opts,
-                    ctx=ctx)
+        warm_step(fd, u)
         u_host.copy_(u, non_blocking=True)
         torch.cuda.synchronize()
         e2e_t.append(time.perf_counter() - t0)
@@ -337,6 +368,10 @@ def main():
                 "note": "curvature-stencil evaluations/s; peak = 152 SM x 16 MUFU/clk x "
                         "2.07 GHz / 8 rsqrt per evaluation (derived, nominal clock)"}
 
+    warm_eval = None
+    if not args.no_warmstart_eval:
+        warm_eval = ws.evaluate(net, n=16, side=1024, alpha=ALPHA, kind=KIND, tol=TOL, ctx=ctx)
+
     batched_res = None
     if not args.no_batched:
         batched_res = batched_measurement(cm, torch, synth, ctx, dev)
@@ -345,22 +380,28 @@ def main():
     if rank == 0 and not args.no_cpu_baseline:
         f64 = img.f.astype(np.float64)
         per_cycle, threads = oracle_cycle_seconds(f64, args.cpu_cycles)
-        mean_cycles = statistics.mean(cycles)
+        mean_cycles = statistics.mean(cycles_plain)   # the oracle runs the plain sweep
         cpu = {"value": per_cycle * mean_cycles, "unit": "s", "cores": threads, "kind": "oracle",
                "sample": f"{args.cpu_cycles} oracle cycle(s) on the {args.side}^2 image, "
-                         f"extrapolated x {mean_cycles:g} cycles to tol",
+                         f"extrapolated x {mean_cycles:g} cycles of the plain sweep to tol",
                "per_cycle_s": per_cycle}
 
     # kernels per cycle: one per colour on levels below the coarse threshold
     # (b < 64); tile sums + one per colour + apply on coarse levels; energy
     coarse = max(0, L - COARSE_LB)
     kernels_per_cycle = opts.ncolors * (L - coarse) + coarse * (opts.ncolors + 2) + 1
-    launches_per_solve = [1 + c * kernels_per_cycle for c in cycles]
+    # per warm step: 6 network kernels, 2 energy checks, then the solve
+    launches_per_solve = [8 + 1 + c * kernels_per_cycle for c in cycles]
     line = {"metric": METRIC, "value": sec_per_solve, "unit": "s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec_per_solve * 1e3,
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic", "config": workload_config(args.side),
             "cycles_to_tol": cycles, "sweeps_per_s": statistics.mean(cycles) / sec_per_solve,
+            "plain": {"s": sec_plain, "cycles_to_tol": cycles_plain, "psnr_db": psnr_plain,
+                      "final_energy": st_plain[-1].energy_final},
+            "warm_vs_plain_speedup": sec_plain / sec_warm,
+            "psnr_db": psnr_warm, "psnr_noisy_db": synth.psnr(img.f, img.clean),
+            "warmstart_eval_16x1024": warm_eval,
             "final_energy": final_E,
             "e2e": {"value": e2e, "unit": "s", "h2d_bytes_per_step": 4 * N,
                     "d2h_bytes_per_step": 4 * N},
