@@ -54,6 +54,8 @@ def parse():
                    help="skip the 16-image warm-start evaluation")
     p.add_argument("--no-batched", action="store_true",
                    help="skip the 64-image batched measurement")
+    p.add_argument("--cnn-only", action="store_true",
+                   help="profiling aid: warm-start inference on 16 x 1024^2 images and exit")
     p.add_argument("--phases-only", action="store_true",
                    help="profiling aid: two warm-up cycles, then one launch of every "
                         "(level, colour) phase on the image and exit")
@@ -187,12 +189,17 @@ def workload_config(side):
             "l2": "flushed between steps (512 MB write)"}
 
 
-def batched_measurement(cm, torch, synth, ctx, dev):
+def batched_measurement(cm, torch, synth, ctx, dev, rank=0, world=1):
     """64 images of uneven sizes (sides from {128, ..., 1024}, half mean and
     half Gaussian curvature, sigma ~ U(0.03, 0.12), alpha in {10, 20}) solved
     to tol 1e-4: one batched call vs one cm_solve call per image.  Metric:
-    aggregate Mpixel-sweeps/s = sum(H W cycles) / time."""
-    items = synth.uneven_batch(64)
+    aggregate Mpixel-sweeps/s = sum(H W cycles) / time.  With several ranks
+    the images are sharded by the LPT rule (no collective on the data path);
+    the job time is the maximum over ranks."""
+    from paper_2204_07921_gb300 import shard
+    all_items = synth.uneven_batch(64)
+    costs = [shard.image_cost(*it.image.f.shape) for it in all_items]
+    items = [all_items[i] for i in shard.my_share(costs, rank, world)]
     fs = [torch.from_numpy(it.image.f).to(dev) for it in items]
     outs = [torch.empty_like(t) for t in fs]
     al = [it.alpha for it in items]
@@ -223,11 +230,19 @@ def batched_measurement(cm, torch, synth, ctx, dev):
         torch.cuda.synchronize()
         t = e0.elapsed_time(e1) / 1e3
         mpx = sum(it.image.f.size * st.cycles_run for it, st in zip(items, sts)) / 1e6
-        res[name] = {"s": t, "mpixel_sweeps_per_s": mpx / t,
-                     "cycles_total": int(sum(st.cycles_run for st in sts))}
+        cyc = float(sum(st.cycles_run for st in sts))
+        if world > 1:
+            import torch.distributed as dist
+            v = torch.tensor([t, mpx, cyc], dtype=torch.float64, device=dev)
+            tmax = v[:1].clone()
+            dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+            dist.all_reduce(v, op=dist.ReduceOp.SUM)
+            t, mpx, cyc = float(tmax.item()), float(v[1].item()), float(v[2].item())
+        res[name] = {"s": t, "mpixel_sweeps_per_s": mpx / t, "cycles_total": int(cyc)}
     res["speedup"] = res["batched"]["mpixel_sweeps_per_s"] / res["one_at_a_time"]["mpixel_sweeps_per_s"]
     res["workload"] = "64 images, sides U{128..1024} x U{128..1024}, half mean / half Gaussian, tol 1e-4"
-    res["pixels"] = int(sum(it.image.f.size for it in items))
+    res["pixels"] = int(sum(it.image.f.size for it in all_items))
+    res["ranks"] = world
     return res
 
 
@@ -258,6 +273,17 @@ def main():
     stream = torch.cuda.current_stream()
     opts = cm.default_options()
     L = cm.cm_auto_levels(args.side, args.side)
+
+    if args.cnn_only:
+        from paper_2204_07921_gb300 import warmstart as ws
+        net = ws.Net.load(WARMSTART_PARAMS, ctx=ctx)
+        F = torch.stack([torch.from_numpy(synth.warmstart_image("test", i, 1024).f)
+                         for i in range(16)]).to(dev).contiguous()
+        net.forward(F)
+        net.forward(F)
+        torch.cuda.synchronize()
+        print(json.dumps({"cnn_only": True, "images": 16}))
+        return
 
     if args.phases_only:
         _, st = cm.cm_solve(f, ALPHA, KIND, cycles=2, u_out=u, options=opts, ctx=ctx)
@@ -374,7 +400,7 @@ def main():
 
     batched_res = None
     if not args.no_batched:
-        batched_res = batched_measurement(cm, torch, synth, ctx, dev)
+        batched_res = batched_measurement(cm, torch, synth, ctx, dev, rank, world)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
