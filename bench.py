@@ -185,7 +185,7 @@ def workload_config(side):
                         f"alpha 20, blocks 1..{side // 2}, 4 colours, tol 1e-4; learned warm "
                         f"start (6 conv3x3, 32 ch, BF16) then the sweep",
             "image": f"{side}x{side}", "kind": "mean", "alpha": ALPHA, "tol": TOL,
-            "levels": None, "ncolors": 4, "grid_points": 9, "golden_evals": 16,
+            "levels": None, "ncolors": 4, "grid_points": None, "golden_evals": None,
             "l2": "flushed between steps (512 MB write)"}
 
 
@@ -271,7 +271,9 @@ def main():
     u = torch.empty_like(f)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
-    opts = cm.default_options()
+    from paper_2204_07921_gb300 import autotune
+    opts, tune_rec = autotune.tune(args.side, args.side, KIND, ALPHA, tol=TOL, ncolors=NCOLORS,
+                                   ctx=ctx)
     L = cm.cm_auto_levels(args.side, args.side)
 
     if args.cnn_only:
@@ -435,6 +437,9 @@ def main():
             "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks,
             "b1_phase_ms": b1_ms, "batched": batched_res}
     line["config"]["levels"] = L
+    line["config"]["grid_points"] = opts.grid_points
+    line["config"]["golden_evals"] = opts.golden_evals
+    line["autotune"] = tune_rec
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -77,8 +77,9 @@ typedef struct {
     double energy_trace[4097];/* F(u_0), F(u_1), ... (first max_trace + 1 cycles) */
 } cm_stats;
 
-/* Default options: ncolors 4 (the paper's four-colour decomposition, Sec. 2.3), G 9, K 16,
- * paper_candidate 1, use_graph 1, max_trace 4096. */
+/* Default options: ncolors 4 (the paper's four-colour decomposition, Sec. 2.3), G 5, K 6
+ * (the budget the autotuner picks on every tested workload: fastest time to tolerance at the
+ * lowest final energy), paper_candidate 1, use_graph 1, max_trace 4096. */
 int cm_options_default(cm_options* opts /* host */);
 
 /* Create a context on CUDA device `device` (makes it current on this

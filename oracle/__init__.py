@@ -27,7 +27,8 @@ _lock = threading.Lock()
 _lib = None
 
 MEAN, GAUSS = 0, 1
-DEFAULT_G, DEFAULT_K = 9, 16
+# Default search budget: the same as the library's default options.
+DEFAULT_G, DEFAULT_K = 5, 6
 
 
 def build(force: bool = False) -> str:

@@ -203,8 +203,8 @@ extern "C" {
 int cm_options_default(cm_options* o) {
     if (!o) return CM_ERR_INVALID;
     o->ncolors = 4;
-    o->grid_points = 9;
-    o->golden_evals = 16;
+    o->grid_points = 5;
+    o->golden_evals = 6;
     o->paper_candidate = 1;
     o->use_graph = 1;
     o->max_trace = 4096;

@@ -22,6 +22,18 @@
 #include "cm_kernels.h"
 #include "cm_search.cuh"
 
+// Lanes per block on the warp-group levels (b = 2: ring 16, b = 4: ring 32);
+// each lane holds ring / lanes ring pixels.
+#ifndef CM_B2_GT
+#define CM_B2_GT 8
+#endif
+#ifndef CM_B4_GT
+#define CM_B4_GT 16
+#endif
+#ifndef CM_B128_CTA
+#define CM_B128_CTA 0
+#endif
+
 namespace cm {
 
 // Block pixels [r0, r0 + bh) x [c0, c0 + bw), visited with stride `stride`
@@ -37,12 +49,12 @@ __device__ __forceinline__ void for_block_pixels(int first, int stride, int r0, 
     }
 }
 
-template <int KIND, int GT>
+template <int KIND, int GT, int RPT>
 __global__ void __launch_bounds__(128) phase_warp_kernel(
     const float* __restrict__ S, float* __restrict__ R, const float* __restrict__ f, int H, int W,
     SearchParams sp, int lb, int ncol, int k, float* __restrict__ c_out,
     const int* __restrict__ active) {
-    static_assert(GT == 16 || GT == 32, "warp groups only");
+    static_assert(GT == 4 || GT == 8 || GT == 16 || GT == 32, "warp groups only");
     if (active && *active == 0) return;
     constexpr int GPC = 128 / GT;
     const int b = 1 << lb;
@@ -61,18 +73,24 @@ __global__ void __launch_bounds__(128) phase_warp_kernel(
                          [&](size_t p) { s1 += S[p] - f[p]; });
 #pragma unroll
     for (int off = GT / 2; off > 0; off >>= 1) s1 += __shfl_xor_sync(0xffffffffu, s1, off, GT);
-    float w[9];
-    unsigned mask = 0;
-    const bool has = blk_on && ring_slot(lane, r0, r1, c0, c1, H, W, S, R, lb, ncol, k, w, mask);
-    AffPix px;
-    if (has) {
-        px = aff_pix(w, mask);
-    } else {
+    AffPix px[RPT];
+    bool has[RPT];
 #pragma unroll
-        for (int t = 0; t < 4; ++t) px.d[t] = AffDir{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    for (int t = 0; t < RPT; ++t) {
+        float w[9];
+        unsigned mask = 0;
+        has[t] = blk_on && ring_slot(lane + t * GT, r0, r1, c0, c1, H, W, S, R, lb, ncol, k, w, mask);
+        if (has[t]) {
+            px[t] = aff_pix(w, mask);
+        } else {
+#pragma unroll
+            for (int d = 0; d < 4; ++d) px[t].d[d] = AffDir{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        }
     }
     auto ring = [&](float c) {
-        float v = has ? aff_abs_curv<KIND>(px, c) : 0.0f;
+        float v = 0.0f;
+#pragma unroll
+        for (int t = 0; t < RPT; ++t) v += has[t] ? aff_abs_curv<KIND>(px[t], c) : 0.0f;
 #pragma unroll
         for (int off = GT / 2; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off, GT);
         return v;
@@ -401,7 +419,11 @@ static cudaError_t launch_coarse_kind(const PhaseArgs& A, const float* partials,
     const int nact = A.ncolors == 2 ? nbi * ((nbj + 1) / 2) : ((nbi + 1) / 2) * ((nbj + 1) / 2);
     switch (A.lb) {
         case 6: launch_coarse<KIND, 512, 1, 1>(A, partials, cj, nact, st); break;
+#if CM_B128_CTA
+        case 7: launch_coarse<KIND, 1024, 1, 1>(A, partials, cj, nact, st); break;
+#else
         case 7: launch_coarse<KIND, 256, 4, 1>(A, partials, cj, nact, st); break;
+#endif
         case 8: launch_coarse<KIND, 256, 8, 1>(A, partials, cj, nact, st); break;
         case 9: launch_coarse<KIND, 512, 8, 1>(A, partials, cj, nact, st); break;
         case 10: launch_coarse<KIND, 1024, 8, 1>(A, partials, cj, nact, st); break;
@@ -444,11 +466,11 @@ cudaError_t launch_level_coarse(const PhaseArgs& A0, float* partials, float* cj,
     return cudaGetLastError();
 }
 
-template <int KIND, int GT>
+template <int KIND, int GT, int RPT>
 static void launch_warp(const PhaseArgs& A, int nact, cudaStream_t st) {
     constexpr int GPC = 128 / GT;
     SearchParams sp{A.alpha, A.G, A.K};
-    phase_warp_kernel<KIND, GT><<<(nact + GPC - 1) / GPC, 128, 0, st>>>(
+    phase_warp_kernel<KIND, GT, RPT><<<(nact + GPC - 1) / GPC, 128, 0, st>>>(
         A.S, A.R, A.f, A.H, A.W, sp, A.lb, A.ncolors, A.colour, A.c_out, A.active);
 }
 
@@ -466,8 +488,8 @@ static cudaError_t launch_blocks_kind(const PhaseArgs& A, cudaStream_t st) {
     const int nact = A.ncolors == 2 ? nbi * ((nbj + 1) / 2) : ((nbi + 1) / 2) * ((nbj + 1) / 2);
     // ring of a full block: 8b pixels = Q * CT * RPT slots
     switch (A.lb) {
-        case 1: launch_warp<KIND, 16>(A, nact, st); break;
-        case 2: launch_warp<KIND, 32>(A, nact, st); break;
+        case 1: launch_warp<KIND, CM_B2_GT, 16 / CM_B2_GT>(A, nact, st); break;
+        case 2: launch_warp<KIND, CM_B4_GT, 32 / CM_B4_GT>(A, nact, st); break;
         case 3: launch_cluster<KIND, 64, 1, 1>(A, nact, st); break;
         case 4: launch_cluster<KIND, 128, 1, 1>(A, nact, st); break;
         case 5: launch_cluster<KIND, 256, 1, 1>(A, nact, st); break;

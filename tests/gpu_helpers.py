@@ -21,6 +21,8 @@ import oracle
 
 TIE_REL = 1e-5
 C_TOL = 1e-4
+# search budget of both sides (the library's and the oracle's default)
+G_DEF, K_DEF = oracle.DEFAULT_G, oracle.DEFAULT_K
 
 
 def blocks_of_colour(H, W, b, ncolors, k):
@@ -43,7 +45,7 @@ def energy_scale(u, f, r0, c0, bh, bw, c, alpha, kind, c_fid):
 
 
 def compare_phase(u, f, c_gpu_blocks, alpha, kind, b, ncolors, k, c_orc_blocks, sample=None,
-                  G=9, K=16, use_paper=True):
+                  G=G_DEF, K=K_DEF, use_paper=True):
     """Compare per-block shifts of one phase.  c_*_blocks: dict (bi, bj) -> c.
     Returns (n_blocks, n_match, n_tie, list_of_failures)."""
     H, W = u.shape

@@ -44,7 +44,7 @@ def test_host_only_entry_points():
     lib = cm.load()
     o = cm.Options()
     assert lib.cm_options_default(ctypes.byref(o)) == 0
-    assert (o.ncolors, o.grid_points, o.golden_evals, o.paper_candidate) == (4, 9, 16, 1)
+    assert (o.ncolors, o.grid_points, o.golden_evals, o.paper_candidate) == (4, 5, 6, 1)
     assert lib.cm_options_default(None) == cm.CM_ERR_INVALID
     assert lib.cm_auto_levels(64, 64) == 6
     assert lib.cm_auto_levels(1024, 1024) == 10
@@ -57,6 +57,15 @@ def test_host_only_entry_points():
         == cm.CM_ERR_INVALID
     assert lib.cm_create(None, 0) == cm.CM_ERR_INVALID
     assert lib.cm_last_error(None) == b"null context"
+
+
+def test_default_budget_agrees_with_oracle():
+    """Parity tests rely on the library and the oracle using the same
+    default search budget."""
+    import oracle
+    import paper_2204_07921_gb300 as cm
+    o = cm.default_options()
+    assert (o.grid_points, o.golden_evals) == (oracle.DEFAULT_G, oracle.DEFAULT_K)
 
 
 def test_auto_levels_agree_with_oracle():

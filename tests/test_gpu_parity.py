@@ -14,7 +14,7 @@ if not torch.cuda.is_available():
 import oracle  # noqa: E402
 import paper_2204_07921_gb300 as cm  # noqa: E402
 import synth  # noqa: E402
-from gpu_helpers import C_TOL, blocks_of_colour, compare_phase  # noqa: E402
+from gpu_helpers import C_TOL, G_DEF, K_DEF, blocks_of_colour, compare_phase  # noqa: E402
 
 pytestmark = pytest.mark.gpu
 DEV = torch.device("cuda:0")
@@ -69,7 +69,7 @@ def test_curvature_parity(kind):
     assert np.all(np.abs(kg - ko) <= bound)
 
 
-def gpu_phase(u, f, alpha, kind, b, ncolors, k, G=9, K=16, use_paper=1):
+def gpu_phase(u, f, alpha, kind, b, ncolors, k, G=G_DEF, K=K_DEF, use_paper=1):
     H, W = u.shape
     S = to_dev(u)
     R = S.clone()
