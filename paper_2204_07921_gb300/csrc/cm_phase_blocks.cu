@@ -1,9 +1,9 @@
 // cm_phase_blocks.cu -- sweep levels with block side b >= 2 (Sec. 2.2).
 //
-//  phase_warp_kernel     b = 2 and 4: 16 or 32 lanes of one warp per block,
-//                        one ring pixel per lane; candidate energies are
-//                        warp-shuffle reductions.
-//  phase_cluster_kernel  b >= 8: one CTA, or a thread-block cluster of up to 8
+//  phase_warp_kernel     b = 2, 4 and 8: 8, 16 or 32 lanes of one warp per
+//                        block, two ring pixels per lane; candidate energies
+//                        are warp-shuffle reductions.
+//  phase_cluster_kernel  b >= 16: one CTA, or a thread-block cluster of up to 8
 //                        CTAs on different SMs, per block, one ring pixel per
 //                        thread; candidate energies reduce through shared
 //                        memory and, across the cluster, distributed shared
@@ -22,8 +22,8 @@
 #include "cm_kernels.h"
 #include "cm_search.cuh"
 
-// Lanes per block on the warp-group levels (b = 2: ring 16, b = 4: ring 32);
-// each lane holds ring / lanes ring pixels.
+// Lanes per block on the warp-group levels (b = 2: ring 16, b = 4: ring 32,
+// b = 8: ring 64 on 32 lanes); each lane holds ring / lanes ring pixels.
 #ifndef CM_B2_GT
 #define CM_B2_GT 8
 #endif
@@ -490,7 +490,7 @@ static cudaError_t launch_blocks_kind(const PhaseArgs& A, cudaStream_t st) {
     switch (A.lb) {
         case 1: launch_warp<KIND, CM_B2_GT, 16 / CM_B2_GT>(A, nact, st); break;
         case 2: launch_warp<KIND, CM_B4_GT, 32 / CM_B4_GT>(A, nact, st); break;
-        case 3: launch_cluster<KIND, 64, 1, 1>(A, nact, st); break;
+        case 3: launch_warp<KIND, 32, 2>(A, nact, st); break;
         case 4: launch_cluster<KIND, 128, 1, 1>(A, nact, st); break;
         case 5: launch_cluster<KIND, 256, 1, 1>(A, nact, st); break;
         case 6: launch_cluster<KIND, 256, 2, 1>(A, nact, st); break;
