@@ -234,6 +234,7 @@ int cm_create(cm_ctx** out, int device) {
     if (e == cudaSuccess) e = cudaMalloc(&ctx->E_dev, 8 * sizeof(double));
     if (e == cudaSuccess) e = cudaMallocHost(&ctx->E_pinned, 8 * sizeof(double));
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cm::coarse_setup();
     if (e != cudaSuccess) {
         cm_destroy(ctx);
         return e == cudaErrorMemoryAllocation ? CM_ERR_OOM : CM_ERR_CUDA;

@@ -189,4 +189,6 @@ __device__ __forceinline__ void consider(Best& b, float c, float E) {
 
 constexpr float GOLDEN = 0.6180339887498949f;   // (sqrt(5) - 1) / 2
 
+
+
 }  // namespace cm

@@ -108,11 +108,8 @@ cudaError_t launch_energy(const float* u, const float* f, int H, int W, float al
                           double* partials, unsigned int* ticket, double* E_out,
                           cudaStream_t st, const int* active) {
     dim3 grid((W + E_TW - 1) / E_TW, (H + E_TH - 1) / E_TH);
-    if (kind == KIND_MEAN)
-        energy_kernel<KIND_MEAN><<<grid, 256, 0, st>>>(u, f, H, W, alpha, partials, ticket, E_out, active);
-    else
-        energy_kernel<KIND_GAUSS><<<grid, 256, 0, st>>>(u, f, H, W, alpha, partials, ticket, E_out, active);
-    return cudaGetLastError();
+    return launch_k(kind == KIND_MEAN ? energy_kernel<KIND_MEAN> : energy_kernel<KIND_GAUSS>, grid,
+                    dim3(256), st, 1, u, f, H, W, alpha, partials, ticket, E_out, active);
 }
 
 size_t energy_partials_needed(int H, int W) {

@@ -5,6 +5,26 @@
 
 namespace cm {
 
+// Launch `kern` on st, as a grid of thread-block clusters of cluster_x CTAs
+// when cluster_x > 1.
+template <class... KArgs, class... Args>
+inline cudaError_t launch_k(void (*kern)(KArgs...), dim3 grid, dim3 block, cudaStream_t st,
+                            unsigned cluster_x, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = cluster_x;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = cluster_x > 1 ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
 struct PhaseArgs {
     const float* S;   // state at the start of the level
     float* R;         // blocks already updated on this level (and the output)
@@ -38,5 +58,8 @@ int coarse_level_log2();
 size_t coarse_partials_needed(int H, int W);
 size_t coarse_c_needed(int H, int W);
 cudaError_t launch_level_coarse(const PhaseArgs& a, float* partials, float* cj, cudaStream_t st);
+// Per-process kernel attributes of the coarse path (cluster sizes above 8);
+// call before the first launch, outside stream capture.
+cudaError_t coarse_setup();
 
 }  // namespace cm

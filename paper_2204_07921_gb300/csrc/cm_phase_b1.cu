@@ -300,24 +300,17 @@ __global__ void __launch_bounds__(128, CM_B1_MIN_BLOCKS) phase_b1_kernel(const f
 
 cudaError_t launch_phase_b1(const PhaseArgs& A, cudaStream_t st) {
     SearchParams sp{A.alpha, A.G, A.K};
-    if (A.ncolors == 2) {
-        dim3 grid((A.W + B1Tile<2>::TW - 1) / B1Tile<2>::TW, (A.H + B1Tile<2>::TH - 1) / B1Tile<2>::TH);
-        if (A.kind == KIND_MEAN)
-            phase_b1_kernel<KIND_MEAN, 2><<<grid, 128, 0, st>>>(A.S, A.R, A.f, A.H, A.W, sp,
-                                                                A.colour, A.use_paper, A.c_out, A.active);
-        else
-            phase_b1_kernel<KIND_GAUSS, 2><<<grid, 128, 0, st>>>(A.S, A.R, A.f, A.H, A.W, sp,
-                                                                 A.colour, A.use_paper, A.c_out, A.active);
-    } else {
-        dim3 grid((A.W + B1Tile<4>::TW - 1) / B1Tile<4>::TW, (A.H + B1Tile<4>::TH - 1) / B1Tile<4>::TH);
-        if (A.kind == KIND_MEAN)
-            phase_b1_kernel<KIND_MEAN, 4><<<grid, 128, 0, st>>>(A.S, A.R, A.f, A.H, A.W, sp,
-                                                                A.colour, A.use_paper, A.c_out, A.active);
-        else
-            phase_b1_kernel<KIND_GAUSS, 4><<<grid, 128, 0, st>>>(A.S, A.R, A.f, A.H, A.W, sp,
-                                                                 A.colour, A.use_paper, A.c_out, A.active);
-    }
-    return cudaGetLastError();
+    auto go = [&](auto kern, int TW, int TH) {
+        dim3 grid((A.W + TW - 1) / TW, (A.H + TH - 1) / TH);
+        return launch_k(kern, grid, dim3(128), st, 1, A.S, A.R, A.f, A.H, A.W, sp, A.colour,
+                        A.use_paper, A.c_out, A.active);
+    };
+    if (A.ncolors == 2)
+        return A.kind == KIND_MEAN
+                   ? go(phase_b1_kernel<KIND_MEAN, 2>, B1Tile<2>::TW, B1Tile<2>::TH)
+                   : go(phase_b1_kernel<KIND_GAUSS, 2>, B1Tile<2>::TW, B1Tile<2>::TH);
+    return A.kind == KIND_MEAN ? go(phase_b1_kernel<KIND_MEAN, 4>, B1Tile<4>::TW, B1Tile<4>::TH)
+                               : go(phase_b1_kernel<KIND_GAUSS, 4>, B1Tile<4>::TW, B1Tile<4>::TH);
 }
 
 }  // namespace cm

@@ -30,9 +30,6 @@
 #ifndef CM_B4_GT
 #define CM_B4_GT 16
 #endif
-#ifndef CM_B128_CTA
-#define CM_B128_CTA 0
-#endif
 
 namespace cm {
 
@@ -265,22 +262,53 @@ __global__ void __launch_bounds__(256) apply_kernel(const float* __restrict__ S,
     }
 }
 
-template <int KIND, int CT, int Q, int RPT, int LA>
-__global__ void __cluster_dims__(Q, 1, 1) __launch_bounds__(CT) phase_coarse_kernel(
+// Warp-transposed sum of 16 values: four exchange steps halve the values a
+// lane holds, so 16 shuffles (not 5 x 16) leave in lanes 2q and 2q + 1 the
+// warp sum of value red16_index(2q).  The order of the additions is fixed.
+__device__ __forceinline__ int red16_index(int lane) {
+    return (((lane >> 4) & 1) << 3) | (((lane >> 3) & 1) << 2) | (((lane >> 2) & 1) << 1) |
+           ((lane >> 1) & 1);
+}
+
+template <int H>
+__device__ __forceinline__ void red16_step(float (&v)[16], int lane) {
+    const bool up = (lane & (2 * H)) != 0;
+#pragma unroll
+    for (int i = 0; i < H; ++i) {
+        const float send = up ? v[i] : v[i + H];
+        const float keep = up ? v[i + H] : v[i];
+        v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 2 * H);
+    }
+}
+
+__device__ __forceinline__ float warp_red16(float (&v)[16], int lane) {
+    red16_step<8>(v, lane);
+    red16_step<4>(v, lane);
+    red16_step<2>(v, lane);
+    red16_step<1>(v, lane);
+    return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
+}
+
+// One block per CTA (Q = 1) or per cluster of Q CTAs; RPT ring pixels per
+// thread.  Launched with the cluster size as a launch attribute.
+template <int KIND, int CT, int Q, int RPT>
+__global__ void __launch_bounds__(CT) phase_coarse_kernel(
     const float* __restrict__ S, const float* __restrict__ partials, float* __restrict__ cj,
     int H, int W, SearchParams sp, int lb, int ncol, int k, float* __restrict__ c_out,
     const int* __restrict__ active) {
     namespace cg = cooperative_groups;
-    if (active && *active == 0) return;   // uniform over the grid
-    constexpr int GT = CT * Q;
+    constexpr unsigned FULL = 0xffffffffu;
     constexpr int NW = CT / 32;
-    constexpr int MB = 9;
-    __shared__ float red[2][MB][NW];
-    __shared__ float tot[2][MB];
-    __shared__ float part[2][Q][MB];
+    static_assert(NW >= 2 && (NW & (NW - 1)) == 0 && Q >= 1 && Q <= 32 && (Q & (Q - 1)) == 0,
+                  "power-of-two warps and cluster ranks");
+    if (active && *active == 0) return;   // uniform over the grid
+    __shared__ float red[2][16][NW + 1];   // warp partials per candidate, double-buffered
+    __shared__ float part[2][Q][16];       // CTA totals pushed by every cluster rank
+    __shared__ float red1[NW];
     const int rank = Q > 1 ? (int)cg::this_cluster().block_rank() : 0;
     const int a = blockIdx.x / Q;
     const int g = rank * CT + threadIdx.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int b = 1 << lb;
     const int nbi = (H + b - 1) >> lb, nbj = (W + b - 1) >> lb;
     int bi, bj;
@@ -288,128 +316,145 @@ __global__ void __cluster_dims__(Q, 1, 1) __launch_bounds__(CT) phase_coarse_ker
     const int r0 = bi << lb, c0 = bj << lb;
     const int r1 = min(r0 + b, H), c1 = min(c0 + b, W);
     const int bh = r1 - r0, bw = c1 - c0;
-    int flip = 0;
-    auto reduce_vec = [&](float* v, int m) {
-#pragma unroll
-        for (int j = 0; j < MB; ++j)
-            if (j < m) {
-#pragma unroll
-                for (int off = 16; off > 0; off >>= 1) v[j] += __shfl_xor_sync(0xffffffffu, v[j], off);
-            }
-        if ((threadIdx.x & 31) == 0) {
-#pragma unroll
-            for (int j = 0; j < MB; ++j)
-                if (j < m) red[flip][j][threadIdx.x >> 5] = v[j];
-        }
-        __syncthreads();
-        if (NW > 8) {
-            // warp j folds candidate j's warp partials (fixed order) and
-            // publishes the CTA total; one more barrier broadcasts it
-            const int wj = threadIdx.x >> 5, ln = threadIdx.x & 31;
-            if (wj < m) {
-                float t = ln < NW ? red[flip][wj][ln] : 0.0f;
-#pragma unroll
-                for (int off = 16; off > 0; off >>= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
-                if (ln == 0) tot[flip][wj] = t;
-            }
-            __syncthreads();
-#pragma unroll
-            for (int j = 0; j < MB; ++j)
-                if (j < m) v[j] = tot[flip][j];
-        } else {
-#pragma unroll
-            for (int j = 0; j < MB; ++j)
-                if (j < m) {
-                    float t = 0.0f;
-#pragma unroll
-                    for (int i = 0; i < NW; ++i) t += red[flip][j][i];
-                    v[j] = t;
-                }
-        }
-        if (Q > 1) {
-            cg::cluster_group cl = cg::this_cluster();
-            if (threadIdx.x < Q) {
-                float* dst = cl.map_shared_rank(&part[flip][rank][0], threadIdx.x);
-#pragma unroll
-                for (int j = 0; j < MB; ++j)
-                    if (j < m) dst[j] = v[j];
-            }
-            cl.sync();
-#pragma unroll
-            for (int j = 0; j < MB; ++j)
-                if (j < m) {
-                    float t = 0.0f;
-#pragma unroll
-                    for (int q = 0; q < Q; ++q) t += part[flip][q][j];
-                    v[j] = t;
-                }
-        }
-        flip ^= 1;
-    };
-    // S1 from the tile sums of the block
-    const int ntc = (W + TILE - 1) / TILE;
-    const int tw = (bw + TILE - 1) / TILE, th = (bh + TILE - 1) / TILE;
-    float s1 = 0.0f;
-    for (int t = g; t < tw * th; t += GT) {
-        const int ti = t / tw, tj = t - ti * tw;
-        s1 += partials[(size_t)(r0 / TILE + ti) * ntc + (c0 / TILE + tj)];
-    }
-    reduce_vec(&s1, 1);
-    const float S1 = s1;
-    // ring windows from the lazy phase state
+
+    // ring windows from the lazy phase state (loads issued before the S1 sum)
     auto value = [&](int r, int c) {
         float v = S[(size_t)r * W + c];
         if (k > 0 && pixel_colour(r, c, lb, ncol) < k) v += cj[(size_t)(r >> lb) * nbj + (c >> lb)];
         return v;
     };
-    AffPix px[RPT];
+    float win[RPT][9];
+    unsigned mask[RPT];
     bool has[RPT];
 #pragma unroll
     for (int t = 0; t < RPT; ++t) {
-        float w[9];
-        unsigned mask = 0;
-        has[t] = ring_slot_v(g + t * GT, r0, r1, c0, c1, H, W, value, w, mask);
+        mask[t] = 0;
+        has[t] = ring_slot_v(g + t * CT * Q, r0, r1, c0, c1, H, W, value, win[t], mask[t]);
+    }
+    // S1 from the tile sums of the block, summed by every CTA in the same
+    // order (no cluster barrier)
+    const int ntc = (W + TILE - 1) / TILE;
+    const int tw = (bw + TILE - 1) / TILE, th = (bh + TILE - 1) / TILE;
+    float s1 = 0.0f;
+    for (int t = threadIdx.x; t < tw * th; t += CT) {
+        const int ti = t / tw, tj = t - ti * tw;
+        s1 += partials[(size_t)(r0 / TILE + ti) * ntc + (c0 / TILE + tj)];
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) s1 += __shfl_xor_sync(FULL, s1, off);
+    if (lane == 0) red1[warp] = s1;
+    __syncthreads();
+    float S1 = lane < NW ? red1[lane] : 0.0f;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) S1 += __shfl_xor_sync(FULL, S1, off);
+
+    AffPix px[RPT];
+#pragma unroll
+    for (int t = 0; t < RPT; ++t) {
         if (has[t]) {
-            px[t] = aff_pix(w, mask);
+            px[t] = aff_pix(win[t], mask[t]);
         } else {
 #pragma unroll
             for (int d = 0; d < 4; ++d) px[t].d[d] = AffDir{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         }
     }
-    auto ringv = [&](const float* cs, int m, float* out) {
+
+    // One round: every thread evaluates its ring pixels at the 16 candidates,
+    // warps reduce (transposed), CTAs fold the warps and, in a cluster, push
+    // their totals to every rank; each warp then folds the ranks (or, Q = 1,
+    // the warps) itself: lane l ends with the total of candidate l / 2.
+    int flip = 0;
+    auto round = [&](float mine, int m) -> float {
+        float v[16];
 #pragma unroll
-        for (int j = 0; j < MB; ++j) {
+        for (int j = 0; j < 16; ++j) {
+            const float c = __shfl_sync(FULL, mine, j);
             float acc = 0.0f;
             if (j < m) {
 #pragma unroll
                 for (int t = 0; t < RPT; ++t)
-                    if (has[t]) acc += aff_abs_curv<KIND>(px[t], cs[j]);
+                    if (has[t]) acc += aff_abs_curv<KIND>(px[t], c);
             }
-            out[j] = acc;
+            v[j] = acc;
         }
-        reduce_vec(out, m);
+        const float ws = warp_red16(v, lane);
+        if ((lane & 1) == 0) red[flip][red16_index(lane)][warp] = ws;
+        __syncthreads();
+        const int jc = lane >> 1, half = lane & 1;
+        float tot = 0.0f;
+        if (Q == 1) {
+#pragma unroll
+            for (int i = 0; i < NW / 2; ++i) tot += red[flip][jc][half * (NW / 2) + i];
+        } else {
+            cg::cluster_group cl = cg::this_cluster();
+            if (threadIdx.x < 16 * NW) {
+                const int j = threadIdx.x / NW, i = threadIdx.x % NW;
+                float t = red[flip][j][i];
+#pragma unroll
+                for (int off = NW / 2; off > 0; off >>= 1) t += __shfl_xor_sync(FULL, t, off);
+                for (int q = i; q < Q; q += NW) {
+                    float* dst = cl.map_shared_rank(&part[flip][0][0], q);
+                    dst[rank * 16 + j] = t;
+                }
+            }
+            cl.sync();
+            if (Q == 2) {
+                tot = part[flip][half][jc];
+            } else {
+#pragma unroll
+                for (int q = 0; q < Q / 2; ++q) tot += part[flip][half * (Q / 2) + q][jc];
+            }
+        }
+        tot += __shfl_xor_sync(FULL, tot, 1);
+        flip ^= 1;
+        return tot;
     };
-    // Cluster reductions cost a cluster barrier each, so clusters run the
-    // golden section with a 3-step lookahead; single CTAs run it step by step.
-    const float cbest = LA == 3 ? block_search_lookahead<MB>(ringv, sp, (float)(bh * bw), S1)
-                                : block_search_batched<MB>(ringv, sp, (float)(bh * bw), S1);
+    const float cbest = block_search_rounds(round, sp, (float)(bh * bw), S1);
     // Blocks of this colour read cj only for blocks of earlier colours, so
-    // writing this block's entry races with no reader.
+    // writing this block's entry races with no reader.  The last DSMEM store
+    // precedes the last cluster barrier, so CTAs may exit without another.
     if (g == 0) {
         cj[(size_t)bi * nbj + bj] = cbest;
         if (c_out) c_out[(size_t)bi * nbj + bj] = cbest;
     }
-    if (Q > 1) cg::this_cluster().sync();
 }
 
 template <int KIND, int CT, int Q, int RPT>
-static void launch_coarse(const PhaseArgs& A, const float* partials, float* cj, int nact,
-                          cudaStream_t st) {
-    SearchParams sp{A.alpha, A.G, A.K};
-    constexpr int LA = Q > 1 ? 3 : 1;
-    phase_coarse_kernel<KIND, CT, Q, RPT, LA><<<nact * Q, CT, 0, st>>>(
-        A.S, partials, cj, A.H, A.W, sp, A.lb, A.ncolors, A.colour, A.c_out, A.active);
+static cudaError_t launch_coarse(const PhaseArgs& A, const float* partials, float* cj, int nact,
+                                 int spec, int dmax, cudaStream_t st) {
+    SearchParams sp{A.alpha, A.G, A.K, spec, dmax};
+    return launch_k(phase_coarse_kernel<KIND, CT, Q, RPT>, dim3(nact * Q), dim3(CT), st, Q, A.S,
+                    partials, cj, A.H, A.W, sp, A.lb, A.ncolors, A.colour, A.c_out, A.active);
 }
+
+// Level -> kernel shape (threads, cluster CTAs, ring pixels per thread; the
+// ring of a full block, 8b pixels, is CT * Q * RPT) and search rounds
+// (speculative first pair, golden steps per round).
+#ifndef CM_L6_CT
+#define CM_L6_CT 256
+#endif
+#ifndef CM_L6_Q
+#define CM_L6_Q 2
+#endif
+#ifndef CM_L6_SPEC
+#define CM_L6_SPEC 1
+#endif
+#ifndef CM_L6_DMAX
+#define CM_L6_DMAX 4
+#endif
+#ifndef CM_L79_SPEC
+#define CM_L79_SPEC 0
+#endif
+#ifndef CM_L79_DMAX
+#define CM_L79_DMAX 4
+#endif
+#define CM_COARSE_SHAPES(X)              \
+    X(6, CM_L6_CT, CM_L6_Q, 1, CM_L6_SPEC, CM_L6_DMAX) \
+    X(7, 256, 4, 1, CM_L79_SPEC, CM_L79_DMAX)          \
+    X(8, 256, 8, 1, CM_L79_SPEC, CM_L79_DMAX)          \
+    X(9, 512, 8, 1, CM_L79_SPEC, CM_L79_DMAX)          \
+    X(10, 512, 8, 2, 1, 4)               \
+    X(11, 512, 16, 2, 1, 4)
 
 template <int KIND>
 static cudaError_t launch_coarse_kind(const PhaseArgs& A, const float* partials, float* cj,
@@ -418,19 +463,28 @@ static cudaError_t launch_coarse_kind(const PhaseArgs& A, const float* partials,
     const int nbi = (A.H + b - 1) / b, nbj = (A.W + b - 1) / b;
     const int nact = A.ncolors == 2 ? nbi * ((nbj + 1) / 2) : ((nbi + 1) / 2) * ((nbj + 1) / 2);
     switch (A.lb) {
-        case 6: launch_coarse<KIND, 512, 1, 1>(A, partials, cj, nact, st); break;
-#if CM_B128_CTA
-        case 7: launch_coarse<KIND, 1024, 1, 1>(A, partials, cj, nact, st); break;
-#else
-        case 7: launch_coarse<KIND, 256, 4, 1>(A, partials, cj, nact, st); break;
-#endif
-        case 8: launch_coarse<KIND, 256, 8, 1>(A, partials, cj, nact, st); break;
-        case 9: launch_coarse<KIND, 512, 8, 1>(A, partials, cj, nact, st); break;
-        case 10: launch_coarse<KIND, 1024, 8, 1>(A, partials, cj, nact, st); break;
-        case 11: launch_coarse<KIND, 1024, 8, 2>(A, partials, cj, nact, st); break;
+#define CM_CASE(LB, CT, Q, RPT, SPEC, DMAX) \
+    case LB: return launch_coarse<KIND, CT, Q, RPT>(A, partials, cj, nact, SPEC, DMAX, st);
+        CM_COARSE_SHAPES(CM_CASE)
+#undef CM_CASE
         default: return cudaErrorInvalidValue;
     }
-    return cudaGetLastError();
+}
+
+// Clusters of more than 8 CTAs need the non-portable size allowed per kernel;
+// run once per process before the first launch (outside stream capture).
+cudaError_t coarse_setup() {
+    cudaError_t e = cudaSuccess;
+#define CM_SETUP(LB, CT, Q, RPT, SPEC, DMAX)                                                  \
+    if (Q > 8 && e == cudaSuccess)                                                            \
+        e = cudaFuncSetAttribute(phase_coarse_kernel<KIND_MEAN, CT, Q, RPT>,                  \
+                                 cudaFuncAttributeNonPortableClusterSizeAllowed, 1);          \
+    if (Q > 8 && e == cudaSuccess)                                                            \
+        e = cudaFuncSetAttribute(phase_coarse_kernel<KIND_GAUSS, CT, Q, RPT>,                 \
+                                 cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    CM_COARSE_SHAPES(CM_SETUP)
+#undef CM_SETUP
+    return e;
 }
 
 size_t coarse_partials_needed(int H, int W) {
@@ -448,8 +502,8 @@ int coarse_level_log2() { return COARSE_LB; }
 cudaError_t launch_level_coarse(const PhaseArgs& A0, float* partials, float* cj,
                                 cudaStream_t st) {
     dim3 tg((A0.W + TILE - 1) / TILE, (A0.H + TILE - 1) / TILE);
-    tile_sums_kernel<<<tg, 256, 0, st>>>(A0.S, A0.f, A0.H, A0.W, partials, A0.active);
-    cudaError_t e = cudaGetLastError();
+    cudaError_t e = launch_k(tile_sums_kernel, tg, dim3(256), st, 1, A0.S, A0.f, A0.H, A0.W,
+                             partials, A0.active);
     if (e != cudaSuccess) return e;
     for (int k = 0; k < A0.ncolors; ++k) {
         PhaseArgs A = A0;
@@ -462,23 +516,23 @@ cudaError_t launch_level_coarse(const PhaseArgs& A0, float* partials, float* cj,
     const int nbj = (A0.W + b - 1) / b;
     const size_t N = (size_t)A0.H * A0.W;
     const int grid = (int)std::min<size_t>((N + 255) / 256, 152 * 16);
-    apply_kernel<<<grid, 256, 0, st>>>(A0.S, A0.R, cj, A0.H, A0.W, A0.lb, nbj, A0.active);
-    return cudaGetLastError();
+    return launch_k(apply_kernel, dim3(grid), dim3(256), st, 1, A0.S, A0.R, cj, A0.H, A0.W, A0.lb,
+                    nbj, A0.active);
 }
 
 template <int KIND, int GT, int RPT>
-static void launch_warp(const PhaseArgs& A, int nact, cudaStream_t st) {
+static cudaError_t launch_warp(const PhaseArgs& A, int nact, cudaStream_t st) {
     constexpr int GPC = 128 / GT;
     SearchParams sp{A.alpha, A.G, A.K};
-    phase_warp_kernel<KIND, GT, RPT><<<(nact + GPC - 1) / GPC, 128, 0, st>>>(
-        A.S, A.R, A.f, A.H, A.W, sp, A.lb, A.ncolors, A.colour, A.c_out, A.active);
+    return launch_k(phase_warp_kernel<KIND, GT, RPT>, dim3((nact + GPC - 1) / GPC), dim3(128), st,
+                    1, A.S, A.R, A.f, A.H, A.W, sp, A.lb, A.ncolors, A.colour, A.c_out, A.active);
 }
 
 template <int KIND, int CT, int Q, int RPT>
-static void launch_cluster(const PhaseArgs& A, int nact, cudaStream_t st) {
+static cudaError_t launch_cluster(const PhaseArgs& A, int nact, cudaStream_t st) {
     SearchParams sp{A.alpha, A.G, A.K};
-    phase_cluster_kernel<KIND, CT, Q, RPT><<<nact * Q, CT, 0, st>>>(
-        A.S, A.R, A.f, A.H, A.W, sp, A.lb, A.ncolors, A.colour, A.c_out, A.active);
+    return launch_k(phase_cluster_kernel<KIND, CT, Q, RPT>, dim3(nact * Q), dim3(CT), st, 1, A.S,
+                    A.R, A.f, A.H, A.W, sp, A.lb, A.ncolors, A.colour, A.c_out, A.active);
 }
 
 template <int KIND>
@@ -488,20 +542,19 @@ static cudaError_t launch_blocks_kind(const PhaseArgs& A, cudaStream_t st) {
     const int nact = A.ncolors == 2 ? nbi * ((nbj + 1) / 2) : ((nbi + 1) / 2) * ((nbj + 1) / 2);
     // ring of a full block: 8b pixels = Q * CT * RPT slots
     switch (A.lb) {
-        case 1: launch_warp<KIND, CM_B2_GT, 16 / CM_B2_GT>(A, nact, st); break;
-        case 2: launch_warp<KIND, CM_B4_GT, 32 / CM_B4_GT>(A, nact, st); break;
-        case 3: launch_warp<KIND, 32, 2>(A, nact, st); break;
-        case 4: launch_cluster<KIND, 128, 1, 1>(A, nact, st); break;
-        case 5: launch_cluster<KIND, 256, 1, 1>(A, nact, st); break;
-        case 6: launch_cluster<KIND, 256, 2, 1>(A, nact, st); break;
-        case 7: launch_cluster<KIND, 256, 4, 1>(A, nact, st); break;
-        case 8: launch_cluster<KIND, 256, 8, 1>(A, nact, st); break;
-        case 9: launch_cluster<KIND, 512, 8, 1>(A, nact, st); break;
-        case 10: launch_cluster<KIND, 1024, 8, 1>(A, nact, st); break;
-        case 11: launch_cluster<KIND, 1024, 8, 2>(A, nact, st); break;
+        case 1: return launch_warp<KIND, CM_B2_GT, 16 / CM_B2_GT>(A, nact, st);
+        case 2: return launch_warp<KIND, CM_B4_GT, 32 / CM_B4_GT>(A, nact, st);
+        case 3: return launch_warp<KIND, 32, 2>(A, nact, st);
+        case 4: return launch_cluster<KIND, 128, 1, 1>(A, nact, st);
+        case 5: return launch_cluster<KIND, 256, 1, 1>(A, nact, st);
+        case 6: return launch_cluster<KIND, 256, 2, 1>(A, nact, st);
+        case 7: return launch_cluster<KIND, 256, 4, 1>(A, nact, st);
+        case 8: return launch_cluster<KIND, 256, 8, 1>(A, nact, st);
+        case 9: return launch_cluster<KIND, 512, 8, 1>(A, nact, st);
+        case 10: return launch_cluster<KIND, 1024, 8, 1>(A, nact, st);
+        case 11: return launch_cluster<KIND, 1024, 8, 2>(A, nact, st);
         default: return cudaErrorInvalidValue;
     }
-    return cudaGetLastError();
 }
 
 cudaError_t launch_phase_blocks(const PhaseArgs& A, cudaStream_t st) {

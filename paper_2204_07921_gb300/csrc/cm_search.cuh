@@ -15,8 +15,10 @@ namespace cm {
 
 struct SearchParams {
     float alpha;
-    int G;   // grid points (odd)
-    int K;   // golden-section evaluations
+    int G;          // grid points (odd)
+    int K;          // golden-section evaluations
+    int spec = 1;   // block_search_rounds: speculate the first golden pair
+    int dmax = 4;   // block_search_rounds: golden steps per round (1..4)
 };
 
 // ring(c) returns the group-uniform sum over the block's ring.  The
@@ -281,14 +283,7 @@ __device__ __forceinline__ float block_search_batched(RingV&& ringv, const Searc
     return best.c;
 }
 
-// The batched search with the golden section advanced LA = 3 steps per
-// reduction.  From a state whose next comparison is known the next point is
-// fixed; the point after it depends on one unknown comparison (2 choices),
-// the one after that on two (4 choices): 7 points cover every path of 3
-// steps.  Only the points on the path actually taken are considered, and
-// each is computed by the same operations as in block_search, so the
-// selected c is identical; the extra evaluations trade idle threads for
-// fewer barriers on levels with few blocks.
+// Golden-section state of the round-based search below.
 struct GoldenState {
     float lo, hi, x1, x2, E1, E2;
 };
@@ -318,117 +313,147 @@ __device__ __forceinline__ void golden_put(GoldenState& st, bool left, float x, 
     }
 }
 
-template <int MB, class RingV>
-__device__ __forceinline__ float block_search_lookahead(RingV&& ringv, const SearchParams& p,
-                                                        float s, float S1) {
-    static_assert(MB >= 7, "a depth-3 lookahead needs 7 candidates per batch");
+// ---------------------------------------------------------------------------
+// Search in rounds, for groups in which every warp holds the same search state
+// (one CTA or one cluster per block, all threads taking part).  A round
+// evaluates up to 16 candidates with one reduction: lane j of each warp
+// generates candidate j as `mine`, and round(mine, m) returns in lane l the
+// ring sum of candidate l / 2.
+//   round 1: c = 0 and c_fid;
+//   round 2: the grid points other than c_fid and, when they fit, the first
+//            golden pair of every grid point that may win (else the grid in
+//            chunks of 16 and the pair in a round of its own);
+//   then golden rounds of up to dmax <= 4 steps, which evaluate the
+//   2^dmax - 1 points of every outcome path of the next dmax comparisons.
+// Only points on the path taken are considered, each computed by the formula
+// of block_search, so the candidates and the decisions are those of
+// block_search.  With speculation and dmax = 4 the reductions of G = 5,
+// K = 6 drop from 7 (one per step) to 3 at 31 instead of 12 evaluations; the
+// kernel picks the trade per level.
+
+__device__ __forceinline__ float grid_t(int i, int G) {
+    return (2.0f * (float)i) / (float)(G - 1) - 1.0f;
+}
+
+__device__ __forceinline__ float grid_point(float c_fid, float rho, int i, int G) {
+    return __fmaf_rn(rho, grid_t(i, G), c_fid);
+}
+
+// Point of node n (heap order: node 1 is the next point, nodes 2n / 2n + 1
+// follow it when the comparison after it goes left / right) of the golden
+// tree grown from st, whose next comparison is known.
+__device__ __forceinline__ float golden_tree_point(GoldenState st, int n) {
+    const int depth = 31 - __clz(n);
+    bool left = st.E1 < st.E2;
+    float x = golden_take(st, left);
+    for (int q = depth - 1; q >= 0; --q) {
+        golden_put(st, left, x, 0.0f);
+        left = ((n >> q) & 1) == 0;
+        x = golden_take(st, left);
+    }
+    return x;
+}
+
+template <class RoundFn>
+__device__ __forceinline__ float block_search_rounds(RoundFn&& round, const SearchParams& p,
+                                                     float s, float S1) {
+    constexpr unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
     const float c_fid = -S1 / s;
     const float half_as = 0.5f * p.alpha * s;
     auto energy = [&](float c, float rk) {
-        float t = c - c_fid;
+        const float t = c - c_fid;
         return fmaf(half_as * t, t, rk);
     };
-    float cs[MB], rk[MB];
-#pragma unroll
-    for (int j = 0; j < MB; ++j) cs[j] = 0.0f;
-    cs[1] = c_fid;
-    ringv(cs, 2, rk);
+    const int mid = (p.G - 1) / 2;
+    const int ng = p.G - 1;                    // grid points other than c_fid
+    const bool spec = p.spec && ng + 2 * p.G <= 16;
+    // round 1: c = 0, c_fid
+    float mine = lane == 1 ? c_fid : 0.0f;
+    float tot = round(mine, 2);
     Best best;
     best.c = 0.0f;
-    best.E = energy(0.0f, rk[0]);
-    const float Rk = rk[1];
+    best.E = energy(0.0f, __shfl_sync(FULL, tot, 0));
+    const float Rk = __shfl_sync(FULL, tot, 2);
     const float rho = sqrtf(2.0f * Rk / (p.alpha * s));
-    const int mid = (p.G - 1) / 2;
+    const float D = 2.0f * rho / (float)(p.G - 1);
+    // grid (+ speculative first pairs)
     float gbest = c_fid, Egbest = INFINITY;
-    for (int i0 = 0; i0 < p.G; i0 += MB) {
-        const int m = min(MB, p.G - i0);
-#pragma unroll
-        for (int j = 0; j < MB; ++j) {
-            float t = (2.0f * (float)(i0 + j)) / (float)(p.G - 1) - 1.0f;
-            cs[j] = c_fid + rho * t;
+    int gwin = mid;
+    int mg = 0;
+    for (int g0 = 0; g0 < ng; g0 += 16) {
+        mg = min(ng - g0, 16);
+        const int m = mg + (spec ? 2 * p.G : 0);
+        mine = 0.0f;
+        if (lane < mg) {
+            const int gi = g0 + lane + ((g0 + lane >= mid) ? 1 : 0);
+            mine = grid_point(c_fid, rho, gi, p.G);
+        } else if (spec && lane < m) {
+            const int q = lane - mg;
+            const float g = grid_point(c_fid, rho, q >> 1, p.G);
+            const float lo = g - D, hi = g + D;
+            mine = (q & 1) ? lo + GOLDEN * (hi - lo) : hi - GOLDEN * (hi - lo);
         }
-        ringv(cs, m, rk);
-#pragma unroll
-        for (int j = 0; j < MB; ++j)
-            if (j < m) {
-                float E = energy(cs[j], (i0 + j == mid) ? Rk : rk[j]);
-                consider(best, cs[j], E);
-                if (E < Egbest) {
-                    Egbest = E;
-                    gbest = cs[j];
+        tot = round(mine, m);
+        for (int j = 0; j < mg; ++j) {
+            const int k = g0 + j;
+            if (k == mid) {   // c_fid, the middle grid point, in index order
+                const float cm = grid_point(c_fid, rho, mid, p.G);
+                const float Em = energy(cm, Rk);
+                consider(best, cm, Em);
+                if (Em < Egbest) {
+                    Egbest = Em;
+                    gbest = cm;
+                    gwin = mid;
                 }
             }
+            const float c = __shfl_sync(FULL, mine, j);
+            const float E = energy(c, __shfl_sync(FULL, tot, 2 * j));
+            consider(best, c, E);
+            if (E < Egbest) {
+                Egbest = E;
+                gbest = c;
+                gwin = k + (k >= mid ? 1 : 0);
+            }
+        }
     }
-    const float D = 2.0f * rho / (float)(p.G - 1);
+    // first golden pair
     GoldenState st;
     st.lo = gbest - D;
     st.hi = gbest + D;
-    st.x1 = st.hi - GOLDEN * (st.hi - st.lo);
-    st.x2 = st.lo + GOLDEN * (st.hi - st.lo);
-    cs[0] = st.x1;
-    cs[1] = st.x2;
-    ringv(cs, 2, rk);
-    st.E1 = energy(st.x1, rk[0]);
+    if (spec) {
+        const int i1 = mg + 2 * gwin;
+        st.x1 = __shfl_sync(FULL, mine, i1);
+        st.x2 = __shfl_sync(FULL, mine, i1 + 1);
+        st.E1 = energy(st.x1, __shfl_sync(FULL, tot, 2 * i1));
+        st.E2 = energy(st.x2, __shfl_sync(FULL, tot, 2 * i1 + 2));
+    } else {
+        st.x1 = st.hi - GOLDEN * (st.hi - st.lo);
+        st.x2 = st.lo + GOLDEN * (st.hi - st.lo);
+        mine = lane == 0 ? st.x1 : (lane == 1 ? st.x2 : 0.0f);
+        tot = round(mine, 2);
+        st.E1 = energy(st.x1, __shfl_sync(FULL, tot, 0));
+        st.E2 = energy(st.x2, __shfl_sync(FULL, tot, 2));
+    }
     consider(best, st.x1, st.E1);
-    st.E2 = energy(st.x2, rk[1]);
     consider(best, st.x2, st.E2);
-    int steps = p.K - 2;
-    while (steps > 0) {
-        const int la = steps >= 3 ? 3 : steps;
-        // step 1 (decision known)
-        const bool l0 = st.E1 < st.E2;
-        GoldenState s0 = st;
-        const float p0 = golden_take(s0, l0);
-        cs[0] = p0;
-        int m = 1;
-        // step 2 after each outcome o1 of the next comparison (0 = left)
-        float p1[2], p2[4];
-        GoldenState s1[2];
-#pragma unroll
-        for (int o1 = 0; o1 < 2; ++o1) {
-            s1[o1] = s0;
-            golden_put(s1[o1], l0, p0, 0.0f);
-            p1[o1] = golden_take(s1[o1], o1 == 0);
-#pragma unroll
-            for (int o2 = 0; o2 < 2; ++o2) {
-                GoldenState s2 = s1[o1];
-                golden_put(s2, o1 == 0, p1[o1], 0.0f);
-                p2[2 * o1 + o2] = golden_take(s2, o2 == 0);
-            }
+    // golden rounds
+    for (int steps = p.K - 2; steps > 0;) {
+        const int d = min(steps, p.dmax);
+        const int m = (1 << d) - 1;
+        mine = lane < m ? golden_tree_point(st, lane + 1) : 0.0f;
+        tot = round(mine, m);
+        int n = 1;
+        for (int q = 0; q < d; ++q) {
+            const bool left = st.E1 < st.E2;
+            golden_take(st, left);
+            const float x = __shfl_sync(FULL, mine, n - 1);
+            const float E = energy(x, __shfl_sync(FULL, tot, 2 * (n - 1)));
+            consider(best, x, E);
+            golden_put(st, left, x, E);
+            n = 2 * n + (st.E1 < st.E2 ? 0 : 1);
         }
-        if (la >= 2) {
-            cs[1] = p1[0];
-            cs[2] = p1[1];
-            m = 3;
-        }
-        if (la >= 3) {
-#pragma unroll
-            for (int q = 0; q < 4; ++q) cs[3 + q] = p2[q];
-            m = 7;
-        }
-        ringv(cs, m, rk);
-        // walk the path actually taken
-        const float E0 = energy(p0, rk[0]);
-        consider(best, p0, E0);
-        st = s0;
-        golden_put(st, l0, p0, E0);
-        if (la >= 2) {
-            const bool l1 = st.E1 < st.E2;
-            const int o1 = l1 ? 0 : 1;
-            const float q1 = golden_take(st, l1);
-            const float E1v = energy(q1, rk[1 + o1]);
-            consider(best, q1, E1v);
-            golden_put(st, l1, q1, E1v);
-            if (la >= 3) {
-                const bool l2 = st.E1 < st.E2;
-                const int o2 = l2 ? 0 : 1;
-                const float q2 = golden_take(st, l2);
-                const float E2v = energy(q2, rk[3 + 2 * o1 + o2]);
-                consider(best, q2, E2v);
-                golden_put(st, l2, q2, E2v);
-            }
-        }
-        steps -= la;
+        steps -= d;
     }
     return best.c;
 }

@@ -208,8 +208,11 @@ def test_solve_equals_level_sequence_and_is_deterministic(shape):
 
 @pytest.mark.parametrize("case", [((512, 512), cm.GAUSS, 15.0, (64, 128, 256)),
                                   ((1024, 1024), cm.MEAN, 20.0, (64, 512)),
-                                  ((300, 260), cm.MEAN, 20.0, (64, 128))],
-                         ids=["512-gauss", "1024-mean", "300x260-mean"])
+                                  ((300, 260), cm.MEAN, 20.0, (64, 128)),
+                                  ((2600, 300), cm.MEAN, 20.0, (1024, 2048)),
+                                  ((2600, 300), cm.GAUSS, 15.0, (1024, 2048))],
+                         ids=["512-gauss", "1024-mean", "300x260-mean", "2600x300-mean",
+                              "2600x300-gauss"])
 def test_level_parity_coarse(case):
     """Coarse levels through cm_level (tile sums, deferred apply): R = S + c
     on every block, and each colour's shifts match the oracle solved from the
