@@ -30,6 +30,14 @@
 #ifndef CM_B4_GT
 #define CM_B4_GT 16
 #endif
+// b = 2: rotation-specialised kernel (1) or the generic warp groups (0), and
+// its minimum CTAs per SM (register cap).
+#ifndef CM_B2_FAST
+#define CM_B2_FAST 1
+#endif
+#ifndef CM_B2_MINB
+#define CM_B2_MINB 4
+#endif
 
 namespace cm {
 
@@ -46,18 +54,20 @@ __device__ __forceinline__ void for_block_pixels(int first, int stride, int r0, 
     }
 }
 
-template <int KIND, int GT, int RPT>
-__global__ void __launch_bounds__(128) phase_warp_kernel(
-    const float* __restrict__ S, float* __restrict__ R, const float* __restrict__ f, int H, int W,
-    SearchParams sp, int lb, int ncol, int k, float* __restrict__ c_out,
-    const int* __restrict__ active) {
+// One block per group of GT lanes of a warp (every lane of the warp runs
+// this with its group's active-block number a, valid or not).  LIGHT keeps
+// the ring windows and rebuilds the affine coefficients per candidate (fewer
+// registers, more arithmetic).
+template <int KIND, int GT, int RPT, bool LIGHT = false>
+__device__ __forceinline__ void warp_group_block(const float* __restrict__ S,
+                                                 float* __restrict__ R,
+                                                 const float* __restrict__ f, int H, int W,
+                                                 const SearchParams& sp, int lb, int ncol, int k,
+                                                 float* __restrict__ c_out, int a) {
     static_assert(GT == 4 || GT == 8 || GT == 16 || GT == 32, "warp groups only");
-    if (active && *active == 0) return;
-    constexpr int GPC = 128 / GT;
+    const int lane = threadIdx.x % GT;
     const int b = 1 << lb;
     const int nbi = (H + b - 1) >> lb, nbj = (W + b - 1) >> lb;
-    const int gid = threadIdx.x / GT, lane = threadIdx.x % GT;
-    const int a = blockIdx.x * GPC + gid;
     int bi, bj;
     const bool blk_on = active_block(a, nbi, nbj, ncol, k, bi, bj);
     // Groups without a block still take part in the shuffles of their warp.
@@ -70,15 +80,22 @@ __global__ void __launch_bounds__(128) phase_warp_kernel(
                          [&](size_t p) { s1 += S[p] - f[p]; });
 #pragma unroll
     for (int off = GT / 2; off > 0; off >>= 1) s1 += __shfl_xor_sync(0xffffffffu, s1, off, GT);
-    AffPix px[RPT];
+    constexpr int NPX = LIGHT ? 1 : RPT;
+    constexpr int NWIN = LIGHT ? RPT : 1;
+    AffPix px[NPX];
+    float win[NWIN][9];
+    unsigned msk[RPT];
     bool has[RPT];
 #pragma unroll
     for (int t = 0; t < RPT; ++t) {
         float w[9];
-        unsigned mask = 0;
-        has[t] = blk_on && ring_slot(lane + t * GT, r0, r1, c0, c1, H, W, S, R, lb, ncol, k, w, mask);
-        if (has[t]) {
-            px[t] = aff_pix(w, mask);
+        msk[t] = 0;
+        has[t] = blk_on && ring_slot(lane + t * GT, r0, r1, c0, c1, H, W, S, R, lb, ncol, k, w, msk[t]);
+        if constexpr (LIGHT) {
+#pragma unroll
+            for (int i = 0; i < 9; ++i) win[t][i] = has[t] ? w[i] : 0.0f;
+        } else if (has[t]) {
+            px[t] = aff_pix(w, msk[t]);
         } else {
 #pragma unroll
             for (int d = 0; d < 4; ++d) px[t].d[d] = AffDir{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
@@ -87,17 +104,239 @@ __global__ void __launch_bounds__(128) phase_warp_kernel(
     auto ring = [&](float c) {
         float v = 0.0f;
 #pragma unroll
-        for (int t = 0; t < RPT; ++t) v += has[t] ? aff_abs_curv<KIND>(px[t], c) : 0.0f;
+        for (int t = 0; t < RPT; ++t) {
+            if constexpr (LIGHT) {
+                if (has[t]) v += aff_abs_curv<KIND>(aff_pix(win[t], msk[t]), c);
+            } else {
+                v += has[t] ? aff_abs_curv<KIND>(px[t], c) : 0.0f;
+            }
+        }
 #pragma unroll
         for (int off = GT / 2; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off, GT);
         return v;
     };
     const float s = blk_on ? (float)(bh * bw) : 1.0f;
-    const float cbest = block_search(ring, sp, s, blk_on ? s1 : 0.0f, false, 0.0f);
+    float cbest;
+    if constexpr (LIGHT)
+        cbest = block_search_1site(ring, sp, s, blk_on ? s1 : 0.0f, false, 0.0f);
+    else
+        cbest = block_search(ring, sp, s, blk_on ? s1 : 0.0f, false, 0.0f);
     if (!blk_on) return;
     for_block_pixels(lane, GT, r0, c0, bh, bw, lb, bw == b, W,
                      [&](size_t p) { R[p] = S[p] + cbest; });
     if (c_out && lane == 0) c_out[(size_t)bi * nbj + bj] = cbest;
+}
+
+template <int KIND, int GT, int RPT>
+__global__ void __launch_bounds__(128) phase_warp_kernel(
+    const float* __restrict__ S, float* __restrict__ R, const float* __restrict__ f, int H, int W,
+    SearchParams sp, int lb, int ncol, int k, float* __restrict__ c_out,
+    const int* __restrict__ active) {
+    if (active && *active == 0) return;
+    constexpr int GPC = 128 / GT;
+    warp_group_block<KIND, GT, RPT>(S, R, f, H, W, sp, lb, ncol, k, c_out,
+                                    blockIdx.x * GPC + threadIdx.x / GT);
+}
+
+// ---------------------------------------------------------------------------
+// b = 2, interior blocks: four lanes per block, lane q taking the quarter of
+// the ring that a rotation by q x 90 degrees about the block centre maps from
+// quarter 0 = {outer corner (-1, -1), outer sides (-1, 0) and (-1, 1), block
+// pixel (0, 0)} (offsets from the block's top-left pixel).  Each lane reads
+// its windows rotated back into the frame of quarter 0, so every lane runs
+// the same code with the window entries that lie in the block known at
+// compile time.  The eight-plane curvature is invariant under the rotation
+// (the four line directions are permuted, a line's end points may swap, which
+// negates Dq exactly and leaves every other term as it is), so each direction
+// value is the one the generic evaluation computes.  Terms that do not depend
+// on c are computed once per block instead of once per candidate: 22 instead
+// of 32 rsqrt per lane and candidate.
+
+// Direction T of a ring pixel whose window entries in the block are MASK.
+template <unsigned MASK, int T>
+struct SpecDir {
+    static constexpr int X = line_x(T), Y = line_y(T), Z1 = line_z1(T), Z2 = line_z2(T);
+    static constexpr int mx = (MASK >> X) & 1, my = (MASK >> Y) & 1, mo = (MASK >> 4) & 1;
+    static constexpr int mz1 = (MASK >> Z1) & 1, mz2 = (MASK >> Z2) & 1;
+    static constexpr float DQ1 = 0.5f * (float)(my - mx);
+    static constexpr float DL1 = line_two_h(T) * (0.5f * (float)(mx + my) - (float)mo);
+    static constexpr float E11 = (float)(mx + my - 2 * mz1);
+    static constexpr float E21 = (float)(mx + my - 2 * mz2);
+    static constexpr bool LINE = DQ1 != 0.0f;   // Dq (so ds) varies with c
+    static constexpr bool CONST = !LINE && DL1 == 0.0f && E11 == 0.0f && E21 == 0.0f;
+    // LINE: dq0, dl0, e10, e20.  Otherwise: fds = 4 ds^2, ds4, dl0, and per
+    // plane its constant rsqrt term or e_i0.  CONST: kb.
+    float a0, a1, a2, a3, a4;
+
+    __device__ __forceinline__ void init(const float w[9]) {
+        const float two_h = line_two_h(T);
+        const float dq0 = 0.5f * (w[Y] - w[X]);
+        const float dl0 = two_h * fmaf(0.5f, w[X] + w[Y], -w[4]);
+        const float Sxy = w[X] + w[Y];
+        const float e10 = fmaf(-2.0f, w[Z1], Sxy);
+        const float e20 = fmaf(-2.0f, w[Z2], Sxy);
+        if constexpr (LINE) {
+            a0 = dq0;
+            a1 = dl0;
+            a2 = e10;
+            a3 = e20;
+        } else {
+            const float ds2 = fmaf(dq0, dq0, line_h2(T));
+            const float fds = 4.0f * ds2;
+            const float ds4 = ds2 * ds2;
+            const float t1 = E11 == 0.0f ? rsqrtf(fmaf(e10, e10, fds) * ds4) : e10;
+            const float t2 = E21 == 0.0f ? rsqrtf(fmaf(e20, e20, fds) * ds4) : e20;
+            if constexpr (CONST) {
+                a0 = dl0 * (t1 + t2);
+            } else {
+                a0 = fds;
+                a1 = ds4;
+                a2 = dl0;
+                a3 = t1;
+                a4 = t2;
+            }
+        }
+    }
+
+    __device__ __forceinline__ float eval(float c) const {
+        if constexpr (CONST) {
+            return a0;
+        } else if constexpr (LINE) {
+            const float Dq = fmaf(DQ1, c, a0);
+            const float ds2 = fmaf(Dq, Dq, line_h2(T));
+            const float fds = 4.0f * ds2;
+            const float ds4 = ds2 * ds2;
+            const float e1 = E11 == 0.0f ? a2 : fmaf(E11, c, a2);
+            const float e2 = E21 == 0.0f ? a3 : fmaf(E21, c, a3);
+            const float r = rsqrtf(fmaf(e1, e1, fds) * ds4) + rsqrtf(fmaf(e2, e2, fds) * ds4);
+            return (DL1 == 0.0f ? a1 : fmaf(DL1, c, a1)) * r;
+        } else {
+            float r1, r2;
+            if constexpr (E11 == 0.0f) {
+                r1 = a3;
+            } else {
+                const float e = fmaf(E11, c, a3);
+                r1 = rsqrtf(fmaf(e, e, a0) * a1);
+            }
+            if constexpr (E21 == 0.0f) {
+                r2 = a4;
+            } else {
+                const float e = fmaf(E21, c, a4);
+                r2 = rsqrtf(fmaf(e, e, a0) * a1);
+            }
+            return (DL1 == 0.0f ? a2 : fmaf(DL1, c, a2)) * (r1 + r2);
+        }
+    }
+};
+
+template <unsigned MASK>
+struct SpecPix {
+    SpecDir<MASK, 0> d0;
+    SpecDir<MASK, 1> d1;
+    SpecDir<MASK, 2> d2;
+    SpecDir<MASK, 3> d3;
+    __device__ __forceinline__ void init(const float w[9]) {
+        d0.init(w);
+        d1.init(w);
+        d2.init(w);
+        d3.init(w);
+    }
+    template <int KIND>
+    __device__ __forceinline__ float abs_curv(float c) const {
+        const float k0 = d0.eval(c), k1 = d1.eval(c), k2 = d2.eval(c), k3 = d3.eval(c);
+        const float kmin = fminf(fminf(k0, k1), fminf(k2, k3));
+        const float kmax = fmaxf(fmaxf(k0, k1), fmaxf(k2, k3));
+        return KIND == KIND_MEAN ? 0.5f * fabsf(kmin + kmax) : fabsf(kmin * kmax);
+    }
+};
+
+// Window entries (row-major 3 x 3, index 3a + b) in the block, quarter 0.
+constexpr unsigned B2_M0 = 1u << 8;                                // corner (-1, -1)
+constexpr unsigned B2_M1 = (1u << 7) | (1u << 8);                  // side (-1, 0)
+constexpr unsigned B2_M2 = (1u << 6) | (1u << 7);                  // side (-1, 1)
+constexpr unsigned B2_M3 = (1u << 4) | (1u << 5) | (1u << 7) | (1u << 8);   // pixel (0, 0)
+
+template <int KIND>
+__global__ void __launch_bounds__(128, CM_B2_MINB) phase_b2_kernel(
+    const float* __restrict__ S, float* __restrict__ R, const float* __restrict__ f, int H, int W,
+    SearchParams sp, int ncol, int k, float* __restrict__ c_out,
+    const int* __restrict__ active) {
+    if (active && *active == 0) return;
+    const int a = blockIdx.x * 32 + threadIdx.x / 4;
+    const int q = threadIdx.x & 3;
+    const int nbi = (H + 1) >> 1, nbj = (W + 1) >> 1;
+    int bi, bj;
+    const bool blk_on = active_block(a, nbi, nbj, ncol, k, bi, bj);
+    const int r0 = bi << 1, c0 = bj << 1;
+    const bool interior = r0 >= 2 && c0 >= 2 && r0 + 3 < H && c0 + 3 < W;
+    if (!__all_sync(0xffffffffu, !blk_on || interior)) {
+        // a warp with a border block runs the generic four-lane search
+        warp_group_block<KIND, 4, 4, true>(S, R, f, H, W, sp, 1, ncol, k, c_out, a);
+        return;
+    }
+    // Frame of quarter 0 -> image: offset (dr, dc) from (r0, c0) rotated q
+    // quarter turns about the block centre.
+    auto img = [&](int dr, int dc, int& r, int& c) {
+        int rr = dr, cc = dc;
+        if (q == 1) { rr = dc; cc = 1 - dr; }
+        else if (q == 2) { rr = 1 - dr; cc = 1 - dc; }
+        else if (q == 3) { rr = 1 - dc; cc = dr; }
+        r = r0 + rr;
+        c = c0 + cc;
+    };
+    // v[dr + 2][dc + 2]: rows -2 .. 1, columns -2 .. 2 of the frame (row 1
+    // only columns -1 .. 1)
+    float v[4][5];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 5; ++j) {
+            v[i][j] = 0.0f;
+            if (blk_on && (i < 3 || (j >= 1 && j <= 3))) {
+                int r, c;
+                img(i - 2, j - 2, r, c);
+                v[i][j] = phase_read(S, R, r, c, W, 1, ncol, k);
+            }
+        }
+    int pr, pc;
+    img(0, 0, pr, pc);
+    const size_t p = (size_t)pr * W + pc;
+    float s1 = blk_on ? v[2][2] - f[p] : 0.0f;
+    s1 += __shfl_xor_sync(0xffffffffu, s1, 1);
+    s1 += __shfl_xor_sync(0xffffffffu, s1, 2);
+    SpecPix<B2_M0> P0;
+    SpecPix<B2_M1> P1;
+    SpecPix<B2_M2> P2;
+    SpecPix<B2_M3> P3;
+    {
+        float w[9];
+        auto win = [&](int i0, int j0) {
+#pragma unroll
+            for (int x = 0; x < 3; ++x)
+#pragma unroll
+                for (int y = 0; y < 3; ++y) w[3 * x + y] = v[i0 + x][j0 + y];
+        };
+        win(0, 0);
+        P0.init(w);
+        win(0, 1);
+        P1.init(w);
+        win(0, 2);
+        P2.init(w);
+        win(1, 1);
+        P3.init(w);
+    }
+    auto ring = [&](float c) {
+        float t = P0.template abs_curv<KIND>(c) + P1.template abs_curv<KIND>(c) +
+                  P2.template abs_curv<KIND>(c) + P3.template abs_curv<KIND>(c);
+        t = blk_on ? t : 0.0f;
+        t += __shfl_xor_sync(0xffffffffu, t, 1);
+        t += __shfl_xor_sync(0xffffffffu, t, 2);
+        return t;
+    };
+    const float cbest = block_search_1site(ring, sp, blk_on ? 4.0f : 1.0f, s1, false, 0.0f);
+    if (!blk_on) return;
+    R[p] = v[2][2] + cbest;
+    if (c_out && q == 0) c_out[(size_t)bi * nbj + bj] = cbest;
 }
 
 template <int KIND, int CT, int Q, int RPT>
@@ -542,7 +781,12 @@ static cudaError_t launch_blocks_kind(const PhaseArgs& A, cudaStream_t st) {
     const int nact = A.ncolors == 2 ? nbi * ((nbj + 1) / 2) : ((nbi + 1) / 2) * ((nbj + 1) / 2);
     // ring of a full block: 8b pixels = Q * CT * RPT slots
     switch (A.lb) {
-        case 1: return launch_warp<KIND, CM_B2_GT, 16 / CM_B2_GT>(A, nact, st);
+        case 1:
+            if (CM_B2_FAST)
+                return launch_k(phase_b2_kernel<KIND>, dim3((nact + 31) / 32), dim3(128), st, 1,
+                                A.S, A.R, A.f, A.H, A.W, SearchParams{A.alpha, A.G, A.K},
+                                A.ncolors, A.colour, A.c_out, A.active);
+            return launch_warp<KIND, CM_B2_GT, 16 / CM_B2_GT>(A, nact, st);
         case 2: return launch_warp<KIND, CM_B4_GT, 32 / CM_B4_GT>(A, nact, st);
         case 3: return launch_warp<KIND, 32, 2>(A, nact, st);
         case 4: return launch_cluster<KIND, 128, 1, 1>(A, nact, st);
