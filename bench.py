@@ -14,6 +14,7 @@ Prints one JSON line (see --help).
 from __future__ import annotations
 
 import argparse
+import datetime
 import json
 import math
 import os
@@ -63,9 +64,11 @@ def parse():
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    """nvidia-smi clocks and throttle reasons, sampled every 20 ms with
+    timestamps; summary() keeps the samples taken inside the marked window
+    (mark_start / mark_end around the timed region)."""
 
-    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
@@ -73,6 +76,7 @@ class ClockSampler:
         self.index = index
         self.proc = None
         self.path = None
+        self.t0 = self.t1 = None
 
     def __enter__(self):
         try:
@@ -80,14 +84,24 @@ class ClockSampler:
             os.close(fd)
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200", "-f", self.path],
+                 "--format=csv,noheader,nounits", "-lms", "20", "-f", self.path],
                 stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+            t_end = time.time() + 5.0          # wait for the first sample
+            while time.time() < t_end and os.path.getsize(self.path) == 0:
+                time.sleep(0.02)
         except Exception:
             self.proc = None
         return self
 
+    def mark_start(self):
+        self.t0 = time.time()
+
+    def mark_end(self):
+        self.t1 = time.time()
+
     def __exit__(self, *exc):
         if self.proc is not None:
+            time.sleep(0.05)
             self.proc.terminate()
             try:
                 self.proc.wait(timeout=5)
@@ -100,20 +114,28 @@ class ClockSampler:
         rows = []
         for line in open(self.path):
             parts = [x.strip() for x in line.split(",")]
-            if len(parts) < 9:
+            if len(parts) < 10:
                 continue
             try:
-                rows.append((float(parts[1]), float(parts[2]), float(parts[3]), parts[5:9]))
+                ts = datetime.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                rows.append((ts, float(parts[2]), float(parts[3]), float(parts[4]), parts[6:10]))
             except ValueError:
                 continue
         os.unlink(self.path)
-        if not rows:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        if self.t0 is not None and self.t1 is not None:
+            inside = [r for r in rows if self.t0 - 0.02 <= r[0] <= self.t1 + 0.02]
+        else:
+            inside = rows
+        if not inside:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples in the window"],
+                    "samples": 0}
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[i] for r in rows for i, v in enumerate(r[3]) if v == "Active"})
-        load = [r[0] for r in rows if r[2] > 200.0] or [r[0] for r in rows]
-        return {"sm_mhz": statistics.median(load), "sm_max_mhz": max(r[1] for r in rows),
-                "reasons": reasons, "samples": len(rows)}
+        reasons = sorted({names[i] for r in inside for i, v in enumerate(r[4]) if v == "Active"})
+        return {"sm_mhz": statistics.median(r[1] for r in inside),
+                "sm_max_mhz": max(r[2] for r in inside), "reasons": reasons,
+                "samples": len(inside), "window_s": round(self.t1 - self.t0, 3)
+                if self.t0 is not None and self.t1 is not None else None,
+                "power_w_median": statistics.median(r[3] for r in inside)}
 
 
 def dist_setup(args):
@@ -343,7 +365,9 @@ def main():
         return t / args.steps, sts
 
     with ClockSampler(local) as clk:
+        clk.mark_start()
         sec_warm, st_warm = timed_steps(warm_step)
+        clk.mark_end()
         psnr_warm = synth.psnr(u.cpu().numpy(), img.clean)
         sec_plain, st_plain = timed_steps(plain_step)
         psnr_plain = synth.psnr(u.cpu().numpy(), img.clean)
@@ -415,11 +439,13 @@ def main():
                "per_cycle_s": per_cycle}
 
     # kernels per cycle: one per colour on levels below the coarse threshold
-    # (b < 64); tile sums + one per colour + apply on coarse levels; energy
+    # (b < 64); tile sums + one per colour + apply on coarse levels; energy;
+    # the device stopping test
     coarse = max(0, L - COARSE_LB)
-    kernels_per_cycle = opts.ncolors * (L - coarse) + coarse * (opts.ncolors + 2) + 1
-    # per warm step: 6 network kernels, 2 energy checks, then the solve
-    launches_per_solve = [8 + 1 + c * kernels_per_cycle for c in cycles]
+    kernels_per_cycle = opts.ncolors * (L - coarse) + coarse * (opts.ncolors + 2) + 2
+    # per warm step: 6 network kernels, 2 energy checks, then the solve graph
+    # (initial energy, state initialisation, the cycles)
+    launches_per_solve = [8 + 2 + c * kernels_per_cycle for c in cycles]
     line = {"metric": METRIC, "value": sec_per_solve, "unit": "s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec_per_solve * 1e3,
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32",

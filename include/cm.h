@@ -61,7 +61,9 @@ typedef struct {
     int grid_points;     /* G: odd, >= 3; points of the bracket grid of the block search */
     int golden_evals;    /* K: >= 2; golden-section evaluations of the block search */
     int paper_candidate; /* 1: also try the paper's one-step FBS estimate on the finest level */
-    int use_graph;       /* 1: capture one cycle in a CUDA graph and replay it */
+    int use_graph;       /* 1: cm_solve runs as one CUDA graph (device loop and
+                            stopping test); 0: one cycle per launch sequence,
+                            host stopping test (same results) */
     int max_trace;       /* entries of the energy trace kept in cm_stats (<= 4096) */
 } cm_options;
 
@@ -149,7 +151,12 @@ int cm_level(cm_ctx* ctx, const float* S, float* R, const float* f, int H, int W
  * cycles (exactly `cycles` when tol == 0).  levels = 0 selects
  * cm_auto_levels(H, W).  f, u0, u_out: device H x W; u_out may alias u0 but
  * not f.  stats (host, nullable).  Returns CM_NOT_CONVERGED if tol > 0 and the
- * cap was reached (u_out valid).  Synchronises `stream`. */
+ * cap was reached (u_out valid).  Synchronises `stream`.
+ * With use_graph the loop runs on the device: the solve is one CUDA graph
+ * (cached per configuration) whose conditional WHILE node repeats a cycle and
+ * a one-thread stopping-test kernel that sets the loop condition; the host
+ * reads the state back once.  Without it the host tests after every cycle;
+ * both give identical u, statistics and energy trace. */
 int cm_solve(cm_ctx* ctx, const float* f, int H, int W, float alpha, int kind, int levels,
              int cycles, double tol, const float* u0, float* u_out,
              const cm_options* opts /* host, nullable */, cm_stats* stats /* host, nullable */,

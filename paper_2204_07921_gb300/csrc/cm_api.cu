@@ -1,15 +1,18 @@
 // cm_api.cu -- C ABI and host runtime of libcm (declared in include/cm.h).
 //
 // The runtime owns a context's scratch (the second ping-pong image, energy
-// partials, a pinned readback slot) and a small cache of CUDA graphs, each
-// holding one full cycle (every phase of every level, then the FP64 energy).
-// The outer loop of Alg. 3 replays the graph and reads back 8 bytes per
-// cycle for the stopping test of Eq. (reerr).
+// partials, a pinned readback slot) and a cached CUDA graph per solve
+// configuration.  The graph holds the whole outer loop of Alg. 3: the initial
+// energy, then a conditional WHILE node whose body is one full cycle (every
+// phase of every level, the FP64 energy) followed by the stopping test of
+// Eq. (reerr) on the device, which sets the loop condition.  The host reads
+// the solve's state back once, after the loop.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
 #include <string>
 
 #include <vector>
@@ -25,6 +28,8 @@ struct GraphKey {
     const float* f;
     int H, W, kind, levels, ncolors, G, K, use_paper;
     float alpha;
+    double tol;
+    int cycles, trace_cap;
     bool operator==(const GraphKey& o) const { return memcmp(this, &o, sizeof(GraphKey)) == 0; }
 };
 
@@ -43,6 +48,12 @@ struct cm_ctx {
     double* E_dev = nullptr;
     double* E_pinned = nullptr;
     cudaStream_t cap_stream = nullptr;
+    cudaStream_t cap_stream2 = nullptr;   // captures the body of the solve loop
+    // single-image solve: device stopping state and energy trace, host mirrors
+    void* sstate = nullptr;
+    void* sstate_host = nullptr;
+    double* strace = nullptr;
+    double* strace_host = nullptr;
     // batched solve: arena, capture streams/events and the cached batch graph
     unsigned char* arena = nullptr;
     size_t arena_cap = 0;
@@ -54,7 +65,7 @@ struct cm_ctx {
         bool valid = false;
         GraphKey key;
         cudaGraphExec_t exec = nullptr;
-    } graphs[2];
+    } sgraph;
 };
 
 namespace {
@@ -77,11 +88,9 @@ int cuda_fail(cm_ctx* ctx, cudaError_t e, const char* where) {
 
 // Cached graphs hold scratch pointers: drop them before any reallocation.
 void drop_graphs(cm_ctx* ctx) {
-    for (auto& g : ctx->graphs) {
-        if (g.exec) cudaGraphExecDestroy(g.exec);
-        g.exec = nullptr;
-        g.valid = false;
-    }
+    if (ctx->sgraph.exec) cudaGraphExecDestroy(ctx->sgraph.exec);
+    ctx->sgraph.exec = nullptr;
+    ctx->sgraph.valid = false;
 }
 
 int ensure_partials(cm_ctx* ctx, int H, int W) {
@@ -120,6 +129,17 @@ int ensure_ubuf(cm_ctx* ctx, size_t n) {
     ctx->ubuf_cap = 0;
     CM_CUDA(cudaMalloc(&ctx->ubuf, n * sizeof(float)));
     ctx->ubuf_cap = n;
+    return CM_OK;
+}
+
+constexpr int TRACE_SLOTS = 4097;   // energy_trace of cm_stats
+
+int ensure_solve_state(cm_ctx* ctx) {
+    if (ctx->sstate) return CM_OK;
+    CM_CUDA(cudaMalloc(&ctx->sstate, cm::batch_state_bytes()));
+    CM_CUDA(cudaMallocHost(&ctx->sstate_host, cm::batch_state_bytes()));
+    CM_CUDA(cudaMalloc(&ctx->strace, TRACE_SLOTS * sizeof(double)));
+    CM_CUDA(cudaMallocHost(&ctx->strace_host, TRACE_SLOTS * sizeof(double)));
     return CM_OK;
 }
 
@@ -178,22 +198,97 @@ cudaError_t enqueue_level(float* tsums, float* cj, const float* S, float* R, con
     return cudaSuccess;
 }
 
-// Enqueue one cycle starting from buffer X (other buffer Y); the state ends
-// in X if `levels` is even, else in Y.  Then the energy of the final state.
+// Enqueue one cycle starting from buffer X (other buffer Y), then the energy
+// of the final state.  The state ends in X if `levels` is even, else in Y;
+// with end_in_x it always ends in X: an odd count runs its last level in
+// place when that level is on the coarse path (whose phases only read S and
+// whose final apply writes each pixel from itself), else copies Y to X.
 cudaError_t enqueue_cycle(cm_ctx* ctx, float* X, float* Y, const float* f, int H, int W,
                           float alpha, int kind, int levels, const cm_options& o,
-                          cudaStream_t st) {
+                          cudaStream_t st, bool end_in_x = false) {
     float* S = X;
     float* R = Y;
     for (int j = 0; j < levels; ++j) {
-        cudaError_t e = enqueue_level(ctx->tsums, ctx->cj, S, R, f, H, W, alpha, kind, j, o,
+        const bool in_place = end_in_x && j == levels - 1 && S == X &&
+                              j >= cm::coarse_level_log2();
+        float* out = in_place ? S : R;
+        cudaError_t e = enqueue_level(ctx->tsums, ctx->cj, S, out, f, H, W, alpha, kind, j, o,
                                       nullptr, nullptr, st);
         if (e != cudaSuccess) return e;
-        float* t = S;
-        S = R;
-        R = t;
+        if (!in_place) {
+            float* t = S;
+            S = R;
+            R = t;
+        }
+    }
+    if (end_in_x && S != X) {
+        cudaError_t e = cudaMemcpyAsync(X, S, (size_t)H * W * sizeof(float),
+                                        cudaMemcpyDeviceToDevice, st);
+        if (e != cudaSuccess) return e;
+        S = X;
     }
     return cm::launch_energy(S, f, H, W, alpha, kind, ctx->partials, ctx->ticket, ctx->E_dev, st);
+}
+
+// Capture the whole solve of u (in place, scratch Y) as one graph: the
+// initial energy, the state's initialisation, and a WHILE node around one
+// cycle plus the stopping test.
+cudaError_t capture_solve(cm_ctx* ctx, float* u, float* Y, const float* f, int H, int W,
+                          float alpha, int kind, int levels, const cm_options& o, double tol,
+                          int cycles, int trace_cap, cudaGraphExec_t* exec) {
+    cm::ImgDev* state = static_cast<cm::ImgDev*>(ctx->sstate);
+    cudaStream_t s1 = ctx->cap_stream, s2 = ctx->cap_stream2;
+    cudaError_t e = cudaStreamBeginCapture(s1, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return e;
+    bool body_open = false;
+    cudaGraph_t g = nullptr;
+    cudaStreamCaptureStatus cs;
+    cudaGraphConditionalHandle h = 0;
+    do {
+        if ((e = cudaStreamGetCaptureInfo(s1, &cs, nullptr, &g)) != cudaSuccess) break;
+        if ((e = cudaGraphConditionalHandleCreate(&h, g, 0, 0)) != cudaSuccess) break;
+        if ((e = cm::launch_energy(u, f, H, W, alpha, kind, ctx->partials, ctx->ticket,
+                                   ctx->E_dev, s1)) != cudaSuccess)
+            break;
+        if ((e = cm::launch_solve_init(state, ctx->E_dev, cycles, ctx->strace, h, s1)) !=
+            cudaSuccess)
+            break;
+        const cudaGraphNode_t* deps = nullptr;
+        size_t nd = 0;
+        if ((e = cudaStreamGetCaptureInfo(s1, &cs, nullptr, nullptr, &deps, nullptr, &nd)) !=
+            cudaSuccess)
+            break;
+        cudaGraphNodeParams cp = {cudaGraphNodeTypeConditional};
+        cp.conditional.handle = h;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        cudaGraphNode_t wnode;
+        if ((e = cudaGraphAddNode(&wnode, g, deps, nullptr, nd, &cp)) != cudaSuccess) break;
+        if ((e = cudaStreamUpdateCaptureDependencies(s1, &wnode, nullptr, 1,
+                                                     cudaStreamSetCaptureDependencies)) !=
+            cudaSuccess)
+            break;
+        cudaGraph_t body = cp.conditional.phGraph_out[0];
+        if ((e = cudaStreamBeginCaptureToGraph(s2, body, nullptr, nullptr, 0,
+                                               cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+            break;
+        body_open = true;
+        if ((e = enqueue_cycle(ctx, u, Y, f, H, W, alpha, kind, levels, o, s2, true)) !=
+            cudaSuccess)
+            break;
+        e = cm::launch_solve_stop(state, ctx->E_dev, tol, cycles, ctx->strace, trace_cap, h, s2);
+    } while (false);
+    if (body_open) {
+        cudaGraph_t b2 = nullptr;
+        cudaError_t ee = cudaStreamEndCapture(s2, &b2);
+        if (e == cudaSuccess) e = ee;
+    }
+    cudaGraph_t done = nullptr;
+    cudaError_t ee = cudaStreamEndCapture(s1, &done);
+    if (e == cudaSuccess) e = ee;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(exec, done, 0);
+    if (done) cudaGraphDestroy(done);
+    return e;
 }
 
 }  // namespace
@@ -234,6 +329,7 @@ int cm_create(cm_ctx** out, int device) {
     if (e == cudaSuccess) e = cudaMalloc(&ctx->E_dev, 8 * sizeof(double));
     if (e == cudaSuccess) e = cudaMallocHost(&ctx->E_pinned, 8 * sizeof(double));
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->cap_stream2, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cm::coarse_setup();
     if (e != cudaSuccess) {
         cm_destroy(ctx);
@@ -246,8 +342,12 @@ int cm_create(cm_ctx** out, int device) {
 void cm_destroy(cm_ctx* ctx) {
     if (!ctx) return;
     cudaSetDevice(ctx->device);
-    for (auto& g : ctx->graphs)
-        if (g.exec) cudaGraphExecDestroy(g.exec);
+    if (ctx->sgraph.exec) cudaGraphExecDestroy(ctx->sgraph.exec);
+    if (ctx->sstate) cudaFree(ctx->sstate);
+    if (ctx->sstate_host) cudaFreeHost(ctx->sstate_host);
+    if (ctx->strace) cudaFree(ctx->strace);
+    if (ctx->strace_host) cudaFreeHost(ctx->strace_host);
+    if (ctx->cap_stream2) cudaStreamDestroy(ctx->cap_stream2);
     if (ctx->ubuf) cudaFree(ctx->ubuf);
     if (ctx->partials) cudaFree(ctx->partials);
     if (ctx->tsums) cudaFree(ctx->tsums);
@@ -365,6 +465,69 @@ int cm_solve(cm_ctx* ctx, const float* f, int H, int W, float alpha, int kind, i
         CM_CUDA(cudaMemcpyAsync(u_out, u0, N * sizeof(float), cudaMemcpyDeviceToDevice, st));
     else if (!u0)
         CM_CUDA(cudaMemcpyAsync(u_out, f, N * sizeof(float), cudaMemcpyDeviceToDevice, st));
+    if (o.use_graph) {
+        // the whole solve as one graph: loop and stopping test on the device
+        rc = ensure_solve_state(ctx);
+        if (rc) return rc;
+        const int trace_cap = std::min(cycles, o.max_trace);
+        GraphKey key;
+        memset(&key, 0, sizeof(key));
+        key.S = u_out;
+        key.R = ctx->ubuf;
+        key.f = f;
+        key.H = H;
+        key.W = W;
+        key.kind = kind;
+        key.levels = L;
+        key.ncolors = o.ncolors;
+        key.G = o.grid_points;
+        key.K = o.golden_evals;
+        key.use_paper = o.paper_candidate;
+        key.alpha = alpha;
+        key.tol = tol;
+        key.cycles = cycles;
+        key.trace_cap = trace_cap;
+        auto& slot = ctx->sgraph;
+        if (!slot.valid || !(slot.key == key)) {
+            drop_graphs(ctx);
+            cudaError_t ce = capture_solve(ctx, u_out, ctx->ubuf, f, H, W, alpha, kind, L, o, tol,
+                                           cycles, trace_cap, &slot.exec);
+            if (ce != cudaSuccess) {
+                slot.exec = nullptr;
+                return cuda_fail(ctx, ce, "capture solve graph");
+            }
+            slot.key = key;
+            slot.valid = true;
+        }
+        CM_CUDA(cudaGraphLaunch(slot.exec, st));
+        CM_CUDA(cudaMemcpyAsync(ctx->sstate_host, ctx->sstate, cm::batch_state_bytes(),
+                                cudaMemcpyDeviceToHost, st));
+        CM_CUDA(cudaStreamSynchronize(st));
+        int ncyc = 0, conv = 0, viol = 0, numeric = 0, act = 0;
+        double E = 0.0;
+        cm::batch_read_state(ctx->sstate_host, &ncyc, &conv, &viol, &E, &numeric, &act);
+        const int tl = std::min(ncyc, trace_cap) + 1;
+        CM_CUDA(cudaMemcpyAsync(ctx->strace_host, ctx->strace, tl * sizeof(double),
+                                cudaMemcpyDeviceToHost, st));
+        CM_CUDA(cudaStreamSynchronize(st));
+        if (stats) {
+            memset(stats, 0, sizeof(*stats));
+            stats->levels = L;
+            stats->energy_initial = ctx->strace_host[0];
+            stats->trace_len = tl;
+            memcpy(stats->energy_trace, ctx->strace_host, tl * sizeof(double));
+            stats->cycles_run = ncyc;
+            stats->converged = conv;
+            stats->monotone_violations = viol;
+            stats->energy_final = ncyc > 0 ? E : ctx->strace_host[0];
+        }
+        if (numeric)
+            return fail(ctx, CM_ERR_NUMERIC, ncyc == 0 ? "cm_solve: non-finite initial energy"
+                                                       : "cm_solve: non-finite energy");
+        if (tol > 0.0 && !conv) return fail(ctx, CM_NOT_CONVERGED, "cm_solve: cycle cap reached");
+        return CM_OK;
+    }
+    // host loop (use_graph = 0): one cycle at a time, 8 bytes read back per cycle
     CM_CUDA(cm::launch_energy(u_out, f, H, W, alpha, kind, ctx->partials, ctx->ticket, ctx->E_dev, st));
     CM_CUDA(cudaMemcpyAsync(ctx->E_pinned, ctx->E_dev, sizeof(double), cudaMemcpyDeviceToHost, st));
     CM_CUDA(cudaStreamSynchronize(st));
@@ -381,42 +544,7 @@ int cm_solve(cm_ctx* ctx, const float* f, int H, int W, float alpha, int kind, i
     while (l < cycles) {
         float* X = bufs[cur];
         float* Y = bufs[cur ^ 1];
-        if (o.use_graph) {
-            GraphKey key;
-            memset(&key, 0, sizeof(key));
-            key.S = X;
-            key.R = Y;
-            key.f = f;
-            key.H = H;
-            key.W = W;
-            key.kind = kind;
-            key.levels = L;
-            key.ncolors = o.ncolors;
-            key.G = o.grid_points;
-            key.K = o.golden_evals;
-            key.use_paper = o.paper_candidate;
-            key.alpha = alpha;
-            auto& slot = ctx->graphs[cur];
-            if (!slot.valid || !(slot.key == key)) {
-                if (slot.exec) cudaGraphExecDestroy(slot.exec);
-                slot.exec = nullptr;
-                slot.valid = false;
-                cudaGraph_t g;
-                CM_CUDA(cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));
-                cudaError_t ce = enqueue_cycle(ctx, X, Y, f, H, W, alpha, kind, L, o, ctx->cap_stream);
-                cudaError_t ee = cudaStreamEndCapture(ctx->cap_stream, &g);
-                if (ce != cudaSuccess) return cuda_fail(ctx, ce, "capture cycle");
-                if (ee != cudaSuccess) return cuda_fail(ctx, ee, "end capture");
-                cudaError_t ie = cudaGraphInstantiate(&slot.exec, g, 0);
-                cudaGraphDestroy(g);
-                if (ie != cudaSuccess) return cuda_fail(ctx, ie, "graph instantiate");
-                slot.key = key;
-                slot.valid = true;
-            }
-            CM_CUDA(cudaGraphLaunch(slot.exec, st));
-        } else {
-            CM_CUDA(enqueue_cycle(ctx, X, Y, f, H, W, alpha, kind, L, o, st));
-        }
+        CM_CUDA(enqueue_cycle(ctx, X, Y, f, H, W, alpha, kind, L, o, st));
         if (L & 1) cur ^= 1;
         CM_CUDA(cudaMemcpyAsync(ctx->E_pinned, ctx->E_dev, sizeof(double), cudaMemcpyDeviceToHost, st));
         CM_CUDA(cudaStreamSynchronize(st));

@@ -49,10 +49,7 @@ __global__ void batch_init_kernel(ImgDev* st, const double* E0, int n, int cycle
 }
 
 // Stopping test of one image after a cycle (Eq. reerr), on the device.
-__global__ void batch_stop_kernel(ImgDev* st, const double* E_now, double tol, int cap,
-                                  double* trace, int trace_cap) {
-    if (threadIdx.x != 0 || st->active == 0) return;
-    const double E = *E_now;
+__device__ void stop_test(ImgDev* st, double E, double tol, int cap, double* trace, int trace_cap) {
     const int l = st->cycles + 1;
     st->cycles = l;
     st->E = E;
@@ -73,6 +70,36 @@ __global__ void batch_stop_kernel(ImgDev* st, const double* E_now, double tol, i
     }
 }
 
+__global__ void batch_stop_kernel(ImgDev* st, const double* E_now, double tol, int cap,
+                                  double* trace, int trace_cap) {
+    if (threadIdx.x != 0 || st->active == 0) return;
+    stop_test(st, *E_now, tol, cap, trace, trace_cap);
+}
+
+// Single-image solve as one graph: the loop of cycles is a conditional WHILE
+// node whose condition these kernels set from the image's state.
+__global__ void solve_init_kernel(ImgDev* st, const double* E0, int cycles, double* trace,
+                                  cudaGraphConditionalHandle h) {
+    if (threadIdx.x != 0) return;
+    const double E = *E0;
+    st->E_prev = E;
+    st->E = E;
+    st->cycles = 0;
+    st->viol = 0;
+    st->converged = 0;
+    st->numeric_error = isfinite(E) ? 0 : 1;
+    st->active = (cycles > 0 && isfinite(E)) ? 1 : 0;
+    trace[0] = E;
+    cudaGraphSetConditional(h, (unsigned)st->active);
+}
+
+__global__ void solve_stop_kernel(ImgDev* st, const double* E_now, double tol, int cap,
+                                  double* trace, int trace_cap, cudaGraphConditionalHandle h) {
+    if (threadIdx.x != 0) return;
+    if (st->active) stop_test(st, *E_now, tol, cap, trace, trace_cap);
+    cudaGraphSetConditional(h, (unsigned)st->active);
+}
+
 __global__ void batch_copy_kernel(const float* __restrict__ src, float* __restrict__ dst, size_t n,
                                   const int* __restrict__ active) {
     if (active && *active == 0) return;
@@ -89,6 +116,18 @@ cudaError_t launch_batch_init(ImgDev* st, const double* E0, int n, int cycles, c
 cudaError_t launch_batch_stop(ImgDev* st, const double* E_now, double tol, int cap,
                               double* trace, int trace_cap, cudaStream_t s) {
     batch_stop_kernel<<<1, 32, 0, s>>>(st, E_now, tol, cap, trace, trace_cap);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_solve_init(ImgDev* st, const double* E0, int cycles, double* trace,
+                              cudaGraphConditionalHandle h, cudaStream_t s) {
+    solve_init_kernel<<<1, 32, 0, s>>>(st, E0, cycles, trace, h);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_solve_stop(ImgDev* st, const double* E_now, double tol, int cap, double* trace,
+                              int trace_cap, cudaGraphConditionalHandle h, cudaStream_t s) {
+    solve_stop_kernel<<<1, 32, 0, s>>>(st, E_now, tol, cap, trace, trace_cap, h);
     return cudaGetLastError();
 }
 

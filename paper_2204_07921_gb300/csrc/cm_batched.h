@@ -12,6 +12,12 @@ size_t batch_active_offset();  // offset of its int `active` flag
 cudaError_t launch_batch_init(ImgDev* st, const double* E0, int n, int cycles, cudaStream_t s);
 cudaError_t launch_batch_stop(ImgDev* st, const double* E_now, double tol, int cap,
                               double* trace, int trace_cap, cudaStream_t s);
+// Single-image solve graph: initial state from the energy E0 (and the loop
+// condition h), and the stopping test after a cycle (sets h to `active`).
+cudaError_t launch_solve_init(ImgDev* st, const double* E0, int cycles, double* trace,
+                              cudaGraphConditionalHandle h, cudaStream_t s);
+cudaError_t launch_solve_stop(ImgDev* st, const double* E_now, double tol, int cap, double* trace,
+                              int trace_cap, cudaGraphConditionalHandle h, cudaStream_t s);
 cudaError_t launch_batch_copy(const float* src, float* dst, size_t n, const int* active,
                               cudaStream_t s);
 // Unpack one image's state copied to the host.

@@ -395,3 +395,35 @@ def test_constant_image_fixed_point_gpu():
     u, st = run_solve(f, 10.0, cm.MEAN, 3)
     np.testing.assert_array_equal(u, f)
     assert st.trace() == [0.0] * 4
+
+
+@pytest.mark.parametrize("shape,cycles,tol,max_trace", [
+    ((300, 260), 0, 1e-4, 4096),      # no cycle: u = f, energy trace [E0]
+    ((300, 260), 6, 0.0, 3),          # trace capped below the cycle count
+    ((131, 97), 40, 1e-4, 4096),      # converges before the cap (odd level count)
+    ((520, 300), 2, 1e-9, 4096),      # cap reached first: CM_NOT_CONVERGED, stats kept
+])
+def test_device_loop_matches_host_loop(shape, cycles, tol, max_trace):
+    """The graph solve (WHILE node, stopping test on the device) against the
+    host loop (one cycle per launch, host stopping test): identical u, cycle
+    count, convergence flag, violations and energy trace."""
+    H, W = shape
+    f = synth.piecewise_image(H, W, 31 + H, 8, 0.08).f
+    out = []
+    for use_graph in (1, 0):
+        opts = cm.default_options(use_graph=use_graph)
+        opts.max_trace = max_trace
+        u, st = cm.cm_solve(to_dev(f), 20.0, cm.MEAN, cycles=cycles, tol=tol, options=opts)
+        torch.cuda.synchronize()
+        out.append((host(u), st))
+    (ua, sa), (ub, sb) = out
+    np.testing.assert_array_equal(ua, ub)
+    for k in ("cycles_run", "converged", "monotone_violations", "trace_len", "levels"):
+        assert getattr(sa, k) == getattr(sb, k), k
+    assert sa.energy_initial == sb.energy_initial
+    assert sa.energy_final == sb.energy_final
+    assert sa.trace() == sb.trace()
+    if cycles == 0:
+        np.testing.assert_array_equal(ua, f)
+        assert sa.trace_len == 1
+    assert sa.trace_len == min(sa.cycles_run, max_trace) + 1
