@@ -8,15 +8,17 @@
 //
 //  conv_in_kernel     1 -> 32 on CUDA cores (9 MACs per output).
 //  conv_mid_kernel    32 -> 32 as an implicit GEMM on the tensor cores:
-//                     M = pixels (8 x 16 tile per CTA), N = 32, K = 9 x 32;
-//                     ldmatrix + mma.sync m16n8k16 BF16 -> FP32.  The same
-//                     kernel computes dX of the backward pass with the
-//                     flipped, transposed weights and the ReLU mask of the
-//                     layer's input fused in the epilogue.
+//                     M = pixels (8 x 16 tiles), N = 32, K = 9 x 32;
+//                     ldmatrix + mma.sync m16n8k16 BF16 -> FP32; persistent
+//                     CTAs (weights staged once) with cp.async double-
+//                     buffered halo tiles.  The same kernel computes dX of
+//                     the backward pass with the flipped, transposed weights
+//                     and the ReLU mask of the layer's input fused in the
+//                     epilogue, and the output layer 32 -> 1 with the
+//                     residual u0 = f + out (one real output column).
 //  dw_mid_kernel      dW = sum_p X[p + tap]^T dZ[p] on the tensor cores, per
 //                     CTA partial sums over a grid-stride set of tiles,
 //                     reduced in a fixed order (deterministic).
-//  conv_out_kernel    32 -> 1 and the residual u0 = f + out (CUDA cores).
 //  out_grad_kernel    dL/dout of the MSE loss, dX of conv6, ReLU mask.
 //  dw_small kernels   dW of conv1 and conv6 (CUDA cores).
 //  adam_kernel        Adam (Kingma and Ba) on the FP32 master weights, then
@@ -83,6 +85,18 @@ __device__ __forceinline__ void mma16816(float (&d)[4], const unsigned (&a)[4], 
         : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
+// 16-byte asynchronous copy global -> shared; zero-filled when !valid (the
+// source address is then not read).
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, bool valid) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(smem_addr(dst)),
+                 "l"(src), "r"(valid ? 16 : 0));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N));
+}
+
 __device__ __forceinline__ float bf(bf16 x) { return __bfloat162float(x); }
 __device__ __forceinline__ float round_bf(float x) { return __bfloat162float(__float2bfloat16(x)); }
 
@@ -127,13 +141,26 @@ __device__ __forceinline__ void load_tile(bf16 (*s)[CS], const bf16* __restrict_
     }
 }
 
+// The halo tile of load_halo, staged with asynchronous copies.
+__device__ __forceinline__ void load_halo_async(bf16 (*s)[CS], const bf16* __restrict__ X,
+                                                const Tile& t, int H, int W) {
+    const size_t img = (size_t)t.n * H * W;
+    for (int i = threadIdx.x; i < HH * HW * 4; i += blockDim.x) {
+        const int pix = i >> 2, q = i & 3;
+        const int gy = t.y0 - 1 + pix / HW, gx = t.x0 - 1 + pix % HW;
+        const bool in = gy >= 0 && gy < H && gx >= 0 && gx < W;
+        const bf16* src = in ? X + (img + (size_t)gy * W + gx) * C + q * 8 : X;
+        cp_async16(&s[pix][q * 8], src, in);
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Forward kernels.
 
 __global__ void __launch_bounds__(256) conv_in_kernel(const float* __restrict__ f,
                                                       const float* __restrict__ P,
                                                       bf16* __restrict__ Y, int N, int H, int W) {
-    __shared__ float sw[9 * C + C];
+    __shared__ __align__(16) float sw[9 * C + C];
     for (int i = threadIdx.x; i < 9 * C + C; i += blockDim.x) sw[i] = round_bf(P[OFF_W1 + i]);
     __syncthreads();
     const size_t total = (size_t)N * H * W;
@@ -147,14 +174,29 @@ __global__ void __launch_bounds__(256) conv_in_kernel(const float* __restrict__ 
         const int yy = y + t / 3 - 1, xx = x + t % 3 - 1;
         v[t] = (yy >= 0 && yy < H && xx >= 0 && xx < W) ? f[img + (size_t)yy * W + xx] : 0.0f;
     }
+    // weights and bias four output channels per 16-byte shared load
+    float a[C];
+#pragma unroll
+    for (int o = 0; o < C; o += 4) {
+        const float4 b4 = *reinterpret_cast<const float4*>(&sw[9 * C + o]);
+        a[o] = b4.x;
+        a[o + 1] = b4.y;
+        a[o + 2] = b4.z;
+        a[o + 3] = b4.w;
+    }
+#pragma unroll
+    for (int t = 0; t < 9; ++t)
+#pragma unroll
+        for (int o = 0; o < C; o += 4) {
+            const float4 w4 = *reinterpret_cast<const float4*>(&sw[t * C + o]);
+            a[o] = fmaf(v[t], w4.x, a[o]);
+            a[o + 1] = fmaf(v[t], w4.y, a[o + 1]);
+            a[o + 2] = fmaf(v[t], w4.z, a[o + 2]);
+            a[o + 3] = fmaf(v[t], w4.w, a[o + 3]);
+        }
     __align__(16) bf16 out[C];
 #pragma unroll
-    for (int o = 0; o < C; ++o) {
-        float a = sw[9 * C + o];
-#pragma unroll
-        for (int t = 0; t < 9; ++t) a = fmaf(v[t], sw[t * C + o], a);
-        out[o] = __float2bfloat16(fmaxf(a, 0.0f));
-    }
+    for (int o = 0; o < C; ++o) out[o] = __float2bfloat16(fmaxf(a[o], 0.0f));
     uint4* dst = reinterpret_cast<uint4*>(Y + p * C);
 #pragma unroll
     for (int q = 0; q < 4; ++q) dst[q] = reinterpret_cast<const uint4*>(out)[q];
@@ -162,113 +204,121 @@ __global__ void __launch_bounds__(256) conv_in_kernel(const float* __restrict__ 
 
 // MODE 0: Y = ReLU(conv(X) + bias).  MODE 1: Y = conv(X) * [mask_src > 0]
 // (the backward dX of a 32 -> 32 layer, X = dZ, weights flipped and
-// transposed).  Wt: [9][32 out][32 in] BF16.
+// transposed).  MODE 2: the output layer, u0 = f + conv(X) + bias[0] with
+// one output channel (weights padded to 16 columns, column 0 real).
+// Wt: [9][NO out][32 in] BF16.  Persistent: every CTA stages the weights once
+// and walks the tiles t = blockIdx.x, + gridDim.x, ..., the halo of the next
+// tile loading (cp.async) while the current one is multiplied.
 template <int MODE>
-__global__ void __launch_bounds__(128) conv_mid_kernel(const bf16* __restrict__ X,
-                                                       const bf16* __restrict__ Wt,
-                                                       const float* __restrict__ bias,
-                                                       const bf16* __restrict__ mask_src,
-                                                       bf16* __restrict__ Y, int H, int W) {
-    __shared__ __align__(16) bf16 s_in[HH * HW][CS];
-    __shared__ __align__(16) bf16 s_w[9 * C][CS];
-    const Tile t = tile_of(blockIdx.x, H, W);
-    for (int i = threadIdx.x; i < 9 * C * 4; i += blockDim.x) {
+constexpr size_t conv_smem_bytes() {
+    return (size_t)(2 * HH * HW + 9 * (MODE == 2 ? 16 : C)) * CS * sizeof(bf16);
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(128, 4) conv_mid_kernel(const bf16* __restrict__ X,
+                                                          const bf16* __restrict__ Wt,
+                                                          const float* __restrict__ bias,
+                                                          const bf16* __restrict__ mask_src,
+                                                          bf16* __restrict__ Y,
+                                                          const float* __restrict__ f,
+                                                          float* __restrict__ u0, int H, int W,
+                                                          int ntiles) {
+    constexpr int NO = MODE == 2 ? 16 : C;   // MMA output columns
+    constexpr int NP = NO / 16;               // ldmatrix x4 loads of B per k-chunk
+    extern __shared__ __align__(16) unsigned char conv_smem[];
+    bf16(*s_in)[HH * HW][CS] = reinterpret_cast<bf16(*)[HH * HW][CS]>(conv_smem);
+    bf16(*s_w)[CS] = reinterpret_cast<bf16(*)[CS]>(conv_smem + 2 * HH * HW * CS * sizeof(bf16));
+    for (int i = threadIdx.x; i < 9 * NO * 4; i += blockDim.x) {
         const int row = i >> 2, q = i & 3;
         *reinterpret_cast<uint4*>(&s_w[row][q * 8]) = reinterpret_cast<const uint4*>(Wt)[i];
     }
-    load_halo(s_in, X, t, H, W);
-    __syncthreads();
+    int tcur = blockIdx.x;
+    if (tcur < ntiles) load_halo_async(s_in[0], X, tile_of(tcur, H, W), H, W);
+    cp_async_commit();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int lrow = lane & 7, lmat = lane >> 3;
-    float acc[2][4][4];
+    const int g = lane >> 2, q = lane & 3;
+    for (int it = 0; tcur < ntiles; ++it, tcur += gridDim.x) {
+        const int buf = it & 1;
+        const int tnext = tcur + gridDim.x;
+        if (tnext < ntiles) load_halo_async(s_in[buf ^ 1], X, tile_of(tnext, H, W), H, W);
+        cp_async_commit();
+        cp_async_wait<1>();   // this tile's copies (all but the newest group) have landed
+        __syncthreads();
+        float acc[2][NO / 8][4];
 #pragma unroll
-    for (int a = 0; a < 2; ++a)
+        for (int x = 0; x < 2; ++x)
 #pragma unroll
-        for (int b = 0; b < 4; ++b)
+            for (int y = 0; y < NO / 8; ++y)
 #pragma unroll
-            for (int c = 0; c < 4; ++c) acc[a][b][c] = 0.0f;
+                for (int z = 0; z < 4; ++z) acc[x][y][z] = 0.0f;
 #pragma unroll 1
-    for (int tap = 0; tap < 9; ++tap) {
-        const int dy = tap / 3 - 1, dx = tap % 3 - 1;
+        for (int tap = 0; tap < 9; ++tap) {
+            const int dy = tap / 3 - 1, dx = tap % 3 - 1;
 #pragma unroll
-        for (int kc = 0; kc < 2; ++kc) {
-            unsigned a[2][4];
-#pragma unroll
-            for (int mt = 0; mt < 2; ++mt) {
-                const int rr = 2 * warp + mt;
-                const int col = lrow + 8 * (lmat & 1);
-                const int pix = (rr + 1 + dy) * HW + (col + 1 + dx);
-                ldsm_x4(a[mt], &s_in[pix][8 * (lmat >> 1) + 16 * kc]);
-            }
-#pragma unroll
-            for (int pr = 0; pr < 2; ++pr) {
-                unsigned b[4];
-                const int o = 16 * pr + 8 * (lmat >> 1) + lrow;
-                ldsm_x4(b, &s_w[tap * C + o][16 * kc + 8 * (lmat & 1)]);
+            for (int kc = 0; kc < 2; ++kc) {
+                unsigned a[2][4];
 #pragma unroll
                 for (int mt = 0; mt < 2; ++mt) {
-                    mma16816(acc[mt][2 * pr], a[mt], b[0], b[1]);
-                    mma16816(acc[mt][2 * pr + 1], a[mt], b[2], b[3]);
+                    const int rr = 2 * warp + mt;
+                    const int col = lrow + 8 * (lmat & 1);
+                    const int pix = (rr + 1 + dy) * HW + (col + 1 + dx);
+                    ldsm_x4(a[mt], &s_in[buf][pix][8 * (lmat >> 1) + 16 * kc]);
+                }
+#pragma unroll
+                for (int pr = 0; pr < NP; ++pr) {
+                    unsigned bb[4];
+                    const int o = 16 * pr + 8 * (lmat >> 1) + lrow;
+                    ldsm_x4(bb, &s_w[tap * NO + o][16 * kc + 8 * (lmat & 1)]);
+#pragma unroll
+                    for (int mt = 0; mt < 2; ++mt) {
+                        mma16816(acc[mt][2 * pr], a[mt], bb[0], bb[1]);
+                        mma16816(acc[mt][2 * pr + 1], a[mt], bb[2], bb[3]);
+                    }
                 }
             }
         }
-    }
-    const int g = lane >> 2, q = lane & 3;
-    const size_t img = (size_t)t.n * H * W;
+        const Tile t = tile_of(tcur, H, W);
+        const size_t img = (size_t)t.n * H * W;
 #pragma unroll
-    for (int mt = 0; mt < 2; ++mt) {
-        const int gy = t.y0 + 2 * warp + mt;
+        for (int mt = 0; mt < 2; ++mt) {
+            const int gy = t.y0 + 2 * warp + mt;
+            if (MODE == 2) {
+                if (q == 0) {
 #pragma unroll
-        for (int nt = 0; nt < 4; ++nt) {
-            const int co = 8 * nt + 2 * q;
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int gx = t.x0 + g + 8 * h;
-                if (gy >= H || gx >= W) continue;
-                const size_t pi = (img + (size_t)gy * W + gx) * C + co;
-                float v0 = acc[mt][nt][2 * h], v1 = acc[mt][nt][2 * h + 1];
-                if (MODE == 0) {
-                    v0 = fmaxf(v0 + bias[co], 0.0f);
-                    v1 = fmaxf(v1 + bias[co + 1], 0.0f);
-                } else {
-                    const __nv_bfloat162 m = *reinterpret_cast<const __nv_bfloat162*>(mask_src + pi);
-                    v0 = bf(m.x) > 0.0f ? v0 : 0.0f;
-                    v1 = bf(m.y) > 0.0f ? v1 : 0.0f;
+                    for (int h = 0; h < 2; ++h) {
+                        const int gx = t.x0 + g + 8 * h;
+                        if (gy >= H || gx >= W) continue;
+                        const size_t pp = img + (size_t)gy * W + gx;
+                        u0[pp] = f[pp] + (acc[mt][0][2 * h] + bias[0]);
+                    }
                 }
-                *reinterpret_cast<__nv_bfloat162*>(Y + pi) = __floats2bfloat162_rn(v0, v1);
+                continue;
+            }
+#pragma unroll
+            for (int nt = 0; nt < NO / 8; ++nt) {
+                const int co = 8 * nt + 2 * q;
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int gx = t.x0 + g + 8 * h;
+                    if (gy >= H || gx >= W) continue;
+                    const size_t pi = (img + (size_t)gy * W + gx) * C + co;
+                    float v0 = acc[mt][nt][2 * h], v1 = acc[mt][nt][2 * h + 1];
+                    if (MODE == 0) {
+                        v0 = fmaxf(v0 + bias[co], 0.0f);
+                        v1 = fmaxf(v1 + bias[co + 1], 0.0f);
+                    } else {
+                        const __nv_bfloat162 m = *reinterpret_cast<const __nv_bfloat162*>(mask_src + pi);
+                        v0 = bf(m.x) > 0.0f ? v0 : 0.0f;
+                        v1 = bf(m.y) > 0.0f ? v1 : 0.0f;
+                    }
+                    *reinterpret_cast<__nv_bfloat162*>(Y + pi) = __floats2bfloat162_rn(v0, v1);
+                }
             }
         }
+        __syncthreads();   // the buffer is refilled two tiles on
     }
-}
-
-__global__ void __launch_bounds__(256) conv_out_kernel(const bf16* __restrict__ X,
-                                                       const float* __restrict__ P,
-                                                       const float* __restrict__ f,
-                                                       float* __restrict__ u0, int N, int H,
-                                                       int W) {
-    __shared__ float sw[9 * C + 1];
-    for (int i = threadIdx.x; i < 9 * C + 1; i += blockDim.x) sw[i] = round_bf(P[OFF_W6 + i]);
-    __syncthreads();
-    const size_t total = (size_t)N * H * W;
-    const size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= total) return;
-    const int x = (int)(p % W), y = (int)((p / W) % H);
-    const size_t img = p - ((size_t)y * W + x);
-    float acc = sw[9 * C];
-#pragma unroll 1
-    for (int t = 0; t < 9; ++t) {
-        const int yy = y + t / 3 - 1, xx = x + t % 3 - 1;
-        if (yy < 0 || yy >= H || xx < 0 || xx >= W) continue;
-        const uint4* src = reinterpret_cast<const uint4*>(X + (img + (size_t)yy * W + xx) * C);
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const uint4 v = src[q];
-            const bf16* e = reinterpret_cast<const bf16*>(&v);
-#pragma unroll
-            for (int j = 0; j < 8; ++j) acc = fmaf(bf(e[j]), sw[t * C + 8 * q + j], acc);
-        }
-    }
-    u0[p] = f[p] + acc;
+    cp_async_wait<0>();
 }
 
 // ---------------------------------------------------------------------------
@@ -527,8 +577,12 @@ __global__ void adam_kernel(float* __restrict__ P, const float* __restrict__ G, 
 // the master [tap][ci][co]) and backward [tap][ci][co] with the tap flipped
 // (dX = conv(dZ, W'), W'[tap][ci][co] = W[8 - tap][ci][co]).
 __global__ void pack_kernel(const float* __restrict__ P, bf16* __restrict__ wf,
-                            bf16* __restrict__ wb) {
+                            bf16* __restrict__ wb, bf16* __restrict__ w6p) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < 9 * 16 * C) {   // output layer: [tap][16 out][32 in], column 0 real
+        const int tap = i / (16 * C), o = (i / C) % 16, ci = i % C;
+        w6p[i] = __float2bfloat16(o == 0 ? P[OFF_W6 + tap * C + ci] : 0.0f);
+    }
     if (i >= 4 * MIDW) return;
     const int l = i / MIDW, r = i % MIDW;
     const int tap = r / (C * C), ci = (r / C) % C, co = r % C;
@@ -540,12 +594,27 @@ __global__ void pack_kernel(const float* __restrict__ P, bf16* __restrict__ wf,
 // ---------------------------------------------------------------------------
 // Host side.
 
+// Dynamic shared memory above 48 KB must be allowed per kernel.
+cudaError_t conv_setup() {
+    cudaError_t e = cudaFuncSetAttribute(conv_mid_kernel<0>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)conv_smem_bytes<0>());
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(conv_mid_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)conv_smem_bytes<1>());
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(conv_mid_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)conv_smem_bytes<2>());
+    return e;
+}
+
 struct Net {
     int device = 0;
     std::string err;
     float *P = nullptr, *G = nullptr, *M = nullptr, *V = nullptr;
-    bf16 *wf = nullptr, *wb = nullptr;
+    bf16 *wf = nullptr, *wb = nullptr, *w6p = nullptr;
     int step = 0;
+    int conv_grid = 0;      // persistent CTAs of the tensor-core convolutions
     // activations (capacity in pixels)
     size_t cap = 0;
     bf16* act[6] = {};      // act[1..5] = X1..X5
@@ -586,7 +655,7 @@ int ensure_acts(Net* net, size_t npx) {
 }
 
 int pack(Net* net, cudaStream_t st) {
-    pack_kernel<<<(4 * MIDW + 255) / 256, 256, 0, st>>>(net->P, net->wf, net->wb);
+    pack_kernel<<<(4 * MIDW + 255) / 256, 256, 0, st>>>(net->P, net->wf, net->wb, net->w6p);
     NET_CUDA(cudaGetLastError());
     return CM_OK;
 }
@@ -594,11 +663,14 @@ int pack(Net* net, cudaStream_t st) {
 int forward(Net* net, const float* f, int N, int H, int W, float* u0, cudaStream_t st) {
     const size_t npx = (size_t)N * H * W;
     const int ntiles = N * ((H + TH - 1) / TH) * ((W + TW - 1) / TW);
+    const int grid = std::min(ntiles, net->conv_grid);
     conv_in_kernel<<<(unsigned)((npx + 255) / 256), 256, 0, st>>>(f, net->P, net->act[1], N, H, W);
     for (int l = 2; l <= 5; ++l)
-        conv_mid_kernel<0><<<ntiles, 128, 0, st>>>(net->act[l - 1], net->wf + (l - 2) * MIDW,
-                                                   net->P + off_b(l), nullptr, net->act[l], H, W);
-    conv_out_kernel<<<(unsigned)((npx + 255) / 256), 256, 0, st>>>(net->act[5], net->P, f, u0, N, H, W);
+        conv_mid_kernel<0><<<grid, 128, conv_smem_bytes<0>(), st>>>(net->act[l - 1], net->wf + (l - 2) * MIDW,
+                                                 net->P + off_b(l), nullptr, net->act[l], nullptr,
+                                                 nullptr, H, W, ntiles);
+    conv_mid_kernel<2><<<grid, 128, conv_smem_bytes<2>(), st>>>(net->act[5], net->w6p, net->P + OFF_B6, nullptr,
+                                             nullptr, f, u0, H, W, ntiles);
     NET_CUDA(cudaGetLastError());
     return CM_OK;
 }
@@ -622,8 +694,9 @@ int backward(Net* net, const float* f, const float* us, int N, int H, int W, cud
         dw_mid_kernel<<<gm, 128, 0, st>>>(net->act[l - 1], net->dz[cur], net->part, N, H, W);
         reduce_parts_kernel<<<(DW_STRIDE + 255) / 256, 256, 0, st>>>(net->part, gm, DW_STRIDE,
                                                                      DW_STRIDE, net->G + off_w(l));
-        conv_mid_kernel<1><<<ntiles, 128, 0, st>>>(net->dz[cur], net->wb + (l - 2) * MIDW, nullptr,
-                                                   net->act[l - 1], net->dz[cur ^ 1], H, W);
+        conv_mid_kernel<1><<<std::min(ntiles, net->conv_grid), 128, conv_smem_bytes<1>(), st>>>(
+            net->dz[cur], net->wb + (l - 2) * MIDW, nullptr, net->act[l - 1], net->dz[cur ^ 1],
+            nullptr, nullptr, H, W, ntiles);
         cur ^= 1;
     }
     const int g1 = std::min(ntiles, DW_GRID);
@@ -691,6 +764,13 @@ int cm_net_create(cm_ctx* ctx, cm_net** out) {
     if (e == cudaSuccess) e = cudaMalloc(&net->V, np);
     if (e == cudaSuccess) e = cudaMalloc(&net->wf, 4 * cm::cnn::MIDW * sizeof(cm::cnn::bf16));
     if (e == cudaSuccess) e = cudaMalloc(&net->wb, 4 * cm::cnn::MIDW * sizeof(cm::cnn::bf16));
+    if (e == cudaSuccess) e = cudaMalloc(&net->w6p, 9 * 16 * cm::cnn::C * sizeof(cm::cnn::bf16));
+    if (e == cudaSuccess) {
+        int nsm = 0;
+        e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, net->device);
+        net->conv_grid = 4 * nsm;   // four resident CTAs per SM (shared memory, registers)
+    }
+    if (e == cudaSuccess) e = cm::cnn::conv_setup();
     if (e == cudaSuccess)
         e = cudaMalloc(&net->part, (size_t)cm::cnn::DW_GRID * cm::cnn::DW_STRIDE * sizeof(float));
     if (e == cudaSuccess) e = cudaMalloc(&net->loss, sizeof(double));
@@ -716,6 +796,7 @@ void cm_net_destroy(cm_net* net) {
     for (float* p : {net->P, net->G, net->M, net->V, net->u0, net->part})
         if (p) cudaFree(p);
     if (net->wf) cudaFree(net->wf);
+    if (net->w6p) cudaFree(net->w6p);
     if (net->wb) cudaFree(net->wb);
     for (int i = 1; i <= 5; ++i)
         if (net->act[i]) cudaFree(net->act[i]);
