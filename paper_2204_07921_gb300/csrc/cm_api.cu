@@ -603,6 +603,10 @@ int cm_warmstart(cm_ctx* ctx, cm_net* net, const float* f, int N, int H, int W, 
             CM_CUDA(cudaMemcpyAsync(ctx->E_pinned, ctx->E_dev, 2 * sizeof(double),
                                     cudaMemcpyDeviceToHost, st));
             CM_CUDA(cudaStreamSynchronize(st));
+            if (n == 0) {
+                rc = cm::cnn::net_status(nn);
+                if (rc) return fail(ctx, rc, std::string("cm_warmstart: ") + cm::cnn::net_error(nn));
+            }
             const bool keep = isfinite(ctx->E_pinned[0]) && ctx->E_pinned[0] <= ctx->E_pinned[1];
             if (!keep)
                 CM_CUDA(cudaMemcpyAsync(ui, fi, npx * sizeof(float), cudaMemcpyDeviceToDevice, st));

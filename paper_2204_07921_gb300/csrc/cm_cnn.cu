@@ -23,13 +23,16 @@
 //  dw_small kernels   dW of conv1 and conv6 (CUDA cores).
 //  adam_kernel        Adam (Kingma and Ba) on the FP32 master weights, then
 //                     the BF16 copies are repacked.
+#include <cuda.h>
 #include <cuda_bf16.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdio.h>
 #include <string.h>
 
 #include <algorithm>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -592,10 +595,318 @@ __global__ void pack_kernel(const float* __restrict__ P, bf16* __restrict__ wf,
 }
 
 // ---------------------------------------------------------------------------
+// 5th-generation tensor cores (tcgen05): the same convolutions with the
+// accumulators in tensor memory.  A work unit is a strip of TR = 8 output
+// rows x 128 columns.  Output row r is one M = 128 (pixels) x N (channels)
+// accumulator in TMEM, summed over 9 taps x 2 K-steps of 16 input channels
+// by tcgen05.mma from shared-memory operands.  The halo of the strip (10 x
+// 130 pixels) is loaded by TMA (four tile copies, one per plane of 8
+// channels, zero outside the image), so plane j holds channels 8j .. 8j + 7
+// of every pixel, 16 bytes each: 8 consecutive pixels are one 128-byte core
+// matrix of the no-swizzle K-major layout, and the operand of tap (dy, dx)
+// is that layout started dy rows and dx pixels further on (descriptor start
+// = plane + pixel x 16 B, K-direction byte offset = the plane stride,
+// M-direction byte offset = 128 B).  The weights are staged the same way
+// ([tap][plane][n] x 16 B).
+//
+// Pipeline (one CTA per SM, persistent over strips): thread 0 waits for a
+// strip's halo, issues its 144 MMAs into one of two TMEM accumulator sets and
+// commits them to an mbarrier; meanwhile the four warps drain the previous
+// strip's accumulators (tcgen05.ld: warp w owns TMEM lanes 32w .. 32w + 31),
+// and as soon as that strip's MMAs are known complete its halo buffer is
+// refilled by TMA with the strip after next.  Every wait is bounded.
+
+constexpr int TR = 6, TXC = 128;                         // strip: 6 rows x 128 columns
+constexpr int NSTAGE = 3;                                // halo buffers in flight
+constexpr int HRW = TR + 2, HCL = TXC + 2;               // halo rows / columns
+constexpr unsigned PLANE_DATA = HRW * HCL * 16;          // bytes of one plane
+constexpr unsigned PLANE = (PLANE_DATA + 127) & ~127u;   // plane stride (TMA: 128-byte aligned)
+constexpr unsigned HALO_BYTES = 4 * PLANE;
+
+template <int MODE>
+constexpr int tc_no() { return MODE == 2 ? 16 : C; }
+
+template <int MODE>
+constexpr size_t tc_smem_bytes() {
+    return 1024 + NSTAGE * (size_t)HALO_BYTES + 9 * 4 * (size_t)tc_no<MODE>() * 16 + 128;
+}
+
+__device__ __forceinline__ uint64_t umma_sdesc(unsigned addr, unsigned lbo, unsigned sbo) {
+    uint64_t d = (uint64_t)((addr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1 << 46;   // descriptor version; base offset 0, no swizzle
+    return d;
+}
+
+// kind::f16 instruction descriptor: FP32 accumulate, BF16 A and B, both
+// K-major, M = 128, N = n.
+__host__ __device__ constexpr unsigned umma_idesc_bf16(int n) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)(n >> 3) << 17) | ((128u >> 4) << 24);
+}
+
+__device__ __forceinline__ void tc_mma(unsigned tmem, uint64_t a, uint64_t b, unsigned idesc,
+                                       unsigned accumulate) {
+    asm volatile(
+        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
+}
+
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned mbar, unsigned parity) {
+    for (int it = 0; it < (1 << 22); ++it) {
+        unsigned done;
+        asm volatile(
+            "{\n.reg .pred q;\nmbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2;\n"
+            "selp.u32 %0, 1, 0, q;\n}\n"
+            : "=r"(done)
+            : "r"(mbar), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void tmem_ld32(unsigned taddr, unsigned (&r)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+        "%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+          "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+          "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+          "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+}
+
+__device__ __forceinline__ void tmem_ld1(unsigned taddr, unsigned& r) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];" : "=r"(r) : "r"(taddr));
+}
+
+// Strip u of the batch: image n, rows y0 .., columns x0 ..
+struct Strip {
+    int n, y0, x0;
+};
+__device__ __forceinline__ Strip strip_of(int u, int H, int W) {
+    const int sx = (W + TXC - 1) / TXC, sy = (H + TR - 1) / TR;
+    Strip s;
+    s.n = u / (sx * sy);
+    const int rem = u - s.n * sx * sy;
+    s.y0 = (rem / sx) * TR;
+    s.x0 = (rem % sx) * TXC;
+    return s;
+}
+
+// TMA: the halo of strip s into `halo` (four planes), completing on lbar.
+__device__ __forceinline__ void tma_strip(unsigned halo, unsigned lbar, const CUtensorMap* tmap,
+                                          const Strip& s) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(lbar),
+                 "r"(4 * PLANE_DATA)
+                 : "memory");
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+        asm volatile(
+            "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
+            "[%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(halo + j * PLANE),
+            "l"(reinterpret_cast<uint64_t>(tmap)), "r"(8 * j), "r"(s.x0 - 1), "r"(s.y0 - 1),
+            "r"(s.n), "r"(lbar)
+            : "memory");
+}
+
+// MODE 0: Y = ReLU(conv(X) + bias).  MODE 1: Y = conv(X) * [mask_src > 0].
+// MODE 2: u0 = f + conv(X) + bias[0] (one output channel of 16 MMA columns).
+// tmap: X as (32 channels, W, H, N) BF16, box (8, 130, TR + 2, 1).  status:
+// set to 1 if a wait timed out (the kernel then stops; results are invalid).
+// Warp-specialised: warp 4 (one lane) is the producer (TMA, MMA issue);
+// warps 0..3 drain the accumulators (warp w owns TMEM lanes 32w ..).  Strip
+// k uses halo buffer k % NSTAGE and TMEM set k & 1: lbar[k % NSTAGE] = halo
+// landed, mbar[k & 1] = MMAs done, tfree[k & 1] = accumulators drained (one
+// arrival per drain warp).  The halo of strip k + NSTAGE - 1 is requested as
+// soon as strip k - 1's MMAs are done, two strips ahead of its use.
+constexpr int TC_THREADS = 160;
+
+template <int MODE>
+__global__ void __launch_bounds__(TC_THREADS, 1) conv_tc_kernel(
+    const __grid_constant__ CUtensorMap tmap, const bf16* __restrict__ Wt,
+    const float* __restrict__ bias, const bf16* __restrict__ mask_src, bf16* __restrict__ Y,
+    const float* __restrict__ f, float* __restrict__ u0, int H, int W, int nunits,
+    int* __restrict__ status) {
+    constexpr int NO = tc_no<MODE>();
+    constexpr unsigned IDESC = umma_idesc_bf16(NO);
+    constexpr unsigned TSET = 256;   // TMEM columns per accumulator set (TR rows x NO <= 256)
+    static_assert(TR * C <= (int)TSET, "accumulator set");
+    extern __shared__ unsigned char tc_raw[];
+    unsigned char* tc_smem = reinterpret_cast<unsigned char*>(
+        (reinterpret_cast<uintptr_t>(tc_raw) + 1023) & ~(uintptr_t)1023);
+    unsigned char* halo = tc_smem;                                // NSTAGE buffers
+    unsigned char* wsm = tc_smem + NSTAGE * HALO_BYTES;           // [tap][plane][n] x 16 B
+    uint64_t* bars = reinterpret_cast<uint64_t*>(wsm + 9 * 4 * NO * 16);
+    unsigned* tslot = reinterpret_cast<unsigned*>(bars + NSTAGE + 4);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(tslot + 1);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const unsigned lbar0 = smem_addr(bars), mbar0 = lbar0 + 8 * NSTAGE, tfree0 = mbar0 + 16;
+    const unsigned hbase0 = smem_addr(halo), wbase = smem_addr(wsm);
+
+    for (int i = tid; i < 9 * NO * 4; i += blockDim.x) {
+        const int j = i & 3, n = (i >> 2) % NO, tap = (i >> 2) / NO;
+        *reinterpret_cast<uint4*>(wsm + ((tap * 4 + j) * NO + n) * 16) =
+            reinterpret_cast<const uint4*>(Wt)[i];
+    }
+    if (tid == 0) {
+        for (int i = 0; i < NSTAGE + 2; ++i)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(lbar0 + 8 * i));
+        for (int i = 0; i < 2; ++i)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 4;" ::"r"(tfree0 + 8 * i));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        *abort_flag = 0;
+    }
+    if (warp == 4) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(
+            smem_addr(tslot)));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const unsigned tmem = *tslot;
+    const int G = gridDim.x;
+    const int nmine = (int)blockIdx.x < nunits ? (nunits - 1 - (int)blockIdx.x) / G + 1 : 0;
+
+    if (warp == 4) {
+        if (lane == 0) {
+            // producer: halo loads and MMAs
+            for (int k = 0; k < NSTAGE && k < nmine; ++k)
+                tma_strip(hbase0 + k * HALO_BYTES, lbar0 + 8 * k, &tmap,
+                          strip_of(blockIdx.x + k * G, H, W));
+            const uint64_t bdesc0 = umma_sdesc(wbase, NO * 16, 128);
+            for (int k = 0; k < nmine; ++k) {
+                const int hb = k % NSTAGE, b = k & 1;
+                bool ok = mbar_wait_bounded(lbar0 + 8 * hb, (unsigned)((k / NSTAGE) & 1));
+                if (ok && k >= 2) ok = mbar_wait_bounded(tfree0 + 8 * b, (unsigned)(((k >> 1) - 1) & 1));
+                if (!ok || *abort_flag) {
+                    *abort_flag = 1;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint64_t adesc0 = umma_sdesc(hbase0 + hb * HALO_BYTES, PLANE, 128);
+                for (int r = 0; r < TR; ++r) {
+                    const unsigned d = tmem + b * TSET + (unsigned)(r * NO);
+#pragma unroll
+                    for (int tap = 0; tap < 9; ++tap) {
+                        const unsigned pix = (unsigned)((r + tap / 3) * HCL + tap % 3);
+#pragma unroll
+                        for (int kc = 0; kc < 2; ++kc)
+                            tc_mma(d, adesc0 + ((2 * kc * PLANE + pix * 16) >> 4),
+                                   bdesc0 + (((tap * 4 + 2 * kc) * NO * 16) >> 4), IDESC,
+                                   (tap | kc) != 0);
+                    }
+                }
+                asm volatile(
+                    "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                        mbar0 + 8 * b)
+                    : "memory");
+                // strip k - 1's MMAs done: its halo buffer takes strip k - 1 + NSTAGE
+                if (k >= 1 && k - 1 + NSTAGE < nmine) {
+                    if (!mbar_wait_bounded(mbar0 + 8 * ((k - 1) & 1), (unsigned)(((k - 1) >> 1) & 1))) {
+                        *abort_flag = 1;
+                        break;
+                    }
+                    const int hbo = (k - 1) % NSTAGE;
+                    tma_strip(hbase0 + hbo * HALO_BYTES, lbar0 + 8 * hbo, &tmap,
+                              strip_of(blockIdx.x + (k - 1 + NSTAGE) * G, H, W));
+                }
+            }
+        }
+    } else {
+        // drain warps
+        float bias_r[MODE == 0 ? C : 1];
+        if (MODE == 0) {
+#pragma unroll
+            for (int o = 0; o < C; ++o) bias_r[o] = bias[o];
+        }
+        for (int k = 0; k < nmine; ++k) {
+            const int b = k & 1;
+            if (!mbar_wait_bounded(mbar0 + 8 * b, (unsigned)((k >> 1) & 1)) || *abort_flag) {
+                *abort_flag = 1;
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const Strip s = strip_of(blockIdx.x + k * G, H, W);
+            const int gx = s.x0 + 32 * warp + lane;
+            const size_t img = (size_t)s.n * H * W;
+            const unsigned lanebase = tmem + b * TSET + ((unsigned)(32 * warp) << 16);
+            for (int r = 0; r < TR; ++r) {
+                const int gy = s.y0 + r;
+                if (MODE == 2) {
+                    unsigned v;
+                    tmem_ld1(lanebase + (unsigned)(r * NO), v);
+                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                    if (gy < H && gx < W) {
+                        const size_t pp = img + (size_t)gy * W + gx;
+                        u0[pp] = f[pp] + (__uint_as_float(v) + bias[0]);
+                    }
+                    continue;
+                }
+                unsigned v[32];
+                tmem_ld32(lanebase + (unsigned)(r * NO), v);
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                if (gy >= H || gx >= W) continue;
+                const size_t pi = (img + (size_t)gy * W + gx) * C;
+                __align__(16) bf16 out[C];
+                if (MODE == 0) {
+#pragma unroll
+                    for (int o = 0; o < C; ++o)
+                        out[o] = __float2bfloat16(fmaxf(__uint_as_float(v[o]) + bias_r[o], 0.0f));
+                } else {
+                    __align__(16) bf16 m[C];
+#pragma unroll
+                    for (int q4 = 0; q4 < 4; ++q4)
+                        reinterpret_cast<uint4*>(m)[q4] = reinterpret_cast<const uint4*>(mask_src + pi)[q4];
+#pragma unroll
+                    for (int o = 0; o < C; ++o)
+                        out[o] = __float2bfloat16(bf(m[o]) > 0.0f ? __uint_as_float(v[o]) : 0.0f);
+                }
+#pragma unroll
+                for (int q4 = 0; q4 < 4; ++q4)
+                    reinterpret_cast<uint4*>(Y + pi)[q4] = reinterpret_cast<const uint4*>(out)[q4];
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tfree0 + 8 * b) : "memory");
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (*abort_flag && tid == 0) atomicExch(status, 1);
+    if (warp == 4) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem));
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Host side.
+
+#ifndef CM_CNN_TC
+#define CM_CNN_TC 1
+#endif
 
 // Dynamic shared memory above 48 KB must be allowed per kernel.
 cudaError_t conv_setup() {
+    if (CM_CNN_TC) {
+        cudaError_t e = cudaSuccess;
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(conv_tc_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)tc_smem_bytes<0>());
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(conv_tc_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)tc_smem_bytes<1>());
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(conv_tc_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)tc_smem_bytes<2>());
+        if (e != cudaSuccess) return e;
+    }
     cudaError_t e = cudaFuncSetAttribute(conv_mid_kernel<0>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)conv_smem_bytes<0>());
@@ -608,13 +919,46 @@ cudaError_t conv_setup() {
     return e;
 }
 
+// The driver's tensor-map encoder, fetched once through the runtime.
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    });
+    return fn;
+}
+
+// TMA map of an activation tensor X (N x H x W x 32 BF16) with the halo box
+// (8 channels, 130 columns, 10 rows, 1 image) of the tcgen05 convolution.
+cudaError_t act_tensor_map(CUtensorMap* m, const bf16* X, int N, int H, int W) {
+    auto fn = tensor_map_encoder();
+    if (!fn) return cudaErrorNotSupported;
+    const cuuint64_t dims[4] = {(cuuint64_t)C, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)N};
+    const cuuint64_t strides[3] = {(cuuint64_t)C * sizeof(bf16), (cuuint64_t)W * C * sizeof(bf16),
+                                   (cuuint64_t)H * W * C * sizeof(bf16)};
+    const cuuint32_t box[4] = {8, (cuuint32_t)HCL, (cuuint32_t)HRW, 1};
+    const cuuint32_t es[4] = {1, 1, 1, 1};
+    const CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<bf16*>(X), dims, strides,
+                          box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
 struct Net {
     int device = 0;
     std::string err;
     float *P = nullptr, *G = nullptr, *M = nullptr, *V = nullptr;
     bf16 *wf = nullptr, *wb = nullptr, *w6p = nullptr;
     int step = 0;
-    int conv_grid = 0;      // persistent CTAs of the tensor-core convolutions
+    int conv_grid = 0;      // persistent CTAs of the mma.sync convolutions
+    int tc_grid = 0;        // persistent CTAs of the tcgen05 convolutions (one per SM)
+    int* status = nullptr;  // device: set when a tensor-core wait timed out
     // activations (capacity in pixels)
     size_t cap = 0;
     bf16* act[6] = {};      // act[1..5] = X1..X5
@@ -662,15 +1006,30 @@ int pack(Net* net, cudaStream_t st) {
 
 int forward(Net* net, const float* f, int N, int H, int W, float* u0, cudaStream_t st) {
     const size_t npx = (size_t)N * H * W;
-    const int ntiles = N * ((H + TH - 1) / TH) * ((W + TW - 1) / TW);
-    const int grid = std::min(ntiles, net->conv_grid);
     conv_in_kernel<<<(unsigned)((npx + 255) / 256), 256, 0, st>>>(f, net->P, net->act[1], N, H, W);
-    for (int l = 2; l <= 5; ++l)
-        conv_mid_kernel<0><<<grid, 128, conv_smem_bytes<0>(), st>>>(net->act[l - 1], net->wf + (l - 2) * MIDW,
-                                                 net->P + off_b(l), nullptr, net->act[l], nullptr,
-                                                 nullptr, H, W, ntiles);
-    conv_mid_kernel<2><<<grid, 128, conv_smem_bytes<2>(), st>>>(net->act[5], net->w6p, net->P + OFF_B6, nullptr,
-                                             nullptr, f, u0, H, W, ntiles);
+    if (CM_CNN_TC) {
+        const int nunits = N * ((H + TR - 1) / TR) * ((W + TXC - 1) / TXC);
+        const int grid = std::min(nunits, net->tc_grid);
+        CUtensorMap m;
+        for (int l = 2; l <= 5; ++l) {
+            NET_CUDA(act_tensor_map(&m, net->act[l - 1], N, H, W));
+            conv_tc_kernel<0><<<grid, TC_THREADS, tc_smem_bytes<0>(), st>>>(
+                m, net->wf + (l - 2) * MIDW, net->P + off_b(l), nullptr, net->act[l], nullptr,
+                nullptr, H, W, nunits, net->status);
+        }
+        NET_CUDA(act_tensor_map(&m, net->act[5], N, H, W));
+        conv_tc_kernel<2><<<grid, TC_THREADS, tc_smem_bytes<2>(), st>>>(
+            m, net->w6p, net->P + OFF_B6, nullptr, nullptr, f, u0, H, W, nunits, net->status);
+    } else {
+        const int ntiles = N * ((H + TH - 1) / TH) * ((W + TW - 1) / TW);
+        const int grid = std::min(ntiles, net->conv_grid);
+        for (int l = 2; l <= 5; ++l)
+            conv_mid_kernel<0><<<grid, 128, conv_smem_bytes<0>(), st>>>(
+                net->act[l - 1], net->wf + (l - 2) * MIDW, net->P + off_b(l), nullptr, net->act[l],
+                nullptr, nullptr, H, W, ntiles);
+        conv_mid_kernel<2><<<grid, 128, conv_smem_bytes<2>(), st>>>(
+            net->act[5], net->w6p, net->P + OFF_B6, nullptr, nullptr, f, u0, H, W, ntiles);
+    }
     NET_CUDA(cudaGetLastError());
     return CM_OK;
 }
@@ -694,9 +1053,18 @@ int backward(Net* net, const float* f, const float* us, int N, int H, int W, cud
         dw_mid_kernel<<<gm, 128, 0, st>>>(net->act[l - 1], net->dz[cur], net->part, N, H, W);
         reduce_parts_kernel<<<(DW_STRIDE + 255) / 256, 256, 0, st>>>(net->part, gm, DW_STRIDE,
                                                                      DW_STRIDE, net->G + off_w(l));
-        conv_mid_kernel<1><<<std::min(ntiles, net->conv_grid), 128, conv_smem_bytes<1>(), st>>>(
-            net->dz[cur], net->wb + (l - 2) * MIDW, nullptr, net->act[l - 1], net->dz[cur ^ 1],
-            nullptr, nullptr, H, W, ntiles);
+        if (CM_CNN_TC) {
+            const int nunits = N * ((H + TR - 1) / TR) * ((W + TXC - 1) / TXC);
+            CUtensorMap m;
+            NET_CUDA(act_tensor_map(&m, net->dz[cur], N, H, W));
+            conv_tc_kernel<1><<<std::min(nunits, net->tc_grid), TC_THREADS, tc_smem_bytes<1>(), st>>>(
+                m, net->wb + (l - 2) * MIDW, nullptr, net->act[l - 1], net->dz[cur ^ 1], nullptr,
+                nullptr, H, W, nunits, net->status);
+        } else {
+            conv_mid_kernel<1><<<std::min(ntiles, net->conv_grid), 128, conv_smem_bytes<1>(), st>>>(
+                net->dz[cur], net->wb + (l - 2) * MIDW, nullptr, net->act[l - 1], net->dz[cur ^ 1],
+                nullptr, nullptr, H, W, ntiles);
+        }
         cur ^= 1;
     }
     const int g1 = std::min(ntiles, DW_GRID);
@@ -739,6 +1107,17 @@ int net_forward_own(Net* net, const float* f, int N, int H, int W, cudaStream_t 
 
 const char* net_error(const Net* net) { return net->err.c_str(); }
 
+// After a synchronisation: CM_ERR_CUDA if a tensor-core wait timed out.
+int net_status(Net* net) {
+    int h = 0;
+    NET_CUDA(cudaMemcpy(&h, net->status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (h) {
+        net->err = "tensor-core convolution: a wait for the MMAs timed out";
+        return CM_ERR_CUDA;
+    }
+    return CM_OK;
+}
+
 }  // namespace cnn
 }  // namespace cm
 
@@ -769,7 +1148,10 @@ int cm_net_create(cm_ctx* ctx, cm_net** out) {
         int nsm = 0;
         e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, net->device);
         net->conv_grid = 4 * nsm;   // four resident CTAs per SM (shared memory, registers)
+        net->tc_grid = nsm;         // one CTA per SM (shared memory; one TMEM allocation)
     }
+    if (e == cudaSuccess) e = cudaMalloc(&net->status, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(net->status, 0, sizeof(int));
     if (e == cudaSuccess) e = cm::cnn::conv_setup();
     if (e == cudaSuccess)
         e = cudaMalloc(&net->part, (size_t)cm::cnn::DW_GRID * cm::cnn::DW_STRIDE * sizeof(float));
@@ -797,6 +1179,7 @@ void cm_net_destroy(cm_net* net) {
         if (p) cudaFree(p);
     if (net->wf) cudaFree(net->wf);
     if (net->w6p) cudaFree(net->w6p);
+    if (net->status) cudaFree(net->status);
     if (net->wb) cudaFree(net->wb);
     for (int i = 1; i <= 5; ++i)
         if (net->act[i]) cudaFree(net->act[i]);
@@ -844,6 +1227,8 @@ int cm_net_gradients(cm_net* net, const float* f, const float* ustar, int N, int
     rc = cm::cnn::backward(net, f, ustar, N, H, W, st);
     if (rc) return rc;
     NET_CUDA(cudaStreamSynchronize(st));
+    rc = cm::cnn::net_status(net);
+    if (rc) return rc;
     if (grad_host)
         NET_CUDA(cudaMemcpy(grad_host, net->G, cm::cnn::NPAR * sizeof(float), cudaMemcpyDeviceToHost));
     if (loss_host) {
@@ -876,6 +1261,8 @@ int cm_net_train_step(cm_net* net, const float* f, const float* ustar, int N, in
         NET_CUDA(cudaMemcpyAsync(&s, net->loss, sizeof(double), cudaMemcpyDeviceToHost, st));
         NET_CUDA(cudaStreamSynchronize(st));
         *loss_host = s / ((double)N * H * W);
+        rc = cm::cnn::net_status(net);
+        if (rc) return rc;
     }
     return CM_OK;
 }
