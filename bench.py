@@ -393,6 +393,42 @@ def main():
         e2e_t.append(time.perf_counter() - t0)
     e2e = statistics.mean(e2e_t)
 
+    # single-step mode (one step of Alg. 2 per block, kept if it lowers E_A):
+    # the plain solve to the same tolerance, timed the same way
+    opts1 = cm.default_options(ncolors=opts.ncolors, grid_points=opts.grid_points,
+                               golden_evals=opts.golden_evals, one_step=1)
+
+    def one_step_solve(fin, out):
+        _, st = cm.cm_solve(fin, ALPHA, KIND, levels=0, cycles=MAX_CYCLES, tol=TOL, u_out=out,
+                            options=opts1, ctx=ctx)
+        return st
+
+    one_step_solve(f, u)
+    torch.cuda.synchronize()
+    sec_one, st_one = timed_steps(one_step_solve)
+    one_step_res = {"s": sec_one, "cycles_to_tol": [s.cycles_run for s in st_one],
+                    "psnr_db": synth.psnr(u.cpu().numpy(), img.clean),
+                    "final_energy": st_one[-1].energy_final,
+                    "converged": bool(st_one[-1].converged),
+                    "vs_search_plain_time": sec_one / sec_plain}
+    # the single-step relative-change test stops far above the search's energy:
+    # also the cycles (and time) it needs to reach the searched solve's energy
+    n_long = 400
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    _, st_long = cm.cm_solve(f, ALPHA, KIND, levels=0, cycles=n_long, tol=0.0, u_out=u,
+                             options=opts1, ctx=ctx)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    per_cycle = e0.elapsed_time(e1) / 1e3 / n_long
+    target = st_plain[-1].energy_final
+    trace = st_long.trace()
+    hit = next((i for i, E in enumerate(trace) if E <= target), None)
+    one_step_res["to_search_energy"] = {
+        "target_energy": target, "cycles_run": n_long, "per_cycle_s": per_cycle,
+        "cycles_to_target": hit, "s_to_target": None if hit is None else hit * per_cycle,
+        "energy_after_run": trace[-1], "psnr_after_run_db": synth.psnr(u.cpu().numpy(), img.clean)}
+
     # dominant kernel: finest-level phase (b = 1), launched on the same stream
     state = u.clone()
     R = state.clone()
@@ -461,7 +497,7 @@ def main():
                     "d2h_bytes_per_step": 4 * N},
             "gpu_launches": int(sum(launches_per_solve)),
             "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks,
-            "b1_phase_ms": b1_ms, "batched": batched_res}
+            "b1_phase_ms": b1_ms, "batched": batched_res, "one_step": one_step_res}
     line["config"]["levels"] = L
     line["config"]["grid_points"] = opts.grid_points
     line["config"]["golden_evals"] = opts.golden_evals

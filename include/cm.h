@@ -65,6 +65,12 @@ typedef struct {
                             stopping test); 0: one cycle per launch sequence,
                             host stopping test (same results) */
     int max_trace;       /* entries of the energy trace kept in cm_stats (<= 4096) */
+    int one_step;        /* 1: instead of the search, every block takes one step of
+                            Alg. 2 (t = 0, c_0 = 0, eta = 1): c_1 = (c_1/2 + alpha f*) /
+                            (2 + alpha), f* the block mean of f - u, c_1/2 the plane-
+                            distance estimate (Eq. c-sol1; Prop. 2 for kind 1) on the
+                            finest level and 0 on coarser ones; c_1 is kept if it lowers
+                            E_A, else the block keeps 0 (two evaluations per block) */
 } cm_options;
 
 /* Solve statistics (host struct, filled by cm_solve). */
@@ -81,7 +87,7 @@ typedef struct {
 
 /* Default options: ncolors 4 (the paper's four-colour decomposition, Sec. 2.3), G 5, K 6
  * (the budget the autotuner picks on every tested workload: fastest time to tolerance at the
- * lowest final energy), paper_candidate 1, use_graph 1, max_trace 4096. */
+ * lowest final energy), paper_candidate 1, use_graph 1, max_trace 4096, one_step 0. */
 int cm_options_default(cm_options* opts /* host */);
 
 /* Create a context on CUDA device `device` (makes it current on this

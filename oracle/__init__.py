@@ -61,13 +61,13 @@ def lib():
                 "orc_local_energy": (d, [dp, dp, i, i, i, i, i, i, d, d, i]),
                 "orc_ring_size": (i, [i, i, i, i, i, i]),
                 "orc_paper_candidate": (d, [dp, dp, i, i, i, i, d, i]),
-                "orc_block_min": (d, [dp, dp, i, i, i, i, i, i, d, i, i, i, i, dp]),
+                "orc_block_min": (d, [dp, dp, i, i, i, i, i, i, d, i, i, i, i, i, i, dp]),
                 "orc_block_colour": (i, [i, i, i]),
                 "orc_auto_levels": (i, [i, i]),
-                "orc_phase": (i, [dp, dp, i, i, d, i, i, i, i, i, i, i, dp]),
-                "orc_level_sequential": (None, [dp, dp, i, i, d, i, i, i, i, i]),
-                "orc_cycle": (None, [dp, dp, i, i, d, i, i, i, i, i, i, i]),
-                "orc_solve": (i, [dp, i, i, d, i, i, i, d, dp, dp, i, i, i, i, i, dp, ip]),
+                "orc_phase": (i, [dp, dp, i, i, d, i, i, i, i, i, i, i, i, dp]),
+                "orc_level_sequential": (None, [dp, dp, i, i, d, i, i, i, i, i, i]),
+                "orc_cycle": (None, [dp, dp, i, i, d, i, i, i, i, i, i, i, i]),
+                "orc_solve": (i, [dp, i, i, d, i, i, i, d, dp, dp, i, i, i, i, i, i, dp, ip]),
                 "orc_num_threads": (i, []),
                 "orc_local_energy_batch": (None, [dp, dp, i, i, i, i, i, i, d, i, dp, i, dp]),
             }
@@ -147,13 +147,18 @@ def paper_candidate(u, f, r, c, alpha, kind) -> float:
     return lib().orc_paper_candidate(_dp(u), _dp(f), H, W, r, c, float(alpha), kind)
 
 
-def block_min(u, f, r0, c0, bh, bw, alpha, kind, G=DEFAULT_G, K=DEFAULT_K, use_paper=True):
-    """Returns (c, info) with info = dict(E_best, E_zero, c_fid, rho, S1, n_eval)."""
+def block_min(u, f, r0, c0, bh, bw, alpha, kind, G=DEFAULT_G, K=DEFAULT_K, use_paper=True,
+              one_step=False, finest=None):
+    """Returns (c, info) with info = dict(E_best, E_zero, c_fid, rho, S1, n_eval).
+    one_step: the paper's single step (Alg. 2, t = 0) kept if it lowers E_A;
+    finest: the block is on the finest level (default: a 1 x 1 block)."""
     u, f = _f64(u), _f64(f)
     H, W = u.shape
     info = np.zeros(6)
+    if finest is None:
+        finest = bh == 1 and bw == 1
     c = lib().orc_block_min(_dp(u), _dp(f), H, W, r0, c0, bh, bw, float(alpha), kind, G, K,
-                            int(use_paper), _dp(info))
+                            int(use_paper), int(one_step), int(finest), _dp(info))
     keys = ("E_best", "E_zero", "c_fid", "rho", "S1", "n_eval")
     return c, dict(zip(keys, info.tolist()))
 
@@ -166,7 +171,8 @@ def auto_levels(H, W) -> int:
     return lib().orc_auto_levels(H, W)
 
 
-def phase(u, f, alpha, kind, b, ncolors, k, G=DEFAULT_G, K=DEFAULT_K, use_paper=True):
+def phase(u, f, alpha, kind, b, ncolors, k, G=DEFAULT_G, K=DEFAULT_K, use_paper=True,
+          one_step=False):
     """One (level, colour) phase from state u; returns (u_new, c_per_block)."""
     u = _f64(u).copy()
     f = _f64(f)
@@ -174,31 +180,32 @@ def phase(u, f, alpha, kind, b, ncolors, k, G=DEFAULT_G, K=DEFAULT_K, use_paper=
     nb = ((H + b - 1) // b) * ((W + b - 1) // b)
     cs = np.zeros(nb)
     lib().orc_phase(_dp(u), _dp(f), H, W, float(alpha), kind, b, ncolors, k, G, K,
-                    int(use_paper), _dp(cs))
+                    int(use_paper), int(one_step), _dp(cs))
     return u, cs
 
 
-def level_sequential(u, f, alpha, kind, b, G=DEFAULT_G, K=DEFAULT_K, use_paper=True):
+def level_sequential(u, f, alpha, kind, b, G=DEFAULT_G, K=DEFAULT_K, use_paper=True,
+                     one_step=False):
     u = _f64(u).copy()
     f = _f64(f)
     H, W = u.shape
     lib().orc_level_sequential(_dp(u), _dp(f), H, W, float(alpha), kind, b, G, K,
-                               int(use_paper))
+                               int(use_paper), int(one_step))
     return u
 
 
 def cycle(u, f, alpha, kind, levels=0, ncolors=2, G=DEFAULT_G, K=DEFAULT_K, use_paper=True,
-          sequential=False):
+          sequential=False, one_step=False):
     u = _f64(u).copy()
     f = _f64(f)
     H, W = u.shape
     lib().orc_cycle(_dp(u), _dp(f), H, W, float(alpha), kind, levels, ncolors, G, K,
-                    int(use_paper), int(sequential))
+                    int(use_paper), int(one_step), int(sequential))
     return u
 
 
 def solve(f, alpha, kind, levels=0, cycles=20, tol=0.0, u0=None, ncolors=2, G=DEFAULT_G,
-          K=DEFAULT_K, use_paper=True, sequential=False):
+          K=DEFAULT_K, use_paper=True, sequential=False, one_step=False):
     """Alg. 3 outer loop.  Returns (u, trace, cycles_run, converged)."""
     f = _f64(f)
     H, W = f.shape
@@ -210,7 +217,8 @@ def solve(f, alpha, kind, levels=0, cycles=20, tol=0.0, u0=None, ncolors=2, G=DE
         u0a = _f64(u0)
         u0p = _dp(u0a)
     n = lib().orc_solve(_dp(f), H, W, float(alpha), kind, levels, cycles, float(tol), u0p,
-                        _dp(u), ncolors, G, K, int(use_paper), int(sequential), _dp(trace),
+                        _dp(u), ncolors, G, K, int(use_paper), int(one_step), int(sequential),
+                        _dp(trace),
                         ctypes.byref(conv))
     return u, trace[: n + 1], n, bool(conv.value)
 

@@ -325,7 +325,8 @@ typedef struct {
  *  (vi)  the result is the best of every evaluated point (tie rule above),
  *        so E_A(c) <= E_A(0): no block update raises F with the others fixed. */
 static blockres_t block_min(const double *u, const double *f, int H, int W, const block_t *A,
-                            double alpha, int kind, int G, int K, int use_paper) {
+                            double alpha, int kind, int G, int K, int use_paper, int one_step,
+                            int finest) {
     blockres_t res;
     double s = (double)(A->r1 - A->r0) * (double)(A->c1 - A->c0);
     double S1 = block_S1(u, f, W, A);
@@ -335,6 +336,26 @@ static blockres_t block_min(const double *u, const double *f, int H, int W, cons
     b.E = local_energy(u, H, W, A, 0.0, alpha, kind, S1);
     b.n_eval = 1;
     double E0 = b.E;
+    if (one_step) {
+        /* One step of Alg. 2 (t = 0, c_0 = 0, eta = 1): c_1 = (c_1/2 + alpha f*) /
+         * (2 + alpha), f* = c_fid the block's mean of f - u.  On the finest level
+         * c_1/2 is the plane-distance estimate (Eq. c-sol1; Prop. 2 for Gaussian
+         * curvature); on coarser levels READING: c_1/2 = 0 (the paper's coarse
+         * tangent-plane sets are not recoverable).  The block keeps c_1 only if
+         * it lowers E_A (tie rule as below), else 0. */
+        double c1 = finest && A->r1 - A->r0 == 1 && A->c1 - A->c0 == 1
+                        ? orc_paper_candidate(u, f, H, W, A->r0, A->c0, alpha, kind)
+                        : alpha * c_fid / (2.0 + alpha);
+        consider(&b, c1, local_energy(u, H, W, A, c1, alpha, kind, S1));
+        res.c = b.c;
+        res.E_best = b.E;
+        res.E_zero = E0;
+        res.c_fid = c_fid;
+        res.rho = 0.0;
+        res.S1 = S1;
+        res.n_eval = b.n_eval;
+        return res;
+    }
     if (use_paper && A->r1 - A->r0 == 1 && A->c1 - A->c0 == 1) {
         double cp = orc_paper_candidate(u, f, H, W, A->r0, A->c0, alpha, kind);
         consider(&b, cp, local_energy(u, H, W, A, cp, alpha, kind, S1));
@@ -382,10 +403,10 @@ static blockres_t block_min(const double *u, const double *f, int H, int W, cons
 }
 
 double orc_block_min(const double *u, const double *f, int H, int W, int r0, int c0, int bh,
-                     int bw, double alpha, int kind, int G, int K, int use_paper,
-                     double *info /* nullable: E_best, E_zero, c_fid, rho, S1, n_eval */) {
+                     int bw, double alpha, int kind, int G, int K, int use_paper, int one_step,
+                     int finest, double *info /* nullable: E_best, E_zero, c_fid, rho, S1, n_eval */) {
     block_t A = {r0, r0 + bh > H ? H : r0 + bh, c0, c0 + bw > W ? W : c0 + bw};
-    blockres_t res = block_min(u, f, H, W, &A, alpha, kind, G, K, use_paper);
+    blockres_t res = block_min(u, f, H, W, &A, alpha, kind, G, K, use_paper, one_step, finest);
     if (info) {
         info[0] = res.E_best; info[1] = res.E_zero; info[2] = res.c_fid;
         info[3] = res.rho; info[4] = res.S1; info[5] = (double)res.n_eval;
@@ -422,7 +443,7 @@ int orc_auto_levels(int H, int W) {
  * Returns the number of blocks; cs (nullable) receives each block's c in
  * block raster order (entries of other colours are left untouched). */
 int orc_phase(double *u, const double *f, int H, int W, double alpha, int kind, int b,
-              int ncolors, int k, int G, int K, int use_paper, double *cs) {
+              int ncolors, int k, int G, int K, int use_paper, int one_step, double *cs) {
     int nbi = (H + b - 1) / b, nbj = (W + b - 1) / b;
     int nb = nbi * nbj;
     double *cloc = (double *)malloc(sizeof(double) * (size_t)nb);
@@ -434,7 +455,7 @@ int orc_phase(double *u, const double *f, int H, int W, double alpha, int kind, 
         if (orc_block_colour(bi, bj, ncolors) != k) continue;
         block_t A = {bi * b, (bi + 1) * b > H ? H : (bi + 1) * b,
                      bj * b, (bj + 1) * b > W ? W : (bj + 1) * b};
-        blockres_t res = block_min(u, f, H, W, &A, alpha, kind, G, K, use_paper);
+        blockres_t res = block_min(u, f, H, W, &A, alpha, kind, G, K, use_paper, one_step, b == 1);
         cloc[idx] = res.c;
         ++count;
     }
@@ -454,13 +475,13 @@ int orc_phase(double *u, const double *f, int H, int W, double alpha, int kind, 
  * applied before the next is solved (Alg. 1 generalised to patches).  Every
  * single update satisfies F(u + c phi_A) <= F(u). */
 void orc_level_sequential(double *u, const double *f, int H, int W, double alpha, int kind,
-                          int b, int G, int K, int use_paper) {
+                          int b, int G, int K, int use_paper, int one_step) {
     int nbi = (H + b - 1) / b, nbj = (W + b - 1) / b;
     for (int bi = 0; bi < nbi; ++bi)
         for (int bj = 0; bj < nbj; ++bj) {
             block_t A = {bi * b, (bi + 1) * b > H ? H : (bi + 1) * b,
                          bj * b, (bj + 1) * b > W ? W : (bj + 1) * b};
-            blockres_t res = block_min(u, f, H, W, &A, alpha, kind, G, K, use_paper);
+            blockres_t res = block_min(u, f, H, W, &A, alpha, kind, G, K, use_paper, one_step, b == 1);
             for (int r = A.r0; r < A.r1; ++r)
                 for (int c = A.c0; c < A.c1; ++c) u[(size_t)r * W + c] += res.c;
         }
@@ -469,15 +490,15 @@ void orc_level_sequential(double *u, const double *f, int H, int W, double alpha
 /* One cycle: fine-to-coarse half V-cycle (Sec. 2.2: the coarse-to-fine half
  * is omitted), colours in ascending order on each level (Alg. 3). */
 void orc_cycle(double *u, const double *f, int H, int W, double alpha, int kind, int levels,
-               int ncolors, int G, int K, int use_paper, int sequential) {
+               int ncolors, int G, int K, int use_paper, int one_step, int sequential) {
     if (levels <= 0) levels = orc_auto_levels(H, W);
     for (int j = 1; j <= levels; ++j) {
         int b = 1 << (j - 1);
         if (sequential) {
-            orc_level_sequential(u, f, H, W, alpha, kind, b, G, K, use_paper);
+            orc_level_sequential(u, f, H, W, alpha, kind, b, G, K, use_paper, one_step);
         } else {
             for (int k = 0; k < ncolors; ++k)
-                orc_phase(u, f, H, W, alpha, kind, b, ncolors, k, G, K, use_paper, NULL);
+                orc_phase(u, f, H, W, alpha, kind, b, ncolors, k, G, K, use_paper, one_step, NULL);
         }
     }
 }
@@ -489,7 +510,7 @@ void orc_cycle(double *u, const double *f, int H, int W, double alpha, int kind,
  * F(u_0), F(u_1), ...  Returns the number of cycles run; *converged is set. */
 int orc_solve(const double *f, int H, int W, double alpha, int kind, int levels, int cycles,
               double tol, const double *u0, double *u_out, int ncolors, int G, int K,
-              int use_paper, int sequential, double *trace, int *converged) {
+              int use_paper, int one_step, int sequential, double *trace, int *converged) {
     size_t N = (size_t)H * W;
     if (u0) memcpy(u_out, u0, N * sizeof(double));
     else memcpy(u_out, f, N * sizeof(double));
@@ -497,7 +518,8 @@ int orc_solve(const double *f, int H, int W, double alpha, int kind, int levels,
     if (trace) trace[0] = Eprev;
     int l = 0, conv = 0;
     while (l < cycles) {
-        orc_cycle(u_out, f, H, W, alpha, kind, levels, ncolors, G, K, use_paper, sequential);
+        orc_cycle(u_out, f, H, W, alpha, kind, levels, ncolors, G, K, use_paper, one_step,
+                  sequential);
         ++l;
         double E = orc_energy(u_out, f, H, W, alpha, kind);
         if (trace) trace[l] = E;

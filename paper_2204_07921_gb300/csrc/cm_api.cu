@@ -26,7 +26,7 @@ struct GraphKey {
     const float* S;
     const float* R;
     const float* f;
-    int H, W, kind, levels, ncolors, G, K, use_paper;
+    int H, W, kind, levels, ncolors, G, K, use_paper, one_step;
     float alpha;
     double tol;
     int cycles, trace_cap;
@@ -152,6 +152,7 @@ int check_opts(cm_ctx* ctx, const cm_options& o) {
     if (o.golden_evals < 2 || o.golden_evals > 1024)
         return fail(ctx, CM_ERR_INVALID, "golden_evals must be 2..1024");
     if (o.max_trace < 0 || o.max_trace > 4096) return fail(ctx, CM_ERR_INVALID, "max_trace 0..4096");
+    if (o.one_step != 0 && o.one_step != 1) return fail(ctx, CM_ERR_INVALID, "one_step must be 0 or 1");
     return CM_OK;
 }
 
@@ -171,6 +172,7 @@ cm::PhaseArgs phase_args(const float* S, float* R, const float* f, int H, int W,
     a.G = o.grid_points;
     a.K = o.golden_evals;
     a.use_paper = o.paper_candidate;
+    a.one_step = o.one_step;
     a.c_out = nullptr;
     return a;
 }
@@ -303,6 +305,7 @@ int cm_options_default(cm_options* o) {
     o->paper_candidate = 1;
     o->use_graph = 1;
     o->max_trace = 4096;
+    o->one_step = 0;
     return CM_OK;
 }
 
@@ -483,6 +486,7 @@ int cm_solve(cm_ctx* ctx, const float* f, int H, int W, float alpha, int kind, i
         key.G = o.grid_points;
         key.K = o.golden_evals;
         key.use_paper = o.paper_candidate;
+        key.one_step = o.one_step;
         key.alpha = alpha;
         key.tol = tol;
         key.cycles = cycles;

@@ -37,6 +37,7 @@ struct PhaseArgs {
     int colour;
     int G, K;         // block-search budget
     int use_paper;    // paper's one-step candidate on the finest level
+    int one_step = 0; // the paper's single step per block instead of the search
     float* c_out;     // nullable: per-block corrections
     const int* active = nullptr;   // nullable: kernels return at once when *active == 0
 };

@@ -219,7 +219,7 @@ __global__ void __launch_bounds__(128, CM_B1_MIN_BLOCKS) phase_b1_kernel(const f
     const float up = w25[12];
     const float S1 = up - f[p];
     float cp = 0.0f;
-    if (use_paper) {
+    if (use_paper || sp.one_step) {
         float w[9];
         nb_window<0, 0>(w25, w);
         cp = paper_candidate<KIND>(w, -S1, sp.alpha);
@@ -261,7 +261,8 @@ __global__ void __launch_bounds__(128, CM_B1_MIN_BLOCKS) phase_b1_kernel(const f
             acc += nb_eval<KIND, 1, 1>(n7, cc);
             return acc;
         };
-        cbest = block_search_1site(ring_fast, sp, 1.0f, S1, use_paper != 0, cp);
+        cbest = sp.one_step ? block_search_onestep(ring_fast, sp, 1.0f, S1, cp)
+                            : block_search_1site(ring_fast, sp, 1.0f, S1, use_paper != 0, cp);
     } else {
         // Border pixel: clamping may duplicate p inside a neighbour's window;
         // evaluate every in-image ring pixel from the shifted 5x5 window.
@@ -292,7 +293,8 @@ __global__ void __launch_bounds__(128, CM_B1_MIN_BLOCKS) phase_b1_kernel(const f
                 }
             return acc;
         };
-        cbest = block_search_1site(ring, sp, 1.0f, S1, use_paper != 0, cp);
+        cbest = sp.one_step ? block_search_onestep(ring, sp, 1.0f, S1, cp)
+                            : block_search_1site(ring, sp, 1.0f, S1, use_paper != 0, cp);
     }
     R[p] = up + cbest;
     if (c_out) c_out[p] = cbest;
@@ -300,6 +302,7 @@ __global__ void __launch_bounds__(128, CM_B1_MIN_BLOCKS) phase_b1_kernel(const f
 
 cudaError_t launch_phase_b1(const PhaseArgs& A, cudaStream_t st) {
     SearchParams sp{A.alpha, A.G, A.K};
+    sp.one_step = A.one_step;
     auto go = [&](auto kern, int TW, int TH) {
         dim3 grid((A.W + TW - 1) / TW, (A.H + TH - 1) / TH);
         return launch_k(kern, grid, dim3(128), st, 1, A.S, A.R, A.f, A.H, A.W, sp, A.colour,

@@ -116,11 +116,14 @@ __device__ __forceinline__ void warp_group_block(const float* __restrict__ S,
         return v;
     };
     const float s = blk_on ? (float)(bh * bw) : 1.0f;
+    const float S1b = blk_on ? s1 : 0.0f;
     float cbest;
-    if constexpr (LIGHT)
-        cbest = block_search_1site(ring, sp, s, blk_on ? s1 : 0.0f, false, 0.0f);
+    if (sp.one_step)
+        cbest = block_search_onestep(ring, sp, s, S1b, fbs_step(sp, s, S1b));
+    else if constexpr (LIGHT)
+        cbest = block_search_1site(ring, sp, s, S1b, false, 0.0f);
     else
-        cbest = block_search(ring, sp, s, blk_on ? s1 : 0.0f, false, 0.0f);
+        cbest = block_search(ring, sp, s, S1b, false, 0.0f);
     if (!blk_on) return;
     for_block_pixels(lane, GT, r0, c0, bh, bw, lb, bw == b, W,
                      [&](size_t p) { R[p] = S[p] + cbest; });
@@ -333,7 +336,10 @@ __global__ void __launch_bounds__(128, CM_B2_MINB) phase_b2_kernel(
         t += __shfl_xor_sync(0xffffffffu, t, 2);
         return t;
     };
-    const float cbest = block_search_1site(ring, sp, blk_on ? 4.0f : 1.0f, s1, false, 0.0f);
+    const float sb = blk_on ? 4.0f : 1.0f;
+    const float cbest = sp.one_step
+                            ? block_search_onestep(ring, sp, sb, s1, fbs_step(sp, sb, s1))
+                            : block_search_1site(ring, sp, sb, s1, false, 0.0f);
     if (!blk_on) return;
     R[p] = v[2][2] + cbest;
     if (c_out && q == 0) c_out[(size_t)bi * nbj + bj] = cbest;
@@ -661,7 +667,7 @@ __global__ void __launch_bounds__(CT) phase_coarse_kernel(
 template <int KIND, int CT, int Q, int RPT>
 static cudaError_t launch_coarse(const PhaseArgs& A, const float* partials, float* cj, int nact,
                                  int spec, int dmax, cudaStream_t st) {
-    SearchParams sp{A.alpha, A.G, A.K, spec, dmax};
+    SearchParams sp{A.alpha, A.G, A.K, spec, dmax, A.one_step};
     return launch_k(phase_coarse_kernel<KIND, CT, Q, RPT>, dim3(nact * Q), dim3(CT), st, Q, A.S,
                     partials, cj, A.H, A.W, sp, A.lb, A.ncolors, A.colour, A.c_out, A.active);
 }
@@ -763,6 +769,7 @@ template <int KIND, int GT, int RPT>
 static cudaError_t launch_warp(const PhaseArgs& A, int nact, cudaStream_t st) {
     constexpr int GPC = 128 / GT;
     SearchParams sp{A.alpha, A.G, A.K};
+    sp.one_step = A.one_step;
     return launch_k(phase_warp_kernel<KIND, GT, RPT>, dim3((nact + GPC - 1) / GPC), dim3(128), st,
                     1, A.S, A.R, A.f, A.H, A.W, sp, A.lb, A.ncolors, A.colour, A.c_out, A.active);
 }
@@ -770,6 +777,7 @@ static cudaError_t launch_warp(const PhaseArgs& A, int nact, cudaStream_t st) {
 template <int KIND, int CT, int Q, int RPT>
 static cudaError_t launch_cluster(const PhaseArgs& A, int nact, cudaStream_t st) {
     SearchParams sp{A.alpha, A.G, A.K};
+    sp.one_step = A.one_step;
     return launch_k(phase_cluster_kernel<KIND, CT, Q, RPT>, dim3(nact * Q), dim3(CT), st, 1, A.S,
                     A.R, A.f, A.H, A.W, sp, A.lb, A.ncolors, A.colour, A.c_out, A.active);
 }
@@ -784,7 +792,8 @@ static cudaError_t launch_blocks_kind(const PhaseArgs& A, cudaStream_t st) {
         case 1:
             if (CM_B2_FAST)
                 return launch_k(phase_b2_kernel<KIND>, dim3((nact + 31) / 32), dim3(128), st, 1,
-                                A.S, A.R, A.f, A.H, A.W, SearchParams{A.alpha, A.G, A.K},
+                                A.S, A.R, A.f, A.H, A.W,
+                                SearchParams{A.alpha, A.G, A.K, 1, 4, A.one_step},
                                 A.ncolors, A.colour, A.c_out, A.active);
             return launch_warp<KIND, CM_B2_GT, 16 / CM_B2_GT>(A, nact, st);
         case 2: return launch_warp<KIND, CM_B4_GT, 32 / CM_B4_GT>(A, nact, st);

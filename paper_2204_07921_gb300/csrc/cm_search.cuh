@@ -17,9 +17,36 @@ struct SearchParams {
     float alpha;
     int G;          // grid points (odd)
     int K;          // golden-section evaluations
-    int spec = 1;   // block_search_rounds: speculate the first golden pair
-    int dmax = 4;   // block_search_rounds: golden steps per round (1..4)
+    int spec = 1;       // block_search_rounds: speculate the first golden pair
+    int dmax = 4;       // block_search_rounds: golden steps per round (1..4)
+    int one_step = 0;   // 1: the paper's single step instead of the search
 };
+
+// One step of Alg. 2 from c_0 = 0 (t = 0, eta = 1) on a block with c_1/2 = 0:
+// c_1 = alpha f* / (2 + alpha), f* = c_fid the block mean of f - u (the
+// finest level uses the plane-distance estimate for c_1/2 instead).
+__device__ __forceinline__ float fbs_step(const SearchParams& p, float s, float S1) {
+    const float c_fid = -S1 / s;
+    return p.alpha * c_fid / (2.0f + p.alpha);
+}
+
+// The single-step mode: the block keeps c1 if it lowers E_A, else 0 (two
+// evaluations; the tie rule of the search).
+template <class Ring>
+__device__ __forceinline__ float block_search_onestep(Ring&& ring, const SearchParams& p, float s,
+                                                      float S1, float c1) {
+    const float c_fid = -S1 / s;
+    const float half_as = 0.5f * p.alpha * s;
+    auto energy = [&](float c, float rk) {
+        const float t = c - c_fid;
+        return fmaf(half_as * t, t, rk);
+    };
+    Best best;
+    best.c = 0.0f;
+    best.E = energy(0.0f, ring(0.0f));
+    consider(best, c1, energy(c1, ring(c1)));
+    return best.c;
+}
 
 // ring(c) returns the group-uniform sum over the block's ring.  The
 // fidelity part is carried as alpha s/2 (c - c_fid)^2, which differs from the
@@ -216,6 +243,15 @@ __device__ __forceinline__ float block_search_batched(RingV&& ringv, const Searc
     float cs[MB], rk[MB];
 #pragma unroll
     for (int j = 0; j < MB; ++j) cs[j] = 0.0f;
+    if (p.one_step) {
+        cs[1] = fbs_step(p, s, S1);
+        ringv(cs, 2, rk);
+        Best b1;
+        b1.c = 0.0f;
+        b1.E = energy(0.0f, rk[0]);
+        consider(b1, cs[1], energy(cs[1], rk[1]));
+        return b1.c;
+    }
     cs[1] = c_fid;
     ringv(cs, 2, rk);
     Best best;
@@ -368,6 +404,15 @@ __device__ __forceinline__ float block_search_rounds(RoundFn&& round, const Sear
     const int mid = (p.G - 1) / 2;
     const int ng = p.G - 1;                    // grid points other than c_fid
     const bool spec = p.spec && ng + 2 * p.G <= 16;
+    if (p.one_step) {
+        const float c1 = fbs_step(p, s, S1);
+        const float t1 = round(lane == 1 ? c1 : 0.0f, 2);
+        Best b1;
+        b1.c = 0.0f;
+        b1.E = energy(0.0f, __shfl_sync(FULL, t1, 0));
+        consider(b1, c1, energy(c1, __shfl_sync(FULL, t1, 2)));
+        return b1.c;
+    }
     // round 1: c = 0, c_fid
     float mine = lane == 1 ? c_fid : 0.0f;
     float tot = round(mine, 2);

@@ -45,7 +45,7 @@ def energy_scale(u, f, r0, c0, bh, bw, c, alpha, kind, c_fid):
 
 
 def compare_phase(u, f, c_gpu_blocks, alpha, kind, b, ncolors, k, c_orc_blocks, sample=None,
-                  G=G_DEF, K=K_DEF, use_paper=True):
+                  G=G_DEF, K=K_DEF, use_paper=True, one_step=False):
     """Compare per-block shifts of one phase.  c_*_blocks: dict (bi, bj) -> c.
     Returns (n_blocks, n_match, n_tie, list_of_failures)."""
     H, W = u.shape
@@ -60,14 +60,14 @@ def compare_phase(u, f, c_gpu_blocks, alpha, kind, b, ncolors, k, c_orc_blocks, 
             co = float(c_orc_blocks[(bi, bj)])
         else:
             co, _ = oracle.block_min(u, f, r0, c0, bh, bw, alpha, kind, G=G, K=K,
-                                     use_paper=use_paper)
+                                     use_paper=use_paper, one_step=one_step, finest=(b == 1))
         if abs(cg - co) <= C_TOL:
             match += 1
             continue
         Eg = oracle.local_energy(u, f, r0, c0, bh, bw, cg, alpha, kind)
         Eo = oracle.local_energy(u, f, r0, c0, bh, bw, co, alpha, kind)
         _, info = oracle.block_min(u, f, r0, c0, bh, bw, alpha, kind, G=G, K=K,
-                                   use_paper=use_paper)
+                                   use_paper=use_paper, one_step=one_step, finest=(b == 1))
         scale = max(energy_scale(u, f, r0, c0, bh, bw, cg, alpha, kind, info["c_fid"]),
                     energy_scale(u, f, r0, c0, bh, bw, co, alpha, kind, info["c_fid"]))
         if Eg - Eo <= TIE_REL * scale:

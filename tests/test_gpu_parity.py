@@ -69,28 +69,28 @@ def test_curvature_parity(kind):
     assert np.all(np.abs(kg - ko) <= bound)
 
 
-def gpu_phase(u, f, alpha, kind, b, ncolors, k, G=G_DEF, K=K_DEF, use_paper=1):
+def gpu_phase(u, f, alpha, kind, b, ncolors, k, G=G_DEF, K=K_DEF, use_paper=1, one_step=0):
     H, W = u.shape
     S = to_dev(u)
     R = S.clone()
     nb = ((H + b - 1) // b) * ((W + b - 1) // b)
     cbuf = torch.full((nb,), float("nan"), device=DEV)
     opts = cm.default_options(ncolors=ncolors, grid_points=G, golden_evals=K,
-                              paper_candidate=use_paper)
+                              paper_candidate=use_paper, one_step=one_step)
     cm.cm_phase(S, R, to_dev(f), alpha, kind, b, k, options=opts, c_out=cbuf)
     torch.cuda.synchronize()
     return host(R), host(cbuf)
 
 
-def check_phase(u, f, alpha, kind, b, ncolors, k, sample=None):
+def check_phase(u, f, alpha, kind, b, ncolors, k, sample=None, one_step=False):
     """GPU phase from state u vs oracle; returns (n, match, tie, fails)."""
     H, W = u.shape
-    Rg, cg = gpu_phase(u, f, alpha, kind, b, ncolors, k)
+    Rg, cg = gpu_phase(u, f, alpha, kind, b, ncolors, k, one_step=int(one_step))
     nbj = (W + b - 1) // b
     cgd, cod = {}, {}
     if sample is None:
         _, co = oracle.phase(u.astype(np.float64), f.astype(np.float64), alpha, kind, b,
-                             ncolors, k)
+                             ncolors, k, one_step=one_step)
     for bi, bj, r0, c0, bh, bw in blocks_of_colour(H, W, b, ncolors, k):
         if sample is not None and (bi, bj) not in sample:
             continue
@@ -109,7 +109,7 @@ def check_phase(u, f, alpha, kind, b, ncolors, k, sample=None):
             mask[r0:r0 + bh, c0:c0 + bw] = True
         np.testing.assert_array_equal(Rg[~mask], u[~mask])
     return compare_phase(u.astype(np.float64), f.astype(np.float64), cgd, alpha, kind, b,
-                         ncolors, k, cod, sample=sample)
+                         ncolors, k, cod, sample=sample, one_step=one_step)
 
 
 def levels_for(H, W):
@@ -427,3 +427,85 @@ def test_device_loop_matches_host_loop(shape, cycles, tol, max_trace):
         np.testing.assert_array_equal(ua, f)
         assert sa.trace_len == 1
     assert sa.trace_len == min(sa.cycles_run, max_trace) + 1
+
+
+# ---------------------------------------------------------------------------
+# Single-step mode (one step of Alg. 2 per block, kept if it lowers E_A).
+
+@pytest.mark.parametrize("shape", [(67, 45), (130, 97), (300, 260)])
+@pytest.mark.parametrize("kind", [cm.MEAN, cm.GAUSS])
+def test_one_step_phase_parity(shape, kind):
+    """Every level and colour of the direct phase kernels in single-step
+    mode against the oracle's single-step phase."""
+    H, W = shape
+    img = synth.piecewise_image(H, W, 700 + H + W, 6, 0.08)
+    f = img.f
+    u = oracle.cycle(f.astype(np.float64), f.astype(np.float64), 20.0, kind,
+                     levels=1).astype(np.float32)
+    tot = dict(n=0, match=0, tie=0)
+    fails = []
+    for b in levels_for(H, W):
+        for k in range(4):
+            n, m, t, fl = check_phase(u, f, 20.0, kind, b, 4, k, one_step=True)
+            tot["n"] += n
+            tot["match"] += m
+            tot["tie"] += t
+            fails += fl
+    print(f"\none-step {shape} kind={kind}: {tot}")
+    assert not fails, fails[:5]
+    assert tot["tie"] <= max(2, 0.01 * tot["n"])
+
+
+@pytest.mark.parametrize("kind", [cm.MEAN, cm.GAUSS])
+def test_one_step_coarse_levels(kind):
+    """The coarse path (tile sums, rounds kernel, deferred apply) in single-
+    step mode: R = S + c and each colour's c against the oracle."""
+    H, W = 300, 260
+    img = synth.piecewise_image(H, W, 4343, 12, 0.08)
+    f = img.f
+    u, _ = run_solve(f, 20.0, kind, 1)
+    opts = cm.default_options(one_step=1)
+    fails, tot = [], 0
+    for b in (64, 128):
+        nbi, nbj = (H + b - 1) // b, (W + b - 1) // b
+        cbuf = torch.full((nbi * nbj,), float("nan"), device=DEV)
+        S = to_dev(u)
+        R = torch.empty_like(S)
+        cm.cm_level(S, R, to_dev(f), 20.0, kind, b, options=opts, c_out=cbuf)
+        torch.cuda.synchronize()
+        cg, Rg = host(cbuf), host(R)
+        for k in range(4):
+            state = u.copy()
+            for kk in range(k):
+                for bi, bj, r0, c0, bh, bw in blocks_of_colour(H, W, b, 4, kk):
+                    state[r0:r0 + bh, c0:c0 + bw] += np.float32(cg[bi * nbj + bj])
+            cgd = {(bi, bj): cg[bi * nbj + bj] for bi, bj, *_ in blocks_of_colour(H, W, b, 4, k)}
+            n, m, t, fl = compare_phase(state.astype(np.float64), f.astype(np.float64), cgd,
+                                        20.0, kind, b, 4, k, {}, one_step=True)
+            tot += n
+            fails += fl
+        for bi in range(nbi):
+            for bj in range(nbj):
+                blk = (slice(bi * b, min((bi + 1) * b, H)), slice(bj * b, min((bj + 1) * b, W)))
+                np.testing.assert_array_equal(Rg[blk], u[blk] + np.float32(cg[bi * nbj + bj]))
+    assert tot > 0
+    assert not fails, fails[:5]
+
+
+@pytest.mark.parametrize("kind", [cm.MEAN, cm.GAUSS])
+def test_one_step_solve_vs_oracle(kind):
+    """A 20-cycle single-step solve of the 64 x 64 workload: the energy the
+    GPU reports equals the oracle's FP64 energy of the GPU's result, and the
+    oracle's own single-step solve reaches the same energy to 1e-3."""
+    img = synth.single_64()
+    f = img.f
+    opts = cm.default_options(one_step=1)
+    u, st = cm.cm_solve(to_dev(f), 20.0, kind, cycles=20, tol=0.0, options=opts)
+    torch.cuda.synchronize()
+    ug = host(u)
+    Eo = oracle.energy(ug.astype(np.float64), f.astype(np.float64), 20.0, kind)
+    assert st.energy_final == pytest.approx(Eo, rel=2e-6)
+    uo, trace, n, _ = oracle.solve(f.astype(np.float64), 20.0, kind, cycles=20, ncolors=4,
+                                   one_step=True)
+    assert st.energy_final == pytest.approx(trace[-1], rel=1e-3)
+    assert st.energy_final < st.energy_initial

@@ -255,3 +255,74 @@ def test_auto_levels():
     assert oracle.auto_levels(1, 100) == 1
     assert oracle.auto_levels(3, 3) == 1
     assert oracle.auto_levels(4, 9) == 2
+
+
+# ---------------------------------------------------------------------------
+# Single-step mode (one step of Alg. 2 per block, kept if it lowers E_A).
+
+def _fbs_by_brute_force(c_fid, alpha):
+    """argmin_c alpha/2 (c - c_fid)^2 + c^2 (the proximal step of Alg. 2 with
+    c_1/2 = 0, eta = 1), located on a fine grid, independent of any formula."""
+    lo, hi = min(0.0, c_fid) - 1.0, max(0.0, c_fid) + 1.0
+    for _ in range(4):
+        g = np.linspace(lo, hi, 2001)
+        q = 0.5 * alpha * (g - c_fid) ** 2 + g ** 2
+        i = int(np.argmin(q))
+        step = g[1] - g[0]
+        lo, hi = g[max(i - 1, 0)] - step, g[min(i + 1, 2000)] + step
+    return g[i]
+
+
+@pytest.mark.parametrize("kind", KINDS)
+@pytest.mark.parametrize("b", [1, 2, 4, 8])
+def test_one_step_picks_zero_or_the_step_and_never_raises_energy(kind, b):
+    H, W = 24, 28
+    u = rand_img(H, W, 300 + b)
+    f = u + 0.08 * np.random.default_rng(400 + b).normal(size=(H, W))
+    alpha = 12.0
+    n_step = 0
+    for bi, bj, r0, c0, bh, bw in blocks_of(H, W, b):
+        c, info = oracle.block_min(u, f, r0, c0, bh, bw, alpha, kind, one_step=True,
+                                   finest=(b == 1))
+        assert info["n_eval"] == 2
+        assert info["E_best"] <= info["E_zero"]
+        if b == 1:
+            c1 = oracle.paper_candidate(u, f, r0, c0, alpha, kind)
+        else:
+            c1 = _fbs_by_brute_force(info["c_fid"], alpha)
+        E1 = oracle.local_energy(u, f, r0, c0, bh, bw, c1, alpha, kind)
+        if c == 0.0:
+            assert E1 >= info["E_zero"] - 1e-9 * abs(info["E_zero"])
+        else:
+            n_step += 1
+            assert c == pytest.approx(c1, abs=1e-6)
+            assert E1 <= info["E_zero"] + 1e-9 * abs(info["E_zero"])
+    assert n_step > 0
+
+
+def test_one_step_alpha_limits():
+    """Large alpha: the step tends to the block's fidelity mean c_fid and is
+    taken; small alpha: the step tends to 0."""
+    H, W = 16, 16
+    u = np.full((H, W), 0.5)
+    f = u.copy()
+    f[4:8, 4:8] += 0.3
+    c_big, info = oracle.block_min(u, f, 4, 4, 4, 4, 1e6, oracle.MEAN, one_step=True)
+    assert c_big == pytest.approx(info["c_fid"], rel=1e-5)
+    assert info["c_fid"] == pytest.approx(0.3)
+    c_small, _ = oracle.block_min(u, f, 4, 4, 4, 4, 1e-6, oracle.MEAN, one_step=True)
+    assert abs(c_small) < 1e-6
+
+
+@pytest.mark.parametrize("kind", KINDS)
+def test_one_step_sequential_levels_never_raise_energy(kind):
+    H, W = 20, 22
+    img = synth.piecewise_image(H, W, 77, 4, 0.08)
+    f = img.f.astype(np.float64)
+    u = f.copy()
+    E = oracle.energy(u, f, 10.0, kind)
+    for b in (1, 2, 4, 8, 1, 2):
+        u = oracle.level_sequential(u, f, 10.0, kind, b, one_step=True)
+        E1 = oracle.energy(u, f, 10.0, kind)
+        assert E1 <= E + 1e-9 * abs(E)
+        E = E1
