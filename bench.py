@@ -315,6 +315,9 @@ def main():
         for j in range(L):
             for k in range(opts.ncolors):
                 cm.cm_phase(u, R, f, ALPHA, KIND, 1 << j, k, options=opts, ctx=ctx)
+        # the coarse levels as the solve runs them (tile sums, rounds, apply)
+        for j in range(COARSE_LB, L):
+            cm.cm_level(u, R, f, ALPHA, KIND, 1 << j, options=opts, ctx=ctx)
         cm.cm_energy(u, f, ALPHA, KIND, ctx=ctx)
         torch.cuda.synchronize()
         print(json.dumps({"phases_only": True, "levels": L, "ncolors": opts.ncolors}))
