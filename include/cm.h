@@ -57,7 +57,11 @@ typedef struct cm_ctx cm_ctx;
 
 /* Solver options.  Fill with cm_options_default() and override fields. */
 typedef struct {
-    int ncolors;         /* 2: checkerboard of blocks; 4: the paper's four colours (Sec. 2.3) */
+    int ncolors;         /* 2: checkerboard of blocks; 4: the paper's four colours (Sec. 2.3);
+                            9, 16: 3 x 3, 4 x 4 colours (p (bi mod p) + (bj mod p));
+                            0: decoupled, per level the smallest p >= 2 with (p - 1) b >= 3,
+                            so that blocks of one colour share no stencil and each colour's
+                            parallel solve equals solving its blocks one at a time */
     int grid_points;     /* G: odd, >= 3; points of the bracket grid of the block search */
     int golden_evals;    /* K: >= 2; golden-section evaluations of the block search */
     int paper_candidate; /* 1: also try the paper's one-step FBS estimate on the finest level */
@@ -71,6 +75,9 @@ typedef struct {
                             distance estimate (Eq. c-sol1; Prop. 2 for kind 1) on the
                             finest level and 0 on coarser ones; c_1 is kept if it lowers
                             E_A, else the block keeps 0 (two evaluations per block) */
+    int vcycle;          /* 1: full V-cycle, levels 1 .. L then L-1 .. 1 (Sec. 2.2, compared
+                            with the half cycle in Sec. 4.1); 0: the half V-cycle of Alg. 3,
+                            levels 1 .. L */
 } cm_options;
 
 /* Solve statistics (host struct, filled by cm_solve). */
@@ -87,7 +94,8 @@ typedef struct {
 
 /* Default options: ncolors 4 (the paper's four-colour decomposition, Sec. 2.3), G 5, K 6
  * (the budget the autotuner picks on every tested workload: fastest time to tolerance at the
- * lowest final energy), paper_candidate 1, use_graph 1, max_trace 4096, one_step 0. */
+ * lowest final energy), paper_candidate 1, use_graph 1, max_trace 4096, one_step 0,
+ * vcycle 0. */
 int cm_options_default(cm_options* opts /* host */);
 
 /* Create a context on CUDA device `device` (makes it current on this

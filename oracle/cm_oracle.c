@@ -356,7 +356,10 @@ static blockres_t block_min(const double *u, const double *f, int H, int W, cons
         res.n_eval = b.n_eval;
         return res;
     }
-    if (use_paper && A->r1 - A->r0 == 1 && A->c1 - A->c0 == 1) {
+    /* READING: the paper's closed-form candidate (Alg. 2, Eq. c-sol1) is the
+     * pixel step of the finest level; a 1 x 1 block clipped at the image corner
+     * on a coarser level is not a level-1 pixel and gets the search alone. */
+    if (use_paper && finest && A->r1 - A->r0 == 1 && A->c1 - A->c0 == 1) {
         double cp = orc_paper_candidate(u, f, H, W, A->r0, A->c0, alpha, kind);
         consider(&b, cp, local_energy(u, H, W, A, cp, alpha, kind, S1));
     }
@@ -420,11 +423,25 @@ double orc_block_min(const double *u, const double *f, int H, int W, int r0, int
 /* anchored at (0, 0) and clipped at the right and bottom edges (the paper   */
 /* uses sides 2^j - 1 and extends the domain; the extended pixels are not    */
 /* part of F).  Colour of block (bi, bj): ncolors = 2 -> (bi + bj) mod 2     */
-/* (checkerboard); ncolors = 4 -> 2 (bi mod 2) + (bj mod 2) (the paper's      */
-/* four-colour decomposition).                                               */
+/* (checkerboard); ncolors = p^2 (p = 2, 3, 4) -> p (bi mod p) + (bj mod p),   */
+/* the p x p decomposition (p = 2: the paper's four colours).                 */
 
 int orc_block_colour(int bi, int bj, int ncolors) {
-    return ncolors == 2 ? ((bi + bj) & 1) : (2 * (bi & 1) + (bj & 1));
+    if (ncolors == 2) return (bi + bj) & 1;
+    int p = ncolors == 16 ? 4 : (ncolors == 9 ? 3 : 2);
+    return p * (bi % p) + (bj % p);
+}
+
+/* Colours of the level with block side b.  ncolors = 0 selects the decoupled
+ * colouring: the smallest p >= 2 with (p - 1) b >= 3, so that two blocks of
+ * one colour are at least 3 pixels apart and share no stencil (a ring pixel
+ * of one is never in the window of a ring pixel of the other); a colour's
+ * parallel solve then equals solving its blocks one after another. */
+int orc_level_colours(int ncolors, int b) {
+    if (ncolors != 0) return ncolors;
+    int p = 2;
+    while ((p - 1) * b < 3) ++p;
+    return p * p;
 }
 
 int orc_auto_levels(int H, int W) {
@@ -489,16 +506,22 @@ void orc_level_sequential(double *u, const double *f, int H, int W, double alpha
 
 /* One cycle: fine-to-coarse half V-cycle (Sec. 2.2: the coarse-to-fine half
  * is omitted), colours in ascending order on each level (Alg. 3). */
+/* One cycle: levels 1 .. L (the half V-cycle of Alg. 3); with vcycle also
+ * back up, levels L - 1 .. 1 (the full V-cycle the paper compares against). */
 void orc_cycle(double *u, const double *f, int H, int W, double alpha, int kind, int levels,
-               int ncolors, int G, int K, int use_paper, int one_step, int sequential) {
+               int ncolors, int G, int K, int use_paper, int one_step, int sequential,
+               int vcycle) {
     if (levels <= 0) levels = orc_auto_levels(H, W);
-    for (int j = 1; j <= levels; ++j) {
+    int nsteps = vcycle ? 2 * levels - 1 : levels;
+    for (int s = 0; s < nsteps; ++s) {
+        int j = s < levels ? s + 1 : 2 * levels - 1 - s;
         int b = 1 << (j - 1);
         if (sequential) {
             orc_level_sequential(u, f, H, W, alpha, kind, b, G, K, use_paper, one_step);
         } else {
-            for (int k = 0; k < ncolors; ++k)
-                orc_phase(u, f, H, W, alpha, kind, b, ncolors, k, G, K, use_paper, one_step, NULL);
+            int nc = orc_level_colours(ncolors, b);
+            for (int k = 0; k < nc; ++k)
+                orc_phase(u, f, H, W, alpha, kind, b, nc, k, G, K, use_paper, one_step, NULL);
         }
     }
 }
@@ -510,7 +533,8 @@ void orc_cycle(double *u, const double *f, int H, int W, double alpha, int kind,
  * F(u_0), F(u_1), ...  Returns the number of cycles run; *converged is set. */
 int orc_solve(const double *f, int H, int W, double alpha, int kind, int levels, int cycles,
               double tol, const double *u0, double *u_out, int ncolors, int G, int K,
-              int use_paper, int one_step, int sequential, double *trace, int *converged) {
+              int use_paper, int one_step, int sequential, int vcycle, double *trace,
+              int *converged) {
     size_t N = (size_t)H * W;
     if (u0) memcpy(u_out, u0, N * sizeof(double));
     else memcpy(u_out, f, N * sizeof(double));
@@ -519,7 +543,7 @@ int orc_solve(const double *f, int H, int W, double alpha, int kind, int levels,
     int l = 0, conv = 0;
     while (l < cycles) {
         orc_cycle(u_out, f, H, W, alpha, kind, levels, ncolors, G, K, use_paper, one_step,
-                  sequential);
+                  sequential, vcycle);
         ++l;
         double E = orc_energy(u_out, f, H, W, alpha, kind);
         if (trace) trace[l] = E;

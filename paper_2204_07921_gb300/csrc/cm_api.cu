@@ -26,7 +26,7 @@ struct GraphKey {
     const float* S;
     const float* R;
     const float* f;
-    int H, W, kind, levels, ncolors, G, K, use_paper, one_step;
+    int H, W, kind, levels, ncolors, G, K, use_paper, one_step, vcycle;
     float alpha;
     double tol;
     int cycles, trace_cap;
@@ -146,13 +146,15 @@ int ensure_solve_state(cm_ctx* ctx) {
 bool finite_positive(float a) { return isfinite(a) && a > 0.0f; }
 
 int check_opts(cm_ctx* ctx, const cm_options& o) {
-    if (o.ncolors != 2 && o.ncolors != 4) return fail(ctx, CM_ERR_INVALID, "ncolors must be 2 or 4");
+    if (o.ncolors != 0 && o.ncolors != 2 && o.ncolors != 4 && o.ncolors != 9 && o.ncolors != 16)
+        return fail(ctx, CM_ERR_INVALID, "ncolors must be 0, 2, 4, 9 or 16");
     if (o.grid_points < 3 || (o.grid_points % 2) == 0 || o.grid_points > 1025)
         return fail(ctx, CM_ERR_INVALID, "grid_points must be odd, 3..1025");
     if (o.golden_evals < 2 || o.golden_evals > 1024)
         return fail(ctx, CM_ERR_INVALID, "golden_evals must be 2..1024");
     if (o.max_trace < 0 || o.max_trace > 4096) return fail(ctx, CM_ERR_INVALID, "max_trace 0..4096");
     if (o.one_step != 0 && o.one_step != 1) return fail(ctx, CM_ERR_INVALID, "one_step must be 0 or 1");
+    if (o.vcycle != 0 && o.vcycle != 1) return fail(ctx, CM_ERR_INVALID, "vcycle must be 0 or 1");
     return CM_OK;
 }
 
@@ -167,7 +169,7 @@ cm::PhaseArgs phase_args(const float* S, float* R, const float* f, int H, int W,
     a.alpha = alpha;
     a.kind = kind;
     a.lb = lb;
-    a.ncolors = o.ncolors;
+    a.ncolors = cm::level_colours(o.ncolors, lb);
     a.colour = colour;
     a.G = o.grid_points;
     a.K = o.golden_evals;
@@ -190,7 +192,8 @@ cudaError_t enqueue_level(float* tsums, float* cj, const float* S, float* R, con
         a.active = active;
         return cm::launch_level_coarse(a, tsums, cj, st);
     }
-    for (int k = 0; k < o.ncolors; ++k) {
+    const int nc = cm::level_colours(o.ncolors, lb);
+    for (int k = 0; k < nc; ++k) {
         cm::PhaseArgs a = phase_args(S, R, f, H, W, alpha, kind, lb, k, o);
         a.c_out = c_out;
         a.active = active;
@@ -199,6 +202,11 @@ cudaError_t enqueue_level(float* tsums, float* cj, const float* S, float* R, con
     }
     return cudaSuccess;
 }
+
+// Level steps of one cycle: levels 0 .. L-1 (the half V-cycle of Alg. 3),
+// with vcycle also back up, L-2 .. 0.
+int level_steps(int L, const cm_options& o) { return o.vcycle ? 2 * L - 1 : L; }
+int level_at(int step, int L) { return step < L ? step : 2 * L - 2 - step; }
 
 // Enqueue one cycle starting from buffer X (other buffer Y), then the energy
 // of the final state.  The state ends in X if `levels` is even, else in Y;
@@ -210,8 +218,10 @@ cudaError_t enqueue_cycle(cm_ctx* ctx, float* X, float* Y, const float* f, int H
                           cudaStream_t st, bool end_in_x = false) {
     float* S = X;
     float* R = Y;
-    for (int j = 0; j < levels; ++j) {
-        const bool in_place = end_in_x && j == levels - 1 && S == X &&
+    const int nsteps = level_steps(levels, o);
+    for (int step = 0; step < nsteps; ++step) {
+        const int j = level_at(step, levels);
+        const bool in_place = end_in_x && step == nsteps - 1 && S == X &&
                               j >= cm::coarse_level_log2();
         float* out = in_place ? S : R;
         cudaError_t e = enqueue_level(ctx->tsums, ctx->cj, S, out, f, H, W, alpha, kind, j, o,
@@ -306,6 +316,7 @@ int cm_options_default(cm_options* o) {
     o->use_graph = 1;
     o->max_trace = 4096;
     o->one_step = 0;
+    o->vcycle = 0;
     return CM_OK;
 }
 
@@ -409,7 +420,8 @@ int cm_phase(cm_ctx* ctx, const float* S, float* R, const float* f, int H, int W
     while ((1 << lb) < b) ++lb;
     if (b < 1 || (1 << lb) != b || lb > cm::max_level_log2())
         return fail(ctx, CM_ERR_INVALID, "cm_phase: b must be a power of two <= 2048");
-    if (colour < 0 || colour >= o.ncolors) return fail(ctx, CM_ERR_INVALID, "cm_phase: bad colour");
+    if (colour < 0 || colour >= cm::level_colours(o.ncolors, lb))
+        return fail(ctx, CM_ERR_INVALID, "cm_phase: bad colour");
     CM_CUDA(cudaSetDevice(ctx->device));
     cm::PhaseArgs a = phase_args(S, R, f, H, W, alpha, kind, lb, colour, o);
     a.c_out = c_out;
@@ -487,6 +499,7 @@ int cm_solve(cm_ctx* ctx, const float* f, int H, int W, float alpha, int kind, i
         key.K = o.golden_evals;
         key.use_paper = o.paper_candidate;
         key.one_step = o.one_step;
+        key.vcycle = o.vcycle;
         key.alpha = alpha;
         key.tol = tol;
         key.cycles = cycles;
@@ -549,7 +562,7 @@ int cm_solve(cm_ctx* ctx, const float* f, int H, int W, float alpha, int kind, i
         float* X = bufs[cur];
         float* Y = bufs[cur ^ 1];
         CM_CUDA(enqueue_cycle(ctx, X, Y, f, H, W, alpha, kind, L, o, st));
-        if (L & 1) cur ^= 1;
+        if (level_steps(L, o) & 1) cur ^= 1;
         CM_CUDA(cudaMemcpyAsync(ctx->E_pinned, ctx->E_dev, sizeof(double), cudaMemcpyDeviceToHost, st));
         CM_CUDA(cudaStreamSynchronize(st));
         ++l;
@@ -753,15 +766,17 @@ int cm_solve_batched(cm_ctx* ctx, int n, const float* const* f, const int* H, co
             float* Y = (float*)(A + L.ubuf);
             float* Sb = X;
             float* Rb = Y;
-            for (int j = 0; j < L.L && ce == cudaSuccess; ++j) {
+            const int nsteps = level_steps(L.L, o);
+            for (int step = 0; step < nsteps && ce == cudaSuccess; ++step) {
                 ce = enqueue_level((float*)(A + L.tsums), (float*)(A + L.cj), Sb, Rb, f[i], H[i],
-                                   W[i], alpha[i], kind[i], j, o, nullptr, active_ptr(i), si);
+                                   W[i], alpha[i], kind[i], level_at(step, L.L), o, nullptr,
+                                   active_ptr(i), si);
                 float* t = Sb;
                 Sb = Rb;
                 Rb = t;
             }
             const size_t N = (size_t)H[i] * W[i];
-            if (ce == cudaSuccess && (L.L & 1)) ce = cm::launch_batch_copy(Sb, X, N, active_ptr(i), si);
+            if (ce == cudaSuccess && (nsteps & 1)) ce = cm::launch_batch_copy(Sb, X, N, active_ptr(i), si);
             if (ce == cudaSuccess)
                 ce = cm::launch_energy(X, f[i], H[i], W[i], alpha[i], kind[i],
                                        (double*)(A + L.partials), (unsigned int*)(A + L.ticket),

@@ -154,11 +154,25 @@ __device__ __forceinline__ float aff_abs_curv(const AffPix& p, float c) {
 // Clamp-to-edge boundary: out-of-image neighbours take the nearest pixel.
 __device__ __forceinline__ int clampi(int v, int lo, int hi) { return min(max(v, lo), hi); }
 
+// Side p of a p x p colouring with `ncolors` = p^2 colours (ncolors = 2 is
+// the checkerboard).
+__host__ __device__ __forceinline__ int colour_side(int ncolors) {
+    return ncolors == 16 ? 4 : (ncolors == 9 ? 3 : 2);
+}
+
+// Colour of block (bi, bj): ncolors == 2: checkerboard; ncolors == p^2:
+// p (bi mod p) + (bj mod p) (p = 2: the paper's four colours).
+__host__ __device__ __forceinline__ int block_colour(int bi, int bj, int ncolors) {
+    if (ncolors == 2) return (bi + bj) & 1;
+    if (ncolors == 4) return ((bi & 1) << 1) | (bj & 1);
+    const int p = colour_side(ncolors);
+    return p * (bi % p) + (bj % p);
+}
+
 // Colour of the block holding pixel (r, c) on the level with block side
-// 1 << lb.  ncolors == 2: checkerboard of blocks; ncolors == 4: 2x2 parity.
+// 1 << lb.
 __device__ __forceinline__ int pixel_colour(int r, int c, int lb, int ncolors) {
-    int bi = r >> lb, bj = c >> lb;
-    return ncolors == 2 ? ((bi + bj) & 1) : (((bi & 1) << 1) | (bj & 1));
+    return block_colour(r >> lb, c >> lb, ncolors);
 }
 
 // Phase-state read.  During phase k of a level, blocks of colours < k have

@@ -25,6 +25,25 @@ inline cudaError_t launch_k(void (*kern)(KArgs...), dim3 grid, dim3 block, cudaS
     return cudaLaunchKernelEx(&cfg, kern, args...);
 }
 
+// Blocks per colour slot on a level with nbi x nbj blocks (an upper bound
+// for every colour; active_block maps a slot to a block or rejects it).
+inline int active_slots(int nbi, int nbj, int ncol) {
+    if (ncol == 2) return nbi * ((nbj + 1) / 2);
+    const int p = ncol == 16 ? 4 : (ncol == 9 ? 3 : 2);
+    return ((nbi + p - 1) / p) * ((nbj + p - 1) / p);
+}
+
+// Colours of the level with block side 1 << lb: ncolors, or for ncolors = 0
+// the decoupled colouring (the smallest p >= 2 with (p - 1) b >= 3, p^2
+// colours), under which a colour's blocks share no stencil.
+inline int level_colours(int ncolors, int lb) {
+    if (ncolors != 0) return ncolors;
+    const int b = 1 << lb;
+    int p = 2;
+    while ((p - 1) * b < 3) ++p;
+    return p * p;
+}
+
 struct PhaseArgs {
     const float* S;   // state at the start of the level
     float* R;         // blocks already updated on this level (and the output)

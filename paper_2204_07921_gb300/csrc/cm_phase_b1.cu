@@ -166,10 +166,13 @@ __device__ __forceinline__ float nb_eval(const NbConst& n, float c) {
     return KIND == KIND_MEAN ? 0.5f * fabsf(kmin + kmax) : fabsf(kmin * kmax);
 }
 
+// Tile of one CTA: 128 active pixels of the colour.  Checkerboard: 32 x 8
+// (every other pixel); p x p colours: 16p x 8p (every p-th pixel each way).
 template <int NCOL>
 struct B1Tile {
-    static constexpr int TW = 32;                       // tile columns
-    static constexpr int TH = NCOL == 2 ? 8 : 16;       // tile rows
+    static constexpr int P = NCOL == 16 ? 4 : (NCOL == 9 ? 3 : 2);
+    static constexpr int TW = NCOL == 2 ? 32 : 16 * P;  // tile columns
+    static constexpr int TH = NCOL == 2 ? 8 : 8 * P;    // tile rows
     static constexpr int THREADS = 128;                 // one per active pixel
 };
 
@@ -200,8 +203,9 @@ __global__ void __launch_bounds__(128, CM_B1_MIN_BLOCKS) phase_b1_kernel(const f
         r = r0 + ty;
         c = c0 + 2 * tx + ((r + k) & 1);
     } else {
-        r = r0 + 2 * ty + (k >> 1);
-        c = c0 + 2 * tx + (k & 1);
+        constexpr int P = B1Tile<NCOL>::P;
+        r = r0 + P * ty + k / P;
+        c = c0 + P * tx + k % P;
     }
     if (r >= H || c >= W) return;
     const int lr = r - r0, lc = c - c0;   // window (i, j) = tile[lr + i][lc + j]
@@ -308,12 +312,26 @@ cudaError_t launch_phase_b1(const PhaseArgs& A, cudaStream_t st) {
         return launch_k(kern, grid, dim3(128), st, 1, A.S, A.R, A.f, A.H, A.W, sp, A.colour,
                         A.use_paper, A.c_out, A.active);
     };
-    if (A.ncolors == 2)
-        return A.kind == KIND_MEAN
-                   ? go(phase_b1_kernel<KIND_MEAN, 2>, B1Tile<2>::TW, B1Tile<2>::TH)
-                   : go(phase_b1_kernel<KIND_GAUSS, 2>, B1Tile<2>::TW, B1Tile<2>::TH);
-    return A.kind == KIND_MEAN ? go(phase_b1_kernel<KIND_MEAN, 4>, B1Tile<4>::TW, B1Tile<4>::TH)
-                               : go(phase_b1_kernel<KIND_GAUSS, 4>, B1Tile<4>::TW, B1Tile<4>::TH);
+    switch (A.ncolors) {
+        case 2:
+            return A.kind == KIND_MEAN
+                       ? go(phase_b1_kernel<KIND_MEAN, 2>, B1Tile<2>::TW, B1Tile<2>::TH)
+                       : go(phase_b1_kernel<KIND_GAUSS, 2>, B1Tile<2>::TW, B1Tile<2>::TH);
+        case 4:
+            return A.kind == KIND_MEAN
+                       ? go(phase_b1_kernel<KIND_MEAN, 4>, B1Tile<4>::TW, B1Tile<4>::TH)
+                       : go(phase_b1_kernel<KIND_GAUSS, 4>, B1Tile<4>::TW, B1Tile<4>::TH);
+        case 9:
+            return A.kind == KIND_MEAN
+                       ? go(phase_b1_kernel<KIND_MEAN, 9>, B1Tile<9>::TW, B1Tile<9>::TH)
+                       : go(phase_b1_kernel<KIND_GAUSS, 9>, B1Tile<9>::TW, B1Tile<9>::TH);
+        case 16:
+            return A.kind == KIND_MEAN
+                       ? go(phase_b1_kernel<KIND_MEAN, 16>, B1Tile<16>::TW, B1Tile<16>::TH)
+                       : go(phase_b1_kernel<KIND_GAUSS, 16>, B1Tile<16>::TW, B1Tile<16>::TH);
+        default:
+            return cudaErrorInvalidValue;
+    }
 }
 
 }  // namespace cm

@@ -706,7 +706,7 @@ static cudaError_t launch_coarse_kind(const PhaseArgs& A, const float* partials,
                                       cudaStream_t st) {
     const int b = 1 << A.lb;
     const int nbi = (A.H + b - 1) / b, nbj = (A.W + b - 1) / b;
-    const int nact = A.ncolors == 2 ? nbi * ((nbj + 1) / 2) : ((nbi + 1) / 2) * ((nbj + 1) / 2);
+    const int nact = active_slots(nbi, nbj, A.ncolors);
     switch (A.lb) {
 #define CM_CASE(LB, CT, Q, RPT, SPEC, DMAX) \
     case LB: return launch_coarse<KIND, CT, Q, RPT>(A, partials, cj, nact, SPEC, DMAX, st);
@@ -786,7 +786,7 @@ template <int KIND>
 static cudaError_t launch_blocks_kind(const PhaseArgs& A, cudaStream_t st) {
     const int b = 1 << A.lb;
     const int nbi = (A.H + b - 1) / b, nbj = (A.W + b - 1) / b;
-    const int nact = A.ncolors == 2 ? nbi * ((nbj + 1) / 2) : ((nbi + 1) / 2) * ((nbj + 1) / 2);
+    const int nact = active_slots(nbi, nbj, A.ncolors);
     // ring of a full block: 8b pixels = Q * CT * RPT slots
     switch (A.lb) {
         case 1:

@@ -516,10 +516,12 @@ __device__ __forceinline__ bool active_block(int a, int nbi, int nbj, int ncol, 
         bj = 2 * (a - bi * half) + ((bi + k) & 1);
         nact = nbi * half;
     } else {
-        int hj = (nbj + 1) >> 1, hi = (nbi + 1) >> 1;
-        int ai = a / hj;
-        bi = 2 * ai + (k >> 1);
-        bj = 2 * (a - ai * hj) + (k & 1);
+        const int p = colour_side(ncol);
+        const int kr = k / p, kc = k - kr * p;
+        const int hj = (nbj + p - 1) / p, hi = (nbi + p - 1) / p;
+        const int ai = a / hj;
+        bi = p * ai + kr;
+        bj = p * (a - ai * hj) + kc;
         nact = hi * hj;
     }
     return a < nact && bi < nbi && bj < nbj;

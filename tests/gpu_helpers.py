@@ -29,7 +29,7 @@ def blocks_of_colour(H, W, b, ncolors, k):
     nbi, nbj = (H + b - 1) // b, (W + b - 1) // b
     for bi in range(nbi):
         for bj in range(nbj):
-            col = ((bi + bj) & 1) if ncolors == 2 else (2 * (bi & 1) + (bj & 1))
+            col = oracle.block_colour(bi, bj, ncolors)
             if col == k:
                 yield bi, bj, bi * b, bj * b, min(b, H - bi * b), min(b, W - bj * b)
 

@@ -509,3 +509,88 @@ def test_one_step_solve_vs_oracle(kind):
                                    one_step=True)
     assert st.energy_final == pytest.approx(trace[-1], rel=1e-3)
     assert st.energy_final < st.energy_initial
+
+
+# ---------------------------------------------------------------------------
+# p x p and decoupled colourings, full V-cycle.
+
+@pytest.mark.parametrize("shape", [(67, 45), (130, 97)])
+@pytest.mark.parametrize("ncolors", [9, 16])
+def test_phase_parity_pxp_colours(shape, ncolors):
+    H, W = shape
+    img = synth.piecewise_image(H, W, 900 + H + ncolors, 5, 0.08)
+    f = img.f
+    u = oracle.cycle(f.astype(np.float64), f.astype(np.float64), 20.0, cm.MEAN,
+                     levels=1).astype(np.float32)
+    tot = dict(n=0, match=0, tie=0)
+    fails = []
+    for b in levels_for(H, W):
+        for k in range(ncolors):
+            n, m, t, fl = check_phase(u, f, 20.0, cm.MEAN, b, ncolors, k)
+            tot["n"] += n
+            tot["match"] += m
+            tot["tie"] += t
+            fails += fl
+    print(f"\n{shape} ncol={ncolors}: {tot}")
+    assert not fails, fails[:5]
+    assert tot["tie"] <= max(2, 0.01 * tot["n"])
+
+
+def test_coarse_level_nine_colours():
+    """Coarse path with 3 x 3 colours: deferred reads S + c of blocks of
+    earlier colours, each colour's c against the oracle."""
+    H, W = 300, 260
+    f = synth.piecewise_image(H, W, 4545, 12, 0.08).f
+    u, _ = run_solve(f, 20.0, cm.MEAN, 1)
+    opts = cm.default_options(ncolors=9)
+    fails, tot = [], 0
+    for b in (64, 128):
+        nbi, nbj = (H + b - 1) // b, (W + b - 1) // b
+        cbuf = torch.full((nbi * nbj,), float("nan"), device=DEV)
+        S = to_dev(u)
+        R = torch.empty_like(S)
+        cm.cm_level(S, R, to_dev(f), 20.0, cm.MEAN, b, options=opts, c_out=cbuf)
+        torch.cuda.synchronize()
+        cg, Rg = host(cbuf), host(R)
+        for k in range(9):
+            state = u.copy()
+            for kk in range(k):
+                for bi, bj, r0, c0, bh, bw in blocks_of_colour(H, W, b, 9, kk):
+                    state[r0:r0 + bh, c0:c0 + bw] += np.float32(cg[bi * nbj + bj])
+            cgd = {(bi, bj): cg[bi * nbj + bj] for bi, bj, *_ in blocks_of_colour(H, W, b, 9, k)}
+            n, m, t, fl = compare_phase(state.astype(np.float64), f.astype(np.float64), cgd,
+                                        20.0, cm.MEAN, b, 9, k, {})
+            tot += n
+            fails += fl
+        for bi in range(nbi):
+            for bj in range(nbj):
+                blk = (slice(bi * b, min((bi + 1) * b, H)), slice(bj * b, min((bj + 1) * b, W)))
+                np.testing.assert_array_equal(Rg[blk], u[blk] + np.float32(cg[bi * nbj + bj]))
+    assert tot > 0
+    assert not fails, fails[:5]
+
+
+@pytest.mark.parametrize("kind", [cm.MEAN, cm.GAUSS])
+@pytest.mark.parametrize("vcycle", [0, 1])
+def test_decoupled_solve(kind, vcycle):
+    """Decoupled colours (and the full V-cycle): the energy never rises beyond
+    FP32 noise, the reported energy is the oracle's energy of the result, and
+    the oracle's own decoupled solve reaches the same energy to 1e-3; the
+    device loop equals the host loop."""
+    f = synth.piecewise_image(96, 88, 61 + vcycle, 8, 0.08).f
+    out = []
+    for use_graph in (1, 0):
+        opts = cm.default_options(ncolors=0, vcycle=vcycle, use_graph=use_graph)
+        u, st = cm.cm_solve(to_dev(f), 15.0, kind, cycles=8, tol=0.0, options=opts)
+        torch.cuda.synchronize()
+        out.append((host(u), st))
+    (ug, st), (uh, sh) = out
+    np.testing.assert_array_equal(ug, uh)
+    assert st.trace() == sh.trace()
+    tr = np.array(st.trace())
+    assert np.all(np.diff(tr) <= 1e-6 * np.abs(tr[1:]))
+    Eo = oracle.energy(ug.astype(np.float64), f.astype(np.float64), 15.0, kind)
+    assert st.energy_final == pytest.approx(Eo, rel=2e-6)
+    _, trace, _, _ = oracle.solve(f.astype(np.float64), 15.0, kind, cycles=8, ncolors=0,
+                                  vcycle=bool(vcycle))
+    assert st.energy_final == pytest.approx(trace[-1], rel=1e-3)

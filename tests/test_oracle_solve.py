@@ -123,3 +123,78 @@ def test_degenerate_shapes(shape):
         assert n == 3
         assert np.all(np.diff(trace) <= 1e-12 * np.abs(trace[1:]))
         assert np.all(np.isfinite(u))
+
+
+# ---------------------------------------------------------------------------
+# Decoupled colourings and the full V-cycle.
+
+def test_decoupled_colours_keep_blocks_three_pixels_apart():
+    """ncolors = 0: on every level two distinct blocks of one colour are at
+    least 3 pixels apart (so no window of a ring pixel of one holds a ring
+    pixel of the other)."""
+    for b in (1, 2, 4, 8, 16):
+        nc = oracle.level_colours(0, b)
+        p = int(round(nc ** 0.5))
+        assert p * p == nc and (p - 1) * b >= 3 and (p == 2 or (p - 2) * b < 3)
+        cols = {}
+        for bi in range(2 * p + 1):
+            for bj in range(2 * p + 1):
+                cols.setdefault(oracle.block_colour(bi, bj, nc), []).append((bi, bj))
+        assert sorted(cols) == list(range(nc))
+        for members in cols.values():
+            for a in members:
+                for c in members:
+                    if a == c:
+                        continue
+                    gap_r = max(0, abs(a[0] - c[0]) * b - b)
+                    gap_c = max(0, abs(a[1] - c[1]) * b - b)
+                    assert max(gap_r, gap_c) >= 3
+
+
+@pytest.mark.parametrize("kind", [oracle.MEAN, oracle.GAUSS])
+@pytest.mark.parametrize("b", [1, 2, 4])
+def test_decoupled_phase_equals_one_block_at_a_time(kind, b):
+    """A colour's parallel (snapshot) solve equals solving its blocks one after
+    another, each applied before the next, when the colouring is decoupled."""
+    H, W = 19, 23
+    img = synth.piecewise_image(H, W, 90 + b, 4, 0.08)
+    f = img.f.astype(np.float64)
+    u = oracle.cycle(f, f, 12.0, kind, levels=1)
+    nc = oracle.level_colours(0, b)
+    nbi, nbj = (H + b - 1) // b, (W + b - 1) // b
+    for k in range(nc):
+        par, _ = oracle.phase(u, f, 12.0, kind, b, nc, k)
+        seq = u.copy()
+        for bi in range(nbi):
+            for bj in range(nbj):
+                if oracle.block_colour(bi, bj, nc) != k:
+                    continue
+                r0, c0 = bi * b, bj * b
+                bh, bw = min(b, H - r0), min(b, W - c0)
+                c, _ = oracle.block_min(seq, f, r0, c0, bh, bw, 12.0, kind, finest=(b == 1))
+                seq[r0:r0 + bh, c0:c0 + bw] += c
+        np.testing.assert_allclose(par, seq, rtol=0, atol=1e-12)
+        u = par
+
+
+@pytest.mark.parametrize("kind", [oracle.MEAN, oracle.GAUSS])
+@pytest.mark.parametrize("vcycle", [False, True])
+def test_decoupled_solve_is_monotone(kind, vcycle):
+    """With decoupled colours every phase is a sequence of block updates that
+    never raise F, so the energy trace never rises."""
+    img = synth.piecewise_image(40, 44, 5, 6, 0.08)
+    u, trace, n, _ = oracle.solve(img.f, 15.0, kind, cycles=6, ncolors=0, vcycle=vcycle)
+    assert n == 6
+    assert np.all(np.diff(trace) <= 1e-10 * np.abs(trace[1:]))
+
+
+def test_vcycle_is_half_cycle_then_levels_back_up():
+    img = synth.piecewise_image(33, 40, 6, 5, 0.08)
+    f = img.f.astype(np.float64)
+    L = oracle.auto_levels(33, 40)
+    uv = oracle.cycle(f, f, 15.0, oracle.MEAN, ncolors=4, vcycle=True)
+    uh = oracle.cycle(f, f, 15.0, oracle.MEAN, ncolors=4)
+    for j in range(L - 1, 0, -1):
+        for k in range(4):
+            uh, _ = oracle.phase(uh, f, 15.0, oracle.MEAN, 1 << (j - 1), 4, k)
+    np.testing.assert_array_equal(uv, uh)
