@@ -432,6 +432,33 @@ def main():
         "cycles_to_target": hit, "s_to_target": None if hit is None else hit * per_cycle,
         "energy_after_run": trace[-1], "psnr_after_run_db": synth.psnr(u.cpu().numpy(), img.clean)}
 
+    # the colouring / cycle variants of the method (plain solve from f to the
+    # same tolerance): the full V-cycle (Sec. 2.2, compared in Sec. 4.1) and
+    # the decoupled colouring (blocks of one colour share no stencil)
+    variants = {}
+    for name, kw in (("vcycle", dict(vcycle=1)), ("decoupled", dict(ncolors=0)),
+                     ("decoupled_vcycle", dict(ncolors=0, vcycle=1))):
+        ov = cm.default_options(grid_points=opts.grid_points, golden_evals=opts.golden_evals,
+                                ncolors=kw.get("ncolors", opts.ncolors), vcycle=kw.get("vcycle", 0))
+
+        def vsolve(fin, out, ov=ov):
+            _, st = cm.cm_solve(fin, ALPHA, KIND, levels=0, cycles=MAX_CYCLES, tol=TOL,
+                                u_out=out, options=ov, ctx=ctx)
+            return st
+
+        vsolve(f, u)
+        torch.cuda.synchronize()
+        sec_v, st_v = timed_steps(vsolve)
+        variants[name] = {"s": sec_v, "cycles_to_tol": st_v[-1].cycles_run,
+                          "psnr_db": synth.psnr(u.cpu().numpy(), img.clean),
+                          "final_energy": st_v[-1].energy_final,
+                          "monotone_violations": st_v[-1].monotone_violations,
+                          "vs_half_cycle_4_colours_time": sec_v / sec_plain}
+    variants["half_cycle_4_colours"] = {"s": sec_plain, "cycles_to_tol": cycles_plain[-1],
+                                        "psnr_db": psnr_plain,
+                                        "final_energy": st_plain[-1].energy_final,
+                                        "monotone_violations": st_plain[-1].monotone_violations}
+
     # dominant kernel: finest-level phase (b = 1), launched on the same stream
     state = u.clone()
     R = state.clone()
@@ -500,7 +527,8 @@ def main():
                     "d2h_bytes_per_step": 4 * N},
             "gpu_launches": int(sum(launches_per_solve)),
             "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks,
-            "b1_phase_ms": b1_ms, "batched": batched_res, "one_step": one_step_res}
+            "b1_phase_ms": b1_ms, "batched": batched_res, "one_step": one_step_res,
+            "cycle_variants": variants}
     line["config"]["levels"] = L
     line["config"]["grid_points"] = opts.grid_points
     line["config"]["golden_evals"] = opts.golden_evals
