@@ -38,6 +38,7 @@ MAX_CYCLES = 2000
 METRIC = ("s to rel-energy tol 1e-4 at 1024^2 (learned warm start + FP32 sweep with FP64 "
           "stopping test; plain sweep reported alongside)")
 WARMSTART_PARAMS = os.path.join(ROOT, "paper_2204_07921_gb300", "data", "warmstart_mean_a20.npz")
+WARMSTART_PARAMS_GAUSS = os.path.join(ROOT, "paper_2204_07921_gb300", "data", "warmstart_gauss_a15.npz")
 L2_FLUSH_BYTES = 512 << 20   # > 129 MB L2
 
 
@@ -486,9 +487,13 @@ def main():
                 "note": "curvature-stencil evaluations/s; peak = 152 SM x 16 MUFU/clk x "
                         "2.07 GHz / 8 rsqrt per evaluation (derived, nominal clock)"}
 
-    warm_eval = None
+    warm_eval = warm_eval_gauss = None
     if not args.no_warmstart_eval:
         warm_eval = ws.evaluate(net, n=16, side=1024, alpha=ALPHA, kind=KIND, tol=TOL, ctx=ctx)
+        # the Gaussian-curvature network (alpha 15) on the same test set
+        net_g = ws.Net.load(WARMSTART_PARAMS_GAUSS, ctx=ctx)
+        warm_eval_gauss = ws.evaluate(net_g, n=16, side=1024, alpha=15.0, kind=1, tol=TOL,
+                                      ctx=ctx)
 
     batched_res = None
     if not args.no_batched:
@@ -522,6 +527,7 @@ def main():
             "warm_vs_plain_speedup": sec_plain / sec_warm,
             "psnr_db": psnr_warm, "psnr_noisy_db": synth.psnr(img.f, img.clean),
             "warmstart_eval_16x1024": warm_eval,
+            "warmstart_eval_gauss_16x1024": warm_eval_gauss,
             "final_energy": final_E,
             "e2e": {"value": e2e, "unit": "s", "h2d_bytes_per_step": 4 * N,
                     "d2h_bytes_per_step": 4 * N},

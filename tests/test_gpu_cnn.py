@@ -98,3 +98,25 @@ def test_warmstart_energy_fallback():
     net0 = ws.Net(ws.init_params(9, zero_last=True))
     u0, used = ws.warmstart(net0, f, 20.0, cm.MEAN, check_energy=True)
     assert used == [1] and torch.equal(u0, f)
+
+
+@pytest.mark.parametrize("name,kind,alpha", [("warmstart_mean_a20.npz", cm.MEAN, 20.0),
+                                             ("warmstart_gauss_a15.npz", cm.GAUSS, 15.0)])
+def test_shipped_warmstart_saves_cycles(name, kind, alpha):
+    """The shipped networks (mean curvature, alpha 20; Gaussian curvature,
+    alpha 15) pass the energy check on fresh test images and the solve from
+    their output needs no more cycles than the solve from f."""
+    import os
+    path = os.path.join(os.path.dirname(ws.__file__), "data", name)
+    net = ws.Net.load(path)
+    saved = 0
+    for i in range(2):
+        im = synth.warmstart_image("test", 100 + i, 512)
+        f = dev(im.f)
+        u0, used = ws.warmstart(net, f[None], alpha, kind, check_energy=True)
+        assert used == [1]
+        _, sp = cm.cm_solve(f, alpha, kind, cycles=200, tol=1e-4)
+        _, sw = cm.cm_solve(f, alpha, kind, cycles=200, tol=1e-4, u0=u0[0].contiguous())
+        assert sw.cycles_run <= sp.cycles_run
+        saved += sp.cycles_run - sw.cycles_run
+    assert saved > 0
