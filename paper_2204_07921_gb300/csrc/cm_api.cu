@@ -185,12 +185,13 @@ cm::PhaseArgs phase_args(const float* S, float* R, const float* f, int H, int W,
 // block's shift.
 cudaError_t enqueue_level(float* tsums, float* cj, const float* S, float* R, const float* f,
                           int H, int W, float alpha, int kind, int lb, const cm_options& o,
-                          float* c_out, const int* active, cudaStream_t st) {
+                          float* c_out, const int* active, cudaStream_t st,
+                          bool sums_ready = false) {
     if (lb >= cm::coarse_level_log2()) {
         cm::PhaseArgs a = phase_args(S, R, f, H, W, alpha, kind, lb, 0, o);
         a.c_out = c_out;
         a.active = active;
-        return cm::launch_level_coarse(a, tsums, cj, st);
+        return cm::launch_level_coarse(a, tsums, cj, st, sums_ready);
     }
     const int nc = cm::level_colours(o.ncolors, lb);
     for (int k = 0; k < nc; ++k) {
@@ -219,13 +220,15 @@ cudaError_t enqueue_cycle(cm_ctx* ctx, float* X, float* Y, const float* f, int H
     float* S = X;
     float* R = Y;
     const int nsteps = level_steps(levels, o);
+    bool sums = false;   // tile sums of the current state already in ctx->tsums
     for (int step = 0; step < nsteps; ++step) {
         const int j = level_at(step, levels);
-        const bool in_place = end_in_x && step == nsteps - 1 && S == X &&
-                              j >= cm::coarse_level_log2();
+        const bool coarse = j >= cm::coarse_level_log2();
+        const bool in_place = end_in_x && step == nsteps - 1 && S == X && coarse;
         float* out = in_place ? S : R;
         cudaError_t e = enqueue_level(ctx->tsums, ctx->cj, S, out, f, H, W, alpha, kind, j, o,
-                                      nullptr, nullptr, st);
+                                      nullptr, nullptr, st, sums);
+        sums = coarse;
         if (e != cudaSuccess) return e;
         if (!in_place) {
             float* t = S;
@@ -767,10 +770,13 @@ int cm_solve_batched(cm_ctx* ctx, int n, const float* const* f, const int* H, co
             float* Sb = X;
             float* Rb = Y;
             const int nsteps = level_steps(L.L, o);
+            bool sums = false;
             for (int step = 0; step < nsteps && ce == cudaSuccess; ++step) {
+                const int j = level_at(step, L.L);
                 ce = enqueue_level((float*)(A + L.tsums), (float*)(A + L.cj), Sb, Rb, f[i], H[i],
-                                   W[i], alpha[i], kind[i], level_at(step, L.L), o, nullptr,
-                                   active_ptr(i), si);
+                                   W[i], alpha[i], kind[i], j, o, nullptr, active_ptr(i), si,
+                                   sums);
+                sums = j >= cm::coarse_level_log2();
                 float* t = Sb;
                 Sb = Rb;
                 Rb = t;

@@ -77,7 +77,10 @@ int max_level_log2();
 int coarse_level_log2();
 size_t coarse_partials_needed(int H, int W);
 size_t coarse_c_needed(int H, int W);
-cudaError_t launch_level_coarse(const PhaseArgs& a, float* partials, float* cj, cudaStream_t st);
+// sums_ready: `partials` already holds the tile sums of S - f (written by the
+// previous coarse level's apply, which leaves those of its output).
+cudaError_t launch_level_coarse(const PhaseArgs& a, float* partials, float* cj, cudaStream_t st,
+                                bool sums_ready = false);
 // Per-process kernel attributes of the coarse path (cluster sizes above 8);
 // call before the first launch, outside stream capture.
 cudaError_t coarse_setup();

@@ -495,15 +495,40 @@ __global__ void __launch_bounds__(256) tile_sums_kernel(const float* __restrict_
     }
 }
 
-__global__ void __launch_bounds__(256) apply_kernel(const float* __restrict__ S,
-                                                    float* __restrict__ R,
+// R = S + c on every pixel (deferred apply of a coarse level) and, in the same
+// pass, the 32 x 32 tile sums of R - f that the next coarse level takes its
+// block sums from (the order of tile_sums_kernel, so the sums are the same).
+// S and R may be the same buffer (every pixel is read and written by one
+// thread).
+__global__ void __launch_bounds__(256) apply_kernel(const float* S, float* R,
+                                                    const float* __restrict__ f,
                                                     const float* __restrict__ cj, int H, int W,
-                                                    int lb, int nbj, const int* __restrict__ active) {
+                                                    int lb, int nbj, float* __restrict__ partials,
+                                                    const int* __restrict__ active) {
     if (active && *active == 0) return;
-    const size_t N = (size_t)H * W;
-    for (size_t p = (size_t)blockIdx.x * 256 + threadIdx.x; p < N; p += (size_t)gridDim.x * 256) {
-        const int r = (int)(p / W), c = (int)(p - (size_t)r * W);
-        R[p] = S[p] + cj[(size_t)(r >> lb) * nbj + (c >> lb)];
+    __shared__ float red[8];
+    const int r0 = blockIdx.y * TILE, c0 = blockIdx.x * TILE;
+    float acc = 0.0f;
+#pragma unroll
+    for (int i = 0; i < TILE * TILE / 256; ++i) {
+        const int idx = threadIdx.x + 256 * i;
+        const int r = r0 + idx / TILE, c = c0 + idx % TILE;
+        if (r < H && c < W) {
+            const size_t p = (size_t)r * W + c;
+            const float v = S[p] + cj[(size_t)(r >> lb) * nbj + (c >> lb)];
+            R[p] = v;
+            acc += v - f[p];
+        }
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float t = 0.0f;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) t += red[i];
+        partials[blockIdx.y * gridDim.x + blockIdx.x] = t;
     }
 }
 
@@ -745,10 +770,12 @@ int coarse_level_log2() { return COARSE_LB; }
 
 // One whole level on the coarse path: tile sums, every colour's search, apply.
 cudaError_t launch_level_coarse(const PhaseArgs& A0, float* partials, float* cj,
-                                cudaStream_t st) {
+                                cudaStream_t st, bool sums_ready) {
     dim3 tg((A0.W + TILE - 1) / TILE, (A0.H + TILE - 1) / TILE);
-    cudaError_t e = launch_k(tile_sums_kernel, tg, dim3(256), st, 1, A0.S, A0.f, A0.H, A0.W,
-                             partials, A0.active);
+    cudaError_t e = cudaSuccess;
+    if (!sums_ready)
+        e = launch_k(tile_sums_kernel, tg, dim3(256), st, 1, A0.S, A0.f, A0.H, A0.W, partials,
+                     A0.active);
     if (e != cudaSuccess) return e;
     for (int k = 0; k < A0.ncolors; ++k) {
         PhaseArgs A = A0;
@@ -759,10 +786,8 @@ cudaError_t launch_level_coarse(const PhaseArgs& A0, float* partials, float* cj,
     }
     const int b = 1 << A0.lb;
     const int nbj = (A0.W + b - 1) / b;
-    const size_t N = (size_t)A0.H * A0.W;
-    const int grid = (int)std::min<size_t>((N + 255) / 256, 152 * 16);
-    return launch_k(apply_kernel, dim3(grid), dim3(256), st, 1, A0.S, A0.R, cj, A0.H, A0.W, A0.lb,
-                    nbj, A0.active);
+    return launch_k(apply_kernel, tg, dim3(256), st, 1, (const float*)A0.S, A0.R, A0.f,
+                    (const float*)cj, A0.H, A0.W, A0.lb, nbj, partials, A0.active);
 }
 
 template <int KIND, int GT, int RPT>

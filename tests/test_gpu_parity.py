@@ -171,7 +171,7 @@ def run_solve(f, alpha, kind, cycles, tol=0.0, use_graph=1, ncolors=4, levels=0)
     return host(u), st
 
 
-@pytest.mark.parametrize("shape", [(67, 45), (300, 260)])
+@pytest.mark.parametrize("shape", [(67, 45), (300, 260), (520, 600)])
 def test_solve_equals_level_sequence_and_is_deterministic(shape):
     """cm_solve (graph replay and direct launches) performs exactly the level
     sequence of Alg. 3: bit-identical to chaining cm_level calls; on levels
