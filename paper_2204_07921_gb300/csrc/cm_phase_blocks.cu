@@ -464,7 +464,7 @@ __global__ void __cluster_dims__(Q, 1, 1) __launch_bounds__(CT) phase_cluster_ke
 // S1 sum.
 
 constexpr int TILE = 32;
-constexpr int COARSE_LB = 6;
+constexpr int COARSE_LB = 6;   // first level on the coarse path (b = 1 << COARSE_LB)
 
 __global__ void __launch_bounds__(256) tile_sums_kernel(const float* __restrict__ S,
                                                         const float* __restrict__ f, int H, int W,
