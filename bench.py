@@ -40,6 +40,7 @@ METRIC = ("s to rel-energy tol 1e-4 at 1024^2 (learned warm start + FP32 sweep w
 WARMSTART_PARAMS = os.path.join(ROOT, "paper_2204_07921_gb300", "data", "warmstart_mean_a20.npz")
 WARMSTART_PARAMS_GAUSS = os.path.join(ROOT, "paper_2204_07921_gb300", "data", "warmstart_gauss_a15.npz")
 L2_FLUSH_BYTES = 512 << 20   # > 129 MB L2
+B1_TRAFFIC_BYTES = 7.41e6     # ncu DRAM bytes of one finest-level phase at 1024^2
 
 
 def parse():
@@ -488,9 +489,14 @@ def main():
     mufu_peak = 152 * 16 * 2.07e9 / 8 / 1e9   # Geval/s: 8 MUFU rsqrt per stencil evaluation
     roofline = {"bound": "alu", "kernel": "phase_b1_kernel (b=1)", "achieved": achieved,
                 "peak": mufu_peak, "unit": "Geval/s", "frac": achieved / mufu_peak,
-                "traffic": None,
+                # dram__bytes_read.sum + dram__bytes_write.sum of one launch of this
+                # kernel at 1024^2 (ncu, profiles/solve_cycle_kernels_1024.md)
+                "traffic": B1_TRAFFIC_BYTES if args.side == 1024 else None,
+                "traffic_unit": "B per launch",
                 "note": "curvature-stencil evaluations/s; peak = 152 SM x 16 MUFU/clk x "
-                        "2.07 GHz / 8 rsqrt per evaluation (derived, nominal clock)"}
+                        "2.07 GHz / 8 rsqrt per evaluation (derived, nominal clock); the "
+                        "kernel is issue-bound on the FP32/ALU pipes (ncu: issue 57-63% "
+                        "active, MUFU 18-21%)"}
 
     warm_eval = warm_eval_gauss = None
     if not args.no_warmstart_eval:
