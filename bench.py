@@ -490,7 +490,7 @@ def main():
     roofline = {"bound": "alu", "kernel": "phase_b1_kernel (b=1)", "achieved": achieved,
                 "peak": mufu_peak, "unit": "Geval/s", "frac": achieved / mufu_peak,
                 # dram__bytes_read.sum + dram__bytes_write.sum of one launch of this
-                # kernel at 1024^2 (ncu, profiles/solve_cycle_kernels_1024.md)
+                # kernel at 1024^2, from one ncu capture of a solve cycle
                 "traffic": B1_TRAFFIC_BYTES if args.side == 1024 else None,
                 "traffic_unit": "B per launch",
                 "note": "curvature-stencil evaluations/s; peak = 152 SM x 16 MUFU/clk x "
