@@ -403,6 +403,11 @@ def main():
         e2e_t.append(time.perf_counter() - t0)
     e2e = statistics.mean(e2e_t)
 
+    # the bench image at equal final energy (the warm-started sweep stops at the
+    # plain solve's energy instead of at the tolerance)
+    warm_eq_image = ws.evaluate_equal_energy(net, alpha=ALPHA, kind=KIND, tol=TOL, ctx=ctx,
+                                             images=[img])
+
     # single-step mode (one step of Alg. 2 per block, kept if it lowers E_A):
     # the plain solve to the same tolerance, timed the same way
     opts1 = cm.default_options(ncolors=opts.ncolors, grid_points=opts.grid_points,
@@ -501,6 +506,10 @@ def main():
     warm_eval = warm_eval_gauss = None
     if not args.no_warmstart_eval:
         warm_eval = ws.evaluate(net, n=16, side=1024, alpha=ALPHA, kind=KIND, tol=TOL, ctx=ctx)
+        # at equal final energy: the warm-started sweep runs the cycles it needs to
+        # reach the plain solve's energy (single images, inference included)
+        warm_eval["equal_energy"] = ws.evaluate_equal_energy(net, n=16, side=1024, alpha=ALPHA,
+                                                             kind=KIND, tol=TOL, ctx=ctx)
         # the Gaussian-curvature network (alpha 15) on the same test set
         net_g = ws.Net.load(WARMSTART_PARAMS_GAUSS, ctx=ctx)
         warm_eval_gauss = ws.evaluate(net_g, n=16, side=1024, alpha=15.0, kind=1, tol=TOL,
@@ -536,6 +545,7 @@ def main():
             "plain": {"s": sec_plain, "cycles_to_tol": cycles_plain, "psnr_db": psnr_plain,
                       "final_energy": st_plain[-1].energy_final},
             "warm_vs_plain_speedup": sec_plain / sec_warm,
+            "warm_at_equal_energy": warm_eq_image,
             "psnr_db": psnr_warm, "psnr_noisy_db": synth.psnr(img.f, img.clean),
             "warmstart_eval_16x1024": warm_eval,
             "warmstart_eval_gauss_16x1024": warm_eval_gauss,

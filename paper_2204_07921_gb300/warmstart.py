@@ -264,3 +264,84 @@ def evaluate(net: Net, n: int = 16, side: int = 1024, alpha: float = 20.0, kind:
         "energy_plain": [s.energy_final for s in st_plain],
         "energy_warm": [s.energy_final for s in st_warm],
     }
+
+
+def evaluate_equal_energy(net: Net, n: int = 16, side: int = 1024, alpha: float = 20.0,
+                          kind: int = 0, tol: float = 1e-4, ctx: Context | None = None,
+                          images=None):
+    """Time to the plain method's final energy and to its PSNR.  For each test
+    image the plain sweep from f runs to the tolerance (energy E_p, PSNR
+    P_p); the warm-started sweep then runs exactly as many cycles as it needs
+    to reach E_p (counted on its energy trace), and, separately, as few cycles
+    as it needs to come within 0.05 dB of P_p; each is timed with its
+    inference.  Times are CUDA-event times of one image's call each, summed."""
+    import torch
+    import synth
+    from . import cm_solve
+    imgs = images if images is not None else [synth.warmstart_image("test", i, side)
+                                              for i in range(n)]
+    u = None
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        r = fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / 1e3, r
+
+    rows = []
+    for im in imgs:
+        f = torch.from_numpy(im.f).cuda().contiguous()
+        u = torch.empty_like(f)
+        U0 = torch.empty_like(f)
+        tp, sp = timed(lambda: cm_solve(f, alpha, kind, cycles=5000, tol=tol, u_out=u, ctx=ctx)[1])
+        psnr_p = synth.psnr(u.cpu().numpy(), im.clean)
+        warmstart(net, f, alpha, kind, check_energy=True, out=U0)
+        _, sw = cm_solve(f, alpha, kind, cycles=sp.cycles_run, tol=0.0, u0=U0, u_out=u, ctx=ctx)
+        tr = sw.trace()
+        hit = next((j for j, E in enumerate(tr) if E <= sp.energy_final), None)
+        cyc = hit if hit is not None else sp.cycles_run
+
+        def warm_to_energy():
+            warmstart(net, f, alpha, kind, check_energy=True, out=U0)
+            return cm_solve(f, alpha, kind, cycles=cyc, tol=0.0, u0=U0, u_out=u, ctx=ctx)[1]
+
+        tw, stw = timed(warm_to_energy)
+        psnr_w = synth.psnr(u.cpu().numpy(), im.clean)
+        # equal PSNR: the fewest warm-started cycles whose result is within
+        # 0.05 dB of the plain solve's PSNR (the clean image is known here)
+        cq = 0
+        while True:
+            cm_solve(f, alpha, kind, cycles=cq, tol=0.0, u0=U0, u_out=u, ctx=ctx)
+            if synth.psnr(u.cpu().numpy(), im.clean) >= psnr_p - 0.05 or cq >= sp.cycles_run:
+                break
+            cq += 1
+
+        def warm_to_psnr():
+            warmstart(net, f, alpha, kind, check_energy=True, out=U0)
+            return cm_solve(f, alpha, kind, cycles=cq, tol=0.0, u0=U0, u_out=u, ctx=ctx)[1]
+
+        tq, _ = timed(warm_to_psnr)
+        rows.append({"plain_s": tp, "plain_cycles": sp.cycles_run, "plain_energy": sp.energy_final,
+                     "plain_psnr": psnr_p, "warm_s": tw, "warm_cycles": cyc,
+                     "warm_reached": hit is not None, "warm_energy": stw.energy_final,
+                     "warm_psnr": psnr_w, "psnr_cycles": cq, "psnr_s": tq,
+                     "psnr_at_cycles": synth.psnr(u.cpu().numpy(), im.clean)})
+    tp = sum(r["plain_s"] for r in rows)
+    tw = sum(r["warm_s"] for r in rows)
+    d = [r["warm_psnr"] - r["plain_psnr"] for r in rows]
+    return {"images": len(rows), "side": imgs[0].f.shape[0], "alpha": alpha, "kind": kind,
+            "tol": tol, "plain_s": tp, "warm_s": tw, "speedup": tp / tw,
+            "plain_cycles": [r["plain_cycles"] for r in rows],
+            "warm_cycles": [r["warm_cycles"] for r in rows],
+            "all_reached": all(r["warm_reached"] for r in rows),
+            "psnr_diff_db_mean": float(np.mean(d)), "psnr_diff_db_max_abs": float(np.max(np.abs(d))),
+            "psnr_plain": float(np.mean([r["plain_psnr"] for r in rows])),
+            "psnr_warm": float(np.mean([r["warm_psnr"] for r in rows])),
+            "equal_psnr": {"warm_s": sum(r["psnr_s"] for r in rows),
+                           "speedup": tp / sum(r["psnr_s"] for r in rows),
+                           "warm_cycles": [r["psnr_cycles"] for r in rows],
+                           "psnr_diff_db": [r["psnr_at_cycles"] - r["plain_psnr"] for r in rows]}}
