@@ -206,8 +206,8 @@ def run_reference(args):
 
 def workload_config(side):
     return {"workload": f"denoise {side}x{side} mean curvature, 20 shapes, sigma 0.08, "
-                        f"alpha 20, blocks 1..{side // 2}, 4 colours, tol 1e-4; learned warm "
-                        f"start (6 conv3x3, 32 ch, BF16) then the sweep",
+                        f"alpha 20, blocks 1..{side // 2}, tuned colour schedule, tol 1e-4; "
+                        f"learned warm start (6 conv3x3, 32 ch, BF16) then the sweep",
             "image": f"{side}x{side}", "kind": "mean", "alpha": ALPHA, "tol": TOL,
             "levels": None, "ncolors": 4, "grid_points": None, "golden_evals": None,
             "l2": "flushed between steps (512 MB write)"}
@@ -228,7 +228,10 @@ def batched_measurement(cm, torch, synth, ctx, dev, rank=0, world=1):
     outs = [torch.empty_like(t) for t in fs]
     al = [it.alpha for it in items]
     kd = [it.kind for it in items]
-    opts = cm.default_options()
+    # one schedule for the whole batch, tuned on a median-sized Gaussian-curvature
+    # calibration image (the batch mixes the kinds, so the colours stay at four)
+    from paper_2204_07921_gb300 import autotune
+    opts, brec = autotune.tune(576, 576, 1, 15.0, tol=TOL, ncolors=4, ctx=ctx)
 
     def batched():
         _, st = cm.cm_solve_batched(fs, al, kd, tol=TOL, cycles=MAX_CYCLES, u_outs=outs,
@@ -243,7 +246,7 @@ def batched_measurement(cm, torch, synth, ctx, dev, rank=0, world=1):
             sts.append(st)
         return sts
 
-    res = {}
+    res = {"schedule": {k: brec[k] for k in ("G", "K", "ncolors", "coarse_spec", "coarse_dmax")}}
     for name, fn in (("batched", batched), ("one_at_a_time", sequential)):
         fn()   # warm-up (graph capture)
         torch.cuda.synchronize()
@@ -296,7 +299,7 @@ def main():
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
     from paper_2204_07921_gb300 import autotune
-    opts, tune_rec = autotune.tune(args.side, args.side, KIND, ALPHA, tol=TOL, ncolors=NCOLORS,
+    opts, tune_rec = autotune.tune(args.side, args.side, KIND, ALPHA, tol=TOL, ncolors=None,
                                    ctx=ctx)
     L = cm.cm_auto_levels(args.side, args.side)
 
@@ -530,10 +533,19 @@ def main():
                "per_cycle_s": per_cycle}
 
     # kernels per cycle: one per colour on levels below the coarse threshold
-    # (b < 64); tile sums + one per colour + apply on coarse levels; energy;
-    # the device stopping test
-    coarse = max(0, L - COARSE_LB)
-    kernels_per_cycle = opts.ncolors * (L - coarse) + coarse * (opts.ncolors + 2) + 2
+    # (b < 64); one per colour + apply on coarse levels (+ tile sums on the
+    # first); energy; the device stopping test
+    def level_colours(nc, b):
+        if nc != 0:
+            return nc
+        p = 2
+        while (p - 1) * b < 3:
+            p += 1
+        return p * p
+
+    kernels_per_cycle = 2 + sum(level_colours(opts.ncolors, 1 << j) +
+                                (0 if j < COARSE_LB else (2 if j == COARSE_LB else 1))
+                                for j in range(L))
     # per warm step: 6 network kernels, 2 energy checks, then the solve graph
     # (initial energy, state initialisation, the cycles)
     launches_per_solve = [8 + 2 + c * kernels_per_cycle for c in cycles]
@@ -559,6 +571,9 @@ def main():
     line["config"]["levels"] = L
     line["config"]["grid_points"] = opts.grid_points
     line["config"]["golden_evals"] = opts.golden_evals
+    line["config"]["ncolors"] = opts.ncolors
+    line["config"]["coarse_spec"] = opts.coarse_spec
+    line["config"]["coarse_dmax"] = opts.coarse_dmax
     line["autotune"] = tune_rec
     if rank == 0:
         print(json.dumps(line), flush=True)

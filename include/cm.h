@@ -78,6 +78,11 @@ typedef struct {
     int vcycle;          /* 1: full V-cycle, levels 1 .. L then L-1 .. 1 (Sec. 2.2, compared
                             with the half cycle in Sec. 4.1); 0: the half V-cycle of Alg. 3,
                             levels 1 .. L */
+    int coarse_spec;     /* coarse levels (b >= 64): -1 the level's default, 0/1 speculate the
+                            first golden pair in the grid's reduction */
+    int coarse_dmax;     /* coarse levels: 0 the level's default, 1 .. 4 golden steps per
+                            reduction (2^d - 1 points of every outcome path); both change only
+                            how many candidates share a reduction, never which are taken */
 } cm_options;
 
 /* Solve statistics (host struct, filled by cm_solve). */
@@ -95,7 +100,7 @@ typedef struct {
 /* Default options: ncolors 4 (the paper's four-colour decomposition, Sec. 2.3), G 5, K 6
  * (the budget the autotuner picks on every tested workload: fastest time to tolerance at the
  * lowest final energy), paper_candidate 1, use_graph 1, max_trace 4096, one_step 0,
- * vcycle 0. */
+ * vcycle 0, coarse_spec -1, coarse_dmax 0. */
 int cm_options_default(cm_options* opts /* host */);
 
 /* Create a context on CUDA device `device` (makes it current on this

@@ -1,16 +1,23 @@
-"""Autotuner of the block-search budget.
+"""Autotuner of the solve's schedule.
 
-The budget of the block search -- G grid points on the bracket and K
-golden-section evaluations -- is a parameter of the method (the oracle takes
-the same two numbers).  It trades the cost of a cycle against how far each
-block's subproblem is minimised, and on this non-convex energy a very precise
-per-block search can also settle in worse local minima than a coarser one.
-The tuner times a solve to tolerance on a calibration image of the requested
-shape class (a seeded image that is not one of the measured workloads) for
-each candidate budget, and picks the fastest whose final energy is within
-`ENERGY_SLACK` of the lowest final energy any candidate reached.  Results are
-cached per GPU model in a JSON file ($CM_AUTOTUNE_CACHE, else
-~/.cache/cm_autotune.json).
+It tunes, in stages, on a calibration image of the requested shape class (a
+seeded image that is not one of the measured workloads):
+
+1. the block-search budget -- G grid points on the bracket and K golden-
+   section evaluations, a parameter of the method (the oracle takes the same
+   two numbers): it trades the cost of a cycle against how far each block's
+   subproblem is minimised, and on this non-convex energy a very precise
+   search can also settle in worse local minima than a coarser one;
+2. the colour schedule -- four colours, the checkerboard, or the decoupled
+   colouring (more colours on the finest levels, no shared stencils);
+3. the coarse levels' kernel shape -- how many candidates share one cluster
+   reduction (first-pair speculation, golden steps per round), which changes
+   the number of barriers and not the decisions.
+
+Each stage times a solve to tolerance for every candidate and keeps the
+fastest whose final energy is within `ENERGY_SLACK` of the lowest final
+energy any candidate of the stage reached.  Results are cached per GPU model
+in a JSON file ($CM_AUTOTUNE_CACHE, else ~/.cache/cm_autotune.json).
 """
 from __future__ import annotations
 
@@ -18,7 +25,10 @@ import json
 import os
 
 CANDIDATES = ((9, 16), (7, 10), (5, 8), (5, 6), (5, 4), (3, 4))
+COLOURS = (4, 2, 0)
+COARSE = ((-1, 0), (0, 4), (1, 4), (0, 2), (0, 1))   # (coarse_spec, coarse_dmax)
 ENERGY_SLACK = 2e-3
+CACHE_VERSION = 2
 
 
 def choose(results, slack: float = ENERGY_SLACK):
@@ -28,7 +38,7 @@ def choose(results, slack: float = ENERGY_SLACK):
         raise ValueError("no results")
     e_best = min(r["energy"] for r in results)
     ok = [r for r in results if r["energy"] <= e_best + slack * abs(e_best)]
-    return min(ok, key=lambda r: (r["seconds"], -r["G"], -r["K"]))
+    return min(ok, key=lambda r: (r["seconds"], -r.get("G", 0), -r.get("K", 0)))
 
 
 def _cache_path():
@@ -44,26 +54,34 @@ def _load_cache(path):
         return {}
 
 
-def tune(H: int, W: int, kind: int, alpha: float, tol: float = 1e-4, ncolors: int = 4,
+def tune(H: int, W: int, kind: int, alpha: float, tol: float = 1e-4, ncolors=None,
          candidates=CANDIDATES, ctx=None, use_cache: bool = True, repeats: int = 2):
-    """Returns (options, record).  record holds every candidate's time, cycles
-    and final energy, and the choice."""
+    """Returns (options, record).  record holds every stage's candidates
+    (time, cycles, final energy) and the choices.  ncolors fixes the colour
+    schedule instead of tuning it."""
     import torch
     import synth
     import paper_2204_07921_gb300 as cm
     gpu = torch.cuda.get_device_name()
-    key = f"{gpu}|{H}x{W}|kind={kind}|alpha={alpha:g}|tol={tol:g}|ncolors={ncolors}"
+    key = (f"v{CACHE_VERSION}|{gpu}|{H}x{W}|kind={kind}|alpha={alpha:g}|tol={tol:g}"
+           f"|ncolors={'tuned' if ncolors is None else ncolors}")
     path = _cache_path()
     cache = _load_cache(path) if use_cache else {}
+
+    def options(rec):
+        return cm.default_options(ncolors=rec["ncolors"], grid_points=rec["G"],
+                                  golden_evals=rec["K"], coarse_spec=rec["coarse_spec"],
+                                  coarse_dmax=rec["coarse_dmax"])
+
     if key in cache:
-        rec = cache[key]
-        return cm.default_options(ncolors=ncolors, grid_points=rec["G"], golden_evals=rec["K"]), rec
-    img = synth.piecewise_image(H, W, synth.BASE_SEED + 900000 + 7 * H + W, 20, 0.08)
+        return options(cache[key]), cache[key]
+    seed = synth.BASE_SEED + 900000 + 7 * H + W
+    img = synth.piecewise_image(H, W, seed, 20, 0.08)
     f = torch.from_numpy(img.f).cuda()
     u = torch.empty_like(f)
-    results = []
-    for G, K in candidates:
-        o = cm.default_options(ncolors=ncolors, grid_points=G, golden_evals=K)
+
+    def run(cfg):
+        o = options(cfg)
         cm.cm_solve(f, alpha, kind, cycles=5000, tol=tol, u_out=u, options=o, ctx=ctx)
         best = None
         for _ in range(repeats):
@@ -71,16 +89,27 @@ def tune(H: int, W: int, kind: int, alpha: float, tol: float = 1e-4, ncolors: in
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record()
-            _, st = cm.cm_solve(f, alpha, kind, cycles=5000, tol=tol, u_out=u, options=o, ctx=ctx)
+            _, st = cm.cm_solve(f, alpha, kind, cycles=5000, tol=tol, u_out=u, options=o,
+                                ctx=ctx)
             e1.record()
             torch.cuda.synchronize()
             t = e0.elapsed_time(e1) / 1e3
             best = t if best is None else min(best, t)
-        results.append({"G": G, "K": K, "seconds": best, "cycles": st.cycles_run,
-                        "energy": st.energy_final})
-    pick = choose(results)
-    rec = {"G": pick["G"], "K": pick["K"], "results": results, "image": f"{H}x{W}",
-           "calibration_seed": synth.BASE_SEED + 900000 + 7 * H + W}
+        return {**cfg, "seconds": best, "cycles": st.cycles_run, "energy": st.energy_final}
+
+    cfg = {"G": 5, "K": 6, "ncolors": 4 if ncolors is None else ncolors, "coarse_spec": -1,
+           "coarse_dmax": 0}
+    stages = {}
+    stages["budget"] = [run({**cfg, "G": G, "K": K}) for G, K in candidates]
+    pick = choose(stages["budget"])
+    cfg.update(G=pick["G"], K=pick["K"])
+    if ncolors is None:
+        stages["colours"] = [run({**cfg, "ncolors": nc}) for nc in COLOURS]
+        cfg["ncolors"] = choose(stages["colours"])["ncolors"]
+    stages["coarse"] = [run({**cfg, "coarse_spec": sp, "coarse_dmax": dm}) for sp, dm in COARSE]
+    pick = choose(stages["coarse"])
+    cfg.update(coarse_spec=pick["coarse_spec"], coarse_dmax=pick["coarse_dmax"])
+    rec = {**cfg, "stages": stages, "image": f"{H}x{W}", "calibration_seed": seed}
     if use_cache:
         cache = _load_cache(path)
         cache[key] = rec
@@ -90,4 +119,4 @@ def tune(H: int, W: int, kind: int, alpha: float, tol: float = 1e-4, ncolors: in
                 json.dump(cache, fh, indent=1)
         except OSError:
             pass
-    return cm.default_options(ncolors=ncolors, grid_points=pick["G"], golden_evals=pick["K"]), rec
+    return options(rec), rec

@@ -26,7 +26,7 @@ struct GraphKey {
     const float* S;
     const float* R;
     const float* f;
-    int H, W, kind, levels, ncolors, G, K, use_paper, one_step, vcycle;
+    int H, W, kind, levels, ncolors, G, K, use_paper, one_step, vcycle, coarse_spec, coarse_dmax;
     float alpha;
     double tol;
     int cycles, trace_cap;
@@ -155,6 +155,10 @@ int check_opts(cm_ctx* ctx, const cm_options& o) {
     if (o.max_trace < 0 || o.max_trace > 4096) return fail(ctx, CM_ERR_INVALID, "max_trace 0..4096");
     if (o.one_step != 0 && o.one_step != 1) return fail(ctx, CM_ERR_INVALID, "one_step must be 0 or 1");
     if (o.vcycle != 0 && o.vcycle != 1) return fail(ctx, CM_ERR_INVALID, "vcycle must be 0 or 1");
+    if (o.coarse_spec < -1 || o.coarse_spec > 1)
+        return fail(ctx, CM_ERR_INVALID, "coarse_spec must be -1, 0 or 1");
+    if (o.coarse_dmax < 0 || o.coarse_dmax > 4)
+        return fail(ctx, CM_ERR_INVALID, "coarse_dmax must be 0 .. 4");
     return CM_OK;
 }
 
@@ -175,6 +179,8 @@ cm::PhaseArgs phase_args(const float* S, float* R, const float* f, int H, int W,
     a.K = o.golden_evals;
     a.use_paper = o.paper_candidate;
     a.one_step = o.one_step;
+    a.coarse_spec = o.coarse_spec;
+    a.coarse_dmax = o.coarse_dmax;
     a.c_out = nullptr;
     return a;
 }
@@ -320,6 +326,8 @@ int cm_options_default(cm_options* o) {
     o->max_trace = 4096;
     o->one_step = 0;
     o->vcycle = 0;
+    o->coarse_spec = -1;
+    o->coarse_dmax = 0;
     return CM_OK;
 }
 
@@ -503,6 +511,8 @@ int cm_solve(cm_ctx* ctx, const float* f, int H, int W, float alpha, int kind, i
         key.use_paper = o.paper_candidate;
         key.one_step = o.one_step;
         key.vcycle = o.vcycle;
+        key.coarse_spec = o.coarse_spec;
+        key.coarse_dmax = o.coarse_dmax;
         key.alpha = alpha;
         key.tol = tol;
         key.cycles = cycles;

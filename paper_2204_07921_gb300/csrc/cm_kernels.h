@@ -57,6 +57,8 @@ struct PhaseArgs {
     int G, K;         // block-search budget
     int use_paper;    // paper's one-step candidate on the finest level
     int one_step = 0; // the paper's single step per block instead of the search
+    int coarse_spec = -1;   // coarse levels: first-pair speculation (-1: the level's default)
+    int coarse_dmax = 0;    // coarse levels: golden steps per reduction (0: the level's default)
     float* c_out;     // nullable: per-block corrections
     const int* active = nullptr;   // nullable: kernels return at once when *active == 0
 };

@@ -733,8 +733,11 @@ static cudaError_t launch_coarse_kind(const PhaseArgs& A, const float* partials,
     const int nbi = (A.H + b - 1) / b, nbj = (A.W + b - 1) / b;
     const int nact = active_slots(nbi, nbj, A.ncolors);
     switch (A.lb) {
-#define CM_CASE(LB, CT, Q, RPT, SPEC, DMAX) \
-    case LB: return launch_coarse<KIND, CT, Q, RPT>(A, partials, cj, nact, SPEC, DMAX, st);
+#define CM_CASE(LB, CT, Q, RPT, SPEC, DMAX)                                                  \
+    case LB:                                                                                  \
+        return launch_coarse<KIND, CT, Q, RPT>(A, partials, cj, nact,                         \
+                                               A.coarse_spec >= 0 ? A.coarse_spec : (SPEC),   \
+                                               A.coarse_dmax > 0 ? A.coarse_dmax : (DMAX), st);
         CM_COARSE_SHAPES(CM_CASE)
 #undef CM_CASE
         default: return cudaErrorInvalidValue;
