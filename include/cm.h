@@ -188,8 +188,10 @@ int cm_solve(cm_ctx* ctx, const float* f, int H, int W, float alpha, int kind, i
  * cm_auto_levels per image).  One CUDA graph holds one cycle of every image
  * (an independent chain per image, so images run concurrently); each image
  * stops on its own relative-energy test (Eq. reerr), evaluated on the device,
- * after which its kernels return at entry; the host replays the graph until no
- * image is active, reading back one small state array per cycle.  Every
+ * after which its kernels return at entry.  The cycle sits in the body of a
+ * conditional WHILE node whose condition a kernel sets to "some image is
+ * active", so the whole batch is one graph launch and one read-back of a
+ * small state array (the loop ends: every image stops at `cycles`).  Every
  * image's result and statistics equal those of cm_solve on that image alone
  * (same kernels, same order).  stats: host array of n (nullable).  Returns
  * CM_NOT_CONVERGED if tol > 0 and an image hit the cap, CM_ERR_NUMERIC on a

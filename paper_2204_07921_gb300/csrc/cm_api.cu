@@ -768,8 +768,37 @@ int cm_solve_batched(cm_ctx* ctx, int n, const float* const* f, const int* H, co
             CM_CUDA(cudaEventCreateWithFlags(&e2, cudaEventDisableTiming));
             ctx->bevents.push_back(e2);
         }
+        // the whole batched solve as one graph: a conditional WHILE node (its
+        // condition reset to 1 at every launch) around one cycle of every
+        // image, the last kernel of which sets the condition to "some image is
+        // still active"; every image stops itself at the cycle cap.
         cudaStream_t cs = ctx->cap_stream;
-        CM_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+        cudaGraph_t top = nullptr;
+        CM_CUDA(cudaGraphCreate(&top, 0));
+        cudaGraphConditionalHandle h = 0;
+        cudaGraph_t body = nullptr;
+        {
+            cudaError_t e1 = cudaGraphConditionalHandleCreate(&h, top, 1, cudaGraphCondAssignDefault);
+            cudaGraphNodeParams cp = {cudaGraphNodeTypeConditional};
+            cp.conditional.handle = h;
+            cp.conditional.type = cudaGraphCondTypeWhile;
+            cp.conditional.size = 1;
+            cudaGraphNode_t wnode;
+            if (e1 == cudaSuccess) e1 = cudaGraphAddNode(&wnode, top, nullptr, nullptr, 0, &cp);
+            if (e1 != cudaSuccess) {
+                cudaGraphDestroy(top);
+                return cuda_fail(ctx, e1, "batch loop node");
+            }
+            body = cp.conditional.phGraph_out[0];
+        }
+        {
+            cudaError_t e1 = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0,
+                                                           cudaStreamCaptureModeThreadLocal);
+            if (e1 != cudaSuccess) {
+                cudaGraphDestroy(top);
+                return cuda_fail(ctx, e1, "capture batch cycle");
+            }
+        }
         cudaError_t ce = cudaEventRecord(ctx->bevents[n], cs);
         for (int i = 0; i < n && ce == cudaSuccess; ++i) {
             cudaStream_t si = ctx->bstreams[i];
@@ -803,37 +832,24 @@ int cm_solve_batched(cm_ctx* ctx, int n, const float* const* f, const int* H, co
             if (ce == cudaSuccess) ce = cudaEventRecord(ctx->bevents[i], si);
             if (ce == cudaSuccess) ce = cudaStreamWaitEvent(cs, ctx->bevents[i], 0);
         }
-        cudaGraph_t g;
+        if (ce == cudaSuccess)
+            ce = cm::launch_batch_any(state_ptr(0), n, h, cs);
+        cudaGraph_t g = nullptr;
         cudaError_t ee = cudaStreamEndCapture(cs, &g);
-        if (ce != cudaSuccess) return cuda_fail(ctx, ce, "capture batch cycle");
-        if (ee != cudaSuccess) return cuda_fail(ctx, ee, "end batch capture");
-        cudaError_t ie = cudaGraphInstantiate(&ctx->bgraph, g, 0);
-        cudaGraphDestroy(g);
+        if (ce != cudaSuccess || ee != cudaSuccess) {
+            cudaGraphDestroy(top);
+            return cuda_fail(ctx, ce != cudaSuccess ? ce : ee, "capture batch cycle");
+        }
+        cudaError_t ie = cudaGraphInstantiate(&ctx->bgraph, top, 0);
+        cudaGraphDestroy(top);
         if (ie != cudaSuccess) return cuda_fail(ctx, ie, "batch graph instantiate");
         ctx->bgraph_key = key;
     }
-    // replay until every image has stopped (each replay is one cycle of
-    // every still-active image)
+    // one launch runs every cycle of every image; the state is read once
+    CM_CUDA(cudaGraphLaunch(ctx->bgraph, st));
     std::vector<unsigned char> host_state((size_t)n * sb);
-    int replays = 0;
-    for (; replays < cycles; ++replays) {
-        CM_CUDA(cudaGraphLaunch(ctx->bgraph, st));
-        CM_CUDA(cudaMemcpyAsync(host_state.data(), state_ptr(0), (size_t)n * sb,
-                                cudaMemcpyDeviceToHost, st));
-        CM_CUDA(cudaStreamSynchronize(st));
-        int any = 0;
-        for (int i = 0; i < n; ++i) {
-            int c, cv, v, ne, act;
-            double E;
-            cm::batch_read_state(host_state.data() + (size_t)i * sb, &c, &cv, &v, &E, &ne, &act);
-            any |= act;
-        }
-        if (!any) break;
-    }
-    if (cycles == 0) {
-        CM_CUDA(cudaMemcpyAsync(host_state.data(), state_ptr(0), (size_t)n * sb,
-                                cudaMemcpyDeviceToHost, st));
-    }
+    CM_CUDA(cudaMemcpyAsync(host_state.data(), state_ptr(0), (size_t)n * sb,
+                            cudaMemcpyDeviceToHost, st));
     std::vector<double> e0h(n);
     CM_CUDA(cudaMemcpyAsync(e0h.data(), E0, n * sizeof(double), cudaMemcpyDeviceToHost, st));
     CM_CUDA(cudaStreamSynchronize(st));

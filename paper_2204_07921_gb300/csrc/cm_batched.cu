@@ -8,8 +8,10 @@
 // Ordering inside an image comes from the graph's edges, never from a kernel
 // waiting on another, so no kernel spins.  Each image's stopping test (Eq.
 // reerr) runs on the device and clears the image's `active` flag; every kernel
-// of a retired image returns at entry, so the host replays the same graph
-// until no image is active.
+// of a retired image returns at entry.  The cycle is the body of a
+// conditional WHILE node whose condition batch_any_kernel sets to "some image
+// is active" after each cycle, so the whole batch is one graph launch; the
+// loop is finite because every image retires at its cycle cap.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <string.h>
@@ -116,6 +118,20 @@ cudaError_t launch_batch_init(ImgDev* st, const double* E0, int n, int cycles, c
 cudaError_t launch_batch_stop(ImgDev* st, const double* E_now, double tol, int cap,
                               double* trace, int trace_cap, cudaStream_t s) {
     batch_stop_kernel<<<1, 32, 0, s>>>(st, E_now, tol, cap, trace, trace_cap);
+    return cudaGetLastError();
+}
+
+// Loop condition of the batched solve graph: 1 while any image is active.
+__global__ void batch_any_kernel(const ImgDev* st, int n, cudaGraphConditionalHandle h) {
+    int any = 0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) any |= st[i].active;
+    any = __syncthreads_or(any);
+    if (threadIdx.x == 0) cudaGraphSetConditional(h, any ? 1u : 0u);
+}
+
+cudaError_t launch_batch_any(const ImgDev* st, int n, cudaGraphConditionalHandle h,
+                             cudaStream_t s) {
+    batch_any_kernel<<<1, 256, 0, s>>>(st, n, h);
     return cudaGetLastError();
 }
 

@@ -18,6 +18,9 @@ cudaError_t launch_solve_init(ImgDev* st, const double* E0, int cycles, double* 
                               cudaGraphConditionalHandle h, cudaStream_t s);
 cudaError_t launch_solve_stop(ImgDev* st, const double* E_now, double tol, int cap, double* trace,
                               int trace_cap, cudaGraphConditionalHandle h, cudaStream_t s);
+// Batched solve graph: sets the loop condition to "some image is active".
+cudaError_t launch_batch_any(const ImgDev* st, int n, cudaGraphConditionalHandle h,
+                             cudaStream_t s);
 cudaError_t launch_batch_copy(const float* src, float* dst, size_t n, const int* active,
                               cudaStream_t s);
 // Unpack one image's state copied to the host.
