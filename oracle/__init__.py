@@ -27,6 +27,9 @@ _lock = threading.Lock()
 _lib = None
 
 MEAN, GAUSS = 0, 1
+# Extension: principal curvatures from a least-squares fit of Euler's formula
+# to the four direction curvatures (instead of their extremes).
+MEAN_EULER, GAUSS_EULER = 2, 3
 # Default search budget: the same as the library's default options.
 DEFAULT_G, DEFAULT_K = 5, 6
 

@@ -31,6 +31,8 @@
 
 #define ORC_MEAN 0
 #define ORC_GAUSS 1
+#define ORC_MEAN_EULER 2   /* extension: principal curvatures from Euler's formula */
+#define ORC_GAUSS_EULER 3
 
 /* ------------------------------------------------------------------------ */
 /* Image access with the boundary condition.                                 */
@@ -127,13 +129,66 @@ void orc_direction_curvatures_f(const field_t *F, int r, int c, double kbar[4], 
  * kappa_min = min_l kappa_l, kappa_max = max_l kappa_l).  Mean curvature
  * H = (kappa_min + kappa_max) / 2 (Table I, Eq. MCM); Gaussian curvature
  * K = kappa_min * kappa_max (Eq. GCM). */
+static void euler_fit(const double kbar[4], double *kmin, double *kmax);
+
 static double curv_from_kbar(const double kbar[4], int kind) {
     double kmin = kbar[0], kmax = kbar[0];
-    for (int t = 1; t < 4; ++t) {
-        if (kbar[t] < kmin) kmin = kbar[t];
-        if (kbar[t] > kmax) kmax = kbar[t];
+    if (kind == ORC_MEAN_EULER || kind == ORC_GAUSS_EULER) {
+        euler_fit(kbar, &kmin, &kmax);
+    } else {
+        for (int t = 1; t < 4; ++t) {
+            if (kbar[t] < kmin) kmin = kbar[t];
+            if (kbar[t] > kmax) kmax = kbar[t];
+        }
     }
-    return kind == ORC_MEAN ? 0.5 * (kmin + kmax) : kmin * kmax;
+    return (kind == ORC_MEAN || kind == ORC_MEAN_EULER) ? 0.5 * (kmin + kmax) : kmin * kmax;
+}
+
+/* Extension (not in the paper): principal curvatures from Euler's theorem.
+ * The normal curvature of a smooth surface in the tangent direction at angle
+ * theta is kappa(theta) = k1 cos^2(theta - phi) + k2 sin^2(theta - phi)
+ *                       = a + b cos(2 theta) + s sin(2 theta),
+ * a = (k1 + k2)/2, sqrt(b^2 + s^2) = |k1 - k2|/2.  The four direction
+ * curvatures are samples of kappa at the angles of their lines in the image
+ * plane; (a, b, s) is their least-squares fit, found here from the 3 x 3
+ * normal equations (D^T D) x = D^T kbar with rows D_t = (1, cos 2 theta_t,
+ * sin 2 theta_t), solved by Gauss-Jordan elimination with partial pivoting.  Then
+ * k1,2 = a -+ sqrt(b^2 + s^2).  Unlike the extreme sampled directions, this
+ * recovers the principal curvatures of a quadric whose principal axes are not
+ * aligned with the pixel grid. */
+static void euler_fit(const double kbar[4], double *kmin, double *kmax) {
+    double M[3][4];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 4; ++j) M[i][j] = 0.0;
+    for (int t = 0; t < 4; ++t) {
+        double dx = (double)(LINE_Y[t][1] - LINE_X[t][1]);   /* column direction */
+        double dy = (double)(LINE_Y[t][0] - LINE_X[t][0]);   /* row direction    */
+        double th = atan2(dy, dx);
+        double row[3] = {1.0, cos(2.0 * th), sin(2.0 * th)};
+        for (int i = 0; i < 3; ++i) {
+            for (int j = 0; j < 3; ++j) M[i][j] += row[i] * row[j];
+            M[i][3] += row[i] * kbar[t];
+        }
+    }
+    for (int col = 0; col < 3; ++col) {
+        int piv = col;
+        for (int i = col + 1; i < 3; ++i)
+            if (fabs(M[i][col]) > fabs(M[piv][col])) piv = i;
+        for (int j = 0; j < 4; ++j) {
+            double tmp = M[col][j];
+            M[col][j] = M[piv][j];
+            M[piv][j] = tmp;
+        }
+        for (int i = 0; i < 3; ++i) {
+            if (i == col) continue;
+            double fct = M[i][col] / M[col][col];
+            for (int j = col; j < 4; ++j) M[i][j] -= fct * M[col][j];
+        }
+    }
+    double a = M[0][3] / M[0][0], b = M[1][3] / M[1][1], s = M[2][3] / M[2][2];
+    double rad = sqrt(b * b + s * s);
+    *kmin = a - rad;
+    *kmax = a + rad;
 }
 
 static double curv_f(const field_t *F, int r, int c, int kind) {
@@ -266,7 +321,7 @@ double orc_paper_candidate(const double *u, const double *f, int H, int W, int r
     double kbar[4], d[8];
     orc_direction_curvatures(u, H, W, r, c, kbar, d);
     double chalf;
-    if (kind == ORC_MEAN) {
+    if (kind == ORC_MEAN || kind == ORC_MEAN_EULER) {
         chalf = 0.0;
         for (int l = 0; l < 8; ++l) chalf += d[l];
         chalf /= 8.0;

@@ -13,6 +13,9 @@ import pytest
 
 import oracle
 
+ALL_KINDS = (oracle.MEAN, oracle.GAUSS, oracle.MEAN_EULER, oracle.GAUSS_EULER)
+MEAN_KINDS = (oracle.MEAN, oracle.MEAN_EULER)
+
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "worked_examples.json")
 
 
@@ -73,7 +76,7 @@ def test_affine_images_have_zero_curvature():
     y, x = np.mgrid[0:9, 0:11].astype(np.float64)
     for a, b, c in [(0.25, -0.5, 0.125), (2.0, 0.0, -1.0), (0.0, 0.0, 0.75), (-3.5, 1.25, 8.0)]:
         u = a * x + b * y + c
-        for kind in (oracle.MEAN, oracle.GAUSS):
+        for kind in ALL_KINDS:
             cmap = oracle.curvature_map(u, kind)
             assert np.all(cmap[1:-1, 1:-1] == 0.0)
             for r in range(1, 8):
@@ -81,7 +84,7 @@ def test_affine_images_have_zero_curvature():
                     kbar, d = oracle.direction_curvatures(u, r, cc)
                     assert np.all(d == 0.0) and np.all(kbar == 0.0)
     const = np.full((9, 11), 0.625)
-    for kind in (oracle.MEAN, oracle.GAUSS):
+    for kind in ALL_KINDS:
         assert np.all(oracle.curvature_map(const, kind) == 0.0)
         assert oracle.energy(const, const, 3.0, kind) == 0.0
 
@@ -91,7 +94,7 @@ def sphere_cap(R, n):
     return np.sqrt(R * R - x * x - y * y)
 
 
-@pytest.mark.parametrize("kind", [oracle.MEAN, oracle.GAUSS])
+@pytest.mark.parametrize("kind", ALL_KINDS)
 def test_sphere_cap_closed_form_and_order(kind):
     """Sphere of radius R (umbilic everywhere): |H| = 1/R, |K| = 1/R^2
     (Table I definitions).  The relative error must fall as (h/R)^2."""
@@ -103,9 +106,9 @@ def test_sphere_cap_closed_form_and_order(kind):
         cmap = oracle.curvature_map(u, kind)
         yy, xx = np.mgrid[0:2 * n + 1, 0:2 * n + 1]
         m = ((yy - n) ** 2 + (xx - n) ** 2 <= (R / 2) ** 2)
-        exact = 1.0 / R if kind == oracle.MEAN else 1.0 / (R * R)
+        exact = 1.0 / R if kind in MEAN_KINDS else 1.0 / (R * R)
         # a cap bulging upward is concave: the sign convention gives H < 0, K > 0
-        if kind == oracle.MEAN:
+        if kind in MEAN_KINDS:
             assert np.all(cmap[m] < 0)
         else:
             assert np.all(cmap[m] > 0)
@@ -125,8 +128,9 @@ def test_paraboloid_vertex():
         u = 0.5 * a * (x * x + y * y)
         kbar, _ = oracle.direction_curvatures(u, 3, 3)
         np.testing.assert_allclose(kbar, [a] * 4, rtol=1e-13)
-        assert oracle.curvature(u, 3, 3, oracle.MEAN) == pytest.approx(a, rel=1e-13)
-        assert oracle.curvature(u, 3, 3, oracle.GAUSS) == pytest.approx(a * a, rel=1e-13)
+        for km, kg in ((oracle.MEAN, oracle.GAUSS), (oracle.MEAN_EULER, oracle.GAUSS_EULER)):
+            assert oracle.curvature(u, 3, 3, km) == pytest.approx(a, rel=1e-13)
+            assert oracle.curvature(u, 3, 3, kg) == pytest.approx(a * a, rel=1e-13)
     errs = []
     for s in (0.4, 0.2, 0.1, 0.05):
         a, b = 1.5 * s, 0.5 * s
@@ -145,8 +149,51 @@ def test_saddle_has_zero_mean_curvature_at_centre():
     by symmetry; K < 0."""
     y, x = np.mgrid[-3:4, -3:4].astype(np.float64)
     u = 0.3 * (x * x - y * y)
-    assert abs(oracle.curvature(u, 3, 3, oracle.MEAN)) < 1e-15
-    assert oracle.curvature(u, 3, 3, oracle.GAUSS) < 0
+    for km, kg in ((oracle.MEAN, oracle.GAUSS), (oracle.MEAN_EULER, oracle.GAUSS_EULER)):
+        assert abs(oracle.curvature(u, 3, 3, km)) < 1e-15
+        assert oracle.curvature(u, 3, 3, kg) < 0
+
+
+def rotated_quadric(eps, k1, k2, phi):
+    """z = eps (k1 x'^2 + k2 y'^2) with (x', y') the pixel axes rotated by
+    phi: a critical point at the centre whose principal curvatures are the
+    eigenvalues of the Hessian, 2 eps k1 and 2 eps k2, along axes at angle phi
+    to the grid."""
+    y, x = np.mgrid[-3:4, -3:4].astype(np.float64)
+    xr = x * math.cos(phi) + y * math.sin(phi)
+    yr = -x * math.sin(phi) + y * math.cos(phi)
+    return eps * (k1 * xr * xr + k2 * yr * yr)
+
+
+@pytest.mark.parametrize("k1,k2", [(1.0, 0.3), (1.0, -0.5), (0.8, 0.0), (-0.6, -0.2)])
+def test_euler_fit_recovers_rotated_principal_curvatures(k1, k2):
+    """Kinds MEAN_EULER / GAUSS_EULER: the least-squares fit of Euler's
+    formula to the four direction curvatures returns H = eps (k1 + k2) and
+    K = 4 eps^2 k1 k2 at the vertex of a quadric for ANY orientation of its
+    principal axes, with an error that falls as eps^2 (the direction
+    curvatures are normal curvatures, exact up to the slope terms).  The
+    extreme sampled directions (kinds MEAN / GAUSS) give the right K only
+    when the axes lie along sampled directions: a cylinder turned by 22.5
+    degrees gets K != 0 from them, 0 from the fit."""
+    for phi in (0.0, math.pi / 8, 0.7, math.pi / 4 + 0.1, 2.0):
+        errs = []
+        for eps in (1e-2, 1e-3):
+            u = rotated_quadric(eps, k1, k2, phi)
+            H = oracle.curvature(u, 3, 3, oracle.MEAN_EULER)
+            K = oracle.curvature(u, 3, 3, oracle.GAUSS_EULER)
+            Hx, Kx = eps * (k1 + k2), 4 * eps * eps * k1 * k2
+            errs.append((abs(H - Hx), abs(K - Kx)))
+            assert H == pytest.approx(Hx, rel=1e-3, abs=1e-3 * eps * abs(k1))
+            assert K == pytest.approx(Kx, rel=1e-3, abs=1e-3 * eps * eps * k1 * k1)
+        # second order: a factor 10 in eps is a factor ~1000 in the error of H
+        # (relative error ~eps^2) and of K (~eps^4 absolute)
+        assert errs[1][0] <= errs[0][0] * 2e-3 + 1e-18
+        assert errs[1][1] <= errs[0][1] * 2e-4 + 1e-22
+    u = rotated_quadric(1e-3, 1.0, 0.0, math.pi / 8)   # cylinder at 22.5 degrees
+    assert abs(oracle.curvature(u, 3, 3, oracle.GAUSS_EULER)) < 1e-11
+    # extreme sampled directions: 2 eps cos^2(22.5 deg) and 2 eps sin^2(22.5 deg),
+    # product eps^2 / 2
+    assert oracle.curvature(u, 3, 3, oracle.GAUSS) == pytest.approx(0.5e-6, rel=1e-3)
 
 
 def test_translation_and_d4_invariance():
@@ -156,7 +203,7 @@ def test_translation_and_d4_invariance():
     rng = np.random.default_rng(3)
     u = rng.random((13, 17))
     f = rng.random((13, 17))
-    for kind in (oracle.MEAN, oracle.GAUSS):
+    for kind in ALL_KINDS:
         E = oracle.energy(u, f, 7.0, kind)
         assert oracle.energy(u + 0.37, f + 0.37, 7.0, kind) == pytest.approx(E, rel=1e-12)
         for k in range(4):
@@ -176,7 +223,7 @@ def test_energy_is_sum_of_pixel_terms():
     rng = np.random.default_rng(4)
     u = rng.random((6, 7))
     f = rng.random((6, 7))
-    for kind in (oracle.MEAN, oracle.GAUSS):
+    for kind in ALL_KINDS:
         cmap = oracle.curvature_map(u, kind)
         ref = np.sum(np.abs(cmap)) + 0.5 * 5.0 * np.sum((u - f) ** 2)
         assert oracle.energy(u, f, 5.0, kind) == pytest.approx(ref, rel=1e-13)

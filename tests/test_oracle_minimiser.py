@@ -10,7 +10,7 @@ import pytest
 import oracle
 import synth
 
-KINDS = [oracle.MEAN, oracle.GAUSS]
+KINDS = [oracle.MEAN, oracle.GAUSS, oracle.MEAN_EULER, oracle.GAUSS_EULER]
 
 
 def rand_img(H, W, seed, smooth=True):
