@@ -9,7 +9,14 @@
  * with kappa the mean curvature H = (kmin + kmax)/2 (kind 0) or the Gaussian
  * curvature K = kmin * kmax (kind 1) of the image surface (x, y, u(x, y)),
  * estimated from the eight tangent planes of each 3x3 window (Sec. 2.1,
- * Eq. distance to tri; Sec. 3).  Minimisation is the coloured
+ * Eq. distance to tri; Sec. 3): kmin and kmax are the extreme curvatures of
+ * the four directions W-E, N-S, NW-SE and NE-SW.  Kinds 2 and 3 (an
+ * extension, not in the paper) take H and K from a least-squares fit of
+ * Euler's formula kappa(theta) = a + b cos 2theta + s sin 2theta to those
+ * four direction curvatures instead: principal curvatures a -+ sqrt(b^2 +
+ * s^2), H = a (kind 2), K = a^2 - b^2 - s^2 (kind 3), exact in the limit for
+ * principal axes at any angle to the pixel grid.  Every entry point that
+ * takes `kind` accepts 0..3.  Minimisation is the coloured
  * block-subspace correction sweep: on each level of the fine-to-coarse
  * hierarchy (block sides 1, 2, 4, ...; Sec. 2.2), the blocks of one colour
  * (Sec. 2.3) each find the constant shift c that minimises F(u + c phi_A)

@@ -17,10 +17,12 @@ from .build import LIB, build as build_library
 __all__ = [
     "CMError", "Options", "Stats", "Context", "load", "cm_energy", "cm_curvature", "cm_phase",
     "cm_level", "cm_energy_noalloc", "cm_solve_batched",
-    "cm_solve", "cm_auto_levels", "MEAN", "GAUSS",
+    "cm_solve", "cm_auto_levels", "MEAN", "GAUSS", "MEAN_EULER", "GAUSS_EULER",
 ]
 
-MEAN, GAUSS = 0, 1
+# Curvature kinds: H or K from the extreme direction curvatures (Sec. 3), or
+# from a least-squares fit of Euler's formula to the four directions.
+MEAN, GAUSS, MEAN_EULER, GAUSS_EULER = 0, 1, 2, 3
 CM_OK, CM_ERR_INVALID, CM_ERR_CUDA, CM_ERR_OOM = 0, 1, 2, 3
 CM_ERR_TIMEOUT, CM_ERR_NUMERIC, CM_NOT_CONVERGED = 4, 5, 6
 STATUS_NAMES = {0: "CM_OK", 1: "CM_ERR_INVALID", 2: "CM_ERR_CUDA", 3: "CM_ERR_OOM",

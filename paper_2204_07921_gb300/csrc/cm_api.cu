@@ -144,6 +144,9 @@ int ensure_solve_state(cm_ctx* ctx) {
 }
 
 bool finite_positive(float a) { return isfinite(a) && a > 0.0f; }
+// Curvature kinds: 0 mean, 1 Gaussian (extreme directions), 2 mean, 3 Gaussian
+// (Euler fit).
+bool valid_kind(int kind) { return kind >= 0 && kind <= 3; }
 
 int check_opts(cm_ctx* ctx, const cm_options& o) {
     if (o.ncolors != 0 && o.ncolors != 2 && o.ncolors != 4 && o.ncolors != 9 && o.ncolors != 16)
@@ -393,7 +396,7 @@ const char* cm_last_error(const cm_ctx* ctx) { return ctx ? ctx->err.c_str() : "
 int cm_energy(cm_ctx* ctx, const float* u, const float* f, int H, int W, float alpha, int kind,
               double* E_host, void* stream) {
     if (!ctx) return CM_ERR_INVALID;
-    if (!u || !f || !E_host || H < 1 || W < 1 || !finite_positive(alpha) || (kind != 0 && kind != 1))
+    if (!u || !f || !E_host || H < 1 || W < 1 || !finite_positive(alpha) || !valid_kind(kind))
         return fail(ctx, CM_ERR_INVALID, "cm_energy: invalid argument");
     CM_CUDA(cudaSetDevice(ctx->device));
     int rc = ensure_partials(ctx, H, W);
@@ -409,7 +412,7 @@ int cm_energy(cm_ctx* ctx, const float* u, const float* f, int H, int W, float a
 
 int cm_curvature(cm_ctx* ctx, const float* u, int H, int W, int kind, float* out, void* stream) {
     if (!ctx) return CM_ERR_INVALID;
-    if (!u || !out || H < 1 || W < 1 || (kind != 0 && kind != 1))
+    if (!u || !out || H < 1 || W < 1 || !valid_kind(kind))
         return fail(ctx, CM_ERR_INVALID, "cm_curvature: invalid argument");
     CM_CUDA(cudaSetDevice(ctx->device));
     CM_CUDA(cm::launch_curvature(u, H, W, kind, out, (cudaStream_t)stream));
@@ -425,7 +428,7 @@ int cm_phase(cm_ctx* ctx, const float* S, float* R, const float* f, int H, int W
     int rc = check_opts(ctx, o);
     if (rc) return rc;
     if (!S || !R || !f || R == S || R == f || H < 1 || W < 1 || !finite_positive(alpha) ||
-        (kind != 0 && kind != 1))
+        !valid_kind(kind))
         return fail(ctx, CM_ERR_INVALID, "cm_phase: invalid argument");
     int lb = 0;
     while ((1 << lb) < b) ++lb;
@@ -449,7 +452,7 @@ int cm_level(cm_ctx* ctx, const float* S, float* R, const float* f, int H, int W
     int rc = check_opts(ctx, o);
     if (rc) return rc;
     if (!S || !R || !f || R == S || R == f || H < 1 || W < 1 || !finite_positive(alpha) ||
-        (kind != 0 && kind != 1))
+        !valid_kind(kind))
         return fail(ctx, CM_ERR_INVALID, "cm_level: invalid argument");
     int lb = 0;
     while ((1 << lb) < b) ++lb;
@@ -473,7 +476,7 @@ int cm_solve(cm_ctx* ctx, const float* f, int H, int W, float alpha, int kind, i
     int rc = check_opts(ctx, o);
     if (rc) return rc;
     if (!f || !u_out || u_out == f || H < 1 || W < 1 || !finite_positive(alpha) ||
-        (kind != 0 && kind != 1) || levels < 0 || cycles < 0 || !(tol >= 0.0) || !isfinite(tol))
+        !valid_kind(kind) || levels < 0 || cycles < 0 || !(tol >= 0.0) || !isfinite(tol))
         return fail(ctx, CM_ERR_INVALID, "cm_solve: invalid argument");
     const int L = levels > 0 ? levels : cm_auto_levels(H, W);
     if (L - 1 > cm::max_level_log2()) return fail(ctx, CM_ERR_INVALID, "cm_solve: too many levels");
@@ -611,7 +614,7 @@ int cm_warmstart(cm_ctx* ctx, cm_net* net, const float* f, int N, int H, int W, 
                  int check_energy, float alpha, int kind, int* used_host, void* stream) {
     if (!ctx) return CM_ERR_INVALID;
     if (!net || !f || !u0_out || u0_out == f || N < 1 || H < 1 || W < 1 ||
-        (check_energy && (!finite_positive(alpha) || (kind != 0 && kind != 1))))
+        (check_energy && (!finite_positive(alpha) || !valid_kind(kind))))
         return fail(ctx, CM_ERR_INVALID, "cm_warmstart: invalid argument");
     CM_CUDA(cudaSetDevice(ctx->device));
     cudaStream_t st = (cudaStream_t)stream;
@@ -677,7 +680,7 @@ int cm_solve_batched(cm_ctx* ctx, int n, const float* const* f, const int* H, co
         return fail(ctx, CM_ERR_INVALID, "cm_solve_batched: invalid argument");
     for (int i = 0; i < n; ++i) {
         if (!f[i] || !u_out[i] || u_out[i] == f[i] || H[i] < 1 || W[i] < 1 ||
-            !finite_positive(alpha[i]) || (kind[i] != 0 && kind[i] != 1))
+            !finite_positive(alpha[i]) || !valid_kind(kind[i]))
             return fail(ctx, CM_ERR_INVALID, "cm_solve_batched: invalid image " + std::to_string(i));
         const int L = levels > 0 ? levels : cm_auto_levels(H[i], W[i]);
         if (L - 1 > cm::max_level_log2())

@@ -28,7 +28,10 @@
 
 namespace cm {
 
-enum { KIND_MEAN = 0, KIND_GAUSS = 1 };
+// Curvature kinds: kappa = H or K from the extreme direction curvatures
+// (Sec. 3), or from a least-squares fit of Euler's formula to the four
+// directions (an extension; see kappa_abs).
+enum { KIND_MEAN = 0, KIND_GAUSS = 1, KIND_MEAN_EULER = 2, KIND_GAUSS_EULER = 3 };
 
 // Direction curvature of one line.  h2 = h^2 (1 or 2), two_h = 2h.
 __device__ __forceinline__ float dir_kbar(float A, float B, float O, float Z1, float Z2,
@@ -64,12 +67,40 @@ __device__ __forceinline__ KBar4 direction_curvatures(const float w[9]) {
     return r;
 }
 
-// |H| or |K| of the pixel whose 3x3 window is w.
-__device__ __forceinline__ float abs_curvature(const float w[9], int kind) {
-    KBar4 r = direction_curvatures(w);
-    float kmin = fminf(fminf(r.k[0], r.k[1]), fminf(r.k[2], r.k[3]));
-    float kmax = fmaxf(fmaxf(r.k[0], r.k[1]), fmaxf(r.k[2], r.k[3]));
-    return kind == KIND_MEAN ? fabsf(0.5f * (kmin + kmax)) : fabsf(kmin * kmax);
+// Signed kappa of a pixel from its direction curvatures k0 (W-E), k1 (N-S),
+// k2 (NW-SE) and k3 (NE-SW).
+//  KIND_MEAN, KIND_GAUSS: principal curvatures = the extreme directions,
+//    H = (kmin + kmax) / 2, K = kmin kmax (Sec. 3, Eq. MCM / Eq. GCM).
+//  KIND_MEAN_EULER, KIND_GAUSS_EULER: Euler's formula
+//    kappa(theta) = a + b cos 2 theta + s sin 2 theta sampled at theta = 0,
+//    90, 45 and 135 degrees.  The columns (1, cos 2 theta, sin 2 theta) of
+//    these four samples are orthogonal, so the least-squares fit is
+//    a = (k0 + k1 + k2 + k3) / 4, b = (k0 - k1) / 2, s = (k2 - k3) / 2, and
+//    the principal curvatures are a -+ sqrt(b^2 + s^2): H = a,
+//    K = a^2 - b^2 - s^2.
+template <int KIND>
+__device__ __forceinline__ float kappa_signed(float k0, float k1, float k2, float k3) {
+    if (KIND == KIND_MEAN || KIND == KIND_GAUSS) {
+        const float kmin = fminf(fminf(k0, k1), fminf(k2, k3));
+        const float kmax = fmaxf(fmaxf(k0, k1), fmaxf(k2, k3));
+        return KIND == KIND_MEAN ? 0.5f * (kmin + kmax) : kmin * kmax;
+    }
+    const float a = 0.25f * ((k0 + k1) + (k2 + k3));
+    if (KIND == KIND_MEAN_EULER) return a;
+    const float b = 0.5f * (k0 - k1), s = 0.5f * (k2 - k3);
+    return fmaf(a, a, -fmaf(b, b, s * s));
+}
+
+template <int KIND>
+__device__ __forceinline__ float kappa_abs(float k0, float k1, float k2, float k3) {
+    return fabsf(kappa_signed<KIND>(k0, k1, k2, k3));
+}
+
+// |kappa| of the pixel whose 3x3 window is w (kind known at compile time).
+template <int KIND>
+__device__ __forceinline__ float abs_curvature(const float w[9]) {
+    const KBar4 r = direction_curvatures(w);
+    return kappa_abs<KIND>(r.k[0], r.k[1], r.k[2], r.k[3]);
 }
 
 // ---------------------------------------------------------------------------
@@ -146,9 +177,7 @@ template <int KIND>
 __device__ __forceinline__ float aff_abs_curv(const AffPix& p, float c) {
     const float k0 = aff_kbar(p.d[0], 1.0f, c), k1 = aff_kbar(p.d[1], 1.0f, c);
     const float k2 = aff_kbar(p.d[2], 2.0f, c), k3 = aff_kbar(p.d[3], 2.0f, c);
-    const float kmin = fminf(fminf(k0, k1), fminf(k2, k3));
-    const float kmax = fmaxf(fmaxf(k0, k1), fmaxf(k2, k3));
-    return KIND == KIND_MEAN ? 0.5f * fabsf(kmin + kmax) : fabsf(kmin * kmax);
+    return kappa_abs<KIND>(k0, k1, k2, k3);
 }
 
 // Clamp-to-edge boundary: out-of-image neighbours take the nearest pixel.

@@ -1,6 +1,7 @@
 // cm_energy.cu -- discrete energy and curvature map kernels.
 //
-//  energy_kernel     F(u) = sum |kappa| + alpha/2 (u - f)^2 (Eq. MCM / Eq. GCM):
+//  energy_kernel     F(u) = sum |kappa| + alpha/2 (u - f)^2 (Eq. MCM / Eq. GCM;
+//                    kappa of any of the four kinds of kappa_signed):
 //                    smem halo tile, FP32 per pixel, FP64 CTA partials and a
 //                    fixed-order FP64 finish in the last CTA (deterministic).
 //  curvature_kernel  signed kappa per pixel (diagnostics and tests).
@@ -49,7 +50,7 @@ __global__ void __launch_bounds__(256) energy_kernel(const float* __restrict__ u
 #pragma unroll
                 for (int b = 0; b < 3; ++b) w[3 * a + b] = tile[lr + a][tx + b];
             float e = w[4] - f[(size_t)r * W + c];
-            acc += abs_curvature(w, KIND) + 0.5f * alpha * e * e;
+            acc += abs_curvature<KIND>(w) + 0.5f * alpha * e * e;
         }
     }
     double d = (double)acc;
@@ -98,18 +99,23 @@ __global__ void curvature_kernel(const float* __restrict__ u, int H, int W,
 #pragma unroll
         for (int b = 0; b < 3; ++b)
             w[3 * a + b] = u[(size_t)clampi(r + a - 1, 0, H - 1) * W + clampi(c + b - 1, 0, W - 1)];
-    KBar4 k = direction_curvatures(w);
-    float kmin = fminf(fminf(k.k[0], k.k[1]), fminf(k.k[2], k.k[3]));
-    float kmax = fmaxf(fmaxf(k.k[0], k.k[1]), fmaxf(k.k[2], k.k[3]));
-    out[(size_t)r * W + c] = KIND == KIND_MEAN ? 0.5f * (kmin + kmax) : kmin * kmax;
+    const KBar4 k = direction_curvatures(w);
+    out[(size_t)r * W + c] = kappa_signed<KIND>(k.k[0], k.k[1], k.k[2], k.k[3]);
 }
 
 cudaError_t launch_energy(const float* u, const float* f, int H, int W, float alpha, int kind,
                           double* partials, unsigned int* ticket, double* E_out,
                           cudaStream_t st, const int* active) {
     dim3 grid((W + E_TW - 1) / E_TW, (H + E_TH - 1) / E_TH);
-    return launch_k(kind == KIND_MEAN ? energy_kernel<KIND_MEAN> : energy_kernel<KIND_GAUSS>, grid,
-                    dim3(256), st, 1, u, f, H, W, alpha, partials, ticket, E_out, active);
+    decltype(&energy_kernel<KIND_MEAN>) k;
+    switch (kind) {
+        case KIND_MEAN: k = energy_kernel<KIND_MEAN>; break;
+        case KIND_GAUSS: k = energy_kernel<KIND_GAUSS>; break;
+        case KIND_MEAN_EULER: k = energy_kernel<KIND_MEAN_EULER>; break;
+        case KIND_GAUSS_EULER: k = energy_kernel<KIND_GAUSS_EULER>; break;
+        default: return cudaErrorInvalidValue;
+    }
+    return launch_k(k, grid, dim3(256), st, 1, u, f, H, W, alpha, partials, ticket, E_out, active);
 }
 
 size_t energy_partials_needed(int H, int W) {
@@ -119,10 +125,17 @@ size_t energy_partials_needed(int H, int W) {
 cudaError_t launch_curvature(const float* u, int H, int W, int kind, float* out,
                              cudaStream_t st) {
     dim3 blk(32, 8), grid((W + 31) / 32, (H + 7) / 8);
-    if (kind == KIND_MEAN)
-        curvature_kernel<KIND_MEAN><<<grid, blk, 0, st>>>(u, H, W, out);
-    else
-        curvature_kernel<KIND_GAUSS><<<grid, blk, 0, st>>>(u, H, W, out);
+    switch (kind) {
+        case KIND_MEAN: curvature_kernel<KIND_MEAN><<<grid, blk, 0, st>>>(u, H, W, out); break;
+        case KIND_GAUSS: curvature_kernel<KIND_GAUSS><<<grid, blk, 0, st>>>(u, H, W, out); break;
+        case KIND_MEAN_EULER:
+            curvature_kernel<KIND_MEAN_EULER><<<grid, blk, 0, st>>>(u, H, W, out);
+            break;
+        case KIND_GAUSS_EULER:
+            curvature_kernel<KIND_GAUSS_EULER><<<grid, blk, 0, st>>>(u, H, W, out);
+            break;
+        default: return cudaErrorInvalidValue;
+    }
     return cudaGetLastError();
 }
 

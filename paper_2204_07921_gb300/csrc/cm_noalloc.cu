@@ -49,7 +49,7 @@ int scratch_for_current_device(void** out) {
 extern "C" int cm_energy_noalloc(const float* u, const float* f, int H, int W, float alpha,
                                  int kind, double* E_dev, void* stream) {
     if (!u || !f || !E_dev || H < 1 || W < 1 || !(alpha > 0.0f) || alpha != alpha ||
-        alpha > 3.0e38f || (kind != 0 && kind != 1))
+        alpha > 3.0e38f || kind < 0 || kind > 3)
         return CM_ERR_INVALID;
     // the energy kernel's grid has one CTA per 32 x 32 tile
     if (cm::energy_partials_needed(H, W) > (size_t)CM_NOALLOC_MAX_TILES) return CM_ERR_INVALID;

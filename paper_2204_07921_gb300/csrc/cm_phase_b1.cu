@@ -47,7 +47,7 @@ __device__ __forceinline__ float paper_candidate(const float w[9], float fstar, 
     dir_dist(w[0], w[8], w[4], w[2], w[6], 8.0f, SQ2x2, d[4], d[5]);
     dir_dist(w[2], w[6], w[4], w[0], w[8], 8.0f, SQ2x2, d[6], d[7]);
     float chalf;
-    if (KIND == KIND_MEAN) {
+    if (KIND == KIND_MEAN || KIND == KIND_MEAN_EULER) {
         chalf = 0.125f * (((d[0] + d[1]) + (d[2] + d[3])) + ((d[4] + d[5]) + (d[6] + d[7])));
     } else {
         KBar4 k = direction_curvatures(w);
@@ -85,7 +85,10 @@ template <> struct PosLines<6> { static constexpr int TF = 3, TH = 2, ZI = 1; };
 struct NbConst {
     float dq0, dl0, e10, e20;             // full direction at c = 0
     float eh0, fds, ds4, thd, kh0;        // half direction
-    float kmin_ab, kmax_ab;               // the two constant directions
+    // the two constant directions ka, kb: (min, max) for the extreme-direction
+    // kinds; (ka + kb, ((ka - kb) / 2)^2) for the Euler-fit kinds, whose
+    // constant pair is the other orthogonal pair of lines
+    float kab0, kab1;
 };
 
 template <int DR, int DC>
@@ -96,10 +99,11 @@ __device__ __forceinline__ void nb_window(const float w25[25], float w[9]) {
         for (int b = 0; b < 3; ++b) w[3 * a + b] = w25[5 * (1 + DR + a) + (1 + DC + b)];
 }
 
-template <int DR, int DC>
+template <int KIND, int DR, int DC>
 __device__ __forceinline__ NbConst nb_init(const float w25[25]) {
     constexpr int POS = 4 - 3 * DR - DC;
     constexpr int TF = PosLines<POS>::TF, TH = PosLines<POS>::TH, ZI = PosLines<POS>::ZI;
+    static_assert((TF >> 1) == (TH >> 1), "the moving lines are one orthogonal pair");
     float w[9];
     nb_window<DR, DC>(w25, w);
     NbConst n;
@@ -116,8 +120,14 @@ __device__ __forceinline__ NbConst nb_init(const float w25[25]) {
                 kb = k.k[t];
             }
         }
-    n.kmin_ab = fminf(ka, kb);
-    n.kmax_ab = fmaxf(ka, kb);
+    if (KIND == KIND_MEAN || KIND == KIND_GAUSS) {
+        n.kab0 = fminf(ka, kb);
+        n.kab1 = fmaxf(ka, kb);
+    } else {
+        const float hd = 0.5f * (ka - kb);
+        n.kab0 = ka + kb;
+        n.kab1 = hd * hd;
+    }
     {   // full direction: affine coefficients at c = 0
         const int X = line_x(TF), Y = line_y(TF);
         const float two_h = line_two_h(TF);
@@ -161,9 +171,17 @@ __device__ __forceinline__ float nb_eval(const NbConst& n, float c) {
     const float kf = fmaf(dl1, c, n.dl0) * r;
     const float e = fmaf(-2.0f, c, n.eh0);
     const float kh = fmaf(n.thd, rsqrtf(fmaf(e, e, n.fds) * n.ds4), n.kh0);
-    const float kmin = fminf(fminf(kf, kh), n.kmin_ab);
-    const float kmax = fmaxf(fmaxf(kf, kh), n.kmax_ab);
-    return KIND == KIND_MEAN ? 0.5f * fabsf(kmin + kmax) : fabsf(kmin * kmax);
+    if (KIND == KIND_MEAN || KIND == KIND_GAUSS) {
+        const float kmin = fminf(fminf(kf, kh), n.kab0);
+        const float kmax = fmaxf(fmaxf(kf, kh), n.kab1);
+        return KIND == KIND_MEAN ? 0.5f * fabsf(kmin + kmax) : fabsf(kmin * kmax);
+    }
+    // Euler fit (kappa_signed): a = (kf + kh + ka + kb) / 4; the moving pair
+    // contributes ((kf - kh) / 2)^2 and the constant pair kab1 to b^2 + s^2
+    const float a = 0.25f * ((kf + kh) + n.kab0);
+    if (KIND == KIND_MEAN_EULER) return fabsf(a);
+    const float hd = 0.5f * (kf - kh);
+    return fabsf(fmaf(a, a, -fmaf(hd, hd, n.kab1)));
 }
 
 // Tile of one CTA: 128 active pixels of the colour.  Checkerboard: 32 x 8
@@ -245,16 +263,14 @@ __global__ void __launch_bounds__(128, CM_B1_MIN_BLOCKS) phase_b1_kernel(const f
             ncs[t] = -sr;
             csd[t] = sr * fmaf(0.5f, w[line_x(t)] + w[line_y(t)], -w[4]);
         }
-        const NbConst n0 = nb_init<-1, -1>(w25), n1 = nb_init<-1, 0>(w25),
-                      n2 = nb_init<-1, 1>(w25), n3 = nb_init<0, -1>(w25),
-                      n4 = nb_init<0, 1>(w25), n5 = nb_init<1, -1>(w25),
-                      n6 = nb_init<1, 0>(w25), n7 = nb_init<1, 1>(w25);
+        const NbConst n0 = nb_init<KIND, -1, -1>(w25), n1 = nb_init<KIND, -1, 0>(w25),
+                      n2 = nb_init<KIND, -1, 1>(w25), n3 = nb_init<KIND, 0, -1>(w25),
+                      n4 = nb_init<KIND, 0, 1>(w25), n5 = nb_init<KIND, 1, -1>(w25),
+                      n6 = nb_init<KIND, 1, 0>(w25), n7 = nb_init<KIND, 1, 1>(w25);
         auto ring_fast = [&](float cc) {
             const float k0 = fmaf(ncs[0], cc, csd[0]), k1 = fmaf(ncs[1], cc, csd[1]);
             const float k2 = fmaf(ncs[2], cc, csd[2]), k3 = fmaf(ncs[3], cc, csd[3]);
-            const float kmin = fminf(fminf(k0, k1), fminf(k2, k3));
-            const float kmax = fmaxf(fmaxf(k0, k1), fmaxf(k2, k3));
-            float acc = KIND == KIND_MEAN ? 0.5f * fabsf(kmin + kmax) : fabsf(kmin * kmax);
+            float acc = kappa_abs<KIND>(k0, k1, k2, k3);
             acc += nb_eval<KIND, -1, -1>(n0, cc);
             acc += nb_eval<KIND, -1, 0>(n1, cc);
             acc += nb_eval<KIND, -1, 1>(n2, cc);
@@ -292,7 +308,7 @@ __global__ void __launch_bounds__(128, CM_B1_MIN_BLOCKS) phase_b1_kernel(const f
                     for (int a = 0; a < 3; ++a)
 #pragma unroll
                         for (int b = 0; b < 3; ++b) w[3 * a + b] = v[5 * (qr + a) + (qc + b)];
-                    float t = abs_curvature(w, KIND);
+                    float t = abs_curvature<KIND>(w);
                     acc += ((ringv >> (3 * qr + qc)) & 1u) ? t : 0.0f;
                 }
             return acc;
@@ -304,7 +320,8 @@ __global__ void __launch_bounds__(128, CM_B1_MIN_BLOCKS) phase_b1_kernel(const f
     if (c_out) c_out[p] = cbest;
 }
 
-cudaError_t launch_phase_b1(const PhaseArgs& A, cudaStream_t st) {
+template <int KIND>
+static cudaError_t launch_b1_kind(const PhaseArgs& A, cudaStream_t st) {
     SearchParams sp{A.alpha, A.G, A.K};
     sp.one_step = A.one_step;
     auto go = [&](auto kern, int TW, int TH) {
@@ -313,24 +330,21 @@ cudaError_t launch_phase_b1(const PhaseArgs& A, cudaStream_t st) {
                         A.use_paper, A.c_out, A.active);
     };
     switch (A.ncolors) {
-        case 2:
-            return A.kind == KIND_MEAN
-                       ? go(phase_b1_kernel<KIND_MEAN, 2>, B1Tile<2>::TW, B1Tile<2>::TH)
-                       : go(phase_b1_kernel<KIND_GAUSS, 2>, B1Tile<2>::TW, B1Tile<2>::TH);
-        case 4:
-            return A.kind == KIND_MEAN
-                       ? go(phase_b1_kernel<KIND_MEAN, 4>, B1Tile<4>::TW, B1Tile<4>::TH)
-                       : go(phase_b1_kernel<KIND_GAUSS, 4>, B1Tile<4>::TW, B1Tile<4>::TH);
-        case 9:
-            return A.kind == KIND_MEAN
-                       ? go(phase_b1_kernel<KIND_MEAN, 9>, B1Tile<9>::TW, B1Tile<9>::TH)
-                       : go(phase_b1_kernel<KIND_GAUSS, 9>, B1Tile<9>::TW, B1Tile<9>::TH);
-        case 16:
-            return A.kind == KIND_MEAN
-                       ? go(phase_b1_kernel<KIND_MEAN, 16>, B1Tile<16>::TW, B1Tile<16>::TH)
-                       : go(phase_b1_kernel<KIND_GAUSS, 16>, B1Tile<16>::TW, B1Tile<16>::TH);
-        default:
-            return cudaErrorInvalidValue;
+        case 2: return go(phase_b1_kernel<KIND, 2>, B1Tile<2>::TW, B1Tile<2>::TH);
+        case 4: return go(phase_b1_kernel<KIND, 4>, B1Tile<4>::TW, B1Tile<4>::TH);
+        case 9: return go(phase_b1_kernel<KIND, 9>, B1Tile<9>::TW, B1Tile<9>::TH);
+        case 16: return go(phase_b1_kernel<KIND, 16>, B1Tile<16>::TW, B1Tile<16>::TH);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_phase_b1(const PhaseArgs& A, cudaStream_t st) {
+    switch (A.kind) {
+        case KIND_MEAN: return launch_b1_kind<KIND_MEAN>(A, st);
+        case KIND_GAUSS: return launch_b1_kind<KIND_GAUSS>(A, st);
+        case KIND_MEAN_EULER: return launch_b1_kind<KIND_MEAN_EULER>(A, st);
+        case KIND_GAUSS_EULER: return launch_b1_kind<KIND_GAUSS_EULER>(A, st);
+        default: return cudaErrorInvalidValue;
     }
 }
 

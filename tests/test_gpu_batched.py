@@ -27,7 +27,7 @@ def test_batched_equals_single_solves(tol, cycles):
     images do (different sizes, level counts, kinds, alphas and stopping
     cycles)."""
     imgs = [synth.piecewise_image(H, W, 900 + i, 6, 0.08) for i, (H, W) in enumerate(SHAPES)]
-    kinds = [i % 2 for i in range(len(imgs))]
+    kinds = [i % 4 for i in range(len(imgs))]   # all four curvature kinds
     alphas = [20.0 if i % 3 else 10.0 for i in range(len(imgs))]
     fs = [dev(im.f) for im in imgs]
     ub, sb = cm.cm_solve_batched(fs, alphas, kinds, cycles=cycles, tol=tol)
@@ -70,4 +70,4 @@ def test_batched_invalid_arguments():
     with pytest.raises(cm.CMError):
         cm.cm_solve_batched([f, f], [1.0, -1.0], [0, 0])
     with pytest.raises(cm.CMError):
-        cm.cm_solve_batched([f], [1.0], [3])
+        cm.cm_solve_batched([f], [1.0], [4])    # kinds are 0..3

@@ -29,10 +29,11 @@ def host(t):
 
 
 SHAPES = [(64, 64), (67, 45), (130, 97), (1, 37), (37, 1), (1, 1), (5, 3)]
+ALL_KINDS = [cm.MEAN, cm.GAUSS, cm.MEAN_EULER, cm.GAUSS_EULER]
 
 
 @pytest.mark.parametrize("shape", SHAPES)
-@pytest.mark.parametrize("kind", [cm.MEAN, cm.GAUSS])
+@pytest.mark.parametrize("kind", ALL_KINDS)
 def test_energy_parity(shape, kind):
     H, W = shape
     img = synth.piecewise_image(H, W, 1000 + H * 7 + W, 5, 0.08)
@@ -43,7 +44,7 @@ def test_energy_parity(shape, kind):
     assert Eg == pytest.approx(Eo, rel=2e-6, abs=1e-9)
 
 
-@pytest.mark.parametrize("kind", [cm.MEAN, cm.GAUSS])
+@pytest.mark.parametrize("kind", ALL_KINDS)
 def test_energy_full_size_and_deterministic(kind):
     img = synth.large(1024)
     u, f = to_dev(img.f), to_dev(img.clean)
@@ -54,7 +55,7 @@ def test_energy_full_size_and_deterministic(kind):
     assert E1 == pytest.approx(Eo, rel=2e-6)
 
 
-@pytest.mark.parametrize("kind", [cm.MEAN, cm.GAUSS])
+@pytest.mark.parametrize("kind", ALL_KINDS)
 def test_curvature_parity(kind):
     img = synth.piecewise_image(67, 45, 5, 6, 0.1)
     kg = host(cm.cm_curvature(to_dev(img.f), kind))
@@ -65,7 +66,7 @@ def test_curvature_parity(kind):
         for c in range(45):
             kb, _ = oracle.direction_curvatures(u64, r, c)
             scale[r, c] = np.max(np.abs(kb))
-    bound = 2e-5 * (1 + scale) if kind == cm.MEAN else 2e-5 * (1 + scale) ** 2
+    bound = 2e-5 * (1 + scale) if kind in (cm.MEAN, cm.MEAN_EULER) else 2e-5 * (1 + scale) ** 2
     assert np.all(np.abs(kg - ko) <= bound)
 
 
@@ -117,7 +118,7 @@ def levels_for(H, W):
 
 
 @pytest.mark.parametrize("shape", [(64, 64), (67, 45), (130, 97), (1, 37), (37, 1), (5, 3)])
-@pytest.mark.parametrize("kind", [cm.MEAN, cm.GAUSS])
+@pytest.mark.parametrize("kind", ALL_KINDS)
 @pytest.mark.parametrize("ncolors", [2, 4])
 def test_phase_parity_small(shape, kind, ncolors):
     """Every level (plus one beyond the automatic count) and colour, from a
@@ -210,9 +211,11 @@ def test_solve_equals_level_sequence_and_is_deterministic(shape):
                                   ((1024, 1024), cm.MEAN, 20.0, (64, 512)),
                                   ((300, 260), cm.MEAN, 20.0, (64, 128)),
                                   ((2600, 300), cm.MEAN, 20.0, (1024, 2048)),
-                                  ((2600, 300), cm.GAUSS, 15.0, (1024, 2048))],
+                                  ((2600, 300), cm.GAUSS, 15.0, (1024, 2048)),
+                                  ((520, 600), cm.MEAN_EULER, 20.0, (64, 128, 256)),
+                                  ((520, 600), cm.GAUSS_EULER, 15.0, (64, 128, 256))],
                          ids=["512-gauss", "1024-mean", "300x260-mean", "2600x300-mean",
-                              "2600x300-gauss"])
+                              "2600x300-gauss", "520x600-mean-euler", "520x600-gauss-euler"])
 def test_level_parity_coarse(case):
     """Coarse levels through cm_level (tile sums, deferred apply): R = S + c
     on every block, and each colour's shifts match the oracle solved from the
@@ -257,7 +260,7 @@ def test_level_parity_coarse(case):
     assert ties <= max(2, 0.02 * tot)
 
 
-@pytest.mark.parametrize("kind", [cm.MEAN, cm.GAUSS])
+@pytest.mark.parametrize("kind", ALL_KINDS)
 def test_per_sweep_parity_64(kind):
     """The 64x64 workload (6 shapes, sigma 0.05, alpha 20), 20 cycles: each
     phase of each cycle is compared with the oracle started from the GPU's
@@ -299,7 +302,7 @@ def test_per_sweep_parity_64(kind):
     assert Eg == pytest.approx(Eo, rel=2e-6)
 
 
-@pytest.mark.parametrize("kind", [cm.MEAN, cm.GAUSS])
+@pytest.mark.parametrize("kind", ALL_KINDS)
 def test_solve_final_energy_vs_oracle_64(kind):
     """The 64x64 workload (2 colours, 20 cycles).  The GPU's FP64-reduced
     final energy equals the oracle's FP64 energy of the GPU's result to 1e-5
@@ -388,6 +391,10 @@ def test_invalid_arguments_rejected():
     with pytest.raises(cm.CMError) as e:
         cm.cm_solve(bad, 1.0, 0, cycles=1)
     assert e.value.code == cm.CM_ERR_NUMERIC
+    for kind in (-1, 4):
+        with pytest.raises(cm.CMError) as e:
+            cm.cm_solve(f, 1.0, kind, cycles=1)
+        assert e.value.code == cm.CM_ERR_INVALID
 
 
 def test_constant_image_fixed_point_gpu():
