@@ -66,11 +66,12 @@ def lib():
                 "orc_paper_candidate": (d, [dp, dp, i, i, i, i, d, i]),
                 "orc_block_min": (d, [dp, dp, i, i, i, i, i, i, d, i, i, i, i, i, i, dp]),
                 "orc_block_colour": (i, [i, i, i]),
-                "orc_auto_levels": (i, [i, i]),
+                "orc_auto_levels": (i, [i, i, i]),
+                "orc_level_side": (i, [i, i]),
                 "orc_phase": (i, [dp, dp, i, i, d, i, i, i, i, i, i, i, i, dp]),
                 "orc_level_sequential": (None, [dp, dp, i, i, d, i, i, i, i, i, i]),
-                "orc_cycle": (None, [dp, dp, i, i, d, i, i, i, i, i, i, i, i, i]),
-                "orc_solve": (i, [dp, i, i, d, i, i, i, d, dp, dp, i, i, i, i, i, i, i, dp, ip]),
+                "orc_cycle": (None, [dp, dp, i, i, d, i, i, i, i, i, i, i, i, i, i]),
+                "orc_solve": (i, [dp, i, i, d, i, i, i, d, dp, dp, i, i, i, i, i, i, i, i, dp, ip]),
                 "orc_level_colours": (i, [i, i]),
                 "orc_num_threads": (i, []),
                 "orc_local_energy_batch": (None, [dp, dp, i, i, i, i, i, i, d, i, dp, i, dp]),
@@ -171,8 +172,14 @@ def block_colour(bi, bj, ncolors) -> int:
     return lib().orc_block_colour(bi, bj, ncolors)
 
 
-def auto_levels(H, W) -> int:
-    return lib().orc_auto_levels(H, W)
+def auto_levels(H, W, sides=0) -> int:
+    """Default level count (sides = 1: the paper's block sides 2^j - 1)."""
+    return lib().orc_auto_levels(H, W, int(sides))
+
+
+def level_side(j, sides=0) -> int:
+    """Block side of level j = 1, 2, ...: 2^(j-1), or 2^j - 1 with sides = 1."""
+    return lib().orc_level_side(j, int(sides))
 
 
 def phase(u, f, alpha, kind, b, ncolors, k, G=DEFAULT_G, K=DEFAULT_K, use_paper=True,
@@ -204,17 +211,18 @@ def level_colours(ncolors, b) -> int:
 
 
 def cycle(u, f, alpha, kind, levels=0, ncolors=2, G=DEFAULT_G, K=DEFAULT_K, use_paper=True,
-          sequential=False, one_step=False, vcycle=False):
+          sequential=False, one_step=False, vcycle=False, sides=0):
     u = _f64(u).copy()
     f = _f64(f)
     H, W = u.shape
     lib().orc_cycle(_dp(u), _dp(f), H, W, float(alpha), kind, levels, ncolors, G, K,
-                    int(use_paper), int(one_step), int(sequential), int(vcycle))
+                    int(use_paper), int(one_step), int(sequential), int(vcycle), int(sides))
     return u
 
 
 def solve(f, alpha, kind, levels=0, cycles=20, tol=0.0, u0=None, ncolors=2, G=DEFAULT_G,
-          K=DEFAULT_K, use_paper=True, sequential=False, one_step=False, vcycle=False):
+          K=DEFAULT_K, use_paper=True, sequential=False, one_step=False, vcycle=False,
+          sides=0):
     """Alg. 3 outer loop.  Returns (u, trace, cycles_run, converged)."""
     f = _f64(f)
     H, W = f.shape
@@ -227,7 +235,7 @@ def solve(f, alpha, kind, levels=0, cycles=20, tol=0.0, u0=None, ncolors=2, G=DE
         u0p = _dp(u0a)
     n = lib().orc_solve(_dp(f), H, W, float(alpha), kind, levels, cycles, float(tol), u0p,
                         _dp(u), ncolors, G, K, int(use_paper), int(one_step), int(sequential),
-                        int(vcycle), _dp(trace),
+                        int(vcycle), int(sides), _dp(trace),
                         ctypes.byref(conv))
     return u, trace[: n + 1], n, bool(conv.value)
 

@@ -499,10 +499,18 @@ int orc_level_colours(int ncolors, int b) {
     return p * p;
 }
 
-int orc_auto_levels(int H, int W) {
+/* Block side of level j = 1, 2, ...  sides = 0: b_j = 2^(j-1) (the reading
+ * used by default; see the notes on Sec. 2.2); sides = 1: the paper's
+ * patches of (2^j - 1) x (2^j - 1) pixels, m_j = ceil(m / (2^j - 1)) patches
+ * down a column (Sec. 2.2). */
+int orc_level_side(int j, int sides) { return sides ? (1 << j) - 1 : 1 << (j - 1); }
+
+/* Default level count: the coarsest block side is the largest one <= half
+ * the shorter image side. */
+int orc_auto_levels(int H, int W, int sides) {
     int m = H < W ? H : W;
-    int L = 1, b = 1;
-    while (2 * b <= m / 2) { b *= 2; ++L; }
+    int L = 1;
+    while (orc_level_side(L + 1, sides) <= m / 2) ++L;
     return L;
 }
 
@@ -565,12 +573,12 @@ void orc_level_sequential(double *u, const double *f, int H, int W, double alpha
  * back up, levels L - 1 .. 1 (the full V-cycle the paper compares against). */
 void orc_cycle(double *u, const double *f, int H, int W, double alpha, int kind, int levels,
                int ncolors, int G, int K, int use_paper, int one_step, int sequential,
-               int vcycle) {
-    if (levels <= 0) levels = orc_auto_levels(H, W);
+               int vcycle, int sides) {
+    if (levels <= 0) levels = orc_auto_levels(H, W, sides);
     int nsteps = vcycle ? 2 * levels - 1 : levels;
     for (int s = 0; s < nsteps; ++s) {
         int j = s < levels ? s + 1 : 2 * levels - 1 - s;
-        int b = 1 << (j - 1);
+        int b = orc_level_side(j, sides);
         if (sequential) {
             orc_level_sequential(u, f, H, W, alpha, kind, b, G, K, use_paper, one_step);
         } else {
@@ -588,7 +596,7 @@ void orc_cycle(double *u, const double *f, int H, int W, double alpha, int kind,
  * F(u_0), F(u_1), ...  Returns the number of cycles run; *converged is set. */
 int orc_solve(const double *f, int H, int W, double alpha, int kind, int levels, int cycles,
               double tol, const double *u0, double *u_out, int ncolors, int G, int K,
-              int use_paper, int one_step, int sequential, int vcycle, double *trace,
+              int use_paper, int one_step, int sequential, int vcycle, int sides, double *trace,
               int *converged) {
     size_t N = (size_t)H * W;
     if (u0) memcpy(u_out, u0, N * sizeof(double));
@@ -598,7 +606,7 @@ int orc_solve(const double *f, int H, int W, double alpha, int kind, int levels,
     int l = 0, conv = 0;
     while (l < cycles) {
         orc_cycle(u_out, f, H, W, alpha, kind, levels, ncolors, G, K, use_paper, one_step,
-                  sequential, vcycle);
+                  sequential, vcycle, sides);
         ++l;
         double E = orc_energy(u_out, f, H, W, alpha, kind);
         if (trace) trace[l] = E;

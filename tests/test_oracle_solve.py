@@ -198,3 +198,63 @@ def test_vcycle_is_half_cycle_then_levels_back_up():
         for k in range(4):
             uh, _ = oracle.phase(uh, f, 15.0, oracle.MEAN, 1 << (j - 1), 4, k)
     np.testing.assert_array_equal(uv, uh)
+
+
+def test_paper_block_sides_schedule():
+    """Sec. 2.2: level j groups the pixels into patches of (2^j - 1) x (2^j - 1)
+    (1, 3, 7, 15, ... pixels a side), ceil(m / (2^j - 1)) x ceil(n / (2^j - 1))
+    of them.  One phase of level j on a 40 x 29 image returns a shift for
+    exactly the patches of its colour, each constant over its patch."""
+    assert [oracle.level_side(j, 1) for j in range(1, 6)] == [1, 3, 7, 15, 31]
+    assert [oracle.level_side(j, 0) for j in range(1, 6)] == [1, 2, 4, 8, 16]
+    # coarsest side <= half the shorter image side
+    assert oracle.auto_levels(64, 64, 1) == 5 and oracle.auto_levels(1024, 1024, 1) == 9
+    assert oracle.auto_levels(13, 100, 1) == 2 and oracle.auto_levels(5, 5, 1) == 1
+    img = synth.piecewise_image(40, 29, 8, 4, 0.08)
+    f = img.f.astype(np.float64)
+    u0 = oracle.cycle(f, f, 15.0, oracle.MEAN, levels=1, ncolors=4)
+    for j in (2, 3, 4):
+        b = oracle.level_side(j, 1)
+        mj, nj = -(-40 // b), -(-29 // b)
+        moved = 0
+        for k in range(4):
+            u1, c = oracle.phase(u0, f, 15.0, oracle.MEAN, b, 4, k)
+            assert c.shape == (mj * nj,)
+            for bi in range(mj):
+                for bj in range(nj):
+                    blk = (slice(bi * b, (bi + 1) * b), slice(bj * b, (bj + 1) * b))
+                    if (2 * (bi % 2) + bj % 2) != k:
+                        assert np.all(u1[blk] == u0[blk])   # other colours untouched
+                    else:   # one constant per patch
+                        assert np.all(u1[blk] == u0[blk] + c[bi * nj + bj])
+                        moved += c[bi * nj + bj] != 0.0
+        assert moved > 0
+
+
+def test_paper_block_sides_cycle_is_its_phase_sequence():
+    img = synth.piecewise_image(33, 40, 6, 5, 0.08)
+    f = img.f.astype(np.float64)
+    L = oracle.auto_levels(33, 40, 1)
+    assert L == 4   # sides 1, 3, 7, 15
+    uc = oracle.cycle(f, f, 15.0, oracle.GAUSS, ncolors=4, sides=1)
+    up = f.copy()
+    for b in (1, 3, 7, 15):
+        for k in range(4):
+            up, _ = oracle.phase(up, f, 15.0, oracle.GAUSS, b, 4, k)
+    np.testing.assert_array_equal(uc, up)
+
+
+@pytest.mark.parametrize("kind", [oracle.MEAN, oracle.GAUSS_EULER])
+def test_paper_block_sides_monotone_and_denoise(kind):
+    """Patches of odd sides keep the defining properties: the sequential
+    (Gauss-Seidel) sweep never raises F, the decoupled colouring never raises
+    F, and the colour-parallel solve lowers F and denoises."""
+    img = synth.piecewise_image(36, 31, 9, 5, 0.08)
+    f = img.f.astype(np.float64)
+    _, tr, n, _ = oracle.solve(f, 15.0, kind, cycles=4, sequential=True, sides=1)
+    assert np.all(np.diff(tr) <= 1e-10 * np.abs(tr[1:]))
+    _, tr, n, _ = oracle.solve(f, 15.0, kind, cycles=4, ncolors=0, sides=1)
+    assert np.all(np.diff(tr) <= 1e-10 * np.abs(tr[1:]))
+    u, tr, n, _ = oracle.solve(f, 15.0, kind, cycles=6, ncolors=4, sides=1)
+    assert tr[-1] < 0.7 * tr[0]
+    assert synth.psnr(u, img.clean) > synth.psnr(f, img.clean)
