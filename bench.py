@@ -474,6 +474,27 @@ def main():
                                         "final_energy": st_plain[-1].energy_final,
                                         "monotone_violations": st_plain[-1].monotone_violations}
 
+    # curvature kinds (plain solve from f to the same tolerance, the same
+    # schedule): H and K from the extreme direction curvatures (the paper's
+    # kinds) and from the least-squares Euler fit; Gaussian kinds at alpha 15
+    kinds_res = {}
+    for name, kd, al in (("mean", cm.MEAN, ALPHA), ("gauss", cm.GAUSS, 15.0),
+                         ("mean_euler", cm.MEAN_EULER, ALPHA),
+                         ("gauss_euler", cm.GAUSS_EULER, 15.0)):
+        def ksolve(fin, out, kd=kd, al=al):
+            _, st = cm.cm_solve(fin, al, kd, levels=0, cycles=MAX_CYCLES, tol=TOL, u_out=out,
+                                options=opts, ctx=ctx)
+            return st
+
+        ksolve(f, u)
+        torch.cuda.synchronize()
+        sec_k, st_k = timed_steps(ksolve)
+        kinds_res[name] = {"kind": kd, "alpha": al, "s": sec_k,
+                           "cycles_to_tol": st_k[-1].cycles_run,
+                           "psnr_db": synth.psnr(u.cpu().numpy(), img.clean),
+                           "final_energy": st_k[-1].energy_final,
+                           "monotone_violations": st_k[-1].monotone_violations}
+
     # dominant kernel: finest-level phase (b = 1), launched on the same stream
     state = u.clone()
     R = state.clone()
@@ -567,7 +588,7 @@ def main():
             "gpu_launches": int(sum(launches_per_solve)),
             "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks,
             "b1_phase_ms": b1_ms, "batched": batched_res, "one_step": one_step_res,
-            "cycle_variants": variants}
+            "cycle_variants": variants, "curvature_kinds": kinds_res}
     line["config"]["levels"] = L
     line["config"]["grid_points"] = opts.grid_points
     line["config"]["golden_evals"] = opts.golden_evals
