@@ -450,14 +450,19 @@ def main():
     # the colouring / cycle variants of the method (plain solve from f to the
     # same tolerance): the full V-cycle (Sec. 2.2, compared in Sec. 4.1) and
     # the decoupled colouring (blocks of one colour share no stencil)
+    # and the paper's block sides 2^j - 1 (Sec. 2.2), with the default level
+    # count (sides up to 511) and with the paper's J = 3 (sides 1, 3, 7)
     variants = {}
     for name, kw in (("vcycle", dict(vcycle=1)), ("decoupled", dict(ncolors=0)),
-                     ("decoupled_vcycle", dict(ncolors=0, vcycle=1))):
+                     ("decoupled_vcycle", dict(ncolors=0, vcycle=1)),
+                     ("paper_sides", dict(block_sides=1)),
+                     ("paper_sides_J3", dict(block_sides=1, levels=3))):
         ov = cm.default_options(grid_points=opts.grid_points, golden_evals=opts.golden_evals,
-                                ncolors=kw.get("ncolors", opts.ncolors), vcycle=kw.get("vcycle", 0))
+                                ncolors=kw.get("ncolors", opts.ncolors), vcycle=kw.get("vcycle", 0),
+                                block_sides=kw.get("block_sides", 0))
 
-        def vsolve(fin, out, ov=ov):
-            _, st = cm.cm_solve(fin, ALPHA, KIND, levels=0, cycles=MAX_CYCLES, tol=TOL,
+        def vsolve(fin, out, ov=ov, lv=kw.get("levels", 0)):
+            _, st = cm.cm_solve(fin, ALPHA, KIND, levels=lv, cycles=MAX_CYCLES, tol=TOL,
                                 u_out=out, options=ov, ctx=ctx)
             return st
 
@@ -465,6 +470,7 @@ def main():
         torch.cuda.synchronize()
         sec_v, st_v = timed_steps(vsolve)
         variants[name] = {"s": sec_v, "cycles_to_tol": st_v[-1].cycles_run,
+                          "levels": st_v[-1].levels,
                           "psnr_db": synth.psnr(u.cpu().numpy(), img.clean),
                           "final_energy": st_v[-1].energy_final,
                           "monotone_violations": st_v[-1].monotone_violations,

@@ -59,6 +59,8 @@ extern "C" {
 
 #define CM_KIND_MEAN 0
 #define CM_KIND_GAUSS 1
+#define CM_KIND_MEAN_EULER 2    /* extension: H from the Euler fit */
+#define CM_KIND_GAUSS_EULER 3   /* extension: K from the Euler fit */
 
 typedef struct cm_ctx cm_ctx;
 
@@ -90,6 +92,10 @@ typedef struct {
     int coarse_dmax;     /* coarse levels: 0 the level's default, 1 .. 4 golden steps per
                             reduction (2^d - 1 points of every outcome path); both change only
                             how many candidates share a reduction, never which are taken */
+    int block_sides;     /* 0: block side 2^(j-1) on level j (default); 1: the paper's patches
+                            of (2^j - 1) x (2^j - 1) pixels (Sec. 2.2: 1, 3, 7, 15, ...), with
+                            levels = 0 meaning the largest side <= min(H, W) / 2.  Levels of
+                            odd side run the per-phase kernels (direct block sums and apply) */
 } cm_options;
 
 /* Solve statistics (host struct, filled by cm_solve). */

@@ -40,7 +40,8 @@ class Options(ctypes.Structure):
                 ("golden_evals", ctypes.c_int), ("paper_candidate", ctypes.c_int),
                 ("use_graph", ctypes.c_int), ("max_trace", ctypes.c_int),
                 ("one_step", ctypes.c_int), ("vcycle", ctypes.c_int),
-                ("coarse_spec", ctypes.c_int), ("coarse_dmax", ctypes.c_int)]
+                ("coarse_spec", ctypes.c_int), ("coarse_dmax", ctypes.c_int),
+                ("block_sides", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):

@@ -26,7 +26,8 @@ struct GraphKey {
     const float* S;
     const float* R;
     const float* f;
-    int H, W, kind, levels, ncolors, G, K, use_paper, one_step, vcycle, coarse_spec, coarse_dmax;
+    int H, W, kind, levels, ncolors, G, K, use_paper, one_step, vcycle, coarse_spec, coarse_dmax,
+        block_sides;
     float alpha;
     double tol;
     int cycles, trace_cap;
@@ -162,11 +163,39 @@ int check_opts(cm_ctx* ctx, const cm_options& o) {
         return fail(ctx, CM_ERR_INVALID, "coarse_spec must be -1, 0 or 1");
     if (o.coarse_dmax < 0 || o.coarse_dmax > 4)
         return fail(ctx, CM_ERR_INVALID, "coarse_dmax must be 0 .. 4");
+    if (o.block_sides != 0 && o.block_sides != 1)
+        return fail(ctx, CM_ERR_INVALID, "block_sides must be 0 or 1");
     return CM_OK;
 }
 
+// Shape class of the block side b of one phase or level: b a power of two or
+// one of the paper's sides 2^j - 1, at most 2048; -1 otherwise.
+int side_lb(int b) {
+    if (b < 1) return -1;
+    const int lb = cm::side_class(b);
+    if (lb > cm::max_level_log2()) return -1;
+    return (b == (1 << lb) || b == (1 << lb) - 1) ? lb : -1;
+}
+
+// Levels of the solve: `levels`, or the default for the block-side rule.
+int solve_levels(int levels, int H, int W, const cm_options& o) {
+    return levels > 0 ? levels : cm::auto_levels(H, W, o.block_sides);
+}
+
+// The coarsest level's side is within the kernels' shapes.
+bool levels_ok(int L, const cm_options& o) {
+    return cm::side_class(cm::level_side(L - 1, o.block_sides)) <= cm::max_level_log2();
+}
+
+// Levels of power-of-two side from the coarse threshold on run the coarse
+// path (tile sums, search, deferred apply).
+bool coarse_side(int b) {
+    const int lb = cm::side_class(b);
+    return b == (1 << lb) && lb >= cm::coarse_level_log2();
+}
+
 cm::PhaseArgs phase_args(const float* S, float* R, const float* f, int H, int W, float alpha,
-                         int kind, int lb, int colour, const cm_options& o) {
+                         int kind, int b, int colour, const cm_options& o) {
     cm::PhaseArgs a;
     a.S = S;
     a.R = R;
@@ -175,8 +204,9 @@ cm::PhaseArgs phase_args(const float* S, float* R, const float* f, int H, int W,
     a.W = W;
     a.alpha = alpha;
     a.kind = kind;
-    a.lb = lb;
-    a.ncolors = cm::level_colours(o.ncolors, lb);
+    a.lb = cm::side_class(b);
+    a.bs = b;
+    a.ncolors = cm::level_colours(o.ncolors, b);
     a.colour = colour;
     a.G = o.grid_points;
     a.K = o.golden_evals;
@@ -188,23 +218,23 @@ cm::PhaseArgs phase_args(const float* S, float* R, const float* f, int H, int W,
     return a;
 }
 
-// Enqueue one level (all colours) from state S into R.  Levels below the
-// coarse threshold run one phase kernel per colour; coarse levels run the
-// tile-sum / search / apply sequence.  c_out (nullable) receives every
-// block's shift.
+// Enqueue one level of block side b (all colours) from state S into R.
+// Levels below the coarse threshold, and levels of odd side, run one phase
+// kernel per colour; coarse levels run the tile-sum / search / apply
+// sequence.  c_out (nullable) receives every block's shift.
 cudaError_t enqueue_level(float* tsums, float* cj, const float* S, float* R, const float* f,
-                          int H, int W, float alpha, int kind, int lb, const cm_options& o,
+                          int H, int W, float alpha, int kind, int b, const cm_options& o,
                           float* c_out, const int* active, cudaStream_t st,
                           bool sums_ready = false) {
-    if (lb >= cm::coarse_level_log2()) {
-        cm::PhaseArgs a = phase_args(S, R, f, H, W, alpha, kind, lb, 0, o);
+    if (coarse_side(b)) {
+        cm::PhaseArgs a = phase_args(S, R, f, H, W, alpha, kind, b, 0, o);
         a.c_out = c_out;
         a.active = active;
         return cm::launch_level_coarse(a, tsums, cj, st, sums_ready);
     }
-    const int nc = cm::level_colours(o.ncolors, lb);
+    const int nc = cm::level_colours(o.ncolors, b);
     for (int k = 0; k < nc; ++k) {
-        cm::PhaseArgs a = phase_args(S, R, f, H, W, alpha, kind, lb, k, o);
+        cm::PhaseArgs a = phase_args(S, R, f, H, W, alpha, kind, b, k, o);
         a.c_out = c_out;
         a.active = active;
         cudaError_t e = cm::launch_phase(a, st);
@@ -231,11 +261,11 @@ cudaError_t enqueue_cycle(cm_ctx* ctx, float* X, float* Y, const float* f, int H
     const int nsteps = level_steps(levels, o);
     bool sums = false;   // tile sums of the current state already in ctx->tsums
     for (int step = 0; step < nsteps; ++step) {
-        const int j = level_at(step, levels);
-        const bool coarse = j >= cm::coarse_level_log2();
+        const int b = cm::level_side(level_at(step, levels), o.block_sides);
+        const bool coarse = coarse_side(b);
         const bool in_place = end_in_x && step == nsteps - 1 && S == X && coarse;
         float* out = in_place ? S : R;
-        cudaError_t e = enqueue_level(ctx->tsums, ctx->cj, S, out, f, H, W, alpha, kind, j, o,
+        cudaError_t e = enqueue_level(ctx->tsums, ctx->cj, S, out, f, H, W, alpha, kind, b, o,
                                       nullptr, nullptr, st, sums);
         sums = coarse;
         if (e != cudaSuccess) return e;
@@ -331,6 +361,7 @@ int cm_options_default(cm_options* o) {
     o->vcycle = 0;
     o->coarse_spec = -1;
     o->coarse_dmax = 0;
+    o->block_sides = 0;
     return CM_OK;
 }
 
@@ -430,14 +461,12 @@ int cm_phase(cm_ctx* ctx, const float* S, float* R, const float* f, int H, int W
     if (!S || !R || !f || R == S || R == f || H < 1 || W < 1 || !finite_positive(alpha) ||
         !valid_kind(kind))
         return fail(ctx, CM_ERR_INVALID, "cm_phase: invalid argument");
-    int lb = 0;
-    while ((1 << lb) < b) ++lb;
-    if (b < 1 || (1 << lb) != b || lb > cm::max_level_log2())
-        return fail(ctx, CM_ERR_INVALID, "cm_phase: b must be a power of two <= 2048");
-    if (colour < 0 || colour >= cm::level_colours(o.ncolors, lb))
+    if (side_lb(b) < 0)
+        return fail(ctx, CM_ERR_INVALID, "cm_phase: b must be 2^j or 2^j - 1, at most 2048");
+    if (colour < 0 || colour >= cm::level_colours(o.ncolors, b))
         return fail(ctx, CM_ERR_INVALID, "cm_phase: bad colour");
     CM_CUDA(cudaSetDevice(ctx->device));
-    cm::PhaseArgs a = phase_args(S, R, f, H, W, alpha, kind, lb, colour, o);
+    cm::PhaseArgs a = phase_args(S, R, f, H, W, alpha, kind, b, colour, o);
     a.c_out = c_out;
     CM_CUDA(cm::launch_phase(a, (cudaStream_t)stream));
     return CM_OK;
@@ -454,14 +483,12 @@ int cm_level(cm_ctx* ctx, const float* S, float* R, const float* f, int H, int W
     if (!S || !R || !f || R == S || R == f || H < 1 || W < 1 || !finite_positive(alpha) ||
         !valid_kind(kind))
         return fail(ctx, CM_ERR_INVALID, "cm_level: invalid argument");
-    int lb = 0;
-    while ((1 << lb) < b) ++lb;
-    if (b < 1 || (1 << lb) != b || lb > cm::max_level_log2())
-        return fail(ctx, CM_ERR_INVALID, "cm_level: b must be a power of two <= 2048");
+    if (side_lb(b) < 0)
+        return fail(ctx, CM_ERR_INVALID, "cm_level: b must be 2^j or 2^j - 1, at most 2048");
     CM_CUDA(cudaSetDevice(ctx->device));
     rc = ensure_coarse(ctx, H, W);
     if (rc) return rc;
-    CM_CUDA(enqueue_level(ctx->tsums, ctx->cj, S, R, f, H, W, alpha, kind, lb, o, c_out, nullptr,
+    CM_CUDA(enqueue_level(ctx->tsums, ctx->cj, S, R, f, H, W, alpha, kind, b, o, c_out, nullptr,
                           (cudaStream_t)stream));
     return CM_OK;
 }
@@ -478,8 +505,8 @@ int cm_solve(cm_ctx* ctx, const float* f, int H, int W, float alpha, int kind, i
     if (!f || !u_out || u_out == f || H < 1 || W < 1 || !finite_positive(alpha) ||
         !valid_kind(kind) || levels < 0 || cycles < 0 || !(tol >= 0.0) || !isfinite(tol))
         return fail(ctx, CM_ERR_INVALID, "cm_solve: invalid argument");
-    const int L = levels > 0 ? levels : cm_auto_levels(H, W);
-    if (L - 1 > cm::max_level_log2()) return fail(ctx, CM_ERR_INVALID, "cm_solve: too many levels");
+    const int L = solve_levels(levels, H, W, o);
+    if (!levels_ok(L, o)) return fail(ctx, CM_ERR_INVALID, "cm_solve: too many levels");
     CM_CUDA(cudaSetDevice(ctx->device));
     cudaStream_t st = (cudaStream_t)stream;
     const size_t N = (size_t)H * W;
@@ -516,6 +543,7 @@ int cm_solve(cm_ctx* ctx, const float* f, int H, int W, float alpha, int kind, i
         key.vcycle = o.vcycle;
         key.coarse_spec = o.coarse_spec;
         key.coarse_dmax = o.coarse_dmax;
+        key.block_sides = o.block_sides;
         key.alpha = alpha;
         key.tol = tol;
         key.cycles = cycles;
@@ -682,8 +710,8 @@ int cm_solve_batched(cm_ctx* ctx, int n, const float* const* f, const int* H, co
         if (!f[i] || !u_out[i] || u_out[i] == f[i] || H[i] < 1 || W[i] < 1 ||
             !finite_positive(alpha[i]) || !valid_kind(kind[i]))
             return fail(ctx, CM_ERR_INVALID, "cm_solve_batched: invalid image " + std::to_string(i));
-        const int L = levels > 0 ? levels : cm_auto_levels(H[i], W[i]);
-        if (L - 1 > cm::max_level_log2())
+        const int L = solve_levels(levels, H[i], W[i], o);
+        if (!levels_ok(L, o))
             return fail(ctx, CM_ERR_INVALID, "cm_solve_batched: too many levels");
     }
     CM_CUDA(cudaSetDevice(ctx->device));
@@ -695,7 +723,7 @@ int cm_solve_batched(cm_ctx* ctx, int n, const float* const* f, const int* H, co
     for (int i = 0; i < n; ++i) {
         const size_t N = (size_t)H[i] * W[i];
         ImgLayout& L = lay[i];
-        L.L = levels > 0 ? levels : cm_auto_levels(H[i], W[i]);
+        L.L = solve_levels(levels, H[i], W[i], o);
         L.ubuf = off; off = align256(off + N * sizeof(float));
         L.partials = off; off = align256(off + cm::energy_partials_needed(H[i], W[i]) * sizeof(double));
         L.ticket = off; off = align256(off + sizeof(unsigned int));
@@ -814,11 +842,11 @@ int cm_solve_batched(cm_ctx* ctx, int n, const float* const* f, const int* H, co
             const int nsteps = level_steps(L.L, o);
             bool sums = false;
             for (int step = 0; step < nsteps && ce == cudaSuccess; ++step) {
-                const int j = level_at(step, L.L);
+                const int b = cm::level_side(level_at(step, L.L), o.block_sides);
                 ce = enqueue_level((float*)(A + L.tsums), (float*)(A + L.cj), Sb, Rb, f[i], H[i],
-                                   W[i], alpha[i], kind[i], j, o, nullptr, active_ptr(i), si,
+                                   W[i], alpha[i], kind[i], b, o, nullptr, active_ptr(i), si,
                                    sums);
-                sums = j >= cm::coarse_level_log2();
+                sums = coarse_side(b);
                 float* t = Sb;
                 Sb = Rb;
                 Rb = t;

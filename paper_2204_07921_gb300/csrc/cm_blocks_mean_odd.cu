@@ -1,0 +1,5 @@
+// cm_blocks_mean_odd.cu -- block-level kernels for the paper's block sides 2^j - 1
+// (Sec. 2.2), curvature kind KIND_MEAN.
+#include "cm_phase_blocks.cuh"
+
+CM_BLOCKS_ODD_INSTANTIATE(cm::KIND_MEAN)

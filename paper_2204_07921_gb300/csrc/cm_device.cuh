@@ -214,6 +214,23 @@ __device__ __forceinline__ float phase_read(const float* __restrict__ S,
     return S[i];
 }
 
+// Block index of pixel row (or column) r on a level whose block side is
+// 1 << lb (POW2) or any side b (the paper's sides 2^j - 1).
+template <bool POW2>
+__device__ __forceinline__ int block_of(int r, int lb, int b) {
+    return POW2 ? r >> lb : r / b;
+}
+
+template <bool POW2>
+__device__ __forceinline__ float phase_read_b(const float* __restrict__ S,
+                                              const float* __restrict__ R, int r, int c, int W,
+                                              int lb, int b, int ncolors, int k) {
+    if (POW2) return phase_read(S, R, r, c, W, lb, ncolors, k);
+    size_t i = (size_t)r * W + c;
+    if (k > 0 && block_colour(r / b, c / b, ncolors) < k) return R[i];
+    return S[i];
+}
+
 // ---------------------------------------------------------------------------
 // Candidate bookkeeping of the block search: lowest energy wins; exactly
 // equal energies keep the smaller |c|, then the smaller c.

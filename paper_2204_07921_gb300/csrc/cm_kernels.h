@@ -33,15 +33,34 @@ inline int active_slots(int nbi, int nbj, int ncol) {
     return ((nbi + p - 1) / p) * ((nbj + p - 1) / p);
 }
 
-// Colours of the level with block side 1 << lb: ncolors, or for ncolors = 0
-// the decoupled colouring (the smallest p >= 2 with (p - 1) b >= 3, p^2
+// Colours of the level with block side b: ncolors, or for ncolors = 0 the
+// decoupled colouring (the smallest p >= 2 with (p - 1) b >= 3, p^2
 // colours), under which a colour's blocks share no stencil.
-inline int level_colours(int ncolors, int lb) {
+inline int level_colours(int ncolors, int b) {
     if (ncolors != 0) return ncolors;
-    const int b = 1 << lb;
     int p = 2;
     while ((p - 1) * b < 3) ++p;
     return p * p;
+}
+
+// Block side of level j = 0, 1, ...: 1 << j, or with the paper's sides
+// (sides = 1, Sec. 2.2) 2^(j+1) - 1.
+inline int level_side(int j, int sides) { return sides ? (2 << j) - 1 : 1 << j; }
+
+// Kernel shape class of block side b: the smallest lb with b <= 1 << lb.
+inline int side_class(int b) {
+    int lb = 0;
+    while ((1 << lb) < b) ++lb;
+    return lb;
+}
+
+// Default level count: the coarsest block side is the largest one <= half
+// the shorter image side.
+inline int auto_levels(int H, int W, int sides) {
+    const int m = H < W ? H : W;
+    int L = 1;
+    while (level_side(L, sides) <= m / 2) ++L;
+    return L;
 }
 
 struct PhaseArgs {
@@ -51,7 +70,8 @@ struct PhaseArgs {
     int H, W;
     float alpha;
     int kind;
-    int lb;           // block side = 1 << lb
+    int lb;           // kernel shape class: block side bs <= 1 << lb
+    int bs;           // block side: 1 << lb, or the paper's 2^lb - 1
     int ncolors;      // 2 or 4
     int colour;
     int G, K;         // block-search budget

@@ -137,7 +137,18 @@ cudaError_t launch_level_coarse(const PhaseArgs& A0, float* partials, float* cj,
                     (const float*)cj, A0.H, A0.W, A0.lb, nbj, partials, A0.active);
 }
 
+static cudaError_t launch_phase_odd(const PhaseArgs& A, cudaStream_t st) {
+    switch (A.kind) {
+        case KIND_MEAN: return blocks_phase_odd_kind<KIND_MEAN>(A, st);
+        case KIND_GAUSS: return blocks_phase_odd_kind<KIND_GAUSS>(A, st);
+        case KIND_MEAN_EULER: return blocks_phase_odd_kind<KIND_MEAN_EULER>(A, st);
+        case KIND_GAUSS_EULER: return blocks_phase_odd_kind<KIND_GAUSS_EULER>(A, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
 cudaError_t launch_phase_blocks(const PhaseArgs& A, cudaStream_t st) {
+    if (A.bs != (1 << A.lb)) return launch_phase_odd(A, st);
     switch (A.kind) {
         case KIND_MEAN: return blocks_phase_kind<KIND_MEAN>(A, st);
         case KIND_GAUSS: return blocks_phase_kind<KIND_GAUSS>(A, st);
@@ -148,7 +159,7 @@ cudaError_t launch_phase_blocks(const PhaseArgs& A, cudaStream_t st) {
 }
 
 cudaError_t launch_phase(const PhaseArgs& A, cudaStream_t st) {
-    if (A.lb == 0) return launch_phase_b1(A, st);
+    if (A.bs == 1) return launch_phase_b1(A, st);
     return launch_phase_blocks(A, st);
 }
 

@@ -66,25 +66,26 @@ __device__ __forceinline__ void for_block_pixels(int first, int stride, int r0, 
 // this with its group's active-block number a, valid or not).  LIGHT keeps
 // the ring windows and rebuilds the affine coefficients per candidate (fewer
 // registers, more arithmetic).
-template <int KIND, int GT, int RPT, bool LIGHT = false>
+template <int KIND, int GT, int RPT, bool LIGHT = false, bool POW2 = true>
 __device__ __forceinline__ void warp_group_block(const float* __restrict__ S,
                                                  float* __restrict__ R,
                                                  const float* __restrict__ f, int H, int W,
                                                  const SearchParams& sp, int lb, int ncol, int k,
-                                                 float* __restrict__ c_out, int a) {
+                                                 float* __restrict__ c_out, int a, int bs = 0) {
     static_assert(GT == 4 || GT == 8 || GT == 16 || GT == 32, "warp groups only");
     const int lane = threadIdx.x % GT;
-    const int b = 1 << lb;
-    const int nbi = (H + b - 1) >> lb, nbj = (W + b - 1) >> lb;
+    // block side 1 << lb, or (POW2 false) bs < 1 << lb
+    const int b = POW2 ? 1 << lb : bs;
+    const int nbi = block_of<POW2>(H + b - 1, lb, b), nbj = block_of<POW2>(W + b - 1, lb, b);
     int bi, bj;
     const bool blk_on = active_block(a, nbi, nbj, ncol, k, bi, bj);
     // Groups without a block still take part in the shuffles of their warp.
-    const int r0 = blk_on ? bi << lb : 0, c0 = blk_on ? bj << lb : 0;
+    const int r0 = blk_on ? bi * b : 0, c0 = blk_on ? bj * b : 0;
     const int r1 = blk_on ? min(r0 + b, H) : 0, c1 = blk_on ? min(c0 + b, W) : 0;
     const int bh = r1 - r0, bw = c1 - c0;
     float s1 = 0.0f;
     if (blk_on)
-        for_block_pixels(lane, GT, r0, c0, bh, bw, lb, bw == b, W,
+        for_block_pixels(lane, GT, r0, c0, bh, bw, lb, POW2 && bw == b, W,
                          [&](size_t p) { s1 += S[p] - f[p]; });
 #pragma unroll
     for (int off = GT / 2; off > 0; off >>= 1) s1 += __shfl_xor_sync(0xffffffffu, s1, off, GT);
@@ -98,7 +99,8 @@ __device__ __forceinline__ void warp_group_block(const float* __restrict__ S,
     for (int t = 0; t < RPT; ++t) {
         float w[9];
         msk[t] = 0;
-        has[t] = blk_on && ring_slot(lane + t * GT, r0, r1, c0, c1, H, W, S, R, lb, ncol, k, w, msk[t]);
+        has[t] = blk_on && ring_slot<POW2>(lane + t * GT, r0, r1, c0, c1, H, W, S, R, lb, ncol,
+                                           k, w, msk[t], b);
         if constexpr (LIGHT) {
 #pragma unroll
             for (int i = 0; i < 9; ++i) win[t][i] = has[t] ? w[i] : 0.0f;
@@ -133,20 +135,20 @@ __device__ __forceinline__ void warp_group_block(const float* __restrict__ S,
     else
         cbest = block_search(ring, sp, s, S1b, false, 0.0f);
     if (!blk_on) return;
-    for_block_pixels(lane, GT, r0, c0, bh, bw, lb, bw == b, W,
+    for_block_pixels(lane, GT, r0, c0, bh, bw, lb, POW2 && bw == b, W,
                      [&](size_t p) { R[p] = S[p] + cbest; });
     if (c_out && lane == 0) c_out[(size_t)bi * nbj + bj] = cbest;
 }
 
-template <int KIND, int GT, int RPT>
+template <int KIND, int GT, int RPT, bool POW2 = true>
 __global__ void __launch_bounds__(128) phase_warp_kernel(
     const float* __restrict__ S, float* __restrict__ R, const float* __restrict__ f, int H, int W,
-    SearchParams sp, int lb, int ncol, int k, float* __restrict__ c_out,
+    SearchParams sp, int lb, int bs, int ncol, int k, float* __restrict__ c_out,
     const int* __restrict__ active) {
     if (active && *active == 0) return;
     constexpr int GPC = 128 / GT;
-    warp_group_block<KIND, GT, RPT>(S, R, f, H, W, sp, lb, ncol, k, c_out,
-                                    blockIdx.x * GPC + threadIdx.x / GT);
+    warp_group_block<KIND, GT, RPT, false, POW2>(S, R, f, H, W, sp, lb, ncol, k, c_out,
+                                                 blockIdx.x * GPC + threadIdx.x / GT, bs);
 }
 
 // ---------------------------------------------------------------------------
@@ -351,10 +353,10 @@ __global__ void __launch_bounds__(128, CM_B2_MINB) phase_b2_kernel(
     if (c_out && q == 0) c_out[(size_t)bi * nbj + bj] = cbest;
 }
 
-template <int KIND, int CT, int Q, int RPT>
+template <int KIND, int CT, int Q, int RPT, bool POW2 = true>
 __global__ void __cluster_dims__(Q, 1, 1) __launch_bounds__(CT) phase_cluster_kernel(
     const float* __restrict__ S, float* __restrict__ R, const float* __restrict__ f, int H, int W,
-    SearchParams sp, int lb, int ncol, int k, float* __restrict__ c_out,
+    SearchParams sp, int lb, int bs, int ncol, int k, float* __restrict__ c_out,
     const int* __restrict__ active) {
     namespace cg = cooperative_groups;
     if (active && *active == 0) return;   // uniform over the grid
@@ -366,11 +368,12 @@ __global__ void __cluster_dims__(Q, 1, 1) __launch_bounds__(CT) phase_cluster_ke
     const int rank = Q > 1 ? (int)cg::this_cluster().block_rank() : 0;
     const int a = blockIdx.x / Q;
     const int g = rank * CT + threadIdx.x;
-    const int b = 1 << lb;
-    const int nbi = (H + b - 1) >> lb, nbj = (W + b - 1) >> lb;
+    // block side 1 << lb, or (POW2 false) bs < 1 << lb
+    const int b = POW2 ? 1 << lb : bs;
+    const int nbi = block_of<POW2>(H + b - 1, lb, b), nbj = block_of<POW2>(W + b - 1, lb, b);
     int bi, bj;
     if (!active_block(a, nbi, nbj, ncol, k, bi, bj)) return;   // uniform over the cluster
-    const int r0 = bi << lb, c0 = bj << lb;
+    const int r0 = bi * b, c0 = bj * b;
     const int r1 = min(r0 + b, H), c1 = min(c0 + b, W);
     const int bh = r1 - r0, bw = c1 - c0;
     int flip = 0;
@@ -421,7 +424,8 @@ __global__ void __cluster_dims__(Q, 1, 1) __launch_bounds__(CT) phase_cluster_ke
     };
 
     float s1 = 0.0f;
-    for_block_pixels(g, GT, r0, c0, bh, bw, lb, bw == b, W, [&](size_t p) { s1 += S[p] - f[p]; });
+    for_block_pixels(g, GT, r0, c0, bh, bw, lb, POW2 && bw == b, W,
+                     [&](size_t p) { s1 += S[p] - f[p]; });
     reduce_vec(&s1, 1);
     const float S1 = s1;
 
@@ -431,7 +435,7 @@ __global__ void __cluster_dims__(Q, 1, 1) __launch_bounds__(CT) phase_cluster_ke
     for (int t = 0; t < RPT; ++t) {
         float w[9];
         unsigned mask = 0;
-        has[t] = ring_slot(g + t * GT, r0, r1, c0, c1, H, W, S, R, lb, ncol, k, w, mask);
+        has[t] = ring_slot<POW2>(g + t * GT, r0, r1, c0, c1, H, W, S, R, lb, ncol, k, w, mask, b);
         if (has[t]) {
             px[t] = aff_pix(w, mask);
         } else {
@@ -453,7 +457,8 @@ __global__ void __cluster_dims__(Q, 1, 1) __launch_bounds__(CT) phase_cluster_ke
         reduce_vec(out, m);
     };
     const float cbest = block_search_batched<MB>(ringv, sp, (float)(bh * bw), S1);
-    for_block_pixels(g, GT, r0, c0, bh, bw, lb, bw == b, W, [&](size_t p) { R[p] = S[p] + cbest; });
+    for_block_pixels(g, GT, r0, c0, bh, bw, lb, POW2 && bw == b, W,
+                     [&](size_t p) { R[p] = S[p] + cbest; });
     if (c_out && g == 0) c_out[(size_t)bi * nbj + bj] = cbest;
     // No CTA may exit while another still reads its shared memory.
     if (Q > 1) cg::this_cluster().sync();
@@ -681,21 +686,23 @@ static cudaError_t launch_coarse_kind(const PhaseArgs& A, const float* partials,
     }
 }
 
-template <int KIND, int GT, int RPT>
+template <int KIND, int GT, int RPT, bool POW2 = true>
 static cudaError_t launch_warp(const PhaseArgs& A, int nact, cudaStream_t st) {
     constexpr int GPC = 128 / GT;
     SearchParams sp{A.alpha, A.G, A.K};
     sp.one_step = A.one_step;
-    return launch_k(phase_warp_kernel<KIND, GT, RPT>, dim3((nact + GPC - 1) / GPC), dim3(128), st,
-                    1, A.S, A.R, A.f, A.H, A.W, sp, A.lb, A.ncolors, A.colour, A.c_out, A.active);
+    return launch_k(phase_warp_kernel<KIND, GT, RPT, POW2>, dim3((nact + GPC - 1) / GPC),
+                    dim3(128), st, 1, A.S, A.R, A.f, A.H, A.W, sp, A.lb, A.bs, A.ncolors,
+                    A.colour, A.c_out, A.active);
 }
 
-template <int KIND, int CT, int Q, int RPT>
+template <int KIND, int CT, int Q, int RPT, bool POW2 = true>
 static cudaError_t launch_cluster(const PhaseArgs& A, int nact, cudaStream_t st) {
     SearchParams sp{A.alpha, A.G, A.K};
     sp.one_step = A.one_step;
-    return launch_k(phase_cluster_kernel<KIND, CT, Q, RPT>, dim3(nact * Q), dim3(CT), st, 1, A.S,
-                    A.R, A.f, A.H, A.W, sp, A.lb, A.ncolors, A.colour, A.c_out, A.active);
+    return launch_k(phase_cluster_kernel<KIND, CT, Q, RPT, POW2>, dim3(nact * Q), dim3(CT), st, 1,
+                    A.S, A.R, A.f, A.H, A.W, sp, A.lb, A.bs, A.ncolors, A.colour, A.c_out,
+                    A.active);
 }
 
 template <int KIND>
@@ -726,9 +733,37 @@ static cudaError_t launch_blocks_kind(const PhaseArgs& A, cudaStream_t st) {
     }
 }
 
+// The paper's block sides b = 2^lb - 1 (Sec. 2.2) on the kernel shapes of
+// side 1 << lb, whose 8 << lb ring slots cover the 8b ring pixels.
+template <int KIND>
+static cudaError_t launch_blocks_odd_kind(const PhaseArgs& A, cudaStream_t st) {
+    const int b = A.bs;
+    if (b < 2 || b > (1 << A.lb) || b <= (1 << (A.lb - 1))) return cudaErrorInvalidValue;
+    const int nbi = (A.H + b - 1) / b, nbj = (A.W + b - 1) / b;
+    const int nact = active_slots(nbi, nbj, A.ncolors);
+    switch (A.lb) {
+        case 2: return launch_warp<KIND, CM_B4_GT, 32 / CM_B4_GT, false>(A, nact, st);
+        case 3: return launch_warp<KIND, 32, 2, false>(A, nact, st);
+        case 4: return launch_cluster<KIND, 128, 1, 1, false>(A, nact, st);
+        case 5: return launch_cluster<KIND, 256, 1, 1, false>(A, nact, st);
+        case 6: return launch_cluster<KIND, 256, 2, 1, false>(A, nact, st);
+        case 7: return launch_cluster<KIND, 256, 4, 1, false>(A, nact, st);
+        case 8: return launch_cluster<KIND, 256, 8, 1, false>(A, nact, st);
+        case 9: return launch_cluster<KIND, 512, 8, 1, false>(A, nact, st);
+        case 10: return launch_cluster<KIND, 1024, 8, 1, false>(A, nact, st);
+        case 11: return launch_cluster<KIND, 1024, 8, 2, false>(A, nact, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
 template <int KIND>
 cudaError_t blocks_phase_kind(const PhaseArgs& A, cudaStream_t st) {
     return launch_blocks_kind<KIND>(A, st);
+}
+
+template <int KIND>
+cudaError_t blocks_phase_odd_kind(const PhaseArgs& A, cudaStream_t st) {
+    return launch_blocks_odd_kind<KIND>(A, st);
 }
 
 template <int KIND>
@@ -753,11 +788,17 @@ cudaError_t coarse_setup_kind() {
 
 }  // namespace cm
 
-// Explicit instantiation of one kind's entry points (in its own unit).
+// Explicit instantiation of one kind's entry points (in its own unit), and of
+// its odd-side entry point (in another).
 #define CM_BLOCKS_INSTANTIATE(KIND)                                                           \
     namespace cm {                                                                            \
     template cudaError_t blocks_phase_kind<KIND>(const PhaseArgs&, cudaStream_t);             \
     template cudaError_t coarse_phase_kind<KIND>(const PhaseArgs&, const float*, float*,      \
                                                  cudaStream_t);                               \
     template cudaError_t coarse_setup_kind<KIND>();                                           \
+    }
+
+#define CM_BLOCKS_ODD_INSTANTIATE(KIND)                                                       \
+    namespace cm {                                                                            \
+    template cudaError_t blocks_phase_odd_kind<KIND>(const PhaseArgs&, cudaStream_t);         \
     }

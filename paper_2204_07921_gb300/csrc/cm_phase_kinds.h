@@ -16,6 +16,10 @@ constexpr int COARSE_LB = 6;   // first level on the coarse path (b = 1 << COARS
 // One colour phase of a level with b in 2 .. 2048 (the per-phase kernels).
 template <int KIND>
 cudaError_t blocks_phase_kind(const PhaseArgs& A, cudaStream_t st);
+// One colour phase of a level with the paper's block side A.bs = 2^j - 1 >= 3
+// (A.lb = j: the shapes of side 1 << j).
+template <int KIND>
+cudaError_t blocks_phase_odd_kind(const PhaseArgs& A, cudaStream_t st);
 // One colour's search on the coarse path (b >= 1 << COARSE_LB).
 template <int KIND>
 cudaError_t coarse_phase_kind(const PhaseArgs& A, const float* partials, float* cj,

@@ -593,13 +593,18 @@ __device__ __forceinline__ bool ring_slot_v(int j, int r0, int r1, int c0, int c
     return true;
 }
 
+// Ring slot j read from the phase state; the level's block side is 1 << lb
+// (POW2) or b.
+template <bool POW2 = true>
 __device__ __forceinline__ bool ring_slot(int j, int r0, int r1, int c0, int c1, int H, int W,
                                           const float* __restrict__ S,
                                           const float* __restrict__ R, int lb, int ncol, int k,
-                                          float w[9], unsigned& mask) {
+                                          float w[9], unsigned& mask, int b = 0) {
     return ring_slot_v(j, r0, r1, c0, c1, H, W,
-                       [&](int r, int c) { return phase_read(S, R, r, c, W, lb, ncol, k); }, w,
-                       mask);
+                       [&](int r, int c) {
+                           return phase_read_b<POW2>(S, R, r, c, W, lb, b, ncol, k);
+                       },
+                       w, mask);
 }
 
 }  // namespace cm

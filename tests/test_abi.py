@@ -46,7 +46,7 @@ def test_host_only_entry_points():
     assert lib.cm_options_default(ctypes.byref(o)) == 0
     assert (o.ncolors, o.grid_points, o.golden_evals, o.paper_candidate) == (4, 5, 6, 1)
     assert (o.use_graph, o.max_trace, o.one_step, o.vcycle) == (1, 4096, 0, 0)
-    assert (o.coarse_spec, o.coarse_dmax) == (-1, 0)
+    assert (o.coarse_spec, o.coarse_dmax, o.block_sides) == (-1, 0, 0)
     assert lib.cm_options_default(None) == cm.CM_ERR_INVALID
     assert lib.cm_auto_levels(64, 64) == 6
     assert lib.cm_auto_levels(1024, 1024) == 10

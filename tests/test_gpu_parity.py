@@ -383,7 +383,7 @@ def test_invalid_arguments_rejected():
     with pytest.raises(cm.CMError):
         cm.cm_solve(f, float("nan"), 0)
     with pytest.raises(cm.CMError):
-        cm.cm_phase(f, f.clone(), f, 1.0, 0, 3, 0)      # b not a power of two
+        cm.cm_phase(f, f.clone(), f, 1.0, 0, 5, 0)      # b neither 2^j nor 2^j - 1
     with pytest.raises(cm.CMError):
         cm.cm_solve(f, 1.0, 0, options=cm.default_options(grid_points=8))
     bad = f.clone()
@@ -626,3 +626,100 @@ def test_coarse_round_shapes_take_the_same_decisions(spec, dmax):
         # another slot of the reduction, so a near-tie may rarely flip
         off = int(np.sum(np.abs(res[1] - res[0]) > 1e-4))
         assert off <= max(1, 0.02 * res[0].size), (b, off)
+
+
+# ---------------------------------------------------------------------------
+# The paper's block sides 2^j - 1 (Sec. 2.2): 1, 3, 7, 15, ... pixels a side.
+
+@pytest.mark.parametrize("shape", [(67, 45), (130, 97), (300, 260), (1, 37), (37, 1), (5, 3)])
+@pytest.mark.parametrize("kind", [cm.MEAN, cm.GAUSS_EULER])
+def test_phase_parity_paper_sides(shape, kind):
+    """Every colour of every level with the paper's odd block sides, through
+    cm_phase, against the oracle's phase from the same state."""
+    H, W = shape
+    img = synth.piecewise_image(H, W, 61 + H, 6, 0.1)
+    f = img.f
+    u = oracle.cycle(f.astype(np.float64), f.astype(np.float64), 20.0, kind, levels=1,
+                     ncolors=4).astype(np.float32)
+    sides = [oracle.level_side(j, 1) for j in range(1, oracle.auto_levels(H, W, 1) + 2)]
+    tot = np.zeros(3, int)
+    fails = []
+    for b in sides:
+        for k in range(4):
+            n, m, t, fl = check_phase(u, f, 20.0, kind, b, 4, k)
+            tot += (n, m, t)
+            fails += fl
+    print(f"\npaper sides {shape} kind={kind} sides={sides}: {tot}")
+    assert not fails, fails[:5]
+    assert tot[2] <= max(2, 0.02 * tot[0])
+
+
+@pytest.mark.parametrize("kind", [cm.MEAN, cm.GAUSS])
+def test_phase_parity_paper_sides_large(kind):
+    """Sides 63 .. 511 (2-, 4- and 8-CTA clusters) on a 1100 x 1030 image."""
+    H, W = 1100, 1030
+    img = synth.piecewise_image(H, W, 5150, 20, 0.08)
+    f = img.f
+    u, _ = run_solve(f, 20.0, kind, 1)
+    tot = np.zeros(3, int)
+    fails = []
+    for b in (63, 127, 255, 511):
+        for k in range(4):
+            n, m, t, fl = check_phase(u, f, 20.0, kind, b, 4, k)
+            tot += (n, m, t)
+            fails += fl
+    print(f"\npaper sides large kind={kind}: {tot}")
+    assert not fails, fails[:5]
+    assert tot[2] <= max(2, 0.02 * tot[0])
+
+
+@pytest.mark.parametrize("kind", [cm.MEAN, cm.GAUSS, cm.MEAN_EULER])
+@pytest.mark.parametrize("levels", [0, 3])
+def test_solve_paper_sides_vs_oracle(kind, levels):
+    """Whole solves with block_sides = 1 (auto levels: sides up to 31 at 64^2;
+    and the paper's J = 3: sides 1, 3, 7): the GPU's final energy against the
+    oracle's FP64 energy of its result, and against an independent oracle
+    solve (loosely: energy ties send the trajectories apart)."""
+    img = synth.single_64()
+    f = img.f
+    opts = cm.default_options(ncolors=4, block_sides=1)
+    u, st = cm.cm_solve(to_dev(f), 20.0 if kind != cm.GAUSS else 15.0, kind, levels=levels,
+                        cycles=12, tol=0.0, options=opts)
+    torch.cuda.synchronize()
+    ug = host(u)
+    alpha = 20.0 if kind != cm.GAUSS else 15.0
+    uo, trace, n, _ = oracle.solve(f.astype(np.float64), alpha, kind, levels=levels, cycles=12,
+                                   ncolors=4, sides=1)
+    Eg = oracle.energy(ug.astype(np.float64), f.astype(np.float64), alpha, kind)
+    assert st.levels == (levels or oracle.auto_levels(64, 64, 1))
+    assert st.cycles_run == 12
+    assert abs(st.energy_final - Eg) <= 1e-5 * abs(Eg)
+    assert abs(Eg - trace[-1]) <= 1e-3 * abs(trace[-1])
+    assert synth.psnr(ug, img.clean) > synth.psnr(f, img.clean)
+
+
+@pytest.mark.parametrize("vcycle,ncolors", [(0, 4), (1, 4), (0, 0)])
+def test_paper_sides_device_loop_batched_and_variants(vcycle, ncolors):
+    """block_sides = 1 with the full V-cycle and the decoupled colouring: the
+    graph solve equals the host loop, the batched solve equals the single
+    solves, and the decoupled colouring never raises the energy."""
+    shapes = [(131, 97), (64, 64), (300, 260)]
+    fs = [to_dev(synth.piecewise_image(H, W, 77 + H, 8, 0.08).f) for H, W in shapes]
+    res = []
+    for use_graph in (1, 0):
+        opts = cm.default_options(ncolors=ncolors, vcycle=vcycle, block_sides=1,
+                                  use_graph=use_graph)
+        res.append([cm.cm_solve(fd, 20.0, cm.MEAN, cycles=40, tol=1e-4, options=opts)
+                    for fd in fs])
+    for (ua, sa), (ub, sb) in zip(*res):
+        assert torch.equal(ua, ub)
+        assert sa.trace() == sb.trace() and sa.cycles_run == sb.cycles_run
+        if ncolors == 0:
+            tr = sa.trace()
+            assert all(b <= a * (1 + 1e-6) for a, b in zip(tr, tr[1:]))
+    opts = cm.default_options(ncolors=ncolors, vcycle=vcycle, block_sides=1)
+    ub, sb = cm.cm_solve_batched(fs, [20.0] * 3, [cm.MEAN] * 3, cycles=40, tol=1e-4,
+                                 options=opts)
+    for (ua, sa), u2, s2 in zip(res[0], ub, sb):
+        assert torch.equal(ua, u2)
+        assert sa.trace() == s2.trace()
