@@ -540,17 +540,24 @@ def main():
     evals_per_block = 3 + (opts.grid_points - 1) + opts.golden_evals   # 0, paper, c_fid, grid, golden
     curv_evals = n_active * evals_per_block * 9
     achieved = curv_evals / (b1_ms / 1e3) / 1e9
-    mufu_peak = 152 * 16 * 2.07e9 / 8 / 1e9   # Geval/s: 8 MUFU rsqrt per stencil evaluation
+    # peak: the measured rsqrtf rate of this GPU (cm_probe_alu) / 8 rsqrt per
+    # generic stencil evaluation (4 directions x 2 planes)
+    alu = cm.cm_probe_alu(local)
+    mufu_peak = alu["rsqrt_per_s"] / 8 / 1e9
     roofline = {"bound": "alu", "kernel": "phase_b1_kernel (b=1)", "achieved": achieved,
                 "peak": mufu_peak, "unit": "Geval/s", "frac": achieved / mufu_peak,
+                "peak_source": "measured (cm_probe_alu)",
+                "measured_rsqrt_per_s": alu["rsqrt_per_s"],
+                "measured_fma_per_s": alu["fma_per_s"],
+                "nominal_peak": 152 * 16 * 2.07e9 / 8 / 1e9,
                 # dram__bytes_read.sum + dram__bytes_write.sum of one launch of this
                 # kernel at 1024^2, from one ncu capture of a solve cycle
                 "traffic": B1_TRAFFIC_BYTES if args.side == 1024 else None,
                 "traffic_unit": "B per launch",
-                "note": "curvature-stencil evaluations/s; peak = 152 SM x 16 MUFU/clk x "
-                        "2.07 GHz / 8 rsqrt per evaluation (derived, nominal clock); the "
-                        "kernel is issue-bound on the FP32/ALU pipes (ncu: issue 57-63% "
-                        "active, MUFU 18-21%)"}
+                "note": "curvature-stencil evaluations/s; peak = measured rsqrtf rate / 8 "
+                        "rsqrt per generic evaluation (nominal: 152 SM x 16 MUFU/clk x "
+                        "2.07 GHz / 8); the kernel is issue-bound on the FP32/ALU pipes "
+                        "(ncu: issue 57-63% active, MUFU 18-21%)"}
 
     warm_eval = warm_eval_gauss = None
     if not args.no_warmstart_eval:

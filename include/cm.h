@@ -280,6 +280,18 @@ int cm_warmstart(cm_ctx* ctx, cm_net* net, const float* f, int N, int H, int W, 
 int cm_energy_noalloc(const float* u, const float* f, int H, int W, float alpha, int kind,
                       double* E_dev, void* stream);
 
+/* Measurement support (not part of the solver).  The sweep kernels are bound
+ * by FP32 and MUFU instruction issue, so their roofline is taken against the
+ * GPU's measured arithmetic rates: fma_per_s (host) receives FP32 fused
+ * multiply-adds per second, rsqrt_per_s (host) rsqrtf operations per second
+ * (one MUFU instruction each), each from a fixed-work kernel of eight
+ * independent dependency chains per thread on every SM (8 CTAs of 256
+ * threads per SM), timed with CUDA events on `stream` after a warm-up launch
+ * (about 10 ms each at the nominal rates).  Allocates and frees 4 bytes of
+ * device memory on `device`; synchronises `stream`.  Returns CM_ERR_INVALID
+ * for null pointers or a negative device, CM_ERR_OOM, or CM_ERR_CUDA. */
+int cm_probe_alu(int device, double* fma_per_s, double* rsqrt_per_s, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

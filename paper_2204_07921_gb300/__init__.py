@@ -16,7 +16,7 @@ from .build import LIB, build as build_library
 
 __all__ = [
     "CMError", "Options", "Stats", "Context", "load", "cm_energy", "cm_curvature", "cm_phase",
-    "cm_level", "cm_energy_noalloc", "cm_solve_batched",
+    "cm_level", "cm_energy_noalloc", "cm_solve_batched", "cm_probe_alu",
     "cm_solve", "cm_auto_levels", "MEAN", "GAUSS", "MEAN_EULER", "GAUSS_EULER",
 ]
 
@@ -71,6 +71,7 @@ SIGNATURES = {
     "cm_curvature": (_I, [_P, _P, _I, _I, _I, _P, _P]),
     "cm_phase": (_I, [_P, _P, _P, _P, _I, _I, _F, _I, _I, _I, ctypes.POINTER(Options), _P, _P]),
     "cm_energy_noalloc": (_I, [_P, _P, _I, _I, _F, _I, _P, _P]),
+    "cm_probe_alu": (_I, [_I, _P, _P, _P]),
     "cm_level": (_I, [_P, _P, _P, _P, _I, _I, _F, _I, _I, ctypes.POINTER(Options), _P, _P]),
     "cm_solve_batched": (_I, [_P, _I, ctypes.POINTER(_P), ctypes.POINTER(_I), ctypes.POINTER(_I),
                               ctypes.POINTER(_F), ctypes.POINTER(_I), _I, _I, _D,
@@ -186,6 +187,15 @@ def cm_energy(u, f, alpha: float, kind: int, ctx: Context | None = None, stream=
     c._check(load().cm_energy(c.handle, u.data_ptr(), f.data_ptr(), H, W, float(alpha), kind,
                               ctypes.byref(E), _stream_ptr(stream)))
     return E.value
+
+
+def cm_probe_alu(device: int = 0, stream=None) -> dict:
+    """Measured FP32 FMA and rsqrtf rates of the GPU (operations per second)."""
+    fma, rsq = ctypes.c_double(), ctypes.c_double()
+    rc = load().cm_probe_alu(device, ctypes.byref(fma), ctypes.byref(rsq), _stream_ptr(stream))
+    if rc != CM_OK:
+        raise CMError(rc, "cm_probe_alu failed")
+    return {"fma_per_s": fma.value, "rsqrt_per_s": rsq.value}
 
 
 def cm_energy_noalloc(u, f, alpha: float, kind: int, E_out, stream=None):
