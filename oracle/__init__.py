@@ -73,6 +73,7 @@ def lib():
                 "orc_cycle": (None, [dp, dp, i, i, d, i, i, i, i, i, i, i, i, i, i]),
                 "orc_solve": (i, [dp, i, i, d, i, i, i, d, dp, dp, i, i, i, i, i, i, i, i, dp, ip]),
                 "orc_level_colours": (i, [i, i]),
+                "orc_chalf_map": (None, [dp, i, i, i, dp]),
                 "orc_num_threads": (i, []),
                 "orc_local_energy_batch": (None, [dp, dp, i, i, i, i, i, i, d, i, dp, i, dp]),
             }
@@ -203,6 +204,16 @@ def level_sequential(u, f, alpha, kind, b, G=DEFAULT_G, K=DEFAULT_K, use_paper=T
     lib().orc_level_sequential(_dp(u), _dp(f), H, W, float(alpha), kind, b, G, K,
                                int(use_paper), int(one_step))
     return u
+
+
+def chalf_map(u, kind) -> np.ndarray:
+    """c_{1/2} of every pixel: the shift the curvature term alone asks for
+    (Eq. c-sol1; Prop. 2 for Gaussian curvature)."""
+    u = _f64(u)
+    H, W = u.shape
+    out = np.zeros((H, W))
+    lib().orc_chalf_map(_dp(u), H, W, kind, _dp(out))
+    return out
 
 
 def level_colours(ncolors, b) -> int:

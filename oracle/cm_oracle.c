@@ -316,8 +316,19 @@ double orc_local_energy(const double *u, const double *f, int H, int W, int r0, 
  * with f* = f - u at the pixel.  The Eq. (FOBOS step2) form with a single
  * prox term would give 1 + alpha eta; Eq. (c-sol2) and the coarse-layer
  * closed form both use 2 + alpha eta, which is followed here. */
+double orc_chalf(const double *u, int H, int W, int r, int c, int kind);
+
 double orc_paper_candidate(const double *u, const double *f, int H, int W, int r, int c,
                            double alpha, int kind) {
+    double chalf = orc_chalf(u, H, W, r, c, kind);
+    double fstar = f[(size_t)r * W + c] - u[(size_t)r * W + c];
+    return (0.0 + chalf + alpha * 1.0 * fstar) / (2.0 + alpha * 1.0);
+}
+
+/* c_{1/2} of the pixel (r, c): the shift that the curvature term alone asks
+ * for (Eq. c-sol1 for mean curvature, Prop. 2 for Gaussian curvature; the
+ * Euler-fit kinds use the rule of their base kind). */
+double orc_chalf(const double *u, int H, int W, int r, int c, int kind) {
     double kbar[4], d[8];
     orc_direction_curvatures(u, H, W, r, c, kbar, d);
     double chalf;
@@ -334,8 +345,13 @@ double orc_paper_candidate(const double *u, const double *f, int H, int W, int r
         int ts = fabs(kbar[tmin]) <= fabs(kbar[tmax]) ? tmin : tmax;
         chalf = 0.5 * (d[2 * ts] + d[2 * ts + 1]);
     }
-    double fstar = f[(size_t)r * W + c] - u[(size_t)r * W + c];
-    return (0.0 + chalf + alpha * 1.0 * fstar) / (2.0 + alpha * 1.0);
+    return chalf;
+}
+
+void orc_chalf_map(const double *u, int H, int W, int kind, double *out) {
+#pragma omp parallel for schedule(static)
+    for (int r = 0; r < H; ++r)
+        for (int c = 0; c < W; ++c) out[(size_t)r * W + c] = orc_chalf(u, H, W, r, c, kind);
 }
 
 /* Candidate bookkeeping: keep the lowest E; energies within the tie

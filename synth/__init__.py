@@ -214,3 +214,48 @@ def psnr(u: np.ndarray, clean: np.ndarray) -> float:
     """10 log10(1 / MSE) for images on [0, 1]."""
     mse = float(np.mean((np.asarray(u, np.float64) - np.asarray(clean, np.float64)) ** 2))
     return float("inf") if mse == 0 else 10.0 * math.log10(1.0 / mse)
+
+
+# ---------------------------------------------------------------------------
+# MRI-like reconstruction inputs (Sec. 5; the paper's MRI data are not
+# available here).
+
+@dataclass
+class MriCase:
+    clean: np.ndarray    # phantom, float32 (H, W)
+    mask: np.ndarray     # sampled k-space rows, uint8 (H, W), 0 or 1
+    kspace: np.ndarray   # observed data b, complex64 (H, W), zero off the mask
+    seed: int
+    sigma: float
+
+
+def mri_case(H: int, W: int, seed: int, accel: float = 3.0, centre: float = 0.08,
+             sigma: float = 0.01, n_shapes: int = 12) -> MriCase:
+    """A seeded undersampled-acquisition case.
+
+    Phantom: the clean image of piecewise_image(H, W, seed, n_shapes, 0).
+    Mask: Cartesian phase-encoding rows of the unshifted 2-D spectrum; every
+    row whose signed frequency |k| (k = i for i < H/2, else i - H) is at most
+    centre * H / 2 is sampled, every other row with the probability that
+    makes the expected sampled fraction 1 / accel (SplitMix64 uniforms).
+    Data: b = mask * (F clean + sigma (n1 + i n2)), F the orthonormal 2-D DFT
+    (numpy.fft.fft2 with norm="ortho"), n1, n2 i.i.d. N(0, 1).  This only
+    simulates the acquisition; the reconstruction applies its own operator.
+    """
+    clean = piecewise_image(H, W, seed, n_shapes, 0.0).clean.astype(np.float64)
+    rng = SplitMix64(_mix64(seed ^ 0x6D7269))
+    freq = np.where(np.arange(H) < (H + 1) // 2, np.arange(H), np.arange(H) - H)
+    low = np.abs(freq) <= centre * H / 2
+    n_low = int(low.sum())
+    p = min(1.0, max(0.0, (H / accel - n_low) / max(H - n_low, 1)))
+    rows = low.copy()
+    for i in range(H):
+        u = rng.uniform()
+        if not low[i] and u < p:
+            rows[i] = True
+    mask = np.broadcast_to(rows[:, None], (H, W)).astype(np.uint8)
+    g = gaussian_noise(_mix64(seed ^ 0x6B7370), 2 * H * W)
+    noise = g[0::2].reshape(H, W) + 1j * g[1::2].reshape(H, W)
+    data = mask * (np.fft.fft2(clean, norm="ortho") + sigma * noise)
+    return MriCase(clean=clean.astype(np.float32), mask=mask,
+                   kspace=data.astype(np.complex64), seed=seed, sigma=sigma)

@@ -1,0 +1,123 @@
+"""Pins of the reconstruction oracle (Sec. 5, MRI-like operator A = M F).
+
+The operator is pinned by its adjoint identity and Parseval; the per-colour
+correction by a closed form (full mask: the Gram matrix is diagonal) and by
+a dense linear solve of the assembled normal equations; the sweep by
+monotone descent of the data term when the regulariser vanishes, and by
+descent and denoising on an undersampled case.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from oracle import recon
+
+
+def test_operator_adjoint_and_parseval():
+    rng = np.random.default_rng(0)
+    H, W = 12, 10
+    mask = (rng.random((H, W)) < 0.4).astype(float)
+    u = rng.normal(size=(H, W))
+    y = rng.normal(size=(H, W)) + 1j * rng.normal(size=(H, W))
+    # <A u, y> = <u, A^H y> (complex inner products; u real)
+    lhs = np.vdot(y, recon.forward(u, mask))
+    rhs = np.vdot(recon.adjoint(y, mask), u)
+    assert lhs == pytest.approx(rhs, rel=1e-12)
+    # orthonormal DFT: ||F u|| = ||u||; the mask can only shrink it
+    full = np.ones((H, W))
+    assert np.linalg.norm(recon.forward(u, full)) == pytest.approx(np.linalg.norm(u), rel=1e-12)
+    assert np.linalg.norm(recon.forward(u, mask)) < np.linalg.norm(u)
+    # the DC entry of F u is sum(u) / sqrt(H W)
+    assert recon.forward(u, full)[0, 0] == pytest.approx(u.sum() / np.sqrt(H * W), rel=1e-12)
+
+
+def test_colour_labels_cover_the_colour():
+    H, W, b = 13, 10, 3
+    for k in range(4):
+        lab, n = recon.colour_labels(H, W, b, 4, k)
+        seen = set()
+        for r in range(H):
+            for c in range(W):
+                bi, bj = r // b, c // b
+                if oracle.block_colour(bi, bj, 4) == k:
+                    assert lab[r, c] >= 0
+                    seen.add(int(lab[r, c]))
+                else:
+                    assert lab[r, c] == -1
+        assert seen == set(range(n))
+
+
+@pytest.mark.parametrize("b", [1, 2, 4])
+def test_full_mask_step_is_the_diagonal_closed_form(b):
+    """With every k-space entry sampled, A^H A = I, so <A phi_i, A phi_j> =
+    s_i delta_ij (disjoint blocks of s_i pixels) and each block's shift is
+    c_i = (<b - A u, A phi_i> + 2 alpha d_i) / (s_i + 2 alpha)."""
+    case = synth.mri_case(20, 17, 3, accel=1.0, sigma=0.02)
+    assert case.mask.all()
+    mask = case.mask.astype(float)
+    kspace = case.kspace.astype(complex)
+    u = np.real(recon.adjoint(kspace, mask)) + 0.05 * np.sin(np.arange(20 * 17)).reshape(20, 17)
+    alpha = 0.3
+    for k in range(4):
+        _, c = recon.colour_step(u, kspace, mask, alpha, oracle.MEAN, b, 4, k, cg_iters=20)
+        lab, n = recon.colour_labels(20, 17, b, 4, k)
+        g = np.real(recon.adjoint(kspace - recon.forward(u, mask), mask))
+        d = oracle.chalf_map(u, oracle.MEAN) if b == 1 else np.zeros_like(u)
+        for i in range(n):
+            blk = lab == i
+            s = blk.sum()
+            di = d[blk].sum() if b == 1 else 0.0
+            want = (g[blk].sum() + 2 * alpha * di) / (s + 2 * alpha)
+            assert c[i] == pytest.approx(want, rel=1e-9, abs=1e-12)
+
+
+def test_cg_equals_dense_normal_equations():
+    """Undersampled mask: assemble the Gram matrix column by column from A
+    applied to every block indicator, solve it densely, and compare with the
+    colour step's CG run to n iterations (exact in exact arithmetic)."""
+    case = synth.mri_case(12, 10, 5, accel=2.5, sigma=0.02)
+    mask = case.mask.astype(float)
+    kspace = case.kspace.astype(complex)
+    u = np.real(recon.adjoint(kspace, mask))
+    alpha = 0.05
+    b, k = 2, 1
+    lab, n = recon.colour_labels(12, 10, b, 4, k)
+    G = np.zeros((n, n))
+    Aphi = [recon.forward((lab == i).astype(float), mask) for i in range(n)]
+    for i in range(n):
+        for j in range(n):
+            G[i, j] = np.real(np.vdot(Aphi[i], Aphi[j]))
+    res = kspace - recon.forward(u, mask)
+    rhs = np.array([np.real(np.vdot(Aphi[i], res)) for i in range(n)])
+    c_dense = np.linalg.solve(G + 2 * alpha * np.eye(n), rhs)
+    _, c = recon.colour_step(u, kspace, mask, alpha, oracle.MEAN, b, 4, k, cg_iters=n)
+    np.testing.assert_allclose(c, c_dense, rtol=1e-8, atol=1e-10)
+
+
+def test_vanishing_regulariser_never_raises_the_data_term():
+    """alpha -> 0: each colour step minimises 1/2 ||A u - b||^2 exactly over
+    its blocks' span (CG run to convergence), so the data term never rises."""
+    case = synth.mri_case(24, 20, 9, accel=3.0, sigma=0.02)
+    mask = case.mask.astype(float)
+    kspace = case.kspace.astype(complex)
+    u = np.real(recon.adjoint(kspace, mask))
+    data = lambda v: 0.5 * np.sum(np.abs(recon.forward(v, mask) - kspace) ** 2)
+    prev = data(u)
+    for j in range(1, 4):
+        b = oracle.level_side(j)
+        for k in range(4):
+            lab, n = recon.colour_labels(24, 20, b, 4, k)
+            u, _ = recon.colour_step(u, kspace, mask, 1e-9, oracle.MEAN, b, 4, k,
+                                     cg_iters=n + 2)
+            cur = data(u)
+            assert cur <= prev * (1 + 1e-9) + 1e-15
+            prev = cur
+
+
+def test_reconstruction_descends_and_denoises():
+    case = synth.mri_case(64, 64, 7, accel=3.0, sigma=0.01)
+    u0 = np.real(recon.adjoint(case.kspace.astype(complex), case.mask.astype(float)))
+    u, trace = recon.solve(case.kspace, case.mask, 0.02, oracle.MEAN, cycles=4, cg_iters=8)
+    assert np.all(np.diff(trace) < 0)
+    assert synth.psnr(u, case.clean) > synth.psnr(u0, case.clean) + 1.0
