@@ -280,6 +280,34 @@ int cm_warmstart(cm_ctx* ctx, cm_net* net, const float* f, int N, int H, int W, 
 int cm_energy_noalloc(const float* u, const float* f, int H, int W, float alpha, int kind,
                       double* E_dev, void* stream);
 
+/* Reconstruction extension (Sec. 5), MRI-like operator: recovers a real
+ * H x W image u from k-space data b by minimising
+ *     J(u) = 1/2 ||A u - b||^2 + alpha sum |kappa(u)|,
+ * A = M F with F the orthonormal 2-D DFT (unitary: F^H F = I, the DC entry is
+ * sum(u) / sqrt(HW)) and M the 0/1 mask of sampled entries.  Each cycle
+ * visits the levels fine to coarse and the colours in order (Alg. 3); the
+ * blocks phi_i of one colour are corrected together by cg_iters conjugate-
+ * gradient iterations (from c = 0; stopping early only on a zero residual or
+ * a non-positive p.Ap) on the normal equations of Sec. 5,
+ *     [Re<A phi_i, A phi_j> + 2 alpha delta_ij] c = Re<b - A u, A phi_i> + 2 alpha d_i,
+ * with d_i = c_{1/2} of Eq. c-sol1 (Prop. 2 for kinds 1 and 3) on the finest
+ * level and 0 on coarser ones.
+ * kspace: device, H x W complex values as (re, im) float pairs, row-major,
+ * zero off the mask.  mask: device, H x W bytes, 0 or 1.  u0: device H x W or
+ * NULL (start from the zero-filled Re(A^H b)); u_out: device H x W (may
+ * alias u0).  levels = 0: cm_auto_levels rule (opts->block_sides applies, as
+ * do opts->ncolors; the search options do not).  trace_host (nullable, host,
+ * cycles + 1 doubles) receives J before the first cycle and after each.
+ * The transforms are cuFFT, loaded on first use (CM_ERR_CUDA with a message
+ * if libcufft.so.12 cannot be loaded); the scratch (two complex images and
+ * the CG vectors) stays in the context.  Synchronises `stream`.  Returns
+ * CM_ERR_INVALID for null pointers, sizes < 1, a bad alpha, kind or option,
+ * cycles outside 0 .. 100000 or cg_iters outside 1 .. 1000. */
+int cm_recon(cm_ctx* ctx, const float* kspace, const unsigned char* mask, int H, int W,
+             float alpha, int kind, int levels, int cycles, int cg_iters, const float* u0,
+             float* u_out, const cm_options* opts /* host, nullable */,
+             double* trace_host /* host, nullable */, void* stream);
+
 /* Measurement support (not part of the solver).  The sweep kernels are bound
  * by FP32 and MUFU instruction issue, so their roofline is taken against the
  * GPU's measured arithmetic rates: fma_per_s (host) receives FP32 fused

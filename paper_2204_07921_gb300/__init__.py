@@ -16,7 +16,7 @@ from .build import LIB, build as build_library
 
 __all__ = [
     "CMError", "Options", "Stats", "Context", "load", "cm_energy", "cm_curvature", "cm_phase",
-    "cm_level", "cm_energy_noalloc", "cm_solve_batched", "cm_probe_alu",
+    "cm_level", "cm_energy_noalloc", "cm_solve_batched", "cm_probe_alu", "cm_recon",
     "cm_solve", "cm_auto_levels", "MEAN", "GAUSS", "MEAN_EULER", "GAUSS_EULER",
 ]
 
@@ -72,6 +72,8 @@ SIGNATURES = {
     "cm_phase": (_I, [_P, _P, _P, _P, _I, _I, _F, _I, _I, _I, ctypes.POINTER(Options), _P, _P]),
     "cm_energy_noalloc": (_I, [_P, _P, _I, _I, _F, _I, _P, _P]),
     "cm_probe_alu": (_I, [_I, _P, _P, _P]),
+    "cm_recon": (_I, [_P, _P, _P, _I, _I, _F, _I, _I, _I, _I, _P, _P, ctypes.POINTER(Options),
+                      _P, _P]),
     "cm_level": (_I, [_P, _P, _P, _P, _I, _I, _F, _I, _I, ctypes.POINTER(Options), _P, _P]),
     "cm_solve_batched": (_I, [_P, _I, ctypes.POINTER(_P), ctypes.POINTER(_I), ctypes.POINTER(_I),
                               ctypes.POINTER(_F), ctypes.POINTER(_I), _I, _I, _D,
@@ -278,6 +280,37 @@ def cm_solve(f, alpha: float, kind: int, levels: int = 0, cycles: int = 20, tol:
                              _stream_ptr(stream)),
              ok=(CM_OK, CM_NOT_CONVERGED))
     return u_out, st
+
+
+def cm_recon(kspace, mask, alpha: float, kind: int = MEAN, levels: int = 0, cycles: int = 5,
+             cg_iters: int = 8, u0=None, u_out=None, options: Options | None = None,
+             ctx: Context | None = None, stream=None):
+    """Reconstruction (Sec. 5) from k-space data of A = M F.  kspace: CUDA
+    complex64 H x W (zero off the mask); mask: CUDA uint8 H x W.  Returns
+    (u_out, trace of J: before the first cycle and after each)."""
+    import numpy as np
+    import torch
+    if not (isinstance(kspace, torch.Tensor) and kspace.is_cuda and
+            kspace.dtype == torch.complex64 and kspace.dim() == 2 and kspace.is_contiguous()):
+        raise TypeError("kspace: expected a contiguous CUDA complex64 H x W tensor")
+    if not (isinstance(mask, torch.Tensor) and mask.is_cuda and mask.dtype == torch.uint8 and
+            mask.shape == kspace.shape and mask.is_contiguous()):
+        raise TypeError("mask: expected a contiguous CUDA uint8 tensor of the data's shape")
+    H, W = kspace.shape
+    c = _ctx(ctx, kspace)
+    if u_out is None:
+        u_out = torch.empty((H, W), dtype=torch.float32, device=kspace.device)
+    _img(u_out, "u_out")
+    if u0 is not None:
+        _img(u0, "u0")
+    opts = options or default_options()
+    trace = np.zeros(cycles + 1)
+    c._check(load().cm_recon(c.handle, kspace.data_ptr(), mask.data_ptr(), H, W, float(alpha),
+                             kind, levels, cycles, cg_iters,
+                             u0.data_ptr() if u0 is not None else None, u_out.data_ptr(),
+                             ctypes.byref(opts), trace.ctypes.data_as(ctypes.c_void_p),
+                             _stream_ptr(stream)))
+    return u_out, trace
 
 
 def cm_solve_batched(fs, alphas, kinds, levels: int = 0, cycles: int = 2000, tol: float = 1e-4,

@@ -21,6 +21,7 @@
 #include "cm_batched.h"
 #include "cm_cnn.h"
 #include "cm_kernels.h"
+#include "cm_recon.h"
 
 struct GraphKey {
     const float* S;
@@ -67,6 +68,7 @@ struct cm_ctx {
         GraphKey key;
         cudaGraphExec_t exec = nullptr;
     } sgraph;
+    cm::ReconWork* recon = nullptr;   // reconstruction buffers (cm_recon)
 };
 
 namespace {
@@ -419,6 +421,7 @@ void cm_destroy(cm_ctx* ctx) {
     for (auto s : ctx->bstreams) cudaStreamDestroy(s);
     for (auto e : ctx->bevents) cudaEventDestroy(e);
     if (ctx->arena) cudaFree(ctx->arena);
+    cm::recon_work_destroy(ctx->recon);
     delete ctx;
 }
 
@@ -910,6 +913,45 @@ int cm_solve_batched(cm_ctx* ctx, int n, const float* const* f, const int* H, co
     }
     if (status == CM_ERR_NUMERIC) return fail(ctx, status, "cm_solve_batched: non-finite energy");
     if (status == CM_NOT_CONVERGED) return fail(ctx, status, "cm_solve_batched: cycle cap reached");
+    return CM_OK;
+}
+
+int cm_recon(cm_ctx* ctx, const float* kspace, const unsigned char* mask, int H, int W,
+             float alpha, int kind, int levels, int cycles, int cg_iters, const float* u0,
+             float* u_out, const cm_options* opts, double* trace_host, void* stream) {
+    if (!ctx) return CM_ERR_INVALID;
+    cm_options o;
+    cm_options_default(&o);
+    if (opts) o = *opts;
+    int rc = check_opts(ctx, o);
+    if (rc) return rc;
+    if (!kspace || !mask || !u_out || H < 1 || W < 1 || !finite_positive(alpha) ||
+        !valid_kind(kind) || levels < 0 || cycles < 0 || cycles > 100000 || cg_iters < 1 ||
+        cg_iters > 1000 || (const void*)u_out == (const void*)kspace)
+        return fail(ctx, CM_ERR_INVALID, "cm_recon: invalid argument");
+    const int L = solve_levels(levels, H, W, o);
+    if (!levels_ok(L, o)) return fail(ctx, CM_ERR_INVALID, "cm_recon: too many levels");
+    CM_CUDA(cudaSetDevice(ctx->device));
+    if (!ctx->recon) ctx->recon = cm::recon_work_create();
+    cm::ReconArgs a;
+    a.kspace = (const float2*)kspace;
+    a.mask = mask;
+    a.H = H;
+    a.W = W;
+    a.alpha = alpha;
+    a.kind = kind;
+    a.levels = L;
+    a.sides = o.block_sides;
+    a.ncolors = o.ncolors;
+    a.cycles = cycles;
+    a.cg_iters = cg_iters;
+    a.u0 = u0;
+    a.u = u_out;
+    a.trace_host = trace_host;
+    const char* msg = "";
+    rc = cm::recon_run(ctx->recon, a, (cudaStream_t)stream, &msg);
+    if (rc == 3) return fail(ctx, CM_ERR_OOM, std::string("cm_recon: ") + msg);
+    if (rc) return fail(ctx, CM_ERR_CUDA, std::string("cm_recon: ") + msg);
     return CM_OK;
 }
 

@@ -180,6 +180,54 @@ __device__ __forceinline__ float aff_abs_curv(const AffPix& p, float c) {
     return kappa_abs<KIND>(k0, k1, k2, k3);
 }
 
+// Plane distances of one line (for the paper's one-step candidate).
+__device__ __forceinline__ void dir_dist(float A, float B, float O, float Z1, float Z2,
+                                         float four_h2, float two_h, float& d1, float& d2) {
+    const float D = B - A, S = A + B;
+    const float delta = fmaf(0.5f, S, -O);
+    const float base = fmaf(D, D, four_h2);
+    const float e1 = fmaf(-2.0f, Z1, S), e2 = fmaf(-2.0f, Z2, S);
+    d1 = two_h * delta * rsqrtf(fmaf(e1, e1, base));
+    d2 = two_h * delta * rsqrtf(fmaf(e2, e2, base));
+}
+
+// c_{1/2} of the pixel whose 3x3 window is w: the shift the curvature term
+// alone asks for -- the mean of the eight plane distances (Eq. c-sol1) or,
+// for Gaussian curvature, the mean distance of the plane pair of the extreme
+// direction curvature with the smaller magnitude (Prop. 2).  The Euler-fit
+// kinds use the rule of their base kind.
+template <int KIND>
+__device__ __forceinline__ float paper_chalf(const float w[9]) {
+    const float SQ2x2 = 2.8284271247461903f;
+    float d[8];
+    dir_dist(w[3], w[5], w[4], w[1], w[7], 4.0f, 2.0f, d[0], d[1]);
+    dir_dist(w[1], w[7], w[4], w[3], w[5], 4.0f, 2.0f, d[2], d[3]);
+    dir_dist(w[0], w[8], w[4], w[2], w[6], 8.0f, SQ2x2, d[4], d[5]);
+    dir_dist(w[2], w[6], w[4], w[0], w[8], 8.0f, SQ2x2, d[6], d[7]);
+    float chalf;
+    if (KIND == KIND_MEAN || KIND == KIND_MEAN_EULER) {
+        chalf = 0.125f * (((d[0] + d[1]) + (d[2] + d[3])) + ((d[4] + d[5]) + (d[6] + d[7])));
+    } else {
+        KBar4 k = direction_curvatures(w);
+        int tmin = 0, tmax = 0;
+#pragma unroll
+        for (int t = 1; t < 4; ++t) {
+            if (k.k[t] < k.k[tmin]) tmin = t;
+            if (k.k[t] > k.k[tmax]) tmax = t;
+        }
+        int ts = fabsf(k.k[tmin]) <= fabsf(k.k[tmax]) ? tmin : tmax;
+        float dd0 = d[0], dd1 = d[1];
+#pragma unroll
+        for (int t = 1; t < 4; ++t)
+            if (ts == t) {
+                dd0 = d[2 * t];
+                dd1 = d[2 * t + 1];
+            }
+        chalf = 0.5f * (dd0 + dd1);
+    }
+    return chalf;
+}
+
 // Clamp-to-edge boundary: out-of-image neighbours take the nearest pixel.
 __device__ __forceinline__ int clampi(int v, int lo, int hi) { return min(max(v, lo), hi); }
 

@@ -23,51 +23,11 @@
 
 namespace cm {
 
-// Plane distances of one line (for the paper's one-step candidate).
-__device__ __forceinline__ void dir_dist(float A, float B, float O, float Z1, float Z2,
-                                         float four_h2, float two_h, float& d1, float& d2) {
-    const float D = B - A, S = A + B;
-    const float delta = fmaf(0.5f, S, -O);
-    const float base = fmaf(D, D, four_h2);
-    const float e1 = fmaf(-2.0f, Z1, S), e2 = fmaf(-2.0f, Z2, S);
-    d1 = two_h * delta * rsqrtf(fmaf(e1, e1, base));
-    d2 = two_h * delta * rsqrtf(fmaf(e2, e2, base));
-}
-
 // The paper's finest-level estimate: Alg. 2 with t = 0, c_0 = 0, eta_0 = 1:
-// c_1 = (c_{1/2} + alpha f*) / (2 + alpha), c_{1/2} the mean plane distance
-// (Eq. c-sol1) or, for Gaussian curvature, the distance pair of the extreme
-// direction curvature with the smaller magnitude (Prop. 2).
+// c_1 = (c_{1/2} + alpha f*) / (2 + alpha), c_{1/2} from paper_chalf.
 template <int KIND>
 __device__ __forceinline__ float paper_candidate(const float w[9], float fstar, float alpha) {
-    const float SQ2x2 = 2.8284271247461903f;
-    float d[8];
-    dir_dist(w[3], w[5], w[4], w[1], w[7], 4.0f, 2.0f, d[0], d[1]);
-    dir_dist(w[1], w[7], w[4], w[3], w[5], 4.0f, 2.0f, d[2], d[3]);
-    dir_dist(w[0], w[8], w[4], w[2], w[6], 8.0f, SQ2x2, d[4], d[5]);
-    dir_dist(w[2], w[6], w[4], w[0], w[8], 8.0f, SQ2x2, d[6], d[7]);
-    float chalf;
-    if (KIND == KIND_MEAN || KIND == KIND_MEAN_EULER) {
-        chalf = 0.125f * (((d[0] + d[1]) + (d[2] + d[3])) + ((d[4] + d[5]) + (d[6] + d[7])));
-    } else {
-        KBar4 k = direction_curvatures(w);
-        int tmin = 0, tmax = 0;
-#pragma unroll
-        for (int t = 1; t < 4; ++t) {
-            if (k.k[t] < k.k[tmin]) tmin = t;
-            if (k.k[t] > k.k[tmax]) tmax = t;
-        }
-        int ts = fabsf(k.k[tmin]) <= fabsf(k.k[tmax]) ? tmin : tmax;
-        float dd0 = d[0], dd1 = d[1];
-#pragma unroll
-        for (int t = 1; t < 4; ++t)
-            if (ts == t) {
-                dd0 = d[2 * t];
-                dd1 = d[2 * t + 1];
-            }
-        chalf = 0.5f * (dd0 + dd1);
-    }
-    return (chalf + alpha * fstar) / (2.0f + alpha);
+    return (paper_chalf<KIND>(w) + alpha * fstar) / (2.0f + alpha);
 }
 
 // For p at window position POS of its neighbour: the line with p as an end

@@ -1,0 +1,606 @@
+// cm_recon.cu -- reconstruction extension (Sec. 5) with an MRI-like operator.
+//
+// Minimises J(u) = 1/2 ||A u - b||^2 + alpha sum |kappa(u)| for a real image u,
+// A = M F (M a 0/1 mask of sampled k-space entries, F the orthonormal 2-D
+// DFT).  The sweep visits the levels fine to coarse and the colours in order
+// (Alg. 3); the blocks phi_i of one colour are solved together, because A
+// couples them: Sec. 5 replaces each block's curvature term by
+// alpha (c_i - d_i)^2 around the curvature-only estimate d_i and solves
+//   [Re<A phi_i, A phi_j> + 2 alpha delta_ij] c = Re<b - A u, A phi_i> + 2 alpha d_i
+// by conjugate gradients, matrix-free: one product is a scatter of the block
+// values, an FFT, the mask, an inverse FFT and block sums.  d_i is c_{1/2} of
+// Eq. c-sol1 (Prop. 2 for Gaussian curvature) on the finest level and 0 on
+// coarser ones; CG runs a fixed number of iterations from c = 0 and stops
+// early only on a zero residual or a non-positive p.Ap.  The start is the
+// zero-filled Re(A^H b).
+//
+// The transforms are cuFFT (single-precision C2C, unnormalised; the two
+// 1/sqrt(HW) factors of the orthonormal pair are folded into the mask
+// kernels), loaded with dlopen on first use so that the rest of the library
+// does not depend on it.  Every other step is a kernel of this file.  The
+// CG scalars stay on the device; the reductions are FP64 with a fixed order
+// (per-CTA partials, the last CTA finishes), so a run is deterministic.  One
+// cycle is captured as a CUDA graph and launched once per cycle.
+#include <cuda_runtime.h>
+#include <cufft.h>
+#include <dlfcn.h>
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+
+#include "cm_device.cuh"
+#include "cm_kernels.h"
+#include "cm_recon.h"
+#include "cm_search.cuh"
+
+namespace cm {
+
+// ---------------------------------------------------------------------------
+// cuFFT entry points, resolved once.
+
+struct CufftApi {
+    decltype(&cufftPlan2d) plan2d = nullptr;
+    decltype(&cufftExecC2C) exec = nullptr;
+    decltype(&cufftSetStream) set_stream = nullptr;
+    decltype(&cufftDestroy) destroy = nullptr;
+    bool ok = false;
+};
+
+static const CufftApi& cufft_api() {
+    static const CufftApi api = [] {
+        CufftApi c;
+        const char* names[] = {"libcufft.so.12", "libcufft.so", "/usr/local/cuda/lib64/libcufft.so.12",
+                               "/usr/local/cuda/lib64/libcufft.so"};
+        void* h = nullptr;
+        for (const char* n : names)
+            if ((h = dlopen(n, RTLD_NOW | RTLD_LOCAL)) != nullptr) break;
+        if (!h) return c;
+        c.plan2d = (decltype(&cufftPlan2d))dlsym(h, "cufftPlan2d");
+        c.exec = (decltype(&cufftExecC2C))dlsym(h, "cufftExecC2C");
+        c.set_stream = (decltype(&cufftSetStream))dlsym(h, "cufftSetStream");
+        c.destroy = (decltype(&cufftDestroy))dlsym(h, "cufftDestroy");
+        c.ok = c.plan2d && c.exec && c.set_stream && c.destroy;
+        return c;
+    }();
+    return api;
+}
+
+// ---------------------------------------------------------------------------
+// Kernels.
+
+constexpr int RT = 256;              // threads per CTA of every kernel here
+constexpr int RED_CTAS = 1024;       // grid of the grid-stride reductions
+constexpr int MAX_CTAS = 1 << 16;    // largest reduction grid (partials size)
+
+// Slot of block (bi, bj) among the blocks of its colour: the inverse of
+// active_block.
+__device__ __forceinline__ int slot_of(int bi, int bj, int nbj, int ncol) {
+    if (ncol == 2) return bi * ((nbj + 1) >> 1) + (bj >> 1);
+    const int p = colour_side(ncol);
+    return (bi / p) * ((nbj + p - 1) / p) + bj / p;
+}
+
+// Sum of v over the CTA; the last CTA to finish adds the per-CTA partials in
+// a fixed order into *out and clears the ticket.  Every thread must call it.
+__device__ void cta_sum_finish(double v, double* partials, unsigned* ticket, double* out) {
+    __shared__ double ws[RT / 32];
+    __shared__ bool last;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int i = 0; i < RT / 32; ++i) t += ws[i];
+        partials[blockIdx.x] = t;
+        __threadfence();
+        last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    double s = 0.0;
+    for (int i = threadIdx.x; i < (int)gridDim.x; i += RT) s += ((volatile double*)partials)[i];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int i = 0; i < RT / 32; ++i) t += ws[i];
+        *out = t;
+        *ticket = 0u;
+    }
+}
+
+__global__ void __launch_bounds__(RT) to_complex_kernel(const float* __restrict__ u,
+                                                        float2* __restrict__ X, size_t N) {
+    for (size_t i = (size_t)blockIdx.x * RT + threadIdx.x; i < N; i += (size_t)gridDim.x * RT)
+        X[i] = make_float2(u[i], 0.0f);
+}
+
+// After X = F_unnormalised u: X <- M (b - s X) s, so that the inverse
+// transform gives A^H (b - A u) (s = 1 / sqrt(HW)).
+__global__ void __launch_bounds__(RT) resid_kernel(float2* __restrict__ X,
+                                                   const float2* __restrict__ bk,
+                                                   const uint8_t* __restrict__ mask, size_t N,
+                                                   float s) {
+    for (size_t i = (size_t)blockIdx.x * RT + threadIdx.x; i < N; i += (size_t)gridDim.x * RT) {
+        const float2 x = X[i], y = bk[i];
+        X[i] = mask[i] ? make_float2((y.x - s * x.x) * s, (y.y - s * x.y) * s)
+                       : make_float2(0.0f, 0.0f);
+    }
+}
+
+// X <- M b s (the zero-filled start A^H b after the inverse transform).
+__global__ void __launch_bounds__(RT) masked_data_kernel(float2* __restrict__ X,
+                                                         const float2* __restrict__ bk,
+                                                         const uint8_t* __restrict__ mask, size_t N,
+                                                         float s) {
+    for (size_t i = (size_t)blockIdx.x * RT + threadIdx.x; i < N; i += (size_t)gridDim.x * RT) {
+        const float2 y = bk[i];
+        X[i] = mask[i] ? make_float2(y.x * s, y.y * s) : make_float2(0.0f, 0.0f);
+    }
+}
+
+__global__ void __launch_bounds__(RT) real_part_kernel(const float2* __restrict__ X,
+                                                       float* __restrict__ u, size_t N) {
+    for (size_t i = (size_t)blockIdx.x * RT + threadIdx.x; i < N; i += (size_t)gridDim.x * RT)
+        u[i] = X[i].x;
+}
+
+// Z <- sum_i v_i phi_i over the blocks of colour k (zero elsewhere).  Starts a
+// CG iteration: a zero residual (rr == 0) ends the iteration loop.
+__global__ void __launch_bounds__(RT) scatter_kernel(const float* __restrict__ v,
+                                                     float2* __restrict__ Z, int H, int W, int b,
+                                                     int ncol, int k, const double* rr, int* stop) {
+    if (*stop) return;
+    if (*rr == 0.0) {
+        *stop = 1;
+        return;
+    }
+    const int nbj = (W + b - 1) / b;
+    const size_t N = (size_t)H * W;
+    for (size_t i = (size_t)blockIdx.x * RT + threadIdx.x; i < N; i += (size_t)gridDim.x * RT) {
+        const int r = (int)(i / W), c = (int)(i - (size_t)r * W);
+        const int bi = r / b, bj = c / b;
+        Z[i] = block_colour(bi, bj, ncol) == k ? make_float2(v[slot_of(bi, bj, nbj, ncol)], 0.0f)
+                                               : make_float2(0.0f, 0.0f);
+    }
+}
+
+// Z <- M Z s2 (s2 = 1 / HW: both normalisations of A^H A).
+__global__ void __launch_bounds__(RT) mask_scale_kernel(float2* __restrict__ Z,
+                                                        const uint8_t* __restrict__ mask, size_t N,
+                                                        float s2, const int* stop) {
+    if (*stop) return;
+    for (size_t i = (size_t)blockIdx.x * RT + threadIdx.x; i < N; i += (size_t)gridDim.x * RT) {
+        const float2 z = Z[i];
+        Z[i] = mask[i] ? make_float2(z.x * s2, z.y * s2) : make_float2(0.0f, 0.0f);
+    }
+}
+
+enum { GATHER_RHS = 0, GATHER_Q = 1 };
+
+// Block sums of Re(Y) over the blocks of colour k, GS threads per block.
+//  GATHER_RHS: r_a = sum + 2 alpha d_a (d_a = c_{1/2}(u) when b = 1), p_a = r_a,
+//              c_a = 0; *dot = r.r.
+//  GATHER_Q:   q_a = sum + 2 alpha p_a; *dot = p.q.
+template <int GS, int MODE, int KIND>
+__global__ void __launch_bounds__(RT) gather_kernel(const float2* __restrict__ Y,
+                                                    const float* __restrict__ u, int H, int W,
+                                                    int b, int ncol, int k, int nslots,
+                                                    float twoalpha, float* __restrict__ out,
+                                                    float* __restrict__ p, float* __restrict__ c,
+                                                    const int* stop, double* partials,
+                                                    unsigned* ticket, double* dot) {
+    if (MODE == GATHER_Q && *stop) return;
+    constexpr int GPC = RT / GS;
+    __shared__ double gs[RT / 32];
+    const int g = threadIdx.x / GS, lane = threadIdx.x % GS;
+    const int a = blockIdx.x * GPC + g;
+    const int nbi = (H + b - 1) / b, nbj = (W + b - 1) / b;
+    int bi = 0, bj = 0;
+    const bool on = a < nslots && active_block(a, nbi, nbj, ncol, k, bi, bj);
+    double s = 0.0;
+    if (on) {
+        const int r0 = bi * b, c0 = bj * b;
+        const int bh = min(b, H - r0), bw = min(b, W - c0);
+        for (int i = lane; i < bh * bw; i += GS) {
+            const int rr = i / bw, cc = i - rr * bw;
+            s += (double)Y[(size_t)(r0 + rr) * W + (c0 + cc)].x;
+        }
+    }
+    if (GS > 1) {
+#pragma unroll
+        for (int off = (GS < 32 ? GS : 32) / 2; off > 0; off >>= 1)
+            s += __shfl_xor_sync(0xffffffffu, s, off);
+    }
+    if (GS > 32) {   // one group per CTA: add the warps
+        if ((threadIdx.x & 31) == 0) gs[threadIdx.x >> 5] = s;
+        __syncthreads();
+        s = 0.0;
+        for (int i = 0; i < RT / 32; ++i) s += gs[i];
+    }
+    double contrib = 0.0;
+    if (lane == 0 && a < nslots) {
+        if (MODE == GATHER_RHS) {
+            float d = 0.0f;
+            if (on && b == 1) {
+                float w[9];
+#pragma unroll
+                for (int i = 0; i < 3; ++i)
+#pragma unroll
+                    for (int j = 0; j < 3; ++j)
+                        w[3 * i + j] = u[(size_t)clampi(bi + i - 1, 0, H - 1) * W +
+                                         clampi(bj + j - 1, 0, W - 1)];
+                d = paper_chalf<KIND>(w);
+            }
+            const float v = on ? fmaf(twoalpha, d, (float)s) : 0.0f;
+            out[a] = v;
+            p[a] = v;
+            c[a] = 0.0f;
+            contrib = (double)v * v;
+        } else {
+            const float pa = p[a];
+            const float v = on ? fmaf(twoalpha, pa, (float)s) : 0.0f;
+            out[a] = v;
+            contrib = (double)pa * v;
+        }
+    }
+    cta_sum_finish(contrib, partials, ticket, dot);
+}
+
+// c += a p, r -= a q with a = rr / pq; *rr_next = r.r.  A non-positive p.q
+// (a singular system) ends the iteration loop.
+__global__ void __launch_bounds__(RT) cg_update_kernel(float* __restrict__ c,
+                                                       float* __restrict__ r,
+                                                       const float* __restrict__ p,
+                                                       const float* __restrict__ q, int n,
+                                                       const double* rr, const double* pq,
+                                                       int* stop, double* partials,
+                                                       unsigned* ticket, double* rr_next) {
+    if (*stop) return;
+    const double pqv = *pq;
+    if (!(pqv > 0.0)) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) *stop = 1;
+        return;
+    }
+    const float al = (float)(*rr / pqv);
+    double acc = 0.0;
+    for (int i = blockIdx.x * RT + threadIdx.x; i < n; i += gridDim.x * RT) {
+        c[i] = fmaf(al, p[i], c[i]);
+        const float ri = fmaf(-al, q[i], r[i]);
+        r[i] = ri;
+        acc += (double)ri * ri;
+    }
+    cta_sum_finish(acc, partials, ticket, rr_next);
+}
+
+// p <- r + (rr_next / rr) p.
+__global__ void __launch_bounds__(RT) cg_dir_kernel(float* __restrict__ p,
+                                                    const float* __restrict__ r, int n,
+                                                    const double* rr, const double* rr_next,
+                                                    const int* stop) {
+    if (*stop) return;
+    const float beta = (float)(*rr_next / *rr);
+    for (int i = blockIdx.x * RT + threadIdx.x; i < n; i += gridDim.x * RT)
+        p[i] = fmaf(beta, p[i], r[i]);
+}
+
+// u += sum_i c_i phi_i over the blocks of colour k.
+__global__ void __launch_bounds__(RT) apply_blocks_kernel(float* __restrict__ u,
+                                                          const float* __restrict__ c, int H,
+                                                          int W, int b, int ncol, int k) {
+    const int nbj = (W + b - 1) / b;
+    const size_t N = (size_t)H * W;
+    for (size_t i = (size_t)blockIdx.x * RT + threadIdx.x; i < N; i += (size_t)gridDim.x * RT) {
+        const int r = (int)(i / W), cc = (int)(i - (size_t)r * W);
+        const int bi = r / b, bj = cc / b;
+        if (block_colour(bi, bj, ncol) == k) u[i] += c[slot_of(bi, bj, nbj, ncol)];
+    }
+}
+
+// *out = sum |M s X - b|^2 (X = F_unnormalised u): twice the data term.
+__global__ void __launch_bounds__(RT) data_term_kernel(const float2* __restrict__ X,
+                                                       const float2* __restrict__ bk,
+                                                       const uint8_t* __restrict__ mask, size_t N,
+                                                       float s, double* partials,
+                                                       unsigned* ticket, double* out) {
+    double acc = 0.0;
+    for (size_t i = (size_t)blockIdx.x * RT + threadIdx.x; i < N; i += (size_t)gridDim.x * RT) {
+        const float2 y = bk[i];
+        const float2 x = mask[i] ? make_float2(s * X[i].x, s * X[i].y) : make_float2(0.0f, 0.0f);
+        const double dx = (double)x.x - y.x, dy = (double)x.y - y.y;
+        acc += dx * dx + dy * dy;
+    }
+    cta_sum_finish(acc, partials, ticket, out);
+}
+
+// trace[(*count)++] = data2 / 2 + alpha * curv.
+__global__ void objective_kernel(const double* data2, const double* curv, float alpha,
+                                 double* trace, int* count, int cap) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const int l = *count;
+    if (l < cap) trace[l] = 0.5 * *data2 + (double)alpha * *curv;
+    *count = l + 1;
+}
+
+// ---------------------------------------------------------------------------
+// Host side.
+
+struct ReconKey {
+    const void *kspace, *mask, *u;
+    int H, W, kind, levels, sides, ncolors, cg_iters;
+    float alpha;
+    bool operator==(const ReconKey& o) const { return memcmp(this, &o, sizeof(ReconKey)) == 0; }
+};
+
+struct ReconWork {
+    int H = 0, W = 0;
+    cufftHandle plan = 0;
+    bool have_plan = false;
+    float2 *X = nullptr, *Z = nullptr;
+    float *c = nullptr, *r = nullptr, *p = nullptr, *q = nullptr;
+    size_t nslots = 0;
+    double* partials = nullptr;   // MAX_CTAS
+    unsigned* ticket = nullptr;
+    double* scal = nullptr;       // 0, 1: rr (alternating); 2: p.q; 3: data term; 4: curvature
+    int* stop = nullptr;
+    double* epart = nullptr;      // energy kernel partials
+    unsigned* eticket = nullptr;
+    double* trace = nullptr;
+    int* count = nullptr;
+    int trace_cap = 0;
+    cudaStream_t cs = nullptr;    // capture stream
+    cudaGraphExec_t graph = nullptr;
+    ReconKey key{};
+};
+
+ReconWork* recon_work_create() { return new ReconWork(); }
+
+static void free_buffers(ReconWork* w) {
+    cudaFree(w->X);
+    cudaFree(w->Z);
+    cudaFree(w->c);
+    cudaFree(w->r);
+    cudaFree(w->p);
+    cudaFree(w->q);
+    cudaFree(w->partials);
+    cudaFree(w->ticket);
+    cudaFree(w->scal);
+    cudaFree(w->stop);
+    cudaFree(w->epart);
+    cudaFree(w->eticket);
+    w->X = w->Z = nullptr;
+    w->c = w->r = w->p = w->q = nullptr;
+    w->partials = w->scal = w->epart = nullptr;
+    w->ticket = w->eticket = nullptr;
+    w->stop = nullptr;
+    if (w->have_plan) cufft_api().destroy(w->plan);
+    w->have_plan = false;
+    w->H = w->W = 0;
+}
+
+void recon_work_destroy(ReconWork* w) {
+    if (!w) return;
+    free_buffers(w);
+    cudaFree(w->trace);
+    cudaFree(w->count);
+    if (w->graph) cudaGraphExecDestroy(w->graph);
+    if (w->cs) cudaStreamDestroy(w->cs);
+    delete w;
+}
+
+static int grid_for(size_t n) {
+    return (int)std::min<size_t>((n + RT - 1) / RT, RED_CTAS);
+}
+
+// The largest slot count of any level of the cycle.
+static size_t max_slots(const ReconArgs& a) {
+    size_t m = 1;
+    for (int j = 0; j < a.levels; ++j) {
+        const int b = level_side(j, a.sides);
+        const int nbi = (a.H + b - 1) / b, nbj = (a.W + b - 1) / b;
+        m = std::max(m, (size_t)active_slots(nbi, nbj, level_colours(a.ncolors, b)));
+    }
+    return m;
+}
+
+#define RC(x)                                                  \
+    do {                                                       \
+        cudaError_t e_ = (x);                                  \
+        if (e_ != cudaSuccess) {                               \
+            *msg = cudaGetErrorString(e_);                     \
+            return e_ == cudaErrorMemoryAllocation ? 3 : 2;    \
+        }                                                      \
+    } while (0)
+
+static int ensure_buffers(ReconWork* w, const ReconArgs& a, const char** msg) {
+    const size_t need = max_slots(a);
+    if (w->H == a.H && w->W == a.W && w->nslots >= need) return 0;
+    free_buffers(w);
+    const size_t N = (size_t)a.H * a.W;
+    RC(cudaMalloc(&w->X, N * sizeof(float2)));
+    RC(cudaMalloc(&w->Z, N * sizeof(float2)));
+    RC(cudaMalloc(&w->c, need * sizeof(float)));
+    RC(cudaMalloc(&w->r, need * sizeof(float)));
+    RC(cudaMalloc(&w->p, need * sizeof(float)));
+    RC(cudaMalloc(&w->q, need * sizeof(float)));
+    RC(cudaMalloc(&w->partials, MAX_CTAS * sizeof(double)));
+    RC(cudaMalloc(&w->ticket, sizeof(unsigned)));
+    RC(cudaMemset(w->ticket, 0, sizeof(unsigned)));
+    RC(cudaMalloc(&w->scal, 8 * sizeof(double)));
+    RC(cudaMemset(w->scal, 0, 8 * sizeof(double)));
+    RC(cudaMalloc(&w->stop, sizeof(int)));
+    RC(cudaMalloc(&w->epart, energy_partials_needed(a.H, a.W) * sizeof(double)));
+    RC(cudaMalloc(&w->eticket, sizeof(unsigned)));
+    RC(cudaMemset(w->eticket, 0, sizeof(unsigned)));
+    w->nslots = need;
+    if (cufft_api().plan2d(&w->plan, a.H, a.W, CUFFT_C2C) != CUFFT_SUCCESS) {
+        *msg = "cufftPlan2d failed";
+        return 2;
+    }
+    w->have_plan = true;
+    w->H = a.H;
+    w->W = a.W;
+    return 0;
+}
+
+static cudaError_t fft(ReconWork* w, float2* X, int dir, cudaStream_t st) {
+    if (cufft_api().set_stream(w->plan, st) != CUFFT_SUCCESS) return cudaErrorUnknown;
+    if (cufft_api().exec(w->plan, X, X, dir) != CUFFT_SUCCESS) return cudaErrorUnknown;
+    return cudaGetLastError();
+}
+
+template <int GS, int MODE>
+static cudaError_t launch_gather(ReconWork* w, const ReconArgs& a, int b, int nc, int k,
+                                 int nslots, float* out, cudaStream_t st) {
+    const int grid = (nslots + RT / GS - 1) / (RT / GS);
+    if (grid > MAX_CTAS) return cudaErrorInvalidValue;
+    auto kern = a.kind == KIND_MEAN         ? gather_kernel<GS, MODE, KIND_MEAN>
+                : a.kind == KIND_GAUSS      ? gather_kernel<GS, MODE, KIND_GAUSS>
+                : a.kind == KIND_MEAN_EULER ? gather_kernel<GS, MODE, KIND_MEAN_EULER>
+                                            : gather_kernel<GS, MODE, KIND_GAUSS_EULER>;
+    const float2* Y = MODE == GATHER_RHS ? w->X : w->Z;
+    kern<<<grid, RT, 0, st>>>(Y, a.u, a.H, a.W, b, nc, k, nslots, 2.0f * a.alpha, out, w->p, w->c,
+                              w->stop, w->partials, w->ticket,
+                              MODE == GATHER_RHS ? w->scal + 0 : w->scal + 2);
+    return cudaGetLastError();
+}
+
+template <int MODE>
+static cudaError_t gather(ReconWork* w, const ReconArgs& a, int b, int nc, int k, int nslots,
+                          float* out, cudaStream_t st) {
+    if (b <= 2) return launch_gather<1, MODE>(w, a, b, nc, k, nslots, out, st);
+    if (b <= 16) return launch_gather<32, MODE>(w, a, b, nc, k, nslots, out, st);
+    return launch_gather<RT, MODE>(w, a, b, nc, k, nslots, out, st);
+}
+
+// J(u) into the trace (on the device).
+static cudaError_t enqueue_objective(ReconWork* w, const ReconArgs& a, cudaStream_t st) {
+    const size_t N = (size_t)a.H * a.W;
+    const float s = 1.0f / sqrtf((float)N);
+    const int gN = grid_for(N);
+    cudaError_t e;
+    to_complex_kernel<<<gN, RT, 0, st>>>(a.u, w->X, N);
+    if ((e = fft(w, w->X, CUFFT_FORWARD, st)) != cudaSuccess) return e;
+    data_term_kernel<<<gN, RT, 0, st>>>(w->X, a.kspace, a.mask, N, s, w->partials, w->ticket,
+                                        w->scal + 3);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    // sum |kappa(u)|: the energy with f = u has no fidelity part
+    if ((e = launch_energy(a.u, a.u, a.H, a.W, 1.0f, a.kind, w->epart, w->eticket, w->scal + 4,
+                           st)) != cudaSuccess)
+        return e;
+    objective_kernel<<<1, 32, 0, st>>>(w->scal + 3, w->scal + 4, a.alpha, w->trace, w->count,
+                                       w->trace_cap);
+    return cudaGetLastError();
+}
+
+// One cycle: every level, every colour: right-hand side, CG, apply.
+static cudaError_t enqueue_cycle(ReconWork* w, const ReconArgs& a, cudaStream_t st) {
+    const size_t N = (size_t)a.H * a.W;
+    const float s = 1.0f / sqrtf((float)N);
+    const float s2 = 1.0f / (float)N;
+    const int gN = grid_for(N);
+    cudaError_t e;
+    for (int j = 0; j < a.levels; ++j) {
+        const int b = level_side(j, a.sides);
+        const int nc = level_colours(a.ncolors, b);
+        const int nbi = (a.H + b - 1) / b, nbj = (a.W + b - 1) / b;
+        const int nslots = active_slots(nbi, nbj, nc);
+        const int gs = grid_for((size_t)nslots);
+        for (int k = 0; k < nc; ++k) {
+            // right-hand side: Re <b - A u, A phi_i> + 2 alpha d_i
+            to_complex_kernel<<<gN, RT, 0, st>>>(a.u, w->X, N);
+            if ((e = fft(w, w->X, CUFFT_FORWARD, st)) != cudaSuccess) return e;
+            resid_kernel<<<gN, RT, 0, st>>>(w->X, a.kspace, a.mask, N, s);
+            if ((e = fft(w, w->X, CUFFT_INVERSE, st)) != cudaSuccess) return e;
+            if ((e = gather<GATHER_RHS>(w, a, b, nc, k, nslots, w->r, st)) != cudaSuccess) return e;
+            if ((e = cudaMemsetAsync(w->stop, 0, sizeof(int), st)) != cudaSuccess) return e;
+            for (int it = 0; it < a.cg_iters; ++it) {
+                double* rr = w->scal + (it & 1);
+                double* rr_next = w->scal + ((it + 1) & 1);
+                scatter_kernel<<<gN, RT, 0, st>>>(w->p, w->Z, a.H, a.W, b, nc, k, rr, w->stop);
+                if ((e = fft(w, w->Z, CUFFT_FORWARD, st)) != cudaSuccess) return e;
+                mask_scale_kernel<<<gN, RT, 0, st>>>(w->Z, a.mask, N, s2, w->stop);
+                if ((e = fft(w, w->Z, CUFFT_INVERSE, st)) != cudaSuccess) return e;
+                if ((e = gather<GATHER_Q>(w, a, b, nc, k, nslots, w->q, st)) != cudaSuccess)
+                    return e;
+                cg_update_kernel<<<gs, RT, 0, st>>>(w->c, w->r, w->p, w->q, nslots, rr,
+                                                    w->scal + 2, w->stop, w->partials, w->ticket,
+                                                    rr_next);
+                cg_dir_kernel<<<gs, RT, 0, st>>>(w->p, w->r, nslots, rr, rr_next, w->stop);
+                if ((e = cudaGetLastError()) != cudaSuccess) return e;
+            }
+            apply_blocks_kernel<<<gN, RT, 0, st>>>(a.u, w->c, a.H, a.W, b, nc, k);
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        }
+    }
+    return enqueue_objective(w, a, st);
+}
+
+int recon_run(ReconWork* w, const ReconArgs& a, cudaStream_t st, const char** msg) {
+    *msg = "";
+    if (!cufft_api().ok) {
+        *msg = "cuFFT (libcufft.so.12) could not be loaded";
+        return 2;
+    }
+    int rc = ensure_buffers(w, a, msg);
+    if (rc) return rc;
+    if (w->trace_cap < a.cycles + 1) {
+        cudaFree(w->trace);
+        w->trace = nullptr;
+        RC(cudaMalloc(&w->trace, (size_t)(a.cycles + 1) * sizeof(double)));
+        w->trace_cap = a.cycles + 1;
+    }
+    if (!w->count) RC(cudaMalloc(&w->count, sizeof(int)));
+    if (!w->cs) RC(cudaStreamCreateWithFlags(&w->cs, cudaStreamNonBlocking));
+    const size_t N = (size_t)a.H * a.W;
+    const float s = 1.0f / sqrtf((float)N);
+    RC(cudaMemsetAsync(w->count, 0, sizeof(int), st));
+    if (a.u0) {
+        if (a.u0 != a.u)
+            RC(cudaMemcpyAsync(a.u, a.u0, N * sizeof(float), cudaMemcpyDeviceToDevice, st));
+    } else {   // zero-filled start Re(A^H b)
+        masked_data_kernel<<<grid_for(N), RT, 0, st>>>(w->X, a.kspace, a.mask, N, s);
+        RC(fft(w, w->X, CUFFT_INVERSE, st));
+        real_part_kernel<<<grid_for(N), RT, 0, st>>>(w->X, a.u, N);
+        RC(cudaGetLastError());
+    }
+    RC(enqueue_objective(w, a, st));
+    // one cycle as a graph, captured once per problem and reused
+    ReconKey key{a.kspace, a.mask, a.u, a.H, a.W, a.kind, a.levels, a.sides, a.ncolors,
+                 a.cg_iters, a.alpha};
+    if (a.cycles > 0 && !(w->graph && w->key == key)) {
+        if (w->graph) cudaGraphExecDestroy(w->graph);
+        w->graph = nullptr;
+        RC(cudaStreamBeginCapture(w->cs, cudaStreamCaptureModeThreadLocal));
+        cudaError_t ce = enqueue_cycle(w, a, w->cs);
+        cudaGraph_t g = nullptr;
+        cudaError_t ee = cudaStreamEndCapture(w->cs, &g);
+        if (ce != cudaSuccess || ee != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            *msg = cudaGetErrorString(ce != cudaSuccess ? ce : ee);
+            return 2;
+        }
+        cudaError_t ie = cudaGraphInstantiate(&w->graph, g, 0);
+        cudaGraphDestroy(g);
+        if (ie != cudaSuccess) {
+            w->graph = nullptr;
+            *msg = cudaGetErrorString(ie);
+            return 2;
+        }
+        w->key = key;
+    }
+    for (int l = 0; l < a.cycles; ++l) RC(cudaGraphLaunch(w->graph, st));
+    if (a.trace_host)
+        RC(cudaMemcpyAsync(a.trace_host, w->trace, (size_t)(a.cycles + 1) * sizeof(double),
+                           cudaMemcpyDeviceToHost, st));
+    RC(cudaStreamSynchronize(st));
+    return 0;
+}
+
+}  // namespace cm
