@@ -57,6 +57,10 @@ def parse():
                    help="skip the 16-image warm-start evaluation")
     p.add_argument("--no-batched", action="store_true",
                    help="skip the 64-image batched measurement")
+    p.add_argument("--no-recon", action="store_true",
+                   help="skip the reconstruction (Sec. 5) measurement")
+    p.add_argument("--recon-only", action="store_true",
+                   help="only run 2 reconstruction cycles at --side (for profiling)")
     p.add_argument("--cnn-only", action="store_true",
                    help="profiling aid: warm-start inference on 16 x 1024^2 images and exit")
     p.add_argument("--phases-only", action="store_true",
@@ -273,6 +277,45 @@ def batched_measurement(cm, torch, synth, ctx, dev, rank=0, world=1):
     return res
 
 
+def recon_measurement(cm, torch, synth, ctx, dev, stream, with_oracle=True):
+    """Reconstruction extension (Sec. 5, A = M F): MRI-like cases (phantom of
+    12 shapes, Cartesian rows at 1/3 sampling with the central 8% kept,
+    complex noise sigma 0.01), alpha 0.02, mean curvature, every level, four
+    colours, 8 CG iterations per colour.  Device time per cycle (CUDA events,
+    the captured cycle already built), PSNR of the zero-filled start and
+    after 5 cycles; the FP64 oracle's time for one cycle at 512^2 beside it."""
+    import time
+    import numpy as np
+    res = {"alpha": 0.02, "kind": "mean", "cg_iters": 8, "accel": 3.0, "sigma": 0.01}
+    for side in (512, 1024):
+        case = synth.mri_case(side, side, synth.workload_seed(6, side), accel=3.0, sigma=0.01)
+        kd = torch.from_numpy(case.kspace).to(dev)
+        md = torch.from_numpy(case.mask).to(dev)
+        u0, tr0 = cm.cm_recon(kd, md, 0.02, cm.MEAN, cycles=0, ctx=ctx)
+        psnr0 = synth.psnr(u0.cpu().numpy(), case.clean)
+        cm.cm_recon(kd, md, 0.02, cm.MEAN, cycles=1, ctx=ctx)      # builds the cycle graph
+        torch.cuda.synchronize()
+        n = 5
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        u, tr = cm.cm_recon(kd, md, 0.02, cm.MEAN, cycles=n, ctx=ctx)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        res[f"{side}x{side}"] = {
+            "s_per_cycle": e0.elapsed_time(e1) / 1e3 / n, "cycles": n,
+            "psnr_zero_filled_db": psnr0, "psnr_db": synth.psnr(u.cpu().numpy(), case.clean),
+            "objective_trace": [float(x) for x in tr], "sampled_fraction": float(case.mask.mean())}
+    if with_oracle:
+        import oracle
+        from oracle import recon as orc
+        case = synth.mri_case(512, 512, synth.workload_seed(6, 512), accel=3.0, sigma=0.01)
+        t = time.perf_counter()
+        orc.solve(case.kspace, case.mask, 0.02, cm.MEAN, cycles=1, cg_iters=8)
+        res["oracle_512_s_per_cycle"] = time.perf_counter() - t
+        res["oracle_threads"] = oracle.num_threads()
+    return res
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -292,6 +335,15 @@ def main():
         dist.init_process_group("nccl", device_id=dev)
     cm.load()
     ctx = cm.Context(local)
+    if args.recon_only:
+        case = synth.mri_case(args.side, args.side, synth.workload_seed(6, args.side),
+                              accel=3.0, sigma=0.01)
+        kd = torch.from_numpy(case.kspace).to(dev)
+        md = torch.from_numpy(case.mask).to(dev)
+        u, tr = cm.cm_recon(kd, md, 0.02, cm.MEAN, cycles=2, ctx=ctx)
+        torch.cuda.synchronize()
+        print(json.dumps({"recon_only": True, "side": args.side, "trace": list(tr)}))
+        return
     img = synth.large(args.side)
     f_host = torch.from_numpy(img.f).pin_memory()
     f = f_host.to(dev)
@@ -574,6 +626,10 @@ def main():
     batched_res = None
     if not args.no_batched:
         batched_res = batched_measurement(cm, torch, synth, ctx, dev, rank, world)
+    recon_res = None
+    if not args.no_recon and rank == 0:
+        recon_res = recon_measurement(cm, torch, synth, ctx, dev, stream,
+                                      with_oracle=not args.no_cpu_baseline)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -620,6 +676,7 @@ def main():
             "gpu_launches": int(sum(launches_per_solve)),
             "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks,
             "b1_phase_ms": b1_ms, "batched": batched_res, "one_step": one_step_res,
+            "reconstruction": recon_res,
             "cycle_variants": variants, "curvature_kinds": kinds_res}
     line["config"]["levels"] = L
     line["config"]["grid_points"] = opts.grid_points

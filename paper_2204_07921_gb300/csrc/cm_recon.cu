@@ -331,9 +331,12 @@ __global__ void objective_kernel(const double* data2, const double* curv, float 
 // ---------------------------------------------------------------------------
 // Host side.
 
+// Everything the captured cycle bakes in: the problem, and every buffer it
+// reads or writes (the trace buffer included: it is reallocated when a call
+// asks for more cycles).
 struct ReconKey {
-    const void *kspace, *mask, *u;
-    int H, W, kind, levels, sides, ncolors, cg_iters;
+    const void *kspace, *mask, *u, *trace;
+    int H, W, kind, levels, sides, ncolors, cg_iters, trace_cap;
     float alpha;
     bool operator==(const ReconKey& o) const { return memcmp(this, &o, sizeof(ReconKey)) == 0; }
 };
@@ -421,6 +424,8 @@ static size_t max_slots(const ReconArgs& a) {
 static int ensure_buffers(ReconWork* w, const ReconArgs& a, const char** msg) {
     const size_t need = max_slots(a);
     if (w->H == a.H && w->W == a.W && w->nslots >= need) return 0;
+    if (w->graph) cudaGraphExecDestroy(w->graph);   // it points at the old buffers
+    w->graph = nullptr;
     free_buffers(w);
     const size_t N = (size_t)a.H * a.W;
     RC(cudaMalloc(&w->X, N * sizeof(float2)));
@@ -551,6 +556,8 @@ int recon_run(ReconWork* w, const ReconArgs& a, cudaStream_t st, const char** ms
     int rc = ensure_buffers(w, a, msg);
     if (rc) return rc;
     if (w->trace_cap < a.cycles + 1) {
+        if (w->graph) cudaGraphExecDestroy(w->graph);   // it points at the old trace
+        w->graph = nullptr;
         cudaFree(w->trace);
         w->trace = nullptr;
         RC(cudaMalloc(&w->trace, (size_t)(a.cycles + 1) * sizeof(double)));
@@ -572,8 +579,21 @@ int recon_run(ReconWork* w, const ReconArgs& a, cudaStream_t st, const char** ms
     }
     RC(enqueue_objective(w, a, st));
     // one cycle as a graph, captured once per problem and reused
-    ReconKey key{a.kspace, a.mask, a.u, a.H, a.W, a.kind, a.levels, a.sides, a.ncolors,
-                 a.cg_iters, a.alpha};
+    ReconKey key;
+    memset(&key, 0, sizeof key);   // padding included: the key is compared bytewise
+    key.kspace = a.kspace;
+    key.mask = a.mask;
+    key.u = a.u;
+    key.trace = w->trace;
+    key.H = a.H;
+    key.W = a.W;
+    key.kind = a.kind;
+    key.levels = a.levels;
+    key.sides = a.sides;
+    key.ncolors = a.ncolors;
+    key.cg_iters = a.cg_iters;
+    key.trace_cap = w->trace_cap;
+    key.alpha = a.alpha;
     if (a.cycles > 0 && !(w->graph && w->key == key)) {
         if (w->graph) cudaGraphExecDestroy(w->graph);
         w->graph = nullptr;

@@ -108,3 +108,18 @@ def test_recon_invalid_arguments():
         with pytest.raises(cm.CMError) as e:
             cm.cm_recon(kd, md, args["alpha"], args["kind"], cg_iters=args["cg_iters"])
         assert e.value.code == cm.CM_ERR_INVALID
+
+
+def test_more_cycles_on_the_same_context():
+    """A call asking for more cycles than the last one grows the trace buffer;
+    the captured cycle must follow it: the trace equals a fresh context's."""
+    case = synth.mri_case(48, 40, 11, accel=3.0, sigma=0.01)
+    kd, md = dev_case(case)
+    ctx = cm.Context(0)
+    cm.cm_recon(kd, md, 0.02, cm.MEAN, cycles=1, ctx=ctx)
+    u1, t1 = cm.cm_recon(kd, md, 0.02, cm.MEAN, cycles=4, ctx=ctx)
+    u1 = u1.clone()
+    u2, t2 = cm.cm_recon(kd, md, 0.02, cm.MEAN, cycles=4, ctx=cm.Context(0))
+    torch.cuda.synchronize()
+    assert np.all(np.isfinite(t1)) and np.all(t1 > 0)
+    assert np.array_equal(t1, t2) and torch.equal(u1, u2)
