@@ -1,7 +1,7 @@
 """Train the warm-start CNN on the GPU and save its parameters.
 
     python -m paper_2204_07921_gb300.train_warmstart [--kind mean|gauss] [--alpha A]
-        [--pairs 4096] [--side 256] [--steps 3000] [--batch 16] [--lr 2e-3] [--out PATH]
+        [--pairs 8192] [--side 256] [--steps 12000] [--batch 16] [--lr 2e-3] [--out PATH]
 
 Training pairs: seeded synthetic 256 x 256 images (20 shapes, sigma ~
 U(0.03, 0.12)) and the plain method's result u* at relative-energy tolerance
@@ -31,9 +31,9 @@ def default_path(kind: str, alpha: float) -> str:
 
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("--pairs", type=int, default=4096)
+    ap.add_argument("--pairs", type=int, default=8192)
     ap.add_argument("--side", type=int, default=256)
-    ap.add_argument("--steps", type=int, default=3000)
+    ap.add_argument("--steps", type=int, default=12000)
     ap.add_argument("--batch", type=int, default=16)
     ap.add_argument("--lr", type=float, default=2e-3)
     ap.add_argument("--lr-final", type=float, default=1e-4)
