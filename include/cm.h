@@ -320,6 +320,19 @@ int cm_recon(cm_ctx* ctx, const float* kspace, const unsigned char* mask, int H,
  * for null pointers or a negative device, CM_ERR_OOM, or CM_ERR_CUDA. */
 int cm_probe_alu(int device, double* fma_per_s, double* rsqrt_per_s, void* stream);
 
+/* Failure detection.  Every wait of the library's kernels on an mbarrier (the
+ * tensor-core convolution's pipeline) gives up after a bounded number of
+ * tries, sets an error status and returns; the entry points that synchronise
+ * report it as CM_ERR_TIMEOUT, and the context stays usable.  This self-test
+ * runs that wait in one CTA on phase 0 of a fresh mbarrier (arrival count 1)
+ * that nothing completes, with `limit` tries (1 .. 2^22): *timed_out = 1 when
+ * the wait gave up; it then arrives once and waits again: *completed = 1 when
+ * that wait saw the phase complete.  Host pointers; synchronises the device.
+ * Out-of-memory is injected on the host: with CM_FAULT_ALLOC_LIMIT=<bytes> in
+ * the environment, a context's scratch allocations larger than that fail as
+ * CM_ERR_OOM. */
+int cm_selftest_wait(int device, int limit, int* timed_out, int* completed);
+
 #ifdef __cplusplus
 }
 #endif

@@ -72,6 +72,7 @@ SIGNATURES = {
     "cm_phase": (_I, [_P, _P, _P, _P, _I, _I, _F, _I, _I, _I, ctypes.POINTER(Options), _P, _P]),
     "cm_energy_noalloc": (_I, [_P, _P, _I, _I, _F, _I, _P, _P]),
     "cm_probe_alu": (_I, [_I, _P, _P, _P]),
+    "cm_selftest_wait": (_I, [_I, _I, _P, _P]),
     "cm_recon": (_I, [_P, _P, _P, _I, _I, _F, _I, _I, _I, _I, _P, _P, ctypes.POINTER(Options),
                       _P, _P]),
     "cm_level": (_I, [_P, _P, _P, _P, _I, _I, _F, _I, _I, ctypes.POINTER(Options), _P, _P]),
@@ -189,6 +190,16 @@ def cm_energy(u, f, alpha: float, kind: int, ctx: Context | None = None, stream=
     c._check(load().cm_energy(c.handle, u.data_ptr(), f.data_ptr(), H, W, float(alpha), kind,
                               ctypes.byref(E), _stream_ptr(stream)))
     return E.value
+
+
+def cm_selftest_wait(device: int = 0, limit: int = 1024) -> dict:
+    """Bounded-wait self-test: a wait that nothing completes must time out,
+    and the same wait after one arrival must complete."""
+    t, c = ctypes.c_int(-1), ctypes.c_int(-1)
+    rc = load().cm_selftest_wait(device, limit, ctypes.byref(t), ctypes.byref(c))
+    if rc != CM_OK:
+        raise CMError(rc, "cm_selftest_wait failed")
+    return {"timed_out": t.value, "completed": c.value}
 
 
 def cm_probe_alu(device: int = 0, stream=None) -> dict:

@@ -9,6 +9,7 @@
 // the solve's state back once, after the loop.
 #include <cuda_runtime.h>
 #include <math.h>
+#include <stdlib.h>
 #include <stdio.h>
 #include <string.h>
 
@@ -78,6 +79,24 @@ int fail(cm_ctx* ctx, int code, const std::string& msg) {
     return code;
 }
 
+// Host-side fault injection for the tests: with CM_FAULT_ALLOC_LIMIT=<bytes>
+// in the environment (read once per process), every scratch allocation of a
+// context larger than that fails as cudaErrorMemoryAllocation, so the
+// out-of-memory path runs without exhausting the GPU.
+size_t fault_alloc_limit() {
+    static const size_t lim = [] {
+        const char* v = getenv("CM_FAULT_ALLOC_LIMIT");
+        return v ? (size_t)strtoull(v, nullptr, 10) : ~(size_t)0;
+    }();
+    return lim;
+}
+
+template <class T>
+cudaError_t dev_alloc(T** p, size_t bytes) {
+    if (bytes > fault_alloc_limit()) return cudaErrorMemoryAllocation;
+    return cudaMalloc((void**)p, bytes);
+}
+
 int cuda_fail(cm_ctx* ctx, cudaError_t e, const char* where) {
     std::string m = std::string(where) + ": " + cudaGetErrorString(e);
     return fail(ctx, e == cudaErrorMemoryAllocation ? CM_ERR_OOM : CM_ERR_CUDA, m);
@@ -103,7 +122,7 @@ int ensure_partials(cm_ctx* ctx, int H, int W) {
     if (ctx->partials) cudaFree(ctx->partials);
     ctx->partials = nullptr;
     ctx->partials_cap = 0;
-    CM_CUDA(cudaMalloc(&ctx->partials, need * sizeof(double)));
+    CM_CUDA(dev_alloc(&ctx->partials, need * sizeof(double)));
     ctx->partials_cap = need;
     return CM_OK;
 }
@@ -117,8 +136,8 @@ int ensure_coarse(cm_ctx* ctx, int H, int W) {
     ctx->tsums = nullptr;
     ctx->cj = nullptr;
     ctx->tsums_cap = ctx->cj_cap = 0;
-    CM_CUDA(cudaMalloc(&ctx->tsums, nt * sizeof(float)));
-    CM_CUDA(cudaMalloc(&ctx->cj, nc * sizeof(float)));
+    CM_CUDA(dev_alloc(&ctx->tsums, nt * sizeof(float)));
+    CM_CUDA(dev_alloc(&ctx->cj, nc * sizeof(float)));
     ctx->tsums_cap = nt;
     ctx->cj_cap = nc;
     return CM_OK;
@@ -130,7 +149,7 @@ int ensure_ubuf(cm_ctx* ctx, size_t n) {
     if (ctx->ubuf) cudaFree(ctx->ubuf);
     ctx->ubuf = nullptr;
     ctx->ubuf_cap = 0;
-    CM_CUDA(cudaMalloc(&ctx->ubuf, n * sizeof(float)));
+    CM_CUDA(dev_alloc(&ctx->ubuf, n * sizeof(float)));
     ctx->ubuf_cap = n;
     return CM_OK;
 }
@@ -139,9 +158,9 @@ constexpr int TRACE_SLOTS = 4097;   // energy_trace of cm_stats
 
 int ensure_solve_state(cm_ctx* ctx) {
     if (ctx->sstate) return CM_OK;
-    CM_CUDA(cudaMalloc(&ctx->sstate, cm::batch_state_bytes()));
+    CM_CUDA(dev_alloc(&ctx->sstate, cm::batch_state_bytes()));
     CM_CUDA(cudaMallocHost(&ctx->sstate_host, cm::batch_state_bytes()));
-    CM_CUDA(cudaMalloc(&ctx->strace, TRACE_SLOTS * sizeof(double)));
+    CM_CUDA(dev_alloc(&ctx->strace, TRACE_SLOTS * sizeof(double)));
     CM_CUDA(cudaMallocHost(&ctx->strace_host, TRACE_SLOTS * sizeof(double)));
     return CM_OK;
 }
@@ -385,9 +404,9 @@ int cm_create(cm_ctx** out, int device) {
     if (cudaSetDevice(device) != cudaSuccess) return CM_ERR_CUDA;
     cm_ctx* ctx = new cm_ctx();
     ctx->device = device;
-    cudaError_t e = cudaMalloc(&ctx->ticket, sizeof(unsigned int));
+    cudaError_t e = dev_alloc(&ctx->ticket, sizeof(unsigned int));
     if (e == cudaSuccess) e = cudaMemset(ctx->ticket, 0, sizeof(unsigned int));
-    if (e == cudaSuccess) e = cudaMalloc(&ctx->E_dev, 8 * sizeof(double));
+    if (e == cudaSuccess) e = dev_alloc(&ctx->E_dev, 8 * sizeof(double));
     if (e == cudaSuccess) e = cudaMallocHost(&ctx->E_pinned, 8 * sizeof(double));
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->cap_stream2, cudaStreamNonBlocking);
@@ -748,7 +767,7 @@ int cm_solve_batched(cm_ctx* ctx, int n, const float* const* f, const int* H, co
         if (ctx->arena) cudaFree(ctx->arena);
         ctx->arena = nullptr;
         ctx->arena_cap = 0;
-        CM_CUDA(cudaMalloc(&ctx->arena, off));
+        CM_CUDA(dev_alloc(&ctx->arena, off));
         ctx->arena_cap = off;
     }
     unsigned char* A = ctx->arena;

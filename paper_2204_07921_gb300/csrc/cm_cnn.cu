@@ -653,8 +653,11 @@ __device__ __forceinline__ void tc_mma(unsigned tmem, uint64_t a, uint64_t b, un
         "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
 }
 
-__device__ __forceinline__ bool mbar_wait_bounded(unsigned mbar, unsigned parity) {
-    for (int it = 0; it < (1 << 22); ++it) {
+// Wait for phase `parity` of an mbarrier, giving up after `limit` tries
+// (false: timed out; the caller sets its error status and returns).
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned mbar, unsigned parity,
+                                                  int limit = 1 << 22) {
+    for (int it = 0; it < limit; ++it) {
         unsigned done;
         asm volatile(
             "{\n.reg .pred q;\nmbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2;\n"
@@ -665,6 +668,24 @@ __device__ __forceinline__ bool mbar_wait_bounded(unsigned mbar, unsigned parity
         if (done) return true;
     }
     return false;
+}
+
+// Failure-detection self-test of the bounded wait: phase 0 of a fresh
+// mbarrier (arrival count 1) that nothing arrives on must time out; after
+// one arrival the same wait must see the phase complete.  out[0] = 1 on the
+// timeout, out[1] = 1 on the completion.
+__global__ void wait_selftest_kernel(int limit, int* out) {
+    __shared__ alignas(8) unsigned long long bar;
+    const unsigned mbar = (unsigned)__cvta_generic_to_shared(&bar);
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbar));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    out[0] = mbar_wait_bounded(mbar, 0u, limit) ? 0 : 1;
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(mbar) : "memory");
+    out[1] = mbar_wait_bounded(mbar, 0u, limit) ? 1 : 0;
 }
 
 __device__ __forceinline__ void tmem_ld32(unsigned taddr, unsigned (&r)[32]) {
@@ -1107,13 +1128,13 @@ int net_forward_own(Net* net, const float* f, int N, int H, int W, cudaStream_t 
 
 const char* net_error(const Net* net) { return net->err.c_str(); }
 
-// After a synchronisation: CM_ERR_CUDA if a tensor-core wait timed out.
+// After a synchronisation: CM_ERR_TIMEOUT if a tensor-core wait timed out.
 int net_status(Net* net) {
     int h = 0;
     NET_CUDA(cudaMemcpy(&h, net->status, sizeof(int), cudaMemcpyDeviceToHost));
     if (h) {
         net->err = "tensor-core convolution: a wait for the MMAs timed out";
-        return CM_ERR_CUDA;
+        return CM_ERR_TIMEOUT;
     }
     return CM_OK;
 }
@@ -1268,3 +1289,23 @@ int cm_net_train_step(cm_net* net, const float* f, const float* ustar, int N, in
 }
 
 }  // extern "C"
+
+extern "C" int cm_selftest_wait(int device, int limit, int* timed_out, int* completed) {
+    if (!timed_out || !completed || device < 0 || limit < 1 || limit > (1 << 22))
+        return CM_ERR_INVALID;
+    if (cudaSetDevice(device) != cudaSuccess) return CM_ERR_CUDA;
+    int* d = nullptr;
+    if (cudaMalloc(&d, 2 * sizeof(int)) != cudaSuccess) return CM_ERR_OOM;
+    int h[2] = {-1, -1};
+    cudaError_t e = cudaMemset(d, 0xff, 2 * sizeof(int));
+    if (e == cudaSuccess) {
+        cm::cnn::wait_selftest_kernel<<<1, 32>>>(limit, d);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(h, d, 2 * sizeof(int), cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    if (e != cudaSuccess) return CM_ERR_CUDA;
+    *timed_out = h[0];
+    *completed = h[1];
+    return CM_OK;
+}
