@@ -248,6 +248,51 @@ int cm_net_gradients(cm_net* net, const float* f, const float* ustar, int N, int
  * the loss before the step (synchronising `stream`). */
 int cm_net_train_step(cm_net* net, const float* f, const float* ustar, int N, int H, int W,
                       float lr, double* loss_host, void* stream);
+/* Checkpoint of a network: the FP32 parameters, the Adam moments and the
+ * Adam step count, so that training resumes exactly.  File layout
+ * (little-endian): "CMNETCK1", uint32 version 1, uint32 parameter count
+ * (37601), uint64 step; float params[n], m[n], v[n]; uint32 CRC-32 (IEEE
+ * 802.3) of all preceding bytes.  cm_net_load rejects a file of another
+ * size, header or checksum with CM_ERR_INVALID (the network is unchanged);
+ * an unopenable path is CM_ERR_INVALID too (message in cm_net_last_error).
+ * Both synchronise the device. */
+int cm_net_save(cm_net* net, const char* path);
+int cm_net_load(cm_net* net, const char* path);
+
+/* Training loop (mean((u0 - u*)^2), Adam as in cm_net_train_step). */
+typedef struct {
+    int steps;          /* Adam steps of this call (>= 1) */
+    int batch;          /* pairs per step, 1 .. N, drawn without replacement */
+    float lr;           /* learning rate at schedule step 0 (> 0) ... */
+    float lr_final;     /* ... decaying by a cosine to this at step total_steps - 1 (> 0) */
+    int total_steps;    /* schedule length; 0: start_step + steps */
+    int start_step;     /* schedule index of this call's first step (resume after a checkpoint) */
+    uint64_t seed;      /* mini-batch sampling */
+    int log_every;      /* record the loss of every log_every-th step of the call (>= 1) */
+} cm_train_opts;
+
+typedef struct {
+    double loss_first;  /* loss of the call's first step, before its update */
+    double loss_last;   /* loss of the call's last step, before its update */
+    int n_logged;       /* entries written */
+    int losses_cap;     /* capacity of the arrays below */
+    double* losses;     /* host, losses_cap entries (nullable when losses_cap = 0) */
+    int* logged_steps;  /* host, nullable: schedule index of each logged loss */
+} cm_train_log;
+
+/* Trains `net` on N device pairs f[i], ustar[i] (each H x W, row-major,
+ * consecutive).  Step t (t = start_step .. start_step + steps - 1) uses the
+ * pairs of a partial Fisher-Yates shuffle of 0 .. N-1 driven by SplitMix64:
+ * the stream's state is its (t + 1)-th output from `seed`, draw j its
+ * (j + 1)-th output from that state, and r = j + draw mod (N - j) is swapped
+ * into place j; the pairs are copied into a scratch batch and one Adam step
+ * runs with lr_t = lr_final + (lr - lr_final)(1 + cos(pi t / max(1, T - 1)))/2,
+ * T = total_steps.  Calls with consecutive step ranges of one schedule, with
+ * a checkpoint in between, give the same parameters as one call.  log
+ * (host, nullable) receives the losses.  Synchronises `stream`. */
+int cm_net_train(cm_ctx* ctx, cm_net* net, const float* f, const float* ustar, int N, int H,
+                 int W, const cm_train_opts* opts, cm_train_log* log, void* stream);
+
 /* u0_out = f + net(f) for N images; with check_energy, an image keeps u0
  * only if F(u0) <= F(f) (energies of Eq. MCM/GCM with alpha and kind), else
  * u0 = f.  used_host (nullable, N ints) receives 1 where u0 was kept. */

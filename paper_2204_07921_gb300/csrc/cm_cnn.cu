@@ -36,6 +36,8 @@
 #include <string>
 #include <vector>
 
+#include <stdint.h>
+
 #include "../../include/cm.h"
 #include "cm_cnn.h"
 
@@ -1286,6 +1288,198 @@ int cm_net_train_step(cm_net* net, const float* f, const float* ustar, int N, in
         if (rc) return rc;
     }
     return CM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Checkpoints: "CMNETCK1", version, parameter count, Adam step (24-byte
+// little-endian header), then the FP32 parameters, the Adam moments m and v,
+// and a CRC-32 (IEEE 802.3, reflected polynomial 0xEDB88320) of everything
+// before it.
+
+static uint32_t ckpt_crc32(uint32_t crc, const unsigned char* p, size_t n) {
+    crc = ~crc;
+    for (size_t i = 0; i < n; ++i) {
+        crc ^= p[i];
+        for (int k = 0; k < 8; ++k) crc = (crc >> 1) ^ (0xEDB88320u & (0u - (crc & 1u)));
+    }
+    return ~crc;
+}
+
+struct CkptHeader {
+    char magic[8];
+    uint32_t version;
+    uint32_t nparams;
+    uint64_t step;
+};
+static_assert(sizeof(CkptHeader) == 24, "checkpoint header layout");
+static const char CKPT_MAGIC[8] = {'C', 'M', 'N', 'E', 'T', 'C', 'K', '1'};
+
+int cm_net_save(cm_net* net, const char* path) {
+    if (!net || !path) return CM_ERR_INVALID;
+    NET_CUDA(cudaSetDevice(net->device));
+    const size_t n = cm::cnn::NPAR;
+    std::vector<unsigned char> buf(sizeof(CkptHeader) + 3 * n * sizeof(float) + 4);
+    CkptHeader h;
+    memcpy(h.magic, CKPT_MAGIC, 8);
+    h.version = 1;
+    h.nparams = (uint32_t)n;
+    h.step = (uint64_t)net->step;
+    memcpy(buf.data(), &h, sizeof h);
+    float* body = (float*)(buf.data() + sizeof h);
+    NET_CUDA(cudaDeviceSynchronize());
+    NET_CUDA(cudaMemcpy(body, net->P, n * sizeof(float), cudaMemcpyDeviceToHost));
+    NET_CUDA(cudaMemcpy(body + n, net->M, n * sizeof(float), cudaMemcpyDeviceToHost));
+    NET_CUDA(cudaMemcpy(body + 2 * n, net->V, n * sizeof(float), cudaMemcpyDeviceToHost));
+    const uint32_t crc = ckpt_crc32(0u, buf.data(), buf.size() - 4);
+    memcpy(buf.data() + buf.size() - 4, &crc, 4);
+    FILE* fp = fopen(path, "wb");
+    if (!fp) {
+        net->err = std::string("cm_net_save: cannot open ") + path;
+        return CM_ERR_INVALID;
+    }
+    const size_t wrote = fwrite(buf.data(), 1, buf.size(), fp);
+    const int closed = fclose(fp);
+    if (wrote != buf.size() || closed != 0) {
+        net->err = std::string("cm_net_save: short write to ") + path;
+        return CM_ERR_INVALID;
+    }
+    return CM_OK;
+}
+
+int cm_net_load(cm_net* net, const char* path) {
+    if (!net || !path) return CM_ERR_INVALID;
+    const size_t n = cm::cnn::NPAR;
+    const size_t want = sizeof(CkptHeader) + 3 * n * sizeof(float) + 4;
+    FILE* fp = fopen(path, "rb");
+    if (!fp) {
+        net->err = std::string("cm_net_load: cannot open ") + path;
+        return CM_ERR_INVALID;
+    }
+    std::vector<unsigned char> buf(want + 1);
+    const size_t got = fread(buf.data(), 1, buf.size(), fp);
+    fclose(fp);
+    CkptHeader h;
+    if (got != want) {
+        net->err = "cm_net_load: not a checkpoint of this network (size)";
+        return CM_ERR_INVALID;
+    }
+    memcpy(&h, buf.data(), sizeof h);
+    uint32_t crc = 0;
+    memcpy(&crc, buf.data() + want - 4, 4);
+    if (memcmp(h.magic, CKPT_MAGIC, 8) != 0 || h.version != 1 || h.nparams != (uint32_t)n) {
+        net->err = "cm_net_load: not a checkpoint of this network (header)";
+        return CM_ERR_INVALID;
+    }
+    if (ckpt_crc32(0u, buf.data(), want - 4) != crc) {
+        net->err = "cm_net_load: checksum mismatch";
+        return CM_ERR_INVALID;
+    }
+    const float* body = (const float*)(buf.data() + sizeof h);
+    NET_CUDA(cudaSetDevice(net->device));
+    NET_CUDA(cudaMemcpy(net->P, body, n * sizeof(float), cudaMemcpyHostToDevice));
+    NET_CUDA(cudaMemcpy(net->M, body + n, n * sizeof(float), cudaMemcpyHostToDevice));
+    NET_CUDA(cudaMemcpy(net->V, body + 2 * n, n * sizeof(float), cudaMemcpyHostToDevice));
+    net->step = (int)h.step;
+    int rc = cm::cnn::pack(net, 0);
+    if (rc) return rc;
+    NET_CUDA(cudaDeviceSynchronize());
+    return CM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Training loop.  Mini-batch of global step t: `batch` distinct pair indices
+// from a partial Fisher-Yates shuffle of 0 .. N-1 driven by SplitMix64
+// (Steele, Lea and Flood, OOPSLA 2014): the stream's state for step t is its
+// (t + 1)-th output from `seed`, and draw j is the (j + 1)-th output from that
+// state; r = j + draw mod (N - j) is swapped into place j.
+
+static uint64_t sm64_mix(uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+static void batch_indices(uint64_t seed, long long t, int N, int batch, std::vector<int>& perm,
+                          std::vector<int>& idx) {
+    const uint64_t gamma = 0x9E3779B97F4A7C15ull;
+    const uint64_t state = sm64_mix(seed + gamma * (uint64_t)(t + 1));
+    for (int i = 0; i < N; ++i) perm[i] = i;
+    for (int j = 0; j < batch; ++j) {
+        const uint64_t x = sm64_mix(state + gamma * (uint64_t)(j + 1));
+        const int r = j + (int)(x % (uint64_t)(N - j));
+        std::swap(perm[j], perm[r]);
+        idx[j] = perm[j];
+    }
+}
+
+int cm_net_train(cm_ctx* ctx, cm_net* net, const float* f, const float* ustar, int N, int H,
+                 int W, const cm_train_opts* o, cm_train_log* log, void* stream) {
+    if (!ctx || !net || !f || !ustar || !o || N < 1 || H < 1 || W < 1 || o->steps < 1 ||
+        o->batch < 1 || o->batch > N || !(o->lr > 0.0f) || !(o->lr_final > 0.0f) ||
+        o->start_step < 0 || o->log_every < 1 || o->total_steps < 0 ||
+        (o->total_steps > 0 && o->start_step + o->steps > o->total_steps))
+        return CM_ERR_INVALID;
+    if (log && log->losses_cap > 0 && !log->losses) return CM_ERR_INVALID;
+    NET_CUDA(cudaSetDevice(net->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t hw = (size_t)H * W;
+    float *fb = nullptr, *ub = nullptr;
+    cudaError_t e = cudaMalloc(&fb, (size_t)o->batch * hw * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&ub, (size_t)o->batch * hw * sizeof(float));
+    if (e != cudaSuccess) {
+        cudaFree(fb);
+        net->err = "cm_net_train: out of device memory for the mini-batch";
+        return e == cudaErrorMemoryAllocation ? CM_ERR_OOM : CM_ERR_CUDA;
+    }
+    const long long T = o->total_steps > 0 ? o->total_steps : (long long)o->start_step + o->steps;
+    std::vector<int> perm(N), idx(o->batch);
+    int rc = CM_OK;
+    if (log) log->n_logged = 0;
+    for (int s = 0; s < o->steps && rc == CM_OK; ++s) {
+        const long long t = (long long)o->start_step + s;
+        batch_indices(o->seed, t, N, o->batch, perm, idx);
+        for (int j = 0; j < o->batch && e == cudaSuccess; ++j) {
+            e = cudaMemcpyAsync(fb + j * hw, f + (size_t)idx[j] * hw, hw * sizeof(float),
+                                cudaMemcpyDeviceToDevice, st);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(ub + j * hw, ustar + (size_t)idx[j] * hw, hw * sizeof(float),
+                                    cudaMemcpyDeviceToDevice, st);
+        }
+        if (e != cudaSuccess) {
+            rc = CM_ERR_CUDA;
+            net->err = std::string("cm_net_train: ") + cudaGetErrorString(e);
+            break;
+        }
+        // cosine decay lr -> lr_final over the schedule's T steps
+        const double lr = (double)o->lr_final + 0.5 * ((double)o->lr - (double)o->lr_final) *
+                                                    (1.0 + cos(3.14159265358979323846 * (double)t /
+                                                               (double)std::max(1LL, T - 1)));
+        const bool want = log && ((s % o->log_every) == 0 || s == o->steps - 1 || s == 0);
+        double loss = 0.0;
+        rc = cm_net_train_step(net, fb, ub, o->batch, H, W, (float)lr, want ? &loss : nullptr,
+                               stream);
+        if (rc == CM_OK && want) {
+            if (s == 0) log->loss_first = loss;
+            log->loss_last = loss;
+            if (log->n_logged < log->losses_cap) {
+                log->losses[log->n_logged] = loss;
+                if (log->logged_steps) log->logged_steps[log->n_logged] = (int)t;
+                log->n_logged += 1;
+            }
+        }
+    }
+    if (rc == CM_OK) {
+        e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) {
+            rc = CM_ERR_CUDA;
+            net->err = std::string("cm_net_train: ") + cudaGetErrorString(e);
+        } else {
+            rc = cm::cnn::net_status(net);
+        }
+    }
+    cudaFree(fb);
+    cudaFree(ub);
+    return rc;
 }
 
 }  // extern "C"

@@ -21,6 +21,24 @@ from . import (CM_OK, CMError, Context, _P, _I, _F, _D, _ctx, _stream_ptr, load,
                cm_solve_batched)
 
 N_PARAMS = 37601
+
+
+class TrainOpts(ctypes.Structure):
+    """cm_train_opts of include/cm.h."""
+    _fields_ = [("steps", ctypes.c_int), ("batch", ctypes.c_int), ("lr", ctypes.c_float),
+                ("lr_final", ctypes.c_float), ("total_steps", ctypes.c_int),
+                ("start_step", ctypes.c_int), ("seed", ctypes.c_uint64),
+                ("log_every", ctypes.c_int)]
+
+
+class TrainLog(ctypes.Structure):
+    """cm_train_log of include/cm.h."""
+    _fields_ = [("loss_first", ctypes.c_double), ("loss_last", ctypes.c_double),
+                ("n_logged", ctypes.c_int), ("losses_cap", ctypes.c_int),
+                ("losses", ctypes.POINTER(ctypes.c_double)),
+                ("logged_steps", ctypes.POINTER(ctypes.c_int))]
+
+
 _SIGS = {
     "cm_net_num_params": (_I, []),
     "cm_net_create": (_I, [_P, ctypes.POINTER(_P)]),
@@ -33,6 +51,10 @@ _SIGS = {
                               ctypes.POINTER(_D), _P]),
     "cm_net_train_step": (_I, [_P, _P, _P, _I, _I, _I, _F, ctypes.POINTER(_D), _P]),
     "cm_warmstart": (_I, [_P, _P, _P, _I, _I, _I, _P, _I, _F, _I, ctypes.POINTER(_I), _P]),
+    "cm_net_save": (_I, [_P, ctypes.c_char_p]),
+    "cm_net_load": (_I, [_P, ctypes.c_char_p]),
+    "cm_net_train": (_I, [_P, _P, _P, _P, _I, _I, _I, ctypes.POINTER(TrainOpts),
+                          ctypes.POINTER(TrainLog), _P]),
 }
 _bound = False
 
@@ -139,6 +161,33 @@ class Net:
                                              float(lr), ctypes.byref(loss) if want_loss else None,
                                              _stream_ptr(stream)))
         return loss.value if want_loss else None
+
+    def train_native(self, F, U, steps: int, batch: int, lr: float, lr_final: float,
+                     seed: int = 0, total_steps: int = 0, start_step: int = 0,
+                     log_every: int = 100, stream=None) -> dict:
+        """The library's training loop (cm_net_train) on the pairs F, U
+        (N x H x W); returns the log (losses with their schedule steps)."""
+        F, N, H, W = _batch(F)
+        U, _, _, _ = _batch(U)
+        o = TrainOpts(steps=steps, batch=batch, lr=lr, lr_final=lr_final, total_steps=total_steps,
+                      start_step=start_step, seed=seed, log_every=log_every)
+        cap = steps // log_every + 2
+        losses = (ctypes.c_double * cap)()
+        at = (ctypes.c_int * cap)()
+        lg = TrainLog(losses_cap=cap, losses=losses, logged_steps=at)
+        self._check(_lib().cm_net_train(self.ctx.handle, self._h, F.data_ptr(), U.data_ptr(), N,
+                                        H, W, ctypes.byref(o), ctypes.byref(lg),
+                                        _stream_ptr(stream)))
+        n = lg.n_logged
+        return {"loss_first": lg.loss_first, "loss_last": lg.loss_last,
+                "steps": [at[i] for i in range(n)], "losses": [losses[i] for i in range(n)]}
+
+    def save_checkpoint(self, path: str):
+        """Parameters, Adam moments and step (cm_net_save)."""
+        self._check(_lib().cm_net_save(self._h, os.fsencode(path)))
+
+    def load_checkpoint(self, path: str):
+        self._check(_lib().cm_net_load(self._h, os.fsencode(path)))
 
     def save(self, path: str, meta: dict | None = None):
         np.savez(path, params=self.get_params(), meta=np.array(repr(meta or {})))
