@@ -551,6 +551,31 @@ def main():
                                         "final_energy": st_plain[-1].energy_final,
                                         "monotone_violations": st_plain[-1].monotone_violations}
 
+    # complexity (the paper's linear-complexity study, Sec. 4): the plain
+    # solve from f to the same tolerance on the same generator's images of
+    # 256^2 .. 4096^2 (all levels, the tuned schedule): cycles, time, and
+    # device time per pixel and cycle
+    complexity = {}
+    for side in (256, 512, 1024, 2048, 4096):
+        im = synth.large(side)
+        fs = torch.from_numpy(im.f).to(dev)
+        us = torch.empty_like(fs)
+        cm.cm_solve(fs, ALPHA, KIND, levels=0, cycles=MAX_CYCLES, tol=TOL, u_out=us,
+                    options=opts, ctx=ctx)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        _, sts = cm.cm_solve(fs, ALPHA, KIND, levels=0, cycles=MAX_CYCLES, tol=TOL, u_out=us,
+                             options=opts, ctx=ctx)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        sec = e0.elapsed_time(e1) / 1e3
+        complexity[f"{side}x{side}"] = {
+            "levels": sts.levels, "cycles_to_tol": sts.cycles_run, "s": sec,
+            "ns_per_pixel_cycle": 1e9 * sec / (side * side * max(1, sts.cycles_run)),
+            "psnr_db": synth.psnr(us.cpu().numpy(), im.clean)}
+        del fs, us
+
     # curvature kinds (plain solve from f to the same tolerance, the same
     # schedule): H and K from the extreme direction curvatures (the paper's
     # kinds) and from the least-squares Euler fit; Gaussian kinds at alpha 15
@@ -677,7 +702,8 @@ def main():
             "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks,
             "b1_phase_ms": b1_ms, "batched": batched_res, "one_step": one_step_res,
             "reconstruction": recon_res,
-            "cycle_variants": variants, "curvature_kinds": kinds_res}
+            "cycle_variants": variants, "curvature_kinds": kinds_res,
+            "complexity": complexity}
     line["config"]["levels"] = L
     line["config"]["grid_points"] = opts.grid_points
     line["config"]["golden_evals"] = opts.golden_evals
