@@ -40,7 +40,7 @@ METRIC = ("s to rel-energy tol 1e-4 at 1024^2 (learned warm start + FP32 sweep w
 WARMSTART_PARAMS = os.path.join(ROOT, "paper_2204_07921_gb300", "data", "warmstart_mean_a20.npz")
 WARMSTART_PARAMS_GAUSS = os.path.join(ROOT, "paper_2204_07921_gb300", "data", "warmstart_gauss_a15.npz")
 L2_FLUSH_BYTES = 512 << 20   # > 129 MB L2
-B1_TRAFFIC_BYTES = 7.41e6     # ncu DRAM bytes of one finest-level phase at 1024^2
+B1_TRAFFIC_BYTES = 7.42e6     # ncu DRAM bytes of one finest-level phase at 1024^2 (mean of 8)
 
 
 def parse():
@@ -628,7 +628,7 @@ def main():
                 "measured_fma_per_s": alu["fma_per_s"],
                 "nominal_peak": 152 * 16 * 2.07e9 / 8 / 1e9,
                 # dram__bytes_read.sum + dram__bytes_write.sum of one launch of this
-                # kernel at 1024^2, from one ncu capture of a solve cycle
+                # kernel at 1024^2: the mean of eight launches of one ncu capture
                 "traffic": B1_TRAFFIC_BYTES if args.side == 1024 else None,
                 "traffic_unit": "B per launch",
                 "note": "curvature-stencil evaluations/s; peak = measured rsqrtf rate / 8 "
