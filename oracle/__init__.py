@@ -70,9 +70,10 @@ def lib():
                 "orc_level_side": (i, [i, i]),
                 "orc_phase": (i, [dp, dp, i, i, d, i, i, i, i, i, i, i, i, dp]),
                 "orc_level_sequential": (None, [dp, dp, i, i, d, i, i, i, i, i, i]),
-                "orc_cycle": (None, [dp, dp, i, i, d, i, i, i, i, i, i, i, i, i, i]),
-                "orc_solve": (i, [dp, i, i, d, i, i, i, d, dp, dp, i, i, i, i, i, i, i, i, dp, ip]),
-                "orc_level_colours": (i, [i, i]),
+                "orc_cycle": (None, [dp, dp, i, i, d, i, i, i, i, i, i, i, i, i, i, i]),
+                "orc_solve": (i, [dp, i, i, d, i, i, i, d, dp, dp, i, i, i, i, i, i, i, i, i, dp,
+                                  ip]),
+                "orc_level_colours": (i, [i, i, i]),
                 "orc_chalf_map": (None, [dp, i, i, i, dp]),
                 "orc_num_threads": (i, []),
                 "orc_local_energy_batch": (None, [dp, dp, i, i, i, i, i, i, d, i, dp, i, dp]),
@@ -216,24 +217,26 @@ def chalf_map(u, kind) -> np.ndarray:
     return out
 
 
-def level_colours(ncolors, b) -> int:
-    """Colours of the level with block side b (ncolors = 0: decoupled)."""
-    return lib().orc_level_colours(ncolors, b)
+def level_colours(ncolors, b, coarse_ncolors=0) -> int:
+    """Colours of the level with block side b (ncolors = 0: decoupled;
+    coarse_ncolors, when set, on the levels with b >= 64)."""
+    return lib().orc_level_colours(ncolors, b, coarse_ncolors)
 
 
 def cycle(u, f, alpha, kind, levels=0, ncolors=2, G=DEFAULT_G, K=DEFAULT_K, use_paper=True,
-          sequential=False, one_step=False, vcycle=False, sides=0):
+          sequential=False, one_step=False, vcycle=False, sides=0, coarse_ncolors=0):
     u = _f64(u).copy()
     f = _f64(f)
     H, W = u.shape
     lib().orc_cycle(_dp(u), _dp(f), H, W, float(alpha), kind, levels, ncolors, G, K,
-                    int(use_paper), int(one_step), int(sequential), int(vcycle), int(sides))
+                    int(use_paper), int(one_step), int(sequential), int(vcycle), int(sides),
+                    int(coarse_ncolors))
     return u
 
 
 def solve(f, alpha, kind, levels=0, cycles=20, tol=0.0, u0=None, ncolors=2, G=DEFAULT_G,
           K=DEFAULT_K, use_paper=True, sequential=False, one_step=False, vcycle=False,
-          sides=0):
+          sides=0, coarse_ncolors=0):
     """Alg. 3 outer loop.  Returns (u, trace, cycles_run, converged)."""
     f = _f64(f)
     H, W = f.shape
@@ -246,7 +249,7 @@ def solve(f, alpha, kind, levels=0, cycles=20, tol=0.0, u0=None, ncolors=2, G=DE
         u0p = _dp(u0a)
     n = lib().orc_solve(_dp(f), H, W, float(alpha), kind, levels, cycles, float(tol), u0p,
                         _dp(u), ncolors, G, K, int(use_paper), int(one_step), int(sequential),
-                        int(vcycle), int(sides), _dp(trace),
+                        int(vcycle), int(sides), int(coarse_ncolors), _dp(trace),
                         ctypes.byref(conv))
     return u, trace[: n + 1], n, bool(conv.value)
 

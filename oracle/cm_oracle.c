@@ -507,8 +507,12 @@ int orc_block_colour(int bi, int bj, int ncolors) {
  * colouring: the smallest p >= 2 with (p - 1) b >= 3, so that two blocks of
  * one colour are at least 3 pixels apart and share no stencil (a ring pixel
  * of one is never in the window of a ring pixel of the other); a colour's
- * parallel solve then equals solving its blocks one after another. */
-int orc_level_colours(int ncolors, int b) {
+ * parallel solve then equals solving its blocks one after another.
+ * coarse_ncolors != 0 sets the colour count of the levels with b >= 64 (a
+ * schedule option: fewer sequential phases on the coarse levels, whose
+ * same-colour blocks then share only corner pixels of their rings). */
+int orc_level_colours(int ncolors, int b, int coarse_ncolors) {
+    if (coarse_ncolors != 0 && b >= 64) return coarse_ncolors;
     if (ncolors != 0) return ncolors;
     int p = 2;
     while ((p - 1) * b < 3) ++p;
@@ -589,7 +593,7 @@ void orc_level_sequential(double *u, const double *f, int H, int W, double alpha
  * back up, levels L - 1 .. 1 (the full V-cycle the paper compares against). */
 void orc_cycle(double *u, const double *f, int H, int W, double alpha, int kind, int levels,
                int ncolors, int G, int K, int use_paper, int one_step, int sequential,
-               int vcycle, int sides) {
+               int vcycle, int sides, int coarse_ncolors) {
     if (levels <= 0) levels = orc_auto_levels(H, W, sides);
     int nsteps = vcycle ? 2 * levels - 1 : levels;
     for (int s = 0; s < nsteps; ++s) {
@@ -598,7 +602,7 @@ void orc_cycle(double *u, const double *f, int H, int W, double alpha, int kind,
         if (sequential) {
             orc_level_sequential(u, f, H, W, alpha, kind, b, G, K, use_paper, one_step);
         } else {
-            int nc = orc_level_colours(ncolors, b);
+            int nc = orc_level_colours(ncolors, b, coarse_ncolors);
             for (int k = 0; k < nc; ++k)
                 orc_phase(u, f, H, W, alpha, kind, b, nc, k, G, K, use_paper, one_step, NULL);
         }
@@ -612,8 +616,8 @@ void orc_cycle(double *u, const double *f, int H, int W, double alpha, int kind,
  * F(u_0), F(u_1), ...  Returns the number of cycles run; *converged is set. */
 int orc_solve(const double *f, int H, int W, double alpha, int kind, int levels, int cycles,
               double tol, const double *u0, double *u_out, int ncolors, int G, int K,
-              int use_paper, int one_step, int sequential, int vcycle, int sides, double *trace,
-              int *converged) {
+              int use_paper, int one_step, int sequential, int vcycle, int sides,
+              int coarse_ncolors, double *trace, int *converged) {
     size_t N = (size_t)H * W;
     if (u0) memcpy(u_out, u0, N * sizeof(double));
     else memcpy(u_out, f, N * sizeof(double));
@@ -622,7 +626,7 @@ int orc_solve(const double *f, int H, int W, double alpha, int kind, int levels,
     int l = 0, conv = 0;
     while (l < cycles) {
         orc_cycle(u_out, f, H, W, alpha, kind, levels, ncolors, G, K, use_paper, one_step,
-                  sequential, vcycle, sides);
+                  sequential, vcycle, sides, coarse_ncolors);
         ++l;
         double E = orc_energy(u_out, f, H, W, alpha, kind);
         if (trace) trace[l] = E;

@@ -258,3 +258,27 @@ def test_paper_block_sides_monotone_and_denoise(kind):
     u, tr, n, _ = oracle.solve(f, 15.0, kind, cycles=6, ncolors=4, sides=1)
     assert tr[-1] < 0.7 * tr[0]
     assert synth.psnr(u, img.clean) > synth.psnr(f, img.clean)
+
+
+def test_coarse_colour_count_schedule():
+    """coarse_ncolors sets the colours of the levels with block side >= 64
+    only; a cycle is then the phase sequence with 4 colours below 64 and 2
+    from 64 on, and the solve still descends and denoises."""
+    assert oracle.level_colours(4, 32, 2) == 4
+    assert oracle.level_colours(4, 64, 2) == 2 and oracle.level_colours(0, 128, 2) == 2
+    assert oracle.level_colours(4, 64, 0) == 4 and oracle.level_colours(0, 64, 0) == 4
+    img = synth.piecewise_image(150, 140, 17, 8, 0.08)
+    f = img.f.astype(np.float64)
+    L = oracle.auto_levels(150, 140)
+    assert L == 7   # sides 1 .. 64
+    uc = oracle.cycle(f, f, 20.0, oracle.MEAN, ncolors=4, coarse_ncolors=2)
+    up = f.copy()
+    for j in range(1, L + 1):
+        b = oracle.level_side(j)
+        nc = 2 if b >= 64 else 4
+        for k in range(nc):
+            up, _ = oracle.phase(up, f, 20.0, oracle.MEAN, b, nc, k)
+    np.testing.assert_array_equal(uc, up)
+    u, tr, n, _ = oracle.solve(f, 20.0, oracle.MEAN, cycles=3, ncolors=4, coarse_ncolors=2)
+    assert np.all(np.diff(tr) < 0)
+    assert synth.psnr(u, img.clean) > synth.psnr(f, img.clean)
