@@ -250,7 +250,8 @@ def batched_measurement(cm, torch, synth, ctx, dev, rank=0, world=1):
             sts.append(st)
         return sts
 
-    res = {"schedule": {k: brec[k] for k in ("G", "K", "ncolors", "coarse_spec", "coarse_dmax")}}
+    res = {"schedule": {k: brec[k] for k in ("G", "K", "ncolors", "coarse_ncolors", "coarse_spec",
+                                             "coarse_dmax")}}
     for name, fn in (("batched", batched), ("one_at_a_time", sequential)):
         fn()   # warm-up (graph capture)
         torch.cuda.synchronize()
@@ -670,6 +671,8 @@ def main():
     # (b < 64); one per colour + apply on coarse levels (+ tile sums on the
     # first); energy; the device stopping test
     def level_colours(nc, b):
+        if opts.coarse_ncolors != 0 and b >= 64:
+            return opts.coarse_ncolors
         if nc != 0:
             return nc
         p = 2
@@ -710,6 +713,7 @@ def main():
     line["config"]["ncolors"] = opts.ncolors
     line["config"]["coarse_spec"] = opts.coarse_spec
     line["config"]["coarse_dmax"] = opts.coarse_dmax
+    line["config"]["coarse_ncolors"] = opts.coarse_ncolors
     line["autotune"] = tune_rec
     if rank == 0:
         print(json.dumps(line), flush=True)

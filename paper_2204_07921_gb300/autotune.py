@@ -10,7 +10,11 @@ seeded image that is not one of the measured workloads):
    search can also settle in worse local minima than a coarser one;
 2. the colour schedule -- four colours, the checkerboard, or the decoupled
    colouring (more colours on the finest levels, no shared stencils);
-3. the coarse levels' kernel shape -- how many candidates share one cluster
+3. the colour count of the coarse levels (block side >= 64): the fine
+   levels' rule or two colours -- fewer sequential phases on the
+   latency-bound coarse levels, whose same-colour blocks then share only
+   corner pixels of their rings;
+4. the coarse levels' kernel shape -- how many candidates share one cluster
    reduction (first-pair speculation, golden steps per round), which changes
    the number of barriers and not the decisions.
 
@@ -26,9 +30,10 @@ import os
 
 CANDIDATES = ((9, 16), (7, 10), (5, 8), (5, 6), (5, 4), (3, 4))
 COLOURS = (4, 2, 0)
+COARSE_COLOURS = (0, 2)
 COARSE = ((-1, 0), (0, 4), (1, 4), (0, 2), (0, 1))   # (coarse_spec, coarse_dmax)
 ENERGY_SLACK = 2e-3
-CACHE_VERSION = 2
+CACHE_VERSION = 3
 
 
 def choose(results, slack: float = ENERGY_SLACK):
@@ -71,7 +76,8 @@ def tune(H: int, W: int, kind: int, alpha: float, tol: float = 1e-4, ncolors=Non
     def options(rec):
         return cm.default_options(ncolors=rec["ncolors"], grid_points=rec["G"],
                                   golden_evals=rec["K"], coarse_spec=rec["coarse_spec"],
-                                  coarse_dmax=rec["coarse_dmax"])
+                                  coarse_dmax=rec["coarse_dmax"],
+                                  coarse_ncolors=rec.get("coarse_ncolors", 0))
 
     if key in cache:
         return options(cache[key]), cache[key]
@@ -98,7 +104,7 @@ def tune(H: int, W: int, kind: int, alpha: float, tol: float = 1e-4, ncolors=Non
         return {**cfg, "seconds": best, "cycles": st.cycles_run, "energy": st.energy_final}
 
     cfg = {"G": 5, "K": 6, "ncolors": 4 if ncolors is None else ncolors, "coarse_spec": -1,
-           "coarse_dmax": 0}
+           "coarse_dmax": 0, "coarse_ncolors": 0}
     stages = {}
     stages["budget"] = [run({**cfg, "G": G, "K": K}) for G, K in candidates]
     pick = choose(stages["budget"])
@@ -106,6 +112,8 @@ def tune(H: int, W: int, kind: int, alpha: float, tol: float = 1e-4, ncolors=Non
     if ncolors is None:
         stages["colours"] = [run({**cfg, "ncolors": nc}) for nc in COLOURS]
         cfg["ncolors"] = choose(stages["colours"])["ncolors"]
+    stages["coarse_colours"] = [run({**cfg, "coarse_ncolors": cn}) for cn in COARSE_COLOURS]
+    cfg["coarse_ncolors"] = choose(stages["coarse_colours"])["coarse_ncolors"]
     stages["coarse"] = [run({**cfg, "coarse_spec": sp, "coarse_dmax": dm}) for sp, dm in COARSE]
     pick = choose(stages["coarse"])
     cfg.update(coarse_spec=pick["coarse_spec"], coarse_dmax=pick["coarse_dmax"])

@@ -29,7 +29,7 @@ struct GraphKey {
     const float* R;
     const float* f;
     int H, W, kind, levels, ncolors, G, K, use_paper, one_step, vcycle, coarse_spec, coarse_dmax,
-        block_sides;
+        block_sides, coarse_ncolors;
     float alpha;
     double tol;
     int cycles, trace_cap;
@@ -186,6 +186,9 @@ int check_opts(cm_ctx* ctx, const cm_options& o) {
         return fail(ctx, CM_ERR_INVALID, "coarse_dmax must be 0 .. 4");
     if (o.block_sides != 0 && o.block_sides != 1)
         return fail(ctx, CM_ERR_INVALID, "block_sides must be 0 or 1");
+    if (o.coarse_ncolors != 0 && o.coarse_ncolors != 2 && o.coarse_ncolors != 4 &&
+        o.coarse_ncolors != 9 && o.coarse_ncolors != 16)
+        return fail(ctx, CM_ERR_INVALID, "coarse_ncolors must be 0, 2, 4, 9 or 16");
     return CM_OK;
 }
 
@@ -227,7 +230,7 @@ cm::PhaseArgs phase_args(const float* S, float* R, const float* f, int H, int W,
     a.kind = kind;
     a.lb = cm::side_class(b);
     a.bs = b;
-    a.ncolors = cm::level_colours(o.ncolors, b);
+    a.ncolors = cm::level_colours(o.ncolors, b, o.coarse_ncolors);
     a.colour = colour;
     a.G = o.grid_points;
     a.K = o.golden_evals;
@@ -253,7 +256,7 @@ cudaError_t enqueue_level(float* tsums, float* cj, const float* S, float* R, con
         a.active = active;
         return cm::launch_level_coarse(a, tsums, cj, st, sums_ready);
     }
-    const int nc = cm::level_colours(o.ncolors, b);
+    const int nc = cm::level_colours(o.ncolors, b, o.coarse_ncolors);
     for (int k = 0; k < nc; ++k) {
         cm::PhaseArgs a = phase_args(S, R, f, H, W, alpha, kind, b, k, o);
         a.c_out = c_out;
@@ -382,6 +385,7 @@ int cm_options_default(cm_options* o) {
     o->vcycle = 0;
     o->coarse_spec = -1;
     o->coarse_dmax = 0;
+    o->coarse_ncolors = 0;
     o->block_sides = 0;
     return CM_OK;
 }
@@ -485,7 +489,7 @@ int cm_phase(cm_ctx* ctx, const float* S, float* R, const float* f, int H, int W
         return fail(ctx, CM_ERR_INVALID, "cm_phase: invalid argument");
     if (side_lb(b) < 0)
         return fail(ctx, CM_ERR_INVALID, "cm_phase: b must be 2^j or 2^j - 1, at most 2048");
-    if (colour < 0 || colour >= cm::level_colours(o.ncolors, b))
+    if (colour < 0 || colour >= cm::level_colours(o.ncolors, b, o.coarse_ncolors))
         return fail(ctx, CM_ERR_INVALID, "cm_phase: bad colour");
     CM_CUDA(cudaSetDevice(ctx->device));
     cm::PhaseArgs a = phase_args(S, R, f, H, W, alpha, kind, b, colour, o);
@@ -566,6 +570,7 @@ int cm_solve(cm_ctx* ctx, const float* f, int H, int W, float alpha, int kind, i
         key.coarse_spec = o.coarse_spec;
         key.coarse_dmax = o.coarse_dmax;
         key.block_sides = o.block_sides;
+        key.coarse_ncolors = o.coarse_ncolors;
         key.alpha = alpha;
         key.tol = tol;
         key.cycles = cycles;

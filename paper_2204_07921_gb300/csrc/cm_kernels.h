@@ -33,10 +33,12 @@ inline int active_slots(int nbi, int nbj, int ncol) {
     return ((nbi + p - 1) / p) * ((nbj + p - 1) / p);
 }
 
-// Colours of the level with block side b: ncolors, or for ncolors = 0 the
-// decoupled colouring (the smallest p >= 2 with (p - 1) b >= 3, p^2
-// colours), under which a colour's blocks share no stencil.
-inline int level_colours(int ncolors, int b) {
+// Colours of the level with block side b: coarse_ncolors when it is set and
+// b >= 64; else ncolors, or for ncolors = 0 the decoupled colouring (the
+// smallest p >= 2 with (p - 1) b >= 3, p^2 colours), under which a colour's
+// blocks share no stencil.
+inline int level_colours(int ncolors, int b, int coarse_ncolors = 0) {
+    if (coarse_ncolors != 0 && b >= 64) return coarse_ncolors;
     if (ncolors != 0) return ncolors;
     int p = 2;
     while ((p - 1) * b < 3) ++p;
