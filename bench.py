@@ -278,6 +278,20 @@ def batched_measurement(cm, torch, synth, ctx, dev, rank=0, world=1):
     return res
 
 
+def level_colours(opts, b):
+    """Colours of the level of block side b under the options (the library's
+    rule: coarse_ncolors on b >= 64 when set, the decoupled count for
+    ncolors = 0)."""
+    if opts.coarse_ncolors != 0 and b >= 64:
+        return opts.coarse_ncolors
+    if opts.ncolors != 0:
+        return opts.ncolors
+    p = 2
+    while (p - 1) * b < 3:
+        p += 1
+    return p * p
+
+
 def recon_measurement(cm, torch, synth, ctx, dev, stream, with_oracle=True):
     """Reconstruction extension (Sec. 5, A = M F): MRI-like cases (phantom of
     12 shapes, Cartesian rows at 1/3 sampling with the central 8% kept,
@@ -371,7 +385,7 @@ def main():
         _, st = cm.cm_solve(f, ALPHA, KIND, cycles=2, u_out=u, options=opts, ctx=ctx)
         R = u.clone()
         for j in range(L):
-            for k in range(opts.ncolors):
+            for k in range(level_colours(opts, 1 << j)):
                 cm.cm_phase(u, R, f, ALPHA, KIND, 1 << j, k, options=opts, ctx=ctx)
         # the coarse levels as the solve runs them (tile sums, rounds, apply)
         for j in range(COARSE_LB, L):
@@ -379,8 +393,8 @@ def main():
         cm.cm_energy(u, f, ALPHA, KIND, ctx=ctx)
         # one cycle of the solve outside a graph (profilers do not look inside
         # the conditional loop of the graph): the solve's own kernel sequence
-        oh = cm.default_options(grid_points=opts.grid_points, golden_evals=opts.golden_evals,
-                                ncolors=opts.ncolors, use_graph=0)
+        oh = cm.Options.from_buffer_copy(opts)
+        oh.use_graph = 0
         cm.cm_solve(f, ALPHA, KIND, cycles=1, u_out=u, options=oh, ctx=ctx)
         torch.cuda.synchronize()
         print(json.dumps({"phases_only": True, "levels": L, "ncolors": opts.ncolors}))
@@ -603,7 +617,7 @@ def main():
     R = state.clone()
     n_launch = 20
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    nc = opts.ncolors
+    nc = level_colours(opts, 1)   # colours of the finest level
     for k in range(nc):
         cm.cm_phase(state, R, f, ALPHA, KIND, 1, k, options=opts, ctx=ctx)
     torch.cuda.synchronize()
@@ -670,17 +684,7 @@ def main():
     # kernels per cycle: one per colour on levels below the coarse threshold
     # (b < 64); one per colour + apply on coarse levels (+ tile sums on the
     # first); energy; the device stopping test
-    def level_colours(nc, b):
-        if opts.coarse_ncolors != 0 and b >= 64:
-            return opts.coarse_ncolors
-        if nc != 0:
-            return nc
-        p = 2
-        while (p - 1) * b < 3:
-            p += 1
-        return p * p
-
-    kernels_per_cycle = 2 + sum(level_colours(opts.ncolors, 1 << j) +
+    kernels_per_cycle = 2 + sum(level_colours(opts, 1 << j) +
                                 (0 if j < COARSE_LB else (2 if j == COARSE_LB else 1))
                                 for j in range(L))
     # per warm step: 6 network kernels, 2 energy checks, then the solve graph
