@@ -1,6 +1,10 @@
-"""Pins of the reconstruction oracle (Sec. 5, MRI-like operator A = M F).
+"""Pins of the reconstruction oracle (Sec. 5: MRI-like operator A = M F, and
+CT with a parallel-beam Radon transform).
 
-The operator is pinned by its adjoint identity and Parseval; the per-colour
+The MRI operator is pinned by its adjoint identity and Parseval, the Radon
+pair by its adjoint identity, mass per angle and the theta = 0 column sums,
+the filtered backprojection by the Ram-Lak kernel's zero DC gain and a
+densely sampled phantom; the per-colour
 correction by a closed form (full mask: the Gram matrix is diagonal) and by
 a dense linear solve of the assembled normal equations; the sweep by
 monotone descent of the data term when the regulariser vanishes, and by
@@ -121,3 +125,65 @@ def test_reconstruction_descends_and_denoises():
     u, trace = recon.solve(case.kspace, case.mask, 0.02, oracle.MEAN, cycles=4, cg_iters=8)
     assert np.all(np.diff(trace) < 0)
     assert synth.psnr(u, case.clean) > synth.psnr(u0, case.clean) + 1.0
+
+
+# ---------------------------------------------------------------------------
+# CT: parallel-beam Radon transform with linear-interpolation weights.
+
+def test_radon_pair_adjoint_mass_and_columns():
+    rng = np.random.default_rng(2)
+    H, W, n = 13, 9, 17
+    u = rng.normal(size=(H, W))
+    y = rng.normal(size=(n, recon.radon_geometry(H, W, n)[0]))
+    Ru = recon.radon_forward(u, n)
+    assert np.sum(Ru * y) == pytest.approx(np.sum(u * recon.radon_adjoint(y, H, W)), rel=1e-12)
+    # every angle's projection carries the image's sum (weights 1 - w, w)
+    np.testing.assert_allclose(Ru.sum(axis=1), u.sum(), rtol=1e-12)
+    # theta = 0 with an odd width: each column falls on one bin, at the centre
+    D = Ru.shape[1]
+    h = (D - 1) // 2
+    np.testing.assert_allclose(Ru[0, h - (W - 1) // 2: h + (W - 1) // 2 + 1], u.sum(axis=0),
+                               rtol=1e-12)
+    assert np.all(Ru[0, :h - (W - 1) // 2] == 0) and np.all(Ru[0, h + (W - 1) // 2 + 1:] == 0)
+
+
+def test_ramp_filter_and_fbp():
+    """The Ram-Lak kernel sums to zero (no DC gain: a constant projection is
+    filtered to ~0 away from the detector's ends), and filtered
+    backprojection of a densely sampled phantom recovers it."""
+    row = np.ones((1, 101))
+    f = recon.ramp_filter(row)[0]
+    assert np.max(np.abs(f[40:61])) < 0.01
+    clean = synth.piecewise_image(32, 32, 5, 6, 0.0).clean.astype(np.float64)
+    u = recon.fbp(recon.radon_forward(clean, 90), 32, 32)
+    assert synth.psnr(u, clean) > 24.0
+
+
+def test_ct_step_equals_dense_normal_equations():
+    H, W, n = 10, 9, 12
+    rng = np.random.default_rng(4)
+    clean = synth.piecewise_image(H, W, 3, 3, 0.0).clean.astype(np.float64)
+    sino = recon.radon_forward(clean, n) + 0.05 * rng.normal(size=(n, recon.radon_geometry(H, W, n)[0]))
+    u = recon.fbp(sino, H, W)
+    op = recon.CtOp(H, W, n)
+    alpha, b, k = 0.3, 2, 2
+    lab, m = recon.colour_labels(H, W, b, 4, k)
+    Aphi = [op.fwd((lab == i).astype(float)) for i in range(m)]
+    G = np.array([[np.sum(Aphi[i] * Aphi[j]) for j in range(m)] for i in range(m)])
+    res = sino - op.fwd(u)
+    rhs = np.array([np.sum(Aphi[i] * res) for i in range(m)])
+    c_dense = np.linalg.solve(G + 2 * alpha * np.eye(m), rhs)
+    _, c = recon.colour_step_op(u, sino, op, alpha, oracle.MEAN, b, 4, k, cg_iters=m)
+    np.testing.assert_allclose(c, c_dense, rtol=1e-7, atol=1e-9)
+
+
+def test_ct_reconstruction_improves_on_fbp():
+    clean = synth.piecewise_image(32, 32, 5, 6, 0.0).clean.astype(np.float64)
+    n = 45
+    rng = np.random.default_rng(1)
+    sino = recon.radon_forward(clean, n)
+    sino = sino + 0.1 * rng.normal(size=sino.shape)
+    u0 = recon.fbp(sino, 32, 32)
+    u, trace = recon.solve_ct(sino, 32, 32, 1.0, oracle.MEAN, cycles=4, cg_iters=8)
+    assert np.all(np.diff(trace) < 0)
+    assert synth.psnr(u, clean) > synth.psnr(u0, clean) + 1.5
