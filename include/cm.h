@@ -357,6 +357,34 @@ int cm_recon(cm_ctx* ctx, const float* kspace, const unsigned char* mask, int H,
              float* u_out, const cm_options* opts /* host, nullable */,
              double* trace_host /* host, nullable */, void* stream);
 
+/* Reconstruction extension, CT case (Sec. 5 with A = R, a parallel-beam
+ * Radon transform): the same sweep and per-colour conjugate gradients as
+ * cm_recon, with the normal equations of R.  Geometry (a reading: Sec. 5
+ * names the Radon transform but no discretisation): n_angles angles
+ * theta_a = pi a / n_angles; the centre of pixel (r, c) is at
+ * x = c - (W-1)/2, y = r - (H-1)/2 and projects to p = x cos theta + y sin
+ * theta + (D-1)/2 on a detector of D = cm_radon_bins(H, W) =
+ * 2 ceil(hypot(H-1, W-1)/2) + 3 unit bins; the pixel's value goes to bins
+ * floor(p) and floor(p) + 1 with weights 1 - frac(p), frac(p) (every p lies
+ * in [1, D-2]).  sino: device, n_angles x D row-major float32.  u0: device
+ * H x W or NULL: start from the filtered backprojection (pi / n_angles)
+ * R^T (h * b), h the Ram-Lak kernel (h[0] = 1/4, h[k] = -1/(pi k)^2 for odd k,
+ * 0 for even k, a direct convolution per angle).  trace_host as in
+ * cm_recon; the CG and colour options as in cm_recon.  Needs no cuFFT.
+ * Synchronises `stream`. */
+int cm_radon_bins(int H, int W);
+int cm_recon_ct(cm_ctx* ctx, const float* sino, int n_angles, int H, int W, float alpha,
+                int kind, int levels, int cycles, int cg_iters, const float* u0, float* u_out,
+                const cm_options* opts /* host, nullable */,
+                double* trace_host /* host, nullable */, void* stream);
+/* The CT operator pair alone: sino = R u (n_angles x D), u = R^T sino (the
+ * exact transpose: both are gathers with the same weights).  Device
+ * pointers; temporaries are allocated and freed; synchronise `stream`. */
+int cm_radon(cm_ctx* ctx, const float* u, int H, int W, int n_angles, float* sino,
+             void* stream);
+int cm_radon_adjoint(cm_ctx* ctx, const float* sino, int n_angles, int H, int W, float* u,
+                     void* stream);
+
 /* Measurement support (not part of the solver).  The sweep kernels are bound
  * by FP32 and MUFU instruction issue, so their roofline is taken against the
  * GPU's measured arithmetic rates: fma_per_s (host) receives FP32 fused

@@ -17,6 +17,7 @@ from .build import LIB, build as build_library
 __all__ = [
     "CMError", "Options", "Stats", "Context", "load", "cm_energy", "cm_curvature", "cm_phase",
     "cm_level", "cm_energy_noalloc", "cm_solve_batched", "cm_probe_alu", "cm_recon",
+    "cm_recon_ct", "cm_radon", "cm_radon_adjoint", "cm_radon_bins",
     "cm_solve", "cm_auto_levels", "MEAN", "GAUSS", "MEAN_EULER", "GAUSS_EULER",
 ]
 
@@ -73,6 +74,11 @@ SIGNATURES = {
     "cm_energy_noalloc": (_I, [_P, _P, _I, _I, _F, _I, _P, _P]),
     "cm_probe_alu": (_I, [_I, _P, _P, _P]),
     "cm_selftest_wait": (_I, [_I, _I, _P, _P]),
+    "cm_radon_bins": (_I, [_I, _I]),
+    "cm_radon": (_I, [_P, _P, _I, _I, _I, _P, _P]),
+    "cm_radon_adjoint": (_I, [_P, _P, _I, _I, _I, _P, _P]),
+    "cm_recon_ct": (_I, [_P, _P, _I, _I, _I, _F, _I, _I, _I, _I, _P, _P,
+                         ctypes.POINTER(Options), _P, _P]),
     "cm_recon": (_I, [_P, _P, _P, _I, _I, _F, _I, _I, _I, _I, _P, _P, ctypes.POINTER(Options),
                       _P, _P]),
     "cm_level": (_I, [_P, _P, _P, _P, _I, _I, _F, _I, _I, ctypes.POINTER(Options), _P, _P]),
@@ -321,6 +327,58 @@ def cm_recon(kspace, mask, alpha: float, kind: int = MEAN, levels: int = 0, cycl
                              u0.data_ptr() if u0 is not None else None, u_out.data_ptr(),
                              ctypes.byref(opts), trace.ctypes.data_as(ctypes.c_void_p),
                              _stream_ptr(stream)))
+    return u_out, trace
+
+
+def cm_radon_bins(H: int, W: int) -> int:
+    """Detector bins of the CT geometry."""
+    return load().cm_radon_bins(H, W)
+
+
+def cm_radon(u, n_angles: int, ctx: Context | None = None, stream=None):
+    """sino = R u (n_angles x cm_radon_bins(H, W))."""
+    import torch
+    _img(u, "u")
+    c = _ctx(ctx, u)
+    H, W = u.shape
+    sino = torch.empty((n_angles, cm_radon_bins(H, W)), dtype=torch.float32, device=u.device)
+    c._check(load().cm_radon(c.handle, u.data_ptr(), H, W, n_angles, sino.data_ptr(),
+                             _stream_ptr(stream)))
+    return sino
+
+
+def cm_radon_adjoint(sino, H: int, W: int, ctx: Context | None = None, stream=None):
+    """u = R^T sino."""
+    import torch
+    _img(sino, "sino")
+    c = _ctx(ctx, sino)
+    u = torch.empty((H, W), dtype=torch.float32, device=sino.device)
+    c._check(load().cm_radon_adjoint(c.handle, sino.data_ptr(), sino.shape[0], H, W,
+                                     u.data_ptr(), _stream_ptr(stream)))
+    return u
+
+
+def cm_recon_ct(sino, H: int, W: int, alpha: float, kind: int = MEAN, levels: int = 0,
+                cycles: int = 5, cg_iters: int = 8, u0=None, u_out=None,
+                options: Options | None = None, ctx: Context | None = None, stream=None):
+    """CT reconstruction (Sec. 5, A = R) from the n_angles x D sinogram.
+    Returns (u_out, trace of J)."""
+    import numpy as np
+    import torch
+    _img(sino, "sino")
+    c = _ctx(ctx, sino)
+    if u_out is None:
+        u_out = torch.empty((H, W), dtype=torch.float32, device=sino.device)
+    _img(u_out, "u_out")
+    if u0 is not None:
+        _img(u0, "u0")
+    opts = options or default_options()
+    trace = np.zeros(cycles + 1)
+    c._check(load().cm_recon_ct(c.handle, sino.data_ptr(), sino.shape[0], H, W, float(alpha),
+                                kind, levels, cycles, cg_iters,
+                                u0.data_ptr() if u0 is not None else None, u_out.data_ptr(),
+                                ctypes.byref(opts), trace.ctypes.data_as(ctypes.c_void_p),
+                                _stream_ptr(stream)))
     return u_out, trace
 
 

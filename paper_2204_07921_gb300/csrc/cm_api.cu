@@ -958,8 +958,11 @@ int cm_recon(cm_ctx* ctx, const float* kspace, const unsigned char* mask, int H,
     CM_CUDA(cudaSetDevice(ctx->device));
     if (!ctx->recon) ctx->recon = cm::recon_work_create();
     cm::ReconArgs a;
+    a.op = cm::RECON_MRI;
     a.kspace = (const float2*)kspace;
     a.mask = mask;
+    a.sino = nullptr;
+    a.n_angles = 0;
     a.H = H;
     a.W = W;
     a.alpha = alpha;
@@ -976,6 +979,76 @@ int cm_recon(cm_ctx* ctx, const float* kspace, const unsigned char* mask, int H,
     rc = cm::recon_run(ctx->recon, a, (cudaStream_t)stream, &msg);
     if (rc == 3) return fail(ctx, CM_ERR_OOM, std::string("cm_recon: ") + msg);
     if (rc) return fail(ctx, CM_ERR_CUDA, std::string("cm_recon: ") + msg);
+    return CM_OK;
+}
+
+int cm_radon_bins(int H, int W) { return (H < 1 || W < 1) ? -1 : cm::radon_bins(H, W); }
+
+int cm_radon(cm_ctx* ctx, const float* u, int H, int W, int n_angles, float* sino,
+             void* stream) {
+    if (!ctx) return CM_ERR_INVALID;
+    if (!u || !sino || H < 1 || W < 1 || n_angles < 1 || n_angles > 100000)
+        return fail(ctx, CM_ERR_INVALID, "cm_radon: invalid argument");
+    CM_CUDA(cudaSetDevice(ctx->device));
+    const char* msg = "";
+    const int rc = cm::radon_forward(u, H, W, n_angles, sino, (cudaStream_t)stream, &msg);
+    if (rc) return fail(ctx, rc == 3 ? CM_ERR_OOM : CM_ERR_CUDA, std::string("cm_radon: ") + msg);
+    return CM_OK;
+}
+
+int cm_radon_adjoint(cm_ctx* ctx, const float* sino, int n_angles, int H, int W, float* u,
+                     void* stream) {
+    if (!ctx) return CM_ERR_INVALID;
+    if (!u || !sino || H < 1 || W < 1 || n_angles < 1 || n_angles > 100000)
+        return fail(ctx, CM_ERR_INVALID, "cm_radon_adjoint: invalid argument");
+    CM_CUDA(cudaSetDevice(ctx->device));
+    const char* msg = "";
+    const int rc = cm::radon_adjoint(sino, n_angles, H, W, u, (cudaStream_t)stream, &msg);
+    if (rc)
+        return fail(ctx, rc == 3 ? CM_ERR_OOM : CM_ERR_CUDA, std::string("cm_radon_adjoint: ") + msg);
+    return CM_OK;
+}
+
+int cm_recon_ct(cm_ctx* ctx, const float* sino, int n_angles, int H, int W, float alpha,
+                int kind, int levels, int cycles, int cg_iters, const float* u0, float* u_out,
+                const cm_options* opts, double* trace_host, void* stream) {
+    if (!ctx) return CM_ERR_INVALID;
+    cm_options o;
+    cm_options_default(&o);
+    if (opts) o = *opts;
+    int rc = check_opts(ctx, o);
+    if (rc) return rc;
+    if (!sino || !u_out || H < 1 || W < 1 || n_angles < 1 || n_angles > 100000 ||
+        !finite_positive(alpha) || !valid_kind(kind) || levels < 0 || cycles < 0 ||
+        cycles > 100000 || cg_iters < 1 || cg_iters > 1000 ||
+        (const void*)u_out == (const void*)sino)
+        return fail(ctx, CM_ERR_INVALID, "cm_recon_ct: invalid argument");
+    const int L = solve_levels(levels, H, W, o);
+    if (!levels_ok(L, o)) return fail(ctx, CM_ERR_INVALID, "cm_recon_ct: too many levels");
+    CM_CUDA(cudaSetDevice(ctx->device));
+    if (!ctx->recon) ctx->recon = cm::recon_work_create();
+    cm::ReconArgs a;
+    a.op = cm::RECON_CT;
+    a.kspace = nullptr;
+    a.mask = nullptr;
+    a.sino = sino;
+    a.n_angles = n_angles;
+    a.H = H;
+    a.W = W;
+    a.alpha = alpha;
+    a.kind = kind;
+    a.levels = L;
+    a.sides = o.block_sides;
+    a.ncolors = o.ncolors;
+    a.cycles = cycles;
+    a.cg_iters = cg_iters;
+    a.u0 = u0;
+    a.u = u_out;
+    a.trace_host = trace_host;
+    const char* msg = "";
+    rc = cm::recon_run(ctx->recon, a, (cudaStream_t)stream, &msg);
+    if (rc == 3) return fail(ctx, CM_ERR_OOM, std::string("cm_recon_ct: ") + msg);
+    if (rc) return fail(ctx, CM_ERR_CUDA, std::string("cm_recon_ct: ") + msg);
     return CM_OK;
 }
 

@@ -1,8 +1,9 @@
 // cm_recon.cu -- reconstruction extension (Sec. 5) with an MRI-like operator.
 //
 // Minimises J(u) = 1/2 ||A u - b||^2 + alpha sum |kappa(u)| for a real image u,
-// A = M F (M a 0/1 mask of sampled k-space entries, F the orthonormal 2-D
-// DFT).  The sweep visits the levels fine to coarse and the colours in order
+// with A = M F (MRI: M a 0/1 mask of sampled k-space entries, F the
+// orthonormal 2-D DFT) or A = R (CT: a parallel-beam Radon transform with
+// linear-interpolation weights, see radon_pos).  The sweep visits the levels fine to coarse and the colours in order
 // (Alg. 3); the blocks phi_i of one colour are solved together, because A
 // couples them: Sec. 5 replaces each block's curvature term by
 // alpha (c_i - d_i)^2 around the curvature-only estimate d_i and solves
@@ -12,7 +13,7 @@
 // Eq. c-sol1 (Prop. 2 for Gaussian curvature) on the finest level and 0 on
 // coarser ones; CG runs a fixed number of iterations from c = 0 and stops
 // early only on a zero residual or a non-positive p.Ap.  The start is the
-// zero-filled Re(A^H b).
+// zero-filled Re(A^H b) for MRI, the filtered backprojection (Ram-Lak) for CT.
 //
 // The transforms are cuFFT (single-precision C2C, unnormalised; the two
 // 1/sqrt(HW) factors of the orthonormal pair are folded into the mask
@@ -28,6 +29,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <vector>
 
 #include "cm_device.cuh"
 #include "cm_kernels.h"
@@ -329,14 +331,140 @@ __global__ void objective_kernel(const double* data2, const double* curv, float 
 }
 
 // ---------------------------------------------------------------------------
+// CT: n angles theta_a = pi a / n (cos, sin tables from the host); the
+// centre of pixel (r, c) sits at x = c - (W-1)/2, y = r - (H-1)/2 and projects
+// to the detector position p = x cos + y sin + (D-1)/2 of D unit bins; its
+// value is shared by bins floor(p) and floor(p) + 1 with weights 1 - frac(p)
+// and frac(p).  D = 2 ceil(hypot(H-1, W-1)/2) + 3 keeps every p in [1, D-2].
+// Forward and adjoint are both gathers that call radon_pos with the same
+// arguments, so the pair is exactly matched (and needs no atomics).
+
+__device__ __forceinline__ float radon_pos(int r, int c, int H, int W, float cs, float sn,
+                                           float half) {
+    const float x = (float)c - 0.5f * (float)(W - 1);
+    const float y = (float)r - 0.5f * (float)(H - 1);
+    return fmaf(x, cs, fmaf(y, sn, half));
+}
+
+// S[a][j] = sum over pixels of weight(p, j) U[pixel].x; one thread per bin.
+// Along the dominant axis of the angle's direction, p is linear with slope
+// >= 1/sqrt(2), so only pixels whose p lies in [j - 1, j + 1) contribute: at
+// most three per row (or column), searched in a window one pixel wider on
+// each side than the exact interval.
+__global__ void __launch_bounds__(RT) radon_fwd_kernel(const float2* __restrict__ U,
+                                                       float* __restrict__ S, int H, int W,
+                                                       int n, int D, const float* __restrict__ cs,
+                                                       const float* __restrict__ sn,
+                                                       const int* stop) {
+    if (stop && *stop) return;
+    const int idx = blockIdx.x * RT + threadIdx.x;
+    if (idx >= n * D) return;
+    const int a = idx / D, j = idx - a * D;
+    const float c = cs[a], sv = sn[a], half = 0.5f * (float)(D - 1);
+    const bool rows = fabsf(c) >= fabsf(sv);
+    const int outer = rows ? H : W, inner = rows ? W : H;
+    const float slope = rows ? c : sv, other = rows ? sv : c;
+    const float off_in = 0.5f * (float)(inner - 1), off_out = 0.5f * (float)(outer - 1);
+    float acc = 0.0f;
+    for (int o = 0; o < outer; ++o) {
+        const float base = fmaf((float)o - off_out, other, half);
+        float x0 = ((float)(j - 1) - base) / slope, x1 = ((float)(j + 1) - base) / slope;
+        if (x0 > x1) {
+            const float t = x0;
+            x0 = x1;
+            x1 = t;
+        }
+        const int i0 = max((int)floorf(x0 + off_in) - 1, 0);
+        const int i1 = min((int)ceilf(x1 + off_in) + 1, inner - 1);
+        for (int i = i0; i <= i1; ++i) {
+            const int r = rows ? o : i, col = rows ? i : o;
+            const float p = radon_pos(r, col, H, W, c, sv, half);
+            const float fl = floorf(p);
+            const int f = (int)fl;
+            const float w = p - fl;
+            const float v = U[(size_t)r * W + col].x;
+            if (f == j) acc = fmaf(1.0f - w, v, acc);
+            else if (f == j - 1) acc = fmaf(w, v, acc);
+        }
+    }
+    S[idx] = acc;
+}
+
+// U[pixel] = scale sum_a ((1 - w) S[a][f] + w S[a][f + 1]) (imaginary part 0).
+__global__ void __launch_bounds__(RT) radon_adj_kernel(const float* __restrict__ S,
+                                                       float2* __restrict__ U, int H, int W,
+                                                       int n, int D, const float* __restrict__ cs,
+                                                       const float* __restrict__ sn, float scale,
+                                                       const int* stop) {
+    if (stop && *stop) return;
+    const float half = 0.5f * (float)(D - 1);
+    const size_t N = (size_t)H * W;
+    for (size_t i = (size_t)blockIdx.x * RT + threadIdx.x; i < N; i += (size_t)gridDim.x * RT) {
+        const int r = (int)(i / W), col = (int)(i - (size_t)r * W);
+        float acc = 0.0f;
+        for (int a = 0; a < n; ++a) {
+            const float p = radon_pos(r, col, H, W, cs[a], sn[a], half);
+            const float fl = floorf(p);
+            const int f = (int)fl;
+            const float w = p - fl;
+            const float* row = S + (size_t)a * D;
+            acc = fmaf(1.0f - w, row[f], acc);
+            acc = fmaf(w, row[f + 1], acc);
+        }
+        U[i] = make_float2(scale * acc, 0.0f);
+    }
+}
+
+// T = b - T over the sinogram.
+__global__ void __launch_bounds__(RT) sino_resid_kernel(float* __restrict__ T,
+                                                        const float* __restrict__ b, int m) {
+    for (int i = blockIdx.x * RT + threadIdx.x; i < m; i += gridDim.x * RT) T[i] = b[i] - T[i];
+}
+
+// Each angle's projection convolved with the Ram-Lak kernel h[0] = 1/4,
+// h[k] = -1 / (pi k)^2 for odd k, 0 for even k != 0, over the D bins.
+__global__ void __launch_bounds__(RT) ramp_filter_kernel(const float* __restrict__ S,
+                                                         float* __restrict__ T, int n, int D) {
+    const int idx = blockIdx.x * RT + threadIdx.x;
+    if (idx >= n * D) return;
+    const int a = idx / D, j = idx - a * D;
+    const float* row = S + (size_t)a * D;
+    const float inv_pi2 = 0.10132118364233778f;   // 1 / pi^2
+    float acc = 0.25f * row[j];
+    // odd offsets m = j - k: k = j - 1, j - 3, ... and j + 1, j + 3, ...
+    for (int k = j - 1; k >= 0; k -= 2) {
+        const float m = (float)(j - k);
+        acc = fmaf(-inv_pi2 / (m * m), row[k], acc);
+    }
+    for (int k = j + 1; k < D; k += 2) {
+        const float m = (float)(k - j);
+        acc = fmaf(-inv_pi2 / (m * m), row[k], acc);
+    }
+    T[idx] = acc;
+}
+
+// *out = sum (T - b)^2 over the sinogram (twice the CT data term).
+__global__ void __launch_bounds__(RT) sino_sq_kernel(const float* __restrict__ T,
+                                                     const float* __restrict__ b, int m,
+                                                     double* partials, unsigned* ticket,
+                                                     double* out) {
+    double acc = 0.0;
+    for (int i = blockIdx.x * RT + threadIdx.x; i < m; i += gridDim.x * RT) {
+        const double d = (double)T[i] - (double)b[i];
+        acc += d * d;
+    }
+    cta_sum_finish(acc, partials, ticket, out);
+}
+
+// ---------------------------------------------------------------------------
 // Host side.
 
 // Everything the captured cycle bakes in: the problem, and every buffer it
 // reads or writes (the trace buffer included: it is reallocated when a call
 // asks for more cycles).
 struct ReconKey {
-    const void *kspace, *mask, *u, *trace;
-    int H, W, kind, levels, sides, ncolors, cg_iters, trace_cap;
+    const void *kspace, *mask, *sino, *u, *trace;
+    int op, n_angles, H, W, kind, levels, sides, ncolors, cg_iters, trace_cap;
     float alpha;
     bool operator==(const ReconKey& o) const { return memcmp(this, &o, sizeof(ReconKey)) == 0; }
 };
@@ -357,6 +485,9 @@ struct ReconWork {
     double* trace = nullptr;
     int* count = nullptr;
     int trace_cap = 0;
+    int op = -1, n_angles = 0;    // operator the buffers were made for
+    float *S = nullptr, *S2 = nullptr;     // CT: sinogram scratch
+    float *cos_t = nullptr, *sin_t = nullptr;
     cudaStream_t cs = nullptr;    // capture stream
     cudaGraphExec_t graph = nullptr;
     ReconKey key{};
@@ -377,6 +508,13 @@ static void free_buffers(ReconWork* w) {
     cudaFree(w->stop);
     cudaFree(w->epart);
     cudaFree(w->eticket);
+    cudaFree(w->S);
+    cudaFree(w->S2);
+    cudaFree(w->cos_t);
+    cudaFree(w->sin_t);
+    w->S = w->S2 = w->cos_t = w->sin_t = nullptr;
+    w->op = -1;
+    w->n_angles = 0;
     w->X = w->Z = nullptr;
     w->c = w->r = w->p = w->q = nullptr;
     w->partials = w->scal = w->epart = nullptr;
@@ -423,7 +561,9 @@ static size_t max_slots(const ReconArgs& a) {
 
 static int ensure_buffers(ReconWork* w, const ReconArgs& a, const char** msg) {
     const size_t need = max_slots(a);
-    if (w->H == a.H && w->W == a.W && w->nslots >= need) return 0;
+    if (w->H == a.H && w->W == a.W && w->nslots >= need && w->op == a.op &&
+        (a.op != RECON_CT || w->n_angles == a.n_angles))
+        return 0;
     if (w->graph) cudaGraphExecDestroy(w->graph);   // it points at the old buffers
     w->graph = nullptr;
     free_buffers(w);
@@ -444,11 +584,29 @@ static int ensure_buffers(ReconWork* w, const ReconArgs& a, const char** msg) {
     RC(cudaMalloc(&w->eticket, sizeof(unsigned)));
     RC(cudaMemset(w->eticket, 0, sizeof(unsigned)));
     w->nslots = need;
-    if (cufft_api().plan2d(&w->plan, a.H, a.W, CUFFT_C2C) != CUFFT_SUCCESS) {
-        *msg = "cufftPlan2d failed";
-        return 2;
+    if (a.op == RECON_MRI) {
+        if (cufft_api().plan2d(&w->plan, a.H, a.W, CUFFT_C2C) != CUFFT_SUCCESS) {
+            *msg = "cufftPlan2d failed";
+            return 2;
+        }
+        w->have_plan = true;
+    } else {
+        const size_t m = (size_t)a.n_angles * radon_bins(a.H, a.W);
+        RC(cudaMalloc(&w->S, m * sizeof(float)));
+        RC(cudaMalloc(&w->S2, m * sizeof(float)));
+        RC(cudaMalloc(&w->cos_t, a.n_angles * sizeof(float)));
+        RC(cudaMalloc(&w->sin_t, a.n_angles * sizeof(float)));
+        std::vector<float> ch(a.n_angles), sh(a.n_angles);
+        for (int i = 0; i < a.n_angles; ++i) {
+            const double th = 3.14159265358979323846 * i / a.n_angles;
+            ch[i] = (float)cos(th);
+            sh[i] = (float)sin(th);
+        }
+        RC(cudaMemcpy(w->cos_t, ch.data(), a.n_angles * sizeof(float), cudaMemcpyHostToDevice));
+        RC(cudaMemcpy(w->sin_t, sh.data(), a.n_angles * sizeof(float), cudaMemcpyHostToDevice));
+        w->n_angles = a.n_angles;
     }
-    w->have_plan = true;
+    w->op = a.op;
     w->H = a.H;
     w->W = a.W;
     return 0;
@@ -457,6 +615,27 @@ static int ensure_buffers(ReconWork* w, const ReconArgs& a, const char** msg) {
 static cudaError_t fft(ReconWork* w, float2* X, int dir, cudaStream_t st) {
     if (cufft_api().set_stream(w->plan, st) != CUFFT_SUCCESS) return cudaErrorUnknown;
     if (cufft_api().exec(w->plan, X, X, dir) != CUFFT_SUCCESS) return cudaErrorUnknown;
+    return cudaGetLastError();
+}
+
+int radon_bins(int H, int W) {
+    return 2 * (int)ceil(0.5 * hypot((double)(H - 1), (double)(W - 1))) + 3;
+}
+
+// CT: S <- R U (U's real parts), optionally stopped by the CG flag.
+static cudaError_t ct_forward(ReconWork* w, const ReconArgs& a, const float2* U, float* S,
+                              const int* stop, cudaStream_t st) {
+    const int D = radon_bins(a.H, a.W), m = a.n_angles * D;
+    radon_fwd_kernel<<<(m + RT - 1) / RT, RT, 0, st>>>(U, S, a.H, a.W, a.n_angles, D, w->cos_t,
+                                                       w->sin_t, stop);
+    return cudaGetLastError();
+}
+
+// CT: U <- scale R^T S.
+static cudaError_t ct_adjoint(ReconWork* w, const ReconArgs& a, const float* S, float2* U,
+                              float scale, const int* stop, cudaStream_t st) {
+    radon_adj_kernel<<<grid_for((size_t)a.H * a.W), RT, 0, st>>>(
+        S, U, a.H, a.W, a.n_angles, radon_bins(a.H, a.W), w->cos_t, w->sin_t, scale, stop);
     return cudaGetLastError();
 }
 
@@ -491,9 +670,16 @@ static cudaError_t enqueue_objective(ReconWork* w, const ReconArgs& a, cudaStrea
     const int gN = grid_for(N);
     cudaError_t e;
     to_complex_kernel<<<gN, RT, 0, st>>>(a.u, w->X, N);
-    if ((e = fft(w, w->X, CUFFT_FORWARD, st)) != cudaSuccess) return e;
-    data_term_kernel<<<gN, RT, 0, st>>>(w->X, a.kspace, a.mask, N, s, w->partials, w->ticket,
-                                        w->scal + 3);
+    if (a.op == RECON_MRI) {
+        if ((e = fft(w, w->X, CUFFT_FORWARD, st)) != cudaSuccess) return e;
+        data_term_kernel<<<gN, RT, 0, st>>>(w->X, a.kspace, a.mask, N, s, w->partials, w->ticket,
+                                            w->scal + 3);
+    } else {
+        if ((e = ct_forward(w, a, w->X, w->S, nullptr, st)) != cudaSuccess) return e;
+        const int m = a.n_angles * radon_bins(a.H, a.W);
+        sino_sq_kernel<<<grid_for((size_t)m), RT, 0, st>>>(w->S, a.sino, m, w->partials,
+                                                           w->ticket, w->scal + 3);
+    }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     // sum |kappa(u)|: the energy with f = u has no fidelity part
     if ((e = launch_energy(a.u, a.u, a.H, a.W, 1.0f, a.kind, w->epart, w->eticket, w->scal + 4,
@@ -520,18 +706,31 @@ static cudaError_t enqueue_cycle(ReconWork* w, const ReconArgs& a, cudaStream_t 
         for (int k = 0; k < nc; ++k) {
             // right-hand side: Re <b - A u, A phi_i> + 2 alpha d_i
             to_complex_kernel<<<gN, RT, 0, st>>>(a.u, w->X, N);
-            if ((e = fft(w, w->X, CUFFT_FORWARD, st)) != cudaSuccess) return e;
-            resid_kernel<<<gN, RT, 0, st>>>(w->X, a.kspace, a.mask, N, s);
-            if ((e = fft(w, w->X, CUFFT_INVERSE, st)) != cudaSuccess) return e;
+            if (a.op == RECON_MRI) {
+                if ((e = fft(w, w->X, CUFFT_FORWARD, st)) != cudaSuccess) return e;
+                resid_kernel<<<gN, RT, 0, st>>>(w->X, a.kspace, a.mask, N, s);
+                if ((e = fft(w, w->X, CUFFT_INVERSE, st)) != cudaSuccess) return e;
+            } else {
+                if ((e = ct_forward(w, a, w->X, w->S, nullptr, st)) != cudaSuccess) return e;
+                const int m = a.n_angles * radon_bins(a.H, a.W);
+                sino_resid_kernel<<<grid_for((size_t)m), RT, 0, st>>>(w->S, a.sino, m);
+                if ((e = ct_adjoint(w, a, w->S, w->X, 1.0f, nullptr, st)) != cudaSuccess) return e;
+            }
             if ((e = gather<GATHER_RHS>(w, a, b, nc, k, nslots, w->r, st)) != cudaSuccess) return e;
             if ((e = cudaMemsetAsync(w->stop, 0, sizeof(int), st)) != cudaSuccess) return e;
             for (int it = 0; it < a.cg_iters; ++it) {
                 double* rr = w->scal + (it & 1);
                 double* rr_next = w->scal + ((it + 1) & 1);
                 scatter_kernel<<<gN, RT, 0, st>>>(w->p, w->Z, a.H, a.W, b, nc, k, rr, w->stop);
-                if ((e = fft(w, w->Z, CUFFT_FORWARD, st)) != cudaSuccess) return e;
-                mask_scale_kernel<<<gN, RT, 0, st>>>(w->Z, a.mask, N, s2, w->stop);
-                if ((e = fft(w, w->Z, CUFFT_INVERSE, st)) != cudaSuccess) return e;
+                if (a.op == RECON_MRI) {
+                    if ((e = fft(w, w->Z, CUFFT_FORWARD, st)) != cudaSuccess) return e;
+                    mask_scale_kernel<<<gN, RT, 0, st>>>(w->Z, a.mask, N, s2, w->stop);
+                    if ((e = fft(w, w->Z, CUFFT_INVERSE, st)) != cudaSuccess) return e;
+                } else {
+                    if ((e = ct_forward(w, a, w->Z, w->S, w->stop, st)) != cudaSuccess) return e;
+                    if ((e = ct_adjoint(w, a, w->S, w->Z, 1.0f, w->stop, st)) != cudaSuccess)
+                        return e;
+                }
                 if ((e = gather<GATHER_Q>(w, a, b, nc, k, nslots, w->q, st)) != cudaSuccess)
                     return e;
                 cg_update_kernel<<<gs, RT, 0, st>>>(w->c, w->r, w->p, w->q, nslots, rr,
@@ -549,7 +748,7 @@ static cudaError_t enqueue_cycle(ReconWork* w, const ReconArgs& a, cudaStream_t 
 
 int recon_run(ReconWork* w, const ReconArgs& a, cudaStream_t st, const char** msg) {
     *msg = "";
-    if (!cufft_api().ok) {
+    if (a.op == RECON_MRI && !cufft_api().ok) {
         *msg = "cuFFT (libcufft.so.12) could not be loaded";
         return 2;
     }
@@ -571,9 +770,17 @@ int recon_run(ReconWork* w, const ReconArgs& a, cudaStream_t st, const char** ms
     if (a.u0) {
         if (a.u0 != a.u)
             RC(cudaMemcpyAsync(a.u, a.u0, N * sizeof(float), cudaMemcpyDeviceToDevice, st));
-    } else {   // zero-filled start Re(A^H b)
+    } else if (a.op == RECON_MRI) {   // zero-filled start Re(A^H b)
         masked_data_kernel<<<grid_for(N), RT, 0, st>>>(w->X, a.kspace, a.mask, N, s);
         RC(fft(w, w->X, CUFFT_INVERSE, st));
+        real_part_kernel<<<grid_for(N), RT, 0, st>>>(w->X, a.u, N);
+        RC(cudaGetLastError());
+    } else {   // filtered backprojection (pi / n) R^T (h * b)
+        const int D = radon_bins(a.H, a.W), m = a.n_angles * D;
+        ramp_filter_kernel<<<(m + RT - 1) / RT, RT, 0, st>>>(a.sino, w->S2, a.n_angles, D);
+        RC(cudaGetLastError());
+        RC(ct_adjoint(w, a, w->S2, w->X, 3.14159265358979323846f / (float)a.n_angles, nullptr,
+                      st));
         real_part_kernel<<<grid_for(N), RT, 0, st>>>(w->X, a.u, N);
         RC(cudaGetLastError());
     }
@@ -581,8 +788,11 @@ int recon_run(ReconWork* w, const ReconArgs& a, cudaStream_t st, const char** ms
     // one cycle as a graph, captured once per problem and reused
     ReconKey key;
     memset(&key, 0, sizeof key);   // padding included: the key is compared bytewise
+    key.op = a.op;
     key.kspace = a.kspace;
     key.mask = a.mask;
+    key.sino = a.sino;
+    key.n_angles = a.n_angles;
     key.u = a.u;
     key.trace = w->trace;
     key.H = a.H;
@@ -621,6 +831,59 @@ int recon_run(ReconWork* w, const ReconArgs& a, cudaStream_t st, const char** ms
                            cudaMemcpyDeviceToHost, st));
     RC(cudaStreamSynchronize(st));
     return 0;
+}
+
+// The operator pair alone, on temporaries (a ReconWork of its own).
+static int radon_apply(const float* in, int H, int W, int n_angles, float* out, bool adjoint,
+                       cudaStream_t st, const char** msg) {
+    *msg = "";
+    ReconWork w;
+    ReconArgs a;
+    a.op = RECON_CT;
+    a.kspace = nullptr;
+    a.mask = nullptr;
+    a.sino = nullptr;
+    a.n_angles = n_angles;
+    a.H = H;
+    a.W = W;
+    a.levels = 1;
+    a.sides = 0;
+    a.ncolors = 4;
+    int rc = ensure_buffers(&w, a, msg);
+    const size_t N = (size_t)H * W;
+    const int m = n_angles * radon_bins(H, W);
+    cudaError_t e = cudaSuccess;
+    if (rc == 0) {
+        if (!adjoint) {
+            to_complex_kernel<<<grid_for(N), RT, 0, st>>>(in, w.X, N);
+            e = cudaGetLastError();
+            if (e == cudaSuccess) e = ct_forward(&w, a, w.X, out, nullptr, st);
+        } else {
+            e = ct_adjoint(&w, a, in, w.X, 1.0f, nullptr, st);
+            if (e == cudaSuccess) {
+                real_part_kernel<<<grid_for(N), RT, 0, st>>>(w.X, out, N);
+                e = cudaGetLastError();
+            }
+        }
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) {
+            *msg = cudaGetErrorString(e);
+            rc = 2;
+        }
+    }
+    (void)m;
+    free_buffers(&w);
+    return rc;
+}
+
+int radon_forward(const float* u, int H, int W, int n_angles, float* sino, cudaStream_t st,
+                  const char** msg) {
+    return radon_apply(u, H, W, n_angles, sino, false, st, msg);
+}
+
+int radon_adjoint(const float* sino, int n_angles, int H, int W, float* u, cudaStream_t st,
+                  const char** msg) {
+    return radon_apply(sino, H, W, n_angles, u, true, st, msg);
 }
 
 }  // namespace cm

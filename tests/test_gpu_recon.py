@@ -123,3 +123,62 @@ def test_more_cycles_on_the_same_context():
     torch.cuda.synchronize()
     assert np.all(np.isfinite(t1)) and np.all(t1 > 0)
     assert np.array_equal(t1, t2) and torch.equal(u1, u2)
+
+
+# ---------------------------------------------------------------------------
+# CT: A = R, the parallel-beam Radon transform.
+
+def ct_case(H, W, n, sigma, seed):
+    clean = synth.piecewise_image(H, W, seed, 6, 0.0).clean.astype(np.float64)
+    rng = np.random.default_rng(seed)
+    sino = recon.radon_forward(clean, n)
+    sino = sino + sigma * rng.normal(size=sino.shape)
+    return clean, sino.astype(np.float32)
+
+
+def test_radon_pair_matches_oracle_and_is_adjoint():
+    H, W, n = 33, 40, 17
+    rng = np.random.default_rng(8)
+    u = rng.random((H, W), dtype=np.float32)
+    y = rng.normal(size=(n, cm.cm_radon_bins(H, W))).astype(np.float32)
+    assert cm.cm_radon_bins(H, W) == recon.radon_geometry(H, W, n)[0]
+    Ru = cm.cm_radon(torch.from_numpy(u).cuda(), n).cpu().numpy()
+    Rty = cm.cm_radon_adjoint(torch.from_numpy(y).cuda(), H, W).cpu().numpy()
+    Ru_o = recon.radon_forward(u.astype(np.float64), n)
+    Rty_o = recon.radon_adjoint(y.astype(np.float64), H, W)
+    assert np.max(np.abs(Ru - Ru_o)) <= 1e-4 * np.max(np.abs(Ru_o))
+    assert np.max(np.abs(Rty - Rty_o)) <= 1e-4 * np.max(np.abs(Rty_o))
+    lhs = np.sum(Ru.astype(np.float64) * y)
+    rhs = np.sum(u.astype(np.float64) * Rty)
+    assert lhs == pytest.approx(rhs, rel=1e-5)
+
+
+@pytest.mark.parametrize("shape", [(48, 48), (37, 52)])
+def test_ct_start_and_finest_cycle_match_oracle(shape):
+    H, W = shape
+    clean, sino = ct_case(H, W, 45, 0.1, 3 + H)
+    sd = torch.from_numpy(sino).cuda()
+    u0, t0 = cm.cm_recon_ct(sd, H, W, 1.0, cm.MEAN, cycles=0)
+    fbp = recon.fbp(sino.astype(np.float64), H, W)
+    assert np.max(np.abs(u0.cpu().numpy() - fbp)) < 1e-3
+    u, tr = cm.cm_recon_ct(sd, H, W, 1.0, cm.MEAN, levels=1, cycles=1, cg_iters=8)
+    torch.cuda.synchronize()
+    uo, tro = recon.solve_ct(sino.astype(np.float64), H, W, 1.0, cm.MEAN, levels=1, cycles=1,
+                             cg_iters=8)
+    assert np.max(np.abs(u.cpu().numpy() - uo)) < 2e-3
+    np.testing.assert_allclose(tr, tro, rtol=1e-3)
+
+
+def test_ct_full_cycles_match_oracle_and_improve_on_fbp():
+    H = W = 48
+    clean, sino = ct_case(H, W, 45, 0.1, 21)
+    sd = torch.from_numpy(sino).cuda()
+    u, tr = cm.cm_recon_ct(sd, H, W, 1.0, cm.MEAN, cycles=3, cg_iters=8)
+    torch.cuda.synchronize()
+    uo, tro = recon.solve_ct(sino.astype(np.float64), H, W, 1.0, cm.MEAN, cycles=3, cg_iters=8)
+    np.testing.assert_allclose(tr, tro, rtol=2e-3)
+    ug = u.cpu().numpy()
+    assert np.max(np.abs(ug - uo)) < 5e-3
+    assert np.all(np.diff(tr) < 0)
+    fbp = recon.fbp(sino.astype(np.float64), H, W)
+    assert synth.psnr(ug, clean) > synth.psnr(fbp, clean) + 0.3
