@@ -320,6 +320,29 @@ def recon_measurement(cm, torch, synth, ctx, dev, stream, with_oracle=True):
             "s_per_cycle": e0.elapsed_time(e1) / 1e3 / n, "cycles": n,
             "psnr_zero_filled_db": psnr0, "psnr_db": synth.psnr(u.cpu().numpy(), case.clean),
             "objective_trace": [float(x) for x in tr], "sampled_fraction": float(case.mask.mean())}
+    # CT (A = R): the phantom's sinogram from the library's own Radon
+    # transform plus seeded noise, 180 angles, the filtered backprojection as
+    # the start, alpha 1
+    side, n_ang = 256, 180
+    clean = synth.piecewise_image(side, side, synth.workload_seed(6, 7 * side), 12, 0.0).clean
+    cd = torch.from_numpy(clean).to(dev)
+    sino = cm.cm_radon(cd, n_ang, ctx=ctx)
+    rng = np.random.default_rng(side)
+    sino += torch.from_numpy((0.1 * rng.normal(size=tuple(sino.shape))).astype(np.float32)).to(dev)
+    u0, _ = cm.cm_recon_ct(sino, side, side, 1.0, cm.MEAN, cycles=0, ctx=ctx)
+    psnr0 = synth.psnr(u0.cpu().numpy(), clean)
+    cm.cm_recon_ct(sino, side, side, 1.0, cm.MEAN, cycles=1, ctx=ctx)   # builds the graph
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    u, tr = cm.cm_recon_ct(sino, side, side, 1.0, cm.MEAN, cycles=3, ctx=ctx)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    res["ct_256x256"] = {"angles": n_ang, "bins": int(sino.shape[1]), "alpha": 1.0,
+                         "noise_sigma": 0.1, "s_per_cycle": e0.elapsed_time(e1) / 1e3 / 3,
+                         "cycles": 3, "psnr_fbp_db": psnr0,
+                         "psnr_db": synth.psnr(u.cpu().numpy(), clean),
+                         "objective_trace": [float(x) for x in tr]}
     if with_oracle:
         import oracle
         from oracle import recon as orc
@@ -329,6 +352,24 @@ def recon_measurement(cm, torch, synth, ctx, dev, stream, with_oracle=True):
         res["cpu_baseline"] = {"value": time.perf_counter() - t, "unit": "s per cycle",
                                "cores": oracle.num_threads(), "kind": "oracle",
                                "sample": "one cycle of the 512^2 case (FP64, numpy FFT)"}
+        # CT oracle: one cycle of a 48^2 case with 45 angles (the 256^2 case
+        # would take tens of minutes in numpy); the GPU on the same case
+        cl48 = synth.piecewise_image(48, 48, 21, 6, 0.0).clean.astype(np.float64)
+        s48 = orc.radon_forward(cl48, 45)
+        t = time.perf_counter()
+        orc.solve_ct(s48, 48, 48, 1.0, cm.MEAN, cycles=1, cg_iters=8)
+        t_orc = time.perf_counter() - t
+        s48d = torch.from_numpy(s48.astype(np.float32)).to(dev)
+        cm.cm_recon_ct(s48d, 48, 48, 1.0, cm.MEAN, cycles=1, ctx=ctx)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        cm.cm_recon_ct(s48d, 48, 48, 1.0, cm.MEAN, cycles=3, ctx=ctx)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        res["ct_48x48_cpu_baseline"] = {"value": t_orc, "unit": "s per cycle",
+                                        "cores": oracle.num_threads(), "kind": "oracle",
+                                        "sample": "one cycle, 48^2, 45 angles",
+                                        "gpu_s_per_cycle": e0.elapsed_time(e1) / 1e3 / 3}
     return res
 
 
