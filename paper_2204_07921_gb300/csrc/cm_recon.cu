@@ -851,7 +851,6 @@ static int radon_apply(const float* in, int H, int W, int n_angles, float* out, 
     a.ncolors = 4;
     int rc = ensure_buffers(&w, a, msg);
     const size_t N = (size_t)H * W;
-    const int m = n_angles * radon_bins(H, W);
     cudaError_t e = cudaSuccess;
     if (rc == 0) {
         if (!adjoint) {
@@ -871,7 +870,6 @@ static int radon_apply(const float* in, int H, int W, int n_angles, float* out, 
             rc = 2;
         }
     }
-    (void)m;
     free_buffers(&w);
     return rc;
 }

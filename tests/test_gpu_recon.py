@@ -1,5 +1,5 @@
-"""GPU parity of the reconstruction extension (Sec. 5, A = M F) against the
-FP64 oracle in oracle/recon.py.
+"""GPU parity of the reconstruction extension (Sec. 5: MRI-like A = M F, and
+CT with the Radon pair) against the FP64 oracle in oracle/recon.py.
 
 Tolerances: the GPU runs the same algorithm in FP32 (cuFFT single precision,
 FP32 CG vectors, FP64 reductions), the oracle in FP64.  One FFT round trip
