@@ -61,6 +61,8 @@ def parse():
                    help="skip the reconstruction (Sec. 5) measurement")
     p.add_argument("--recon-only", action="store_true",
                    help="only run 2 reconstruction cycles at --side (for profiling)")
+    p.add_argument("--ct-only", action="store_true",
+                   help="only run 2 CT reconstruction cycles at --side, 180 angles (profiling)")
     p.add_argument("--cnn-only", action="store_true",
                    help="profiling aid: warm-start inference on 16 x 1024^2 images and exit")
     p.add_argument("--phases-only", action="store_true",
@@ -392,6 +394,14 @@ def main():
         dist.init_process_group("nccl", device_id=dev)
     cm.load()
     ctx = cm.Context(local)
+    if args.ct_only:
+        clean = synth.piecewise_image(args.side, args.side, synth.workload_seed(6, 7 * args.side),
+                                      12, 0.0).clean
+        sino = cm.cm_radon(torch.from_numpy(clean).to(dev), 180, ctx=ctx)
+        u, tr = cm.cm_recon_ct(sino, args.side, args.side, 1.0, cm.MEAN, cycles=2, ctx=ctx)
+        torch.cuda.synchronize()
+        print(json.dumps({"ct_only": True, "side": args.side, "trace": list(tr)}))
+        return
     if args.recon_only:
         case = synth.mri_case(args.side, args.side, synth.workload_seed(6, args.side),
                               accel=3.0, sigma=0.01)

@@ -365,10 +365,13 @@ __global__ void __launch_bounds__(RT) radon_fwd_kernel(const float2* __restrict_
     const int outer = rows ? H : W, inner = rows ? W : H;
     const float slope = rows ? c : sv, other = rows ? sv : c;
     const float off_in = 0.5f * (float)(inner - 1), off_out = 0.5f * (float)(outer - 1);
+    // the window needs no exact division: it is one pixel wider on each side
+    // than the interval, and membership is decided by radon_pos itself
+    const float inv = 1.0f / slope;
     float acc = 0.0f;
     for (int o = 0; o < outer; ++o) {
         const float base = fmaf((float)o - off_out, other, half);
-        float x0 = ((float)(j - 1) - base) / slope, x1 = ((float)(j + 1) - base) / slope;
+        float x0 = ((float)(j - 1) - base) * inv, x1 = ((float)(j + 1) - base) * inv;
         if (x0 > x1) {
             const float t = x0;
             x0 = x1;
