@@ -371,6 +371,24 @@ cudaError_t capture_solve(cm_ctx* ctx, float* u, float* Y, const float* f, int H
 
 }  // namespace
 
+// Shared tail of cm_recon and cm_recon_ct: levels from the options, the
+// context's reconstruction buffers, the run and its status.
+int run_recon(cm_ctx* ctx, cm::ReconArgs& a, int levels, const cm_options& o, void* stream,
+              const char* name) {
+    const int L = solve_levels(levels, a.H, a.W, o);
+    if (!levels_ok(L, o)) return fail(ctx, CM_ERR_INVALID, std::string(name) + ": too many levels");
+    CM_CUDA(cudaSetDevice(ctx->device));
+    if (!ctx->recon) ctx->recon = cm::recon_work_create();
+    a.levels = L;
+    a.sides = o.block_sides;
+    a.ncolors = o.ncolors;
+    const char* msg = "";
+    const int rc = cm::recon_run(ctx->recon, a, (cudaStream_t)stream, &msg);
+    if (rc == 3) return fail(ctx, CM_ERR_OOM, std::string(name) + ": " + msg);
+    if (rc) return fail(ctx, CM_ERR_CUDA, std::string(name) + ": " + msg);
+    return CM_OK;
+}
+
 extern "C" {
 
 int cm_options_default(cm_options* o) {
@@ -953,10 +971,6 @@ int cm_recon(cm_ctx* ctx, const float* kspace, const unsigned char* mask, int H,
         !valid_kind(kind) || levels < 0 || cycles < 0 || cycles > 100000 || cg_iters < 1 ||
         cg_iters > 1000 || (const void*)u_out == (const void*)kspace)
         return fail(ctx, CM_ERR_INVALID, "cm_recon: invalid argument");
-    const int L = solve_levels(levels, H, W, o);
-    if (!levels_ok(L, o)) return fail(ctx, CM_ERR_INVALID, "cm_recon: too many levels");
-    CM_CUDA(cudaSetDevice(ctx->device));
-    if (!ctx->recon) ctx->recon = cm::recon_work_create();
     cm::ReconArgs a;
     a.op = cm::RECON_MRI;
     a.kspace = (const float2*)kspace;
@@ -967,19 +981,12 @@ int cm_recon(cm_ctx* ctx, const float* kspace, const unsigned char* mask, int H,
     a.W = W;
     a.alpha = alpha;
     a.kind = kind;
-    a.levels = L;
-    a.sides = o.block_sides;
-    a.ncolors = o.ncolors;
     a.cycles = cycles;
     a.cg_iters = cg_iters;
     a.u0 = u0;
     a.u = u_out;
     a.trace_host = trace_host;
-    const char* msg = "";
-    rc = cm::recon_run(ctx->recon, a, (cudaStream_t)stream, &msg);
-    if (rc == 3) return fail(ctx, CM_ERR_OOM, std::string("cm_recon: ") + msg);
-    if (rc) return fail(ctx, CM_ERR_CUDA, std::string("cm_recon: ") + msg);
-    return CM_OK;
+    return run_recon(ctx, a, levels, o, stream, "cm_recon");
 }
 
 int cm_radon_bins(int H, int W) { return (H < 1 || W < 1) ? -1 : cm::radon_bins(H, W); }
@@ -1023,10 +1030,6 @@ int cm_recon_ct(cm_ctx* ctx, const float* sino, int n_angles, int H, int W, floa
         cycles > 100000 || cg_iters < 1 || cg_iters > 1000 ||
         (const void*)u_out == (const void*)sino)
         return fail(ctx, CM_ERR_INVALID, "cm_recon_ct: invalid argument");
-    const int L = solve_levels(levels, H, W, o);
-    if (!levels_ok(L, o)) return fail(ctx, CM_ERR_INVALID, "cm_recon_ct: too many levels");
-    CM_CUDA(cudaSetDevice(ctx->device));
-    if (!ctx->recon) ctx->recon = cm::recon_work_create();
     cm::ReconArgs a;
     a.op = cm::RECON_CT;
     a.kspace = nullptr;
@@ -1037,19 +1040,12 @@ int cm_recon_ct(cm_ctx* ctx, const float* sino, int n_angles, int H, int W, floa
     a.W = W;
     a.alpha = alpha;
     a.kind = kind;
-    a.levels = L;
-    a.sides = o.block_sides;
-    a.ncolors = o.ncolors;
     a.cycles = cycles;
     a.cg_iters = cg_iters;
     a.u0 = u0;
     a.u = u_out;
     a.trace_host = trace_host;
-    const char* msg = "";
-    rc = cm::recon_run(ctx->recon, a, (cudaStream_t)stream, &msg);
-    if (rc == 3) return fail(ctx, CM_ERR_OOM, std::string("cm_recon_ct: ") + msg);
-    if (rc) return fail(ctx, CM_ERR_CUDA, std::string("cm_recon_ct: ") + msg);
-    return CM_OK;
+    return run_recon(ctx, a, levels, o, stream, "cm_recon_ct");
 }
 
 }  // extern "C"
