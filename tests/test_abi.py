@@ -75,3 +75,20 @@ def test_auto_levels_agree_with_oracle():
     import paper_2204_07921_gb300 as cm
     for H, W in [(64, 64), (512, 512), (1024, 1024), (67, 45), (1, 1), (3, 100), (130, 97)]:
         assert cm.cm_auto_levels(H, W) == oracle.auto_levels(H, W)
+
+
+def test_header_is_plain_c(tmp_path):
+    """include/cm.h compiles as C99 with warnings as errors (a C ABI, not a
+    C++ one)."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "use_cm.c"
+    src.write_text('#include "cm.h"\nint main(void) { cm_options o; '
+                   'return cm_options_default(&o); }\n')
+    r = subprocess.run([cc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror",
+                        "-fsyntax-only", "-I", HEADER_DIR, str(src)],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
