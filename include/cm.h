@@ -223,7 +223,7 @@ int cm_solve_batched(cm_ctx* ctx, int n, const float* const* f, const int* H, co
 /* ---------------------------------------------------------------------------
  * Learned warm start (not in the paper): a small CNN maps f to an initial
  * u0 for the sweep, which then runs from u0 and is both the fallback and the
- * judge of the network's output.  Network: six 3x3 convolutions with zero
+ * arbiter of the network's output.  Network: six 3x3 convolutions with zero
  * padding, channels 1 -> 32 -> 32 -> 32 -> 32 -> 32 -> 1, ReLU after the first
  * five, residual output u0 = f + conv6(...).  BF16 weights and activations,
  * FP32 accumulation (the 32 -> 32 layers on the tensor cores).

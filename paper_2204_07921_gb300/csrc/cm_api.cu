@@ -701,7 +701,7 @@ int cm_warmstart(cm_ctx* ctx, cm_net* net, const float* f, int N, int H, int W, 
         for (int n = 0; n < N; ++n) {
             const float* fi = f + n * npx;
             float* ui = u0_out + n * npx;
-            // the sweep's energy judges the network: keep u0 only if F(u0) <= F(f)
+            // the sweep's energy decides on the network's output: keep u0 only if F(u0) <= F(f)
             CM_CUDA(cm::launch_energy(ui, fi, H, W, alpha, kind, ctx->partials, ctx->ticket,
                                       &ctx->E_dev[0], st));
             CM_CUDA(cm::launch_energy(fi, fi, H, W, alpha, kind, ctx->partials, ctx->ticket,

@@ -355,9 +355,9 @@ __device__ __forceinline__ void golden_put(GoldenState& st, bool left, float x, 
 // evaluates up to 16 candidates with one reduction: lane j of each warp
 // generates candidate j as `mine`, and round(mine, m) returns in lane l the
 // ring sum of candidate l / 2.
-//   round 1: c = 0 and c_fid;
-//   round 2: the grid points other than c_fid and, when they fit, the first
-//            golden pair of every grid point that may win (else the grid in
+//   the first round: c = 0 and c_fid;
+//   the second: the grid points other than c_fid and, when they fit, the
+//            first golden pair of every grid point that may win (else the grid in
 //            chunks of 16 and the pair in a round of its own);
 //   then golden rounds of up to dmax <= 4 steps, which evaluate the
 //   2^dmax - 1 points of every outcome path of the next dmax comparisons.
@@ -413,7 +413,7 @@ __device__ __forceinline__ float block_search_rounds(RoundFn&& round, const Sear
         consider(b1, c1, energy(c1, __shfl_sync(FULL, t1, 2)));
         return b1.c;
     }
-    // round 1: c = 0, c_fid
+    // the first round: c = 0, c_fid
     float mine = lane == 1 ? c_fid : 0.0f;
     float tot = round(mine, 2);
     Best best;
