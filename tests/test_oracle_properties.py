@@ -1,6 +1,7 @@
-"""Property-based pins of the oracle (hypothesis): the identities of the
-fixed-example pins, drawn over random images, blocks, shifts and all four
-curvature kinds."""
+"""Property-based pins of the oracle (hypothesis, deterministic draws): the
+identities of the fixed-example pins, drawn over random images, blocks,
+shifts and all four curvature kinds, and the reconstruction operators'
+adjoint identities over random shapes, masks and angle counts."""
 import math
 
 import numpy as np
@@ -93,3 +94,34 @@ def test_block_search_never_raises_the_local_energy(img, kind, data):
     E0 = oracle.local_energy(u, f, r0, c0, bh, bw, 0.0, 15.0, kind)
     Ec = oracle.local_energy(u, f, r0, c0, bh, bw, c, 15.0, kind)
     assert Ec <= E0 + 1e-12 * (1.0 + abs(E0))
+
+
+@settings(max_examples=40, deadline=None, derandomize=True)
+@given(images(1, 12), st.integers(1, 40), st.integers(0, 2 ** 31 - 1))
+def test_radon_pair_is_adjoint_and_keeps_mass(img, n, seed):
+    """<R u, y> = <u, R^T y>, and every angle's projection sums to the image's
+    sum, for any shape and angle count (every p lies inside the detector)."""
+    from oracle import recon
+    u, _ = img
+    H, W = u.shape
+    D = recon.radon_geometry(H, W, n)[0]
+    y = np.random.default_rng(seed).normal(size=(n, D))
+    Ru = recon.radon_forward(u, n)
+    assert np.sum(Ru * y) == pytest.approx(np.sum(u * recon.radon_adjoint(y, H, W)),
+                                           rel=1e-10, abs=1e-10)
+    np.testing.assert_allclose(Ru.sum(axis=1), u.sum(), rtol=1e-12)
+
+
+@settings(max_examples=40, deadline=None, derandomize=True)
+@given(images(1, 12), st.floats(0.05, 1.0), st.integers(0, 2 ** 31 - 1))
+def test_mri_operator_is_adjoint_and_contractive(img, frac, seed):
+    from oracle import recon
+    u, _ = img
+    H, W = u.shape
+    rng = np.random.default_rng(seed)
+    mask = (rng.random((H, W)) < frac).astype(float)
+    y = rng.normal(size=(H, W)) + 1j * rng.normal(size=(H, W))
+    Au = recon.forward(u, mask)
+    assert np.vdot(y, Au) == pytest.approx(np.vdot(recon.adjoint(y, mask), u), rel=1e-10,
+                                           abs=1e-10)
+    assert np.linalg.norm(Au) <= np.linalg.norm(u) * (1 + 1e-12)
