@@ -801,3 +801,45 @@ def test_solve_two_coarse_colours_vs_oracle_and_loops():
                                  tol=0.0, options=opts)
     for (ua, sa), u2, s2 in zip(res[0], ub, sb):
         assert torch.equal(ua, u2) and sa.trace() == s2.trace()
+
+
+# ---------------------------------------------------------------------------
+# Option combinations.
+
+@pytest.mark.parametrize("sides,coarse", [(0, 2), (1, 0), (1, 2)])
+def test_batched_equals_single_with_combined_options(sides, coarse):
+    """All four curvature kinds in one batch, with the paper's block sides
+    and/or two coarse colours: every image bit-identical to its own solve."""
+    shapes = [(300, 260), (140, 150), (200, 130), (96, 160)]
+    fs = [to_dev(synth.piecewise_image(H, W, 500 + H, 8, 0.08).f) for H, W in shapes]
+    kinds = [cm.MEAN, cm.GAUSS, cm.MEAN_EULER, cm.GAUSS_EULER]
+    alphas = [20.0, 15.0, 20.0, 15.0]
+    opts = cm.default_options(ncolors=4, block_sides=sides)
+    opts.coarse_ncolors = coarse
+    ub, sb = cm.cm_solve_batched(fs, alphas, kinds, cycles=40, tol=1e-4, options=opts)
+    torch.cuda.synchronize()
+    for i, fd in enumerate(fs):
+        us, ss = cm.cm_solve(fd, alphas[i], kinds[i], cycles=40, tol=1e-4, options=opts)
+        torch.cuda.synchronize()
+        assert torch.equal(ub[i], us)
+        assert sb[i].trace() == ss.trace() and sb[i].cycles_run == ss.cycles_run
+
+
+@pytest.mark.parametrize("kind", [cm.MEAN_EULER, cm.GAUSS_EULER])
+def test_one_step_phase_parity_euler_kinds(kind):
+    """The single-step mode on every level and colour with the Euler-fit
+    kinds (the paper's candidate of the base kind on the finest level)."""
+    H, W = 130, 97
+    img = synth.piecewise_image(H, W, 811, 6, 0.1)
+    f = img.f
+    u = oracle.cycle(f.astype(np.float64), f.astype(np.float64), 20.0, kind, levels=1,
+                     ncolors=4).astype(np.float32)
+    tot = np.zeros(3, int)
+    fails = []
+    for b in levels_for(H, W):
+        for k in range(4):
+            n, m, t, fl = check_phase(u, f, 20.0, kind, b, 4, k, one_step=True)
+            tot += (n, m, t)
+            fails += fl
+    assert not fails, fails[:5]
+    assert tot[2] <= max(2, 0.02 * tot[0])
