@@ -25,6 +25,8 @@ _BUILD = os.path.join(_HERE, "_build")
 _SO = os.path.join(_BUILD, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
+# ring(c, ctx) -> sum over the block's ring of |kappa_q(u + c phi_A)|
+_RING_FN = ctypes.CFUNCTYPE(ctypes.c_double, ctypes.c_double, ctypes.c_void_p)
 
 MEAN, GAUSS = 0, 1
 # Extension: principal curvatures from a least-squares fit of Euler's formula
@@ -77,6 +79,7 @@ def lib():
                 "orc_chalf_map": (None, [dp, i, i, i, dp]),
                 "orc_num_threads": (i, []),
                 "orc_local_energy_batch": (None, [dp, dp, i, i, i, i, i, i, d, i, dp, i, dp]),
+                "orc_block_search": (d, [d, d, d, i, i, i, d, _RING_FN, ctypes.c_void_p, dp]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(L, name)
@@ -166,6 +169,35 @@ def block_min(u, f, r0, c0, bh, bw, alpha, kind, G=DEFAULT_G, K=DEFAULT_K, use_p
         finest = bh == 1 and bw == 1
     c = lib().orc_block_min(_dp(u), _dp(f), H, W, r0, c0, bh, bw, float(alpha), kind, G, K,
                             int(use_paper), int(one_step), int(finest), _dp(info))
+    keys = ("E_best", "E_zero", "c_fid", "rho", "S1", "n_eval")
+    return c, dict(zip(keys, info.tolist()))
+
+
+def block_search(s, S1, alpha, ring, G=DEFAULT_G, K=DEFAULT_K, one_step=False, cand=None):
+    """The steps of block_min for a block seen only through s = |A|,
+    S1 = sum_A (u - f) and ring(c), a callable returning the ring sum
+    sum_{q in ring(A)} |kappa_q(u + c phi_A)| (e.g. assembled from the partial
+    sums of several row strips); cand: the closed-form candidate (the
+    paper's c_1 on the finest level) or None.  ring is called in the search's
+    own order, the same on every caller.  Returns (c, info) as block_min."""
+    err = []
+
+    def cb(c, _ctx):
+        if err:
+            return 0.0
+        try:
+            return float(ring(c))
+        except BaseException as e:   # noqa: BLE001 -- re-raised below
+            err.append(e)
+            return 0.0
+
+    fn = _RING_FN(cb)
+    info = np.zeros(6)
+    c = lib().orc_block_search(float(s), float(S1), float(alpha), G, K, int(one_step),
+                               float("nan") if cand is None else float(cand), fn, None,
+                               _dp(info))
+    if err:
+        raise err[0]
     keys = ("E_best", "E_zero", "c_fid", "rho", "S1", "n_eval")
     return c, dict(zip(keys, info.tolist()))
 

@@ -381,6 +381,99 @@ typedef struct {
     int n_eval;
 } blockres_t;
 
+/* The search sees the block only through s, S1 and its ring sum
+ * R(c) = sum_{q in ring(A)} |kappa_q(u + c phi_A)|, so that the same steps
+ * serve a block whose ring is summed by several owners (each adds the ring
+ * pixels of its rows).  cand: the closed-form candidate (the paper's c_1 on
+ * the finest level), or NaN for none. */
+typedef double (*ring_fn)(double c, void *ctx);
+
+static double search_energy(double s, double S1, double alpha, double c, ring_fn ring,
+                            void *ctx) {
+    return 0.5 * alpha * (s * c * c + 2.0 * c * S1) + ring(c, ctx);
+}
+
+static blockres_t block_search(double s, double S1, double alpha, int G, int K, int one_step,
+                               double cand, ring_fn ring, void *ctx) {
+    blockres_t res;
+    double c_fid = -S1 / s;
+    best_t b;
+    b.c = 0.0;
+    b.E = search_energy(s, S1, alpha, 0.0, ring, ctx);
+    b.n_eval = 1;
+    double E0 = b.E;
+    if (one_step) {
+        /* One step of Alg. 2 (t = 0, c_0 = 0, eta = 1): c_1 = (c_1/2 + alpha f*) /
+         * (2 + alpha), f* = c_fid the block's mean of f - u.  On the finest level
+         * c_1/2 is the plane-distance estimate (Eq. c-sol1; Prop. 2 for Gaussian
+         * curvature), passed in as cand; on coarser levels READING: c_1/2 = 0
+         * (the paper's coarse tangent-plane sets are not recoverable).  The
+         * block keeps c_1 only if it lowers E_A (tie rule as below), else 0. */
+        double c1 = cand == cand ? cand : alpha * c_fid / (2.0 + alpha);
+        consider(&b, c1, search_energy(s, S1, alpha, c1, ring, ctx));
+        res.c = b.c;
+        res.E_best = b.E;
+        res.E_zero = E0;
+        res.c_fid = c_fid;
+        res.rho = 0.0;
+        res.S1 = S1;
+        res.n_eval = b.n_eval;
+        return res;
+    }
+    if (cand == cand) consider(&b, cand, search_energy(s, S1, alpha, cand, ring, ctx));
+    double Rk = ring(c_fid, ctx);
+    double rho = sqrt(2.0 * Rk / (alpha * s));
+    /* grid */
+    double gbest = c_fid, Egbest = INFINITY;
+    for (int i = 0; i < G; ++i) {
+        double g = c_fid + rho * (2.0 * i / (double)(G - 1) - 1.0);
+        double E = search_energy(s, S1, alpha, g, ring, ctx);
+        consider(&b, g, E);
+        if (E < Egbest) { Egbest = E; gbest = g; }
+    }
+    /* golden section */
+    double D = 2.0 * rho / (double)(G - 1);
+    const double phi = 0.5 * (sqrt(5.0) - 1.0);
+    double lo = gbest - D, hi = gbest + D;
+    double x1 = hi - phi * (hi - lo), x2 = lo + phi * (hi - lo);
+    double E1 = search_energy(s, S1, alpha, x1, ring, ctx);
+    double E2 = search_energy(s, S1, alpha, x2, ring, ctx);
+    consider(&b, x1, E1);
+    consider(&b, x2, E2);
+    for (int k = 2; k < K; ++k) {
+        if (E1 < E2) {
+            hi = x2; x2 = x1; E2 = E1;
+            x1 = hi - phi * (hi - lo);
+            E1 = search_energy(s, S1, alpha, x1, ring, ctx);
+            consider(&b, x1, E1);
+        } else {
+            lo = x1; x1 = x2; E1 = E2;
+            x2 = lo + phi * (hi - lo);
+            E2 = search_energy(s, S1, alpha, x2, ring, ctx);
+            consider(&b, x2, E2);
+        }
+    }
+    res.c = b.c;
+    res.E_best = b.E;
+    res.E_zero = E0;
+    res.c_fid = c_fid;
+    res.rho = rho;
+    res.S1 = S1;
+    res.n_eval = b.n_eval;
+    return res;
+}
+
+typedef struct {
+    const double *u;
+    int H, W, kind;
+    const block_t *A;
+} image_ring_t;
+
+static double image_ring(double c, void *ctx) {
+    const image_ring_t *r = (const image_ring_t *)ctx;
+    return ring_curv_sum(r->u, r->H, r->W, r->A, c, r->kind);
+}
+
 /* Block minimiser.  The paper solves the 1-D problem approximately with a
  * closed-form FBS step (Alg. 2, Eq. c-sol2, and the coarse closed form of
  * Sec. 2.2); the objective of each subproblem is min_c F(u + c phi_A)
@@ -394,86 +487,35 @@ typedef struct {
  *        best grid point and D the grid step.
  *  (v)   also c = 0 and, on the finest layer, the paper's c_1 above.
  *  (vi)  the result is the best of every evaluated point (tie rule above),
- *        so E_A(c) <= E_A(0): no block update raises F with the others fixed. */
+ *        so E_A(c) <= E_A(0): no block update raises F with the others fixed.
+ * READING: the paper's closed-form candidate (Alg. 2, Eq. c-sol1) is the
+ * pixel step of the finest level; a 1 x 1 block clipped at the image corner
+ * on a coarser level is not a level-1 pixel and gets the search alone. */
 static blockres_t block_min(const double *u, const double *f, int H, int W, const block_t *A,
                             double alpha, int kind, int G, int K, int use_paper, int one_step,
                             int finest) {
-    blockres_t res;
     double s = (double)(A->r1 - A->r0) * (double)(A->c1 - A->c0);
     double S1 = block_S1(u, f, W, A);
-    double c_fid = -S1 / s;
-    best_t b;
-    b.c = 0.0;
-    b.E = local_energy(u, H, W, A, 0.0, alpha, kind, S1);
-    b.n_eval = 1;
-    double E0 = b.E;
-    if (one_step) {
-        /* One step of Alg. 2 (t = 0, c_0 = 0, eta = 1): c_1 = (c_1/2 + alpha f*) /
-         * (2 + alpha), f* = c_fid the block's mean of f - u.  On the finest level
-         * c_1/2 is the plane-distance estimate (Eq. c-sol1; Prop. 2 for Gaussian
-         * curvature); on coarser levels READING: c_1/2 = 0 (the paper's coarse
-         * tangent-plane sets are not recoverable).  The block keeps c_1 only if
-         * it lowers E_A (tie rule as below), else 0. */
-        double c1 = finest && A->r1 - A->r0 == 1 && A->c1 - A->c0 == 1
-                        ? orc_paper_candidate(u, f, H, W, A->r0, A->c0, alpha, kind)
-                        : alpha * c_fid / (2.0 + alpha);
-        consider(&b, c1, local_energy(u, H, W, A, c1, alpha, kind, S1));
-        res.c = b.c;
-        res.E_best = b.E;
-        res.E_zero = E0;
-        res.c_fid = c_fid;
-        res.rho = 0.0;
-        res.S1 = S1;
-        res.n_eval = b.n_eval;
-        return res;
+    int pixel = finest && A->r1 - A->r0 == 1 && A->c1 - A->c0 == 1;
+    double cand = NAN;
+    if (pixel && (one_step || use_paper))
+        cand = orc_paper_candidate(u, f, H, W, A->r0, A->c0, alpha, kind);
+    image_ring_t ctx = {u, H, W, kind, A};
+    return block_search(s, S1, alpha, G, K, one_step, cand, image_ring, &ctx);
+}
+
+/* The search alone, for a block whose ring sum the caller assembles (e.g.
+ * from the partial sums of several row strips): s = |A|, S1 = sum_A (u - f),
+ * ring(c) = sum_{q in ring(A)} |kappa_q(u + c phi_A)|, cand = the closed-form
+ * candidate or NaN.  info as in orc_block_min. */
+double orc_block_search(double s, double S1, double alpha, int G, int K, int one_step,
+                        double cand, double (*ring)(double, void *), void *ctx, double *info) {
+    blockres_t res = block_search(s, S1, alpha, G, K, one_step, cand, ring, ctx);
+    if (info) {
+        info[0] = res.E_best; info[1] = res.E_zero; info[2] = res.c_fid;
+        info[3] = res.rho; info[4] = res.S1; info[5] = (double)res.n_eval;
     }
-    /* READING: the paper's closed-form candidate (Alg. 2, Eq. c-sol1) is the
-     * pixel step of the finest level; a 1 x 1 block clipped at the image corner
-     * on a coarser level is not a level-1 pixel and gets the search alone. */
-    if (use_paper && finest && A->r1 - A->r0 == 1 && A->c1 - A->c0 == 1) {
-        double cp = orc_paper_candidate(u, f, H, W, A->r0, A->c0, alpha, kind);
-        consider(&b, cp, local_energy(u, H, W, A, cp, alpha, kind, S1));
-    }
-    double Rk = ring_curv_sum(u, H, W, A, c_fid, kind);
-    double rho = sqrt(2.0 * Rk / (alpha * s));
-    /* grid */
-    double gbest = c_fid, Egbest = INFINITY;
-    for (int i = 0; i < G; ++i) {
-        double g = c_fid + rho * (2.0 * i / (double)(G - 1) - 1.0);
-        double E = local_energy(u, H, W, A, g, alpha, kind, S1);
-        consider(&b, g, E);
-        if (E < Egbest) { Egbest = E; gbest = g; }
-    }
-    /* golden section */
-    double D = 2.0 * rho / (double)(G - 1);
-    const double phi = 0.5 * (sqrt(5.0) - 1.0);
-    double lo = gbest - D, hi = gbest + D;
-    double x1 = hi - phi * (hi - lo), x2 = lo + phi * (hi - lo);
-    double E1 = local_energy(u, H, W, A, x1, alpha, kind, S1);
-    double E2 = local_energy(u, H, W, A, x2, alpha, kind, S1);
-    consider(&b, x1, E1);
-    consider(&b, x2, E2);
-    for (int k = 2; k < K; ++k) {
-        if (E1 < E2) {
-            hi = x2; x2 = x1; E2 = E1;
-            x1 = hi - phi * (hi - lo);
-            E1 = local_energy(u, H, W, A, x1, alpha, kind, S1);
-            consider(&b, x1, E1);
-        } else {
-            lo = x1; x1 = x2; E1 = E2;
-            x2 = lo + phi * (hi - lo);
-            E2 = local_energy(u, H, W, A, x2, alpha, kind, S1);
-            consider(&b, x2, E2);
-        }
-    }
-    res.c = b.c;
-    res.E_best = b.E;
-    res.E_zero = E0;
-    res.c_fid = c_fid;
-    res.rho = rho;
-    res.S1 = S1;
-    res.n_eval = b.n_eval;
-    return res;
+    return res.c;
 }
 
 double orc_block_min(const double *u, const double *f, int H, int W, int r0, int c0, int bh,
