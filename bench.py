@@ -170,7 +170,7 @@ def oracle_cycle_seconds(f64, n_cycles: int):
 
 
 def run_reference(args):
-    """The reference arm of this build is the FP64 oracle, run as it stands
+    """The reference arm is the FP64 oracle, run as it stands
     on the host cores: one full solve to tol 1e-4 (its own cycle count and
     time), then warm-up and timed single-cycle samples; value = mean cycle
     time x the oracle's cycle count."""
