@@ -18,8 +18,9 @@
  * tri) and hand geometry, curvature against sphere caps and paraboloids
  * (closed forms, O(h^2) order), affine/constant invariants, D4 and
  * translation invariance, the ring-energy identity against the full energy
- * difference, brute-force block minimisation on 8x8 images, and monotone
- * descent in sequential mode.
+ * difference, brute-force block minimisation on 8x8 images, the search
+ * with a caller-supplied ring sum (orc_block_search) against the whole-image
+ * search, and monotone descent in sequential mode.
  */
 #include <math.h>
 #include <stdint.h>

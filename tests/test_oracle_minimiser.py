@@ -1,7 +1,8 @@
 """Pins of the oracle's block subproblem (Sec. 2.2, Alg. 3) and sweep.
 
 The ring-only local energy is pinned to the full energy difference, the
-block search to brute force, the phase to its snapshot definition, and the
+block search to brute force (and, handed its ring sum by the caller, to
+itself on the whole image), the phase to its snapshot definition, and the
 whole sweep to monotone descent in sequential (Gauss-Seidel) order.
 """
 import numpy as np
@@ -326,3 +327,43 @@ def test_one_step_sequential_levels_never_raise_energy(kind):
         E1 = oracle.energy(u, f, 10.0, kind)
         assert E1 <= E + 1e-9 * abs(E)
         E = E1
+
+
+@pytest.mark.parametrize("kind", KINDS)
+@pytest.mark.parametrize("one_step", [False, True])
+def test_search_with_a_supplied_ring_sum_is_block_min(kind, one_step):
+    """The search seen only through s, S1 and the ring sum (the form a block
+    split over row strips uses, the ring sum assembled by the caller) picks
+    the same shift as block_min after the same number of evaluations; the
+    ring sum it is handed here is the full energy difference less the
+    fidelity part, computed from the whole image."""
+    H, W, alpha = 14, 12, 9.0
+    u = rand_img(H, W, 40 + kind)
+    f = rand_img(H, W, 50 + kind, smooth=False)
+    for b in (1, 2, 3, 5):
+        for _, _, r0, c0, bh, bw in blocks_of(H, W, b):
+            c, info = oracle.block_min(u, f, r0, c0, bh, bw, alpha, kind, one_step=one_step,
+                                       finest=(b == 1))
+            s = bh * bw
+            S1 = float(np.sum(u[r0:r0 + bh, c0:c0 + bw] - f[r0:r0 + bh, c0:c0 + bw]))
+            F0 = oracle.energy(u, f, alpha, kind)
+            curv0 = F0 - 0.5 * alpha * float(np.sum((u - f) ** 2))
+            calls = []
+
+            def ring(cc):
+                v = u.copy()
+                v[r0:r0 + bh, c0:c0 + bw] += cc
+                calls.append(cc)
+                ring0 = oracle.local_energy(u, f, r0, c0, bh, bw, 0.0, alpha, kind)
+                # sum over ring(A) of |kappa(v)| = (total |kappa(v)|) - (the rest,
+                # unchanged by the shift) = curv(v) - (curv0 - ring0 at c = 0)
+                curv = np.sum(np.abs(oracle.curvature_map(v, kind)))
+                return curv - (curv0 - ring0)
+
+            cand = oracle.paper_candidate(u, f, r0, c0, alpha, kind) if b == 1 else None
+            c2, info2 = oracle.block_search(s, S1, alpha, ring, one_step=one_step, cand=cand)
+            assert c2 == pytest.approx(c, abs=1e-9), (b, r0, c0)
+            assert info2["n_eval"] == info["n_eval"]
+            # ring evaluations: E(0), E at every considered point, and (the
+            # search) the bracket's ring sum at c_fid
+            assert len(calls) == info["n_eval"] + (0 if one_step else 1)
