@@ -64,6 +64,25 @@ def test_levels_reduce_iterations():
     assert tL[-1] <= t1[-1] * (1 + 1e-3)
 
 
+def test_cycle_count_does_not_grow_with_the_image():
+    """Table "linear" trend: with every level down to blocks of half the
+    image side, the cycles to the relative-energy tolerance stay in a narrow
+    band as the pixel count grows 16-fold (32^2 to 128^2, two images of
+    each size from the same generator), so the cost grows with the pixels
+    alone."""
+    counts = {}
+    for side in (32, 64, 128):
+        counts[side] = []
+        for i in (0, 1):
+            f = synth.large(side, i).f.astype(np.float64)
+            _, _, n, conv = oracle.solve(f, 20.0, oracle.MEAN, cycles=200, tol=1e-4, ncolors=4)
+            assert conv
+            counts[side].append(n)
+    flat = [n for v in counts.values() for n in v]
+    assert max(flat) - min(flat) <= 3, counts
+    assert max(counts[128]) <= min(counts[32]) + 3, counts
+
+
 def test_denoising_improves_psnr():
     """The minimiser of the curvature energy removes noise: PSNR against the
     clean synthetic image rises (Sec. 4 measures PSNR)."""
