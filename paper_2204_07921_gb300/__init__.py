@@ -130,13 +130,43 @@ def _stream_ptr(stream=None) -> int:
     return int(s.cuda_stream)
 
 
-def _img(t, name):
+def _on_gpu(t) -> bool:
+    return t.is_cuda
+
+
+def _img(t, name, shape=None, like=None):
+    """Checks that t is a contiguous CUDA float32 matrix (of `shape`, on the
+    device of `like`) before its pointer reaches the library, which trusts
+    the sizes it is given."""
     import torch
-    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float32:
+    if not isinstance(t, torch.Tensor) or not _on_gpu(t) or t.dtype != torch.float32:
         raise TypeError(f"{name}: expected a CUDA float32 tensor")
     if t.dim() != 2 or not t.is_contiguous():
         raise ValueError(f"{name}: expected a contiguous H x W tensor")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name}: expected shape {tuple(shape)}, got {tuple(t.shape)}")
+    if like is not None and t.device != like.device:
+        raise ValueError(f"{name}: on {t.device}, expected {like.device}")
     return t
+
+
+def _blocks_out(c_out, H, W, b, like):
+    """c_out of cm_phase / cm_level: CUDA float32, one entry per block of the
+    level (ceil(H / b) x ceil(W / b)); None passes through."""
+    import torch
+    if c_out is None:
+        return None
+    if not (isinstance(c_out, torch.Tensor) and _on_gpu(c_out) and c_out.dtype == torch.float32
+            and c_out.is_contiguous()):
+        raise TypeError("c_out: expected a contiguous CUDA float32 tensor")
+    if b < 1:
+        raise ValueError("b: expected a block side >= 1")
+    nb = ((H + b - 1) // b) * ((W + b - 1) // b)
+    if c_out.numel() < nb:
+        raise ValueError(f"c_out: {c_out.numel()} entries, the level has {nb} blocks")
+    if c_out.device != like.device:
+        raise ValueError(f"c_out: on {c_out.device}, expected {like.device}")
+    return c_out.data_ptr()
 
 
 class Context:
@@ -187,9 +217,8 @@ def _ctx(ctx: Context | None, t) -> Context:
 
 def cm_energy(u, f, alpha: float, kind: int, ctx: Context | None = None, stream=None) -> float:
     """F(u) of Eq. (MCM)/(GCM), FP64 device reduction."""
-    _img(u, "u"), _img(f, "f")
-    if u.shape != f.shape:
-        raise ValueError("u and f differ in shape")
+    _img(u, "u")
+    _img(f, "f", u.shape, u)
     c = _ctx(ctx, u)
     H, W = u.shape
     E = ctypes.c_double(0.0)
@@ -221,12 +250,13 @@ def cm_energy_noalloc(u, f, alpha: float, kind: int, E_out, stream=None):
     """F(u) into the one-element float64 CUDA tensor E_out, without any
     device allocation (the library's fixed scratch array; see include/cm.h)."""
     import torch
-    _img(u, "u"), _img(f, "f")
-    if u.shape != f.shape:
-        raise ValueError("u and f differ in shape")
-    if not (isinstance(E_out, torch.Tensor) and E_out.is_cuda and E_out.dtype == torch.float64
-            and E_out.numel() >= 1):
+    _img(u, "u")
+    _img(f, "f", u.shape, u)
+    if not (isinstance(E_out, torch.Tensor) and _on_gpu(E_out) and
+            E_out.dtype == torch.float64 and E_out.numel() >= 1):
         raise TypeError("E_out: expected a CUDA float64 tensor")
+    if E_out.device != u.device:
+        raise ValueError(f"E_out: on {E_out.device}, expected {u.device}")
     H, W = u.shape
     rc = load().cm_energy_noalloc(u.data_ptr(), f.data_ptr(), H, W, float(alpha), kind,
                                   E_out.data_ptr(), _stream_ptr(stream))
@@ -238,7 +268,7 @@ def cm_energy_noalloc(u, f, alpha: float, kind: int, E_out, stream=None):
 def cm_curvature(u, kind: int, out=None, ctx: Context | None = None, stream=None):
     import torch
     _img(u, "u")
-    out = torch.empty_like(u) if out is None else _img(out, "out")
+    out = torch.empty_like(u) if out is None else _img(out, "out", u.shape, u)
     c = _ctx(ctx, u)
     H, W = u.shape
     c._check(load().cm_curvature(c.handle, u.data_ptr(), H, W, kind, out.data_ptr(),
@@ -249,14 +279,15 @@ def cm_curvature(u, kind: int, out=None, ctx: Context | None = None, stream=None
 def cm_phase(S, R, f, alpha: float, kind: int, b: int, colour: int, options: Options | None = None,
              c_out=None, ctx: Context | None = None, stream=None):
     """One (level, colour) phase: writes R on the colour's blocks."""
-    for t, n in ((S, "S"), (R, "R"), (f, "f")):
-        _img(t, n)
-    c = _ctx(ctx, S)
+    _img(S, "S")
     H, W = S.shape
+    _img(R, "R", S.shape, S)
+    _img(f, "f", S.shape, S)
+    cp = _blocks_out(c_out, H, W, b, S)
+    c = _ctx(ctx, S)
     opts = options or default_options()
     c._check(load().cm_phase(c.handle, S.data_ptr(), R.data_ptr(), f.data_ptr(), H, W,
-                             float(alpha), kind, b, colour, ctypes.byref(opts),
-                             c_out.data_ptr() if c_out is not None else None,
+                             float(alpha), kind, b, colour, ctypes.byref(opts), cp,
                              _stream_ptr(stream)))
     return R
 
@@ -264,14 +295,15 @@ def cm_phase(S, R, f, alpha: float, kind: int, b: int, colour: int, options: Opt
 def cm_level(S, R, f, alpha: float, kind: int, b: int, options: Options | None = None,
              c_out=None, ctx: Context | None = None, stream=None):
     """One whole level (every colour) from state S; R receives the new state."""
-    for t, n in ((S, "S"), (R, "R"), (f, "f")):
-        _img(t, n)
-    c = _ctx(ctx, S)
+    _img(S, "S")
     H, W = S.shape
+    _img(R, "R", S.shape, S)
+    _img(f, "f", S.shape, S)
+    cp = _blocks_out(c_out, H, W, b, S)
+    c = _ctx(ctx, S)
     opts = options or default_options()
     c._check(load().cm_level(c.handle, S.data_ptr(), R.data_ptr(), f.data_ptr(), H, W,
-                             float(alpha), kind, b, ctypes.byref(opts),
-                             c_out.data_ptr() if c_out is not None else None,
+                             float(alpha), kind, b, ctypes.byref(opts), cp,
                              _stream_ptr(stream)))
     return R
 
@@ -282,13 +314,13 @@ def cm_solve(f, alpha: float, kind: int, levels: int = 0, cycles: int = 20, tol:
     """Alg. 3 solve on the device.  Returns (u_out, Stats)."""
     import torch
     _img(f, "f")
-    c = _ctx(ctx, f)
     H, W = f.shape
     if u_out is None:
         u_out = torch.empty_like(f)
-    _img(u_out, "u_out")
+    _img(u_out, "u_out", f.shape, f)
     if u0 is not None:
-        _img(u0, "u0")
+        _img(u0, "u0", f.shape, f)
+    c = _ctx(ctx, f)
     opts = options or default_options()
     st = Stats()
     c._check(load().cm_solve(c.handle, f.data_ptr(), H, W, float(alpha), kind, levels, cycles,
@@ -307,19 +339,23 @@ def cm_recon(kspace, mask, alpha: float, kind: int = MEAN, levels: int = 0, cycl
     (u_out, trace of J: before the first cycle and after each)."""
     import numpy as np
     import torch
-    if not (isinstance(kspace, torch.Tensor) and kspace.is_cuda and
+    if not (isinstance(kspace, torch.Tensor) and _on_gpu(kspace) and
             kspace.dtype == torch.complex64 and kspace.dim() == 2 and kspace.is_contiguous()):
         raise TypeError("kspace: expected a contiguous CUDA complex64 H x W tensor")
-    if not (isinstance(mask, torch.Tensor) and mask.is_cuda and mask.dtype == torch.uint8 and
-            mask.shape == kspace.shape and mask.is_contiguous()):
-        raise TypeError("mask: expected a contiguous CUDA uint8 tensor of the data's shape")
+    if not (isinstance(mask, torch.Tensor) and _on_gpu(mask) and mask.dtype == torch.uint8 and
+            mask.shape == kspace.shape and mask.is_contiguous() and
+            mask.device == kspace.device):
+        raise TypeError("mask: expected a contiguous CUDA uint8 tensor of the data's shape "
+                        "and device")
     H, W = kspace.shape
-    c = _ctx(ctx, kspace)
     if u_out is None:
         u_out = torch.empty((H, W), dtype=torch.float32, device=kspace.device)
-    _img(u_out, "u_out")
+    _img(u_out, "u_out", (H, W), kspace)
     if u0 is not None:
-        _img(u0, "u0")
+        _img(u0, "u0", (H, W), kspace)
+    if cycles < 0:
+        raise ValueError("cycles: expected >= 0")
+    c = _ctx(ctx, kspace)
     opts = options or default_options()
     trace = np.zeros(cycles + 1)
     c._check(load().cm_recon(c.handle, kspace.data_ptr(), mask.data_ptr(), H, W, float(alpha),
@@ -335,10 +371,23 @@ def cm_radon_bins(H: int, W: int) -> int:
     return load().cm_radon_bins(H, W)
 
 
+def _sinogram(sino, H, W):
+    """sino: n_angles x cm_radon_bins(H, W), n_angles >= 1."""
+    _img(sino, "sino")
+    if H < 1 or W < 1:
+        raise ValueError("H, W: expected >= 1")
+    D = cm_radon_bins(H, W)
+    if sino.shape[0] < 1 or sino.shape[1] != D:
+        raise ValueError(f"sino: expected n_angles x {D} for a {H} x {W} image, "
+                         f"got {tuple(sino.shape)}")
+
+
 def cm_radon(u, n_angles: int, ctx: Context | None = None, stream=None):
     """sino = R u (n_angles x cm_radon_bins(H, W))."""
     import torch
     _img(u, "u")
+    if n_angles < 1:
+        raise ValueError("n_angles: expected >= 1")
     c = _ctx(ctx, u)
     H, W = u.shape
     sino = torch.empty((n_angles, cm_radon_bins(H, W)), dtype=torch.float32, device=u.device)
@@ -350,7 +399,7 @@ def cm_radon(u, n_angles: int, ctx: Context | None = None, stream=None):
 def cm_radon_adjoint(sino, H: int, W: int, ctx: Context | None = None, stream=None):
     """u = R^T sino."""
     import torch
-    _img(sino, "sino")
+    _sinogram(sino, H, W)
     c = _ctx(ctx, sino)
     u = torch.empty((H, W), dtype=torch.float32, device=sino.device)
     c._check(load().cm_radon_adjoint(c.handle, sino.data_ptr(), sino.shape[0], H, W,
@@ -365,13 +414,15 @@ def cm_recon_ct(sino, H: int, W: int, alpha: float, kind: int = MEAN, levels: in
     Returns (u_out, trace of J)."""
     import numpy as np
     import torch
-    _img(sino, "sino")
-    c = _ctx(ctx, sino)
+    _sinogram(sino, H, W)
     if u_out is None:
         u_out = torch.empty((H, W), dtype=torch.float32, device=sino.device)
-    _img(u_out, "u_out")
+    _img(u_out, "u_out", (H, W), sino)
     if u0 is not None:
-        _img(u0, "u0")
+        _img(u0, "u0", (H, W), sino)
+    if cycles < 0:
+        raise ValueError("cycles: expected >= 0")
+    c = _ctx(ctx, sino)
     opts = options or default_options()
     trace = np.zeros(cycles + 1)
     c._check(load().cm_recon_ct(c.handle, sino.data_ptr(), sino.shape[0], H, W, float(alpha),
@@ -391,10 +442,19 @@ def cm_solve_batched(fs, alphas, kinds, levels: int = 0, cycles: int = 2000, tol
     n = len(fs)
     if n == 0:
         return [], []
+    if len(alphas) != n or len(kinds) != n:
+        raise ValueError(f"alphas, kinds: expected {n} entries each, got {len(alphas)} and "
+                         f"{len(kinds)}")
     for i, t in enumerate(fs):
-        _img(t, f"f[{i}]")
+        _img(t, f"f[{i}]", like=fs[0])
     if u_outs is None:
         u_outs = [torch.empty_like(t) for t in fs]
+    if len(u_outs) != n or (u0s is not None and len(u0s) != n):
+        raise ValueError(f"u_outs, u0s: expected {n} entries")
+    for i in range(n):
+        _img(u_outs[i], f"u_outs[{i}]", fs[i].shape, fs[0])
+        if u0s is not None and u0s[i] is not None:
+            _img(u0s[i], f"u0s[{i}]", fs[i].shape, fs[0])
     c = _ctx(ctx, fs[0])
     PA = _P * n
     f_arr = PA(*[t.data_ptr() for t in fs])

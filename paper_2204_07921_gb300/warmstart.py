@@ -86,15 +86,23 @@ def init_params(seed: int, zero_last: bool = True) -> np.ndarray:
     return p
 
 
-def _batch(t):
+def _batch(t, name="f", shape=None, like=None):
+    """(t, N, H, W) of a contiguous CUDA float32 batch, (H, W) or (N, H, W),
+    checked against `shape` and the device of `like` when given, before its
+    pointer reaches the library, which trusts the sizes it is given."""
     import torch
-    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float32
+    from . import _on_gpu
+    if not (isinstance(t, torch.Tensor) and _on_gpu(t) and t.dtype == torch.float32
             and t.is_contiguous()):
-        raise TypeError("expected a contiguous CUDA float32 tensor")
+        raise TypeError(f"{name}: expected a contiguous CUDA float32 tensor")
+    if t.dim() not in (2, 3):
+        raise ValueError(f"{name}: expected (H, W) or (N, H, W)")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name}: expected shape {tuple(shape)}, got {tuple(t.shape)}")
+    if like is not None and t.device != like.device:
+        raise ValueError(f"{name}: on {t.device}, expected {like.device}")
     if t.dim() == 2:
         return t, 1, t.shape[0], t.shape[1]
-    if t.dim() != 3:
-        raise ValueError("expected (H, W) or (N, H, W)")
     return t, t.shape[0], t.shape[1], t.shape[2]
 
 
@@ -140,13 +148,14 @@ class Net:
     def forward(self, f, out=None, stream=None):
         import torch
         f, N, H, W = _batch(f)
-        out = torch.empty_like(f) if out is None else out
+        out = torch.empty_like(f) if out is None else _batch(out, "out", f.shape, f)[0]
         self._check(_lib().cm_net_forward(self._h, f.data_ptr(), N, H, W, out.data_ptr(),
                                           _stream_ptr(stream)))
         return out
 
     def gradients(self, f, ustar, stream=None):
         f, N, H, W = _batch(f)
+        _batch(ustar, "ustar", f.shape, f)
         g = np.zeros(N_PARAMS, np.float32)
         loss = ctypes.c_double()
         self._check(_lib().cm_net_gradients(self._h, f.data_ptr(), ustar.data_ptr(), N, H, W,
@@ -156,6 +165,7 @@ class Net:
 
     def train_step(self, f, ustar, lr: float, want_loss: bool = True, stream=None):
         f, N, H, W = _batch(f)
+        _batch(ustar, "ustar", f.shape, f)
         loss = ctypes.c_double()
         self._check(_lib().cm_net_train_step(self._h, f.data_ptr(), ustar.data_ptr(), N, H, W,
                                              float(lr), ctypes.byref(loss) if want_loss else None,
@@ -167,8 +177,8 @@ class Net:
                      log_every: int = 100, stream=None) -> dict:
         """The library's training loop (cm_net_train) on the pairs F, U
         (N x H x W); returns the log (losses with their schedule steps)."""
-        F, N, H, W = _batch(F)
-        U, _, _, _ = _batch(U)
+        F, N, H, W = _batch(F, "F")
+        U, _, _, _ = _batch(U, "U", F.shape, F)
         o = TrainOpts(steps=steps, batch=batch, lr=lr, lr_final=lr_final, total_steps=total_steps,
                       start_step=start_step, seed=seed, log_every=log_every)
         cap = steps // log_every + 2
@@ -204,7 +214,7 @@ def warmstart(net: Net, f, alpha: float, kind: int, check_energy: bool = True, o
     if F(u0) <= F(f).  Returns (u0, used flags)."""
     import torch
     f, N, H, W = _batch(f)
-    out = torch.empty_like(f) if out is None else out
+    out = torch.empty_like(f) if out is None else _batch(out, "out", f.shape, f)[0]
     used = (_I * N)()
     rc = _lib().cm_warmstart(net.ctx.handle, net._h, f.data_ptr(), N, H, W, out.data_ptr(),
                              int(check_energy), float(alpha), int(kind), used,
