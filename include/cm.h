@@ -50,12 +50,18 @@ extern "C" {
 
 /* Status codes. */
 #define CM_OK 0
-#define CM_ERR_INVALID 1     /* null pointer, size < 1, alpha <= 0 or non-finite, bad kind/option */
+#define CM_ERR_INVALID 1     /* null pointer, size out of range, alpha <= 0 or non-finite, bad kind/option */
 #define CM_ERR_CUDA 2        /* a CUDA runtime call failed (message in cm_last_error) */
 #define CM_ERR_OOM 3         /* scratch allocation failed */
 #define CM_ERR_TIMEOUT 4     /* a device-side wait hit its iteration limit */
 #define CM_ERR_NUMERIC 5     /* NaN or Inf energy */
 #define CM_NOT_CONVERGED 6   /* cycle cap reached with tol > 0; u_out is still valid */
+
+/* Image sizes: 1 .. CM_MAX_SIDE rows and columns and at most CM_MAX_PIXELS
+ * pixels per image (8 GiB of FP32; block and tile counts are int).  Larger
+ * images are rejected with CM_ERR_INVALID (cm_radon_bins returns -1). */
+#define CM_MAX_SIDE (1 << 20)
+#define CM_MAX_PIXELS 2147483647LL
 
 #define CM_KIND_MEAN 0
 #define CM_KIND_GAUSS 1

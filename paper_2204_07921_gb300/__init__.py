@@ -368,7 +368,10 @@ def cm_recon(kspace, mask, alpha: float, kind: int = MEAN, levels: int = 0, cycl
 
 def cm_radon_bins(H: int, W: int) -> int:
     """Detector bins of the CT geometry."""
-    return load().cm_radon_bins(H, W)
+    D = load().cm_radon_bins(H, W)
+    if D < 0:
+        raise ValueError(f"image size {H} x {W} out of range")
+    return D
 
 
 def _sinogram(sino, H, W):

@@ -166,6 +166,11 @@ int ensure_solve_state(cm_ctx* ctx) {
 }
 
 bool finite_positive(float a) { return isfinite(a) && a > 0.0f; }
+// Image sizes the kernels index within (include/cm.h: CM_MAX_SIDE, CM_MAX_PIXELS).
+bool dims_ok(int H, int W) {
+    return H >= 1 && W >= 1 && H <= CM_MAX_SIDE && W <= CM_MAX_SIDE &&
+           (long long)H * W <= CM_MAX_PIXELS;
+}
 // Curvature kinds: 0 mean, 1 Gaussian (extreme directions), 2 mean, 3 Gaussian
 // (Euler fit).
 bool valid_kind(int kind) { return kind >= 0 && kind <= 3; }
@@ -471,7 +476,7 @@ const char* cm_last_error(const cm_ctx* ctx) { return ctx ? ctx->err.c_str() : "
 int cm_energy(cm_ctx* ctx, const float* u, const float* f, int H, int W, float alpha, int kind,
               double* E_host, void* stream) {
     if (!ctx) return CM_ERR_INVALID;
-    if (!u || !f || !E_host || H < 1 || W < 1 || !finite_positive(alpha) || !valid_kind(kind))
+    if (!u || !f || !E_host || !dims_ok(H, W) || !finite_positive(alpha) || !valid_kind(kind))
         return fail(ctx, CM_ERR_INVALID, "cm_energy: invalid argument");
     CM_CUDA(cudaSetDevice(ctx->device));
     int rc = ensure_partials(ctx, H, W);
@@ -487,7 +492,7 @@ int cm_energy(cm_ctx* ctx, const float* u, const float* f, int H, int W, float a
 
 int cm_curvature(cm_ctx* ctx, const float* u, int H, int W, int kind, float* out, void* stream) {
     if (!ctx) return CM_ERR_INVALID;
-    if (!u || !out || H < 1 || W < 1 || !valid_kind(kind))
+    if (!u || !out || !dims_ok(H, W) || !valid_kind(kind))
         return fail(ctx, CM_ERR_INVALID, "cm_curvature: invalid argument");
     CM_CUDA(cudaSetDevice(ctx->device));
     CM_CUDA(cm::launch_curvature(u, H, W, kind, out, (cudaStream_t)stream));
@@ -502,7 +507,7 @@ int cm_phase(cm_ctx* ctx, const float* S, float* R, const float* f, int H, int W
     if (opts) o = *opts;
     int rc = check_opts(ctx, o);
     if (rc) return rc;
-    if (!S || !R || !f || R == S || R == f || H < 1 || W < 1 || !finite_positive(alpha) ||
+    if (!S || !R || !f || R == S || R == f || !dims_ok(H, W) || !finite_positive(alpha) ||
         !valid_kind(kind))
         return fail(ctx, CM_ERR_INVALID, "cm_phase: invalid argument");
     if (side_lb(b) < 0)
@@ -524,7 +529,7 @@ int cm_level(cm_ctx* ctx, const float* S, float* R, const float* f, int H, int W
     if (opts) o = *opts;
     int rc = check_opts(ctx, o);
     if (rc) return rc;
-    if (!S || !R || !f || R == S || R == f || H < 1 || W < 1 || !finite_positive(alpha) ||
+    if (!S || !R || !f || R == S || R == f || !dims_ok(H, W) || !finite_positive(alpha) ||
         !valid_kind(kind))
         return fail(ctx, CM_ERR_INVALID, "cm_level: invalid argument");
     if (side_lb(b) < 0)
@@ -546,7 +551,7 @@ int cm_solve(cm_ctx* ctx, const float* f, int H, int W, float alpha, int kind, i
     if (opts) o = *opts;
     int rc = check_opts(ctx, o);
     if (rc) return rc;
-    if (!f || !u_out || u_out == f || H < 1 || W < 1 || !finite_positive(alpha) ||
+    if (!f || !u_out || u_out == f || !dims_ok(H, W) || !finite_positive(alpha) ||
         !valid_kind(kind) || levels < 0 || cycles < 0 || !(tol >= 0.0) || !isfinite(tol))
         return fail(ctx, CM_ERR_INVALID, "cm_solve: invalid argument");
     const int L = solve_levels(levels, H, W, o);
@@ -686,7 +691,7 @@ int cm_solve(cm_ctx* ctx, const float* f, int H, int W, float alpha, int kind, i
 int cm_warmstart(cm_ctx* ctx, cm_net* net, const float* f, int N, int H, int W, float* u0_out,
                  int check_energy, float alpha, int kind, int* used_host, void* stream) {
     if (!ctx) return CM_ERR_INVALID;
-    if (!net || !f || !u0_out || u0_out == f || N < 1 || H < 1 || W < 1 ||
+    if (!net || !f || !u0_out || u0_out == f || N < 1 || !dims_ok(H, W) ||
         (check_energy && (!finite_positive(alpha) || !valid_kind(kind))))
         return fail(ctx, CM_ERR_INVALID, "cm_warmstart: invalid argument");
     CM_CUDA(cudaSetDevice(ctx->device));
@@ -752,7 +757,7 @@ int cm_solve_batched(cm_ctx* ctx, int n, const float* const* f, const int* H, co
         !(tol >= 0.0) || !isfinite(tol))
         return fail(ctx, CM_ERR_INVALID, "cm_solve_batched: invalid argument");
     for (int i = 0; i < n; ++i) {
-        if (!f[i] || !u_out[i] || u_out[i] == f[i] || H[i] < 1 || W[i] < 1 ||
+        if (!f[i] || !u_out[i] || u_out[i] == f[i] || !dims_ok(H[i], W[i]) ||
             !finite_positive(alpha[i]) || !valid_kind(kind[i]))
             return fail(ctx, CM_ERR_INVALID, "cm_solve_batched: invalid image " + std::to_string(i));
         const int L = solve_levels(levels, H[i], W[i], o);
@@ -967,7 +972,7 @@ int cm_recon(cm_ctx* ctx, const float* kspace, const unsigned char* mask, int H,
     if (opts) o = *opts;
     int rc = check_opts(ctx, o);
     if (rc) return rc;
-    if (!kspace || !mask || !u_out || H < 1 || W < 1 || !finite_positive(alpha) ||
+    if (!kspace || !mask || !u_out || !dims_ok(H, W) || !finite_positive(alpha) ||
         !valid_kind(kind) || levels < 0 || cycles < 0 || cycles > 100000 || cg_iters < 1 ||
         cg_iters > 1000 || (const void*)u_out == (const void*)kspace)
         return fail(ctx, CM_ERR_INVALID, "cm_recon: invalid argument");
@@ -989,12 +994,12 @@ int cm_recon(cm_ctx* ctx, const float* kspace, const unsigned char* mask, int H,
     return run_recon(ctx, a, levels, o, stream, "cm_recon");
 }
 
-int cm_radon_bins(int H, int W) { return (H < 1 || W < 1) ? -1 : cm::radon_bins(H, W); }
+int cm_radon_bins(int H, int W) { return dims_ok(H, W) ? cm::radon_bins(H, W) : -1; }
 
 int cm_radon(cm_ctx* ctx, const float* u, int H, int W, int n_angles, float* sino,
              void* stream) {
     if (!ctx) return CM_ERR_INVALID;
-    if (!u || !sino || H < 1 || W < 1 || n_angles < 1 || n_angles > 100000)
+    if (!u || !sino || !dims_ok(H, W) || n_angles < 1 || n_angles > 100000)
         return fail(ctx, CM_ERR_INVALID, "cm_radon: invalid argument");
     CM_CUDA(cudaSetDevice(ctx->device));
     const char* msg = "";
@@ -1006,7 +1011,7 @@ int cm_radon(cm_ctx* ctx, const float* u, int H, int W, int n_angles, float* sin
 int cm_radon_adjoint(cm_ctx* ctx, const float* sino, int n_angles, int H, int W, float* u,
                      void* stream) {
     if (!ctx) return CM_ERR_INVALID;
-    if (!u || !sino || H < 1 || W < 1 || n_angles < 1 || n_angles > 100000)
+    if (!u || !sino || !dims_ok(H, W) || n_angles < 1 || n_angles > 100000)
         return fail(ctx, CM_ERR_INVALID, "cm_radon_adjoint: invalid argument");
     CM_CUDA(cudaSetDevice(ctx->device));
     const char* msg = "";
@@ -1025,7 +1030,7 @@ int cm_recon_ct(cm_ctx* ctx, const float* sino, int n_angles, int H, int W, floa
     if (opts) o = *opts;
     int rc = check_opts(ctx, o);
     if (rc) return rc;
-    if (!sino || !u_out || H < 1 || W < 1 || n_angles < 1 || n_angles > 100000 ||
+    if (!sino || !u_out || !dims_ok(H, W) || n_angles < 1 || n_angles > 100000 ||
         !finite_positive(alpha) || !valid_kind(kind) || levels < 0 || cycles < 0 ||
         cycles > 100000 || cg_iters < 1 || cg_iters > 1000 ||
         (const void*)u_out == (const void*)sino)

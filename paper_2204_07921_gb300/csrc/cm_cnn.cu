@@ -1099,7 +1099,8 @@ int backward(Net* net, const float* f, const float* us, int N, int H, int W, cud
 }
 
 int check_images(Net* net, const float* f, int N, int H, int W) {
-    if (!f || N < 1 || H < 1 || W < 1) {
+    if (!f || N < 1 || H < 1 || W < 1 || H > CM_MAX_SIDE || W > CM_MAX_SIDE ||
+        (long long)H * W > CM_MAX_PIXELS) {
         net->err = "invalid image arguments";
         return CM_ERR_INVALID;
     }
@@ -1414,7 +1415,8 @@ static void batch_indices(uint64_t seed, long long t, int N, int batch, std::vec
 
 int cm_net_train(cm_ctx* ctx, cm_net* net, const float* f, const float* ustar, int N, int H,
                  int W, const cm_train_opts* o, cm_train_log* log, void* stream) {
-    if (!ctx || !net || !f || !ustar || !o || N < 1 || H < 1 || W < 1 || o->steps < 1 ||
+    if (!ctx || !net || !f || !ustar || !o || N < 1 || H < 1 || W < 1 || H > CM_MAX_SIDE ||
+        W > CM_MAX_SIDE || (long long)H * W > CM_MAX_PIXELS || o->steps < 1 ||
         o->batch < 1 || o->batch > N || !(o->lr > 0.0f) || !(o->lr_final > 0.0f) ||
         o->start_step < 0 || o->log_every < 1 || o->total_steps < 0 ||
         (o->total_steps > 0 && o->start_step + o->steps > o->total_steps))

@@ -61,6 +61,27 @@ def test_host_only_entry_points():
     assert lib.cm_last_error(None) == b"null context"
 
 
+def test_image_size_limits():
+    """Images of 1 .. CM_MAX_SIDE rows and columns and at most CM_MAX_PIXELS
+    pixels are accepted; the host-only cm_radon_bins shows the same rule
+    the entry points apply before any CUDA call."""
+    import numpy as np
+    import paper_2204_07921_gb300 as cm
+    text = open(os.path.join(HEADER_DIR, "cm.h")).read()
+    assert re.search(r"#define CM_MAX_SIDE \(1 << 20\)", text)
+    assert re.search(r"#define CM_MAX_PIXELS 2147483647LL", text)
+    lib = cm.load()
+    side, pixels = 1 << 20, 2 ** 31 - 1
+    for H, W in ((1, 1), (side, 1), (1, side), (side, 2047), (46340, 46340)):
+        assert H * W <= pixels
+        assert lib.cm_radon_bins(H, W) == 2 * int(np.ceil(np.hypot(H - 1, W - 1) / 2)) + 3
+    for H, W in ((0, 5), (5, 0), (-1, 5), (side + 1, 1), (1, side + 1), (side, 2048),
+                 (46341, 46341), (50000, 50000)):
+        assert lib.cm_radon_bins(H, W) == -1, (H, W)
+    with pytest.raises(ValueError):
+        cm.cm_radon_bins(50000, 50000)
+
+
 def test_default_budget_agrees_with_oracle():
     """Parity tests rely on the library and the oracle using the same
     default search budget."""
