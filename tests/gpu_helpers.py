@@ -15,8 +15,6 @@ Tolerances, derived from FP32 arithmetic:
   1e-5 times the block's energy scale (ring curvature plus fidelity distance,
   both non-negative).  Ties are counted and reported.
 """
-import numpy as np
-
 import oracle
 
 TIE_REL = 1e-5

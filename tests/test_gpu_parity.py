@@ -14,7 +14,7 @@ if not torch.cuda.is_available():
 import oracle  # noqa: E402
 import paper_2204_07921_gb300 as cm  # noqa: E402
 import synth  # noqa: E402
-from gpu_helpers import C_TOL, G_DEF, K_DEF, blocks_of_colour, compare_phase  # noqa: E402
+from gpu_helpers import G_DEF, K_DEF, blocks_of_colour, compare_phase  # noqa: E402
 
 pytestmark = pytest.mark.gpu
 DEV = torch.device("cuda:0")

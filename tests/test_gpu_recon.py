@@ -14,7 +14,6 @@ import pytest
 
 torch = pytest.importorskip("torch")
 
-import oracle  # noqa: E402
 import paper_2204_07921_gb300 as cm  # noqa: E402
 import synth  # noqa: E402
 from oracle import recon  # noqa: E402

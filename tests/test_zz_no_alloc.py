@@ -8,7 +8,6 @@ last so that a stop at its first failure has already run every other test.
 """
 import ctypes
 
-import numpy as np
 import pytest
 
 torch = pytest.importorskip("torch")
