@@ -58,6 +58,7 @@ constexpr int OFF_W6 = 9 * C + C + 4 * (MIDW + C);
 constexpr int OFF_B6 = OFF_W6 + 9 * C;
 constexpr int NPAR = OFF_B6 + 1;
 static_assert(NPAR == 37601, "parameter count");
+static_assert(OFF_B1 + C == off_w(2) && OFF_W1 + 9 * C == OFF_B1, "layer 1: weights, bias");
 constexpr int DW_STRIDE = MIDW + C;            // one CTA partial of a 32 -> 32 layer
 constexpr int DW_GRID = 2 * 152;               // CTAs of the weight-gradient kernels
 
