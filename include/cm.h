@@ -356,8 +356,11 @@ int cm_energy_noalloc(const float* u, const float* f, int H, int W, float alpha,
  * The transforms are cuFFT, loaded on first use (CM_ERR_CUDA with a message
  * if libcufft.so.12 cannot be loaded); the scratch (two complex images and
  * the CG vectors) stays in the context.  Synchronises `stream`.  Returns
- * CM_ERR_INVALID for null pointers, sizes < 1, a bad alpha, kind or option,
- * cycles outside 0 .. 100000 or cg_iters outside 1 .. 1000. */
+ * CM_ERR_INVALID for null pointers, sizes out of range (CM_MAX_SIDE,
+ * CM_MAX_PIXELS), u_out aliasing kspace, a bad alpha, kind or option, cycles
+ * outside 0 .. 100000 or cg_iters outside 1 .. 1000; CM_ERR_OOM when the
+ * scratch cannot be allocated; CM_ERR_CUDA otherwise on a failed CUDA or
+ * cuFFT call. */
 int cm_recon(cm_ctx* ctx, const float* kspace, const unsigned char* mask, int H, int W,
              float alpha, int kind, int levels, int cycles, int cg_iters, const float* u0,
              float* u_out, const cm_options* opts /* host, nullable */,
@@ -377,7 +380,11 @@ int cm_recon(cm_ctx* ctx, const float* kspace, const unsigned char* mask, int H,
  * R^T (h * b), h the Ram-Lak kernel (h[0] = 1/4, h[k] = -1/(pi k)^2 for odd k,
  * 0 for even k, a direct convolution per angle).  trace_host as in
  * cm_recon; the CG and colour options as in cm_recon.  Needs no cuFFT.
- * Synchronises `stream`. */
+ * Synchronises `stream`.  Returns CM_ERR_INVALID for null pointers, sizes out
+ * of range, n_angles outside 1 .. 100000, u_out aliasing sino, a bad alpha,
+ * kind or option, cycles outside 0 .. 100000 or cg_iters outside 1 .. 1000;
+ * CM_ERR_OOM or CM_ERR_CUDA as cm_recon.  cm_radon_bins is host-only: D, or
+ * -1 for sizes out of range. */
 int cm_radon_bins(int H, int W);
 int cm_recon_ct(cm_ctx* ctx, const float* sino, int n_angles, int H, int W, float alpha,
                 int kind, int levels, int cycles, int cg_iters, const float* u0, float* u_out,
@@ -385,7 +392,10 @@ int cm_recon_ct(cm_ctx* ctx, const float* sino, int n_angles, int H, int W, floa
                 double* trace_host /* host, nullable */, void* stream);
 /* The CT operator pair alone: sino = R u (n_angles x D), u = R^T sino (the
  * exact transpose: both are gathers with the same weights).  Device
- * pointers; temporaries are allocated and freed; synchronise `stream`. */
+ * pointers, caller-owned: u is H x W and sino n_angles x D, both row-major
+ * float32; temporaries are allocated and freed; synchronise `stream`.
+ * Return CM_ERR_INVALID for null pointers, sizes out of range or n_angles
+ * outside 1 .. 100000, CM_ERR_OOM, or CM_ERR_CUDA. */
 int cm_radon(cm_ctx* ctx, const float* u, int H, int W, int n_angles, float* sino,
              void* stream);
 int cm_radon_adjoint(cm_ctx* ctx, const float* sino, int n_angles, int H, int W, float* u,
