@@ -278,6 +278,16 @@ def batched_measurement(cm, torch, synth, ctx, dev, rank=0, world=1):
     return res
 
 
+def kernels_per_cycle(opts, L):
+    """Kernels of one solve cycle over levels b = 1, 2, .. 2^(L-1): one per
+    colour on the levels below the coarse threshold (b < 64); one per colour
+    and the apply on the coarse levels, plus the tile sums before the first;
+    the energy; the device stopping test."""
+    return 2 + sum(level_colours(opts, 1 << j) +
+                   (0 if j < COARSE_LB else (2 if j == COARSE_LB else 1))
+                   for j in range(L))
+
+
 def level_colours(opts, b):
     """Colours of the level of block side b under the options (the library's
     rule: coarse_ncolors on b >= 64 when set, the decoupled count for
@@ -736,15 +746,10 @@ def main():
                          f"extrapolated x {mean_cycles:g} cycles of the plain sweep to tol",
                "per_cycle_s": per_cycle}
 
-    # kernels per cycle: one per colour on levels below the coarse threshold
-    # (b < 64); one per colour + apply on coarse levels (+ tile sums on the
-    # first); energy; the device stopping test
-    kernels_per_cycle = 2 + sum(level_colours(opts, 1 << j) +
-                                (0 if j < COARSE_LB else (2 if j == COARSE_LB else 1))
-                                for j in range(L))
     # per warm step: 6 network kernels, 2 energy checks, then the solve graph
     # (initial energy, state initialisation, the cycles)
-    launches_per_solve = [8 + 2 + c * kernels_per_cycle for c in cycles]
+    per_cycle = kernels_per_cycle(opts, L)
+    launches_per_solve = [8 + 2 + c * per_cycle for c in cycles]
     line = {"metric": METRIC, "value": sec_per_solve, "unit": "s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec_per_solve * 1e3,
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32",

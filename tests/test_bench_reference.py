@@ -45,3 +45,23 @@ def test_reference_other_ranks_exit_without_work():
     p = _run({"RANK": "1", "WORLD_SIZE": "2", "LOCAL_RANK": "1"})
     assert p.returncode == 0, p.stderr
     assert p.stdout.strip() == ""
+
+
+def test_launch_count_follows_the_schedule():
+    """gpu_launches counts the solve's kernels from the level schedule: the
+    bench's colour rule equals the oracle's for every option, and a 1024^2
+    cycle of the tuned schedule (4 colours, 2 on the coarse levels) is the
+    39 kernels of its ncu launch list (32 phases, 4 coarse applies, the tile
+    sums, the energy, the stopping test)."""
+    import bench
+    import oracle
+    import paper_2204_07921_gb300 as cm
+    for nc in (0, 2, 4, 9, 16):
+        for cn in (0, 2, 4):
+            o = cm.default_options(ncolors=nc, coarse_ncolors=cn)
+            for j in range(12):
+                b = 1 << j
+                assert bench.level_colours(o, b) == oracle.level_colours(nc, b, cn), (nc, cn, b)
+    assert bench.kernels_per_cycle(cm.default_options(ncolors=4, coarse_ncolors=2), 10) == 39
+    assert bench.kernels_per_cycle(cm.default_options(ncolors=4), 10) == 47
+    assert bench.kernels_per_cycle(cm.default_options(ncolors=4), 6) == 2 + 6 * 4
