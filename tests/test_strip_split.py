@@ -33,6 +33,12 @@ CASES3 = [
     (30, 26, 3, dict(kind=oracle.MEAN, ncolors=4)),
     (29, 24, 3, dict(kind=oracle.GAUSS, ncolors=2, coarse_ncolors=0)),
 ]
+# strips of 3, 3, 2 and 2 rows: a block of side 8 spans three strips, and
+# the halo of a 2-row strip is its neighbour's whole strip
+CASES4 = [
+    (10, 24, 4, dict(kind=oracle.MEAN, ncolors=4, levels=4)),
+    (10, 24, 4, dict(kind=oracle.GAUSS_EULER, ncolors=2, levels=4)),
+]
 
 
 def _f(H, W, seed):
@@ -99,6 +105,14 @@ def test_two_rank_strip_split_equals_the_whole_image_solve():
 def test_three_rank_strip_split_equals_the_whole_image_solve():
     results = _run(CASES3, 3)
     _check(CASES3, results, 3)
+
+
+def test_four_rank_strip_split_with_blocks_over_three_strips():
+    R = strip_rows(10, 4)
+    assert R == [0, 3, 6, 8, 10]
+    assert sum(1 for x in R[1:-1] if 0 < x < 8) == 2      # rows 0 .. 7: three strips
+    results = _run(CASES4, 4)
+    _check(CASES4, results, 4)
 
 
 def test_strip_rows_and_round_counts():
