@@ -68,3 +68,24 @@ def test_warmstart_sets_are_disjoint(split):
     a = synth.warmstart_image(split, 0, 32)
     b = synth.warmstart_image("test" if split == "train" else "train", 0, 32)
     assert a.seed != b.seed
+
+
+def test_mri_case_recipe():
+    """The undersampled acquisition: whole phase-encoding rows, every row
+    within 8% of the centre frequency sampled, about 1/accel of the rows in
+    all, the data zero off the mask and equal to the masked orthonormal
+    spectrum up to the noise, and the same case for the same seed."""
+    H, W, accel = 256, 64, 3.0
+    c = synth.mri_case(H, W, 17, accel=accel, sigma=0.0)
+    rows = c.mask[:, 0].astype(bool)
+    assert np.all(c.mask == c.mask[:, :1])                      # whole rows
+    freq = np.where(np.arange(H) < (H + 1) // 2, np.arange(H), np.arange(H) - H)
+    assert np.all(rows[np.abs(freq) <= 0.08 * H / 2])            # the centre rows
+    assert abs(rows.mean() - 1 / accel) < 0.08
+    assert np.all(c.kspace[~rows] == 0)
+    ref = np.fft.fft2(c.clean.astype(np.float64), norm="ortho")[rows]
+    np.testing.assert_allclose(c.kspace[rows], ref, rtol=0, atol=1e-5 * np.abs(ref).max())
+    d = synth.mri_case(H, W, 17, accel=accel, sigma=0.0)
+    assert np.array_equal(d.mask, c.mask) and np.array_equal(d.kspace, c.kspace)
+    full = synth.mri_case(32, 16, 3, accel=1.0)
+    assert full.mask.all()
