@@ -243,3 +243,30 @@ def test_clamped_boundary_reading():
     assert kbar[0] < 0
     one = np.array([[0.4]])
     assert oracle.curvature(one, 0, 0, oracle.MEAN) == 0.0
+
+
+def test_euler_fit_is_the_closed_form_of_the_four_directions():
+    """At the sampled angles 0, 90, 45 and 135 degrees the columns
+    (1, cos 2theta, sin 2theta) of the least-squares design are orthogonal,
+    so the fit of kappa(theta) = a + b cos 2theta + s sin 2theta has the
+    closed form a = (k0 + k1 + k2 + k3)/4, b = (k0 - k1)/2, s = (k2 - k3)/2
+    (numpy's least squares agrees), and the principal curvatures a -+
+    sqrt(b^2 + s^2) give H = a, K = a^2 - b^2 - s^2.  The oracle's kinds 2
+    and 3 (normal equations from the lines' angles, Gauss-Jordan) match it
+    on every pixel of random images, borders included."""
+    X = np.array([[1, 1, 0], [1, -1, 0], [1, 0, 1], [1, 0, -1]], dtype=float)
+    rng = np.random.default_rng(12)
+    for trial in range(3):
+        u = rng.random((7, 9)) * (0.2 + trial)
+        for r in range(7):
+            for c in range(9):
+                kbar, _ = oracle.direction_curvatures(u, r, c)
+                a, b, s = np.linalg.lstsq(X, kbar, rcond=None)[0]
+                assert a == pytest.approx(kbar.sum() / 4, abs=1e-12)
+                assert b == pytest.approx((kbar[0] - kbar[1]) / 2, abs=1e-12)
+                assert s == pytest.approx((kbar[2] - kbar[3]) / 2, abs=1e-12)
+                H = oracle.curvature(u, r, c, oracle.MEAN_EULER)
+                K = oracle.curvature(u, r, c, oracle.GAUSS_EULER)
+                scale = 1.0 + np.max(np.abs(kbar)) ** 2
+                assert abs(H - a) <= 1e-12 * scale
+                assert abs(K - (a * a - b * b - s * s)) <= 1e-12 * scale
