@@ -19,8 +19,9 @@ more because a block's ring reaches one row beyond the block).  A phase
      search runs the same steps on every rank, so the rounds line up);
   4. every rank adds the shifts to its own rows.
 
-Each cycle ends with an all-reduce of the ranks' FP64 energy sums (Eq. MCM /
-GCM), which feeds the stopping test.
+Each cycle ends with one more halo exchange (the energy's stencils read the
+neighbours' rows as the last phase left them) and an all-reduce of the
+ranks' FP64 energy sums (Eq. MCM / GCM), which feeds the stopping test.
 
 The emulation runs the straddling blocks' searches one after another (one
 round per evaluation); a GPU split would run all straddling blocks of a
