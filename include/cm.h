@@ -59,8 +59,10 @@ extern "C" {
 
 /* Image sizes: 1 .. CM_MAX_SIDE rows and columns and at most CM_MAX_PIXELS
  * pixels per image (8 GiB of FP32; block and tile counts are int).  Larger
- * images are rejected with CM_ERR_INVALID (cm_radon_bins returns -1). */
-#define CM_MAX_SIDE (1 << 20)
+ * images are rejected with CM_ERR_INVALID (cm_radon_bins returns -1).
+ * CM_MAX_SIDE = 65535 x 8: the kernels with the shortest row tiles (8 rows)
+ * put the row-tile count in a grid's y dimension, whose limit is 65535. */
+#define CM_MAX_SIDE 524280
 #define CM_MAX_PIXELS 2147483647LL
 
 #define CM_KIND_MEAN 0
@@ -322,12 +324,15 @@ int cm_warmstart(cm_ctx* ctx, cm_net* net, const float* f, int N, int H, int W, 
  * u, f: device, H x W, row-major float32 on the current device.  E_dev:
  * device pointer to one double that receives F(u) when the work on `stream`
  * completes (the call does not synchronise).
- * Returns CM_ERR_INVALID for null pointers, sizes < 1, a bad alpha or kind,
+ * Returns CM_ERR_INVALID for null pointers, sizes < 1 or beyond CM_MAX_SIDE
+ * and CM_MAX_PIXELS, a bad alpha or kind,
  * and for images with more than CM_NOALLOC_MAX_TILES tiles of 32 x 32 pixels
  * (ceil(H/32) * ceil(W/32) > 16384, e.g. larger than 4096 x 4096);
  * CM_ERR_CUDA if a CUDA call fails.
  * The first call on a device looks up the array's device address (with that
- * device current); make that first call before any stream capture.  Every
+ * device current) and keeps it until the process exits; make that first call
+ * before any stream capture, and make no call on a device after
+ * cudaDeviceReset of it (the kept address is then stale).  Every
  * call shares the one array and clears its counter before use, so calls whose
  * work overlaps on the GPU (on different streams, or from several host
  * threads without ordering) race and must be serialised by the caller. */
@@ -383,9 +388,15 @@ int cm_recon(cm_ctx* ctx, const float* kspace, const unsigned char* mask, int H,
  * Synchronises `stream`.  Returns CM_ERR_INVALID for null pointers, sizes out
  * of range, n_angles outside 1 .. 100000, u_out aliasing sino, a bad alpha,
  * kind or option, cycles outside 0 .. 100000 or cg_iters outside 1 .. 1000;
- * CM_ERR_OOM or CM_ERR_CUDA as cm_recon.  cm_radon_bins is host-only: D, or
- * -1 for sizes out of range. */
+ * CM_ERR_OOM or CM_ERR_CUDA as cm_recon.  The sinogram is indexed with
+ * int: n_angles x D above CM_MAX_SINO entries is rejected with
+ * CM_ERR_INVALID by every CT entry point.  cm_radon_bins and
+ * cm_radon_entries are host-only: D, or the sinogram's entry count
+ * n_angles x D, or -1 where the image size, n_angles or the entry count is
+ * out of range. */
+#define CM_MAX_SINO 2147483647LL
 int cm_radon_bins(int H, int W);
+long long cm_radon_entries(int H, int W, int n_angles);
 int cm_recon_ct(cm_ctx* ctx, const float* sino, int n_angles, int H, int W, float alpha,
                 int kind, int levels, int cycles, int cg_iters, const float* u0, float* u_out,
                 const cm_options* opts /* host, nullable */,

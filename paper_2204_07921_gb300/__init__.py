@@ -17,7 +17,7 @@ from .build import LIB, build as build_library
 __all__ = [
     "CMError", "Options", "Stats", "Context", "load", "cm_energy", "cm_curvature", "cm_phase",
     "cm_level", "cm_energy_noalloc", "cm_solve_batched", "cm_probe_alu", "cm_recon",
-    "cm_recon_ct", "cm_radon", "cm_radon_adjoint", "cm_radon_bins",
+    "cm_recon_ct", "cm_radon", "cm_radon_adjoint", "cm_radon_bins", "cm_radon_entries",
     "cm_solve", "cm_auto_levels", "MEAN", "GAUSS", "MEAN_EULER", "GAUSS_EULER",
 ]
 
@@ -75,6 +75,7 @@ SIGNATURES = {
     "cm_probe_alu": (_I, [_I, _P, _P, _P]),
     "cm_selftest_wait": (_I, [_I, _I, _P, _P]),
     "cm_radon_bins": (_I, [_I, _I]),
+    "cm_radon_entries": (ctypes.c_longlong, [_I, _I, _I]),
     "cm_radon": (_I, [_P, _P, _I, _I, _I, _P, _P]),
     "cm_radon_adjoint": (_I, [_P, _P, _I, _I, _I, _P, _P]),
     "cm_recon_ct": (_I, [_P, _P, _I, _I, _I, _F, _I, _I, _I, _I, _P, _P,
@@ -374,6 +375,15 @@ def cm_radon_bins(H: int, W: int) -> int:
     return D
 
 
+def cm_radon_entries(H: int, W: int, n_angles: int) -> int:
+    """Entries of the n_angles x D sinogram of an H x W image; ValueError
+    where the library's limits reject the case."""
+    m = load().cm_radon_entries(H, W, n_angles)
+    if m < 0:
+        raise ValueError(f"CT case {H} x {W} with {n_angles} angles out of range")
+    return m
+
+
 def _sinogram(sino, H, W):
     """sino: n_angles x cm_radon_bins(H, W), n_angles >= 1."""
     _img(sino, "sino")
@@ -383,6 +393,7 @@ def _sinogram(sino, H, W):
     if sino.shape[0] < 1 or sino.shape[1] != D:
         raise ValueError(f"sino: expected n_angles x {D} for a {H} x {W} image, "
                          f"got {tuple(sino.shape)}")
+    cm_radon_entries(H, W, sino.shape[0])
 
 
 def cm_radon(u, n_angles: int, ctx: Context | None = None, stream=None):
@@ -393,6 +404,7 @@ def cm_radon(u, n_angles: int, ctx: Context | None = None, stream=None):
         raise ValueError("n_angles: expected >= 1")
     c = _ctx(ctx, u)
     H, W = u.shape
+    cm_radon_entries(H, W, n_angles)
     sino = torch.empty((n_angles, cm_radon_bins(H, W)), dtype=torch.float32, device=u.device)
     c._check(load().cm_radon(c.handle, u.data_ptr(), H, W, n_angles, sino.data_ptr(),
                              _stream_ptr(stream)))

@@ -996,10 +996,16 @@ int cm_recon(cm_ctx* ctx, const float* kspace, const unsigned char* mask, int H,
 
 int cm_radon_bins(int H, int W) { return dims_ok(H, W) ? cm::radon_bins(H, W) : -1; }
 
+long long cm_radon_entries(int H, int W, int n_angles) {
+    if (!dims_ok(H, W) || n_angles < 1 || n_angles > 100000) return -1;
+    const long long m = (long long)n_angles * cm::radon_bins(H, W);
+    return m <= CM_MAX_SINO ? m : -1;
+}
+
 int cm_radon(cm_ctx* ctx, const float* u, int H, int W, int n_angles, float* sino,
              void* stream) {
     if (!ctx) return CM_ERR_INVALID;
-    if (!u || !sino || !dims_ok(H, W) || n_angles < 1 || n_angles > 100000)
+    if (!u || !sino || cm_radon_entries(H, W, n_angles) < 0)
         return fail(ctx, CM_ERR_INVALID, "cm_radon: invalid argument");
     CM_CUDA(cudaSetDevice(ctx->device));
     const char* msg = "";
@@ -1011,7 +1017,7 @@ int cm_radon(cm_ctx* ctx, const float* u, int H, int W, int n_angles, float* sin
 int cm_radon_adjoint(cm_ctx* ctx, const float* sino, int n_angles, int H, int W, float* u,
                      void* stream) {
     if (!ctx) return CM_ERR_INVALID;
-    if (!u || !sino || !dims_ok(H, W) || n_angles < 1 || n_angles > 100000)
+    if (!u || !sino || cm_radon_entries(H, W, n_angles) < 0)
         return fail(ctx, CM_ERR_INVALID, "cm_radon_adjoint: invalid argument");
     CM_CUDA(cudaSetDevice(ctx->device));
     const char* msg = "";
@@ -1030,9 +1036,9 @@ int cm_recon_ct(cm_ctx* ctx, const float* sino, int n_angles, int H, int W, floa
     if (opts) o = *opts;
     int rc = check_opts(ctx, o);
     if (rc) return rc;
-    if (!sino || !u_out || !dims_ok(H, W) || n_angles < 1 || n_angles > 100000 ||
-        !finite_positive(alpha) || !valid_kind(kind) || levels < 0 || cycles < 0 ||
-        cycles > 100000 || cg_iters < 1 || cg_iters > 1000 ||
+    if (!sino || !u_out || cm_radon_entries(H, W, n_angles) < 0 || !finite_positive(alpha) ||
+        !valid_kind(kind) || levels < 0 || cycles < 0 || cycles > 100000 || cg_iters < 1 ||
+        cg_iters > 1000 ||
         (const void*)u_out == (const void*)sino)
         return fail(ctx, CM_ERR_INVALID, "cm_recon_ct: invalid argument");
     cm::ReconArgs a;

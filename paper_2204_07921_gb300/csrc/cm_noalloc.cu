@@ -26,7 +26,10 @@ constexpr size_t kScratchBytes = kPartialBytes + 256;
 static __device__ __align__(256) unsigned char g_energy_scratch[kScratchBytes];
 
 // Device address of g_energy_scratch, looked up once per device (the name is
-// only a host-side stand-in in host code).
+// only a host-side stand-in in host code) and kept for the life of the
+// process.  cudaDeviceReset destroys the module that holds the array, so the
+// kept address is stale afterwards: a process that resets a device must not
+// call cm_energy_noalloc on it again.
 constexpr int kMaxDevices = 64;
 std::mutex g_mutex;
 void* g_scratch_ptr[kMaxDevices] = {};
@@ -51,7 +54,10 @@ extern "C" int cm_energy_noalloc(const float* u, const float* f, int H, int W, f
     if (!u || !f || !E_dev || H < 1 || W < 1 || !(alpha > 0.0f) || alpha != alpha ||
         alpha > 3.0e38f || kind < 0 || kind > 3)
         return CM_ERR_INVALID;
-    // the energy kernel's grid has one CTA per 32 x 32 tile
+    // the image limits of every entry point first (the tile count below is
+    // computed in int), then the energy kernel's grid: one CTA per 32 x 32 tile
+    if (H > CM_MAX_SIDE || W > CM_MAX_SIDE || (long long)H * W > CM_MAX_PIXELS)
+        return CM_ERR_INVALID;
     if (cm::energy_partials_needed(H, W) > (size_t)CM_NOALLOC_MAX_TILES) return CM_ERR_INVALID;
     void* base = nullptr;
     int rc = scratch_for_current_device(&base);

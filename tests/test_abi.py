@@ -68,18 +68,46 @@ def test_image_size_limits():
     import numpy as np
     import paper_2204_07921_gb300 as cm
     text = open(os.path.join(HEADER_DIR, "cm.h")).read()
-    assert re.search(r"#define CM_MAX_SIDE \(1 << 20\)", text)
+    assert re.search(r"#define CM_MAX_SIDE 524280", text)
     assert re.search(r"#define CM_MAX_PIXELS 2147483647LL", text)
     lib = cm.load()
-    side, pixels = 1 << 20, 2 ** 31 - 1
-    for H, W in ((1, 1), (side, 1), (1, side), (side, 2047), (46340, 46340)):
+    # 65535 row tiles of 8 rows: the y-dimension limit of a launch grid
+    side, pixels = 65535 * 8, 2 ** 31 - 1
+    for H, W in ((1, 1), (side, 1), (1, side), (side, 4096), (46340, 46340)):
         assert H * W <= pixels
         assert lib.cm_radon_bins(H, W) == 2 * int(np.ceil(np.hypot(H - 1, W - 1) / 2)) + 3
-    for H, W in ((0, 5), (5, 0), (-1, 5), (side + 1, 1), (1, side + 1), (side, 2048),
-                 (46341, 46341), (50000, 50000)):
+    for H, W in ((0, 5), (5, 0), (-1, 5), (side + 1, 1), (1, side + 1), (side, 4097),
+                 (1 << 20, 1), (46341, 46341), (50000, 50000)):
         assert lib.cm_radon_bins(H, W) == -1, (H, W)
     with pytest.raises(ValueError):
         cm.cm_radon_bins(50000, 50000)
+
+
+def test_sinogram_entry_limit():
+    """The CT entry points index the n_angles x D sinogram with int: the
+    host-only cm_radon_entries (the check cm_radon, cm_radon_adjoint and
+    cm_recon_ct apply before any CUDA call) gives n_angles x D, and -1 once
+    that count passes CM_MAX_SINO = 2^31 - 1, for image sizes that are
+    themselves within the limits."""
+    import numpy as np
+    import paper_2204_07921_gb300 as cm
+    text = open(os.path.join(HEADER_DIR, "cm.h")).read()
+    assert re.search(r"#define CM_MAX_SINO 2147483647LL", text)
+    lib = cm.load()
+    for H, W, n in ((32, 32, 1), (256, 256, 180), (32768, 32768, 100), (46340, 46340, 1)):
+        D = 2 * int(np.ceil(np.hypot(H - 1, W - 1) / 2)) + 3
+        assert n * D <= 2 ** 31 - 1
+        assert lib.cm_radon_entries(H, W, n) == n * D
+    # 32768^2 (D = 46343): 46339 angles fit, 50000 (2.3e9 entries) do not
+    D = lib.cm_radon_bins(32768, 32768)
+    assert D == 46343
+    n_fit = (2 ** 31 - 1) // D
+    assert lib.cm_radon_entries(32768, 32768, n_fit) == n_fit * D
+    for H, W, n in ((32768, 32768, n_fit + 1), (32768, 32768, 50000), (32, 32, 0),
+                    (32, 32, 100001), (0, 32, 5), (600000, 1, 5)):
+        assert lib.cm_radon_entries(H, W, n) == -1, (H, W, n)
+    with pytest.raises(ValueError):
+        cm.cm_radon_entries(32768, 32768, 50000)
 
 
 def test_default_budget_agrees_with_oracle():

@@ -72,7 +72,7 @@ def test_warmstart_sets_are_disjoint(split):
 
 def test_mri_case_recipe():
     """The undersampled acquisition: whole phase-encoding rows, every row
-    within 8% of the centre frequency sampled, about 1/accel of the rows in
+    whose frequency satisfies |k| <= 8% of H/2 sampled, about 1/accel of the rows in
     all, the data zero off the mask and equal to the masked orthonormal
     spectrum up to the noise, and the same case for the same seed."""
     H, W, accel = 256, 64, 3.0

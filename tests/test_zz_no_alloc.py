@@ -56,6 +56,13 @@ def test_noalloc_rejects_oversize_and_bad_arguments():
                                4097, 4097, ctypes.c_float(1.0), 0,
                                ctypes.c_void_p(E_dev.data_ptr()), stream)
     assert rc == cm.CM_ERR_INVALID
+    # sizes beyond the image limits of every entry point (W = INT_MAX would
+    # overflow the int tile count) are rejected before the tile count is formed
+    for H, W in ((1, 2 ** 31 - 1), (2 ** 31 - 1, 1), (1, 524281)):
+        rc = lib.cm_energy_noalloc(ctypes.c_void_p(u.data_ptr()), ctypes.c_void_p(u.data_ptr()),
+                                   H, W, ctypes.c_float(1.0), 0,
+                                   ctypes.c_void_p(E_dev.data_ptr()), stream)
+        assert rc == cm.CM_ERR_INVALID, (H, W)
     rc = lib.cm_energy_noalloc(None, ctypes.c_void_p(u.data_ptr()), 8, 8, ctypes.c_float(1.0), 0,
                                ctypes.c_void_p(E_dev.data_ptr()), stream)
     assert rc == cm.CM_ERR_INVALID
