@@ -49,8 +49,6 @@ def parse():
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--side", type=int, default=SIDE)
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--cpu-cycles", type=int, default=1,
-                   help="oracle cycles timed for the CPU baseline sample")
     p.add_argument("--no-warmstart-eval", action="store_true",
                    help="skip the 16-image warm-start evaluation")
     p.add_argument("--no-batched", action="store_true",
@@ -155,23 +153,50 @@ def dist_setup(args):
 # oracle (CPU) timing: shared by the cpu_baseline field and --impl reference
 
 
-def oracle_cycle_seconds(f64, n_cycles: int):
-    """Wall seconds per cycle of the FP64 oracle on this image (as it stands,
-    OpenMP over the blocks of a colour on all host cores)."""
+# The schedule the autotuner picks for the 1024^2 workload on the GB300
+# (search budget (5, 6), four colours, two on the coarse levels b >= 64): the
+# CPU legs run the oracle with it, since they have no GPU to tune on.
+REF_SCHEDULE = {"G": 5, "K": 6, "ncolors": 4, "coarse_ncolors": 2}
+
+
+def oracle_cycle_seconds(u0, f64, n_cycles: int, sched=None):
+    """Wall seconds per cycle of the FP64 oracle from state u0 (as it stands,
+    OpenMP over the blocks of a colour on the host cores it is given)."""
     import oracle
-    u = f64.copy()
+    sc = sched or REF_SCHEDULE
+    u = u0.copy()
     t0 = time.perf_counter()
     for _ in range(n_cycles):
-        u = oracle.cycle(u, f64, ALPHA, KIND, ncolors=NCOLORS)
+        u = oracle.cycle(u, f64, ALPHA, KIND, ncolors=sc["ncolors"], G=sc["G"], K=sc["K"],
+                         coarse_ncolors=sc["coarse_ncolors"])
         oracle.energy(u, f64, ALPHA, KIND)
     return (time.perf_counter() - t0) / n_cycles, oracle.num_threads()
 
 
+def oracle_warmstart(f64):
+    """The learned warm start in FP64 on the host: the network's forward pass
+    (oracle/cnn.py, the shipped weights) and the energy check that keeps u0
+    only if F(u0) <= F(f).  Returns (u0, seconds, kept)."""
+    import numpy as np
+    import oracle
+    from oracle import cnn as ocnn
+    params = np.load(WARMSTART_PARAMS)["params"].astype(np.float64)
+    t0 = time.perf_counter()
+    u0, _ = ocnn.forward(params, f64[None])
+    u0 = u0[0]
+    kept = oracle.energy(u0, f64, ALPHA, KIND) <= oracle.energy(f64, f64, ALPHA, KIND)
+    if not kept:
+        u0 = f64
+    return u0, time.perf_counter() - t0, bool(kept)
+
+
 def run_reference(args):
-    """The reference arm is the FP64 oracle, run as it stands
-    on the host cores: one full solve to tol 1e-4 (its own cycle count and
-    time), then warm-up and timed single-cycle samples; value = mean cycle
-    time x the oracle's cycle count."""
+    """The reference arm is the FP64 oracle, run as it stands on the host
+    cores, on the same workload as the GPU line: the learned warm start (the
+    network's forward pass in FP64 and the energy check), then the sweep from
+    its output with the same schedule to tol 1e-4 (one full solve: its own
+    cycle count), then warm-up and timed single-cycle samples.  value = warm
+    start time + mean cycle time x the oracle's cycle count."""
     rank, world, _ = dist_setup(args)
     if rank != 0:
         return
@@ -180,41 +205,112 @@ def run_reference(args):
     import synth
     img = synth.large(args.side)
     f64 = img.f.astype(np.float64)
+    u0, t_ws, kept = oracle_warmstart(f64)
+    sc = REF_SCHEDULE
     t0 = time.perf_counter()
-    _, trace, cycles, conv = oracle.solve(f64, ALPHA, KIND, cycles=MAX_CYCLES, tol=TOL,
-                                          ncolors=NCOLORS)
+    u, trace, cycles, conv = oracle.solve(f64, ALPHA, KIND, cycles=MAX_CYCLES, tol=TOL, u0=u0,
+                                          ncolors=sc["ncolors"], G=sc["G"], K=sc["K"],
+                                          coarse_ncolors=sc["coarse_ncolors"])
     full_s = time.perf_counter() - t0
     times = []
     threads = 1
     for i in range(args.warmup + args.steps):
-        per_cycle, threads = oracle_cycle_seconds(f64, 1)
+        per_cycle, threads = oracle_cycle_seconds(u0, f64, 1)
         if i >= args.warmup:
             times.append(per_cycle)
     per_cycle = statistics.mean(times)
-    value = per_cycle * cycles
-    sample = (f"oracle: one full solve to tol ({cycles} cycles, {full_s:.1f} s), then "
-              f"{args.steps} timed single-cycle samples of the {args.side}^2 image x {cycles}")
+    value = t_ws + per_cycle * cycles
+    sample = (f"oracle: warm start {t_ws:.1f} s, one full solve from it to tol ({cycles} "
+              f"cycles, {full_s:.1f} s), then {args.steps} timed single-cycle samples; "
+              f"value = warm start + mean cycle x {cycles}")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": per_cycle * 1e3, "higher_is_better": False, "scaling": "weak",
+            "ms_per_step": value * 1e3, "higher_is_better": False, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": workload_config(args.side), "oracle_cycles": cycles,
-            "oracle_converged": bool(conv), "oracle_full_solve_s": full_s,
-            "oracle_final_energy": float(trace[-1]),
+            "config": workload_config(args.side, L=_auto_levels(args.side), sched=sc),
+            "oracle_cycles": cycles, "oracle_converged": bool(conv),
+            "oracle_full_solve_s": full_s, "oracle_warmstart_s": t_ws,
+            "oracle_warmstart_kept": kept, "oracle_final_energy": float(trace[-1]),
+            "psnr_db": synth.psnr(u.astype(np.float32), img.clean),
             "cpu_baseline": {"value": value, "unit": "s", "cores": threads, "kind": "oracle",
-                             "sample": sample},
+                             "sample": sample, "per_cycle_s": per_cycle},
             "e2e": {"value": value, "unit": "s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
-def workload_config(side):
-    return {"workload": f"denoise {side}x{side} mean curvature, 20 shapes, sigma 0.08, "
-                        f"alpha 20, blocks 1..{side // 2}, tuned colour schedule, tol 1e-4; "
-                        f"learned warm start (6 conv3x3, 32 ch, BF16) then the sweep",
-            "image": f"{side}x{side}", "kind": "mean", "alpha": ALPHA, "tol": TOL,
-            "levels": None, "ncolors": 4, "grid_points": None, "golden_evals": None,
+def _auto_levels(side):
+    """Levels of the sides 1, 2, 4, .. up to the largest <= side / 2."""
+    L, b = 0, 1
+    while 2 * b <= side:
+        L += 1
+        b *= 2
+    return L
+
+
+def workload_config(side, L, sched):
+    """The workload both arms run (same keys and values when the autotuner
+    picks the schedule the CPU legs use)."""
+    return {"workload": f"denoise {side}^2 mean curv., learned warm start + sweep to tol 1e-4",
+            "image": f"{side}x{side}", "shapes": 20, "sigma": 0.08, "kind": "mean",
+            "alpha": ALPHA, "tol": TOL, "levels": L, "block_sides": f"1..{1 << (L - 1)}",
+            "grid_points": sched["G"], "golden_evals": sched["K"], "ncolors": sched["ncolors"],
+            "coarse_ncolors": sched["coarse_ncolors"],
+            "warm_start": "6 conv3x3, 32 ch, residual (shipped weights), energy check",
             "l2": "flushed between steps (512 MB write)"}
+
+
+def cpu_legs(img, cycles_warm, opts, cm, torch, ctx, dev):
+    """The oracle on the host cores (as it stands):
+    * value: the same workload as the GPU line -- the FP64 warm start, then
+      two timed oracle cycles from its output, extrapolated to the GPU's
+      cycle count (a bounded sample);
+    * single_thread: one oracle cycle with one thread on the 512 x 512
+      top-left corner of the image, x 4 for the full image (a sample);
+    * parity_vs_gpu: the plain solve from f with the oracle's own schedule
+      (four colours on every level, (G, K) = (5, 6)) by the oracle and by the
+      GPU: final energies, their relative difference and max |u_gpu - u_orc|
+      (both FP32-vs-FP64 trajectories; energy ties separate them)."""
+    import numpy as np
+    import oracle
+    f64 = img.f.astype(np.float64)
+    u0, t_ws, kept = oracle_warmstart(f64)
+    n_s = 2
+    per_cycle, threads = oracle_cycle_seconds(u0, f64, n_s)
+    mean_cycles = statistics.mean(cycles_warm)
+    res = {"value": t_ws + per_cycle * mean_cycles, "unit": "s", "cores": threads,
+           "kind": "oracle",
+           "sample": f"FP64 warm start ({t_ws:.1f} s) + {n_s} oracle cycles from it on the "
+                     f"{img.f.shape[0]}^2 image, extrapolated x {mean_cycles:g} cycles (the "
+                     f"GPU's count)", "per_cycle_s": per_cycle, "warmstart_s": t_ws}
+    crop = f64[:512, :512].copy()
+    try:
+        oracle.set_num_threads(1)
+        pc1, _ = oracle_cycle_seconds(crop, crop, 1)
+    finally:
+        oracle.set_num_threads(threads)
+    scale = f64.size / crop.size
+    res["single_thread"] = {"value": t_ws + pc1 * scale * mean_cycles, "per_cycle_s": pc1 * scale,
+                            "cores": 1, "sample": "one cycle, 1 thread, 512^2 corner x 4 "
+                                                  "(the warm start as timed above)"}
+    t0 = time.perf_counter()
+    uo, trace, n_o, conv = oracle.solve(f64, ALPHA, KIND, cycles=MAX_CYCLES, tol=TOL,
+                                        ncolors=4, G=5, K=6)
+    t_full = time.perf_counter() - t0
+    o4 = cm.default_options(ncolors=4, grid_points=5, golden_evals=6)
+    fd = torch.from_numpy(img.f).to(dev)
+    ug, st = cm.cm_solve(fd, ALPHA, KIND, cycles=MAX_CYCLES, tol=TOL, options=o4, ctx=ctx)
+    ugh = ug.cpu().numpy()
+    Eg = oracle.energy(ugh.astype(np.float64), f64, ALPHA, KIND)
+    res["parity_vs_gpu"] = {
+        "schedule": "plain from f, 4 colours on every level, (G, K) = (5, 6), tol 1e-4",
+        "oracle_cycles": n_o, "gpu_cycles": st.cycles_run, "oracle_s": t_full,
+        "oracle_final_energy": float(trace[-1]), "gpu_final_energy": Eg,
+        "gpu_reported_energy": st.energy_final,
+        "rel_energy_diff": (Eg - float(trace[-1])) / float(trace[-1]),
+        "max_abs_du": float(np.abs(ugh - uo).max()),
+        "mean_abs_du": float(np.abs(ugh - uo).mean())}
+    return res
 
 
 def batched_measurement(cm, torch, synth, ctx, dev, rank=0, world=1):
@@ -276,6 +372,61 @@ def batched_measurement(cm, torch, synth, ctx, dev, rank=0, world=1):
     res["pixels"] = int(sum(it.image.f.size for it in all_items))
     res["ranks"] = world
     return res
+
+
+def measured_hbm_peak():
+    """The machine's measured copy bandwidth (MEASURED_PEAKS.json), else the
+    fallback figure of one earlier GB300 measurement."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured"
+    except (OSError, ValueError, KeyError):
+        return 6800.0, "fallback"
+
+
+def hbm_measurement(cm, torch, synth, ctx, dev, stream, opts, flush, b1_ms, N, nc):
+    """GB/s of algorithmic bytes for the finest-level phase and the energy
+    kernel (CUDA events on the launching stream), against the HBM peak."""
+    peak, src = measured_hbm_peak()
+    out = {"peak_gbs": peak, "peak_source": src}
+    b1_bytes = 12.0 / nc * N
+    out["phase_b1_1024"] = {"bytes_per_launch": b1_bytes, "ms": b1_ms,
+                            "gbs": b1_bytes / (b1_ms / 1e3) / 1e9,
+                            "frac": b1_bytes / (b1_ms / 1e3) / 1e9 / peak,
+                            "note": "working set in L2 (1024^2)"}
+    side = 4096
+    im = synth.large(side)
+    u4 = torch.from_numpy(im.f).to(dev)
+    f4 = torch.from_numpy(im.clean).to(dev)
+    R4 = u4.clone()
+    E_dev = torch.zeros(1, dtype=torch.float64, device=dev)
+    n4 = side * side
+    reps = 6
+
+    def timed(fn):
+        fn(0)
+        torch.cuda.synchronize()
+        tot = 0.0
+        for i in range(reps):
+            flush.fill_(float(i))
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn(i)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            tot += e0.elapsed_time(e1)
+        return tot / reps
+
+    ms = timed(lambda i: cm.cm_phase(u4, R4, f4, ALPHA, KIND, 1, i % nc, options=opts, ctx=ctx))
+    by = 12.0 / nc * n4
+    out["phase_b1_4096"] = {"bytes_per_launch": by, "ms": ms, "gbs": by / (ms / 1e3) / 1e9,
+                            "frac": by / (ms / 1e3) / 1e9 / peak, "note": "L2 flushed"}
+    ms = timed(lambda i: cm.cm_energy_noalloc(u4, f4, ALPHA, KIND, E_dev))
+    by = 8.0 * n4
+    out["energy_4096"] = {"bytes_per_launch": by, "ms": ms, "gbs": by / (ms / 1e3) / 1e9,
+                          "frac": by / (ms / 1e3) / 1e9 / peak, "note": "L2 flushed"}
+    del u4, f4, R4
+    return out
 
 
 def kernels_per_cycle(opts, L):
@@ -396,6 +547,10 @@ def main():
     import synth
 
     rank, world, local = dist_setup(args)
+    # the autotuner's cache: a file this script writes itself (in the build
+    # folder of the package) unless the caller names one
+    os.environ.setdefault("CM_AUTOTUNE_CACHE", os.path.join(
+        ROOT, "paper_2204_07921_gb300", "_build", f"autotune_rank{rank}.json"))
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     if world > 1:
@@ -716,6 +871,18 @@ def main():
                         "2.07 GHz / 8); the kernel is issue-bound on the FP32/ALU pipes "
                         "(ncu: issue 57-63% active, MUFU 18-21%)"}
 
+    # HBM side of the roofline: algorithmic bytes per launch / device time.
+    # The sweep's algorithmic bytes are 12 B per pixel and level (read u and
+    # f, write u), so one phase of nc colours moves 12 / nc B per image pixel;
+    # the energy reads u and f (8 B per pixel).  At 1024^2 the working set
+    # stays in the 129 MB L2; at 4096^2 (134 MB of u and f) the L2 is flushed
+    # (512 MB write) before every timed launch, so the bytes come from HBM.
+    roofline["hbm"] = hbm_measurement(cm, torch, synth, ctx, dev, stream, opts, flush,
+                                      b1_ms, N, nc)
+    roofline["solve"] = {"warm_s": sec_warm, "warm_cycles": cycles, "plain_s": sec_plain,
+                         "plain_cycles": cycles_plain, "warm_vs_plain": sec_plain / sec_warm,
+                         "psnr_warm_db": psnr_warm, "psnr_plain_db": psnr_plain}
+
     warm_eval = warm_eval_gauss = None
     if not args.no_warmstart_eval:
         warm_eval = ws.evaluate(net, n=16, side=1024, alpha=ALPHA, kind=KIND, tol=TOL, ctx=ctx)
@@ -738,13 +905,7 @@ def main():
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        f64 = img.f.astype(np.float64)
-        per_cycle, threads = oracle_cycle_seconds(f64, args.cpu_cycles)
-        mean_cycles = statistics.mean(cycles_plain)   # the oracle runs the plain sweep
-        cpu = {"value": per_cycle * mean_cycles, "unit": "s", "cores": threads, "kind": "oracle",
-               "sample": f"{args.cpu_cycles} oracle cycle(s) on the {args.side}^2 image, "
-                         f"extrapolated x {mean_cycles:g} cycles of the plain sweep to tol",
-               "per_cycle_s": per_cycle}
+        cpu = cpu_legs(img, cycles, opts, cm, torch, ctx, dev)
 
     # per warm step: 6 network kernels, 2 energy checks, then the solve graph
     # (initial energy, state initialisation, the cycles)
@@ -753,7 +914,11 @@ def main():
     line = {"metric": METRIC, "value": sec_per_solve, "unit": "s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec_per_solve * 1e3,
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-            "data": "synthetic", "config": workload_config(args.side),
+            "data": "synthetic",
+            "config": workload_config(args.side, L, {"G": opts.grid_points,
+                                                     "K": opts.golden_evals,
+                                                     "ncolors": opts.ncolors,
+                                                     "coarse_ncolors": opts.coarse_ncolors}),
             "cycles_to_tol": cycles, "sweeps_per_s": statistics.mean(cycles) / sec_per_solve,
             "plain": {"s": sec_plain, "cycles_to_tol": cycles_plain, "psnr_db": psnr_plain,
                       "final_energy": st_plain[-1].energy_final},
@@ -771,13 +936,6 @@ def main():
             "reconstruction": recon_res,
             "cycle_variants": variants, "curvature_kinds": kinds_res,
             "complexity": complexity}
-    line["config"]["levels"] = L
-    line["config"]["grid_points"] = opts.grid_points
-    line["config"]["golden_evals"] = opts.golden_evals
-    line["config"]["ncolors"] = opts.ncolors
-    line["config"]["coarse_spec"] = opts.coarse_spec
-    line["config"]["coarse_dmax"] = opts.coarse_dmax
-    line["config"]["coarse_ncolors"] = opts.coarse_ncolors
     line["autotune"] = tune_rec
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -78,6 +78,7 @@ def lib():
                 "orc_level_colours": (i, [i, i, i]),
                 "orc_chalf_map": (None, [dp, i, i, i, dp]),
                 "orc_num_threads": (i, []),
+                "orc_set_num_threads": (None, [i]),
                 "orc_local_energy_batch": (None, [dp, dp, i, i, i, i, i, i, d, i, dp, i, dp]),
                 "orc_block_search": (d, [d, d, d, i, i, i, d, _RING_FN, ctypes.c_void_p, dp]),
             }
@@ -288,3 +289,8 @@ def solve(f, alpha, kind, levels=0, cycles=20, tol=0.0, u0=None, ncolors=2, G=DE
 
 def num_threads() -> int:
     return lib().orc_num_threads()
+
+
+def set_num_threads(n: int) -> None:
+    """OpenMP threads of the following calls (results do not depend on it)."""
+    lib().orc_set_num_threads(int(n))

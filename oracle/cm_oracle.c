@@ -688,6 +688,16 @@ int orc_num_threads(void) {
 #endif
 }
 
+/* Threads of the OpenMP loops from now on (timing runs; results do not depend
+ * on it, every parallel loop writes disjoint outputs). */
+void orc_set_num_threads(int n) {
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
 /* E_A at n points (used by the brute-force checks of the block minimiser). */
 void orc_local_energy_batch(const double *u, const double *f, int H, int W, int r0, int c0,
                             int bh, int bw, double alpha, int kind, const double *cs, int n,

@@ -71,9 +71,9 @@ SIGNATURES = {
     "cm_energy": (_I, [_P, _P, _P, _I, _I, _F, _I, ctypes.POINTER(_D), _P]),
     "cm_curvature": (_I, [_P, _P, _I, _I, _I, _P, _P]),
     "cm_phase": (_I, [_P, _P, _P, _P, _I, _I, _F, _I, _I, _I, ctypes.POINTER(Options), _P, _P]),
-    "cm_energy_noalloc": (_I, [_P, _P, _I, _I, _F, _I, _P, _P]),
     "cm_probe_alu": (_I, [_I, _P, _P, _P]),
     "cm_selftest_wait": (_I, [_I, _I, _P, _P]),
+    "cm_energy_noalloc": (_I, [_P, _P, _I, _I, _F, _I, _P, _P]),
     "cm_radon_bins": (_I, [_I, _I]),
     "cm_radon_entries": (ctypes.c_longlong, [_I, _I, _I]),
     "cm_radon": (_I, [_P, _P, _I, _I, _I, _P, _P]),

@@ -599,10 +599,10 @@ __global__ void pack_kernel(const float* __restrict__ P, bf16* __restrict__ wf,
 
 // ---------------------------------------------------------------------------
 // 5th-generation tensor cores (tcgen05): the same convolutions with the
-// accumulators in tensor memory.  A work unit is a strip of TR = 8 output
+// accumulators in tensor memory.  A work unit is a strip of TR = 6 output
 // rows x 128 columns.  Output row r is one M = 128 (pixels) x N (channels)
 // accumulator in TMEM, summed over 9 taps x 2 K-steps of 16 input channels
-// by tcgen05.mma from shared-memory operands.  The halo of the strip (10 x
+// by tcgen05.mma from shared-memory operands.  The halo of the strip (8 x
 // 130 pixels) is loaded by TMA (four tile copies, one per plane of 8
 // channels, zero outside the image), so plane j holds channels 8j .. 8j + 7
 // of every pixel, 16 bytes each: 8 consecutive pixels are one 128-byte core
@@ -613,7 +613,7 @@ __global__ void pack_kernel(const float* __restrict__ P, bf16* __restrict__ wf,
 // ([tap][plane][n] x 16 B).
 //
 // Pipeline (one CTA per SM, persistent over strips): thread 0 waits for a
-// strip's halo, issues its 144 MMAs into one of two TMEM accumulator sets and
+// strip's halo, issues its 108 MMAs into one of two TMEM accumulator sets and
 // commits them to an mbarrier; meanwhile the four warps drain the previous
 // strip's accumulators (tcgen05.ld: warp w owns TMEM lanes 32w .. 32w + 31),
 // and as soon as that strip's MMAs are known complete its halo buffer is
@@ -799,14 +799,18 @@ __global__ void __launch_bounds__(TC_THREADS, 1) conv_tc_kernel(
 
     if (warp == 4) {
         if (lane == 0) {
-            // producer: halo loads and MMAs
-            for (int k = 0; k < NSTAGE && k < nmine; ++k)
+            // producer: halo loads and MMAs.  issued / landed count the strips
+            // whose halo load was requested / seen complete; committed the
+            // strips whose MMAs were committed (for the drain on abort).
+            int issued = 0, landed = 0, committed = 0;
+            for (int k = 0; k < NSTAGE && k < nmine; ++k, ++issued)
                 tma_strip(hbase0 + k * HALO_BYTES, lbar0 + 8 * k, &tmap,
                           strip_of(blockIdx.x + k * G, H, W));
             const uint64_t bdesc0 = umma_sdesc(wbase, NO * 16, 128);
             for (int k = 0; k < nmine; ++k) {
                 const int hb = k % NSTAGE, b = k & 1;
                 bool ok = mbar_wait_bounded(lbar0 + 8 * hb, (unsigned)((k / NSTAGE) & 1));
+                if (ok) landed = k + 1;
                 if (ok && k >= 2) ok = mbar_wait_bounded(tfree0 + 8 * b, (unsigned)(((k >> 1) - 1) & 1));
                 if (!ok || *abort_flag) {
                     *abort_flag = 1;
@@ -830,6 +834,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) conv_tc_kernel(
                     "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                         mbar0 + 8 * b)
                     : "memory");
+                committed = k + 1;
                 // strip k - 1's MMAs done: its halo buffer takes strip k - 1 + NSTAGE
                 if (k >= 1 && k - 1 + NSTAGE < nmine) {
                     if (!mbar_wait_bounded(mbar0 + 8 * ((k - 1) & 1), (unsigned)(((k - 1) >> 1) & 1))) {
@@ -839,7 +844,19 @@ __global__ void __launch_bounds__(TC_THREADS, 1) conv_tc_kernel(
                     const int hbo = (k - 1) % NSTAGE;
                     tma_strip(hbase0 + hbo * HALO_BYTES, lbar0 + 8 * hbo, &tmap,
                               strip_of(blockIdx.x + (k - 1 + NSTAGE) * G, H, W));
+                    ++issued;
                 }
+            }
+            // Drain before the CTA frees its TMEM and exits: wait (bounded) for
+            // every halo load still in flight into shared memory (at most one
+            // per buffer, so each has its own phase; none on the normal path)
+            // and for the last commit, which covers every MMA issued before it
+            // (on the normal path the drain warps wait for it as well).
+            for (int k = landed; k < issued; ++k)
+                mbar_wait_bounded(lbar0 + 8 * (k % NSTAGE), (unsigned)((k / NSTAGE) & 1));
+            if (committed > 0) {
+                const int kc = committed - 1;
+                mbar_wait_bounded(mbar0 + 8 * (kc & 1), (unsigned)((kc >> 1) & 1));
             }
         }
     } else {

@@ -19,6 +19,9 @@ import oracle
 
 TIE_REL = 1e-5
 C_TOL = 1e-4
+# (E_A(c_gpu) - E_A(c_oracle)) / scale of every block whose shifts differ by
+# more than C_TOL, collected over a test session for the terminal summary
+TIE_LOG = []
 # search budget of both sides (the library's and the oracle's default)
 G_DEF, K_DEF = oracle.DEFAULT_G, oracle.DEFAULT_K
 
@@ -68,6 +71,7 @@ def compare_phase(u, f, c_gpu_blocks, alpha, kind, b, ncolors, k, c_orc_blocks, 
                                    use_paper=use_paper, one_step=one_step, finest=(b == 1))
         scale = max(energy_scale(u, f, r0, c0, bh, bw, cg, alpha, kind, info["c_fid"]),
                     energy_scale(u, f, r0, c0, bh, bw, co, alpha, kind, info["c_fid"]))
+        TIE_LOG.append((Eg - Eo) / max(scale, 1e-300))
         if Eg - Eo <= TIE_REL * scale:
             tie += 1
         else:

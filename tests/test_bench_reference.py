@@ -1,7 +1,8 @@
-"""The benchmark's reference arm (the FP64 oracle on the host cores) keeps
-the one-JSON-line contract on CPU: the keys and their types, value =
-cpu_baseline.value = e2e.value, and under several ranks only rank 0 runs
-and prints."""
+"""The benchmark's reference arm (the FP64 oracle on the host cores: the
+warm start in FP64, then the sweep with the same schedule) keeps the
+one-JSON-line contract on CPU: the keys and their types, value =
+cpu_baseline.value = e2e.value, the GPU line's config, and under several
+ranks only rank 0 runs and prints."""
 import json
 import os
 import subprocess
@@ -31,7 +32,11 @@ def test_reference_line_contract():
         assert k in d, k
     assert d["steps"] == 2 and d["warmup"] == 1 and d["n_gpus"] == 1
     assert d["higher_is_better"] is False and d["unit"] == "s" and d["value"] > 0
-    assert d["config"]["workload"].startswith("denoise 64x64")
+    assert d["config"]["workload"].startswith("denoise 64^2")
+    # the GPU line's config when the autotuner picks the CPU legs' schedule
+    import bench
+    assert d["config"] == bench.workload_config(64, bench._auto_levels(64), bench.REF_SCHEDULE)
+    assert d["oracle_warmstart_s"] > 0 and isinstance(d["oracle_warmstart_kept"], bool)
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["sample"]
     assert cb["value"] == d["value"] and cb["unit"] == d["unit"]

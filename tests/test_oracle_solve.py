@@ -131,6 +131,22 @@ def test_thread_count_does_not_change_result():
     assert outs[0] == outs[1]
 
 
+def test_set_num_threads_keeps_results():
+    """The timing runs' thread setting: the count takes effect and the solve
+    is bit-identical with one thread and with all of them."""
+    f = synth.piecewise_image(40, 36, 4, 5, 0.1).f.astype(np.float64)
+    n0 = oracle.num_threads()
+    try:
+        oracle.set_num_threads(1)
+        assert oracle.num_threads() == 1
+        u1, _, _, _ = oracle.solve(f, 20.0, 0, cycles=2, ncolors=4)
+    finally:
+        oracle.set_num_threads(n0)
+    assert oracle.num_threads() == n0
+    un, _, _, _ = oracle.solve(f, 20.0, 0, cycles=2, ncolors=4)
+    np.testing.assert_array_equal(u1, un)
+
+
 @pytest.mark.parametrize("shape", [(1, 9), (9, 1), (1, 1), (3, 2), (7, 5)])
 def test_degenerate_shapes(shape):
     """Single-row, single-column, single-pixel and tiny images run and never
