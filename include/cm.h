@@ -358,14 +358,32 @@ int cm_energy_noalloc(const float* u, const float* f, int H, int W, float alpha,
  * alias u0).  levels = 0: cm_auto_levels rule (opts->block_sides applies, as
  * do opts->ncolors; the search options do not).  trace_host (nullable, host,
  * cycles + 1 doubles) receives J before the first cycle and after each.
- * The transforms are cuFFT, loaded on first use (CM_ERR_CUDA with a message
- * if libcufft.so.12 cannot be loaded); the scratch (two complex images and
+ * The transforms are the library's own (cm_fft2d below), so H and W are
+ * each a power of two up to CM_FFT_MAX_POW2 or any length up to
+ * CM_FFT_MAX_OTHER; the scratch (two complex images, the transform tables and
  * the CG vectors) stays in the context.  Synchronises `stream`.  Returns
  * CM_ERR_INVALID for null pointers, sizes out of range (CM_MAX_SIDE,
- * CM_MAX_PIXELS), u_out aliasing kspace, a bad alpha, kind or option, cycles
- * outside 0 .. 100000 or cg_iters outside 1 .. 1000; CM_ERR_OOM when the
- * scratch cannot be allocated; CM_ERR_CUDA otherwise on a failed CUDA or
- * cuFFT call. */
+ * CM_MAX_PIXELS, the transform's limits), u_out aliasing kspace, a bad alpha,
+ * kind or option, cycles outside 0 .. 100000 or cg_iters outside 1 .. 1000;
+ * CM_ERR_OOM when the scratch cannot be allocated; CM_ERR_CUDA otherwise on a
+ * failed CUDA call. */
+/* The 2-D discrete Fourier transform of the MRI-like operator A = M F
+ * (Sec. 5), unnormalised: out[k, l] = sum_{r, c} in[r, c]
+ * exp(-+2 pi i (k r / H + l c / W)) with the minus sign (inverse = 0) or the
+ * plus sign (inverse = 1); the orthonormal F is this times 1/sqrt(HW).  in,
+ * out: device, H x W complex values as (re, im) float pairs, row-major; out
+ * may equal in (in place).  FP32 arithmetic with twiddle and chirp tables
+ * computed in FP64: rows, then columns, each line in one CTA's shared memory
+ * (radix-2; a length that is not a power of two by Bluestein's chirp
+ * z-transform with a power-of-two length >= 2n - 1).  Allocates the tables
+ * for the call and frees them; synchronises `stream`.  Returns CM_ERR_INVALID
+ * for null pointers, inverse not 0 or 1, and sizes other than a power of two
+ * <= CM_FFT_MAX_POW2 or a length <= CM_FFT_MAX_OTHER per axis; CM_ERR_OOM or
+ * CM_ERR_CUDA on a failed allocation or CUDA call. */
+#define CM_FFT_MAX_POW2 16384
+#define CM_FFT_MAX_OTHER 8192
+int cm_fft2d(cm_ctx* ctx, const float* in, float* out, int H, int W, int inverse, void* stream);
+
 int cm_recon(cm_ctx* ctx, const float* kspace, const unsigned char* mask, int H, int W,
              float alpha, int kind, int levels, int cycles, int cg_iters, const float* u0,
              float* u_out, const cm_options* opts /* host, nullable */,
@@ -384,7 +402,7 @@ int cm_recon(cm_ctx* ctx, const float* kspace, const unsigned char* mask, int H,
  * H x W or NULL: start from the filtered backprojection (pi / n_angles)
  * R^T (h * b), h the Ram-Lak kernel (h[0] = 1/4, h[k] = -1/(pi k)^2 for odd k,
  * 0 for even k, a direct convolution per angle).  trace_host as in
- * cm_recon; the CG and colour options as in cm_recon.  Needs no cuFFT.
+ * cm_recon; the CG and colour options as in cm_recon; no Fourier transform.
  * Synchronises `stream`.  Returns CM_ERR_INVALID for null pointers, sizes out
  * of range, n_angles outside 1 .. 100000, u_out aliasing sino, a bad alpha,
  * kind or option, cycles outside 0 .. 100000 or cg_iters outside 1 .. 1000;

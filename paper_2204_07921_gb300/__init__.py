@@ -18,6 +18,7 @@ __all__ = [
     "CMError", "Options", "Stats", "Context", "load", "cm_energy", "cm_curvature", "cm_phase",
     "cm_level", "cm_energy_noalloc", "cm_solve_batched", "cm_probe_alu", "cm_recon",
     "cm_recon_ct", "cm_radon", "cm_radon_adjoint", "cm_radon_bins", "cm_radon_entries",
+    "cm_fft2d",
     "cm_solve", "cm_auto_levels", "MEAN", "GAUSS", "MEAN_EULER", "GAUSS_EULER",
 ]
 
@@ -80,6 +81,7 @@ SIGNATURES = {
     "cm_radon_adjoint": (_I, [_P, _P, _I, _I, _I, _P, _P]),
     "cm_recon_ct": (_I, [_P, _P, _I, _I, _I, _F, _I, _I, _I, _I, _P, _P,
                          ctypes.POINTER(Options), _P, _P]),
+    "cm_fft2d": (_I, [_P, _P, _P, _I, _I, _I, _P]),
     "cm_recon": (_I, [_P, _P, _P, _I, _I, _F, _I, _I, _I, _I, _P, _P, ctypes.POINTER(Options),
                       _P, _P]),
     "cm_level": (_I, [_P, _P, _P, _P, _I, _I, _F, _I, _I, ctypes.POINTER(Options), _P, _P]),
@@ -330,6 +332,26 @@ def cm_solve(f, alpha: float, kind: int, levels: int = 0, cycles: int = 20, tol:
                              _stream_ptr(stream)),
              ok=(CM_OK, CM_NOT_CONVERGED))
     return u_out, st
+
+
+def cm_fft2d(x, inverse: bool = False, out=None, ctx: Context | None = None, stream=None):
+    """Unnormalised 2-D DFT of a CUDA complex64 H x W tensor (the library's
+    own transform of the MRI-like operator; exp(-2 pi i ...) forward,
+    exp(+2 pi i ...) inverse).  Returns out (may be x: in place)."""
+    import torch
+    if not (isinstance(x, torch.Tensor) and _on_gpu(x) and x.dtype == torch.complex64 and
+            x.dim() == 2 and x.is_contiguous()):
+        raise TypeError("x: expected a contiguous CUDA complex64 H x W tensor")
+    H, W = x.shape
+    if out is None:
+        out = torch.empty_like(x)
+    elif not (isinstance(out, torch.Tensor) and out.dtype == torch.complex64 and
+              out.shape == x.shape and out.is_contiguous() and out.device == x.device):
+        raise TypeError("out: expected a contiguous complex64 tensor of x's shape and device")
+    c = _ctx(ctx, x)
+    c._check(load().cm_fft2d(c.handle, x.data_ptr(), out.data_ptr(), H, W, int(bool(inverse)),
+                             _stream_ptr(stream)))
+    return out
 
 
 def cm_recon(kspace, mask, alpha: float, kind: int = MEAN, levels: int = 0, cycles: int = 5,

@@ -22,6 +22,7 @@
 #include "cm_batched.h"
 #include "cm_cnn.h"
 #include "cm_kernels.h"
+#include "cm_fft.h"
 #include "cm_recon.h"
 
 struct GraphKey {
@@ -389,6 +390,7 @@ int run_recon(cm_ctx* ctx, cm::ReconArgs& a, int levels, const cm_options& o, vo
     a.ncolors = o.ncolors;
     const char* msg = "";
     const int rc = cm::recon_run(ctx->recon, a, (cudaStream_t)stream, &msg);
+    if (rc == 1) return fail(ctx, CM_ERR_INVALID, std::string(name) + ": " + msg);
     if (rc == 3) return fail(ctx, CM_ERR_OOM, std::string(name) + ": " + msg);
     if (rc) return fail(ctx, CM_ERR_CUDA, std::string(name) + ": " + msg);
     return CM_OK;
@@ -438,6 +440,7 @@ int cm_create(cm_ctx** out, int device) {
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->cap_stream2, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cm::coarse_setup();
+    if (e == cudaSuccess) e = cm::fft_setup();
     if (e != cudaSuccess) {
         cm_destroy(ctx);
         return e == cudaErrorMemoryAllocation ? CM_ERR_OOM : CM_ERR_CUDA;
@@ -992,6 +995,28 @@ int cm_recon(cm_ctx* ctx, const float* kspace, const unsigned char* mask, int H,
     a.u = u_out;
     a.trace_host = trace_host;
     return run_recon(ctx, a, levels, o, stream, "cm_recon");
+}
+
+int cm_fft2d(cm_ctx* ctx, const float* in, float* out, int H, int W, int inverse,
+             void* stream) {
+    if (!ctx) return CM_ERR_INVALID;
+    if (!in || !out || !dims_ok(H, W) || !cm::fft_length_ok(H) || !cm::fft_length_ok(W) ||
+        (inverse != 0 && inverse != 1))
+        return fail(ctx, CM_ERR_INVALID, "cm_fft2d: invalid argument");
+    CM_CUDA(cudaSetDevice(ctx->device));
+    cm::FftPlan plan;
+    const int rc = cm::fft_plan_make(&plan, H, W);
+    if (rc) return fail(ctx, rc == 3 ? CM_ERR_OOM : CM_ERR_CUDA, "cm_fft2d: transform tables");
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = cudaSuccess;
+    if (out != in)
+        e = cudaMemcpyAsync(out, in, (size_t)H * W * 2 * sizeof(float), cudaMemcpyDeviceToDevice,
+                            st);
+    if (e == cudaSuccess) e = cm::fft2d(plan, reinterpret_cast<float2*>(out), inverse != 0, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cm::fft_plan_free(&plan);
+    if (e != cudaSuccess) return fail(ctx, CM_ERR_CUDA, std::string("cm_fft2d: ") + cudaGetErrorString(e));
+    return CM_OK;
 }
 
 int cm_radon_bins(int H, int W) { return dims_ok(H, W) ? cm::radon_bins(H, W) : -1; }

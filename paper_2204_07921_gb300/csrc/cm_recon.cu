@@ -15,16 +15,14 @@
 // early only on a zero residual or a non-positive p.Ap.  The start is the
 // zero-filled Re(A^H b) for MRI, the filtered backprojection (Ram-Lak) for CT.
 //
-// The transforms are cuFFT (single-precision C2C, unnormalised; the two
-// 1/sqrt(HW) factors of the orthonormal pair are folded into the mask
-// kernels), loaded with dlopen on first use so that the rest of the library
-// does not depend on it.  Every other step is a kernel of this file.  The
+// The transforms are the library's own (cm_fft.cu: single-precision
+// complex, unnormalised; the two 1/sqrt(HW) factors of the orthonormal pair
+// are folded into the mask kernels).  Every other step is a kernel of this
+// file.  The
 // CG scalars stay on the device; the reductions are FP64 with a fixed order
 // (per-CTA partials, the last CTA finishes), so a run is deterministic.  One
 // cycle is captured as a CUDA graph and launched once per cycle.
 #include <cuda_runtime.h>
-#include <cufft.h>
-#include <dlfcn.h>
 #include <math.h>
 #include <string.h>
 
@@ -32,41 +30,12 @@
 #include <vector>
 
 #include "cm_device.cuh"
+#include "cm_fft.h"
 #include "cm_kernels.h"
 #include "cm_recon.h"
 #include "cm_search.cuh"
 
 namespace cm {
-
-// ---------------------------------------------------------------------------
-// cuFFT entry points, resolved once.
-
-struct CufftApi {
-    decltype(&cufftPlan2d) plan2d = nullptr;
-    decltype(&cufftExecC2C) exec = nullptr;
-    decltype(&cufftSetStream) set_stream = nullptr;
-    decltype(&cufftDestroy) destroy = nullptr;
-    bool ok = false;
-};
-
-static const CufftApi& cufft_api() {
-    static const CufftApi api = [] {
-        CufftApi c;
-        const char* names[] = {"libcufft.so.12", "libcufft.so", "/usr/local/cuda/lib64/libcufft.so.12",
-                               "/usr/local/cuda/lib64/libcufft.so"};
-        void* h = nullptr;
-        for (const char* n : names)
-            if ((h = dlopen(n, RTLD_NOW | RTLD_LOCAL)) != nullptr) break;
-        if (!h) return c;
-        c.plan2d = (decltype(&cufftPlan2d))dlsym(h, "cufftPlan2d");
-        c.exec = (decltype(&cufftExecC2C))dlsym(h, "cufftExecC2C");
-        c.set_stream = (decltype(&cufftSetStream))dlsym(h, "cufftSetStream");
-        c.destroy = (decltype(&cufftDestroy))dlsym(h, "cufftDestroy");
-        c.ok = c.plan2d && c.exec && c.set_stream && c.destroy;
-        return c;
-    }();
-    return api;
-}
 
 // ---------------------------------------------------------------------------
 // Kernels.
@@ -474,8 +443,7 @@ struct ReconKey {
 
 struct ReconWork {
     int H = 0, W = 0;
-    cufftHandle plan = 0;
-    bool have_plan = false;
+    FftPlan plan;                 // MRI: the 2-D DFT tables
     float2 *X = nullptr, *Z = nullptr;
     float *c = nullptr, *r = nullptr, *p = nullptr, *q = nullptr;
     size_t nslots = 0;
@@ -523,8 +491,7 @@ static void free_buffers(ReconWork* w) {
     w->partials = w->scal = w->epart = nullptr;
     w->ticket = w->eticket = nullptr;
     w->stop = nullptr;
-    if (w->have_plan) cufft_api().destroy(w->plan);
-    w->have_plan = false;
+    fft_plan_free(&w->plan);
     w->H = w->W = 0;
 }
 
@@ -588,11 +555,11 @@ static int ensure_buffers(ReconWork* w, const ReconArgs& a, const char** msg) {
     RC(cudaMemset(w->eticket, 0, sizeof(unsigned)));
     w->nslots = need;
     if (a.op == RECON_MRI) {
-        if (cufft_api().plan2d(&w->plan, a.H, a.W, CUFFT_C2C) != CUFFT_SUCCESS) {
-            *msg = "cufftPlan2d failed";
-            return 2;
+        const int frc = fft_plan_make(&w->plan, a.H, a.W);
+        if (frc != 0) {
+            *msg = frc == 1 ? "image size beyond the transform's limits" : "FFT tables failed";
+            return frc == 3 ? 3 : 2;
         }
-        w->have_plan = true;
     } else {
         const size_t m = (size_t)a.n_angles * radon_bins(a.H, a.W);
         RC(cudaMalloc(&w->S, m * sizeof(float)));
@@ -615,10 +582,10 @@ static int ensure_buffers(ReconWork* w, const ReconArgs& a, const char** msg) {
     return 0;
 }
 
+enum { FFT_FORWARD = 0, FFT_INVERSE = 1 };
+
 static cudaError_t fft(ReconWork* w, float2* X, int dir, cudaStream_t st) {
-    if (cufft_api().set_stream(w->plan, st) != CUFFT_SUCCESS) return cudaErrorUnknown;
-    if (cufft_api().exec(w->plan, X, X, dir) != CUFFT_SUCCESS) return cudaErrorUnknown;
-    return cudaGetLastError();
+    return fft2d(w->plan, X, dir == FFT_INVERSE, st);
 }
 
 int radon_bins(int H, int W) {
@@ -674,7 +641,7 @@ static cudaError_t enqueue_objective(ReconWork* w, const ReconArgs& a, cudaStrea
     cudaError_t e;
     to_complex_kernel<<<gN, RT, 0, st>>>(a.u, w->X, N);
     if (a.op == RECON_MRI) {
-        if ((e = fft(w, w->X, CUFFT_FORWARD, st)) != cudaSuccess) return e;
+        if ((e = fft(w, w->X, FFT_FORWARD, st)) != cudaSuccess) return e;
         data_term_kernel<<<gN, RT, 0, st>>>(w->X, a.kspace, a.mask, N, s, w->partials, w->ticket,
                                             w->scal + 3);
     } else {
@@ -710,9 +677,9 @@ static cudaError_t enqueue_cycle(ReconWork* w, const ReconArgs& a, cudaStream_t 
             // right-hand side: Re <b - A u, A phi_i> + 2 alpha d_i
             to_complex_kernel<<<gN, RT, 0, st>>>(a.u, w->X, N);
             if (a.op == RECON_MRI) {
-                if ((e = fft(w, w->X, CUFFT_FORWARD, st)) != cudaSuccess) return e;
+                if ((e = fft(w, w->X, FFT_FORWARD, st)) != cudaSuccess) return e;
                 resid_kernel<<<gN, RT, 0, st>>>(w->X, a.kspace, a.mask, N, s);
-                if ((e = fft(w, w->X, CUFFT_INVERSE, st)) != cudaSuccess) return e;
+                if ((e = fft(w, w->X, FFT_INVERSE, st)) != cudaSuccess) return e;
             } else {
                 if ((e = ct_forward(w, a, w->X, w->S, nullptr, st)) != cudaSuccess) return e;
                 const int m = a.n_angles * radon_bins(a.H, a.W);
@@ -726,9 +693,9 @@ static cudaError_t enqueue_cycle(ReconWork* w, const ReconArgs& a, cudaStream_t 
                 double* rr_next = w->scal + ((it + 1) & 1);
                 scatter_kernel<<<gN, RT, 0, st>>>(w->p, w->Z, a.H, a.W, b, nc, k, rr, w->stop);
                 if (a.op == RECON_MRI) {
-                    if ((e = fft(w, w->Z, CUFFT_FORWARD, st)) != cudaSuccess) return e;
+                    if ((e = fft(w, w->Z, FFT_FORWARD, st)) != cudaSuccess) return e;
                     mask_scale_kernel<<<gN, RT, 0, st>>>(w->Z, a.mask, N, s2, w->stop);
-                    if ((e = fft(w, w->Z, CUFFT_INVERSE, st)) != cudaSuccess) return e;
+                    if ((e = fft(w, w->Z, FFT_INVERSE, st)) != cudaSuccess) return e;
                 } else {
                     if ((e = ct_forward(w, a, w->Z, w->S, w->stop, st)) != cudaSuccess) return e;
                     if ((e = ct_adjoint(w, a, w->S, w->Z, 1.0f, w->stop, st)) != cudaSuccess)
@@ -751,9 +718,9 @@ static cudaError_t enqueue_cycle(ReconWork* w, const ReconArgs& a, cudaStream_t 
 
 int recon_run(ReconWork* w, const ReconArgs& a, cudaStream_t st, const char** msg) {
     *msg = "";
-    if (a.op == RECON_MRI && !cufft_api().ok) {
-        *msg = "cuFFT (libcufft.so.12) could not be loaded";
-        return 2;
+    if (a.op == RECON_MRI && (!fft_length_ok(a.H) || !fft_length_ok(a.W))) {
+        *msg = "image size beyond the transform's limits";
+        return 1;
     }
     int rc = ensure_buffers(w, a, msg);
     if (rc) return rc;
@@ -775,7 +742,7 @@ int recon_run(ReconWork* w, const ReconArgs& a, cudaStream_t st, const char** ms
             RC(cudaMemcpyAsync(a.u, a.u0, N * sizeof(float), cudaMemcpyDeviceToDevice, st));
     } else if (a.op == RECON_MRI) {   // zero-filled start Re(A^H b)
         masked_data_kernel<<<grid_for(N), RT, 0, st>>>(w->X, a.kspace, a.mask, N, s);
-        RC(fft(w, w->X, CUFFT_INVERSE, st));
+        RC(fft(w, w->X, FFT_INVERSE, st));
         real_part_kernel<<<grid_for(N), RT, 0, st>>>(w->X, a.u, N);
         RC(cudaGetLastError());
     } else {   // filtered backprojection (pi / n) R^T (h * b)

@@ -5,7 +5,7 @@
 
 namespace cm {
 
-struct ReconWork;   // device buffers, the FFT plan and the captured cycle
+struct ReconWork;   // device buffers, the FFT tables and the captured cycle
 
 ReconWork* recon_work_create();
 void recon_work_destroy(ReconWork* w);
@@ -34,8 +34,9 @@ struct ReconArgs {
     double* trace_host;       // nullable, cycles + 1 entries: J before and after each cycle
 };
 
-// Runs the reconstruction on `st` and synchronises it.  Returns 0, or
-// 3 when out of memory, 2 for a CUDA or cuFFT failure (with *msg set).
+// Runs the reconstruction on `st` and synchronises it.  Returns 0, 1 for an
+// MRI image size beyond the transform's limits (fft_length_ok), 3 when out of
+// memory, 2 for a CUDA failure (with *msg set).
 int recon_run(ReconWork* w, const ReconArgs& a, cudaStream_t st, const char** msg);
 
 // The CT operator pair alone (device buffers; allocates temporaries;

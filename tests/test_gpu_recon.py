@@ -1,7 +1,7 @@
 """GPU parity of the reconstruction extension (Sec. 5: MRI-like A = M F, and
 CT with the Radon pair) against the FP64 oracle in oracle/recon.py.
 
-Tolerances: the GPU runs the same algorithm in FP32 (cuFFT single precision,
+Tolerances: the GPU runs the same algorithm in FP32 (the library's own FFT,
 FP32 CG vectors, FP64 reductions), the oracle in FP64.  One FFT round trip
 keeps ~1e-6 relative accuracy; the eight CG iterations of a colour step
 amplify rounding by at most a few times the system's condition number
