@@ -2,11 +2,13 @@
 //
 //  energy_kernel     F(u) = sum |kappa| + alpha/2 (u - f)^2 (Eq. MCM / Eq. GCM;
 //                    kappa of any of the four kinds of kappa_signed):
-//                    smem halo tile, FP32 per pixel, FP64 CTA partials and a
-//                    fixed-order FP64 finish in the last CTA (deterministic).
+//                    smem halo tile, FP32 per pixel and per warp, FP64 CTA
+//                    partials and a fixed-order FP64 finish in the last CTA
+//                    (deterministic).
 //  curvature_kernel  signed kappa per pixel (diagnostics and tests).
 #include <cuda_runtime.h>
 #include <math.h>
+#include <stdint.h>
 
 #include "cm_device.cuh"
 #include "cm_kernels.h"
@@ -19,6 +21,12 @@ namespace cm {
 constexpr int E_TW = 32;   // tile columns
 constexpr int E_TH = 32;   // tile rows (each thread 4 rows)
 
+// Reduction: FP32 per pixel, per thread (4 pixels) and per warp (a fixed
+// shuffle tree over 128 non-negative terms: relative error <= 8 eps32 ~ 5e-7),
+// then FP64: the CTA's 8 warp sums by one thread, the grid's CTA sums in a
+// fixed order by the last CTA.  FP64 stays out of the warp-wide code: the
+// GB300's FP64 pipe runs at a small fraction of its FP32 rate, and FP64
+// conversions and shuffles in every warp kept it about half busy.
 template <int KIND>
 __global__ void __launch_bounds__(256) energy_kernel(const float* __restrict__ u,
                                                      const float* __restrict__ f, int H, int W,
@@ -28,16 +36,44 @@ __global__ void __launch_bounds__(256) energy_kernel(const float* __restrict__ u
                                                      const int* __restrict__ active) {
     if (active && *active == 0) return;
     __shared__ float tile[E_TH + 2][E_TW + 3];
-    __shared__ double wsum[8];
+    __shared__ float wsum[8];
+    __shared__ double dsum[8];
     __shared__ bool is_last;
     const int r0 = blockIdx.y * E_TH, c0 = blockIdx.x * E_TW;
-    for (int i = threadIdx.x; i < (E_TH + 2) * (E_TW + 2); i += 256) {
-        int lr = i / (E_TW + 2), lc = i - lr * (E_TW + 2);
-        int r = clampi(r0 - 1 + lr, 0, H - 1), c = clampi(c0 - 1 + lc, 0, W - 1);
-        tile[lr][lc] = u[(size_t)r * W + c];
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    // the f values of this thread's pixels, requested before the tile barrier
+    float fv[E_TH / 8];
+#pragma unroll
+    for (int i = 0; i < E_TH / 8; ++i) {
+        const int r = r0 + ty + 8 * i, c = c0 + tx;
+        fv[i] = (r < H && c < W) ? f[(size_t)r * W + c] : 0.0f;
+    }
+    // Tiles away from the left and right edges of an image whose rows are
+    // 16-byte aligned read the halo columns c0 - 1 .. c0 + 32 as the float4
+    // words of the aligned span c0 - 4 .. c0 + 35; rows clamp as below.
+    const bool vec = (W & 3) == 0 && (reinterpret_cast<uintptr_t>(u) & 15) == 0 && c0 >= 4 &&
+                     c0 + E_TW + 4 <= W;
+    if (vec) {
+        constexpr int NV = (E_TW + 8) / 4;   // float4 words per tile row
+        for (int i = threadIdx.x; i < (E_TH + 2) * NV; i += 256) {
+            const int lr = i / NV, v = i - lr * NV;
+            const int r = clampi(r0 - 1 + lr, 0, H - 1);
+            const float4 q4 = *reinterpret_cast<const float4*>(u + (size_t)r * W + (c0 - 4 + 4 * v));
+            const float e[4] = {q4.x, q4.y, q4.z, q4.w};
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int lc = 4 * v - 3 + q;   // column c0 - 4 + 4v + q, tile column + 1
+                if (lc >= 0 && lc < E_TW + 2) tile[lr][lc] = e[q];
+            }
+        }
+    } else {
+        for (int i = threadIdx.x; i < (E_TH + 2) * (E_TW + 2); i += 256) {
+            int lr = i / (E_TW + 2), lc = i - lr * (E_TW + 2);
+            int r = clampi(r0 - 1 + lr, 0, H - 1), c = clampi(c0 - 1 + lc, 0, W - 1);
+            tile[lr][lc] = u[(size_t)r * W + c];
+        }
     }
     __syncthreads();
-    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
     float acc = 0.0f;
 #pragma unroll
     for (int i = 0; i < E_TH / 8; ++i) {
@@ -49,20 +85,19 @@ __global__ void __launch_bounds__(256) energy_kernel(const float* __restrict__ u
             for (int a = 0; a < 3; ++a)
 #pragma unroll
                 for (int b = 0; b < 3; ++b) w[3 * a + b] = tile[lr + a][tx + b];
-            float e = w[4] - f[(size_t)r * W + c];
+            float e = w[4] - fv[i];
             acc += abs_curvature<KIND>(w) + 0.5f * alpha * e * e;
         }
     }
-    double d = (double)acc;
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) d += __shfl_xor_sync(0xffffffffu, d, off);
-    if (tx == 0) wsum[ty] = d;
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+    if (tx == 0) wsum[ty] = acc;
     __syncthreads();
     const int nblk = gridDim.x * gridDim.y;
     const int bid = blockIdx.y * gridDim.x + blockIdx.x;
     if (threadIdx.x == 0) {
         double s = 0.0;
-        for (int i = 0; i < 8; ++i) s += wsum[i];
+        for (int i = 0; i < 8; ++i) s += (double)wsum[i];
         partials[bid] = s;
         __threadfence();
         unsigned int t = atomicAdd(ticket, 1u);
@@ -77,11 +112,11 @@ __global__ void __launch_bounds__(256) energy_kernel(const float* __restrict__ u
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
     __syncthreads();
-    if (tx == 0) wsum[ty] = s;
+    if (tx == 0) dsum[ty] = s;
     __syncthreads();
     if (threadIdx.x == 0) {
         double t = 0.0;
-        for (int i = 0; i < 8; ++i) t += wsum[i];
+        for (int i = 0; i < 8; ++i) t += dsum[i];
         *E_out = t;
         *ticket = 0u;   // ready for the next launch
     }

@@ -16,6 +16,7 @@
 // image border, where clamping duplicates p); only FP32 rounding differs.
 #include <cuda_runtime.h>
 #include <math.h>
+#include <stdint.h>
 
 #include "cm_device.cuh"
 #include "cm_kernels.h"
@@ -169,10 +170,42 @@ __global__ void __launch_bounds__(128, CM_B1_MIN_BLOCKS) phase_b1_kernel(const f
     constexpr int TW = B1Tile<NCOL>::TW, TH = B1Tile<NCOL>::TH;
     __shared__ float tile[TH + 4][TW + 5];
     const int r0 = blockIdx.y * TH, c0 = blockIdx.x * TW;
-    for (int i = threadIdx.x; i < (TH + 4) * (TW + 4); i += 128) {
-        int lr = i / (TW + 4), lc = i - lr * (TW + 4);
-        int r = clampi(r0 - 2 + lr, 0, H - 1), c = clampi(c0 - 2 + lc, 0, W - 1);
-        tile[lr][lc] = phase_read(S, R, r, c, W, 0, NCOL, k);
+    // Tiles away from the left and right edges of an image whose rows are
+    // 16-byte aligned: the halo columns c0 - 2 .. c0 + TW + 1 lie in the
+    // aligned span c0 - 4 .. c0 + TW + 3, read as float4 words of S (and of R
+    // from the second colour on); each pixel keeps the array that holds its
+    // phase state (R for colours < k).  Rows clamp as in the scalar path.
+    const bool vec = (W & 3) == 0 &&
+                     ((reinterpret_cast<uintptr_t>(S) | reinterpret_cast<uintptr_t>(R)) & 15) == 0 &&
+                     c0 >= 4 && c0 + TW + 4 <= W;
+    if (vec) {
+        constexpr int NV = (TW + 8) / 4;   // float4 words per tile row
+        for (int i = threadIdx.x; i < (TH + 4) * NV; i += 128) {
+            const int lr = i / NV, v = i - lr * NV;
+            const int r = clampi(r0 - 2 + lr, 0, H - 1);
+            const int cb = c0 - 4 + 4 * v;   // column of the word's first element
+            const size_t off = (size_t)r * W + cb;
+            const float4 sv = *reinterpret_cast<const float4*>(S + off);
+            float e[4] = {sv.x, sv.y, sv.z, sv.w};
+            if (k > 0) {
+                const float4 rv = *reinterpret_cast<const float4*>(R + off);
+                const float o[4] = {rv.x, rv.y, rv.z, rv.w};
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    if (pixel_colour(r, cb + q, 0, NCOL) < k) e[q] = o[q];
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int lc = 4 * v - 2 + q;   // cb + q - (c0 - 2)
+                if (lc >= 0 && lc < TW + 4) tile[lr][lc] = e[q];
+            }
+        }
+    } else {
+        for (int i = threadIdx.x; i < (TH + 4) * (TW + 4); i += 128) {
+            int lr = i / (TW + 4), lc = i - lr * (TW + 4);
+            int r = clampi(r0 - 2 + lr, 0, H - 1), c = clampi(c0 - 2 + lc, 0, W - 1);
+            tile[lr][lc] = phase_read(S, R, r, c, W, 0, NCOL, k);
+        }
     }
     __syncthreads();
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
