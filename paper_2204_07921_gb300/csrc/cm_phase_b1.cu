@@ -172,9 +172,12 @@ __global__ void __launch_bounds__(128, CM_B1_MIN_BLOCKS) phase_b1_kernel(const f
     const int r0 = blockIdx.y * TH, c0 = blockIdx.x * TW;
     // Tiles away from the left and right edges of an image whose rows are
     // 16-byte aligned: the halo columns c0 - 2 .. c0 + TW + 1 lie in the
-    // aligned span c0 - 4 .. c0 + TW + 3, read as float4 words of S (and of R
-    // from the second colour on); each pixel keeps the array that holds its
-    // phase state (R for colours < k).  Rows clamp as in the scalar path.
+    // aligned span c0 - 4 .. c0 + TW + 3, read as float4 words; each pixel
+    // keeps the array that holds its phase state (R for colours < k).  A row
+    // of 1 x 1 blocks holds the colours cmin .. cmax (both for the
+    // checkerboard, p (r mod p) + 0 .. p - 1 for p x p colourings), so R is
+    // read only on rows with a colour < k and S only on rows with a colour
+    // >= k.  Rows clamp as in the scalar path.
     const bool vec = (W & 3) == 0 &&
                      ((reinterpret_cast<uintptr_t>(S) | reinterpret_cast<uintptr_t>(R)) & 15) == 0 &&
                      c0 >= 4 && c0 + TW + 4 <= W;
@@ -185,15 +188,17 @@ __global__ void __launch_bounds__(128, CM_B1_MIN_BLOCKS) phase_b1_kernel(const f
             const int r = clampi(r0 - 2 + lr, 0, H - 1);
             const int cb = c0 - 4 + 4 * v;   // column of the word's first element
             const size_t off = (size_t)r * W + cb;
-            const float4 sv = *reinterpret_cast<const float4*>(S + off);
+            constexpr int P = B1Tile<NCOL>::P;
+            const int cmin = NCOL == 2 ? 0 : P * (r % P);
+            const int cmax = NCOL == 2 ? 1 : cmin + P - 1;
+            float4 sv = make_float4(0.0f, 0.0f, 0.0f, 0.0f), rv = sv;
+            if (cmax >= k) sv = *reinterpret_cast<const float4*>(S + off);
+            if (k > cmin) rv = *reinterpret_cast<const float4*>(R + off);
             float e[4] = {sv.x, sv.y, sv.z, sv.w};
-            if (k > 0) {
-                const float4 rv = *reinterpret_cast<const float4*>(R + off);
-                const float o[4] = {rv.x, rv.y, rv.z, rv.w};
+            const float o[4] = {rv.x, rv.y, rv.z, rv.w};
 #pragma unroll
-                for (int q = 0; q < 4; ++q)
-                    if (pixel_colour(r, cb + q, 0, NCOL) < k) e[q] = o[q];
-            }
+            for (int q = 0; q < 4; ++q)
+                if (pixel_colour(r, cb + q, 0, NCOL) < k) e[q] = o[q];
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 const int lc = 4 * v - 2 + q;   // cb + q - (c0 - 2)
