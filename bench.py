@@ -347,7 +347,7 @@ def batched_measurement(cm, torch, synth, ctx, dev, rank=0, world=1):
         return sts
 
     res = {"schedule": {k: brec[k] for k in ("G", "K", "ncolors", "coarse_ncolors", "coarse_spec",
-                                             "coarse_dmax")}}
+                                             "coarse_dmax", "shapes")}}
     for name, fn in (("batched", batched), ("one_at_a_time", sequential)):
         fn()   # warm-up (graph capture)
         torch.cuda.synchronize()

@@ -108,6 +108,20 @@ typedef struct {
                             of (2^j - 1) x (2^j - 1) pixels (Sec. 2.2: 1, 3, 7, 15, ...), with
                             levels = 0 meaning the largest side <= min(H, W) / 2.  Levels of
                             odd side run the per-phase kernels (direct block sums and apply) */
+    int shapes;          /* kernel shapes of the levels b = 2 .. 32 (power-of-two sides), one
+                            bit each, 0 = the default shape (cm_options_default: 0), chosen by
+                            the autotuner per shape class; the candidates searched and the
+                            tie rule are the same, only the threads per block and the FP32
+                            order of the ring sums differ:
+                            bit 0 (b = 2):  8 lanes, two ring pixels each, instead of the
+                                            rotation-specialised 4-lane kernel;
+                            bit 1 (b = 4):  32 lanes, one ring pixel each, instead of 16 x 2;
+                            bit 2 (b = 8):  a 64-thread CTA, one ring pixel each, instead of
+                                            a warp with two;
+                            bit 3 (b = 16): a warp, four ring pixels per lane, instead of a
+                                            128-thread CTA with one;
+                            bit 4 (b = 32): a 128-thread CTA, two ring pixels per thread,
+                                            instead of a 256-thread CTA with one */
 } cm_options;
 
 /* Solve statistics (host struct, filled by cm_solve). */

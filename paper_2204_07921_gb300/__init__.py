@@ -43,7 +43,8 @@ class Options(ctypes.Structure):
                 ("use_graph", ctypes.c_int), ("max_trace", ctypes.c_int),
                 ("one_step", ctypes.c_int), ("vcycle", ctypes.c_int),
                 ("coarse_spec", ctypes.c_int), ("coarse_dmax", ctypes.c_int),
-                ("coarse_ncolors", ctypes.c_int), ("block_sides", ctypes.c_int)]
+                ("coarse_ncolors", ctypes.c_int), ("block_sides", ctypes.c_int),
+                ("shapes", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):

@@ -16,7 +16,12 @@ seeded image that is not one of the measured workloads):
    corner pixels of their rings;
 4. the coarse levels' kernel shape -- how many candidates share one cluster
    reduction (first-pair speculation, golden steps per round), which changes
-   the number of barriers and not the decisions.
+   the number of barriers and not the decisions;
+5. the kernel shapes of the levels b = 2 .. 32 (cm_options.shapes: threads
+   per block and ring pixels per thread), one level at a time: the level's
+   alternative shape is kept only if the solve is faster by more than
+   `SHAPE_MARGIN` at an energy within the slack (the shapes differ only in
+   the FP32 order of the ring sums, so their energies agree to rounding).
 
 Each stage times a solve to tolerance for every candidate and keeps the
 fastest whose final energy is within `ENERGY_SLACK` of the lowest final
@@ -33,7 +38,9 @@ COLOURS = (4, 2, 0)
 COARSE_COLOURS = (0, 2)
 COARSE = ((-1, 0), (0, 4), (1, 4), (0, 2), (0, 1))   # (coarse_spec, coarse_dmax)
 ENERGY_SLACK = 2e-3
-CACHE_VERSION = 3
+SHAPE_MARGIN = 0.01
+SHAPE_LEVELS = 5          # cm_options.shapes: bits for b = 2, 4, 8, 16, 32
+CACHE_VERSION = 4
 
 
 def choose(results, slack: float = ENERGY_SLACK):
@@ -44,6 +51,21 @@ def choose(results, slack: float = ENERGY_SLACK):
     e_best = min(r["energy"] for r in results)
     ok = [r for r in results if r["energy"] <= e_best + slack * abs(e_best)]
     return min(ok, key=lambda r: (r["seconds"], -r.get("G", 0), -r.get("K", 0)))
+
+
+def choose_shape(base, alt, slack: float = ENERGY_SLACK, margin: float = SHAPE_MARGIN):
+    """base, alt: results of the solve with a level's default and alternative
+    kernel shape.  The alternative wins only if it is faster by more than
+    `margin` (relative) and its energy is within `slack` of base's."""
+    if alt["energy"] > base["energy"] + slack * abs(base["energy"]):
+        return base
+    return alt if alt["seconds"] < (1.0 - margin) * base["seconds"] else base
+
+
+def shape_bits(levels: int):
+    """Bits of cm_options.shapes that concern a solve with `levels` levels
+    (block sides 1 .. 2^(levels - 1)): bit lb - 1 for b = 2^lb, lb = 1 .. 5."""
+    return [lb - 1 for lb in range(1, min(SHAPE_LEVELS, levels - 1) + 1)]
 
 
 def _cache_path():
@@ -77,7 +99,8 @@ def tune(H: int, W: int, kind: int, alpha: float, tol: float = 1e-4, ncolors=Non
         return cm.default_options(ncolors=rec["ncolors"], grid_points=rec["G"],
                                   golden_evals=rec["K"], coarse_spec=rec["coarse_spec"],
                                   coarse_dmax=rec["coarse_dmax"],
-                                  coarse_ncolors=rec.get("coarse_ncolors", 0))
+                                  coarse_ncolors=rec.get("coarse_ncolors", 0),
+                                  shapes=rec.get("shapes", 0))
 
     if key in cache:
         return options(cache[key]), cache[key]
@@ -104,7 +127,7 @@ def tune(H: int, W: int, kind: int, alpha: float, tol: float = 1e-4, ncolors=Non
         return {**cfg, "seconds": best, "cycles": st.cycles_run, "energy": st.energy_final}
 
     cfg = {"G": 5, "K": 6, "ncolors": 4 if ncolors is None else ncolors, "coarse_spec": -1,
-           "coarse_dmax": 0, "coarse_ncolors": 0}
+           "coarse_dmax": 0, "coarse_ncolors": 0, "shapes": 0}
     stages = {}
     stages["budget"] = [run({**cfg, "G": G, "K": K}) for G, K in candidates]
     pick = choose(stages["budget"])
@@ -117,6 +140,13 @@ def tune(H: int, W: int, kind: int, alpha: float, tol: float = 1e-4, ncolors=Non
     stages["coarse"] = [run({**cfg, "coarse_spec": sp, "coarse_dmax": dm}) for sp, dm in COARSE]
     pick = choose(stages["coarse"])
     cfg.update(coarse_spec=pick["coarse_spec"], coarse_dmax=pick["coarse_dmax"])
+    base = run(cfg)
+    stages["shapes"] = [base]
+    for bit in shape_bits(cm.cm_auto_levels(H, W)):
+        alt = run({**cfg, "shapes": cfg["shapes"] ^ (1 << bit)})
+        stages["shapes"].append(alt)
+        base = choose_shape(base, alt)
+        cfg["shapes"] = base["shapes"]
     rec = {**cfg, "stages": stages, "image": f"{H}x{W}", "calibration_seed": seed}
     if use_cache:
         cache = _load_cache(path)

@@ -30,7 +30,7 @@ struct GraphKey {
     const float* R;
     const float* f;
     int H, W, kind, levels, ncolors, G, K, use_paper, one_step, vcycle, coarse_spec, coarse_dmax,
-        block_sides, coarse_ncolors;
+        block_sides, coarse_ncolors, shapes;
     float alpha;
     double tol;
     int cycles, trace_cap;
@@ -192,6 +192,7 @@ int check_opts(cm_ctx* ctx, const cm_options& o) {
         return fail(ctx, CM_ERR_INVALID, "coarse_dmax must be 0 .. 4");
     if (o.block_sides != 0 && o.block_sides != 1)
         return fail(ctx, CM_ERR_INVALID, "block_sides must be 0 or 1");
+    if (o.shapes < 0 || o.shapes > 31) return fail(ctx, CM_ERR_INVALID, "shapes must be 0 .. 31");
     if (o.coarse_ncolors != 0 && o.coarse_ncolors != 2 && o.coarse_ncolors != 4 &&
         o.coarse_ncolors != 9 && o.coarse_ncolors != 16)
         return fail(ctx, CM_ERR_INVALID, "coarse_ncolors must be 0, 2, 4, 9 or 16");
@@ -244,6 +245,7 @@ cm::PhaseArgs phase_args(const float* S, float* R, const float* f, int H, int W,
     a.one_step = o.one_step;
     a.coarse_spec = o.coarse_spec;
     a.coarse_dmax = o.coarse_dmax;
+    a.shapes = o.shapes;
     a.c_out = nullptr;
     return a;
 }
@@ -410,6 +412,7 @@ int cm_options_default(cm_options* o) {
     o->vcycle = 0;
     o->coarse_spec = -1;
     o->coarse_dmax = 0;
+    o->shapes = 0;
     o->coarse_ncolors = 0;
     o->block_sides = 0;
     return CM_OK;
@@ -597,6 +600,7 @@ int cm_solve(cm_ctx* ctx, const float* f, int H, int W, float alpha, int kind, i
         key.coarse_dmax = o.coarse_dmax;
         key.block_sides = o.block_sides;
         key.coarse_ncolors = o.coarse_ncolors;
+        key.shapes = o.shapes;
         key.alpha = alpha;
         key.tol = tol;
         key.cycles = cycles;

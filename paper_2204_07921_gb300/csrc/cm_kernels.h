@@ -81,6 +81,7 @@ struct PhaseArgs {
     int one_step = 0; // the paper's single step per block instead of the search
     int coarse_spec = -1;   // coarse levels: first-pair speculation (-1: the level's default)
     int coarse_dmax = 0;    // coarse levels: golden steps per reduction (0: the level's default)
+    int shapes = 0;         // bit lb - 1: the alternative kernel shape of level b = 1 << lb (2 .. 32)
     float* c_out;     // nullable: per-block corrections
     const int* active = nullptr;   // nullable: kernels return at once when *active == 0
 };

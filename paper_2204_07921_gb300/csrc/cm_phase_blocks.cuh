@@ -710,19 +710,29 @@ static cudaError_t launch_blocks_kind(const PhaseArgs& A, cudaStream_t st) {
     const int b = 1 << A.lb;
     const int nbi = (A.H + b - 1) / b, nbj = (A.W + b - 1) / b;
     const int nact = active_slots(nbi, nbj, A.ncolors);
-    // ring of a full block: 8b pixels = Q * CT * RPT slots
+    // ring of a full block: 8b pixels = Q * CT * RPT slots.  Bit lb - 1 of
+    // A.shapes (levels b = 2 .. 32) selects the level's alternative shape.
+    const bool alt = A.lb >= 1 && A.lb <= 5 && ((A.shapes >> (A.lb - 1)) & 1);
     switch (A.lb) {
         case 1:
-            if (CM_B2_FAST)
+            if (CM_B2_FAST && !alt)
                 return launch_k(phase_b2_kernel<KIND>, dim3((nact + 31) / 32), dim3(128), st, 1,
                                 A.S, A.R, A.f, A.H, A.W,
                                 SearchParams{A.alpha, A.G, A.K, 1, 4, A.one_step},
                                 A.ncolors, A.colour, A.c_out, A.active);
             return launch_warp<KIND, CM_B2_GT, 16 / CM_B2_GT>(A, nact, st);
-        case 2: return launch_warp<KIND, CM_B4_GT, 32 / CM_B4_GT>(A, nact, st);
-        case 3: return launch_warp<KIND, 32, 2>(A, nact, st);
-        case 4: return launch_cluster<KIND, 128, 1, 1>(A, nact, st);
-        case 5: return launch_cluster<KIND, 256, 1, 1>(A, nact, st);
+        case 2:
+            if (alt) return launch_warp<KIND, 32, 1>(A, nact, st);
+            return launch_warp<KIND, CM_B4_GT, 32 / CM_B4_GT>(A, nact, st);
+        case 3:
+            if (alt) return launch_cluster<KIND, 64, 1, 1>(A, nact, st);
+            return launch_warp<KIND, 32, 2>(A, nact, st);
+        case 4:
+            if (alt) return launch_warp<KIND, 32, 4>(A, nact, st);
+            return launch_cluster<KIND, 128, 1, 1>(A, nact, st);
+        case 5:
+            if (alt) return launch_cluster<KIND, 128, 1, 2>(A, nact, st);
+            return launch_cluster<KIND, 256, 1, 1>(A, nact, st);
         case 6: return launch_cluster<KIND, 256, 2, 1>(A, nact, st);
         case 7: return launch_cluster<KIND, 256, 4, 1>(A, nact, st);
         case 8: return launch_cluster<KIND, 256, 8, 1>(A, nact, st);

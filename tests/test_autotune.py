@@ -19,3 +19,19 @@ def test_choose_ties_prefer_larger_budget():
     assert autotune.choose(res)["G"] == 9
     with pytest.raises(ValueError):
         autotune.choose([])
+
+
+def test_shape_needs_a_margin_and_the_energy():
+    base = dict(shapes=0, seconds=0.0100, energy=100.0)
+    assert autotune.choose_shape(base, dict(shapes=1, seconds=0.0099, energy=100.0)) is base
+    alt = dict(shapes=1, seconds=0.0098, energy=100.0)
+    assert autotune.choose_shape(base, alt) is alt
+    assert autotune.choose_shape(base, dict(shapes=1, seconds=0.005, energy=101.0)) is base
+    assert autotune.choose_shape(base, dict(shapes=1, seconds=0.005, energy=99.0))["shapes"] == 1
+
+
+def test_shape_bits_follow_the_levels():
+    assert autotune.shape_bits(1) == []          # b = 1 only
+    assert autotune.shape_bits(3) == [0, 1]      # b = 2, 4
+    assert autotune.shape_bits(6) == [0, 1, 2, 3, 4]
+    assert autotune.shape_bits(10) == [0, 1, 2, 3, 4]

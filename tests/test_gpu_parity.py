@@ -108,23 +108,24 @@ def test_curvature_parity(kind):
     assert np.all(np.abs(kg - ko) <= bound)
 
 
-def gpu_phase(u, f, alpha, kind, b, ncolors, k, G=G_DEF, K=K_DEF, use_paper=1, one_step=0):
+def gpu_phase(u, f, alpha, kind, b, ncolors, k, G=G_DEF, K=K_DEF, use_paper=1, one_step=0,
+              shapes=0):
     H, W = u.shape
     S = to_dev(u)
     R = S.clone()
     nb = ((H + b - 1) // b) * ((W + b - 1) // b)
     cbuf = torch.full((nb,), float("nan"), device=DEV)
     opts = cm.default_options(ncolors=ncolors, grid_points=G, golden_evals=K,
-                              paper_candidate=use_paper, one_step=one_step)
+                              paper_candidate=use_paper, one_step=one_step, shapes=shapes)
     cm.cm_phase(S, R, to_dev(f), alpha, kind, b, k, options=opts, c_out=cbuf)
     torch.cuda.synchronize()
     return host(R), host(cbuf)
 
 
-def check_phase(u, f, alpha, kind, b, ncolors, k, sample=None, one_step=False):
+def check_phase(u, f, alpha, kind, b, ncolors, k, sample=None, one_step=False, shapes=0):
     """GPU phase from state u vs oracle; returns (n, match, tie, fails)."""
     H, W = u.shape
-    Rg, cg = gpu_phase(u, f, alpha, kind, b, ncolors, k, one_step=int(one_step))
+    Rg, cg = gpu_phase(u, f, alpha, kind, b, ncolors, k, one_step=int(one_step), shapes=shapes)
     nbj = (W + b - 1) // b
     cgd, cod = {}, {}
     if sample is None:
@@ -181,6 +182,57 @@ def test_phase_parity_small(shape, kind, ncolors):
     print(f"\n{shape} kind={kind} ncol={ncolors}: {tot}")
     assert not fails, fails[:5]
     assert tot["tie"] <= max(2, 0.01 * tot["n"])
+
+
+@pytest.mark.parametrize("kind", [cm.MEAN, cm.GAUSS_EULER])
+@pytest.mark.parametrize("bit", range(5))
+@pytest.mark.parametrize("ncolors", [2, 4])
+def test_alternative_shapes_phase_parity(kind, bit, ncolors):
+    """Each level's alternative kernel shape (cm_options.shapes bit
+    lb - 1, b = 2 .. 32) on every colour of its level against the oracle,
+    on a ragged image (partial blocks at the right and bottom edges)."""
+    H, W = 137, 150
+    img = synth.piecewise_image(H, W, 600 + bit, 8, 0.08)
+    f = img.f
+    u = oracle.cycle(f.astype(np.float64), f.astype(np.float64), 20.0, kind,
+                     levels=1).astype(np.float32)
+    b = 2 << bit
+    tot = np.zeros(3, int)
+    fails = []
+    for k in range(ncolors):
+        n, m, t, fl = check_phase(u, f, 20.0, kind, b, ncolors, k, shapes=1 << bit)
+        tot += (n, m, t)
+        fails += fl
+    print(f"\nshape bit {bit} (b={b}) kind={kind} ncol={ncolors}: {tot}")
+    assert not fails, fails[:5]
+    assert tot[2] <= max(2, 0.01 * tot[0])
+
+
+def test_alternative_shapes_solve():
+    """With every alternative shape: the device loop equals the host loop,
+    the batched solve equals the single ones bit for bit, and the final
+    energy is the default shapes' to 1e-3 (only the FP32 order of the ring
+    sums differs) and the oracle's energy of the result to 1e-5."""
+    shapes = [(300, 260), (140, 150)]
+    fs = [synth.piecewise_image(H, W, 70 + H, 10, 0.08).f for H, W in shapes]
+    res = []
+    for use_graph in (1, 0):
+        opts = cm.default_options(ncolors=4, use_graph=use_graph, shapes=31)
+        res.append([cm.cm_solve(to_dev(f), 20.0, cm.MEAN, cycles=8, tol=0.0, options=opts)
+                    for f in fs])
+    for (ua, sa), (ub, sb) in zip(*res):
+        assert torch.equal(ua, ub) and sa.trace() == sb.trace()
+    opts = cm.default_options(ncolors=4, shapes=31)
+    ub, sb = cm.cm_solve_batched([to_dev(f) for f in fs], [20.0] * 2, [cm.MEAN] * 2, cycles=8,
+                                 tol=0.0, options=opts)
+    for (ua, sa), u2, s2 in zip(res[0], ub, sb):
+        assert torch.equal(ua, u2) and sa.trace() == s2.trace()
+    for f, (u, st) in zip(fs, res[0]):
+        _, sd = cm.cm_solve(to_dev(f), 20.0, cm.MEAN, cycles=8, tol=0.0,
+                            options=cm.default_options(ncolors=4))
+        Eg = oracle.energy(host(u).astype(np.float64), f.astype(np.float64), 20.0, cm.MEAN)
+        assert abs(st.energy_final - Eg) <= 1e-5 * abs(Eg)
+        assert abs(st.energy_final - sd.energy_final) <= 1e-3 * abs(sd.energy_final)
 
 
 def test_phase_parity_512_gauss_sampled():
