@@ -158,8 +158,9 @@ const char* cm_last_error(const cm_ctx* ctx);
 int cm_auto_levels(int H, int W);
 
 /* Discrete energy F(u) of Eq. (MCM) (kind 0) or Eq. (GCM) (kind 1).
- * u, f: device, H x W.  Per-pixel terms in FP32, summed in FP64 on the
- * device in a fixed order (bit-reproducible).  *E_host (host) receives F.
+ * u, f: device, H x W.  Per-pixel terms in FP32, summed in FP32 over each
+ * 32 x 32 tile and those sums in FP64, on the device in a fixed order
+ * (bit-reproducible).  *E_host (host) receives F.
  * Synchronises `stream`. */
 int cm_energy(cm_ctx* ctx, const float* u, const float* f, int H, int W, float alpha,
               int kind, double* E_host, void* stream);

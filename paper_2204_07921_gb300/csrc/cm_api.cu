@@ -13,7 +13,10 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include <algorithm>
+#include <chrono>
 #include <string>
 
 #include <vector>
@@ -36,6 +39,45 @@ struct GraphKey {
     int cycles, trace_cap;
     bool operator==(const GraphKey& o) const { return memcmp(this, &o, sizeof(GraphKey)) == 0; }
 };
+
+// Tracing: an NVTX range (header-only NVTX 3; a no-op unless a profiler
+// injects its tool) over every call, cycle, level and colour enqueued on the
+// host.  A graph-captured solve carries the ranges of its capture; its
+// replays appear as one range per call.
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    NvtxRange(const char* fmt, int a, int b = 0, int c = 0) {
+        char buf[96];
+        snprintf(buf, sizeof buf, fmt, a, b, c);
+        nvtxRangePushA(buf);
+    }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
+
+// Logging: CM_LOG=1 prints one line per solve to stderr (size, kind, alpha,
+// cycles, first and last energy, convergence, energy rises, wall time of the
+// call); CM_LOG=2 adds the energy of every cycle.  Read once per process.
+int log_level() {
+    static const int level = [] {
+        const char* e = getenv("CM_LOG");
+        return e ? atoi(e) : 0;
+    }();
+    return level;
+}
+
+void log_solve(const char* what, int i, int H, int W, int kind, float alpha, int L,
+               const cm_stats& st, double ms) {
+    fprintf(stderr,
+            "[cm] %s%s%d %dx%d kind=%d alpha=%g levels=%d cycles=%d E %.9g -> %.9g "
+            "converged=%d rises=%d %.3f ms\n",
+            what, i >= 0 ? " image " : "", i >= 0 ? i : 0, H, W, kind, alpha, L, st.cycles_run,
+            st.energy_initial, st.energy_final, st.converged, st.monotone_violations, ms);
+    if (log_level() >= 2)
+        for (int c = 0; c < st.trace_len; ++c)
+            fprintf(stderr, "[cm]   cycle %d E %.12g\n", c, st.energy_trace[c]);
+}
 
 struct cm_ctx {
     int device = 0;
@@ -258,6 +300,7 @@ cudaError_t enqueue_level(float* tsums, float* cj, const float* S, float* R, con
                           int H, int W, float alpha, int kind, int b, const cm_options& o,
                           float* c_out, const int* active, cudaStream_t st,
                           bool sums_ready = false) {
+    NvtxRange level("level b=%d", b);
     if (coarse_side(b)) {
         cm::PhaseArgs a = phase_args(S, R, f, H, W, alpha, kind, b, 0, o);
         a.c_out = c_out;
@@ -266,6 +309,7 @@ cudaError_t enqueue_level(float* tsums, float* cj, const float* S, float* R, con
     }
     const int nc = cm::level_colours(o.ncolors, b, o.coarse_ncolors);
     for (int k = 0; k < nc; ++k) {
+        NvtxRange colour("colour %d", k);
         cm::PhaseArgs a = phase_args(S, R, f, H, W, alpha, kind, b, k, o);
         a.c_out = c_out;
         a.active = active;
@@ -383,6 +427,7 @@ cudaError_t capture_solve(cm_ctx* ctx, float* u, float* Y, const float* f, int H
 // context's reconstruction buffers, the run and its status.
 int run_recon(cm_ctx* ctx, cm::ReconArgs& a, int levels, const cm_options& o, void* stream,
               const char* name) {
+    NvtxRange range(a.op == cm::RECON_MRI ? "cm_recon %dx%d" : "cm_recon_ct %dx%d", a.H, a.W);
     const int L = solve_levels(levels, a.H, a.W, o);
     if (!levels_ok(L, o)) return fail(ctx, CM_ERR_INVALID, std::string(name) + ": too many levels");
     CM_CUDA(cudaSetDevice(ctx->device));
@@ -548,9 +593,34 @@ int cm_level(cm_ctx* ctx, const float* S, float* R, const float* f, int H, int W
     return CM_OK;
 }
 
+static int solve_impl(cm_ctx* ctx, const float* f, int H, int W, float alpha, int kind,
+                      int levels, int cycles, double tol, const float* u0, float* u_out,
+                      const cm_options* opts, cm_stats* stats, void* stream);
+
 int cm_solve(cm_ctx* ctx, const float* f, int H, int W, float alpha, int kind, int levels,
              int cycles, double tol, const float* u0, float* u_out, const cm_options* opts,
              cm_stats* stats, void* stream) {
+    NvtxRange range("cm_solve %dx%d", H, W);
+    if (!log_level())
+        return solve_impl(ctx, f, H, W, alpha, kind, levels, cycles, tol, u0, u_out, opts, stats,
+                          stream);
+    cm_stats local;
+    cm_stats* st = stats ? stats : &local;
+    const auto t0 = std::chrono::steady_clock::now();
+    const int rc = solve_impl(ctx, f, H, W, alpha, kind, levels, cycles, tol, u0, u_out, opts,
+                              st, stream);
+    const double ms =
+        std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    if (rc == CM_OK || rc == CM_NOT_CONVERGED)
+        log_solve("cm_solve", -1, H, W, kind, alpha, st->levels, *st, ms);
+    else
+        fprintf(stderr, "[cm] cm_solve %dx%d: status %d (%s)\n", H, W, rc, cm_last_error(ctx));
+    return rc;
+}
+
+static int solve_impl(cm_ctx* ctx, const float* f, int H, int W, float alpha, int kind,
+                      int levels, int cycles, double tol, const float* u0, float* u_out,
+                      const cm_options* opts, cm_stats* stats, void* stream) {
     if (!ctx) return CM_ERR_INVALID;
     cm_options o;
     cm_options_default(&o);
@@ -660,6 +730,7 @@ int cm_solve(cm_ctx* ctx, const float* f, int H, int W, float alpha, int kind, i
     }
     int cur = 0, l = 0, conv = 0, viol = 0;
     while (l < cycles) {
+        NvtxRange cyc("cycle %d", l + 1);
         float* X = bufs[cur];
         float* Y = bufs[cur ^ 1];
         CM_CUDA(enqueue_cycle(ctx, X, Y, f, H, W, alpha, kind, L, o, st));
@@ -697,6 +768,7 @@ int cm_solve(cm_ctx* ctx, const float* f, int H, int W, float alpha, int kind, i
 
 int cm_warmstart(cm_ctx* ctx, cm_net* net, const float* f, int N, int H, int W, float* u0_out,
                  int check_energy, float alpha, int kind, int* used_host, void* stream) {
+    NvtxRange range("cm_warmstart %d x %dx%d", N, H, W);
     if (!ctx) return CM_ERR_INVALID;
     if (!net || !f || !u0_out || u0_out == f || N < 1 || !dims_ok(H, W) ||
         (check_energy && (!finite_positive(alpha) || !valid_kind(kind))))
@@ -750,10 +822,41 @@ struct ImgLayout {
 
 }  // namespace
 
+static int solve_batched_impl(cm_ctx* ctx, int n, const float* const* f, const int* H,
+                              const int* W, const float* alpha, const int* kind, int levels,
+                              int cycles, double tol, const float* const* u0,
+                              float* const* u_out, const cm_options* opts, cm_stats* stats,
+                              void* stream);
+
 int cm_solve_batched(cm_ctx* ctx, int n, const float* const* f, const int* H, const int* W,
                      const float* alpha, const int* kind, int levels, int cycles, double tol,
                      const float* const* u0, float* const* u_out, const cm_options* opts,
                      cm_stats* stats, void* stream) {
+    NvtxRange range("cm_solve_batched %d images", n);
+    if (!log_level() || n < 1 || !H || !W || !alpha || !kind)
+        return solve_batched_impl(ctx, n, f, H, W, alpha, kind, levels, cycles, tol, u0, u_out,
+                                  opts, stats, stream);
+    std::vector<cm_stats> local(stats ? 0 : (size_t)n);
+    cm_stats* st = stats ? stats : local.data();
+    const auto t0 = std::chrono::steady_clock::now();
+    const int rc = solve_batched_impl(ctx, n, f, H, W, alpha, kind, levels, cycles, tol, u0,
+                                      u_out, opts, st, stream);
+    const double ms =
+        std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    if (rc == CM_OK || rc == CM_NOT_CONVERGED)
+        for (int i = 0; i < n; ++i)
+            log_solve("cm_solve_batched", i, H[i], W[i], kind[i], alpha[i], st[i].levels, st[i],
+                      ms);
+    else
+        fprintf(stderr, "[cm] cm_solve_batched: status %d (%s)\n", rc, cm_last_error(ctx));
+    return rc;
+}
+
+static int solve_batched_impl(cm_ctx* ctx, int n, const float* const* f, const int* H,
+                              const int* W, const float* alpha, const int* kind, int levels,
+                              int cycles, double tol, const float* const* u0,
+                              float* const* u_out, const cm_options* opts, cm_stats* stats,
+                              void* stream) {
     if (!ctx) return CM_ERR_INVALID;
     cm_options o;
     cm_options_default(&o);

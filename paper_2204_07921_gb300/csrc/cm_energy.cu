@@ -2,9 +2,9 @@
 //
 //  energy_kernel     F(u) = sum |kappa| + alpha/2 (u - f)^2 (Eq. MCM / Eq. GCM;
 //                    kappa of any of the four kinds of kappa_signed):
-//                    smem halo tile, FP32 per pixel and per warp, FP64 CTA
-//                    partials and a fixed-order FP64 finish in the last CTA
-//                    (deterministic).
+//                    smem halo tile, FP32 per pixel, warp and CTA, a
+//                    fixed-order FP64 sum of the CTA partials in the last
+//                    CTA (deterministic).
 //  curvature_kernel  signed kappa per pixel (diagnostics and tests).
 #include <cuda_runtime.h>
 #include <math.h>
@@ -21,12 +21,13 @@ namespace cm {
 constexpr int E_TW = 32;   // tile columns
 constexpr int E_TH = 32;   // tile rows (each thread 4 rows)
 
-// Reduction: FP32 per pixel, per thread (4 pixels) and per warp (a fixed
-// shuffle tree over 128 non-negative terms: relative error <= 8 eps32 ~ 5e-7),
-// then FP64: the CTA's 8 warp sums by one thread, the grid's CTA sums in a
-// fixed order by the last CTA.  FP64 stays out of the warp-wide code: the
-// GB300's FP64 pipe runs at a small fraction of its FP32 rate, and FP64
-// conversions and shuffles in every warp kept it about half busy.
+// Reduction: FP32 per pixel, per thread (4 pixels), per warp (a fixed
+// shuffle tree) and per CTA (the 8 warp sums in order): a sum of 1024
+// non-negative terms with relative error <= 11 eps32 ~ 7e-7; then FP64 for
+// the grid: the CTA sums, in a fixed order, by the last CTA.  FP64 stays out
+// of the per-CTA code: the GB300's FP64 pipe runs at a small fraction of its
+// FP32 rate, and FP64 conversions and shuffles in every warp kept it about
+// half busy (one FP64 sum per CTA still took a fifth of it).
 template <int KIND>
 __global__ void __launch_bounds__(256) energy_kernel(const float* __restrict__ u,
                                                      const float* __restrict__ f, int H, int W,
@@ -96,9 +97,10 @@ __global__ void __launch_bounds__(256) energy_kernel(const float* __restrict__ u
     const int nblk = gridDim.x * gridDim.y;
     const int bid = blockIdx.y * gridDim.x + blockIdx.x;
     if (threadIdx.x == 0) {
-        double s = 0.0;
-        for (int i = 0; i < 8; ++i) s += (double)wsum[i];
-        partials[bid] = s;
+        float s = 0.0f;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) s += wsum[i];
+        partials[bid] = (double)s;
         __threadfence();
         unsigned int t = atomicAdd(ticket, 1u);
         is_last = (t == (unsigned)nblk - 1);
