@@ -69,11 +69,16 @@ int log_level() {
 
 void log_solve(const char* what, int i, int H, int W, int kind, float alpha, int L,
                const cm_stats& st, double ms) {
+    char label[64];
+    if (i >= 0)
+        snprintf(label, sizeof label, "%s image %d", what, i);
+    else
+        snprintf(label, sizeof label, "%s", what);
     fprintf(stderr,
-            "[cm] %s%s%d %dx%d kind=%d alpha=%g levels=%d cycles=%d E %.9g -> %.9g "
+            "[cm] %s %dx%d kind=%d alpha=%g levels=%d cycles=%d E %.9g -> %.9g "
             "converged=%d rises=%d %.3f ms\n",
-            what, i >= 0 ? " image " : "", i >= 0 ? i : 0, H, W, kind, alpha, L, st.cycles_run,
-            st.energy_initial, st.energy_final, st.converged, st.monotone_violations, ms);
+            label, H, W, kind, alpha, L, st.cycles_run, st.energy_initial, st.energy_final,
+            st.converged, st.monotone_violations, ms);
     if (log_level() >= 2)
         for (int c = 0; c < st.trace_len; ++c)
             fprintf(stderr, "[cm]   cycle %d E %.12g\n", c, st.energy_trace[c]);
