@@ -38,7 +38,7 @@ METRIC = ("s to rel-energy tol 1e-4 at 1024^2 (learned warm start + FP32 sweep w
 WARMSTART_PARAMS = os.path.join(ROOT, "paper_2204_07921_gb300", "data", "warmstart_mean_a20.npz")
 WARMSTART_PARAMS_GAUSS = os.path.join(ROOT, "paper_2204_07921_gb300", "data", "warmstart_gauss_a15.npz")
 L2_FLUSH_BYTES = 512 << 20   # > 129 MB L2
-B1_TRAFFIC_BYTES = 7.42e6     # ncu DRAM bytes of one finest-level phase at 1024^2 (mean of 8)
+B1_TRAFFIC_BYTES = 7.41e6     # ncu DRAM bytes of one finest-level phase at 1024^2 (mean of 4)
 
 
 def parse():
