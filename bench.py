@@ -39,6 +39,7 @@ WARMSTART_PARAMS = os.path.join(ROOT, "paper_2204_07921_gb300", "data", "warmsta
 WARMSTART_PARAMS_GAUSS = os.path.join(ROOT, "paper_2204_07921_gb300", "data", "warmstart_gauss_a15.npz")
 L2_FLUSH_BYTES = 512 << 20   # > 129 MB L2
 B1_TRAFFIC_BYTES = 7.41e6     # ncu DRAM bytes of one finest-level phase at 1024^2 (mean of 4)
+F_KAPPA = 130.0               # FP32 operations per ring-pixel curvature evaluation
 
 
 def parse():
@@ -851,25 +852,33 @@ def main():
     n_active = N // nc
     evals_per_block = 3 + (opts.grid_points - 1) + opts.golden_evals   # 0, paper, c_fid, grid, golden
     curv_evals = n_active * evals_per_block * 9
-    achieved = curv_evals / (b1_ms / 1e3) / 1e9
-    # peak: the measured rsqrtf rate of this GPU (cm_probe_alu) / 8 rsqrt per
-    # generic stencil evaluation (4 directions x 2 planes)
+    evals_per_s = curv_evals / (b1_ms / 1e3)
+    # Algorithmic FP32 work: F_KAPPA operations per ring-pixel curvature
+    # evaluation (the per-unit figure of the hot-path scope: 8 plane distances,
+    # 4 direction curvatures, their extremes, |kappa|) x the evaluations of the
+    # launch; the peak is this GPU's measured FP32 rate (cm_probe_alu: FFMA/s
+    # x 2 operations).  The kernel is issue-bound on the FP32 and ALU pipes
+    # (ncu: 64% issue-active), not on the MUFU pipe.
     alu = cm.cm_probe_alu(local)
+    fp32_peak = 2.0 * alu["fma_per_s"] / 1e12
+    achieved = evals_per_s * F_KAPPA / 1e12
     mufu_peak = alu["rsqrt_per_s"] / 8 / 1e9
     roofline = {"bound": "alu", "kernel": "phase_b1_kernel (b=1)", "achieved": achieved,
-                "peak": mufu_peak, "unit": "Geval/s", "frac": achieved / mufu_peak,
-                "peak_source": "measured (cm_probe_alu)",
+                "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak,
+                "peak_source": "measured (cm_probe_alu: FFMA rate x 2)",
+                "flop_per_eval": F_KAPPA, "evals_per_launch": curv_evals,
+                "launch_ms": b1_ms,
+                "issue_active": {"value": 0.64, "source": "profiles/phase_b1_kernel_1024.md"},
+                "rsqrt_view": {"achieved_geval_s": evals_per_s / 1e9, "peak_geval_s": mufu_peak,
+                               "frac": evals_per_s / 1e9 / mufu_peak,
+                               "note": "peak = measured rsqrtf rate / 8 rsqrt per generic "
+                                       "evaluation"},
                 "measured_rsqrt_per_s": alu["rsqrt_per_s"],
                 "measured_fma_per_s": alu["fma_per_s"],
-                "nominal_peak": 152 * 16 * 2.07e9 / 8 / 1e9,
                 # dram__bytes_read.sum + dram__bytes_write.sum of one launch of this
-                # kernel at 1024^2: the mean of eight launches of one ncu capture
+                # kernel at 1024^2: the mean of four launches of one ncu capture
                 "traffic": B1_TRAFFIC_BYTES if args.side == 1024 else None,
-                "traffic_unit": "B per launch",
-                "note": "curvature-stencil evaluations/s; peak = measured rsqrtf rate / 8 "
-                        "rsqrt per generic evaluation (nominal: 152 SM x 16 MUFU/clk x "
-                        "2.07 GHz / 8); the kernel is issue-bound on the FP32/ALU pipes "
-                        "(ncu: issue 57-63% active, MUFU 18-21%)"}
+                "traffic_unit": "B per launch"}
 
     # HBM side of the roofline: algorithmic bytes per launch / device time.
     # The sweep's algorithmic bytes are 12 B per pixel and level (read u and

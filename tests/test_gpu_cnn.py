@@ -167,6 +167,62 @@ def test_gradient_parity_multi_strip():
     _check_gradients(gg, go, "x".join(map(str, shape)))
 
 
+def test_inference_16x1024_sampled():
+    """The warm-start workload's inference, as the bench launches it: the
+    shipped network on a batch of 16 test images of 1024^2.  The network's
+    receptive field has radius 6 (six 3 x 3 layers), so the oracle's output at
+    a pixel is exact from the crop of radius 6 around it, clipped at the image
+    border (where every layer's own zero padding then applies as in the whole
+    image); 640 sampled pixels, corners and edges included, element by
+    element."""
+    import os
+    path = os.path.join(os.path.dirname(ws.__file__), "data", "warmstart_mean_a20.npz")
+    p = np.load(path)["params"].astype(np.float64)
+    net = ws.Net.load(path)
+    F = np.stack([synth.warmstart_image("test", i, 1024).f for i in range(16)])
+    out_g = (net.forward(dev(F)) - dev(F)).cpu().numpy().astype(np.float64)
+    rng = np.random.default_rng(16)
+    R = 6
+    picks = []
+    for n in range(16):
+        rc = [(0, 0), (0, 1023), (1023, 0), (1023, 1023), (0, 500), (511, 1023)]
+        rc += [tuple(x) for x in rng.integers(0, 1024, size=(34, 2))]
+        picks += [(n, r, c) for r, c in rc]
+    ref = np.zeros(len(picks))
+    for i, (n, r, c) in enumerate(picks):
+        r0, c0 = max(0, r - R), max(0, c - R)
+        crop = F[n, r0:r + R + 1, c0:c + R + 1].astype(np.float64)
+        u0, _ = ocnn.forward(p, crop[None])
+        ref[i] = u0[0, r - r0, c - c0] - crop[r - r0, c - c0]
+    got = np.array([out_g[n, r, c] for n, r, c in picks])
+    rms = np.sqrt(np.mean(ref ** 2))
+    ratio = np.abs(got - ref) / (np.abs(ref) + rms)
+    print(f"\ninference 16x1024^2: {len(picks)} pixels, max |d|/(|ref|+rms) {ratio.max():.3e}")
+    assert rms > 1e-3
+    assert np.all(ratio <= FWD_TOL)
+
+
+def test_gradient_parity_training_batch():
+    """Every gradient element at the training workload's batch shape (16
+    images of 256^2, the shape the training loop steps on)."""
+    shape = (16, 256, 256)
+    rng = np.random.default_rng(41)
+    p = ws.init_params(23, zero_last=False)
+    p[-289:] *= 3.0
+    f = rng.random(shape).astype(np.float32)
+    us = (f + 0.05 * rng.normal(size=shape)).astype(np.float32)
+    net = ws.Net(p)
+    Lg, gg = net.gradients(dev(f), dev(us))
+    Lo, go = 0.0, np.zeros(ocnn.N_PARAMS)
+    for n in range(shape[0]):
+        L1, g1 = ocnn.gradients(p.astype(np.float64), f[n:n + 1].astype(np.float64),
+                                us[n:n + 1].astype(np.float64))
+        Lo += L1 / shape[0]
+        go += g1 / shape[0]
+    assert Lg == pytest.approx(Lo, rel=LOSS_TOL)
+    _check_gradients(gg, go, "16x256x256")
+
+
 def test_train_step_follows_adam_and_lowers_loss():
     """The first Adam step moves every parameter with a clear gradient by
     ~lr * sign(g); a few steps on one batch lower the loss."""

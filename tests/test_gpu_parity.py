@@ -541,6 +541,82 @@ def test_full_size_1024_phase_sampled():
     assert ties <= max(2, 0.01 * tot)
 
 
+def test_full_size_2048_bench_schedule():
+    """The 2048^2 mean-curvature workload in the bench's launch configuration
+    (the tuned schedule: four colours on b = 1 .. 32, two on the coarse levels,
+    (G, K) = (5, 6)), from the state after one GPU cycle: sampled blocks of
+    every colour of the fine levels (cm_phase) and of three coarse levels
+    through the coarse path (cm_level: tile sums, rounds search, deferred
+    apply), each colour from the state the earlier colours left."""
+    img = synth.large(2048)
+    f = img.f
+    H, W = f.shape
+    opts = cm.default_options(ncolors=4, coarse_ncolors=2)
+    ug, _ = cm.cm_solve(to_dev(f), 20.0, cm.MEAN, cycles=1, tol=0.0, options=opts)
+    u = host(ug)
+    rng = np.random.default_rng(21)
+    tot = ties = 0
+    fails = []
+    for b in (1, 2, 4, 8, 16, 32):
+        for k in range(4):
+            blocks = [(bi, bj) for bi, bj, *_ in blocks_of_colour(H, W, b, 4, k)]
+            idx = rng.choice(len(blocks), size=min(40, len(blocks)), replace=False)
+            n, m, t, fl = check_phase(u, f, 20.0, cm.MEAN, b, 4, k,
+                                      sample={blocks[i] for i in idx})
+            tot += n
+            ties += t
+            fails += fl
+    fd = to_dev(f)
+    for b in (64, 256, 1024):
+        nbi, nbj = (H + b - 1) // b, (W + b - 1) // b
+        cbuf = torch.full((nbi * nbj,), float("nan"), device=DEV)
+        R = torch.empty_like(ug)
+        cm.cm_level(ug, R, fd, 20.0, cm.MEAN, b, options=opts, c_out=cbuf)
+        torch.cuda.synchronize()
+        cg, Rg = host(cbuf), host(R)
+        for k in range(2):
+            state = u.copy()
+            if k == 1:
+                for bi, bj, r0, c0, bh, bw in blocks_of_colour(H, W, b, 2, 0):
+                    state[r0:r0 + bh, c0:c0 + bw] += np.float32(cg[bi * nbj + bj])
+            blocks = [(bi, bj) for bi, bj, *_ in blocks_of_colour(H, W, b, 2, k)]
+            pick = rng.choice(len(blocks), size=min(12, len(blocks)), replace=False)
+            sample = {blocks[i] for i in pick}
+            for bi, bj in sample:
+                blk = (slice(bi * b, min((bi + 1) * b, H)), slice(bj * b, min((bj + 1) * b, W)))
+                np.testing.assert_array_equal(Rg[blk], u[blk] + np.float32(cg[bi * nbj + bj]))
+            cgd = {(bi, bj): cg[bi * nbj + bj] for bi, bj in sample}
+            n, m, t, fl = compare_phase(state.astype(np.float64), f.astype(np.float64), cgd,
+                                        20.0, cm.MEAN, b, 2, k, {}, sample=sample)
+            tot += n
+            ties += t
+            fails += fl
+    print(f"\n2048 bench schedule: blocks={tot} ties={ties}")
+    assert not fails, fails[:5]
+    assert ties <= max(2, 0.01 * tot)
+
+
+def test_batched_64_uneven_equals_single():
+    """The 64-image workload (sides from 128 .. 1024, half mean, half
+    Gaussian curvature, alpha 10 or 20) in one batched launch, with the
+    schedule the bench's autotuner picks for it (two coarse colours, the
+    generic 8-lane kernel at b = 2): every image bit-identical to its own
+    cm_solve, cycles and trace included."""
+    items = synth.uneven_batch(64)
+    fs = [to_dev(it.image.f) for it in items]
+    al = [it.alpha for it in items]
+    kd = [it.kind for it in items]
+    opts = cm.default_options(ncolors=4, coarse_ncolors=2, coarse_spec=1, coarse_dmax=4,
+                              shapes=1)
+    ub, sb = cm.cm_solve_batched(fs, al, kd, cycles=400, tol=1e-4, options=opts)
+    torch.cuda.synchronize()
+    for i in range(len(fs)):
+        us, ss = cm.cm_solve(fs[i], al[i], kd[i], cycles=400, tol=1e-4, options=opts)
+        torch.cuda.synchronize()
+        assert torch.equal(ub[i], us), i
+        assert sb[i].trace() == ss.trace() and sb[i].cycles_run == ss.cycles_run, i
+
+
 def test_invalid_arguments_rejected():
     f = to_dev(np.zeros((8, 8), np.float32))
     with pytest.raises(cm.CMError) as e:

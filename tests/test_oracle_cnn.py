@@ -63,3 +63,28 @@ def test_adam_first_step_moves_by_lr_times_sign():
 
 def test_parameter_count():
     assert cnn.N_PARAMS == 9 * 32 + 32 + 4 * (9 * 32 * 32 + 32) + 9 * 32 + 1
+
+
+def test_receptive_field_radius_six():
+    """Six 3 x 3 layers with zero padding per layer: the output at a pixel
+    depends only on the inputs within Chebyshev radius 6, and the oracle on the
+    radius-6 crop (clipped at the image border) gives the same value; one
+    input changed at radius 7 leaves it unchanged, at radius 6 changes it."""
+    import numpy as np
+    from oracle import cnn as ocnn
+    rng = np.random.default_rng(4)
+    p = ocnn.init_params(3, zero_last=False)
+    p[-289:] *= 3.0
+    F = rng.random((1, 40, 37))
+    u0, _ = ocnn.forward(p, F)
+    for r, c in [(0, 0), (20, 18), (39, 36), (5, 30), (0, 20), (39, 0)]:
+        r0, c0 = max(0, r - 6), max(0, c - 6)
+        crop = F[0, r0:r + 7, c0:c + 7]
+        v, _ = ocnn.forward(p, crop[None])
+        assert abs(v[0, r - r0, c - c0] - u0[0, r, c]) <= 1e-12
+    G = F.copy()
+    G[0, 20 + 7, 18] += 1.0
+    assert ocnn.forward(p, G)[0][0, 20, 18] == u0[0, 20, 18]
+    G = F.copy()
+    G[0, 20 + 6, 18 + 6] += 1.0
+    assert ocnn.forward(p, G)[0][0, 20, 18] != u0[0, 20, 18]
