@@ -44,6 +44,35 @@ def blocks_of_colour(H, W, b, ncolors, k):
                 yield bi, bj, bi * b, bj * b, min(b, H - bi * b), min(b, W - bj * b)
 
 
+def block_rect(H, W, b, bi, bj):
+    r0, c0 = bi * b, bj * b
+    return r0, c0, min(b, H - r0), min(b, W - c0)
+
+
+def sample_blocks(H, W, b, ncolors, k, n, rng):
+    """Up to n distinct blocks (bi, bj) of colour k drawn at random; large
+    levels are drawn from their colour lattice without walking every block."""
+    nbi, nbj = (H + b - 1) // b, (W + b - 1) // b
+    if nbi * nbj <= 64 * n:
+        blocks = [(bi, bj) for bi, bj, *_ in blocks_of_colour(H, W, b, ncolors, k)]
+        idx = rng.choice(len(blocks), size=min(n, len(blocks)), replace=False)
+        return {blocks[i] for i in idx}
+    out = set()
+    p = 1 if ncolors == 2 else int(round(ncolors ** 0.5))
+    for _ in range(100 * n):
+        if len(out) >= n:
+            break
+        if ncolors == 2:
+            bi, bj = int(rng.integers(nbi)), int(rng.integers(nbj))
+            if (bi + bj) % 2 != k:
+                continue
+        else:
+            ni, nj = (nbi - k // p + p - 1) // p, (nbj - k % p + p - 1) // p
+            bi, bj = k // p + p * int(rng.integers(ni)), k % p + p * int(rng.integers(nj))
+        out.add((bi, bj))
+    return out
+
+
 def energy_scale(u, f, r0, c0, bh, bw, c, alpha, kind, c_fid):
     """Non-negative parts of E_A at c: ring curvature + alpha s/2 (c - c_fid)^2."""
     s = bh * bw
@@ -61,9 +90,12 @@ def compare_phase(u, f, c_gpu_blocks, alpha, kind, b, ncolors, k, c_orc_blocks, 
     H, W = u.shape
     n = match = tie = 0
     fails = []
-    for bi, bj, r0, c0, bh, bw in blocks_of_colour(H, W, b, ncolors, k):
-        if sample is not None and (bi, bj) not in sample:
-            continue
+    if sample is None:
+        blocks = blocks_of_colour(H, W, b, ncolors, k)
+    else:
+        blocks = [(bi, bj, *block_rect(H, W, b, bi, bj)) for bi, bj in sorted(sample)]
+        assert all(oracle.block_colour(bi, bj, ncolors) == k for bi, bj in sample)
+    for bi, bj, r0, c0, bh, bw in blocks:
         n += 1
         cg = float(c_gpu_blocks[(bi, bj)])
         if (bi, bj) in c_orc_blocks:

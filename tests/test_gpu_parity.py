@@ -14,7 +14,8 @@ if not torch.cuda.is_available():
 import oracle  # noqa: E402
 import paper_2204_07921_gb300 as cm  # noqa: E402
 import synth  # noqa: E402
-from gpu_helpers import G_DEF, K_DEF, blocks_of_colour, compare_phase  # noqa: E402
+from gpu_helpers import (G_DEF, K_DEF, block_rect, blocks_of_colour, compare_phase,  # noqa: E402
+                         sample_blocks)
 
 pytestmark = pytest.mark.gpu
 DEV = torch.device("cuda:0")
@@ -131,9 +132,10 @@ def check_phase(u, f, alpha, kind, b, ncolors, k, sample=None, one_step=False, s
     if sample is None:
         _, co = oracle.phase(u.astype(np.float64), f.astype(np.float64), alpha, kind, b,
                              ncolors, k, one_step=one_step)
-    for bi, bj, r0, c0, bh, bw in blocks_of_colour(H, W, b, ncolors, k):
-        if sample is not None and (bi, bj) not in sample:
-            continue
+        blocks = blocks_of_colour(H, W, b, ncolors, k)
+    else:
+        blocks = [(bi, bj, *block_rect(H, W, b, bi, bj)) for bi, bj in sorted(sample)]
+    for bi, bj, r0, c0, bh, bw in blocks:
         c = cg[bi * nbj + bj]
         assert np.isfinite(c)
         cgd[(bi, bj)] = c
@@ -530,10 +532,8 @@ def test_full_size_1024_phase_sampled():
     fails, tot, ties = [], 0, 0
     for b in (1, 2, 64, 512):
         for k in range(2):
-            blocks = [(bi, bj) for bi, bj, *_ in blocks_of_colour(H, W, b, 2, k)]
-            idx = rng.choice(len(blocks), size=min(60, len(blocks)), replace=False)
             n, m, t, fl = check_phase(f, f, 20.0, cm.MEAN, b, 2, k,
-                                      sample={blocks[i] for i in idx})
+                                      sample=sample_blocks(H, W, b, 2, k, 60, rng))
             tot += n
             ties += t
             fails += fl
@@ -559,10 +559,8 @@ def test_full_size_2048_bench_schedule():
     fails = []
     for b in (1, 2, 4, 8, 16, 32):
         for k in range(4):
-            blocks = [(bi, bj) for bi, bj, *_ in blocks_of_colour(H, W, b, 4, k)]
-            idx = rng.choice(len(blocks), size=min(40, len(blocks)), replace=False)
             n, m, t, fl = check_phase(u, f, 20.0, cm.MEAN, b, 4, k,
-                                      sample={blocks[i] for i in idx})
+                                      sample=sample_blocks(H, W, b, 4, k, 40, rng))
             tot += n
             ties += t
             fails += fl
@@ -579,9 +577,7 @@ def test_full_size_2048_bench_schedule():
             if k == 1:
                 for bi, bj, r0, c0, bh, bw in blocks_of_colour(H, W, b, 2, 0):
                     state[r0:r0 + bh, c0:c0 + bw] += np.float32(cg[bi * nbj + bj])
-            blocks = [(bi, bj) for bi, bj, *_ in blocks_of_colour(H, W, b, 2, k)]
-            pick = rng.choice(len(blocks), size=min(12, len(blocks)), replace=False)
-            sample = {blocks[i] for i in pick}
+            sample = sample_blocks(H, W, b, 2, k, 12, rng)
             for bi, bj in sample:
                 blk = (slice(bi * b, min((bi + 1) * b, H)), slice(bj * b, min((bj + 1) * b, W)))
                 np.testing.assert_array_equal(Rg[blk], u[blk] + np.float32(cg[bi * nbj + bj]))
