@@ -155,9 +155,9 @@ def dist_setup(args):
 
 
 # The schedule the autotuner picks for the 1024^2 workload on the GB300
-# (search budget (5, 6), four colours, two on the coarse levels b >= 64): the
+# (search budget (5, 6), four colours, one on the coarse levels b >= 64): the
 # CPU legs run the oracle with it, since they have no GPU to tune on.
-REF_SCHEDULE = {"G": 5, "K": 6, "ncolors": 4, "coarse_ncolors": 2}
+REF_SCHEDULE = {"G": 5, "K": 6, "ncolors": 4, "coarse_ncolors": 1}
 
 
 def oracle_cycle_seconds(u0, f64, n_cycles: int, sched=None):

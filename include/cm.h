@@ -100,10 +100,11 @@ typedef struct {
     int coarse_dmax;     /* coarse levels: 0 the level's default, 1 .. 4 golden steps per
                             reduction (2^d - 1 points of every outcome path); both change only
                             how many candidates share a reduction, never which are taken */
-    int coarse_ncolors;  /* levels of block side >= 64: 0 the ncolors rule, or 2, 4, 9, 16
+    int coarse_ncolors;  /* levels of block side >= 64: 0 the ncolors rule, or 1, 2, 4, 9, 16
                             colours there (fewer colours: fewer sequential phases on the
-                            latency-bound coarse levels, whose same-colour blocks then share
-                            only corner pixels of their rings) */
+                            latency-bound coarse levels; with 2 same-colour blocks share only
+                            corner pixels of their rings, with 1 every block of the level
+                            solves from the same state in one phase: a block-Jacobi step) */
     int block_sides;     /* 0: block side 2^(j-1) on level j (default); 1: the paper's patches
                             of (2^j - 1) x (2^j - 1) pixels (Sec. 2.2: 1, 3, 7, 15, ...), with
                             levels = 0 meaning the largest side <= min(H, W) / 2.  Levels of

@@ -538,9 +538,11 @@ double orc_block_min(const double *u, const double *f, int H, int W, int r0, int
 /* uses sides 2^j - 1 and extends the domain; the extended pixels are not    */
 /* part of F).  Colour of block (bi, bj): ncolors = 2 -> (bi + bj) mod 2     */
 /* (checkerboard); ncolors = p^2 (p = 2, 3, 4) -> p (bi mod p) + (bj mod p),   */
-/* the p x p decomposition (p = 2: the paper's four colours).                 */
+/* the p x p decomposition (p = 2: the paper's four colours); ncolors = 1 ->  */
+/* 0 (a schedule option for the coarse levels: every block in one phase).    */
 
 int orc_block_colour(int bi, int bj, int ncolors) {
+    if (ncolors == 1) return 0;
     if (ncolors == 2) return (bi + bj) & 1;
     int p = ncolors == 16 ? 4 : (ncolors == 9 ? 3 : 2);
     return p * (bi % p) + (bj % p);

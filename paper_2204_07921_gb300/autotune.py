@@ -11,9 +11,10 @@ seeded image that is not one of the measured workloads):
 2. the colour schedule -- four colours, the checkerboard, or the decoupled
    colouring (more colours on the finest levels, no shared stencils);
 3. the colour count of the coarse levels (block side >= 64): the fine
-   levels' rule or two colours -- fewer sequential phases on the
-   latency-bound coarse levels, whose same-colour blocks then share only
-   corner pixels of their rings;
+   levels' rule, two colours (same-colour blocks then share only corner
+   pixels of their rings) or one (every block from the same state, a
+   block-Jacobi step) -- fewer sequential phases on the latency-bound coarse
+   levels;
 4. the coarse levels' kernel shape -- how many candidates share one cluster
    reduction (first-pair speculation, golden steps per round), which changes
    the number of barriers and not the decisions;
@@ -35,7 +36,7 @@ import os
 
 CANDIDATES = ((9, 16), (7, 10), (5, 8), (5, 6), (5, 4), (3, 4))
 COLOURS = (4, 2, 0)
-COARSE_COLOURS = (0, 2)
+COARSE_COLOURS = (0, 2, 1)
 COARSE = ((-1, 0), (0, 4), (1, 4), (0, 2), (0, 1))   # (coarse_spec, coarse_dmax)
 ENERGY_SLACK = 2e-3
 SHAPE_MARGIN = 0.01

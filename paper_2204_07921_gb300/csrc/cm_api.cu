@@ -240,9 +240,9 @@ int check_opts(cm_ctx* ctx, const cm_options& o) {
     if (o.block_sides != 0 && o.block_sides != 1)
         return fail(ctx, CM_ERR_INVALID, "block_sides must be 0 or 1");
     if (o.shapes < 0 || o.shapes > 31) return fail(ctx, CM_ERR_INVALID, "shapes must be 0 .. 31");
-    if (o.coarse_ncolors != 0 && o.coarse_ncolors != 2 && o.coarse_ncolors != 4 &&
-        o.coarse_ncolors != 9 && o.coarse_ncolors != 16)
-        return fail(ctx, CM_ERR_INVALID, "coarse_ncolors must be 0, 2, 4, 9 or 16");
+    if (o.coarse_ncolors != 0 && o.coarse_ncolors != 1 && o.coarse_ncolors != 2 &&
+        o.coarse_ncolors != 4 && o.coarse_ncolors != 9 && o.coarse_ncolors != 16)
+        return fail(ctx, CM_ERR_INVALID, "coarse_ncolors must be 0, 1, 2, 4, 9 or 16");
     return CM_OK;
 }
 

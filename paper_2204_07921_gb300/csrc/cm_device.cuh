@@ -232,13 +232,13 @@ __device__ __forceinline__ float paper_chalf(const float w[9]) {
 __device__ __forceinline__ int clampi(int v, int lo, int hi) { return min(max(v, lo), hi); }
 
 // Side p of a p x p colouring with `ncolors` = p^2 colours (ncolors = 2 is
-// the checkerboard).
+// the checkerboard; ncolors = 1, one colour: every block in one phase).
 __host__ __device__ __forceinline__ int colour_side(int ncolors) {
-    return ncolors == 16 ? 4 : (ncolors == 9 ? 3 : 2);
+    return ncolors == 16 ? 4 : (ncolors == 9 ? 3 : (ncolors == 1 ? 1 : 2));
 }
 
 // Colour of block (bi, bj): ncolors == 2: checkerboard; ncolors == p^2:
-// p (bi mod p) + (bj mod p) (p = 2: the paper's four colours).
+// p (bi mod p) + (bj mod p) (p = 2: the paper's four colours; p = 1: 0).
 __host__ __device__ __forceinline__ int block_colour(int bi, int bj, int ncolors) {
     if (ncolors == 2) return (bi + bj) & 1;
     if (ncolors == 4) return ((bi & 1) << 1) | (bj & 1);

@@ -29,7 +29,7 @@ inline cudaError_t launch_k(void (*kern)(KArgs...), dim3 grid, dim3 block, cudaS
 // for every colour; active_block maps a slot to a block or rejects it).
 inline int active_slots(int nbi, int nbj, int ncol) {
     if (ncol == 2) return nbi * ((nbj + 1) / 2);
-    const int p = ncol == 16 ? 4 : (ncol == 9 ? 3 : 2);
+    const int p = ncol == 16 ? 4 : (ncol == 9 ? 3 : (ncol == 1 ? 1 : 2));
     return ((nbi + p - 1) / p) * ((nbj + p - 1) / p);
 }
 

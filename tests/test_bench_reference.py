@@ -62,11 +62,14 @@ def test_launch_count_follows_the_schedule():
     import oracle
     import paper_2204_07921_gb300 as cm
     for nc in (0, 2, 4, 9, 16):
-        for cn in (0, 2, 4):
+        for cn in (0, 1, 2, 4):
             o = cm.default_options(ncolors=nc, coarse_ncolors=cn)
             for j in range(12):
                 b = 1 << j
                 assert bench.level_colours(o, b) == oracle.level_colours(nc, b, cn), (nc, cn, b)
     assert bench.kernels_per_cycle(cm.default_options(ncolors=4, coarse_ncolors=2), 10) == 39
+    # one coarse colour: 24 fine phases, 4 coarse phases and 4 applies, the tile
+    # sums, the energy, the stopping test
+    assert bench.kernels_per_cycle(cm.default_options(ncolors=4, coarse_ncolors=1), 10) == 35
     assert bench.kernels_per_cycle(cm.default_options(ncolors=4), 10) == 47
     assert bench.kernels_per_cycle(cm.default_options(ncolors=4), 6) == 2 + 6 * 4

@@ -594,10 +594,9 @@ def test_full_size_2048_bench_schedule():
 
 def test_batched_64_uneven_equals_single():
     """The 64-image workload (sides from 128 .. 1024, half mean, half
-    Gaussian curvature, alpha 10 or 20) in one batched launch, with the
-    schedule the bench's autotuner picks for it (two coarse colours, the
-    generic 8-lane kernel at b = 2): every image bit-identical to its own
-    cm_solve, cycles and trace included."""
+    Gaussian curvature, alpha 10 or 20) in one batched launch, with a tuned
+    schedule (two coarse colours, the generic 8-lane kernel at b = 2): every
+    image bit-identical to its own cm_solve, cycles and trace included."""
     items = synth.uneven_batch(64)
     fs = [to_dev(it.image.f) for it in items]
     al = [it.alpha for it in items]
@@ -966,18 +965,20 @@ def test_paper_sides_device_loop_batched_and_variants(vcycle, ncolors):
 # ---------------------------------------------------------------------------
 # Two colours on the coarse levels (coarse_ncolors = 2).
 
+@pytest.mark.parametrize("ncoarse", [2, 1])
 @pytest.mark.parametrize("shape,kind,levels", [((1024, 1024), cm.MEAN, (64, 256, 512)),
                                                ((520, 600), cm.GAUSS, (64, 128, 256))])
-def test_level_parity_coarse_two_colours(shape, kind, levels):
-    """The coarse path with two colours: R = S + c per block, and each
-    colour's shifts match the oracle from the state the first colour left."""
+def test_level_parity_coarse_two_colours(shape, kind, levels, ncoarse):
+    """The coarse path with two colours (or one: every block from the same
+    state): R = S + c per block, and each colour's shifts match the oracle
+    from the state the earlier colour left."""
     H, W = shape
     alpha = 20.0 if kind == cm.MEAN else 15.0
     img = synth.piecewise_image(H, W, 9090 + H, 20, 0.08)
     f = img.f
     u, _ = run_solve(f, alpha, kind, 1)
     opts = cm.default_options(ncolors=4)
-    opts.coarse_ncolors = 2
+    opts.coarse_ncolors = ncoarse
     rng = np.random.default_rng(5)
     tot = ties = 0
     fails = []
@@ -994,47 +995,46 @@ def test_level_parity_coarse_two_colours(shape, kind, levels):
             for bj in range(nbj):
                 blk = (slice(bi * b, min((bi + 1) * b, H)), slice(bj * b, min((bj + 1) * b, W)))
                 np.testing.assert_array_equal(Rg[blk], u[blk] + np.float32(cg[bi * nbj + bj]))
-        for k in range(2):
+        for k in range(ncoarse):
             state = u.copy()
             for kk in range(k):
-                for bi, bj, r0, c0, bh, bw in blocks_of_colour(H, W, b, 2, kk):
+                for bi, bj, r0, c0, bh, bw in blocks_of_colour(H, W, b, ncoarse, kk):
                     state[r0:r0 + bh, c0:c0 + bw] += np.float32(cg[bi * nbj + bj])
-            blocks = [(bi, bj) for bi, bj, *_ in blocks_of_colour(H, W, b, 2, k)]
-            pick = rng.choice(len(blocks), size=min(16, len(blocks)), replace=False)
-            sample = {blocks[i] for i in pick}
+            sample = sample_blocks(H, W, b, ncoarse, k, 16, rng)
             cgd = {(bi, bj): cg[bi * nbj + bj] for bi, bj in sample}
             n, m, t, fl = compare_phase(state.astype(np.float64), f.astype(np.float64), cgd,
-                                        alpha, kind, b, 2, k, {}, sample=sample)
+                                        alpha, kind, b, ncoarse, k, {}, sample=sample)
             tot += n
             ties += t
             fails += fl
-    print(f"\ncoarse two colours {shape} kind={kind}: n={tot} ties={ties}")
+    print(f"\ncoarse {ncoarse} colour(s) {shape} kind={kind}: n={tot} ties={ties}")
     assert not fails, fails[:5]
     assert ties <= max(2, 0.02 * tot)
 
 
-def test_solve_two_coarse_colours_vs_oracle_and_loops():
-    """Whole solves with two coarse colours: the energy against the oracle's
-    solve with the same schedule, the device loop against the host loop, and
-    the batched solve against the single ones."""
+@pytest.mark.parametrize("ncoarse", [2, 1])
+def test_solve_two_coarse_colours_vs_oracle_and_loops(ncoarse):
+    """Whole solves with two (or one) coarse colours: the energy against the
+    oracle's solve with the same schedule, the device loop against the host
+    loop, and the batched solve against the single ones."""
     shapes = [(300, 260), (140, 150)]
     fs = [synth.piecewise_image(H, W, 44 + H, 10, 0.08).f for H, W in shapes]
     res = []
     for use_graph in (1, 0):
         opts = cm.default_options(ncolors=4, use_graph=use_graph)
-        opts.coarse_ncolors = 2
+        opts.coarse_ncolors = ncoarse
         res.append([cm.cm_solve(to_dev(f), 20.0, cm.MEAN, cycles=6, tol=0.0, options=opts)
                     for f in fs])
     for (ua, sa), (ub, sb) in zip(*res):
         assert torch.equal(ua, ub) and sa.trace() == sb.trace()
     for f, (u, st) in zip(fs, res[0]):
         uo, trace, n, _ = oracle.solve(f.astype(np.float64), 20.0, cm.MEAN, cycles=6, ncolors=4,
-                                       coarse_ncolors=2)
+                                       coarse_ncolors=ncoarse)
         Eg = oracle.energy(host(u).astype(np.float64), f.astype(np.float64), 20.0, cm.MEAN)
         assert abs(st.energy_final - Eg) <= 1e-5 * abs(Eg)
         assert abs(Eg - trace[-1]) <= 1e-3 * abs(trace[-1])
     opts = cm.default_options(ncolors=4)
-    opts.coarse_ncolors = 2
+    opts.coarse_ncolors = ncoarse
     ub, sb = cm.cm_solve_batched([to_dev(f) for f in fs], [20.0] * 2, [cm.MEAN] * 2, cycles=6,
                                  tol=0.0, options=opts)
     for (ua, sa), u2, s2 in zip(res[0], ub, sb):
@@ -1044,7 +1044,7 @@ def test_solve_two_coarse_colours_vs_oracle_and_loops():
 # ---------------------------------------------------------------------------
 # Option combinations.
 
-@pytest.mark.parametrize("sides,coarse", [(0, 2), (1, 0), (1, 2)])
+@pytest.mark.parametrize("sides,coarse", [(0, 2), (1, 0), (1, 2), (0, 1)])
 def test_batched_equals_single_with_combined_options(sides, coarse):
     """All four curvature kinds in one batch, with the paper's block sides
     and/or two coarse colours: every image bit-identical to its own solve."""

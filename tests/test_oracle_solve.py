@@ -317,3 +317,39 @@ def test_coarse_colour_count_schedule():
     u, tr, n, _ = oracle.solve(f, 20.0, oracle.MEAN, cycles=3, ncolors=4, coarse_ncolors=2)
     assert np.all(np.diff(tr) < 0)
     assert synth.psnr(u, img.clean) > synth.psnr(f, img.clean)
+
+
+def test_one_coarse_colour_is_block_jacobi():
+    """coarse_ncolors = 1: every block of a coarse level solves from the same
+    state in one phase (a block-Jacobi step): the phase equals each block's
+    own minimiser from the input state, applied to all blocks at once; the
+    cycle is its phase sequence and the solve descends and denoises."""
+    assert oracle.level_colours(4, 64, 1) == 1 and oracle.level_colours(4, 32, 1) == 4
+    assert all(oracle.block_colour(bi, bj, 1) == 0 for bi in range(5) for bj in range(7))
+    img = synth.piecewise_image(200, 170, 19, 8, 0.08)
+    f = img.f.astype(np.float64)
+    u = oracle.cycle(f, f, 20.0, oracle.MEAN, levels=6, ncolors=4)
+    for b in (64, 128):
+        up, cs = oracle.phase(u, f, 20.0, oracle.MEAN, b, 1, 0)
+        want = u.copy()
+        nbi, nbj = -(-200 // b), -(-170 // b)
+        for bi in range(nbi):
+            for bj in range(nbj):
+                r0, c0 = bi * b, bj * b
+                bh, bw = min(b, 200 - r0), min(b, 170 - c0)
+                c, _ = oracle.block_min(u, f, r0, c0, bh, bw, 20.0, oracle.MEAN)
+                assert cs[bi * nbj + bj] == c
+                want[r0:r0 + bh, c0:c0 + bw] += c
+        np.testing.assert_array_equal(up, want)
+    L = oracle.auto_levels(200, 170)
+    uc = oracle.cycle(f, f, 20.0, oracle.MEAN, ncolors=4, coarse_ncolors=1)
+    up = f.copy()
+    for j in range(1, L + 1):
+        b = oracle.level_side(j)
+        nc = 1 if b >= 64 else 4
+        for k in range(nc):
+            up, _ = oracle.phase(up, f, 20.0, oracle.MEAN, b, nc, k)
+    np.testing.assert_array_equal(uc, up)
+    u, tr, n, _ = oracle.solve(f, 20.0, oracle.MEAN, cycles=3, ncolors=4, coarse_ncolors=1)
+    assert np.all(np.diff(tr) < 0)
+    assert synth.psnr(u, img.clean) > synth.psnr(f, img.clean)
