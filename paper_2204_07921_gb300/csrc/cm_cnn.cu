@@ -2,8 +2,11 @@
 //
 // Network: six 3x3 convolutions with zero padding, channels 1 -> 32 -> 32 ->
 // 32 -> 32 -> 32 -> 1, ReLU after the first five, residual output
-// u0 = f + conv6(...).  Activations are NHWC BF16 (64 bytes per pixel per
-// layer); weights are kept in FP32 (master copy, Adam) and used in BF16;
+// u0 = f + conv6(...).  Activations are BF16, 64 bytes per pixel per layer,
+// stored plane-major within each image row: [n][y][plane q][x][8 channels],
+// plane q holding channels 8q .. 8q + 7 (act_off), so a run of pixels of
+// one plane is contiguous and a TMA box of one plane reads whole 32-byte
+// sectors.  Weights are kept in FP32 (master copy, Adam) and used in BF16;
 // every product is accumulated in FP32.
 //
 //  conv_in_kernel     1 -> 32 on CUDA cores (9 MACs per output).
@@ -104,6 +107,16 @@ __device__ __forceinline__ void cp_async_wait() {
 }
 
 __device__ __forceinline__ float bf(bf16 x) { return __bfloat162float(x); }
+
+// Activation layout (BF16, 32 channels), plane-major per image row: element
+// (pixel (n, y, x), channel c) sits at ((row 4 + c / 8) W + x) 8 + c mod 8,
+// row = n H + y.  In each row the four planes of 8 channels (16 bytes per
+// pixel) are contiguous along x, so a TMA box of one plane reads whole
+// 32-byte sectors (with pixel-major rows it took 16 bytes of each pixel's
+// 64 and fetched every sector twice).
+__host__ __device__ __forceinline__ size_t act_off(size_t row, int x, int q, int W) {
+    return ((row * 4 + (size_t)q) * (size_t)W + (size_t)x) * 8;
+}
 __device__ __forceinline__ float round_bf(float x) { return __bfloat162float(__float2bfloat16(x)); }
 
 // Tile geometry shared by the tiled kernels: tile t of image n.
@@ -123,13 +136,12 @@ __device__ __forceinline__ Tile tile_of(int t, int H, int W) {
 // Stage the (TH+2) x (TW+2) x 32 BF16 halo tile of X (zero outside the image).
 __device__ __forceinline__ void load_halo(bf16 (*s)[CS], const bf16* __restrict__ X, const Tile& t,
                                           int H, int W) {
-    const size_t img = (size_t)t.n * H * W;
     for (int i = threadIdx.x; i < HH * HW * 4; i += blockDim.x) {
         const int pix = i >> 2, q = i & 3;
         const int gy = t.y0 - 1 + pix / HW, gx = t.x0 - 1 + pix % HW;
         uint4 v = make_uint4(0u, 0u, 0u, 0u);
         if (gy >= 0 && gy < H && gx >= 0 && gx < W)
-            v = reinterpret_cast<const uint4*>(X + (img + (size_t)gy * W + gx) * C)[q];
+            v = *reinterpret_cast<const uint4*>(X + act_off((size_t)t.n * H + gy, gx, q, W));
         *reinterpret_cast<uint4*>(&s[pix][q * 8]) = v;
     }
 }
@@ -137,12 +149,12 @@ __device__ __forceinline__ void load_halo(bf16 (*s)[CS], const bf16* __restrict_
 // Stage the TH x TW x 32 tile of X (zero outside the image).
 __device__ __forceinline__ void load_tile(bf16 (*s)[CS], const bf16* __restrict__ X, const Tile& t,
                                           int H, int W) {
-    const size_t img = (size_t)t.n * H * W;
     for (int i = threadIdx.x; i < TH * TW * 4; i += blockDim.x) {
         const int pix = i >> 2, q = i & 3;
         const int gy = t.y0 + pix / TW, gx = t.x0 + pix % TW;
         uint4 v = make_uint4(0u, 0u, 0u, 0u);
-        if (gy < H && gx < W) v = reinterpret_cast<const uint4*>(X + (img + (size_t)gy * W + gx) * C)[q];
+        if (gy < H && gx < W)
+            v = *reinterpret_cast<const uint4*>(X + act_off((size_t)t.n * H + gy, gx, q, W));
         *reinterpret_cast<uint4*>(&s[pix][q * 8]) = v;
     }
 }
@@ -150,12 +162,11 @@ __device__ __forceinline__ void load_tile(bf16 (*s)[CS], const bf16* __restrict_
 // The halo tile of load_halo, staged with asynchronous copies.
 __device__ __forceinline__ void load_halo_async(bf16 (*s)[CS], const bf16* __restrict__ X,
                                                 const Tile& t, int H, int W) {
-    const size_t img = (size_t)t.n * H * W;
     for (int i = threadIdx.x; i < HH * HW * 4; i += blockDim.x) {
         const int pix = i >> 2, q = i & 3;
         const int gy = t.y0 - 1 + pix / HW, gx = t.x0 - 1 + pix % HW;
         const bool in = gy >= 0 && gy < H && gx >= 0 && gx < W;
-        const bf16* src = in ? X + (img + (size_t)gy * W + gx) * C + q * 8 : X;
+        const bf16* src = in ? X + act_off((size_t)t.n * H + gy, gx, q, W) : X;
         cp_async16(&s[pix][q * 8], src, in);
     }
 }
@@ -203,9 +214,9 @@ __global__ void __launch_bounds__(256) conv_in_kernel(const float* __restrict__ 
     __align__(16) bf16 out[C];
 #pragma unroll
     for (int o = 0; o < C; ++o) out[o] = __float2bfloat16(fmaxf(a[o], 0.0f));
-    uint4* dst = reinterpret_cast<uint4*>(Y + p * C);
 #pragma unroll
-    for (int q = 0; q < 4; ++q) dst[q] = reinterpret_cast<const uint4*>(out)[q];
+    for (int q = 0; q < 4; ++q)
+        *reinterpret_cast<uint4*>(Y + act_off(p / W, x, q, W)) = reinterpret_cast<const uint4*>(out)[q];
 }
 
 // MODE 0: Y = ReLU(conv(X) + bias).  MODE 1: Y = conv(X) * [mask_src > 0]
@@ -308,7 +319,7 @@ __global__ void __launch_bounds__(128, 4) conv_mid_kernel(const bf16* __restrict
                 for (int h = 0; h < 2; ++h) {
                     const int gx = t.x0 + g + 8 * h;
                     if (gy >= H || gx >= W) continue;
-                    const size_t pi = (img + (size_t)gy * W + gx) * C + co;
+                    const size_t pi = act_off((size_t)t.n * H + gy, gx, co >> 3, W) + (co & 7);
                     float v0 = acc[mt][nt][2 * h], v1 = acc[mt][nt][2 * h + 1];
                     if (MODE == 0) {
                         v0 = fmaxf(v0 + bias[co], 0.0f);
@@ -361,11 +372,11 @@ __global__ void __launch_bounds__(256) out_grad_kernel(const float* __restrict__
                 d[t] = scale * (u0[q] - us[q]);
             }
         }
-        const uint4* xs = reinterpret_cast<const uint4*>(X5 + p * C);
+        const size_t row = p / W;
         __align__(16) bf16 out[C];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-            const uint4 v = xs[q];
+            const uint4 v = *reinterpret_cast<const uint4*>(X5 + act_off(row, x, q, W));
             const bf16* e8 = reinterpret_cast<const bf16*>(&v);
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
@@ -376,9 +387,10 @@ __global__ void __launch_bounds__(256) out_grad_kernel(const float* __restrict__
                 out[c] = __float2bfloat16(bf(e8[j]) > 0.0f ? a : 0.0f);
             }
         }
-        uint4* dst = reinterpret_cast<uint4*>(dZ + p * C);
 #pragma unroll
-        for (int q = 0; q < 4; ++q) dst[q] = reinterpret_cast<const uint4*>(out)[q];
+        for (int q = 0; q < 4; ++q)
+            *reinterpret_cast<uint4*>(dZ + act_off(row, x, q, W)) =
+                reinterpret_cast<const uint4*>(out)[q];
     }
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, off);
@@ -599,39 +611,53 @@ __global__ void pack_kernel(const float* __restrict__ P, bf16* __restrict__ wf,
 
 // ---------------------------------------------------------------------------
 // 5th-generation tensor cores (tcgen05): the same convolutions with the
-// accumulators in tensor memory.  A work unit is a strip of TR = 6 output
-// rows x 128 columns.  Output row r is one M = 128 (pixels) x N (channels)
-// accumulator in TMEM, summed over 9 taps x 2 K-steps of 16 input channels
-// by tcgen05.mma from shared-memory operands.  The halo of the strip (8 x
-// 130 pixels) is loaded by TMA (four tile copies, one per plane of 8
-// channels, zero outside the image), so plane j holds channels 8j .. 8j + 7
-// of every pixel, 16 bytes each: 8 consecutive pixels are one 128-byte core
-// matrix of the no-swizzle K-major layout, and the operand of tap (dy, dx)
-// is that layout started dy rows and dx pixels further on (descriptor start
-// = plane + pixel x 16 B, K-direction byte offset = the plane stride,
-// M-direction byte offset = 128 B).  The weights are staged the same way
-// ([tap][plane][n] x 16 B).
+// accumulators in tensor memory.  A work unit is a strip of TR = 4 output
+// rows x 128 columns.  Output row r is one M = 128 (pixels) x NO (channels)
+// accumulator slot in TMEM.  The three vertical taps of one input row share
+// their A operand, so one tcgen05.mma of N = 3 NO (the weights of taps
+// dy = +1, 0, -1 side by side) adds that input row's contribution to three
+// output rows at once: with the slots of the strip's rows r0 - 2 .. r0 + TR + 1
+// laid out consecutively in TMEM, input row r0 - 1 + hr writes the slots
+// hr, hr + 1, hr + 2 (output rows r0 - 2 + hr .. r0 + hr), a contiguous range
+// of 3 NO columns.  Per strip: one MMA that clears the accumulator set
+// (zero operands, no accumulate), then (TR + 2) input rows x 3 horizontal
+// taps x 2 K-steps of 16 input channels = 36 MMAs of N = 96 (N = 48 for the
+// one-channel output layer).  The two outermost slots at each end collect
+// halo rows only and are not drained.  The halo of the strip (6 x 130 pixels)
+// is loaded by TMA (four tile copies, one per plane of 8 channels, zero
+// outside the image), so plane j holds channels 8j .. 8j + 7 of every pixel,
+// 16 bytes each: 8 consecutive pixels are one 128-byte core matrix of the
+// no-swizzle K-major layout, and the operand of input row hr and horizontal
+// tap dx is that layout started hr rows and dx pixels further on (descriptor
+// start = plane + pixel x 16 B, K-direction byte offset = the plane stride,
+// M-direction byte offset = 128 B).  The weights are staged the same way,
+// [dx][plane][jj NO + n] x 16 B with jj = 0, 1, 2 for dy = +1, 0, -1.
 //
 // Pipeline (one CTA per SM, persistent over strips): thread 0 waits for a
-// strip's halo, issues its 108 MMAs into one of two TMEM accumulator sets and
+// strip's halo, issues its 37 MMAs into one of two TMEM accumulator sets and
 // commits them to an mbarrier; meanwhile the four warps drain the previous
 // strip's accumulators (tcgen05.ld: warp w owns TMEM lanes 32w .. 32w + 31),
 // and as soon as that strip's MMAs are known complete its halo buffer is
 // refilled by TMA with the strip after next.  Every wait is bounded.
 
-constexpr int TR = 6, TXC = 128;                         // strip: 6 rows x 128 columns
+constexpr int TR = 4, TXC = 128;                         // strip: 4 rows x 128 columns
 constexpr int NSTAGE = 3;                                // halo buffers in flight
 constexpr int HRW = TR + 2, HCL = TXC + 2;               // halo rows / columns
+constexpr int NSLOT = TR + 4;                            // accumulator slots per set
 constexpr unsigned PLANE_DATA = HRW * HCL * 16;          // bytes of one plane
 constexpr unsigned PLANE = (PLANE_DATA + 127) & ~127u;   // plane stride (TMA: 128-byte aligned)
 constexpr unsigned HALO_BYTES = 4 * PLANE;
+// Zero operands of the clearing MMA: A = 128 pixels x 2 planes, B = up to
+// NSLOT x 32 rows x 2 planes, both read from one zero-filled region.
+constexpr unsigned ZERO_BYTES = 2 * NSLOT * 32 * 16;
 
 template <int MODE>
 constexpr int tc_no() { return MODE == 2 ? 16 : C; }
 
 template <int MODE>
 constexpr size_t tc_smem_bytes() {
-    return 1024 + NSTAGE * (size_t)HALO_BYTES + 9 * 4 * (size_t)tc_no<MODE>() * 16 + 128;
+    return 1024 + NSTAGE * (size_t)HALO_BYTES + 9 * 4 * (size_t)tc_no<MODE>() * 16 +
+           ZERO_BYTES + 128;
 }
 
 __device__ __forceinline__ uint64_t umma_sdesc(unsigned addr, unsigned lbo, unsigned sbo) {
@@ -730,24 +756,27 @@ __device__ __forceinline__ void tma_strip(unsigned halo, unsigned lbar, const CU
 #pragma unroll
     for (int j = 0; j < 4; ++j)
         asm volatile(
-            "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
-            "[%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(halo + j * PLANE),
-            "l"(reinterpret_cast<uint64_t>(tmap)), "r"(8 * j), "r"(s.x0 - 1), "r"(s.y0 - 1),
+            "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
+            "[%0], [%1, {%2, %3, %4, %5, %6}], [%7];" ::"r"(halo + j * PLANE),
+            "l"(reinterpret_cast<uint64_t>(tmap)), "r"(0), "r"(s.x0 - 1), "r"(j), "r"(s.y0 - 1),
             "r"(s.n), "r"(lbar)
             : "memory");
 }
 
 // MODE 0: Y = ReLU(conv(X) + bias).  MODE 1: Y = conv(X) * [mask_src > 0].
 // MODE 2: u0 = f + conv(X) + bias[0] (one output channel of 16 MMA columns).
-// tmap: X as (32 channels, W, H, N) BF16, box (8, 130, TR + 2, 1).  status:
+// tmap: X as (8 channels, W, 4 planes, H, N) BF16, box (8, 130, 1, TR + 2, 1).  status:
 // set to 1 if a wait timed out (the kernel then stops; results are invalid).
-// Warp-specialised: warp 4 (one lane) is the producer (TMA, MMA issue);
-// warps 0..3 drain the accumulators (warp w owns TMEM lanes 32w ..).  Strip
+// Warp-specialised: warp TC_DRAIN = 8 (one lane) is the producer (TMA, MMA
+// issue); warps 0..7 drain the accumulators: a warp reads the TMEM lanes of
+// its quarter, 32 (w mod 4) .., and warps w and w + 4 take the even and odd
+// rows of a strip, so two TMEM loads per lane quarter are in flight.  Strip
 // k uses halo buffer k % NSTAGE and TMEM set k & 1: lbar[k % NSTAGE] = halo
 // landed, mbar[k & 1] = MMAs done, tfree[k & 1] = accumulators drained (one
 // arrival per drain warp).  The halo of strip k + NSTAGE - 1 is requested as
 // soon as strip k - 1's MMAs are done, two strips ahead of its use.
-constexpr int TC_THREADS = 160;
+constexpr int TC_DRAIN = 8;                      // drain warps (two per TMEM lane quarter)
+constexpr int TC_THREADS = 32 * (TC_DRAIN + 1);
 
 template <int MODE>
 __global__ void __launch_bounds__(TC_THREADS, 1) conv_tc_kernel(
@@ -756,35 +785,47 @@ __global__ void __launch_bounds__(TC_THREADS, 1) conv_tc_kernel(
     const float* __restrict__ f, float* __restrict__ u0, int H, int W, int nunits,
     int* __restrict__ status) {
     constexpr int NO = tc_no<MODE>();
-    constexpr unsigned IDESC = umma_idesc_bf16(NO);
-    constexpr unsigned TSET = 256;   // TMEM columns per accumulator set (TR rows x NO <= 256)
-    static_assert(TR * C <= (int)TSET, "accumulator set");
+    constexpr int N3 = 3 * NO;                               // N of one MMA: three vertical taps
+    constexpr unsigned IDESC = umma_idesc_bf16(N3);
+    constexpr unsigned IDESC_ZERO = umma_idesc_bf16(NSLOT * NO);
+    constexpr unsigned TSET = 256;   // TMEM columns per accumulator set (NSLOT slots x NO <= 256)
+    static_assert(NSLOT * NO <= (int)TSET && NSLOT * NO <= 256, "accumulator set");
+    static_assert((N3 % 16) == 0 && ((NSLOT * NO) % 16) == 0, "MMA N of M = 128");
+    static_assert(NSLOT * NO * 2 * 16 <= (int)ZERO_BYTES && 128 * 2 * 16 <= (int)ZERO_BYTES,
+                  "zero operands");
     extern __shared__ unsigned char tc_raw[];
     unsigned char* tc_smem = reinterpret_cast<unsigned char*>(
         (reinterpret_cast<uintptr_t>(tc_raw) + 1023) & ~(uintptr_t)1023);
     unsigned char* halo = tc_smem;                                // NSTAGE buffers
-    unsigned char* wsm = tc_smem + NSTAGE * HALO_BYTES;           // [tap][plane][n] x 16 B
-    uint64_t* bars = reinterpret_cast<uint64_t*>(wsm + 9 * 4 * NO * 16);
+    unsigned char* wsm = tc_smem + NSTAGE * HALO_BYTES;           // [dx][plane][N3] x 16 B
+    unsigned char* zsm = wsm + 9 * 4 * NO * 16;                   // zero operands
+    uint64_t* bars = reinterpret_cast<uint64_t*>(zsm + ZERO_BYTES);
     unsigned* tslot = reinterpret_cast<unsigned*>(bars + NSTAGE + 4);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tslot + 1);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const unsigned lbar0 = smem_addr(bars), mbar0 = lbar0 + 8 * NSTAGE, tfree0 = mbar0 + 16;
-    const unsigned hbase0 = smem_addr(halo), wbase = smem_addr(wsm);
+    const unsigned hbase0 = smem_addr(halo), wbase = smem_addr(wsm), zbase = smem_addr(zsm);
 
+    // Wt: [tap][n][plane] x 16 B, tap = (dy + 1) 3 + (dx + 1); staged as
+    // [dx][plane][jj NO + n] with jj = 2 - (dy + 1)
     for (int i = tid; i < 9 * NO * 4; i += blockDim.x) {
         const int j = i & 3, n = (i >> 2) % NO, tap = (i >> 2) / NO;
-        *reinterpret_cast<uint4*>(wsm + ((tap * 4 + j) * NO + n) * 16) =
+        const int ty = tap / 3, tx = tap - 3 * ty;
+        *reinterpret_cast<uint4*>(wsm + ((tx * 4 + j) * N3 + (2 - ty) * NO + n) * 16) =
             reinterpret_cast<const uint4*>(Wt)[i];
     }
+    for (int i = tid; i < (int)(ZERO_BYTES / 16); i += blockDim.x)
+        reinterpret_cast<uint4*>(zsm)[i] = make_uint4(0u, 0u, 0u, 0u);
     if (tid == 0) {
         for (int i = 0; i < NSTAGE + 2; ++i)
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(lbar0 + 8 * i));
         for (int i = 0; i < 2; ++i)
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 4;" ::"r"(tfree0 + 8 * i));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(tfree0 + 8 * i),
+                         "r"(TC_DRAIN));
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         *abort_flag = 0;
     }
-    if (warp == 4) {
+    if (warp == TC_DRAIN) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(
             smem_addr(tslot)));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
@@ -797,7 +838,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) conv_tc_kernel(
     const int G = gridDim.x;
     const int nmine = (int)blockIdx.x < nunits ? (nunits - 1 - (int)blockIdx.x) / G + 1 : 0;
 
-    if (warp == 4) {
+    if (warp == TC_DRAIN) {
         if (lane == 0) {
             // producer: halo loads and MMAs.  issued / landed count the strips
             // whose halo load was requested / seen complete; committed the
@@ -806,7 +847,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1) conv_tc_kernel(
             for (int k = 0; k < NSTAGE && k < nmine; ++k, ++issued)
                 tma_strip(hbase0 + k * HALO_BYTES, lbar0 + 8 * k, &tmap,
                           strip_of(blockIdx.x + k * G, H, W));
-            const uint64_t bdesc0 = umma_sdesc(wbase, NO * 16, 128);
+            const uint64_t bdesc0 = umma_sdesc(wbase, N3 * 16, 128);
+            // clearing MMA: A = 128 zero pixels (plane stride 2 KB), B = NSLOT NO
+            // zero rows (plane stride NSLOT NO x 16 B)
+            const uint64_t azero = umma_sdesc(zbase, 128 * 16, 128);
+            const uint64_t bzero = umma_sdesc(zbase, NSLOT * NO * 16, 128);
             for (int k = 0; k < nmine; ++k) {
                 const int hb = k % NSTAGE, b = k & 1;
                 bool ok = mbar_wait_bounded(lbar0 + 8 * hb, (unsigned)((k / NSTAGE) & 1));
@@ -818,16 +863,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1) conv_tc_kernel(
                 }
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 const uint64_t adesc0 = umma_sdesc(hbase0 + hb * HALO_BYTES, PLANE, 128);
-                for (int r = 0; r < TR; ++r) {
-                    const unsigned d = tmem + b * TSET + (unsigned)(r * NO);
+                tc_mma(tmem + b * TSET, azero, bzero, IDESC_ZERO, 0u);
+                for (int hr = 0; hr < HRW; ++hr) {
+                    // slots hr .. hr + 2: output rows r0 - 2 + hr .. r0 + hr
+                    const unsigned d = tmem + b * TSET + (unsigned)(hr * NO);
 #pragma unroll
-                    for (int tap = 0; tap < 9; ++tap) {
-                        const unsigned pix = (unsigned)((r + tap / 3) * HCL + tap % 3);
+                    for (int tx = 0; tx < 3; ++tx) {
+                        const unsigned pix = (unsigned)(hr * HCL + tx);
 #pragma unroll
                         for (int kc = 0; kc < 2; ++kc)
                             tc_mma(d, adesc0 + ((2 * kc * PLANE + pix * 16) >> 4),
-                                   bdesc0 + (((tap * 4 + 2 * kc) * NO * 16) >> 4), IDESC,
-                                   (tap | kc) != 0);
+                                   bdesc0 + (((tx * 4 + 2 * kc) * N3 * 16) >> 4), IDESC, 1u);
                     }
                 }
                 asm volatile(
@@ -874,14 +920,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1) conv_tc_kernel(
             }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const Strip s = strip_of(blockIdx.x + k * G, H, W);
-            const int gx = s.x0 + 32 * warp + lane;
+            const int quarter = warp & 3;
+            const int gx = s.x0 + 32 * quarter + lane;
             const size_t img = (size_t)s.n * H * W;
-            const unsigned lanebase = tmem + b * TSET + ((unsigned)(32 * warp) << 16);
-            for (int r = 0; r < TR; ++r) {
+            const unsigned lanebase = tmem + b * TSET + ((unsigned)(32 * quarter) << 16);
+            for (int r = warp >> 2; r < TR; r += 2) {
                 const int gy = s.y0 + r;
                 if (MODE == 2) {
                     unsigned v;
-                    tmem_ld1(lanebase + (unsigned)(r * NO), v);
+                    tmem_ld1(lanebase + (unsigned)((r + 2) * NO), v);
                     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
                     if (gy < H && gx < W) {
                         const size_t pp = img + (size_t)gy * W + gx;
@@ -890,10 +937,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) conv_tc_kernel(
                     continue;
                 }
                 unsigned v[32];
-                tmem_ld32(lanebase + (unsigned)(r * NO), v);
+                tmem_ld32(lanebase + (unsigned)((r + 2) * NO), v);
                 asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
                 if (gy >= H || gx >= W) continue;
-                const size_t pi = (img + (size_t)gy * W + gx) * C;
+                const size_t row = (size_t)s.n * H + gy;
                 __align__(16) bf16 out[C];
                 if (MODE == 0) {
 #pragma unroll
@@ -903,14 +950,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1) conv_tc_kernel(
                     __align__(16) bf16 m[C];
 #pragma unroll
                     for (int q4 = 0; q4 < 4; ++q4)
-                        reinterpret_cast<uint4*>(m)[q4] = reinterpret_cast<const uint4*>(mask_src + pi)[q4];
+                        reinterpret_cast<uint4*>(m)[q4] =
+                            *reinterpret_cast<const uint4*>(mask_src + act_off(row, gx, q4, W));
 #pragma unroll
                     for (int o = 0; o < C; ++o)
                         out[o] = __float2bfloat16(bf(m[o]) > 0.0f ? __uint_as_float(v[o]) : 0.0f);
                 }
 #pragma unroll
                 for (int q4 = 0; q4 < 4; ++q4)
-                    reinterpret_cast<uint4*>(Y + pi)[q4] = reinterpret_cast<const uint4*>(out)[q4];
+                    *reinterpret_cast<uint4*>(Y + act_off(row, gx, q4, W)) =
+                        reinterpret_cast<const uint4*>(out)[q4];
             }
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             __syncwarp();
@@ -920,7 +969,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) conv_tc_kernel(
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (*abort_flag && tid == 0) atomicExch(status, 1);
-    if (warp == 4) {
+    if (warp == TC_DRAIN) {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem));
     }
@@ -975,17 +1024,20 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
     return fn;
 }
 
-// TMA map of an activation tensor X (N x H x W x 32 BF16) with the halo box
-// (8 channels, 130 columns, 10 rows, 1 image) of the tcgen05 convolution.
+// TMA map of an activation tensor X (the plane-major layout of act_off: 8
+// channels, W columns, 4 planes, H rows, N images) with the halo box of the
+// tcgen05 convolution: 8 channels x 130 columns of one plane x HRW rows of
+// one image, zero outside the image.
 cudaError_t act_tensor_map(CUtensorMap* m, const bf16* X, int N, int H, int W) {
     auto fn = tensor_map_encoder();
     if (!fn) return cudaErrorNotSupported;
-    const cuuint64_t dims[4] = {(cuuint64_t)C, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)N};
-    const cuuint64_t strides[3] = {(cuuint64_t)C * sizeof(bf16), (cuuint64_t)W * C * sizeof(bf16),
+    const cuuint64_t dims[5] = {8, (cuuint64_t)W, 4, (cuuint64_t)H, (cuuint64_t)N};
+    const cuuint64_t strides[4] = {(cuuint64_t)8 * sizeof(bf16), (cuuint64_t)W * 8 * sizeof(bf16),
+                                   (cuuint64_t)W * C * sizeof(bf16),
                                    (cuuint64_t)H * W * C * sizeof(bf16)};
-    const cuuint32_t box[4] = {8, (cuuint32_t)HCL, (cuuint32_t)HRW, 1};
-    const cuuint32_t es[4] = {1, 1, 1, 1};
-    const CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<bf16*>(X), dims, strides,
+    const cuuint32_t box[5] = {8, (cuuint32_t)HCL, 1, (cuuint32_t)HRW, 1};
+    const cuuint32_t es[5] = {1, 1, 1, 1, 1};
+    const CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<bf16*>(X), dims, strides,
                           box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                           CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;

@@ -96,17 +96,17 @@ def _check_gradients(gg, go, label):
 
 
 def _strips(N, H, W):
-    """Work units of the tcgen05 convolution: strips of 6 rows x 128 columns."""
-    return N * (-(-H // 6)) * (-(-W // 128))
+    """Work units of the tcgen05 convolution: strips of 4 rows x 128 columns."""
+    return N * (-(-H // 4)) * (-(-W // 128))
 
 
 # Shapes with more strips than the persistent grid has CTAs (one per SM, 152
-# on a GB300): the first gives every CTA three or four strips, so the halo
+# on a GB300): the first gives every CTA four or five strips, so the halo
 # ring wraps (strip k >= 3 reuses buffer k mod 3), both TMEM accumulator sets
 # alternate, and the halo of strip k + 2 is refilled while strip k is in the
 # tensor cores; both have W > 128 (column strips that share a halo column,
-# a ragged last column strip) and H not a multiple of 6 (a ragged last row
-# strip).
+# a ragged last column strip) and the first has H not a multiple of 4 (a
+# ragged last row strip).
 MULTI_STRIP = [(4, 250, 260), (2, 200, 300)]
 
 
