@@ -109,13 +109,16 @@ __device__ __forceinline__ void cp_async_wait() {
 __device__ __forceinline__ float bf(bf16 x) { return __bfloat162float(x); }
 
 // Activation layout (BF16, 32 channels), plane-major per image row: element
-// (pixel (n, y, x), channel c) sits at ((row 4 + c / 8) W + x) 8 + c mod 8,
-// row = n H + y.  In each row the four planes of 8 channels (16 bytes per
-// pixel) are contiguous along x, so a TMA box of one plane reads whole
-// 32-byte sectors (with pixel-major rows it took 16 bytes of each pixel's
-// 64 and fetched every sector twice).
+// (pixel (n, y, x), channel c) sits at ((row 4 + c / 8) Wp + x) 8 + c mod 8,
+// row = n H + y, Wp = W rounded up to a multiple of 4.  In each row the four
+// planes of 8 channels (16 bytes per pixel) are contiguous along x, and the
+// tensor-core convolution's TMA boxes read them in groups of 4 pixels
+// (64 bytes, two whole 32-byte sectors): a box whose innermost extent is one
+// 16-byte pixel costs a sector per pixel, twice the bytes.  The Wp - W pad
+// pixels of a row are never written; readers skip them or zero them.
+__host__ __device__ __forceinline__ int act_wp(int W) { return (W + 3) & ~3; }
 __host__ __device__ __forceinline__ size_t act_off(size_t row, int x, int q, int W) {
-    return ((row * 4 + (size_t)q) * (size_t)W + (size_t)x) * 8;
+    return ((row * 4 + (size_t)q) * (size_t)act_wp(W) + (size_t)x) * 8;
 }
 __device__ __forceinline__ float round_bf(float x) { return __bfloat162float(__float2bfloat16(x)); }
 
@@ -623,9 +626,11 @@ __global__ void pack_kernel(const float* __restrict__ P, bf16* __restrict__ wf,
 // (zero operands, no accumulate), then (TR + 2) input rows x 3 horizontal
 // taps x 2 K-steps of 16 input channels = 36 MMAs of N = 96 (N = 48 for the
 // one-channel output layer).  The two outermost slots at each end collect
-// halo rows only and are not drained.  The halo of the strip (6 x 130 pixels)
-// is loaded by TMA (four tile copies, one per plane of 8 channels, zero
-// outside the image), so plane j holds channels 8j .. 8j + 7 of every pixel,
+// halo rows only and are not drained.  The halo of the strip (6 rows x 136
+// pixels, the 130 it needs widened to whole groups of 4) is loaded by TMA
+// (four tile copies, one per plane of 8 channels, zero outside the tensor;
+// the row pad is zeroed after the copy), so plane j holds channels 8j ..
+// 8j + 7 of every pixel,
 // 16 bytes each: 8 consecutive pixels are one 128-byte core matrix of the
 // no-swizzle K-major layout, and the operand of input row hr and horizontal
 // tap dx is that layout started hr rows and dx pixels further on (descriptor
@@ -642,7 +647,10 @@ __global__ void pack_kernel(const float* __restrict__ P, bf16* __restrict__ wf,
 
 constexpr int TR = 4, TXC = 128;                         // strip: 4 rows x 128 columns
 constexpr int NSTAGE = 3;                                // halo buffers in flight
-constexpr int HRW = TR + 2, HCL = TXC + 2;               // halo rows / columns
+// The halo of a strip at columns x0 .. x0 + 127 is loaded as 34 groups of 4
+// pixels, x0 - 4 .. x0 + 131 (halo pixel i is column x0 - 4 + i), so
+// column x0 - 1 is halo pixel HOFF.
+constexpr int HRW = TR + 2, HCL = TXC + 8, HOFF = 3;     // halo rows / columns
 constexpr int NSLOT = TR + 4;                            // accumulator slots per set
 constexpr unsigned PLANE_DATA = HRW * HCL * 16;          // bytes of one plane
 constexpr unsigned PLANE = (PLANE_DATA + 127) & ~127u;   // plane stride (TMA: 128-byte aligned)
@@ -758,14 +766,15 @@ __device__ __forceinline__ void tma_strip(unsigned halo, unsigned lbar, const CU
         asm volatile(
             "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
             "[%0], [%1, {%2, %3, %4, %5, %6}], [%7];" ::"r"(halo + j * PLANE),
-            "l"(reinterpret_cast<uint64_t>(tmap)), "r"(0), "r"(s.x0 - 1), "r"(j), "r"(s.y0 - 1),
+            "l"(reinterpret_cast<uint64_t>(tmap)), "r"(0), "r"(s.x0 / 4 - 1), "r"(j), "r"(s.y0 - 1),
             "r"(s.n), "r"(lbar)
             : "memory");
 }
 
 // MODE 0: Y = ReLU(conv(X) + bias).  MODE 1: Y = conv(X) * [mask_src > 0].
 // MODE 2: u0 = f + conv(X) + bias[0] (one output channel of 16 MMA columns).
-// tmap: X as (8 channels, W, 4 planes, H, N) BF16, box (8, 130, 1, TR + 2, 1).  status:
+// tmap: X as (4 pixels x 8 channels, Wp / 4, 4 planes, H, N) BF16, box (32, 34, 1, TR + 2,
+// 1).  status:
 // set to 1 if a wait timed out (the kernel then stops; results are invalid).
 // Warp-specialised: warp TC_DRAIN = 8 (one lane) is the producer (TMA, MMA
 // issue); warps 0..7 drain the accumulators: a warp reads the TMEM lanes of
@@ -862,6 +871,22 @@ __global__ void __launch_bounds__(TC_THREADS, 1) conv_tc_kernel(
                     break;
                 }
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                if ((W & 3) != 0) {
+                    // the row pad W .. Wp - 1 lies inside the padded tensor, so
+                    // the TMA copied it (never written): zero it in the halo
+                    // before the MMAs read it as the image's right border
+                    const Strip s = strip_of(blockIdx.x + k * G, H, W);
+                    const int i0 = W - s.x0 + 4, i1 = min(act_wp(W) - s.x0 + 4, HCL);
+                    if (i0 < HCL) {
+                        unsigned char* hp = halo + hb * HALO_BYTES;
+                        for (int j = 0; j < 4; ++j)
+                            for (int hr = 0; hr < HRW; ++hr)
+                                for (int i = i0; i < i1; ++i)
+                                    *reinterpret_cast<uint4*>(hp + j * PLANE + (hr * HCL + i) * 16) =
+                                        make_uint4(0u, 0u, 0u, 0u);
+                        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    }
+                }
                 const uint64_t adesc0 = umma_sdesc(hbase0 + hb * HALO_BYTES, PLANE, 128);
                 tc_mma(tmem + b * TSET, azero, bzero, IDESC_ZERO, 0u);
                 for (int hr = 0; hr < HRW; ++hr) {
@@ -869,7 +894,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) conv_tc_kernel(
                     const unsigned d = tmem + b * TSET + (unsigned)(hr * NO);
 #pragma unroll
                     for (int tx = 0; tx < 3; ++tx) {
-                        const unsigned pix = (unsigned)(hr * HCL + tx);
+                        const unsigned pix = (unsigned)(hr * HCL + HOFF + tx);
 #pragma unroll
                         for (int kc = 0; kc < 2; ++kc)
                             tc_mma(d, adesc0 + ((2 * kc * PLANE + pix * 16) >> 4),
@@ -1031,11 +1056,13 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
 cudaError_t act_tensor_map(CUtensorMap* m, const bf16* X, int N, int H, int W) {
     auto fn = tensor_map_encoder();
     if (!fn) return cudaErrorNotSupported;
-    const cuuint64_t dims[5] = {8, (cuuint64_t)W, 4, (cuuint64_t)H, (cuuint64_t)N};
-    const cuuint64_t strides[4] = {(cuuint64_t)8 * sizeof(bf16), (cuuint64_t)W * 8 * sizeof(bf16),
-                                   (cuuint64_t)W * C * sizeof(bf16),
-                                   (cuuint64_t)H * W * C * sizeof(bf16)};
-    const cuuint32_t box[5] = {8, (cuuint32_t)HCL, 1, (cuuint32_t)HRW, 1};
+    // (32 = 4 pixels x 8 channels, Wp / 4 pixel groups, 4 planes, H, N)
+    const int Wp = act_wp(W);
+    const cuuint64_t dims[5] = {32, (cuuint64_t)(Wp / 4), 4, (cuuint64_t)H, (cuuint64_t)N};
+    const cuuint64_t strides[4] = {(cuuint64_t)32 * sizeof(bf16), (cuuint64_t)Wp * 8 * sizeof(bf16),
+                                   (cuuint64_t)Wp * C * sizeof(bf16),
+                                   (cuuint64_t)H * Wp * C * sizeof(bf16)};
+    const cuuint32_t box[5] = {32, (cuuint32_t)(HCL / 4), 1, (cuuint32_t)HRW, 1};
     const cuuint32_t es[5] = {1, 1, 1, 1, 1};
     const CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<bf16*>(X), dims, strides,
                           box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
@@ -1074,6 +1101,7 @@ namespace {
         }                                                           \
     } while (0)
 
+// npx: pixels of the padded activation rows, N H act_wp(W).
 int ensure_acts(Net* net, size_t npx) {
     if (npx <= net->cap) return CM_OK;
     for (int i = 1; i <= 5; ++i)
@@ -1184,7 +1212,7 @@ int net_forward(Net* net, const float* f, int N, int H, int W, float* u0, cudaSt
     int rc = check_images(net, f, N, H, W);
     if (rc || !u0) return rc ? rc : CM_ERR_INVALID;
     NET_CUDA(cudaSetDevice(net->device));
-    rc = ensure_acts(net, (size_t)N * H * W);
+    rc = ensure_acts(net, (size_t)N * H * act_wp(W));
     if (rc) return rc;
     return forward(net, f, N, H, W, u0, st);
 }
@@ -1194,7 +1222,7 @@ int net_forward_own(Net* net, const float* f, int N, int H, int W, cudaStream_t 
     int rc = check_images(net, f, N, H, W);
     if (rc) return rc;
     NET_CUDA(cudaSetDevice(net->device));
-    rc = ensure_acts(net, (size_t)N * H * W);
+    rc = ensure_acts(net, (size_t)N * H * act_wp(W));
     if (rc) return rc;
     return forward(net, f, N, H, W, net->u0, st);
 }

@@ -105,9 +105,10 @@ def _strips(N, H, W):
 # ring wraps (strip k >= 3 reuses buffer k mod 3), both TMEM accumulator sets
 # alternate, and the halo of strip k + 2 is refilled while strip k is in the
 # tensor cores; both have W > 128 (column strips that share a halo column,
-# a ragged last column strip) and the first has H not a multiple of 4 (a
-# ragged last row strip).
-MULTI_STRIP = [(4, 250, 260), (2, 200, 300)]
+# a ragged last column strip) and H not a multiple of 4 (a ragged last row
+# strip); the second has W not a multiple of 4, so its activation rows carry
+# a pad that the last column strip's halo zeroes.
+MULTI_STRIP = [(4, 250, 260), (2, 202, 301)]
 
 
 def _oracle_forward_out(p, f):
