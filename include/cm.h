@@ -265,7 +265,8 @@ const char* cm_net_last_error(const cm_net* net);
 /* Host FP32 parameter vector in / out; setting resets the Adam moments. */
 int cm_net_set_params(cm_net* net, const float* params_host);
 int cm_net_get_params(cm_net* net, float* params_host);
-/* u0 = f + net(f): f, u0_out device, N images of H x W, row-major. */
+/* u0 = f + net(f): f, u0_out device, N images of H x W, row-major.  Every
+ * cm_net_* call on images takes N H W < 2^31 (else CM_ERR_INVALID). */
 int cm_net_forward(cm_net* net, const float* f, int N, int H, int W, float* u0_out, void* stream);
 /* Gradient of the loss mean((u0 - u*)^2) over all N H W pixels (grad_host:
  * 37601 floats, nullable; loss_host nullable).  Synchronises `stream`. */

@@ -9,7 +9,8 @@
 // sectors.  Weights are kept in FP32 (master copy, Adam) and used in BF16;
 // every product is accumulated in FP32.
 //
-//  conv_in_kernel     1 -> 32 on CUDA cores (9 MACs per output).
+//  conv_in_kernel     1 -> 32 on CUDA cores (9 MACs per output), two pixels
+//                     per thread.
 //  conv_mid_kernel    32 -> 32 as an implicit GEMM on the tensor cores:
 //                     M = pixels (8 x 16 tiles), N = 32, K = 9 x 32;
 //                     ldmatrix + mma.sync m16n8k16 BF16 -> FP32; persistent
@@ -177,49 +178,71 @@ __device__ __forceinline__ void load_halo_async(bf16 (*s)[CS], const bf16* __res
 // ---------------------------------------------------------------------------
 // Forward kernels.
 
-__global__ void __launch_bounds__(256) conv_in_kernel(const float* __restrict__ f,
-                                                      const float* __restrict__ P,
-                                                      bf16* __restrict__ Y, int N, int H, int W) {
+// Thread: output pixels x, x + 1 of image row `row` = blockIdx.x (= n H + y),
+// x = 2 (blockIdx.y blockDim.x + threadIdx.x): the two share their 3 x 4
+// input neighbourhood and every 16-byte weight load (8 MACs per load).
+constexpr int CI_THREADS = 128, CI_PX = 2 * CI_THREADS;   // pixels of a row per CTA
+__global__ void __launch_bounds__(CI_THREADS) conv_in_kernel(const float* __restrict__ f,
+                                                             const float* __restrict__ P,
+                                                             bf16* __restrict__ Y, int H, int W) {
     __shared__ __align__(16) float sw[9 * C + C];
     for (int i = threadIdx.x; i < 9 * C + C; i += blockDim.x) sw[i] = round_bf(P[OFF_W1 + i]);
     __syncthreads();
-    const size_t total = (size_t)N * H * W;
-    const size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= total) return;
-    const int x = (int)(p % W), y = (int)((p / W) % H);
-    const size_t img = p - ((size_t)y * W + x);
-    float v[9];
+    const int row = blockIdx.x, y = row % H;
+    const int x = 2 * (blockIdx.y * blockDim.x + threadIdx.x);
+    if (x >= W) return;
+    const bool two = x + 1 < W;
+    // v[r][c]: f at image row y + r - 1, column x + c - 1 (zero outside)
+    float v[3][4];
 #pragma unroll
-    for (int t = 0; t < 9; ++t) {
-        const int yy = y + t / 3 - 1, xx = x + t % 3 - 1;
-        v[t] = (yy >= 0 && yy < H && xx >= 0 && xx < W) ? f[img + (size_t)yy * W + xx] : 0.0f;
+    for (int r = 0; r < 3; ++r) {
+        const int yy = y + r - 1;
+        const bool rin = yy >= 0 && yy < H;
+        const float* fr = f + (size_t)(rin ? row + r - 1 : row) * (size_t)W;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const int xx = x + c - 1;
+            v[r][c] = (rin && xx >= 0 && xx < W) ? fr[xx] : 0.0f;
+        }
     }
     // weights and bias four output channels per 16-byte shared load
-    float a[C];
+    float a[2][C];
 #pragma unroll
     for (int o = 0; o < C; o += 4) {
         const float4 b4 = *reinterpret_cast<const float4*>(&sw[9 * C + o]);
-        a[o] = b4.x;
-        a[o + 1] = b4.y;
-        a[o + 2] = b4.z;
-        a[o + 3] = b4.w;
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            a[k][o] = b4.x;
+            a[k][o + 1] = b4.y;
+            a[k][o + 2] = b4.z;
+            a[k][o + 3] = b4.w;
+        }
     }
 #pragma unroll
     for (int t = 0; t < 9; ++t)
 #pragma unroll
         for (int o = 0; o < C; o += 4) {
             const float4 w4 = *reinterpret_cast<const float4*>(&sw[t * C + o]);
-            a[o] = fmaf(v[t], w4.x, a[o]);
-            a[o + 1] = fmaf(v[t], w4.y, a[o + 1]);
-            a[o + 2] = fmaf(v[t], w4.z, a[o + 2]);
-            a[o + 3] = fmaf(v[t], w4.w, a[o + 3]);
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+                const float vt = v[t / 3][t % 3 + k];
+                a[k][o] = fmaf(vt, w4.x, a[k][o]);
+                a[k][o + 1] = fmaf(vt, w4.y, a[k][o + 1]);
+                a[k][o + 2] = fmaf(vt, w4.z, a[k][o + 2]);
+                a[k][o + 3] = fmaf(vt, w4.w, a[k][o + 3]);
+            }
         }
-    __align__(16) bf16 out[C];
 #pragma unroll
-    for (int o = 0; o < C; ++o) out[o] = __float2bfloat16(fmaxf(a[o], 0.0f));
+    for (int k = 0; k < 2; ++k) {
+        if (k == 1 && !two) break;
+        __align__(16) bf16 out[C];
 #pragma unroll
-    for (int q = 0; q < 4; ++q)
-        *reinterpret_cast<uint4*>(Y + act_off(p / W, x, q, W)) = reinterpret_cast<const uint4*>(out)[q];
+        for (int o = 0; o < C; ++o) out[o] = __float2bfloat16(fmaxf(a[k][o], 0.0f));
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            *reinterpret_cast<uint4*>(Y + act_off((size_t)row, x + k, q, W)) =
+                reinterpret_cast<const uint4*>(out)[q];
+    }
 }
 
 // MODE 0: Y = ReLU(conv(X) + bias).  MODE 1: Y = conv(X) * [mask_src > 0]
@@ -615,58 +638,61 @@ __global__ void pack_kernel(const float* __restrict__ P, bf16* __restrict__ wf,
 // ---------------------------------------------------------------------------
 // 5th-generation tensor cores (tcgen05): the same convolutions with the
 // accumulators in tensor memory.  A work unit is a strip of TR = 4 output
-// rows x 128 columns.  Output row r is one M = 128 (pixels) x NO (channels)
-// accumulator slot in TMEM.  The three vertical taps of one input row share
-// their A operand, so one tcgen05.mma of N = 3 NO (the weights of taps
-// dy = +1, 0, -1 side by side) adds that input row's contribution to three
-// output rows at once: with the slots of the strip's rows r0 - 2 .. r0 + TR + 1
-// laid out consecutively in TMEM, input row r0 - 1 + hr writes the slots
-// hr, hr + 1, hr + 2 (output rows r0 - 2 + hr .. r0 + hr), a contiguous range
-// of 3 NO columns.  Per strip: one MMA that clears the accumulator set
-// (zero operands, no accumulate), then (TR + 2) input rows x 3 horizontal
-// taps x 2 K-steps of 16 input channels = 36 MMAs of N = 96 (N = 48 for the
-// one-channel output layer).  The two outermost slots at each end collect
-// halo rows only and are not drained.  The halo of the strip (6 rows x 136
+// rows x 128 columns.  Output row o of the strip is one M = 128 (pixels) x NO
+// (channels) accumulator slot in TMEM, the TR slots side by side.  The three
+// vertical taps of one input row share their A operand, so one tcgen05.mma
+// with the weights of several taps side by side along N adds that input
+// row's contribution to several output rows at once: input row hr of the
+// halo (image row r0 - 1 + hr) feeds output row o = hr - 2 + jj through the
+// tap dy = 1 - jj, jj = 0, 1, 2, and the jj with 0 <= o < TR form one
+// contiguous range of slots.  So per input row, horizontal tap and K-step of
+// 16 input channels one MMA of N = NO, 2 NO or 3 NO (rows 0 and TR + 1: one
+// output row; rows 1 and TR: two; the rest: three): per strip 36 MMAs doing
+// exactly the strip's TR x 9 x 32 products, after one MMA with zero operands
+// (no accumulate) that clears the set.  The halo of the strip (6 rows x 136
 // pixels, the 130 it needs widened to whole groups of 4) is loaded by TMA
 // (four tile copies, one per plane of 8 channels, zero outside the tensor;
 // the row pad is zeroed after the copy), so plane j holds channels 8j ..
-// 8j + 7 of every pixel,
-// 16 bytes each: 8 consecutive pixels are one 128-byte core matrix of the
-// no-swizzle K-major layout, and the operand of input row hr and horizontal
-// tap dx is that layout started hr rows and dx pixels further on (descriptor
-// start = plane + pixel x 16 B, K-direction byte offset = the plane stride,
-// M-direction byte offset = 128 B).  The weights are staged the same way,
-// [dx][plane][jj NO + n] x 16 B with jj = 0, 1, 2 for dy = +1, 0, -1.
+// 8j + 7 of every pixel, 16 bytes each: 8 consecutive pixels are one
+// 128-byte core matrix of the no-swizzle K-major layout, and the operand of
+// input row hr and horizontal tap dx is that layout started hr rows and dx
+// pixels further on (descriptor start = plane + pixel x 16 B, K-direction
+// byte offset = the plane stride, M-direction byte offset = 128 B).  The
+// weights are staged the same way, [dx][plane][jj NO + n] x 16 B, so the
+// taps of a range of jj are one operand too.
 //
-// Pipeline (one CTA per SM, persistent over strips): thread 0 waits for a
-// strip's halo, issues its 37 MMAs into one of two TMEM accumulator sets and
-// commits them to an mbarrier; meanwhile the four warps drain the previous
-// strip's accumulators (tcgen05.ld: warp w owns TMEM lanes 32w .. 32w + 31),
-// and as soon as that strip's MMAs are known complete its halo buffer is
-// refilled by TMA with the strip after next.  Every wait is bounded.
+// Pipeline (one CTA per SM, persistent over strips): one thread waits for a
+// strip's halo, issues its 37 MMAs into one of NSET TMEM accumulator sets
+// and commits them to an mbarrier; meanwhile the drain warps empty the sets
+// of earlier strips (tcgen05.ld; a warp reads the TMEM lanes of its lane
+// quarter), and as soon as a strip's MMAs are known complete its halo buffer
+// is refilled by TMA with a strip NSTAGE further on.  Every wait is bounded.
 
 constexpr int TR = 4, TXC = 128;                         // strip: 4 rows x 128 columns
-constexpr int NSTAGE = 3;                                // halo buffers in flight
+constexpr int NSTAGE = 4;                                // halo buffers in flight
+constexpr int NSET = 4;                                  // TMEM accumulator sets
+constexpr unsigned TSET = 128;                           // TMEM columns per set (TR x NO)
 // The halo of a strip at columns x0 .. x0 + 127 is loaded as 34 groups of 4
 // pixels, x0 - 4 .. x0 + 131 (halo pixel i is column x0 - 4 + i), so
 // column x0 - 1 is halo pixel HOFF.
 constexpr int HRW = TR + 2, HCL = TXC + 8, HOFF = 3;     // halo rows / columns
-constexpr int NSLOT = TR + 4;                            // accumulator slots per set
 constexpr unsigned PLANE_DATA = HRW * HCL * 16;          // bytes of one plane
 constexpr unsigned PLANE = (PLANE_DATA + 127) & ~127u;   // plane stride (TMA: 128-byte aligned)
 constexpr unsigned HALO_BYTES = 4 * PLANE;
-// Zero operands of the clearing MMA: A = 128 pixels x 2 planes, B = up to
-// NSLOT x 32 rows x 2 planes, both read from one zero-filled region.
-constexpr unsigned ZERO_BYTES = 2 * NSLOT * 32 * 16;
+// Zero operands of the clearing MMA: A = 128 pixels x 2 planes, B = TR NO
+// <= 128 rows x 2 planes, both read from one zero-filled region.
+constexpr unsigned ZERO_BYTES = 2 * 128 * 16;
+static_assert(NSET * TSET <= 512 && TR * C <= (int)TSET, "TMEM accumulator sets");
 
 template <int MODE>
 constexpr int tc_no() { return MODE == 2 ? 16 : C; }
 
 template <int MODE>
 constexpr size_t tc_smem_bytes() {
-    return 1024 + NSTAGE * (size_t)HALO_BYTES + 9 * 4 * (size_t)tc_no<MODE>() * 16 +
+    return 128 + NSTAGE * (size_t)HALO_BYTES + 9 * 4 * (size_t)tc_no<MODE>() * 16 +
            ZERO_BYTES + 128;
 }
+static_assert(tc_smem_bytes<0>() <= 227 * 1024, "conv_tc shared memory");
 
 __device__ __forceinline__ uint64_t umma_sdesc(unsigned addr, unsigned lbo, unsigned sbo) {
     uint64_t d = (uint64_t)((addr & 0x3FFFFu) >> 4);
@@ -780,10 +806,12 @@ __device__ __forceinline__ void tma_strip(unsigned halo, unsigned lbar, const CU
 // issue); warps 0..7 drain the accumulators: a warp reads the TMEM lanes of
 // its quarter, 32 (w mod 4) .., and warps w and w + 4 take the even and odd
 // rows of a strip, so two TMEM loads per lane quarter are in flight.  Strip
-// k uses halo buffer k % NSTAGE and TMEM set k & 1: lbar[k % NSTAGE] = halo
-// landed, mbar[k & 1] = MMAs done, tfree[k & 1] = accumulators drained (one
-// arrival per drain warp).  The halo of strip k + NSTAGE - 1 is requested as
-// soon as strip k - 1's MMAs are done, two strips ahead of its use.
+// k uses halo buffer k % NSTAGE and TMEM set k % NSET: lbar[k % NSTAGE] =
+// halo landed, mbar[k % NSET] = MMAs done, tfree[k % NSET] = accumulators
+// drained (one arrival per drain warp), so the MMAs of strip k wait only for
+// the drain of strip k - NSET.  The halo of strip k + NSTAGE - 1 is
+// requested as soon as strip k - 1's MMAs are done, NSTAGE - 1 strips ahead
+// of its use.
 constexpr int TC_DRAIN = 8;                      // drain warps (two per TMEM lane quarter)
 constexpr int TC_THREADS = 32 * (TC_DRAIN + 1);
 
@@ -794,25 +822,20 @@ __global__ void __launch_bounds__(TC_THREADS, 1) conv_tc_kernel(
     const float* __restrict__ f, float* __restrict__ u0, int H, int W, int nunits,
     int* __restrict__ status) {
     constexpr int NO = tc_no<MODE>();
-    constexpr int N3 = 3 * NO;                               // N of one MMA: three vertical taps
-    constexpr unsigned IDESC = umma_idesc_bf16(N3);
-    constexpr unsigned IDESC_ZERO = umma_idesc_bf16(NSLOT * NO);
-    constexpr unsigned TSET = 256;   // TMEM columns per accumulator set (NSLOT slots x NO <= 256)
-    static_assert(NSLOT * NO <= (int)TSET && NSLOT * NO <= 256, "accumulator set");
-    static_assert((N3 % 16) == 0 && ((NSLOT * NO) % 16) == 0, "MMA N of M = 128");
-    static_assert(NSLOT * NO * 2 * 16 <= (int)ZERO_BYTES && 128 * 2 * 16 <= (int)ZERO_BYTES,
-                  "zero operands");
+    constexpr int N3 = 3 * NO;                               // weight rows per (dx, plane)
+    constexpr unsigned IDESC_ZERO = umma_idesc_bf16(TR * NO);
+    static_assert((NO % 16) == 0 && TR * NO <= 128, "MMA N of M = 128; zero operand rows");
     extern __shared__ unsigned char tc_raw[];
     unsigned char* tc_smem = reinterpret_cast<unsigned char*>(
-        (reinterpret_cast<uintptr_t>(tc_raw) + 1023) & ~(uintptr_t)1023);
+        (reinterpret_cast<uintptr_t>(tc_raw) + 127) & ~(uintptr_t)127);   // TMA: 128-byte aligned
     unsigned char* halo = tc_smem;                                // NSTAGE buffers
     unsigned char* wsm = tc_smem + NSTAGE * HALO_BYTES;           // [dx][plane][N3] x 16 B
     unsigned char* zsm = wsm + 9 * 4 * NO * 16;                   // zero operands
     uint64_t* bars = reinterpret_cast<uint64_t*>(zsm + ZERO_BYTES);
-    unsigned* tslot = reinterpret_cast<unsigned*>(bars + NSTAGE + 4);
+    unsigned* tslot = reinterpret_cast<unsigned*>(bars + NSTAGE + 2 * NSET);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tslot + 1);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const unsigned lbar0 = smem_addr(bars), mbar0 = lbar0 + 8 * NSTAGE, tfree0 = mbar0 + 16;
+    const unsigned lbar0 = smem_addr(bars), mbar0 = lbar0 + 8 * NSTAGE, tfree0 = mbar0 + 8 * NSET;
     const unsigned hbase0 = smem_addr(halo), wbase = smem_addr(wsm), zbase = smem_addr(zsm);
 
     // Wt: [tap][n][plane] x 16 B, tap = (dy + 1) 3 + (dx + 1); staged as
@@ -826,9 +849,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) conv_tc_kernel(
     for (int i = tid; i < (int)(ZERO_BYTES / 16); i += blockDim.x)
         reinterpret_cast<uint4*>(zsm)[i] = make_uint4(0u, 0u, 0u, 0u);
     if (tid == 0) {
-        for (int i = 0; i < NSTAGE + 2; ++i)
+        for (int i = 0; i < NSTAGE + NSET; ++i)
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(lbar0 + 8 * i));
-        for (int i = 0; i < 2; ++i)
+        for (int i = 0; i < NSET; ++i)
             asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(tfree0 + 8 * i),
                          "r"(TC_DRAIN));
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -857,15 +880,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1) conv_tc_kernel(
                 tma_strip(hbase0 + k * HALO_BYTES, lbar0 + 8 * k, &tmap,
                           strip_of(blockIdx.x + k * G, H, W));
             const uint64_t bdesc0 = umma_sdesc(wbase, N3 * 16, 128);
-            // clearing MMA: A = 128 zero pixels (plane stride 2 KB), B = NSLOT NO
-            // zero rows (plane stride NSLOT NO x 16 B)
+            // clearing MMA: A = 128 zero pixels (plane stride 2 KB), B = TR NO
+            // zero rows (plane stride TR NO x 16 B)
             const uint64_t azero = umma_sdesc(zbase, 128 * 16, 128);
-            const uint64_t bzero = umma_sdesc(zbase, NSLOT * NO * 16, 128);
+            const uint64_t bzero = umma_sdesc(zbase, TR * NO * 16, 128);
             for (int k = 0; k < nmine; ++k) {
-                const int hb = k % NSTAGE, b = k & 1;
+                const int hb = k % NSTAGE, b = k % NSET;
                 bool ok = mbar_wait_bounded(lbar0 + 8 * hb, (unsigned)((k / NSTAGE) & 1));
                 if (ok) landed = k + 1;
-                if (ok && k >= 2) ok = mbar_wait_bounded(tfree0 + 8 * b, (unsigned)(((k >> 1) - 1) & 1));
+                if (ok && k >= NSET)
+                    ok = mbar_wait_bounded(tfree0 + 8 * b, (unsigned)((k / NSET - 1) & 1));
                 if (!ok || *abort_flag) {
                     *abort_flag = 1;
                     break;
@@ -888,17 +912,23 @@ __global__ void __launch_bounds__(TC_THREADS, 1) conv_tc_kernel(
                     }
                 }
                 const uint64_t adesc0 = umma_sdesc(hbase0 + hb * HALO_BYTES, PLANE, 128);
-                tc_mma(tmem + b * TSET, azero, bzero, IDESC_ZERO, 0u);
+                const unsigned dset = tmem + b * TSET;
+                tc_mma(dset, azero, bzero, IDESC_ZERO, 0u);
+#pragma unroll
                 for (int hr = 0; hr < HRW; ++hr) {
-                    // slots hr .. hr + 2: output rows r0 - 2 + hr .. r0 + hr
-                    const unsigned d = tmem + b * TSET + (unsigned)(hr * NO);
+                    // output rows hr - 2 + jj for jj = jlo .. jhi, the ones inside
+                    // the strip: slots hr - 2 + jlo .., weight rows jlo NO ..
+                    const int jlo = hr < 2 ? 2 - hr : 0, jhi = hr > TR - 1 ? TR + 1 - hr : 2;
+                    const unsigned idesc = umma_idesc_bf16((jhi - jlo + 1) * NO);
+                    const unsigned d = dset + (unsigned)((hr - 2 + jlo) * NO);
 #pragma unroll
                     for (int tx = 0; tx < 3; ++tx) {
                         const unsigned pix = (unsigned)(hr * HCL + HOFF + tx);
 #pragma unroll
                         for (int kc = 0; kc < 2; ++kc)
                             tc_mma(d, adesc0 + ((2 * kc * PLANE + pix * 16) >> 4),
-                                   bdesc0 + (((tx * 4 + 2 * kc) * N3 * 16) >> 4), IDESC, 1u);
+                                   bdesc0 + ((((tx * 4 + 2 * kc) * N3 + jlo * NO) * 16) >> 4),
+                                   idesc, 1u);
                     }
                 }
                 asm volatile(
@@ -908,7 +938,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) conv_tc_kernel(
                 committed = k + 1;
                 // strip k - 1's MMAs done: its halo buffer takes strip k - 1 + NSTAGE
                 if (k >= 1 && k - 1 + NSTAGE < nmine) {
-                    if (!mbar_wait_bounded(mbar0 + 8 * ((k - 1) & 1), (unsigned)(((k - 1) >> 1) & 1))) {
+                    if (!mbar_wait_bounded(mbar0 + 8 * ((k - 1) % NSET),
+                                           (unsigned)(((k - 1) / NSET) & 1))) {
                         *abort_flag = 1;
                         break;
                     }
@@ -927,7 +958,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) conv_tc_kernel(
                 mbar_wait_bounded(lbar0 + 8 * (k % NSTAGE), (unsigned)((k / NSTAGE) & 1));
             if (committed > 0) {
                 const int kc = committed - 1;
-                mbar_wait_bounded(mbar0 + 8 * (kc & 1), (unsigned)((kc >> 1) & 1));
+                mbar_wait_bounded(mbar0 + 8 * (kc % NSET), (unsigned)((kc / NSET) & 1));
             }
         }
     } else {
@@ -938,8 +969,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) conv_tc_kernel(
             for (int o = 0; o < C; ++o) bias_r[o] = bias[o];
         }
         for (int k = 0; k < nmine; ++k) {
-            const int b = k & 1;
-            if (!mbar_wait_bounded(mbar0 + 8 * b, (unsigned)((k >> 1) & 1)) || *abort_flag) {
+            const int b = k % NSET;
+            if (!mbar_wait_bounded(mbar0 + 8 * b, (unsigned)((k / NSET) & 1)) || *abort_flag) {
                 *abort_flag = 1;
                 break;
             }
@@ -953,7 +984,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) conv_tc_kernel(
                 const int gy = s.y0 + r;
                 if (MODE == 2) {
                     unsigned v;
-                    tmem_ld1(lanebase + (unsigned)((r + 2) * NO), v);
+                    tmem_ld1(lanebase + (unsigned)(r * NO), v);
                     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
                     if (gy < H && gx < W) {
                         const size_t pp = img + (size_t)gy * W + gx;
@@ -962,7 +993,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) conv_tc_kernel(
                     continue;
                 }
                 unsigned v[32];
-                tmem_ld32(lanebase + (unsigned)((r + 2) * NO), v);
+                tmem_ld32(lanebase + (unsigned)(r * NO), v);
                 asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
                 if (gy >= H || gx >= W) continue;
                 const size_t row = (size_t)s.n * H + gy;
@@ -1127,7 +1158,8 @@ int pack(Net* net, cudaStream_t st) {
 
 int forward(Net* net, const float* f, int N, int H, int W, float* u0, cudaStream_t st) {
     const size_t npx = (size_t)N * H * W;
-    conv_in_kernel<<<(unsigned)((npx + 255) / 256), 256, 0, st>>>(f, net->P, net->act[1], N, H, W);
+    conv_in_kernel<<<dim3((unsigned)(N * H), (unsigned)((W + CI_PX - 1) / CI_PX)), CI_THREADS, 0, st>>>(
+        f, net->P, net->act[1], H, W);
     if (CM_CNN_TC) {
         const int nunits = N * ((H + TR - 1) / TR) * ((W + TXC - 1) / TXC);
         const int grid = std::min(nunits, net->tc_grid);
@@ -1197,8 +1229,9 @@ int backward(Net* net, const float* f, const float* us, int N, int H, int W, cud
 }
 
 int check_images(Net* net, const float* f, int N, int H, int W) {
+    // (pixels of the batch < 2^31: the kernels index rows and strips in int)
     if (!f || N < 1 || H < 1 || W < 1 || H > CM_MAX_SIDE || W > CM_MAX_SIDE ||
-        (long long)H * W > CM_MAX_PIXELS) {
+        (long long)H * W > CM_MAX_PIXELS || (long long)N * H * W > 0x7fffffffLL) {
         net->err = "invalid image arguments";
         return CM_ERR_INVALID;
     }

@@ -46,6 +46,18 @@ def dev(a):
     return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
 
 
+def test_batch_pixel_limit_is_rejected_before_any_access():
+    """N H W >= 2^31 is refused with CM_ERR_INVALID up front (the kernels
+    index rows and strips in int); the small buffer is never read."""
+    net = ws.Net(ws.init_params(1, zero_last=True))
+    f = dev(np.zeros((1, 4, 4)))
+    lib = ws._lib()
+    rc = lib.cm_net_forward(net._h, f.data_ptr(), 2 ** 27, 4, 4, f.data_ptr(), None)
+    assert rc == cm.CM_ERR_INVALID
+    assert lib.cm_net_forward(net._h, f.data_ptr(), 1, 4, 4, f.data_ptr(), None) == cm.CM_OK
+    torch.cuda.synchronize()
+
+
 def test_zero_net_returns_f_exactly():
     net = ws.Net(ws.init_params(1, zero_last=True))
     f = dev(np.random.default_rng(0).random((2, 19, 33)))
@@ -101,10 +113,10 @@ def _strips(N, H, W):
 
 
 # Shapes with more strips than the persistent grid has CTAs (one per SM, 152
-# on a GB300): the first gives every CTA four or five strips, so the halo
-# ring wraps (strip k >= 3 reuses buffer k mod 3), both TMEM accumulator sets
-# alternate, and the halo of strip k + 2 is refilled while strip k is in the
-# tensor cores; both have W > 128 (column strips that share a halo column,
+# on a GB300): the first gives most CTAs five strips, so the halo ring wraps
+# (strip 4 reuses buffer 0 of the four), the TMEM accumulator set of strip 0
+# is reused by strip 4 after its drain, and the halo of strip k + 3 is
+# refilled while strip k is in the tensor cores; both have W > 128 (column strips that share a halo column,
 # a ragged last column strip) and H not a multiple of 4 (a ragged last row
 # strip); the second has W not a multiple of 4, so its activation rows carry
 # a pad that the last column strip's halo zeroes.
@@ -128,7 +140,7 @@ def test_forward_parity_multi_strip(shape):
     nsm = torch.cuda.get_device_properties(0).multi_processor_count
     assert _strips(*shape) > nsm
     if shape == MULTI_STRIP[0]:
-        assert _strips(*shape) > 3 * nsm   # some CTAs run four strips: ring wrap + refill
+        assert _strips(*shape) > 4 * nsm   # some CTAs run five strips: ring and set wrap
     rng = np.random.default_rng(sum(shape) + 1)
     p = ws.init_params(17, zero_last=False)
     f = rng.random(shape).astype(np.float32)
