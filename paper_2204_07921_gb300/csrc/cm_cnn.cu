@@ -10,7 +10,7 @@
 // every product is accumulated in FP32.
 //
 //  conv_in_kernel     1 -> 32 on CUDA cores (9 MACs per output), two pixels
-//                     per thread.
+//                     and 16 channels per thread, persistent CTAs.
 //  conv_mid_kernel    32 -> 32 as an implicit GEMM on the tensor cores:
 //                     M = pixels (8 x 16 tiles), N = 32, K = 9 x 32;
 //                     ldmatrix + mma.sync m16n8k16 BF16 -> FP32; persistent
@@ -178,70 +178,84 @@ __device__ __forceinline__ void load_halo_async(bf16 (*s)[CS], const bf16* __res
 // ---------------------------------------------------------------------------
 // Forward kernels.
 
-// Thread: output pixels x, x + 1 of image row `row` = blockIdx.x (= n H + y),
-// x = 2 (blockIdx.y blockDim.x + threadIdx.x): the two share their 3 x 4
-// input neighbourhood and every 16-byte weight load (8 MACs per load).
-constexpr int CI_THREADS = 128, CI_PX = 2 * CI_THREADS;   // pixels of a row per CTA
-__global__ void __launch_bounds__(CI_THREADS) conv_in_kernel(const float* __restrict__ f,
-                                                             const float* __restrict__ P,
-                                                             bf16* __restrict__ Y, int H, int W) {
+// Persistent: a CTA stages the weights once and walks the work items
+// (image row `row` = n H + y, chunk of CI_PX columns) it = blockIdx.x,
+// + gridDim.x, ...  Warp w of the CTA takes the pixel pairs x, x + 1 with
+// x = 64 (w / 2) + 2 lane of the chunk and the 16 output channels 16 (w mod
+// 2) ..: a thread's two pixels share their 3 x 4 input neighbourhood and
+// every 16-byte weight load (8 MACs per load), and 16 channels keep the
+// registers low enough for eight resident CTAs.  ReLU and the BF16 rounding
+// are one conversion.
+constexpr int CI_THREADS = 128, CI_PX = 128;   // pixels of a row per work item
+constexpr int CI_PER_SM = 8;                   // resident CTAs
+__global__ void __launch_bounds__(CI_THREADS, CI_PER_SM) conv_in_kernel(
+    const float* __restrict__ f, const float* __restrict__ P, bf16* __restrict__ Y, int H, int W,
+    int nitems) {
     __shared__ __align__(16) float sw[9 * C + C];
     for (int i = threadIdx.x; i < 9 * C + C; i += blockDim.x) sw[i] = round_bf(P[OFF_W1 + i]);
     __syncthreads();
-    const int row = blockIdx.x, y = row % H;
-    const int x = 2 * (blockIdx.y * blockDim.x + threadIdx.x);
-    if (x >= W) return;
-    const bool two = x + 1 < W;
-    // v[r][c]: f at image row y + r - 1, column x + c - 1 (zero outside)
-    float v[3][4];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int c0 = 16 * (warp & 1), q0 = c0 / 8;
+    const int nchunk = (W + CI_PX - 1) / CI_PX;
+    for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+        const int row = it / nchunk, y = row % H;
+        const int x = (it - row * nchunk) * CI_PX + 64 * (warp >> 1) + 2 * lane;
+        if (x >= W) continue;
+        const bool two = x + 1 < W;
+        // v[r][c]: f at image row y + r - 1, column x + c - 1 (zero outside)
+        float v[3][4];
 #pragma unroll
-    for (int r = 0; r < 3; ++r) {
-        const int yy = y + r - 1;
-        const bool rin = yy >= 0 && yy < H;
-        const float* fr = f + (size_t)(rin ? row + r - 1 : row) * (size_t)W;
+        for (int r = 0; r < 3; ++r) {
+            const int yy = y + r - 1;
+            const bool rin = yy >= 0 && yy < H;
+            const float* fr = f + (size_t)(rin ? row + r - 1 : row) * (size_t)W;
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            const int xx = x + c - 1;
-            v[r][c] = (rin && xx >= 0 && xx < W) ? fr[xx] : 0.0f;
+            for (int c = 0; c < 4; ++c) {
+                const int xx = x + c - 1;
+                v[r][c] = (rin && xx >= 0 && xx < W) ? fr[xx] : 0.0f;
+            }
         }
-    }
-    // weights and bias four output channels per 16-byte shared load
-    float a[2][C];
+        // weights and bias four output channels per 16-byte shared load
+        float a[2][16];
 #pragma unroll
-    for (int o = 0; o < C; o += 4) {
-        const float4 b4 = *reinterpret_cast<const float4*>(&sw[9 * C + o]);
-#pragma unroll
-        for (int k = 0; k < 2; ++k) {
-            a[k][o] = b4.x;
-            a[k][o + 1] = b4.y;
-            a[k][o + 2] = b4.z;
-            a[k][o + 3] = b4.w;
-        }
-    }
-#pragma unroll
-    for (int t = 0; t < 9; ++t)
-#pragma unroll
-        for (int o = 0; o < C; o += 4) {
-            const float4 w4 = *reinterpret_cast<const float4*>(&sw[t * C + o]);
+        for (int o = 0; o < 16; o += 4) {
+            const float4 b4 = *reinterpret_cast<const float4*>(&sw[9 * C + c0 + o]);
 #pragma unroll
             for (int k = 0; k < 2; ++k) {
-                const float vt = v[t / 3][t % 3 + k];
-                a[k][o] = fmaf(vt, w4.x, a[k][o]);
-                a[k][o + 1] = fmaf(vt, w4.y, a[k][o + 1]);
-                a[k][o + 2] = fmaf(vt, w4.z, a[k][o + 2]);
-                a[k][o + 3] = fmaf(vt, w4.w, a[k][o + 3]);
+                a[k][o] = b4.x;
+                a[k][o + 1] = b4.y;
+                a[k][o + 2] = b4.z;
+                a[k][o + 3] = b4.w;
             }
         }
 #pragma unroll
-    for (int k = 0; k < 2; ++k) {
-        if (k == 1 && !two) break;
-        __align__(16) bf16 out[C];
+        for (int t = 0; t < 9; ++t)
 #pragma unroll
-        for (int o = 0; o < C; ++o) out[o] = __float2bfloat16(fmaxf(a[k][o], 0.0f));
+            for (int o = 0; o < 16; o += 4) {
+                const float4 w4 = *reinterpret_cast<const float4*>(&sw[t * C + c0 + o]);
 #pragma unroll
-        for (int q = 0; q < 4; ++q)
-            *reinterpret_cast<uint4*>(Y + act_off((size_t)row, x + k, q, W)) =
-                reinterpret_cast<const uint4*>(out)[q];
+                for (int k = 0; k < 2; ++k) {
+                    const float vt = v[t / 3][t % 3 + k];
+                    a[k][o] = fmaf(vt, w4.x, a[k][o]);
+                    a[k][o + 1] = fmaf(vt, w4.y, a[k][o + 1]);
+                    a[k][o + 2] = fmaf(vt, w4.z, a[k][o + 2]);
+                    a[k][o + 3] = fmaf(vt, w4.w, a[k][o + 3]);
+                }
+            }
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            if (k == 1 && !two) break;
+            __align__(16) unsigned out[8];   // channels c0 + 2 j (low half), c0 + 2 j + 1
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+                asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;"
+                    : "=r"(out[j])
+                    : "f"(a[k][2 * j + 1]), "f"(a[k][2 * j]));
+#pragma unroll
+            for (int q = 0; q < 2; ++q)
+                *reinterpret_cast<uint4*>(Y + act_off((size_t)row, x + k, q0 + q, W)) =
+                    reinterpret_cast<const uint4*>(out)[q];
+        }
     }
 }
 
@@ -1109,6 +1123,7 @@ struct Net {
     int step = 0;
     int conv_grid = 0;      // persistent CTAs of the mma.sync convolutions
     int tc_grid = 0;        // persistent CTAs of the tcgen05 convolutions (one per SM)
+    int ci_grid = 0;        // persistent CTAs of the first layer
     int* status = nullptr;  // device: set when a tensor-core wait timed out
     // activations (capacity in pixels)
     size_t cap = 0;
@@ -1158,8 +1173,9 @@ int pack(Net* net, cudaStream_t st) {
 
 int forward(Net* net, const float* f, int N, int H, int W, float* u0, cudaStream_t st) {
     const size_t npx = (size_t)N * H * W;
-    conv_in_kernel<<<dim3((unsigned)(N * H), (unsigned)((W + CI_PX - 1) / CI_PX)), CI_THREADS, 0, st>>>(
-        f, net->P, net->act[1], H, W);
+    const int ci_items = N * H * ((W + CI_PX - 1) / CI_PX);
+    conv_in_kernel<<<std::min(ci_items, net->ci_grid), CI_THREADS, 0, st>>>(f, net->P, net->act[1],
+                                                                           H, W, ci_items);
     if (CM_CNN_TC) {
         const int nunits = N * ((H + TR - 1) / TR) * ((W + TXC - 1) / TXC);
         const int grid = std::min(nunits, net->tc_grid);
@@ -1304,6 +1320,7 @@ int cm_net_create(cm_ctx* ctx, cm_net** out) {
         e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, net->device);
         net->conv_grid = 4 * nsm;   // four resident CTAs per SM (shared memory, registers)
         net->tc_grid = nsm;         // one CTA per SM (shared memory; one TMEM allocation)
+        net->ci_grid = cm::cnn::CI_PER_SM * nsm;
     }
     if (e == cudaSuccess) e = cudaMalloc(&net->status, sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(net->status, 0, sizeof(int));
