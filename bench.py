@@ -61,7 +61,10 @@ def parse():
     p.add_argument("--ct-only", action="store_true",
                    help="only run 2 CT reconstruction cycles at --side, 180 angles (profiling)")
     p.add_argument("--cnn-only", action="store_true",
-                   help="profiling aid: warm-start inference on 16 x 1024^2 images and exit")
+                   help="profiling aid: warm-start inference on --cnn-images 1024^2 images "
+                        "(two passes) and exit")
+    p.add_argument("--cnn-images", type=int, default=16,
+                   help="images of the --cnn-only inference (default 16)")
     p.add_argument("--phases-only", action="store_true",
                    help="profiling aid: two warm-up cycles, then one launch of every "
                         "(level, colour) phase on the image and exit")
@@ -590,11 +593,11 @@ def main():
         from paper_2204_07921_gb300 import warmstart as ws
         net = ws.Net.load(WARMSTART_PARAMS, ctx=ctx)
         F = torch.stack([torch.from_numpy(synth.warmstart_image("test", i, 1024).f)
-                         for i in range(16)]).to(dev).contiguous()
+                         for i in range(args.cnn_images)]).to(dev).contiguous()
         net.forward(F)
         net.forward(F)
         torch.cuda.synchronize()
-        print(json.dumps({"cnn_only": True, "images": 16}))
+        print(json.dumps({"cnn_only": True, "images": args.cnn_images}))
         return
 
     if args.phases_only:
