@@ -433,6 +433,42 @@ def hbm_measurement(cm, torch, synth, ctx, dev, stream, opts, flush, b1_ms, N, n
     return out
 
 
+# HBM bytes per pixel of one pass of the warm-start network: the first layer
+# reads f (4 B) and writes 32 BF16 channels (64 B); each of the four 32 -> 32
+# layers reads and writes 64 B; the output layer reads 64 B and f (4 B) and
+# writes u0 (4 B).
+CNN_BYTES_PER_PIXEL = 4 + 64 + 4 * 128 + 64 + 4 + 4
+
+
+def cnn_measurement(torch, synth, net, dev, stream, n=16, side=1024, reps=10):
+    """Inference of the warm-start network on n test images of side^2 (every
+    activation far above the L2), timed with CUDA events on the launching
+    stream after warm-up: algorithmic HBM bytes / device time against the
+    HBM peak."""
+    peak, src = measured_hbm_peak()
+    F = torch.stack([torch.from_numpy(synth.warmstart_image("test", i, side).f)
+                     for i in range(n)]).to(dev).contiguous()
+    out = torch.empty_like(F)
+    for _ in range(3):
+        net.forward(F, out=out, stream=stream)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        net.forward(F, out=out, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    by = float(CNN_BYTES_PER_PIXEL) * n * side * side
+    del F, out
+    return {"images": n, "side": side, "ms": ms, "bytes_per_pass": by,
+            "gbs": by / (ms / 1e3) / 1e9, "peak_gbs": peak, "peak_source": src,
+            "frac": by / (ms / 1e3) / 1e9 / peak,
+            "note": "whole forward (first layer on CUDA cores, four 32 -> 32 layers and the "
+                    "output layer on tcgen05); per-layer counters: "
+                    "profiles/cnn_forward_kernels_1024.md"}
+
+
 def kernels_per_cycle(opts, L):
     """Kernels of one solve cycle over levels b = 1, 2, .. 2^(L-1): one per
     colour on the levels below the coarse threshold (b < 64); one per colour
@@ -891,6 +927,7 @@ def main():
     # (512 MB write) before every timed launch, so the bytes come from HBM.
     roofline["hbm"] = hbm_measurement(cm, torch, synth, ctx, dev, stream, opts, flush,
                                       b1_ms, N, nc)
+    roofline["cnn_forward"] = cnn_measurement(torch, synth, net, dev, stream)
     roofline["solve"] = {"warm_s": sec_warm, "warm_cycles": cycles, "plain_s": sec_plain,
                          "plain_cycles": cycles_plain, "warm_vs_plain": sec_plain / sec_warm,
                          "psnr_warm_db": psnr_warm, "psnr_plain_db": psnr_plain}
