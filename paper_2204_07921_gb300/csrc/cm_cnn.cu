@@ -1094,10 +1094,10 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
     return fn;
 }
 
-// TMA map of an activation tensor X (the plane-major layout of act_off: 8
-// channels, W columns, 4 planes, H rows, N images) with the halo box of the
-// tcgen05 convolution: 8 channels x 130 columns of one plane x HRW rows of
-// one image, zero outside the image.
+// TMA map of an activation tensor X (the plane-major layout of act_off:
+// groups of 4 pixels x 8 channels, Wp / 4 groups, 4 planes, H rows, N
+// images) with the halo box of the tcgen05 convolution: 34 groups (136
+// columns) of one plane x HRW rows of one image, zero outside the tensor.
 cudaError_t act_tensor_map(CUtensorMap* m, const bf16* X, int N, int H, int W) {
     auto fn = tensor_map_encoder();
     if (!fn) return cudaErrorNotSupported;
