@@ -300,11 +300,13 @@ cm::PhaseArgs phase_args(const float* S, float* R, const float* f, int H, int W,
 // Enqueue one level of block side b (all colours) from state S into R.
 // Levels below the coarse threshold, and levels of odd side, run one phase
 // kernel per colour; coarse levels run the tile-sum / search / apply
-// sequence.  c_out (nullable) receives every block's shift.
+// sequence.  c_out (nullable) receives every block's shift.  read_colour
+// (phase kernels of b >= 2): -1 as the colour, or 0 with R == S to run the
+// level in place (cm::in_place_ok).
 cudaError_t enqueue_level(float* tsums, float* cj, const float* S, float* R, const float* f,
                           int H, int W, float alpha, int kind, int b, const cm_options& o,
                           float* c_out, const int* active, cudaStream_t st,
-                          bool sums_ready = false) {
+                          bool sums_ready = false, int read_colour = -1) {
     NvtxRange level("level b=%d", b);
     if (coarse_side(b)) {
         cm::PhaseArgs a = phase_args(S, R, f, H, W, alpha, kind, b, 0, o);
@@ -318,6 +320,7 @@ cudaError_t enqueue_level(float* tsums, float* cj, const float* S, float* R, con
         cm::PhaseArgs a = phase_args(S, R, f, H, W, alpha, kind, b, k, o);
         a.c_out = c_out;
         a.active = active;
+        a.read_colour = read_colour;
         cudaError_t e = cm::launch_phase(a, st);
         if (e != cudaSuccess) return e;
     }
@@ -330,13 +333,18 @@ int level_steps(int L, const cm_options& o) { return o.vcycle ? 2 * L - 1 : L; }
 int level_at(int step, int L) { return step < L ? step : 2 * L - 2 - step; }
 
 // Enqueue one cycle starting from buffer X (other buffer Y), then the energy
-// of the final state.  The state ends in X if `levels` is even, else in Y;
-// with end_in_x it always ends in X: an odd count runs its last level in
+// of the final state.  Levels of b >= 2 whose colouring keeps same-coloured
+// blocks out of each other's read windows (cm::in_place_ok) run in place:
+// a phase then reads the state being updated, which holds the new values of
+// the earlier colours and the old values of the rest, exactly what the
+// S / R pair of Alg. 1's snapshot gives, without the per-pixel colour test.
+// Every other level reads S and writes R, and the two swap.  With end_in_x
+// the state always ends in X: an odd count of swaps runs its last level in
 // place when that level is on the coarse path (whose phases only read S and
 // whose final apply writes each pixel from itself), else copies Y to X.
 cudaError_t enqueue_cycle(cm_ctx* ctx, float* X, float* Y, const float* f, int H, int W,
                           float alpha, int kind, int levels, const cm_options& o,
-                          cudaStream_t st, bool end_in_x = false) {
+                          cudaStream_t st, bool end_in_x = false, bool* ended_in_y = nullptr) {
     float* S = X;
     float* R = Y;
     const int nsteps = level_steps(levels, o);
@@ -344,10 +352,13 @@ cudaError_t enqueue_cycle(cm_ctx* ctx, float* X, float* Y, const float* f, int H
     for (int step = 0; step < nsteps; ++step) {
         const int b = cm::level_side(level_at(step, levels), o.block_sides);
         const bool coarse = coarse_side(b);
-        const bool in_place = end_in_x && step == nsteps - 1 && S == X && coarse;
+        const bool fine_in_place =
+            !coarse && cm::in_place_ok(b, cm::level_colours(o.ncolors, b, o.coarse_ncolors));
+        const bool in_place =
+            fine_in_place || (end_in_x && step == nsteps - 1 && S == X && coarse);
         float* out = in_place ? S : R;
         cudaError_t e = enqueue_level(ctx->tsums, ctx->cj, S, out, f, H, W, alpha, kind, b, o,
-                                      nullptr, nullptr, st, sums);
+                                      nullptr, nullptr, st, sums, fine_in_place ? 0 : -1);
         sums = coarse;
         if (e != cudaSuccess) return e;
         if (!in_place) {
@@ -362,6 +373,7 @@ cudaError_t enqueue_cycle(cm_ctx* ctx, float* X, float* Y, const float* f, int H
         if (e != cudaSuccess) return e;
         S = X;
     }
+    if (ended_in_y) *ended_in_y = S != X;
     return cm::launch_energy(S, f, H, W, alpha, kind, ctx->partials, ctx->ticket, ctx->E_dev, st);
 }
 
@@ -738,8 +750,9 @@ static int solve_impl(cm_ctx* ctx, const float* f, int H, int W, float alpha, in
         NvtxRange cyc("cycle %d", l + 1);
         float* X = bufs[cur];
         float* Y = bufs[cur ^ 1];
-        CM_CUDA(enqueue_cycle(ctx, X, Y, f, H, W, alpha, kind, L, o, st));
-        if (level_steps(L, o) & 1) cur ^= 1;
+        bool in_y = false;
+        CM_CUDA(enqueue_cycle(ctx, X, Y, f, H, W, alpha, kind, L, o, st, false, &in_y));
+        if (in_y) cur ^= 1;
         CM_CUDA(cudaMemcpyAsync(ctx->E_pinned, ctx->E_dev, sizeof(double), cudaMemcpyDeviceToHost, st));
         CM_CUDA(cudaStreamSynchronize(st));
         ++l;
@@ -1008,16 +1021,21 @@ static int solve_batched_impl(cm_ctx* ctx, int n, const float* const* f, const i
             bool sums = false;
             for (int step = 0; step < nsteps && ce == cudaSuccess; ++step) {
                 const int b = cm::level_side(level_at(step, L.L), o.block_sides);
-                ce = enqueue_level((float*)(A + L.tsums), (float*)(A + L.cj), Sb, Rb, f[i], H[i],
-                                   W[i], alpha[i], kind[i], b, o, nullptr, active_ptr(i), si,
-                                   sums);
+                // in place as in enqueue_cycle
+                const bool ip = !coarse_side(b) &&
+                                cm::in_place_ok(b, cm::level_colours(o.ncolors, b, o.coarse_ncolors));
+                ce = enqueue_level((float*)(A + L.tsums), (float*)(A + L.cj), Sb, ip ? Sb : Rb,
+                                   f[i], H[i], W[i], alpha[i], kind[i], b, o, nullptr,
+                                   active_ptr(i), si, sums, ip ? 0 : -1);
                 sums = coarse_side(b);
-                float* t = Sb;
-                Sb = Rb;
-                Rb = t;
+                if (!ip) {
+                    float* t = Sb;
+                    Sb = Rb;
+                    Rb = t;
+                }
             }
             const size_t N = (size_t)H[i] * W[i];
-            if (ce == cudaSuccess && (nsteps & 1)) ce = cm::launch_batch_copy(Sb, X, N, active_ptr(i), si);
+            if (ce == cudaSuccess && Sb != X) ce = cm::launch_batch_copy(Sb, X, N, active_ptr(i), si);
             if (ce == cudaSuccess)
                 ce = cm::launch_energy(X, f[i], H[i], W[i], alpha[i], kind[i],
                                        (double*)(A + L.partials), (unsigned int*)(A + L.ticket),

@@ -84,7 +84,21 @@ struct PhaseArgs {
     int shapes = 0;         // bit lb - 1: the alternative kernel shape of level b = 1 << lb (2 .. 32)
     float* c_out;     // nullable: per-block corrections
     const int* active = nullptr;   // nullable: kernels return at once when *active == 0
+    // Levels b >= 2 (not the coarse path): reads take R for the blocks of
+    // colours below read_colour (-1: the phase's colour).  0 with R == S runs
+    // the level in place, valid when no block's read window (the block and
+    // 2 pixels around it) reaches another block of its colour:
+    // in_place_ok(b, ncolors).
+    int read_colour = -1;
 };
+
+// A level of block side b >= 2 with p x p colours can run in place: blocks of
+// one colour are (p - 1) b >= 2 pixels apart, beyond each other's 2-pixel
+// read window (two colours: diagonal neighbours touch).
+inline bool in_place_ok(int b, int ncolors) {
+    const int p = ncolors == 4 ? 2 : ncolors == 9 ? 3 : ncolors == 16 ? 4 : 0;
+    return b >= 2 && p >= 2 && (p - 1) * b >= 2;
+}
 
 cudaError_t launch_energy(const float* u, const float* f, int H, int W, float alpha, int kind,
                           double* partials, unsigned int* ticket, double* E_out,

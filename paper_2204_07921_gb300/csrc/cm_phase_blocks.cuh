@@ -66,12 +66,15 @@ __device__ __forceinline__ void for_block_pixels(int first, int stride, int r0, 
 // this with its group's active-block number a, valid or not).  LIGHT keeps
 // the ring windows and rebuilds the affine coefficients per candidate (fewer
 // registers, more arithmetic).
+// rk: reads take R for blocks of colours below rk (the colour k, or 0 when
+// the level runs in place and S is the state being updated).
 template <int KIND, int GT, int RPT, bool LIGHT = false, bool POW2 = true>
 __device__ __forceinline__ void warp_group_block(const float* __restrict__ S,
                                                  float* __restrict__ R,
                                                  const float* __restrict__ f, int H, int W,
                                                  const SearchParams& sp, int lb, int ncol, int k,
-                                                 float* __restrict__ c_out, int a, int bs = 0) {
+                                                 int rk, float* __restrict__ c_out, int a,
+                                                 int bs = 0) {
     static_assert(GT == 4 || GT == 8 || GT == 16 || GT == 32, "warp groups only");
     const int lane = threadIdx.x % GT;
     // block side 1 << lb, or (POW2 false) bs < 1 << lb
@@ -100,7 +103,7 @@ __device__ __forceinline__ void warp_group_block(const float* __restrict__ S,
         float w[9];
         msk[t] = 0;
         has[t] = blk_on && ring_slot<POW2>(lane + t * GT, r0, r1, c0, c1, H, W, S, R, lb, ncol,
-                                           k, w, msk[t], b);
+                                           rk, w, msk[t], b);
         if constexpr (LIGHT) {
 #pragma unroll
             for (int i = 0; i < 9; ++i) win[t][i] = has[t] ? w[i] : 0.0f;
@@ -143,11 +146,11 @@ __device__ __forceinline__ void warp_group_block(const float* __restrict__ S,
 template <int KIND, int GT, int RPT, bool POW2 = true>
 __global__ void __launch_bounds__(128) phase_warp_kernel(
     const float* __restrict__ S, float* __restrict__ R, const float* __restrict__ f, int H, int W,
-    SearchParams sp, int lb, int bs, int ncol, int k, float* __restrict__ c_out,
+    SearchParams sp, int lb, int bs, int ncol, int k, int rk, float* __restrict__ c_out,
     const int* __restrict__ active) {
     if (active && *active == 0) return;
     constexpr int GPC = 128 / GT;
-    warp_group_block<KIND, GT, RPT, false, POW2>(S, R, f, H, W, sp, lb, ncol, k, c_out,
+    warp_group_block<KIND, GT, RPT, false, POW2>(S, R, f, H, W, sp, lb, ncol, k, rk, c_out,
                                                  blockIdx.x * GPC + threadIdx.x / GT, bs);
 }
 
@@ -270,7 +273,7 @@ constexpr unsigned B2_M3 = (1u << 4) | (1u << 5) | (1u << 7) | (1u << 8);   // p
 template <int KIND>
 __global__ void __launch_bounds__(128, CM_B2_MINB) phase_b2_kernel(
     const float* __restrict__ S, float* __restrict__ R, const float* __restrict__ f, int H, int W,
-    SearchParams sp, int ncol, int k, float* __restrict__ c_out,
+    SearchParams sp, int ncol, int k, int rk, float* __restrict__ c_out,
     const int* __restrict__ active) {
     if (active && *active == 0) return;
     const int a = blockIdx.x * 32 + threadIdx.x / 4;
@@ -282,7 +285,7 @@ __global__ void __launch_bounds__(128, CM_B2_MINB) phase_b2_kernel(
     const bool interior = r0 >= 2 && c0 >= 2 && r0 + 3 < H && c0 + 3 < W;
     if (!__all_sync(0xffffffffu, !blk_on || interior)) {
         // a warp with a border block runs the generic four-lane search
-        warp_group_block<KIND, 4, 4, true>(S, R, f, H, W, sp, 1, ncol, k, c_out, a);
+        warp_group_block<KIND, 4, 4, true>(S, R, f, H, W, sp, 1, ncol, k, rk, c_out, a);
         return;
     }
     // Frame of quarter 0 -> image: offset (dr, dc) from (r0, c0) rotated q
@@ -306,7 +309,7 @@ __global__ void __launch_bounds__(128, CM_B2_MINB) phase_b2_kernel(
             if (blk_on && (i < 3 || (j >= 1 && j <= 3))) {
                 int r, c;
                 img(i - 2, j - 2, r, c);
-                v[i][j] = phase_read(S, R, r, c, W, 1, ncol, k);
+                v[i][j] = phase_read(S, R, r, c, W, 1, ncol, rk);
             }
         }
     int pr, pc;
@@ -356,7 +359,7 @@ __global__ void __launch_bounds__(128, CM_B2_MINB) phase_b2_kernel(
 template <int KIND, int CT, int Q, int RPT, bool POW2 = true>
 __global__ void __cluster_dims__(Q, 1, 1) __launch_bounds__(CT) phase_cluster_kernel(
     const float* __restrict__ S, float* __restrict__ R, const float* __restrict__ f, int H, int W,
-    SearchParams sp, int lb, int bs, int ncol, int k, float* __restrict__ c_out,
+    SearchParams sp, int lb, int bs, int ncol, int k, int rk, float* __restrict__ c_out,
     const int* __restrict__ active) {
     namespace cg = cooperative_groups;
     if (active && *active == 0) return;   // uniform over the grid
@@ -435,7 +438,7 @@ __global__ void __cluster_dims__(Q, 1, 1) __launch_bounds__(CT) phase_cluster_ke
     for (int t = 0; t < RPT; ++t) {
         float w[9];
         unsigned mask = 0;
-        has[t] = ring_slot<POW2>(g + t * GT, r0, r1, c0, c1, H, W, S, R, lb, ncol, k, w, mask, b);
+        has[t] = ring_slot<POW2>(g + t * GT, r0, r1, c0, c1, H, W, S, R, lb, ncol, rk, w, mask, b);
         if (has[t]) {
             px[t] = aff_pix(w, mask);
         } else {
@@ -686,6 +689,12 @@ static cudaError_t launch_coarse_kind(const PhaseArgs& A, const float* partials,
     }
 }
 
+// Colour bound of the kernels' R reads: the phase's colour, or the
+// caller's read_colour (0 for a level run in place).
+static inline int read_colour(const PhaseArgs& A) {
+    return A.read_colour < 0 ? A.colour : A.read_colour;
+}
+
 template <int KIND, int GT, int RPT, bool POW2 = true>
 static cudaError_t launch_warp(const PhaseArgs& A, int nact, cudaStream_t st) {
     constexpr int GPC = 128 / GT;
@@ -693,7 +702,7 @@ static cudaError_t launch_warp(const PhaseArgs& A, int nact, cudaStream_t st) {
     sp.one_step = A.one_step;
     return launch_k(phase_warp_kernel<KIND, GT, RPT, POW2>, dim3((nact + GPC - 1) / GPC),
                     dim3(128), st, 1, A.S, A.R, A.f, A.H, A.W, sp, A.lb, A.bs, A.ncolors,
-                    A.colour, A.c_out, A.active);
+                    A.colour, read_colour(A), A.c_out, A.active);
 }
 
 template <int KIND, int CT, int Q, int RPT, bool POW2 = true>
@@ -701,8 +710,8 @@ static cudaError_t launch_cluster(const PhaseArgs& A, int nact, cudaStream_t st)
     SearchParams sp{A.alpha, A.G, A.K};
     sp.one_step = A.one_step;
     return launch_k(phase_cluster_kernel<KIND, CT, Q, RPT, POW2>, dim3(nact * Q), dim3(CT), st, 1,
-                    A.S, A.R, A.f, A.H, A.W, sp, A.lb, A.bs, A.ncolors, A.colour, A.c_out,
-                    A.active);
+                    A.S, A.R, A.f, A.H, A.W, sp, A.lb, A.bs, A.ncolors, A.colour,
+                    read_colour(A), A.c_out, A.active);
 }
 
 template <int KIND>
@@ -719,7 +728,7 @@ static cudaError_t launch_blocks_kind(const PhaseArgs& A, cudaStream_t st) {
                 return launch_k(phase_b2_kernel<KIND>, dim3((nact + 31) / 32), dim3(128), st, 1,
                                 A.S, A.R, A.f, A.H, A.W,
                                 SearchParams{A.alpha, A.G, A.K, 1, 4, A.one_step},
-                                A.ncolors, A.colour, A.c_out, A.active);
+                                A.ncolors, A.colour, read_colour(A), A.c_out, A.active);
             return launch_warp<KIND, CM_B2_GT, 16 / CM_B2_GT>(A, nact, st);
         case 2:
             if (alt) return launch_warp<KIND, 32, 1>(A, nact, st);
