@@ -302,6 +302,35 @@ def test_solve_equals_level_sequence_and_is_deterministic(shape):
         np.testing.assert_array_equal(ua, host(S))
 
 
+@pytest.mark.parametrize("opt", [dict(ncolors=4, coarse_ncolors=1), dict(ncolors=9),
+                                 dict(ncolors=16), dict(ncolors=0),
+                                 dict(ncolors=4, block_sides=1), dict(ncolors=4, shapes=31),
+                                 dict(ncolors=4, vcycle=1), dict(ncolors=2)])
+def test_in_place_levels_equal_the_level_chain(opt):
+    """The solve runs a level of b >= 2 in place when blocks of one colour
+    stay out of each other's read windows (four colours from b = 2, nine and
+    sixteen, the decoupled colouring); cm_level always reads S and writes R.
+    Both give the same state bit for bit: every colouring (two colours: never
+    in place), the paper's block sides, the alternative kernel shapes, the
+    V-cycle, on a ragged image (border blocks on every level)."""
+    H, W = 300, 260
+    f = synth.piecewise_image(H, W, 123, 8, 0.08).f
+    opts = cm.default_options(**opt)
+    u, st = cm.cm_solve(to_dev(f), 20.0, cm.MEAN, cycles=2, tol=0.0, options=opts)
+    L = st.levels
+    sides = opt.get("block_sides", 0)
+    seq = list(range(L)) + (list(range(L - 2, -1, -1)) if opt.get("vcycle") else [])
+    fd = to_dev(f)
+    S, R = to_dev(f), torch.empty_like(fd)
+    for _ in range(2):
+        for j in seq:
+            cm.cm_level(S, R, fd, 20.0, cm.MEAN, oracle.level_side(j + 1, sides), options=opts)
+            S, R = R, S
+    torch.cuda.synchronize()
+    assert torch.equal(u, S)
+    assert st.trace()[-1] == cm.cm_energy(S, fd, 20.0, cm.MEAN)
+
+
 @pytest.mark.parametrize("case", [((512, 512), cm.GAUSS, 15.0, (64, 128, 256)),
                                   ((1024, 1024), cm.MEAN, 20.0, (64, 512)),
                                   ((300, 260), cm.MEAN, 20.0, (64, 128)),
