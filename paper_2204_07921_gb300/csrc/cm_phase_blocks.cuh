@@ -67,10 +67,12 @@ __device__ __forceinline__ void for_block_pixels(int first, int stride, int r0, 
 // the ring windows and rebuilds the affine coefficients per candidate (fewer
 // registers, more arithmetic).
 // rk: reads take R for blocks of colours below rk (the colour k, or 0 when
-// the level runs in place and S is the state being updated).
+// the level runs in place and S is the state being updated).  S and R are
+// then one buffer, so neither is declared __restrict__ in the kernels that
+// write R (a block reads each of its own pixels before writing it, and no
+// other block of the phase reads them).
 template <int KIND, int GT, int RPT, bool LIGHT = false, bool POW2 = true>
-__device__ __forceinline__ void warp_group_block(const float* __restrict__ S,
-                                                 float* __restrict__ R,
+__device__ __forceinline__ void warp_group_block(const float* S, float* R,
                                                  const float* __restrict__ f, int H, int W,
                                                  const SearchParams& sp, int lb, int ncol, int k,
                                                  int rk, float* __restrict__ c_out, int a,
@@ -145,7 +147,7 @@ __device__ __forceinline__ void warp_group_block(const float* __restrict__ S,
 
 template <int KIND, int GT, int RPT, bool POW2 = true>
 __global__ void __launch_bounds__(128) phase_warp_kernel(
-    const float* __restrict__ S, float* __restrict__ R, const float* __restrict__ f, int H, int W,
+    const float* S, float* R, const float* __restrict__ f, int H, int W,
     SearchParams sp, int lb, int bs, int ncol, int k, int rk, float* __restrict__ c_out,
     const int* __restrict__ active) {
     if (active && *active == 0) return;
@@ -272,7 +274,7 @@ constexpr unsigned B2_M3 = (1u << 4) | (1u << 5) | (1u << 7) | (1u << 8);   // p
 
 template <int KIND>
 __global__ void __launch_bounds__(128, CM_B2_MINB) phase_b2_kernel(
-    const float* __restrict__ S, float* __restrict__ R, const float* __restrict__ f, int H, int W,
+    const float* S, float* R, const float* __restrict__ f, int H, int W,
     SearchParams sp, int ncol, int k, int rk, float* __restrict__ c_out,
     const int* __restrict__ active) {
     if (active && *active == 0) return;
@@ -358,7 +360,7 @@ __global__ void __launch_bounds__(128, CM_B2_MINB) phase_b2_kernel(
 
 template <int KIND, int CT, int Q, int RPT, bool POW2 = true>
 __global__ void __cluster_dims__(Q, 1, 1) __launch_bounds__(CT) phase_cluster_kernel(
-    const float* __restrict__ S, float* __restrict__ R, const float* __restrict__ f, int H, int W,
+    const float* S, float* R, const float* __restrict__ f, int H, int W,
     SearchParams sp, int lb, int bs, int ncol, int k, int rk, float* __restrict__ c_out,
     const int* __restrict__ active) {
     namespace cg = cooperative_groups;
