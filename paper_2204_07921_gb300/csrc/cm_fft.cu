@@ -2,10 +2,11 @@
 //
 // The 2-D transform is a pass of 1-D transforms along the rows followed by
 // a pass along the columns.  One CTA transforms L whole lines in shared
-// memory: the line is loaded in bit-reversed order and the log2(M) radix-2
-// decimation-in-time stages run in place, two at a time as radix-4 steps in
-// registers with one CTA barrier per step, so the result comes out in
-// natural order.  A column pass loads L >= 4 neighbouring columns at once, so
+// memory with radix-4 stages (radix-2 for an odd stage count), one CTA
+// barrier per stage: up to 8192 points per CTA in the self-sorting
+// (Stockham) form, two padded copies in natural order; longer lines in
+// place, loaded in bit-reversed order, as decimation-in-time stages taken
+// two at a time in registers.  A column pass loads L >= 4 neighbouring columns at once, so
 // every row segment it reads or writes is L consecutive complex values.
 //
 // Lines whose length n is not a power of two use Bluestein's chirp
@@ -41,6 +42,15 @@ constexpr int FFT_THREADS = 256;
 constexpr int FFT_TARGET_POINTS = 1024;
 constexpr int FFT_POINTS_PER_CTA = 8192;
 constexpr int FFT_MIN_COLS = 4;
+// The self-sorting kernel holds two padded copies of its lines: up to 8192
+// points per CTA (2 x 9216 x 8 bytes of shared memory); longer lines use the
+// in-place kernel.
+constexpr int FFT_STOCK_POINTS = 8192;
+constexpr int FFT_STOCK_SMEM = 2 * (FFT_STOCK_POINTS + FFT_STOCK_POINTS / 8 + 64) * 8;
+// Line pitch in the self-sorting kernel's shared memory: spad(M) + 4 float2,
+// so that the L lines of a column pass, read and written a row at a time,
+// start in different banks.
+__host__ __device__ __forceinline__ int stock_pitch(int M) { return M + (M >> 3) + 4; }
 
 struct FftAxis {
     int n = 0, M = 0, log2M = 0;
@@ -128,6 +138,134 @@ __device__ void fft_stages(float2* P, int M, int log2M, int L, const float2* __r
 
 __device__ __forceinline__ int bitrev(int i, int bits) { return (int)(__brev((unsigned)i) >> (32 - bits)); }
 
+// Self-sorting (Stockham) form, used when two copies of the CTA's lines fit
+// in shared memory: the lines stay in natural order and every stage reads
+// buffer x and writes buffer y.  A radix-4 stage combines four transforms of
+// size Ns into one of size 4 Ns: group j (k = j mod Ns) takes a_t = x[j + t M
+// / 4] w^(t k) (w = exp(-+2 pi i / (4 Ns))), a 4-point DFT, and writes b_t to
+// y[4 (j - k) + k + t Ns]; an odd stage count ends with the radix-2 stage.
+// Reads are unit-stride; shared-memory indices carry one float2 of padding
+// per 8 (spad) so that the strided writes of the first stages spread over
+// the banks.  (The in-place decimation-in-time form above loads in
+// bit-reversed order, 32 consecutive points into one bank.)
+__device__ __forceinline__ int spad(int i) { return i + (i >> 3); }
+
+// exp(-2 pi i m / M), conjugated for the inverse, 0 <= m < M, from the half
+// table tw (m >= M / 2: minus the entry m - M / 2).
+__device__ __forceinline__ float2 twid(const float2* __restrict__ tw, int m, int M, bool inverse) {
+    const int h = M >> 1;
+    float2 w = m < h ? tw[m] : tw[m - h];
+    if (m >= h) w = make_float2(-w.x, -w.y);
+    return inverse ? conjf2(w) : w;
+}
+
+// The stages over L lines of M points (line l at offset l * Mp in x and y);
+// returns the buffer that holds the result.
+__device__ float2* fft_stockham(float2* x, float2* y, int M, int log2M, int L, int Mp,
+                                const float2* __restrict__ tw, bool inverse) {
+    int Ns = 1;
+    const int Q = M >> 2;
+    for (int st = 0; st + 2 <= log2M; st += 2) {
+        const int total = L * Q;
+        for (int t = threadIdx.x; t < total; t += blockDim.x) {
+            const int l = t >> (log2M - 2), j = t & (Q - 1);
+            const int k = j & (Ns - 1);
+            const float2* xl = x + (size_t)l * Mp;
+            float2 a0 = xl[spad(j)], a1 = xl[spad(j + Q)], a2 = xl[spad(j + 2 * Q)],
+                   a3 = xl[spad(j + 3 * Q)];
+            if (Ns > 1) {
+                const int m = k * (M / (4 * Ns));   // exp(-+2 pi i t k / (4 Ns)) = twid(t m)
+                a1 = cmul(a1, twid(tw, m, M, inverse));
+                a2 = cmul(a2, twid(tw, 2 * m, M, inverse));
+                a3 = cmul(a3, twid(tw, 3 * m, M, inverse));
+            }
+            const float2 s02 = make_float2(a0.x + a2.x, a0.y + a2.y);
+            const float2 d02 = make_float2(a0.x - a2.x, a0.y - a2.y);
+            const float2 s13 = make_float2(a1.x + a3.x, a1.y + a3.y);
+            const float2 d13 = make_float2(a1.x - a3.x, a1.y - a3.y);
+            // -i d13 (forward), +i d13 (inverse)
+            const float2 r = inverse ? make_float2(-d13.y, d13.x) : make_float2(d13.y, -d13.x);
+            const int base = ((j - k) << 2) + k;
+            float2* yl = y + (size_t)l * Mp;
+            yl[spad(base)] = make_float2(s02.x + s13.x, s02.y + s13.y);
+            yl[spad(base + Ns)] = make_float2(d02.x + r.x, d02.y + r.y);
+            yl[spad(base + 2 * Ns)] = make_float2(s02.x - s13.x, s02.y - s13.y);
+            yl[spad(base + 3 * Ns)] = make_float2(d02.x - r.x, d02.y - r.y);
+        }
+        __syncthreads();
+        float2* tmp = x;
+        x = y;
+        y = tmp;
+        Ns <<= 2;
+    }
+    if (log2M & 1) {   // Ns = M / 2: k = j
+        const int hM = M >> 1;
+        const int total = L * hM;
+        for (int t = threadIdx.x; t < total; t += blockDim.x) {
+            const int l = t >> (log2M - 1), j = t & (hM - 1);
+            const float2* xl = x + (size_t)l * Mp;
+            const float2 a0 = xl[spad(j)];
+            float2 a1 = xl[spad(j + hM)];
+            if (Ns > 1) a1 = cmul(a1, twid(tw, j, M, inverse));   // exp(-+2 pi i j / M)
+            float2* yl = y + (size_t)l * Mp;
+            yl[spad(j)] = make_float2(a0.x + a1.x, a0.y + a1.y);
+            yl[spad(j + hM)] = make_float2(a0.x - a1.x, a0.y - a1.y);
+        }
+        __syncthreads();
+        x = y;
+    }
+    return x;
+}
+
+// fft_lines_kernel with the self-sorting stages: shared memory holds two
+// copies of the L lines (padded); Bluestein's two transforms need no
+// reordering in between.  Launched with one thread per radix-4 group of a
+// stage (L M / 4, at most 1024), so a column pass of few wide CTAs still
+// keeps its SMs busy.
+template <bool POW2, bool COLS>
+__global__ void __launch_bounds__(1024) fft_lines_stockham_kernel(
+    float2* __restrict__ X, int n, int M, int log2M, int L, long long elem_stride,
+    long long line_stride, int nlines, const float2* __restrict__ tw,
+    const float2* __restrict__ chirp, const float2* __restrict__ B, int inverse) {
+    extern __shared__ float2 P[];
+    const int Mp = stock_pitch(M);
+    float2* P0 = P;
+    float2* P1 = P + (size_t)L * Mp;
+    const int l0 = blockIdx.x * L;
+    const int nl = min(L, nlines - l0);
+    const bool inv = inverse != 0;
+    for (int t = threadIdx.x; t < L * M; t += blockDim.x) {
+        const int l = COLS ? t % L : t >> log2M;
+        const int e = COLS ? t / L : t & (M - 1);
+        float2 v = make_float2(0.0f, 0.0f);
+        if (l < nl && e < n) {
+            v = X[(size_t)(l0 + l) * line_stride + (size_t)e * elem_stride];
+            if (!POW2) v = cmul(v, inv ? conjf2(chirp[e]) : chirp[e]);
+        }
+        P0[(size_t)l * Mp + spad(e)] = v;
+    }
+    __syncthreads();
+    float2* R = fft_stockham(P0, P1, M, log2M, L, Mp, tw, POW2 ? inv : false);
+    if (!POW2) {
+        for (int t = threadIdx.x; t < L * M; t += blockDim.x) {
+            const int l = t >> log2M, e = t & (M - 1);
+            float2* q = R + (size_t)l * Mp + spad(e);
+            *q = cmul(*q, B[e]);
+        }
+        __syncthreads();
+        R = fft_stockham(R, R == P0 ? P1 : P0, M, log2M, L, Mp, tw, true);
+    }
+    for (int t = threadIdx.x; t < L * M; t += blockDim.x) {
+        const int l = COLS ? t % L : t >> log2M;
+        const int e = COLS ? t / L : t & (M - 1);
+        if (l < nl && e < n) {
+            float2 v = R[(size_t)l * Mp + spad(e)];
+            if (!POW2) v = cmul(v, inv ? conjf2(chirp[e]) : chirp[e]);
+            X[(size_t)(l0 + l) * line_stride + (size_t)e * elem_stride] = v;
+        }
+    }
+}
+
 // Transforms nlines lines of X (element e of line l at X[l * line_stride +
 // e * elem_stride]) in place.  COLS: the lines are columns (line_stride 1),
 // so consecutive threads take consecutive lines; else consecutive elements.
@@ -195,6 +333,18 @@ cudaError_t fft_setup() {
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(fft_lines_kernel<false, true>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(fft_lines_stockham_kernel<true, false>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, FFT_STOCK_SMEM);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(fft_lines_stockham_kernel<true, true>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, FFT_STOCK_SMEM);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(fft_lines_stockham_kernel<false, false>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, FFT_STOCK_SMEM);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(fft_lines_stockham_kernel<false, true>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, FFT_STOCK_SMEM);
     return e;
 }
 
@@ -319,6 +469,19 @@ static cudaError_t lines(const FftAxis& a, float2* X, long long elem_stride, lon
     const dim3 grid((unsigned)((nlines + L - 1) / L));
     const size_t sm = (size_t)L * a.M * sizeof(float2);
     const float2* B = inverse ? a.Bi : a.Bf;
+    const size_t sm2 = 2 * (size_t)L * stock_pitch(a.M) * sizeof(float2);
+    if ((long long)L * a.M <= FFT_STOCK_POINTS && sm2 <= (size_t)FFT_STOCK_SMEM) {
+        const int nt = std::max(32, std::min(1024, L * a.M / 4));
+        if (a.pow2)
+            fft_lines_stockham_kernel<true, COLS><<<grid, nt, sm2, st>>>(
+                X, a.n, a.M, a.log2M, L, elem_stride, line_stride, nlines, a.tw, a.chirp, B,
+                inverse ? 1 : 0);
+        else
+            fft_lines_stockham_kernel<false, COLS><<<grid, nt, sm2, st>>>(
+                X, a.n, a.M, a.log2M, L, elem_stride, line_stride, nlines, a.tw, a.chirp, B,
+                inverse ? 1 : 0);
+        return cudaGetLastError();
+    }
     if (a.pow2)
         fft_lines_kernel<true, COLS><<<grid, FFT_THREADS, sm, st>>>(
             X, a.n, a.M, a.log2M, L, elem_stride, line_stride, nlines, a.tw, a.chirp, B,
