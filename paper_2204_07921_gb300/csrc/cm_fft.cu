@@ -469,16 +469,21 @@ static cudaError_t lines(const FftAxis& a, float2* X, long long elem_stride, lon
     const dim3 grid((unsigned)((nlines + L - 1) / L));
     const size_t sm = (size_t)L * a.M * sizeof(float2);
     const float2* B = inverse ? a.Bi : a.Bf;
-    const size_t sm2 = 2 * (size_t)L * stock_pitch(a.M) * sizeof(float2);
-    if ((long long)L * a.M <= FFT_STOCK_POINTS && sm2 <= (size_t)FFT_STOCK_SMEM) {
-        const int nt = std::max(32, std::min(1024, L * a.M / 4));
+    // self-sorting kernel: fewer lines per CTA when the pass has few lines,
+    // aiming at about 256 CTAs (a column pass keeps two or more columns per
+    // CTA, so its row segments stay 16 bytes or longer)
+    const int Ls = std::min(L, std::max(COLS ? 2 : 1, nlines / 256));
+    const size_t sm2 = 2 * (size_t)Ls * stock_pitch(a.M) * sizeof(float2);
+    if ((long long)Ls * a.M <= FFT_STOCK_POINTS && sm2 <= (size_t)FFT_STOCK_SMEM) {
+        const dim3 grid2((unsigned)((nlines + Ls - 1) / Ls));
+        const int nt = std::max(32, std::min(1024, Ls * a.M / 4));
         if (a.pow2)
-            fft_lines_stockham_kernel<true, COLS><<<grid, nt, sm2, st>>>(
-                X, a.n, a.M, a.log2M, L, elem_stride, line_stride, nlines, a.tw, a.chirp, B,
+            fft_lines_stockham_kernel<true, COLS><<<grid2, nt, sm2, st>>>(
+                X, a.n, a.M, a.log2M, Ls, elem_stride, line_stride, nlines, a.tw, a.chirp, B,
                 inverse ? 1 : 0);
         else
-            fft_lines_stockham_kernel<false, COLS><<<grid, nt, sm2, st>>>(
-                X, a.n, a.M, a.log2M, L, elem_stride, line_stride, nlines, a.tw, a.chirp, B,
+            fft_lines_stockham_kernel<false, COLS><<<grid2, nt, sm2, st>>>(
+                X, a.n, a.M, a.log2M, Ls, elem_stride, line_stride, nlines, a.tw, a.chirp, B,
                 inverse ? 1 : 0);
         return cudaGetLastError();
     }
