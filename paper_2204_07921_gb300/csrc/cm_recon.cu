@@ -315,75 +315,99 @@ __device__ __forceinline__ float radon_pos(int r, int c, int H, int W, float cs,
     return fmaf(x, cs, fmaf(y, sn, half));
 }
 
-// S[a][j] = sum over pixels of weight(p, j) U[pixel].x; one thread per bin.
-// Along the dominant axis of the angle's direction, p is linear with slope
-// >= 1/sqrt(2), so only pixels whose p lies in [j - 1, j + 1) contribute: at
+// S[a][j] = sum over pixels of weight(p, j) U[pixel].x; RADON_LANES
+// consecutive lanes per bin, lane g taking the rows (or columns) g, g +
+// RADON_LANES, ..., their partial sums added by a fixed butterfly.  Along the
+// dominant axis of the angle's direction, p is linear with slope >=
+// 1/sqrt(2), so only pixels whose p lies in [j - 1, j + 1) contribute: at
 // most three per row (or column), searched in a window one pixel wider on
 // each side than the exact interval.
+constexpr int RADON_LANES = 8;
 __global__ void __launch_bounds__(RT) radon_fwd_kernel(const float2* __restrict__ U,
                                                        float* __restrict__ S, int H, int W,
                                                        int n, int D, const float* __restrict__ cs,
                                                        const float* __restrict__ sn,
                                                        const int* stop) {
-    if (stop && *stop) return;
-    const int idx = blockIdx.x * RT + threadIdx.x;
-    if (idx >= n * D) return;
-    const int a = idx / D, j = idx - a * D;
-    const float c = cs[a], sv = sn[a], half = 0.5f * (float)(D - 1);
-    const bool rows = fabsf(c) >= fabsf(sv);
-    const int outer = rows ? H : W, inner = rows ? W : H;
-    const float slope = rows ? c : sv, other = rows ? sv : c;
-    const float off_in = 0.5f * (float)(inner - 1), off_out = 0.5f * (float)(outer - 1);
-    // the window needs no exact division: it is one pixel wider on each side
-    // than the interval, and membership is decided by radon_pos itself
-    const float inv = 1.0f / slope;
+    if (stop && *stop) return;   // uniform over the grid
+    const long long gi = (long long)blockIdx.x * RT + threadIdx.x;
+    const int g = (int)(gi & (RADON_LANES - 1));
+    const long long bin = gi / RADON_LANES;
     float acc = 0.0f;
-    for (int o = 0; o < outer; ++o) {
-        const float base = fmaf((float)o - off_out, other, half);
-        float x0 = ((float)(j - 1) - base) * inv, x1 = ((float)(j + 1) - base) * inv;
-        if (x0 > x1) {
-            const float t = x0;
-            x0 = x1;
-            x1 = t;
-        }
-        const int i0 = max((int)floorf(x0 + off_in) - 1, 0);
-        const int i1 = min((int)ceilf(x1 + off_in) + 1, inner - 1);
-        for (int i = i0; i <= i1; ++i) {
-            const int r = rows ? o : i, col = rows ? i : o;
-            const float p = radon_pos(r, col, H, W, c, sv, half);
-            const float fl = floorf(p);
-            const int f = (int)fl;
-            const float w = p - fl;
-            const float v = U[(size_t)r * W + col].x;
-            if (f == j) acc = fmaf(1.0f - w, v, acc);
-            else if (f == j - 1) acc = fmaf(w, v, acc);
+    if (bin < (long long)n * D) {
+        const int idx = (int)bin;
+        const int a = idx / D, j = idx - a * D;
+        const float c = cs[a], sv = sn[a], half = 0.5f * (float)(D - 1);
+        const bool rows = fabsf(c) >= fabsf(sv);
+        const int outer = rows ? H : W, inner = rows ? W : H;
+        const float slope = rows ? c : sv, other = rows ? sv : c;
+        const float off_in = 0.5f * (float)(inner - 1), off_out = 0.5f * (float)(outer - 1);
+        // the window needs no exact division: it is one pixel wider on each side
+        // than the interval, and membership is decided by radon_pos itself
+        const float inv = 1.0f / slope;
+        for (int o = g; o < outer; o += RADON_LANES) {
+            const float base = fmaf((float)o - off_out, other, half);
+            float x0 = ((float)(j - 1) - base) * inv, x1 = ((float)(j + 1) - base) * inv;
+            if (x0 > x1) {
+                const float t = x0;
+                x0 = x1;
+                x1 = t;
+            }
+            const int i0 = max((int)floorf(x0 + off_in) - 1, 0);
+            const int i1 = min((int)ceilf(x1 + off_in) + 1, inner - 1);
+            for (int i = i0; i <= i1; ++i) {
+                const int r = rows ? o : i, col = rows ? i : o;
+                const float p = radon_pos(r, col, H, W, c, sv, half);
+                const float fl = floorf(p);
+                const int f = (int)fl;
+                const float w = p - fl;
+                const float v = U[(size_t)r * W + col].x;
+                if (f == j) acc = fmaf(1.0f - w, v, acc);
+                else if (f == j - 1) acc = fmaf(w, v, acc);
+            }
         }
     }
-    S[idx] = acc;
+#pragma unroll
+    for (int off = RADON_LANES / 2; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+    if (g == 0 && bin < (long long)n * D) S[bin] = acc;
 }
 
-// U[pixel] = scale sum_a ((1 - w) S[a][f] + w S[a][f + 1]) (imaginary part 0).
+// U[pixel] = scale sum_a ((1 - w) S[a][f] + w S[a][f + 1]) (imaginary part 0);
+// RADJ_LANES consecutive lanes per pixel, lane g taking the angles g, g +
+// RADJ_LANES, ..., their partial sums added by a fixed butterfly.  A warp
+// holds 32 / RADJ_LANES consecutive pixels and every warp runs the same
+// number of grid sweeps, so all its lanes reach the shuffles.
+constexpr int RADJ_LANES = 4;
 __global__ void __launch_bounds__(RT) radon_adj_kernel(const float* __restrict__ S,
                                                        float2* __restrict__ U, int H, int W,
                                                        int n, int D, const float* __restrict__ cs,
                                                        const float* __restrict__ sn, float scale,
                                                        const int* stop) {
-    if (stop && *stop) return;
+    if (stop && *stop) return;   // uniform over the grid
     const float half = 0.5f * (float)(D - 1);
     const size_t N = (size_t)H * W;
-    for (size_t i = (size_t)blockIdx.x * RT + threadIdx.x; i < N; i += (size_t)gridDim.x * RT) {
-        const int r = (int)(i / W), col = (int)(i - (size_t)r * W);
+    constexpr int PPW = 32 / RADJ_LANES;   // pixels per warp
+    const int g = threadIdx.x & (RADJ_LANES - 1), slot = (threadIdx.x & 31) / RADJ_LANES;
+    const size_t sweep = (size_t)gridDim.x * (RT / RADJ_LANES);
+    for (size_t w0 = (size_t)blockIdx.x * (RT / RADJ_LANES) + (threadIdx.x >> 5) * PPW; w0 < N;
+         w0 += sweep) {
+        const size_t i = w0 + slot;
         float acc = 0.0f;
-        for (int a = 0; a < n; ++a) {
-            const float p = radon_pos(r, col, H, W, cs[a], sn[a], half);
-            const float fl = floorf(p);
-            const int f = (int)fl;
-            const float w = p - fl;
-            const float* row = S + (size_t)a * D;
-            acc = fmaf(1.0f - w, row[f], acc);
-            acc = fmaf(w, row[f + 1], acc);
+        if (i < N) {
+            const int r = (int)(i / W), col = (int)(i - (size_t)r * W);
+            for (int a = g; a < n; a += RADJ_LANES) {
+                const float p = radon_pos(r, col, H, W, cs[a], sn[a], half);
+                const float fl = floorf(p);
+                const int f = (int)fl;
+                const float w = p - fl;
+                const float* row = S + (size_t)a * D;
+                acc = fmaf(1.0f - w, row[f], acc);
+                acc = fmaf(w, row[f + 1], acc);
+            }
         }
-        U[i] = make_float2(scale * acc, 0.0f);
+#pragma unroll
+        for (int off = RADJ_LANES / 2; off > 0; off >>= 1)
+            acc += __shfl_xor_sync(0xffffffffu, acc, off);
+        if (g == 0 && i < N) U[i] = make_float2(scale * acc, 0.0f);
     }
 }
 
@@ -596,15 +620,16 @@ int radon_bins(int H, int W) {
 static cudaError_t ct_forward(ReconWork* w, const ReconArgs& a, const float2* U, float* S,
                               const int* stop, cudaStream_t st) {
     const int D = radon_bins(a.H, a.W), m = a.n_angles * D;
-    radon_fwd_kernel<<<(m + RT - 1) / RT, RT, 0, st>>>(U, S, a.H, a.W, a.n_angles, D, w->cos_t,
-                                                       w->sin_t, stop);
+    const long long nt = (long long)m * RADON_LANES;
+    radon_fwd_kernel<<<(unsigned)((nt + RT - 1) / RT), RT, 0, st>>>(U, S, a.H, a.W, a.n_angles, D,
+                                                                    w->cos_t, w->sin_t, stop);
     return cudaGetLastError();
 }
 
 // CT: U <- scale R^T S.
 static cudaError_t ct_adjoint(ReconWork* w, const ReconArgs& a, const float* S, float2* U,
                               float scale, const int* stop, cudaStream_t st) {
-    radon_adj_kernel<<<grid_for((size_t)a.H * a.W), RT, 0, st>>>(
+    radon_adj_kernel<<<grid_for((size_t)a.H * a.W * RADJ_LANES), RT, 0, st>>>(
         S, U, a.H, a.W, a.n_angles, radon_bins(a.H, a.W), w->cos_t, w->sin_t, scale, stop);
     return cudaGetLastError();
 }
