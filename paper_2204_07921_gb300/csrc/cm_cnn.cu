@@ -5,21 +5,23 @@
 // u0 = f + conv6(...).  Activations are BF16, 64 bytes per pixel per layer,
 // stored plane-major within each image row: [n][y][plane q][x][8 channels],
 // plane q holding channels 8q .. 8q + 7 (act_off), so a run of pixels of
-// one plane is contiguous and a TMA box of one plane reads whole 32-byte
-// sectors.  Weights are kept in FP32 (master copy, Adam) and used in BF16;
-// every product is accumulated in FP32.
+// one plane is contiguous and a TMA box of 4-pixel groups of one plane reads
+// whole 32-byte sectors.  Weights are kept in FP32 (master copy, Adam) and
+// used in BF16; every product is accumulated in FP32.
 //
 //  conv_in_kernel     1 -> 32 on CUDA cores (9 MACs per output), two pixels
 //                     and 16 channels per thread, persistent CTAs.
-//  conv_mid_kernel    32 -> 32 as an implicit GEMM on the tensor cores:
-//                     M = pixels (8 x 16 tiles), N = 32, K = 9 x 32;
-//                     ldmatrix + mma.sync m16n8k16 BF16 -> FP32; persistent
-//                     CTAs (weights staged once) with cp.async double-
-//                     buffered halo tiles.  The same kernel computes dX of
-//                     the backward pass with the flipped, transposed weights
-//                     and the ReLU mask of the layer's input fused in the
-//                     epilogue, and the output layer 32 -> 1 with the
-//                     residual u0 = f + out (one real output column).
+//  conv_tc_kernel     32 -> 32 (and the output layer 32 -> 1 with the
+//                     residual, and dX of the backward pass with the ReLU
+//                     mask of the layer's input) on the 5th-generation
+//                     tensor cores: TMA-loaded strip halos, tcgen05.mma into
+//                     TMEM accumulators, warp-specialised and persistent
+//                     (details at the kernel).
+//  conv_mid_kernel    the same three roles as an implicit GEMM with
+//                     ldmatrix + mma.sync m16n8k16 BF16 -> FP32: M = pixels
+//                     (8 x 16 tiles), N = 32, K = 9 x 32; persistent CTAs
+//                     (weights staged once) with cp.async double-buffered
+//                     halo tiles.  Built with CM_CNN_TC=0, for comparison.
 //  dw_mid_kernel      dW = sum_p X[p + tap]^T dZ[p] on the tensor cores, per
 //                     CTA partial sums over a grid-stride set of tiles,
 //                     reduced in a fixed order (deterministic).
