@@ -22,6 +22,7 @@
 // FP32 tables; the arithmetic on the device is FP32.
 #include <cuda_runtime.h>
 #include <math.h>
+#include <stdint.h>
 
 #include <algorithm>
 #include <complex>
@@ -226,7 +227,8 @@ template <bool POW2, bool COLS>
 __global__ void __launch_bounds__(1024) fft_lines_stockham_kernel(
     float2* __restrict__ X, int n, int M, int log2M, int L, long long elem_stride,
     long long line_stride, int nlines, const float2* __restrict__ tw,
-    const float2* __restrict__ chirp, const float2* __restrict__ B, int inverse) {
+    const float2* __restrict__ chirp, const float2* __restrict__ B, int inverse,
+    const uint8_t* __restrict__ mask, float mscale) {
     extern __shared__ float2 P[];
     const int Mp = stock_pitch(M);
     float2* P0 = P;
@@ -261,7 +263,9 @@ __global__ void __launch_bounds__(1024) fft_lines_stockham_kernel(
         if (l < nl && e < n) {
             float2 v = R[(size_t)l * Mp + spad(e)];
             if (!POW2) v = cmul(v, inv ? conjf2(chirp[e]) : chirp[e]);
-            X[(size_t)(l0 + l) * line_stride + (size_t)e * elem_stride] = v;
+            const size_t o = (size_t)(l0 + l) * line_stride + (size_t)e * elem_stride;
+            if (mask) v = mask[o] ? make_float2(v.x * mscale, v.y * mscale) : make_float2(0.0f, 0.0f);
+            X[o] = v;
         }
     }
 }
@@ -273,7 +277,8 @@ template <bool POW2, bool COLS>
 __global__ void __launch_bounds__(FFT_THREADS) fft_lines_kernel(
     float2* __restrict__ X, int n, int M, int log2M, int L, long long elem_stride,
     long long line_stride, int nlines, const float2* __restrict__ tw,
-    const float2* __restrict__ chirp, const float2* __restrict__ B, int inverse) {
+    const float2* __restrict__ chirp, const float2* __restrict__ B, int inverse,
+    const uint8_t* __restrict__ mask, float mscale) {
     extern __shared__ float2 P[];
     const int l0 = blockIdx.x * L;
     const int nl = min(L, nlines - l0);
@@ -313,7 +318,9 @@ __global__ void __launch_bounds__(FFT_THREADS) fft_lines_kernel(
         if (l < nl && e < n) {
             float2 v = P[(size_t)l * M + e];
             if (!POW2) v = cmul(v, inv ? conjf2(chirp[e]) : chirp[e]);
-            X[(size_t)(l0 + l) * line_stride + (size_t)e * elem_stride] = v;
+            const size_t o = (size_t)(l0 + l) * line_stride + (size_t)e * elem_stride;
+            if (mask) v = mask[o] ? make_float2(v.x * mscale, v.y * mscale) : make_float2(0.0f, 0.0f);
+            X[o] = v;
         }
     }
 }
@@ -464,7 +471,8 @@ void fft_plan_free(FftPlan* p) {
 
 template <bool COLS>
 static cudaError_t lines(const FftAxis& a, float2* X, long long elem_stride, long long line_stride,
-                         int nlines, bool inverse, cudaStream_t st) {
+                         int nlines, bool inverse, cudaStream_t st, const uint8_t* mask = nullptr,
+                         float mscale = 1.0f) {
     const int L = COLS ? a.Lc : a.L;
     const dim3 grid((unsigned)((nlines + L - 1) / L));
     const size_t sm = (size_t)L * a.M * sizeof(float2);
@@ -480,30 +488,36 @@ static cudaError_t lines(const FftAxis& a, float2* X, long long elem_stride, lon
         if (a.pow2)
             fft_lines_stockham_kernel<true, COLS><<<grid2, nt, sm2, st>>>(
                 X, a.n, a.M, a.log2M, Ls, elem_stride, line_stride, nlines, a.tw, a.chirp, B,
-                inverse ? 1 : 0);
+                inverse ? 1 : 0, mask, mscale);
         else
             fft_lines_stockham_kernel<false, COLS><<<grid2, nt, sm2, st>>>(
                 X, a.n, a.M, a.log2M, Ls, elem_stride, line_stride, nlines, a.tw, a.chirp, B,
-                inverse ? 1 : 0);
+                inverse ? 1 : 0, mask, mscale);
         return cudaGetLastError();
     }
     if (a.pow2)
         fft_lines_kernel<true, COLS><<<grid, FFT_THREADS, sm, st>>>(
             X, a.n, a.M, a.log2M, L, elem_stride, line_stride, nlines, a.tw, a.chirp, B,
-            inverse ? 1 : 0);
+            inverse ? 1 : 0, mask, mscale);
     else
         fft_lines_kernel<false, COLS><<<grid, FFT_THREADS, sm, st>>>(
             X, a.n, a.M, a.log2M, L, elem_stride, line_stride, nlines, a.tw, a.chirp, B,
-            inverse ? 1 : 0);
+            inverse ? 1 : 0, mask, mscale);
     return cudaGetLastError();
 }
 
-cudaError_t fft2d(const FftPlan& p, float2* X, bool inverse, cudaStream_t st) {
+cudaError_t fft2d(const FftPlan& p, float2* X, bool inverse, cudaStream_t st, const uint8_t* mask,
+                  float mscale) {
     if (!p.rows || !p.cols) return cudaErrorInvalidValue;
-    // a line of length 1 is its own transform
+    // a line of length 1 is its own transform; the mask goes with the last
+    // pass (the columns, or the rows of a one-row image)
     cudaError_t e = cudaSuccess;
-    if (p.W > 1) e = lines<false>(*p.rows, X, 1, p.W, p.H, inverse, st);
-    if (e == cudaSuccess && p.H > 1) e = lines<true>(*p.cols, X, p.W, 1, p.W, inverse, st);
+    const bool cols = p.H > 1;
+    if (p.W > 1)
+        e = lines<false>(*p.rows, X, 1, p.W, p.H, inverse, st, cols ? nullptr : mask, mscale);
+    if (e == cudaSuccess && cols) e = lines<true>(*p.cols, X, p.W, 1, p.W, inverse, st, mask, mscale);
+    if (e == cudaSuccess && mask && p.H == 1 && p.W == 1)   // no pass ran: a 1 x 1 image
+        e = cudaErrorInvalidValue;
     return e;
 }
 

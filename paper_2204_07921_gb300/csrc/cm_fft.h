@@ -2,6 +2,7 @@
 // A = M F of the reconstruction extension (Sec. 5): host side of cm_fft.cu.
 #pragma once
 #include <cuda_runtime.h>
+#include <stdint.h>
 
 namespace cm {
 
@@ -30,9 +31,13 @@ void fft_plan_free(FftPlan* p);
 
 // In place, on `st`: X (H x W complex, row-major) <- its unnormalised 2-D
 // DFT, X[k, l] = sum_{r, c} X[r, c] exp(-+2 pi i (k r / H + l c / W)), the
-// minus sign for the forward transform, the plus sign for the inverse.  No
-// allocation; the launches can be captured in a CUDA graph.
-cudaError_t fft2d(const FftPlan& p, float2* X, bool inverse, cudaStream_t st);
+// minus sign for the forward transform, the plus sign for the inverse.  With
+// mask (H x W, nullable) every output entry is then multiplied by mscale
+// where mask is nonzero and set to 0 elsewhere, in the last pass's store
+// (H W > 1: a 1 x 1 image has no pass, and a mask is then refused).
+// No allocation; the launches can be captured in a CUDA graph.
+cudaError_t fft2d(const FftPlan& p, float2* X, bool inverse, cudaStream_t st,
+                  const uint8_t* mask = nullptr, float mscale = 1.0f);
 
 // Dynamic shared memory of the line kernels above 48 KB (once per process).
 cudaError_t fft_setup();

@@ -718,8 +718,15 @@ static cudaError_t enqueue_cycle(ReconWork* w, const ReconArgs& a, cudaStream_t 
                 double* rr_next = w->scal + ((it + 1) & 1);
                 scatter_kernel<<<gN, RT, 0, st>>>(w->p, w->Z, a.H, a.W, b, nc, k, rr, w->stop);
                 if (a.op == RECON_MRI) {
-                    if ((e = fft(w, w->Z, FFT_FORWARD, st)) != cudaSuccess) return e;
-                    mask_scale_kernel<<<gN, RT, 0, st>>>(w->Z, a.mask, N, s2, w->stop);
+                    // M Z s2 in the forward transform's last store (N > 1);
+                    // with the CG stopped its result is not read
+                    if (N > 1) {
+                        if ((e = fft2d(w->plan, w->Z, false, st, a.mask, s2)) != cudaSuccess)
+                            return e;
+                    } else {
+                        if ((e = fft(w, w->Z, FFT_FORWARD, st)) != cudaSuccess) return e;
+                        mask_scale_kernel<<<gN, RT, 0, st>>>(w->Z, a.mask, N, s2, w->stop);
+                    }
                     if ((e = fft(w, w->Z, FFT_INVERSE, st)) != cudaSuccess) return e;
                 } else {
                     if ((e = ct_forward(w, a, w->Z, w->S, w->stop, st)) != cudaSuccess) return e;
